@@ -1,0 +1,267 @@
+"""Pins of the oracle's Debye-Hueckel solve (Sec. 4.3, 5.3-5.5) and of the EDL
+field / body force (Sec. 5.6).  CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_08741_gb300 import workloads as W
+
+
+def _wl(dims, periodic, kappa, particles=(), pot_bc=(0,) * 6, pot_val=(0.0,) * 6, levels=1,
+        res_rf=1e-14, max_cycles=400, E=(0.0, 0.0, 0.0)):
+    wl = W.Workload(name="pot", dims=list(dims), periodic=periodic, tau=1.0, kappa=kappa, eps=1.0,
+                    E_ext=E, levels=levels, res_rf=res_rf, max_cycles=max_cycles, pot_bc=pot_bc,
+                    pot_val=pot_val, coarse_sweeps=40)
+    n = len(particles)
+    if n:
+        wl.x = np.array([p[0] for p in particles], dtype=float).reshape(n, 3)
+        wl.v = np.zeros((n, 3))
+        wl.w = np.zeros((n, 3))
+        wl.R = np.array([p[1] for p in particles], dtype=float)
+        wl.kind = np.array([p[2] for p in particles], dtype=np.int32)
+        wl.zeta = np.array([p[3] for p in particles], dtype=float)
+        wl.q = np.array([p[4] for p in particles], dtype=float)
+    return wl
+
+
+def _dense_system(dims, periodic, kappa, owner, kinds, zetas, qs, pot_bc, pot_val):
+    """Assemble the finite-volume system of Sec. 4.3 directly: for every fluid
+    cell, the flux through each face is the central difference of Eq.
+    NormalFlux; a face to a Dirichlet cell uses the boundary value linearly
+    extrapolated to that cell, a face to a Neumann cell the prescribed flux,
+    a zero-flux wall no flux (Sec. 5.4).  Neumann particles spread their
+    charge evenly over their faces."""
+    nx, ny, nz = dims
+    idx = -np.ones(owner.shape, dtype=int)
+    cells = [(k, j, i) for k in range(nz) for j in range(ny) for i in range(nx) if owner[k, j, i] < 0]
+    for n, c in enumerate(cells):
+        idx[c] = n
+    faces = {}
+    for (k, j, i) in cells:
+        for d in range(6):
+            ax, s = d // 2, (1 if d % 2 else -1)
+            p = [i, j, k]
+            p[ax] += s
+            if 0 <= p[ax] < dims[ax] or periodic[ax]:
+                p[ax] %= dims[ax]
+                o = owner[p[2], p[1], p[0]]
+                if o >= 0:
+                    faces[o] = faces.get(o, 0) + 1
+    A = np.zeros((len(cells), len(cells)))
+    b = np.zeros(len(cells))
+    for n, (k, j, i) in enumerate(cells):
+        A[n, n] += kappa ** 2
+        for d in range(6):
+            ax, s = d // 2, (1 if d % 2 else -1)
+            p = [i, j, k]
+            p[ax] += s
+            if not (0 <= p[ax] < dims[ax]) and not periodic[ax]:
+                face = 2 * ax + (1 if s > 0 else 0)
+                if pot_bc[face] == 1:  # psi_ghost = 2 v - psi
+                    A[n, n] += 2.0
+                    b[n] += 2.0 * pot_val[face]
+                continue
+            p[ax] %= dims[ax]
+            o = owner[p[2], p[1], p[0]]
+            if o < 0:  # flux (psi_j - psi_i)
+                A[n, n] += 1.0
+                A[n, idx[p[2], p[1], p[0]]] -= 1.0
+            elif kinds[o] == W.KIND_ZETA:
+                A[n, n] += 2.0
+                b[n] += 2.0 * zetas[o]
+            else:
+                b[n] += qs[o] / faces[o]
+    return A, b, idx, faces
+
+
+@pytest.mark.parametrize("case", ["periodic_zeta", "walls_charge", "mixed"])
+def test_dense_solve_8cubed(case):
+    if case == "periodic_zeta":
+        wl = _wl((8, 8, 8), (1, 1, 1), 0.4, [((4.0, 4.0, 4.0), 1.6, W.KIND_ZETA, 0.8, 0.0)], levels=2)
+    elif case == "walls_charge":
+        wl = _wl((8, 8, 8), (1, 0, 0), 0.3, [((3.7, 4.2, 4.1), 1.7, W.KIND_CHARGE, 0.0, 1.3)],
+                 pot_bc=(0, 0, 1, 0, 0, 1), pot_val=(0, 0, 0.25, 0, 0, -0.4), levels=3)
+    else:
+        wl = _wl((8, 8, 8), (0, 1, 1), 0.5, [((2.5, 2.5, 3.0), 1.2, W.KIND_ZETA, -0.6, 0.0),
+                                              ((5.6, 5.5, 5.5), 1.5, W.KIND_CHARGE, 0.0, -0.9)],
+                 pot_bc=(1, 0, 0, 0, 0, 0), pot_val=(0.3, 0, 0, 0, 0, 0), levels=2)
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    info = o.solve()
+    assert info["status"] == 0 and info["r"] < info["tol"]
+    owner = o.owner()
+    A, b, idx, faces = _dense_system(wl.dims, wl.periodic, wl.kappa, owner, wl.kind, wl.zeta, wl.q,
+                                     wl.pot_bc, wl.pot_val)
+    nf = o.nfaces()
+    for p, n in faces.items():
+        assert nf[p] == n
+    x = np.linalg.solve(A, b)
+    psi = o.field(oracle.FIELD_PSI)
+    got = psi[owner < 0]
+    ref = x[idx[owner < 0]]
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-12
+
+
+def test_one_dimensional_discrete_closed_form():
+    """Slab periodic in x and y, Dirichlet value zeta at z = 0 and zero flux at
+    z = H.  By symmetry the x/y fluxes vanish, and the stencil of Sec. 4.3
+    reduces to (2 + kappa^2) psi_k - psi_{k-1} - psi_{k+1} = 0, whose
+    solutions are A mu^k + B mu^-k with mu + 1/mu = 2 + kappa^2; the two
+    boundary rows fix A and B."""
+    H, kappa, zeta = 24, 0.35, 1.7
+    wl = _wl((8, 8, H), (1, 1, 0), kappa, pot_bc=(0, 0, 0, 0, 1, 0), pot_val=(0, 0, 0, 0, zeta, 0),
+             levels=3)
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    info = o.solve()
+    assert info["status"] == 0
+    s = 2.0 + kappa ** 2
+    mu = (s - np.sqrt(s * s - 4.0)) / 2.0
+    # row 0: (s + 1) psi_0 - psi_1 = 2 zeta; row H-1: (s - 1) psi_{H-1} - psi_{H-2} = 0
+    M = np.array([[(s + 1.0) - mu, (s + 1.0) - 1.0 / mu],
+                  [(s - 1.0) * mu ** (H - 1) - mu ** (H - 2), (s - 1.0) * mu ** (1 - H) - mu ** (2 - H)]])
+    A, B = np.linalg.solve(M, np.array([2.0 * zeta, 0.0]))
+    k = np.arange(H)
+    exact = A * mu ** k + B * mu ** (-k)
+    psi = o.field(oracle.FIELD_PSI)
+    for j in range(8):
+        for i in range(8):
+            np.testing.assert_allclose(psi[:, j, i], exact, rtol=1e-12, atol=0)
+
+
+def _sphere_error(R):
+    n = int(8 * R)
+    kappa = 1.0 / R
+    c = n / 2.0
+    wl = _wl((n, n, n), (0, 0, 0), kappa, [((c, c, c), R, W.KIND_ZETA, 1.0, 0.0)], levels=3,
+             res_rf=1e-10)
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    o.solve()
+    psi = o.field(oracle.FIELD_PSI)
+    z, y, x = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5, np.arange(n) + 0.5, indexing="ij")
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    exact = R / r * np.exp(-kappa * (r - R))
+    band = (r > R + 1.0) & (r < 3.0 * R)
+    return np.sqrt(np.mean((psi[band] - exact[band]) ** 2)) / np.sqrt(np.mean(exact[band] ** 2))
+
+
+def test_screened_sphere_potential():
+    """zeta sphere in a large zero-flux box, kappa R = 1: compare with
+    psi(r) = zeta (R/r) exp(-kappa (r - R)) (Eq. PotDistrSphereDH).  The
+    staircase surface (Sec. 4.2) is the main error; it shrinks as R grows."""
+    e4 = _sphere_error(4.0)
+    e8 = _sphere_error(8.0)
+    assert e4 < 0.05
+    assert e8 < 0.03
+    assert e8 < 0.75 * e4
+
+
+def test_gauss_law_for_surface_charge():
+    """Summing the discrete equations over all fluid cells, interior face
+    fluxes cancel and zero-flux walls carry none, so kappa^2 eps sum(psi)
+    equals the charge imposed at the particle faces: the total charge in the
+    EDL balances the particles' charge (Eq. ChrgDensDHA)."""
+    q1, q2 = 1.3, -0.45
+    wl = _wl((16, 16, 16), (1, 0, 1), 0.4, [((5.2, 6.1, 7.3), 2.6, W.KIND_CHARGE, 0.0, q1),
+                                             ((11.0, 10.4, 12.2), 2.2, W.KIND_CHARGE, 0.0, q2)],
+             levels=3, res_rf=1e-13)
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    info = o.solve()
+    assert info["status"] == 0
+    psi = o.field(oracle.FIELD_PSI)
+    fluid = o.owner() < 0
+    total = wl.kappa ** 2 * wl.eps * psi[fluid].sum()
+    assert abs(total - (q1 + q2)) < 1e-9
+    # positive charge raises the potential next to the particle, negative lowers it
+    assert psi[7, 6, 5 + 3] > 0.0 and psi[12, 10, 11 + 3] < 0.0
+
+
+def test_multigrid_cycle_contracts_residual():
+    """Every V-cycle must cut the residual well below the previous one."""
+    wl = W.channel(n=32, n_spheres=4, radius=4.0, levels=3)
+    o = oracle.Oracle(wl, dict(max_cycles=1, res_rf=1e-30))
+    o.map_particles()
+    r_prev = None
+    for _ in range(5):
+        info = o.solve(forced_cycles=1)
+        if r_prev is not None:
+            assert info["r"] < 0.3 * r_prev
+        r_prev = info["r"]
+
+
+def test_solver_stops_on_tolerance_and_reports_nonconvergence():
+    wl = W.single_sphere(n=16, radius=3.0, levels=2, res_rf=1e-6)
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    info = o.solve()
+    assert info["cycles"] > 0 and info["r"] < info["tol"] <= info["r0"] * 1e-6 * (1 + 1e-12)
+    again = o.solve()
+    assert again["cycles"] == 0  # the check comes before the first cycle
+    wl2 = W.single_sphere(n=16, radius=3.0, levels=2, res_rf=1e-12)
+    o2 = oracle.Oracle(wl2, dict(max_cycles=1))
+    o2.map_particles()
+    res = o2.solve(check=False)
+    assert res["status"] == oracle.OR_ENOTCONVERGED and res["cycles"] == 1
+
+
+def test_gradient_exact_for_linear_potential():
+    """Both the D3Q19 stencil (Eq. ElPotGradComp) and the D3Q7 central
+    differences with linearly extrapolated Dirichlet values are exact for a
+    linear potential; the wall values are the linear function at the faces."""
+    a, gx, gy, gz = 0.3, 0.02, -0.05, 0.04
+    dims = (6, 6, 10)
+    # periodic x/y would break linearity, so use walls with Dirichlet values
+    # on the z faces and a linear field only along z; x/y stay periodic.
+    wl = _wl(dims, (1, 1, 0), 0.2, pot_bc=(0, 0, 0, 0, 1, 1),
+             pot_val=(0, 0, 0, 0, a + gz * 0.0, a + gz * dims[2]), E=(1e-3, 2e-3, 3e-3))
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    z = np.arange(dims[2]) + 0.5
+    psi = np.broadcast_to((a + gz * z)[:, None, None], dims[::-1]).copy()
+    o.set_field(oracle.FIELD_PSI, psi)
+    g = o.gradient()
+    np.testing.assert_allclose(g[2], gz, rtol=1e-13)
+    np.testing.assert_allclose(g[:2], 0.0, atol=1e-15)
+    # body force: f_b = -kappa^2 eps psi (E_ext - grad psi) (Sec. 5.6)
+    o.body_force()
+    fb = o.field(oracle.FIELD_FB)
+    E = np.array(wl.E_ext)
+    E_tot = E - np.array([0.0, 0.0, gz])
+    for d in range(3):
+        np.testing.assert_allclose(fb[d], -wl.kappa ** 2 * psi * E_tot[d], rtol=1e-13, atol=1e-20)
+    # one axis at a time with Dirichlet values equal to the linear field on
+    # the two faces of that axis, periodic along the other two
+    xs = np.arange(8) + 0.5
+    for ax in range(3):
+        grad = [0.0, 0.0, 0.0]
+        grad[ax] = [gx, gy, gz][ax]
+        vals = [0.0] * 6
+        vals[2 * ax] = a
+        vals[2 * ax + 1] = a + grad[ax] * 8
+        bc = [0] * 6
+        bc[2 * ax] = bc[2 * ax + 1] = 1
+        periodic = [1, 1, 1]
+        periodic[ax] = 0
+        wl3 = _wl((8, 8, 8), tuple(periodic), 0.2, pot_bc=tuple(bc), pot_val=tuple(vals))
+        o3 = oracle.Oracle(wl3)
+        o3.map_particles()
+        Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+        field = a + grad[0] * X + grad[1] * Y + grad[2] * Z
+        o3.set_field(oracle.FIELD_PSI, field)
+        g3 = o3.gradient()
+        for d in range(3):
+            np.testing.assert_allclose(g3[d], grad[d], rtol=1e-12, atol=1e-15)
+
+
+def test_uniform_potential_body_force():
+    """psi = const in a periodic box: no EDL field, f_b = -kappa^2 eps psi E."""
+    wl = _wl((4, 4, 4), (1, 1, 1), 0.5, E=(1e-3, -2e-3, 5e-4))
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    o.set_field(oracle.FIELD_PSI, np.full((4, 4, 4), 0.7))
+    o.body_force()
+    fb = o.field(oracle.FIELD_FB)
+    for d in range(3):
+        np.testing.assert_allclose(fb[d], -0.25 * 0.7 * wl.E_ext[d], rtol=1e-14)
