@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled electrophoresis time step on GB300.
+
+One step is Algorithm 1 of the paper on the GPU: particle mapping, the
+multigrid Debye-Hueckel solve to the residual tolerance, EDL field and body
+force, the fused stream-collide sweep, momentum-exchange forces and the
+rigid-body update.  Workload: a 512^3 periodic suspension of 2,880 charged
+spheres of radius 5 (the per-GPU weak-scaling shape), MIXED32 form.
+
+Prints one JSON line.  Under torchrun every rank runs an independent replica
+on its own GPU (the step has no exchange across GPUs here); the timed region
+is bracketed by barriers and the slowest rank's time is used.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS & %HBM roofline at 512^3; served runs/s, p99 latency mixed vs FP64"
+UNIT = "MLUPS"
+# algorithmic bytes per fluid cell of the stream-collide kernel in the MIXED32
+# form: 19 FP32 populations read + 19 written, 3 FP32 body-force components,
+# 1 flag byte; obstacle cells only read their flag byte
+LBM_BYTES_FLUID = 2 * 19 * 4 + 3 * 4 + 1
+LBM_BYTES_SOLID = 1
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512, help="cells per axis")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer run (default: --steps)")
+    return ap.parse_args()
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(steps_timed=1, n=128):
+    """The FP64 oracle as it stands, single-threaded on a host core, on a
+    sub-box of the same suspension (same sphere density, radius, charges,
+    Debye length and field).  One untimed step (the cold solve), then timed
+    steps; value in MLUPS."""
+    import oracle
+    from paper_1708_08741_gb300 import workloads as W
+
+    wl = W.suspension_sample(n)
+    o = oracle.Oracle(wl)
+    o.step()
+    t0 = time.perf_counter()
+    for _ in range(steps_timed):
+        o.step()
+    dt = time.perf_counter() - t0
+    return {"value": wl.n_cells * steps_timed / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n}^3 periodic sub-box, {wl.n_particles} spheres R=5 (same density as 2,880 in 512^3), "
+                      f"FP64 C oracle, {steps_timed} timed step(s) after 1 untimed step, 1 thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, _, world = rank_info()
+    if rank != 0:
+        return
+    n = 128 if (args.steps + args.warmup) <= 14 else 64
+    import oracle
+    from paper_1708_08741_gb300 import workloads as W
+
+    wl = W.suspension_sample(n)
+    o = oracle.Oracle(wl)
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step()
+    dt = time.perf_counter() - t0
+    value = wl.n_cells * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"suspension sample {n}^3, {wl.n_particles} spheres R=5 (density of 2,880 in 512^3)",
+                   "parallelism": "host core"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step one oracle step of the {n}^3 sub-box"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import workloads as W
+
+    rank, local, world = rank_info()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    wl = W.suspension(n=args.n, n_spheres=int(round(2880 * (args.n / 512) ** 3)),
+                      levels=6 if args.n % 32 == 0 else 4)
+    sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev))
+    stream = sim.stream
+    N = wl.n_cells
+
+    for _ in range(max(args.warmup, 0)):
+        sim.step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    start, stop = ev(), ev()
+    lbm_ev = [(ev(), ev()) for _ in range(args.steps)]
+    phase_ev = [[ev() for _ in range(5)] for _ in range(args.steps)]
+    cycles = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = sim.kernel_launches()
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for k in range(args.steps):
+            pe = phase_ev[k]
+            pe[0].record(stream)
+            sim.map_particles()
+            pe[1].record(stream)
+            info = sim.solve()
+            cycles.append(info["cycles"])
+            pe[2].record(stream)
+            lbm_ev[k][0].record(stream)
+            sim.lbm_step()
+            lbm_ev[k][1].record(stream)
+            pe[3].record(stream)
+            sim.forces_device()
+            sim.advance()
+            pe[4].record(stream)
+        stop.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = sim.kernel_launches() - launches0
+    barrier()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    t = start.elapsed_time(stop) / 1e3
+    t_all = t
+    if dist is not None:
+        tt = torch.tensor([t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_all = float(tt.item())
+    lbm_ms = statistics.mean(a.elapsed_time(b) for a, b in lbm_ev)
+    phases = {name: statistics.mean(pe[i].elapsed_time(pe[i + 1]) for pe in phase_ev)
+              for i, name in enumerate(["map", "solve_and_body_force", "lbm", "forces_advance"])}
+    vcycles = sum(cycles)
+
+    own = torch.empty(N, dtype=torch.int32, device=dev)
+    sim.field_device(es.FIELD_OWNER, own)
+    n_solid = int((own >= 0).sum().item())
+    del own
+    n_fluid = N - n_solid
+    lbm_bytes = LBM_BYTES_FLUID * n_fluid + LBM_BYTES_SOLID * n_solid
+    peak, peak_kind = measured_peaks()
+    achieved = lbm_bytes / (lbm_ms / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers: the particle state comes
+    # in from host memory each step and the new state and forces go back
+    e2e_steps = args.e2e_steps or args.steps
+    parts = es.pack_particles(wl.x, wl.v, wl.w, wl.R, wl.kind, wl.zeta, wl.q)
+    sim.lib.es_get_particles(sim.h, parts, wl.n_particles)
+    F = np.zeros(3 * wl.n_particles)
+    T = np.zeros(3 * wl.n_particles)
+    info_c = es.SolveInfo()
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim._check(sim.lib.es_set_particles(sim.h, parts, wl.n_particles), "es_set_particles")
+        sim._check(sim.lib.es_map_particles(sim.h), "es_map_particles")
+        sim._check(sim.lib.es_potential_solve(sim.h, -1, info_c), "es_potential_solve")
+        sim._check(sim.lib.es_lbm_step(sim.h), "es_lbm_step")
+        sim._check(sim.lib.es_forces(sim.h, F.ctypes.data, T.ctypes.data, 0), "es_forces")
+        sim._check(sim.lib.es_advance(sim.h), "es_advance")
+        sim._check(sim.lib.es_get_particles(sim.h, parts, wl.n_particles), "es_get_particles")
+    torch.cuda.synchronize(dev)
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    psize = ctypes_sizeof_particle(es)
+    h2d = wl.n_particles * psize
+    d2h = wl.n_particles * (psize + 48)
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline()
+    sim.close()
+    if rank != 0:
+        return
+    value = N * args.steps * world / t_all / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"suspension {args.n}^3 periodic, {wl.n_particles} charged spheres R=5, "
+                               f"lambda_D=4, E=1e-3, MIXED32, {sim.params.levels}-level V(2,2) to RES_RF 1e-8",
+                   "cells": N, "fluid_cells": n_fluid, "parallelism": f"replicas x{world}",
+                   "l2_policy": "inputs larger than L2 (PDF fields 20 GB)"},
+        "mflups": n_fluid * args.steps * world / t_all / 1e6,
+        "vcycles_per_step": vcycles / args.steps,
+        "phases_ms": phases,
+        "roofline": {"kernel": "k_lbm<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "bytes_per_launch": lbm_bytes, "ms_per_launch": lbm_ms},
+        "e2e": {"value": N * e2e_steps * world / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": base,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def ctypes_sizeof_particle(es):
+    import ctypes
+
+    return ctypes.sizeof(es.Particle)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

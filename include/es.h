@@ -1,0 +1,237 @@
+/*
+ * es.h -- C ABI of libes, a single-GPU (sm_103a) implementation of the
+ * Eulerian grid work of one coupled electrophoresis time step of
+ * Bartuschat & Ruede, arXiv 1708.08741 (Algorithm 1, Sec. 5.7).
+ *
+ * One time step is the call sequence
+ *     es_map_particles      particle -> grid mapping, PDF reconstruction,
+ *                           potential stencil/RHS assembly
+ *     es_potential_solve    multigrid solve of the Debye-Hueckel equation,
+ *                           EDL field and electric body force
+ *     es_lbm_step           fused TRT stream-collide with moving bounce-back
+ *     es_forces             momentum-exchange force/torque plus q E_ext
+ *     es_advance            rigid-body update
+ * or es_step, which issues all five.
+ *
+ * Conventions for every function:
+ *  - Return value: ES_OK (0) or a negative ES_E* status.  A failing call
+ *    leaves a message retrievable with es_last_error().  No C++ exception
+ *    crosses this boundary.
+ *  - Units are lattice units: dx = dt = rho_0 = 1 (Sec. 4.4); eps is the
+ *    fluid permittivity in those units.
+ *  - Grid layout: cell (i, j, k) has linear index i + nx (j + ny k) (x
+ *    fastest) and centre (i + 1/2, j + 1/2, k + 1/2) (Sec. 4.3, Eq.
+ *    FineLattice with 0-based indices).
+ *  - All work is issued on the CUDA stream given to es_create, in order, and
+ *    does not wait for the GPU, except where a function says it does.
+ *    Asynchronous kernel errors and device-side statuses (overlapping
+ *    particles) surface at the next call that synchronises.
+ *  - The context owns every device buffer it uses; callers' arrays are
+ *    copied and never retained.
+ *  - A context is not thread safe: one host thread at a time.
+ */
+#ifndef ES_H
+#define ES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ES_OK 0
+#define ES_EINVAL (-1)         /* invalid argument or parameter set        */
+#define ES_ENOMEM (-2)         /* device or host allocation failed         */
+#define ES_ECUDA (-3)          /* a CUDA runtime call or kernel failed      */
+#define ES_ENOTCONVERGED (-4)  /* solver hit max_cycles above tolerance     */
+#define ES_ENAN (-5)           /* residual norm is NaN or infinite          */
+#define ES_EOVERLAP (-6)       /* two particles claim a cell, or a sphere cuts a wall */
+
+/* arithmetic forms */
+#define ES_FP64 0    /* everything in double precision                           */
+#define ES_MIXED32 1 /* PDFs stored as FP32 deviations from w_q, FP32 collision,
+                        FP32 multigrid cycles inside an FP64 defect correction,
+                        FP64 force/torque sums and rigid-body update           */
+
+/* particle electric boundary conditions (Sec. 5.5) */
+#define ES_KIND_ZETA 0   /* prescribed zeta potential: Dirichlet             */
+#define ES_KIND_CHARGE 1 /* prescribed total surface charge q: Neumann       */
+
+/* potential condition on a non-periodic domain face (Sec. 5.4) */
+#define ES_POT_ZERO_FLUX 0
+#define ES_POT_DIRICHLET 1
+
+/* fields for es_get_field / es_set_field; all exchanged as double except
+ * OWNER (int32) and FLAGS (uint8).  Multi-component fields are component
+ * major: component c of cell i at [c * N + i].                             */
+#define ES_FIELD_PSI 0      /* N: EDL potential psi (boundary cells: zeta or 0) */
+#define ES_FIELD_RHO 1      /* N: density of the stored state                   */
+#define ES_FIELD_U 2        /* 3N: velocity u = sum c f - f_b/2 of the stored state
+                               (the modified velocity of Eq. modified_velocity) */
+#define ES_FIELD_FB 3       /* 3N: electric body force density f_b (Sec. 5.6)  */
+#define ES_FIELD_PDF 4      /* 19N: populations the next es_lbm_step pulls from,
+                               in the direction order of es_lattice            */
+#define ES_FIELD_OWNER 5    /* N int32: particle index of an obstacle cell, -1 fluid */
+#define ES_FIELD_FLAGS 6    /* N uint8: bit 0 obstacle cell, bit 1 fluid cell with a
+                               D3Q19 neighbour that is an obstacle or beyond a wall */
+#define ES_FIELD_PDF_LAST 7 /* 19N: populations the last es_lbm_step pulled from */
+
+typedef struct {
+    int dims[3];        /* cells per axis; each a multiple of 2^(levels-1)          */
+    int periodic[3];    /* 1: periodic axis; 0: no-slip walls half-way outside the
+                           first and last layer (LBM) with pot_bc on both faces     */
+    int pot_bc[6];      /* faces x-lo, x-hi, y-lo, y-hi, z-lo, z-hi of non-periodic axes */
+    double pot_val[6];  /* Dirichlet values of those faces                          */
+    double tau;         /* LBM relaxation time, nu = (tau - 1/2)/3 (Eq. kinVisc); > 1/2 */
+    double kappa;       /* Debye-Hueckel parameter 1/lambda_D (Eq. DebyHuckApproxPot) */
+    double eps;         /* fluid permittivity (Eq. ChrgDensDHA)                   */
+    double E_ext[3];    /* applied field (Sec. 5.6)                               */
+    double accel[3];    /* additional uniform body force density on the fluid      */
+    double rho_p_ratio; /* particle / fluid density (1.195 in Sec. 6.1)           */
+    int precision;      /* ES_FP64 or ES_MIXED32                                  */
+    int levels;         /* multigrid levels, 1..12                                */
+    int nu1, nu2;       /* pre- and post-smoothing red-black sweeps per level     */
+    int coarse_sweeps;  /* red-black sweeps on the coarsest level                 */
+    double omega;       /* smoother relaxation (1: Gauss-Seidel; the paper's SOR uses 1.7) */
+    double res_rf;      /* residual reduction factor w.r.t. the first solve (Sec. 5.3) */
+    int max_cycles;     /* cycle cap per es_potential_solve                        */
+} es_params;
+
+typedef struct {
+    double x[3]; /* centre                  */
+    double v[3]; /* translational velocity  */
+    double w[3]; /* angular velocity        */
+    double R;    /* radius                  */
+    int kind;    /* ES_KIND_ZETA or ES_KIND_CHARGE */
+    double zeta; /* surface potential (ES_KIND_ZETA)  */
+    double q;    /* total charge (ES_KIND_CHARGE)      */
+} es_particle;
+
+typedef struct {
+    int cycles;       /* V-cycles applied                                  */
+    double r_initial; /* residual L2 norm before the first cycle          */
+    double r_final;   /* residual L2 norm after the last cycle            */
+    double tol;       /* absolute tolerance res_rf * (norm at the first solve) */
+} es_solve_info;
+
+typedef struct es_ctx es_ctx;
+
+/* Device allocator hooks: alloc returns device memory of at least `bytes`
+ * (256-byte aligned) or NULL; free releases it.  `user` is passed through. */
+typedef void* (*es_alloc_fn)(size_t bytes, void* user);
+typedef void (*es_free_fn)(void* ptr, void* user);
+
+/* Creates a simulation: validates the parameters (the PhysicalCheck role of
+ * Sec. 5.1; ES_EINVAL on violation), allocates all device state with
+ * cudaMalloc, sets the fluid at rest (f_q = w_q), psi = 0, copies the n
+ * particles (host array, n >= 0) and binds the CUDA stream `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *out receives the
+ * context, or NULL on failure.  Synchronises once at the end.            */
+int es_create(const es_params* params, const es_particle* particles, int n, void* stream,
+              es_ctx** out);
+
+/* As es_create, with all device memory taken from alloc/free (for example a
+ * framework's caching allocator).  alloc == NULL selects cudaMalloc.      */
+int es_create_with_allocator(const es_params* params, const es_particle* particles, int n,
+                             void* stream, es_alloc_fn alloc, es_free_fn free_fn, void* user,
+                             es_ctx** out);
+
+/* Synchronises the stream and releases everything; ctx may be NULL. */
+int es_destroy(es_ctx* ctx);
+
+/* Algorithm 1, "set electric BCs of particles" and "set velocity BCs of
+ * particles" (Sec. 5.5, Sec. 4.2): maps every sphere onto the lattice (a
+ * cell belongs to a sphere iff its centre lies inside), reconstructs the
+ * PDFs of cells uncovered since the last mapping as f^eq(rho_0, u_s) with
+ * the surface velocity at that mapping, writes the boundary values into psi
+ * and assembles the quasi-constant stencil: boundary flags per multigrid
+ * level and, per charged sphere, sigma = q / (number of its fluid faces).
+ * Work is limited to each sphere's bounding box.  Overlap or a sphere that
+ * cuts a wall is reported as ES_EOVERLAP by the next synchronising call. */
+int es_map_particles(es_ctx* ctx);
+
+/* Algorithm 1, "while residual >= tol: iterate" and the coupling block
+ * (Sec. 5.3, Sec. 5.6): r = b - A psi in FP64 with the 7-point
+ * finite-volume stencil of Sec. 4.3 and the boundary treatment of Sec. 5.4;
+ * tol = res_rf * ||r|| of the first solve of the run; while ||r|| >= tol,
+ * psi += V-cycle(r).  forced_cycles >= 0 applies exactly that many cycles
+ * and skips the tolerance test.  Then computes the EDL field grad psi
+ * (Eq. ElPotGradComp), the charge density -kappa^2 eps psi (Eq.
+ * ChrgDensDHA) and the body force f_b = rho_e (E_ext - grad psi).
+ * Synchronises once per cycle to read the residual norm.  info may be
+ * NULL.  Returns ES_ENOTCONVERGED after max_cycles, ES_ENAN on a NaN norm,
+ * ES_EOVERLAP if the preceding mapping found overlapping spheres.        */
+int es_potential_solve(es_ctx* ctx, int forced_cycles, es_solve_info* info);
+
+/* Algorithm 1, "perform fused stream-collide step" (Sec. 4.1, Sec. 4.2):
+ * one pull stream-collide sweep over all fluid cells with the TRT operator
+ * (Eq. LBMcollideStep), incompressible equilibrium (Eq. EqPDF_TRT), Luo
+ * forcing with the modified velocity (Eq. LBE_forcetermLuo, Eq.
+ * modified_velocity) and velocity bounce-back at moving sphere cells (Eq.
+ * LBMMovWall) and at resting walls.                                       */
+int es_lbm_step(es_ctx* ctx);
+
+/* Algorithm 1, "apply hydrodynamic force to particles" (Sec. 4.2, Eq.
+ * LBMhydrodynForce, torque by the same sum with (x_s - X) x dF) plus the
+ * electrostatic force F_C = q E_ext (Sec. 5.6), summed in FP64 in a fixed
+ * order (deterministic).  Uses the populations bounced by the last
+ * es_lbm_step.  F and T receive n x 3 doubles each (particle major); either
+ * may be NULL.  on_device != 0: F/T are device pointers (no
+ * synchronisation); 0: host pointers (synchronises).  The sums are also
+ * kept for es_advance.                                                    */
+int es_forces(es_ctx* ctx, double* F, double* T, int on_device);
+
+/* Algorithm 1, "pe moves particles": semi-implicit Euler with dt = 1,
+ * V += F/m, X += V (wrapped on periodic axes), Omega += T/I with
+ * m = rho_p_ratio (4/3) pi R^3 and I = (2/5) m R^2, using the force and
+ * torque of the last es_forces / es_set_forces.                          */
+int es_advance(es_ctx* ctx);
+
+/* One whole time step: es_map_particles, es_potential_solve, es_lbm_step,
+ * es_forces (kept on the device), es_advance.                             */
+int es_step(es_ctx* ctx, int forced_cycles, es_solve_info* info);
+
+/* Copies a field (ES_FIELD_*) to dst, converting PDFs to plain FP64 values.
+ * bytes must equal the field size; on_device selects device or host dst.
+ * Synchronises.                                                           */
+int es_get_field(es_ctx* ctx, int which, void* dst, size_t bytes, int on_device);
+
+/* Values of a field at n selected cells (linear indices idx, host array)
+ * into the host array out, component major: out[k * n + i] is component k
+ * of cell idx[i].  Fields as for es_get_field (OWNER and FLAGS converted to
+ * double); 1 <= n <= 65536; indices must lie in [0, N).  Synchronises.   */
+int es_gather(es_ctx* ctx, int which, const int64_t* idx, int n, double* out);
+
+/* Overwrites ES_FIELD_PSI, ES_FIELD_FB or ES_FIELD_PDF from doubles.      */
+int es_set_field(es_ctx* ctx, int which, const void* src, size_t bytes, int on_device);
+
+/* Host copies of the particle state (n must equal the context's count). */
+int es_get_particles(es_ctx* ctx, es_particle* dst, int n);
+int es_set_particles(es_ctx* ctx, const es_particle* src, int n);
+
+/* Overrides the kept force and torque (host arrays, n x 3) for es_advance. */
+int es_set_forces(es_ctx* ctx, const double* F, const double* T, int n);
+
+/* Waits for the stream and reports pending device statuses. */
+int es_synchronize(es_ctx* ctx);
+
+/* The library's own D3Q19 velocity (19 x 3 ints) and weight tables. */
+int es_lattice(int* c57, double* w19);
+
+/* Number of CUDA kernels this context has launched so far (telemetry). */
+uint64_t es_kernel_launches(const es_ctx* ctx);
+
+/* Device bytes a context with these parameters and n particles will hold. */
+size_t es_device_bytes(const es_params* params, int n);
+
+/* Message of the last failure on ctx (or of the last failed es_create when
+ * ctx is NULL); never NULL.                                               */
+const char* es_last_error(const es_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ES_H */

@@ -82,7 +82,8 @@ typedef struct {
     int n[3];
     long N;
     int np;
-    or_particle *part, *prev;
+    or_particle *part;
+    or_particle *mapped; /* particle state used by the last mapping */
     double *f[2];
     int cur;      /* field the next LBM step pulls from */
     int last_src; /* field the last LBM step pulled from, -1 before the first */
@@ -197,7 +198,7 @@ static double particle_charge(const or_ctx* c, const or_particle* p) {
 void or_destroy(or_ctx* c) {
     if (!c) return;
     free(c->part);
-    free(c->prev);
+    free(c->mapped);
     free(c->f[0]);
     free(c->f[1]);
     free(c->owner);
@@ -243,10 +244,10 @@ int or_create(const or_params* P, const or_particle* parts, int np, or_ctx** out
     c->N = (long)c->n[0] * c->n[1] * c->n[2];
     c->np = np;
     c->part = (or_particle*)calloc(np > 0 ? np : 1, sizeof(or_particle));
-    c->prev = (or_particle*)calloc(np > 0 ? np : 1, sizeof(or_particle));
+    c->mapped = (or_particle*)calloc(np > 0 ? np : 1, sizeof(or_particle));
     if (np > 0) {
         memcpy(c->part, parts, sizeof(or_particle) * np);
-        memcpy(c->prev, parts, sizeof(or_particle) * np);
+        memcpy(c->mapped, parts, sizeof(or_particle) * np);
     }
     c->f[0] = (double*)malloc(sizeof(double) * 19 * c->N);
     c->f[1] = (double*)malloc(sizeof(double) * 19 * c->N);
@@ -259,7 +260,7 @@ int or_create(const or_params* P, const or_particle* parts, int np, or_ctx** out
     c->T = (double*)calloc(3 * (np > 0 ? np : 1), sizeof(double));
     c->nfaces = (int*)calloc(np > 0 ? np : 1, sizeof(int));
     c->sigma = (double*)calloc(np > 0 ? np : 1, sizeof(double));
-    if (!c->part || !c->prev || !c->f[0] || !c->f[1] || !c->owner || !c->owner_prev || !c->psi ||
+    if (!c->part || !c->mapped || !c->f[0] || !c->f[1] || !c->owner || !c->owner_prev || !c->psi ||
         !c->b || !c->fb || !c->F || !c->T || !c->nfaces || !c->sigma) {
         or_destroy(c);
         return OR_ENOMEM;
@@ -461,7 +462,8 @@ int or_map(or_ctx* c) {
                 }
     }
     /* PDF reconstruction at uncovered cells (Sec. 4.2): equilibrium with the
-     * surface velocity of the old owner from the previous time step.         */
+     * surface velocity of the old owner in the state of the previous mapping
+     * (the previous time step).                                              */
     double* f = c->f[c->cur];
     for (int k = 0; k < c->n[2]; k++)
         for (int j = 0; j < c->n[1]; j++)
@@ -469,7 +471,7 @@ int or_map(or_ctx* c) {
                 long id = cidx(c, i, j, k);
                 if (!(c->owner_prev[id] >= 0 && c->owner[id] < 0)) continue;
                 double u[3];
-                surface_velocity(c, &c->prev[c->owner_prev[id]], i, j, k, u);
+                surface_velocity(c, &c->mapped[c->owner_prev[id]], i, j, k, u);
                 for (int q = 0; q < 19; q++) f[q * c->N + id] = feq_unit_density(q, u);
             }
     /* boundary values kept in the solution field at boundary cells (Sec. 5.4) */
@@ -478,6 +480,7 @@ int or_map(or_ctx* c) {
         if (p >= 0) c->psi[i] = c->part[p].kind == OR_KIND_ZETA ? c->part[p].zeta : 0.0;
     }
     assemble(c);
+    if (c->np > 0) memcpy(c->mapped, c->part, sizeof(or_particle) * c->np);
     return status;
 }
 
@@ -853,12 +856,10 @@ int or_forces(or_ctx* c, double* Fout, double* Tout) {
 
 /* READING: the paper leaves the integrator to the pe engine (Sec. 5.7).  Here
  * it is semi-implicit Euler with dt = 1: V += F/m, X += V, Omega += T/I, with
- * m = (rho_p/rho_f) (4/3) pi R^3 rho_0 and I = (2/5) m R^2 of a solid sphere.
- * The state before the update is kept for the reconstruction of Sec. 4.2.    */
+ * m = (rho_p/rho_f) (4/3) pi R^3 rho_0 and I = (2/5) m R^2 of a solid sphere. */
 int or_advance(or_ctx* c) {
     for (int p = 0; p < c->np; p++) {
         or_particle* P = &c->part[p];
-        c->prev[p] = *P;
         double m = c->P.rho_p_ratio * RHO0 * (4.0 / 3.0) * M_PI * P->R * P->R * P->R;
         double I = 0.4 * m * P->R * P->R;
         for (int a = 0; a < 3; a++) {

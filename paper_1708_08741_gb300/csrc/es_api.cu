@@ -1,0 +1,561 @@
+// es_api.cu -- the C ABI of libes (declared in include/es.h): parameter
+// validation, device state, and the host side of Algorithm 1 (Sec. 5.7).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "es_internal.cuh"
+
+using namespace es;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(es_ctx* c, int code, const std::string& msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(es_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, ES_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define ES_CUDA(ctx, call)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+// Parameter checks (the role of PhysicalCheck, Sec. 5.1).
+int validate(const es_params* P, const es_particle* parts, int n, std::string& why) {
+    if (!P) return why = "params is NULL", ES_EINVAL;
+    if (n < 0 || (n > 0 && !parts)) return why = "bad particle array", ES_EINVAL;
+    if (P->precision != ES_FP64 && P->precision != ES_MIXED32) return why = "unknown precision", ES_EINVAL;
+    if (P->levels < 1 || P->levels > ES_MAXLEV) return why = "levels must be in 1..12", ES_EINVAL;
+    if (!(P->tau > 0.5)) return why = "tau must exceed 1/2", ES_EINVAL;
+    if (!(P->eps > 0.0) || !(P->kappa >= 0.0)) return why = "eps must be > 0 and kappa >= 0", ES_EINVAL;
+    if (P->nu1 < 0 || P->nu2 < 0 || P->coarse_sweeps < 0 || P->max_cycles < 0)
+        return why = "negative sweep or cycle count", ES_EINVAL;
+    if (!(P->omega > 0.0 && P->omega < 2.0)) return why = "omega must be in (0, 2)", ES_EINVAL;
+    if (!(P->rho_p_ratio > 0.0)) return why = "rho_p_ratio must be > 0", ES_EINVAL;
+    for (int a = 0; a < 3; a++) {
+        int d = P->dims[a];
+        if (d < 1 || d > (1 << 20)) return why = "dims out of range", ES_EINVAL;
+        if (d % (1 << (P->levels - 1)) != 0) return why = "dims must be multiples of 2^(levels-1)", ES_EINVAL;
+        if (P->periodic[a] && d > 1 && ((d >> (P->levels - 1)) % 2) != 0)
+            return why = "periodic extents must stay even on every level (red-black ordering)", ES_EINVAL;
+    }
+    for (int f = 0; f < 6; f++)
+        if (P->pot_bc[f] != ES_POT_ZERO_FLUX && P->pot_bc[f] != ES_POT_DIRICHLET)
+            return why = "unknown potential boundary kind", ES_EINVAL;
+    for (int p = 0; p < n; p++) {
+        if (!(parts[p].R > 0.0)) return why = "particle radius must be > 0", ES_EINVAL;
+        if (parts[p].kind != ES_KIND_ZETA && parts[p].kind != ES_KIND_CHARGE)
+            return why = "unknown particle kind", ES_EINVAL;
+        for (int a = 0; a < 3; a++)
+            if (P->periodic[a] && !(2.0 * parts[p].R + 2.0 < (double)P->dims[a]))
+                return why = "sphere too large for a periodic axis", ES_EINVAL;
+    }
+    return ES_OK;
+}
+
+DParticle to_device(const es_params& P, const es_particle& s, double sigma) {
+    DParticle d;
+    for (int a = 0; a < 3; a++) {
+        d.x[a] = s.x[a];
+        d.v[a] = s.v[a];
+        d.w[a] = s.w[a];
+    }
+    d.R = s.R;
+    d.zeta = s.zeta;
+    d.q = s.q;
+    d.sigma = sigma;
+    // charge for F_C: q itself, or 4 pi R^2 sigma_s with the Debye-Hueckel
+    // zeta-sigma relation (Eq. SurfChrgZetaRelationDebHuck)
+    if (s.kind == ES_KIND_CHARGE) {
+        d.qeff = s.q;
+    } else {
+        double sig = s.zeta * P.eps * (1.0 + P.kappa * s.R) / s.R;
+        d.qeff = 4.0 * M_PI * s.R * s.R * sig;
+    }
+    d.mass = P.rho_p_ratio * 1.0 * (4.0 / 3.0) * M_PI * s.R * s.R * s.R;
+    d.inertia = 0.4 * d.mass * s.R * s.R;
+    return d;
+}
+
+size_t field_bytes(const es_params* P, int n, size_t* per_level) {
+    long long N = (long long)P->dims[0] * P->dims[1] * P->dims[2];
+    size_t s = P->precision == ES_MIXED32 ? 4 : 8;
+    size_t b = 0;
+    b += 2 * 19 * N * s;  // pdf ping-pong
+    b += 3 * N * s;       // body force
+    b += N * 8;           // psi
+    b += N * 4 + N;       // owner, flags
+    size_t lv = 0;
+    for (int l = 0; l < P->levels; l++) {
+        long long Nl = (long long)(P->dims[0] >> l) * (P->dims[1] >> l) * (P->dims[2] >> l);
+        lv += Nl * (1 + 2 * s);
+    }
+    if (per_level) *per_level = lv;
+    b += lv;
+    b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8);
+    b += 4096 * 8 + 64;
+    return b;
+}
+
+void* dev_alloc(es_ctx* c, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, c->user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        c->allocs.push_back(p);
+        c->bytes += bytes;
+    }
+    return p;
+}
+
+void release(es_ctx* c) {
+    cudaStreamSynchronize(c->stream);
+    for (void* p : c->allocs) {
+        if (c->alloc)
+            c->freefn(p, c->user);
+        else
+            cudaFree(p);
+    }
+    c->allocs.clear();
+    if (c->h_norm) cudaFreeHost(c->h_norm);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    c->h_norm = nullptr;
+    c->h_status = nullptr;
+}
+
+// Reads the residual norm and the device status word (synchronises).
+int read_norm_status(es_ctx* c, double* norm, int* status) {
+    ES_CUDA(c, cudaMemcpyAsync(c->h_norm, c->d_norm, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    ES_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    *norm = c->h_norm[0];
+    *status = c->h_status[0];
+    return ES_OK;
+}
+
+int status_error(es_ctx* c, int st) {
+    if (st & DS_OVERLAP) return fail(c, ES_EOVERLAP, "two particles claim the same cell");
+    if (st & DS_WALLCUT) return fail(c, ES_EOVERLAP, "a sphere cuts a non-periodic wall");
+    return ES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int es_create_with_allocator(const es_params* params, const es_particle* parts, int n, void* stream,
+                             es_alloc_fn alloc, es_free_fn free_fn, void* user, es_ctx** out) {
+    if (!out) return fail(nullptr, ES_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    int v = validate(params, parts, n, why);
+    if (v != ES_OK) return fail(nullptr, v, why);
+    if (alloc && !free_fn) return fail(nullptr, ES_EINVAL, "alloc given without free");
+    es_ctx* c = new (std::nothrow) es_ctx();
+    if (!c) return fail(nullptr, ES_ENOMEM, "host allocation failed");
+    c->P = *params;
+    c->stream = (cudaStream_t)stream;
+    c->alloc = alloc;
+    c->freefn = free_fn;
+    c->user = user;
+    c->np = n;
+    c->g.nx = params->dims[0];
+    c->g.ny = params->dims[1];
+    c->g.nz = params->dims[2];
+    for (int a = 0; a < 3; a++) c->g.per[a] = params->periodic[a] ? 1 : 0;
+    c->g.N = (long long)c->g.nx * c->g.ny * c->g.nz;
+    for (int f = 0; f < 6; f++) {
+        c->S.pot_bc[f] = params->pot_bc[f];
+        c->S.pot_val[f] = params->pot_val[f];
+    }
+    c->S.kappa = params->kappa;
+    c->S.eps = params->eps;
+    c->L = params->levels;
+    for (int l = 0; l < c->L; l++)
+        for (int a = 0; a < 3; a++) c->ln[l][a] = params->dims[a] >> l;
+    // TRT rates (Sec. 4.1)
+    c->lambda_e = -1.0 / params->tau;
+    c->lambda_o = -8.0 * (2.0 - 1.0 / params->tau) / (8.0 - 1.0 / params->tau);
+    c->cur = 0;
+    c->last_src = -1;
+    c->red_blocks = 4 * 152;
+
+    const long long N = c->g.N;
+    const size_t s = mixed(c) ? 4 : 8;
+    const int np1 = n > 0 ? n : 1;
+    bool ok = true;
+    auto A = [&](size_t bytes) {
+        void* p = dev_alloc(c, bytes);
+        if (!p) ok = false;
+        return p;
+    };
+    c->pdf[0] = A(19 * N * s);
+    c->pdf[1] = A(19 * N * s);
+    c->fb = A(3 * N * s);
+    c->psi = (double*)A(N * 8);
+    c->owner = (int32_t*)A(N * 4);
+    c->flags = (uint8_t*)A(N);
+    for (int l = 0; l < c->L; l++) {
+        long long Nl = (long long)c->ln[l][0] * c->ln[l][1] * c->ln[l][2];
+        c->st[l] = (uint8_t*)A(Nl);
+        c->e[l] = A(Nl * s);
+        c->rhs[l] = A(Nl * s);
+    }
+    c->part = (DParticle*)A(np1 * sizeof(DParticle));
+    c->mapped = (double*)A(np1 * 9 * 8);
+    c->kind = (int*)A(np1 * 4);
+    c->nfaces = (int*)A(np1 * 4);
+    c->F = (double*)A(np1 * 3 * 8);
+    c->T = (double*)A(np1 * 3 * 8);
+    c->partial = (double*)A(c->red_blocks * 8);
+    c->d_norm = (double*)A(64);
+    c->d_status = (int*)A(64);
+    if (!ok) {
+        release(c);
+        delete c;
+        return fail(nullptr, ES_ENOMEM, "device allocation failed");
+    }
+    if (cudaMallocHost(&c->h_norm, 64) != cudaSuccess || cudaMallocHost(&c->h_status, 64) != cudaSuccess) {
+        cudaGetLastError();
+        release(c);
+        delete c;
+        return fail(nullptr, ES_ENOMEM, "pinned host allocation failed");
+    }
+    // initial state: fluid at rest, psi = 0, no obstacle cells
+    cudaError_t e = cudaSuccess;
+    std::vector<DParticle> hp(np1);
+    std::vector<int> hk(np1, 0);
+    std::vector<double> hm(9 * np1, 0.0);
+    for (int p = 0; p < n; p++) {
+        hp[p] = to_device(*params, parts[p], 0.0);
+        hk[p] = parts[p].kind;
+        for (int a = 0; a < 3; a++) {
+            hm[9 * p + a] = parts[p].x[a];
+            hm[9 * p + 3 + a] = parts[p].v[a];
+            hm[9 * p + 6 + a] = parts[p].w[a];
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->part, hp.data(), np1 * sizeof(DParticle), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->kind, hk.data(), np1 * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->mapped, hm.data(), np1 * 9 * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->psi, 0, N * 8, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->fb, 0, 3 * N * s, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->F, 0, np1 * 3 * 8, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->T, 0, np1 * 3 * 8, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 64, c->stream);
+    if (e == cudaSuccess) e = launch_init_flags(c);
+    if (e == cudaSuccess) e = launch_coarse_states(c);
+    if (e == cudaSuccess) e = launch_fill_rest(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("initialisation failed: ") + cudaGetErrorString(e);
+        release(c);
+        delete c;
+        return fail(nullptr, ES_ECUDA, msg);
+    }
+    *out = c;
+    return ES_OK;
+}
+
+int es_create(const es_params* params, const es_particle* parts, int n, void* stream, es_ctx** out) {
+    return es_create_with_allocator(params, parts, n, stream, nullptr, nullptr, nullptr, out);
+}
+
+int es_destroy(es_ctx* c) {
+    if (!c) return ES_OK;
+    release(c);
+    delete c;
+    return ES_OK;
+}
+
+int es_map_particles(es_ctx* c) {
+    if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
+    ES_CUDA(c, launch_map(c));
+    ES_CUDA(c, launch_coarse_states(c));
+    return ES_OK;
+}
+
+int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
+    if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
+    double norm;
+    int st;
+    ES_CUDA(c, launch_outer_residual(c));
+    int rc = read_norm_status(c, &norm, &st);
+    if (rc != ES_OK) return rc;
+    if (st) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        return status_error(c, st);
+    }
+    const double norm0 = norm;
+    if (!c->have_tol) {
+        c->tol = c->P.res_rf * norm;
+        c->have_tol = 1;
+    }
+    int cycles = 0;
+    int result = ES_OK;
+    for (;;) {
+        if (std::isnan(norm) || std::isinf(norm)) {
+            result = fail(c, ES_ENAN, "residual norm is not finite");
+            break;
+        }
+        if (forced_cycles >= 0) {
+            if (cycles >= forced_cycles) break;
+        } else {
+            if (!(norm >= c->tol)) break;
+            if (cycles >= c->P.max_cycles) {
+                result = fail(c, ES_ENOTCONVERGED, "max_cycles reached above tolerance");
+                break;
+            }
+        }
+        ES_CUDA(c, launch_vcycle(c));
+        ES_CUDA(c, launch_correct(c));
+        ES_CUDA(c, launch_outer_residual(c));
+        rc = read_norm_status(c, &norm, &st);
+        if (rc != ES_OK) return rc;
+        cycles++;
+    }
+    if (info) {
+        info->cycles = cycles;
+        info->r_initial = norm0;
+        info->r_final = norm;
+        info->tol = c->tol;
+    }
+    ES_CUDA(c, launch_body_force(c));
+    return result;
+}
+
+int es_lbm_step(es_ctx* c) {
+    if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
+    ES_CUDA(c, launch_lbm(c));
+    c->last_src = c->cur;
+    c->cur = 1 - c->cur;
+    return ES_OK;
+}
+
+int es_forces(es_ctx* c, double* F, double* T, int on_device) {
+    if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
+    ES_CUDA(c, launch_forces(c));
+    size_t b = (size_t)c->np * 3 * sizeof(double);
+    if (c->np == 0) return ES_OK;
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (F) ES_CUDA(c, cudaMemcpyAsync(F, c->F, b, k, c->stream));
+    if (T) ES_CUDA(c, cudaMemcpyAsync(T, c->T, b, k, c->stream));
+    if (!on_device && (F || T)) ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    return ES_OK;
+}
+
+int es_advance(es_ctx* c) {
+    if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
+    ES_CUDA(c, launch_advance(c));
+    return ES_OK;
+}
+
+int es_step(es_ctx* c, int forced_cycles, es_solve_info* info) {
+    int rc = es_map_particles(c);
+    if (rc != ES_OK) return rc;
+    rc = es_potential_solve(c, forced_cycles, info);
+    if (rc != ES_OK) return rc;
+    rc = es_lbm_step(c);
+    if (rc != ES_OK) return rc;
+    rc = es_forces(c, nullptr, nullptr, 1);
+    if (rc != ES_OK) return rc;
+    return es_advance(c);
+}
+
+static size_t field_size(const es_ctx* c, int which) {
+    long long N = c->g.N;
+    switch (which) {
+    case ES_FIELD_PSI:
+    case ES_FIELD_RHO: return N * 8;
+    case ES_FIELD_U:
+    case ES_FIELD_FB: return 3 * N * 8;
+    case ES_FIELD_PDF:
+    case ES_FIELD_PDF_LAST: return 19 * N * 8;
+    case ES_FIELD_OWNER: return N * 4;
+    case ES_FIELD_FLAGS: return N;
+    }
+    return 0;
+}
+
+static double* io_buffer(es_ctx* c) {
+    if (!c->io) c->io = dev_alloc(c, 19 * c->g.N * 8);
+    return (double*)c->io;
+}
+
+int es_get_field(es_ctx* c, int which, void* dst, size_t bytes, int on_device) {
+    if (!c || !dst) return fail(c, ES_EINVAL, "NULL argument");
+    size_t need = field_size(c, which);
+    if (need == 0 || bytes != need) return fail(c, ES_EINVAL, "unknown field or wrong size");
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const void* srcp = nullptr;
+    if (which == ES_FIELD_PSI) srcp = c->psi;
+    if (which == ES_FIELD_OWNER) srcp = c->owner;
+    if (which == ES_FIELD_FLAGS) srcp = c->flags;
+    if (!srcp) {
+        double* buf = on_device ? (double*)dst : io_buffer(c);
+        if (!buf) return fail(c, ES_ENOMEM, "staging buffer allocation failed");
+        if (which == ES_FIELD_PDF) ES_CUDA(c, launch_get_pdf(c, c->cur, buf));
+        if (which == ES_FIELD_PDF_LAST) {
+            if (c->last_src < 0) return fail(c, ES_EINVAL, "no LBM step yet");
+            ES_CUDA(c, launch_get_pdf(c, c->last_src, buf));
+        }
+        if (which == ES_FIELD_RHO) ES_CUDA(c, launch_get_moments(c, buf, nullptr));
+        if (which == ES_FIELD_U) ES_CUDA(c, launch_get_moments(c, nullptr, buf));
+        if (which == ES_FIELD_FB) ES_CUDA(c, launch_get_fb(c, buf));
+        srcp = on_device ? nullptr : buf;
+    }
+    if (srcp) ES_CUDA(c, cudaMemcpyAsync(dst, srcp, bytes, k, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    return ES_OK;
+}
+
+int es_gather(es_ctx* c, int which, const int64_t* idx, int n, double* out) {
+    if (!c || !idx || !out) return fail(c, ES_EINVAL, "NULL argument");
+    if (n < 1 || n > 65536) return fail(c, ES_EINVAL, "n must be in 1..65536");
+    if (field_size(c, which) == 0) return fail(c, ES_EINVAL, "unknown field");
+    if (which == ES_FIELD_PDF_LAST && c->last_src < 0) return fail(c, ES_EINVAL, "no LBM step yet");
+    for (int i = 0; i < n; i++)
+        if (idx[i] < 0 || idx[i] >= c->g.N) return fail(c, ES_EINVAL, "cell index out of range");
+    const size_t kmax = 65536;
+    if (!c->gather) c->gather = dev_alloc(c, kmax * 8 + 19 * kmax * 8);
+    if (!c->gather) return fail(c, ES_ENOMEM, "gather scratch allocation failed");
+    long long* didx = (long long*)c->gather;
+    double* dout = (double*)((char*)c->gather + kmax * 8);
+    int comps = (which == ES_FIELD_PDF || which == ES_FIELD_PDF_LAST) ? 19
+                : (which == ES_FIELD_U || which == ES_FIELD_FB) ? 3 : 1;
+    ES_CUDA(c, cudaMemcpyAsync(didx, idx, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+    ES_CUDA(c, launch_gather(c, which, didx, n, dout));
+    ES_CUDA(c, cudaMemcpyAsync(out, dout, (size_t)comps * n * 8, cudaMemcpyDeviceToHost, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    return ES_OK;
+}
+
+int es_set_field(es_ctx* c, int which, const void* src, size_t bytes, int on_device) {
+    if (!c || !src) return fail(c, ES_EINVAL, "NULL argument");
+    if (which != ES_FIELD_PSI && which != ES_FIELD_PDF && which != ES_FIELD_FB)
+        return fail(c, ES_EINVAL, "field is read-only");
+    if (bytes != field_size(c, which)) return fail(c, ES_EINVAL, "wrong size");
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (which == ES_FIELD_PSI) {
+        ES_CUDA(c, cudaMemcpyAsync(c->psi, src, bytes, k, c->stream));
+    } else {
+        const double* dsrc = (const double*)src;
+        if (!on_device) {
+            double* buf = io_buffer(c);
+            if (!buf) return fail(c, ES_ENOMEM, "staging buffer allocation failed");
+            ES_CUDA(c, cudaMemcpyAsync(buf, src, bytes, cudaMemcpyHostToDevice, c->stream));
+            dsrc = buf;
+        }
+        if (which == ES_FIELD_PDF) ES_CUDA(c, launch_set_pdf(c, dsrc));
+        if (which == ES_FIELD_FB) ES_CUDA(c, launch_set_fb(c, dsrc));
+    }
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    return ES_OK;
+}
+
+int es_get_particles(es_ctx* c, es_particle* dst, int n) {
+    if (!c || (n > 0 && !dst) || n != c->np) return fail(c, ES_EINVAL, "bad particle array");
+    if (n == 0) return ES_OK;
+    std::vector<DParticle> hp(n);
+    std::vector<int> hk(n);
+    ES_CUDA(c, cudaMemcpyAsync(hp.data(), c->part, n * sizeof(DParticle), cudaMemcpyDeviceToHost, c->stream));
+    ES_CUDA(c, cudaMemcpyAsync(hk.data(), c->kind, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int p = 0; p < n; p++) {
+        for (int a = 0; a < 3; a++) {
+            dst[p].x[a] = hp[p].x[a];
+            dst[p].v[a] = hp[p].v[a];
+            dst[p].w[a] = hp[p].w[a];
+        }
+        dst[p].R = hp[p].R;
+        dst[p].kind = hk[p];
+        dst[p].zeta = hp[p].zeta;
+        dst[p].q = hp[p].q;
+    }
+    return ES_OK;
+}
+
+int es_set_particles(es_ctx* c, const es_particle* src, int n) {
+    if (!c || (n > 0 && !src) || n != c->np) return fail(c, ES_EINVAL, "bad particle array");
+    std::string why;
+    int v = validate(&c->P, src, n, why);
+    if (v != ES_OK) return fail(c, v, why);
+    if (n == 0) return ES_OK;
+    // sigma is recomputed by the next mapping; keep the current one meanwhile
+    std::vector<DParticle> cur(n);
+    ES_CUDA(c, cudaMemcpyAsync(cur.data(), c->part, n * sizeof(DParticle), cudaMemcpyDeviceToHost, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<DParticle> hp(n);
+    std::vector<int> hk(n);
+    for (int p = 0; p < n; p++) {
+        hp[p] = to_device(c->P, src[p], cur[p].sigma);
+        hk[p] = src[p].kind;
+    }
+    ES_CUDA(c, cudaMemcpyAsync(c->part, hp.data(), n * sizeof(DParticle), cudaMemcpyHostToDevice, c->stream));
+    ES_CUDA(c, cudaMemcpyAsync(c->kind, hk.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    return ES_OK;
+}
+
+int es_set_forces(es_ctx* c, const double* F, const double* T, int n) {
+    if (!c || n != c->np || (n > 0 && (!F || !T))) return fail(c, ES_EINVAL, "bad force arrays");
+    if (n == 0) return ES_OK;
+    ES_CUDA(c, cudaMemcpyAsync(c->F, F, n * 3 * 8, cudaMemcpyHostToDevice, c->stream));
+    ES_CUDA(c, cudaMemcpyAsync(c->T, T, n * 3 * 8, cudaMemcpyHostToDevice, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    return ES_OK;
+}
+
+int es_synchronize(es_ctx* c) {
+    if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
+    ES_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    int st = c->h_status[0];
+    if (st) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        return status_error(c, st);
+    }
+    return ES_OK;
+}
+
+int es_lattice(int* c57, double* w19) {
+    if (!c57 || !w19) return ES_EINVAL;
+    for (int q = 0; q < 19; q++) {
+        c57[3 * q] = cx(q);
+        c57[3 * q + 1] = cy(q);
+        c57[3 * q + 2] = cz(q);
+        w19[q] = wq(q);
+    }
+    return ES_OK;
+}
+
+uint64_t es_kernel_launches(const es_ctx* c) { return c ? (uint64_t)c->launches : 0; }
+
+size_t es_device_bytes(const es_params* params, int n) {
+    std::string why;
+    if (!params || validate(params, nullptr, 0, why) != ES_OK) return 0;
+    return field_bytes(params, n, nullptr);
+}
+
+const char* es_last_error(const es_ctx* c) {
+    if (c) return c->err.c_str();
+    return g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// es_internal.cuh -- device data layout and kernel launchers of libes.
+//
+// Layout in HBM (N = nx*ny*nz cells, x fastest):
+//   pdf[2]      19 x N populations, structure of arrays, ping-pong (pull
+//               scheme).  FP64 form: f_q.  MIXED32 form: f_q - w_q as float,
+//               which keeps FP32 resolution for the small deviations.
+//   flags       N bytes: F_SOLID, F_NEAR19 (LBM / gradient fast path switch)
+//   owner       N int32: sphere index of an obstacle cell, -1 fluid
+//   psi         N doubles: EDL potential (outer FP64 iterate)
+//   fb          3 x N body force in the storage type of the PDFs
+//   st[l]       per multigrid level N_l bytes: kind (unknown / Dirichlet /
+//               Neumann) and a "near boundary" bit; the stencil is implied by
+//               these flags (quasi-constant stencil, Sec. 5.3)
+//   e[l], rhs[l] per level N_l values of the inner multigrid type
+//   particles   array of 128-byte records (DParticle) + kinds + forces
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/es.h"
+
+#define ES_MAXLEV 12
+
+namespace es {
+
+// level-0 cell flags
+enum : uint8_t { F_SOLID = 1, F_NEAR19 = 2 };
+// multigrid level states: kind in the low two bits, near-boundary bit
+enum : uint8_t { ST_UNKNOWN = 0, ST_DIR = 1, ST_NEU = 2, ST_KIND = 3, ST_NEAR = 4 };
+// device status bits
+enum : int { DS_OVERLAP = 1, DS_WALLCUT = 2 };
+
+// D3Q19 (Sec. 4.1).  Direction q in 1..9 and q+9 are opposite.
+__host__ __device__ constexpr int cx(int q) {
+    constexpr int t[19] = {0, 1, 0, 0, 1, 1, 1, 1, 0, 0, -1, 0, 0, -1, -1, -1, -1, 0, 0};
+    return t[q];
+}
+__host__ __device__ constexpr int cy(int q) {
+    constexpr int t[19] = {0, 0, 1, 0, 1, -1, 0, 0, 1, 1, 0, -1, 0, -1, 1, 0, 0, -1, -1};
+    return t[q];
+}
+__host__ __device__ constexpr int cz(int q) {
+    constexpr int t[19] = {0, 0, 0, 1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 0, 0, -1, 1, -1, 1};
+    return t[q];
+}
+__host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : (q <= 9 ? q + 9 : q - 9); }
+__host__ __device__ constexpr double wq(int q) {
+    return q == 0 ? 1.0 / 3.0 : ((q <= 3 || (q >= 10 && q <= 12)) ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// 128-byte particle record (FP64)
+struct DParticle {
+    double x[3], v[3], w[3];
+    double R, zeta, q, sigma, qeff, mass, inertia;
+};
+
+// grid description passed by value to kernels
+struct Grid {
+    int nx, ny, nz;
+    int per[3];
+    long long N;
+};
+
+struct Solver {
+    int pot_bc[6];
+    double pot_val[6];
+    double kappa, eps;
+};
+
+}  // namespace es
+
+struct es_ctx {
+    es_params P;
+    es::Grid g;
+    es::Solver S;
+    int np;
+    cudaStream_t stream;
+    es_alloc_fn alloc;
+    es_free_fn freefn;
+    void* user;
+    std::vector<void*> allocs;
+    // particles
+    es::DParticle* part;   // current state
+    double* mapped;        // np x 9: x, v, w used by the last mapping
+    int* kind;
+    int* nfaces;
+    double *F, *T;         // np x 3
+    // fields
+    void* pdf[2];
+    int cur, last_src;
+    uint8_t* flags;
+    int32_t* owner;
+    double* psi;
+    void* fb;
+    // multigrid
+    int L;
+    int ln[ES_MAXLEV][3];
+    uint8_t* st[ES_MAXLEV];
+    void* e[ES_MAXLEV];
+    void* rhs[ES_MAXLEV];
+    double* partial;
+    int red_blocks;
+    double* d_norm;
+    int* d_status;
+    double* h_norm;  // pinned: [0] norm
+    int* h_status;   // pinned
+    double tol;
+    int have_tol;
+    double lambda_e, lambda_o;
+    size_t bytes;
+    unsigned long long launches;  // kernels launched by this context
+    void* io;        // lazily allocated staging buffer of 19 N doubles
+    void* gather;    // lazily allocated gather scratch (indices + values)
+    std::string err;
+};
+
+namespace es {
+
+// ---- launchers (stream-ordered; return cudaGetLastError) ----
+// mapping (es_map.cu)
+cudaError_t launch_init_flags(es_ctx* c);
+cudaError_t launch_map(es_ctx* c);
+cudaError_t launch_coarse_states(es_ctx* c);
+// solver (es_solver.cu)
+cudaError_t launch_outer_residual(es_ctx* c);
+cudaError_t launch_vcycle(es_ctx* c);
+cudaError_t launch_correct(es_ctx* c);
+cudaError_t launch_body_force(es_ctx* c);
+// lbm and particles (es_lbm.cu)
+cudaError_t launch_lbm(es_ctx* c);
+cudaError_t launch_forces(es_ctx* c);
+cudaError_t launch_advance(es_ctx* c);
+cudaError_t launch_fill_rest(es_ctx* c);
+cudaError_t launch_get_pdf(es_ctx* c, int which_buf, double* dst);
+cudaError_t launch_set_pdf(es_ctx* c, const double* src);
+cudaError_t launch_get_moments(es_ctx* c, double* rho, double* u);
+cudaError_t launch_set_fb(es_ctx* c, const double* src);
+cudaError_t launch_get_fb(es_ctx* c, double* dst);
+cudaError_t launch_gather(es_ctx* c, int which, const long long* idx, int n, double* out);
+
+inline bool mixed(const es_ctx* c) { return c->P.precision == ES_MIXED32; }
+
+// Every launch site adds its kernel count here.
+inline void count(es_ctx* c, unsigned long long n = 1) { c->launches += n; }
+
+}  // namespace es

@@ -1,0 +1,425 @@
+// es_lbm.cu -- fused stream-collide (a7), momentum-exchange force/torque (a8)
+// and rigid-body update (a9); Sec. 4.1, Sec. 4.2, Sec. 5.7.
+//
+// Stream-collide is a single pull sweep over a structure-of-arrays PDF
+// field: a thread per cell gathers f_q(x) = f~_q(x - e_q) from the 19
+// streams (a warp reads 32 consecutive cells of each stream; the +-x
+// shifted streams are one element off and are served by the same L1/L2
+// sectors), collides in registers and writes its 19 populations.  Cells
+// next to an obstacle or a wall (F_NEAR19) take the moving bounce-back of
+// Eq. LBMMovWall instead of the pull for the affected directions.
+//
+// MIXED32 stores f_q - w_q in float: the collision is linear in f, and the
+// weights cancel in every term except the density, which becomes 1 + sum.
+#include "es_device.cuh"
+
+namespace es {
+
+namespace {
+
+template <class S>
+struct Store {
+    static constexpr bool shifted = sizeof(S) == 4;
+    __device__ static S base(int q) { return shifted ? (S)0 : (S)wq(q); }
+};
+
+template <class S>
+__global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, S* __restrict__ dst,
+                                             const uint8_t* __restrict__ flags, const int32_t* __restrict__ owner,
+                                             const DParticle* __restrict__ part, const S* __restrict__ fb,
+                                             S ax, S ay, S az, S lam_e, S lam_o) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long N = g.N;
+    const long long c = lin(g, x, y, z);
+    const uint8_t fl = flags[c];
+    if (fl & F_SOLID) return;  // obstacle cells are not updated
+
+    S f[19];
+    if (!(fl & F_NEAR19)) {
+        // all 18 pull sources are fluid cells inside the (periodic) domain
+        const int xs[3] = {x == g.nx - 1 ? 0 : x + 1, x, x == 0 ? g.nx - 1 : x - 1};
+        const int ys[3] = {y == g.ny - 1 ? 0 : y + 1, y, y == 0 ? g.ny - 1 : y - 1};
+        const int zs[3] = {z == g.nz - 1 ? 0 : z + 1, z, z == 0 ? g.nz - 1 : z - 1};
+#pragma unroll
+        for (int q = 0; q < 19; q++) {
+            long long s = lin(g, xs[1 + cx(q)], ys[1 + cy(q)], zs[1 + cz(q)]);
+            f[q] = __ldg(src + (long long)q * N + s);
+        }
+    } else {
+        f[0] = src[c];
+#pragma unroll
+        for (int q = 1; q < 19; q++) {
+            long long nb;
+            if (!neighbour(g, x, y, z, -cx(q), -cy(q), -cz(q), nb)) {
+                // resting no-slip wall half-way outside: bounce back
+                f[q] = src[(long long)opp(q) * N + c];
+                continue;
+            }
+            int o = owner[nb];
+            if (o < 0) {
+                f[q] = src[(long long)q * N + nb];
+                continue;
+            }
+            // moving bounce-back (Eq. LBMMovWall): the population sent from x
+            // towards the surface cell returns with 2 w_q rho_0 (c_q . u_s)/c_s^2
+            int bx = x - cx(q), by = y - cy(q), bz = z - cz(q);
+            bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
+            by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
+            bz = bz < 0 ? bz + g.nz : (bz >= g.nz ? bz - g.nz : bz);
+            double us[3];
+            surface_velocity(g, part[o].x, part[o].v, part[o].w, bx, by, bz, us);
+            double cu = cx(q) * us[0] + cy(q) * us[1] + cz(q) * us[2];
+            f[q] = src[(long long)opp(q) * N + c] + (S)(6.0 * wq(q) * cu);
+        }
+    }
+
+    // body force (Sec. 5.6) plus a uniform acceleration
+    const S fx = fb[c] + ax, fy = fb[N + c] + ay, fz = fb[2 * N + c] + az;
+
+    // moments (Eq. MacroscopVel) with the modified velocity (Eq. modified_velocity)
+    S rho = (S)0, jx = (S)0, jy = (S)0, jz = (S)0;
+#pragma unroll
+    for (int q = 0; q < 19; q++) {
+        rho += f[q];
+        if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
+        if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
+        if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
+    }
+    // in the shifted form rho holds rho - 1; w_q * rho below is then the
+    // shifted equilibrium directly
+    const S ux = jx + (S)0.5 * fx, uy = jy + (S)0.5 * fy, uz = jz + (S)0.5 * fz;
+    const S uu = ux * ux + uy * uy + uz * uz;
+    const S uf = ux * fx + uy * fy + uz * fz;
+    const S ae = (S)1 + (S)0.5 * lam_e, ao = (S)1 + (S)0.5 * lam_o;
+
+    // rest population: even part only
+    {
+        const S w0 = (S)wq(0);
+        const S eq0 = w0 * (rho - (S)1.5 * uu);
+        const S F0 = w0 * ((S)-3 * uf);
+        dst[c] = f[0] + lam_e * (f[0] - eq0) + ae * F0;
+    }
+    // pairs (q, q+9): TRT split into even and odd parts (Eq. TRTOp, Eq. EqPDF_TRT)
+#pragma unroll
+    for (int q = 1; q <= 9; q++) {
+        const S w = (S)wq(q);
+        const S cu = (S)cx(q) * ux + (S)cy(q) * uy + (S)cz(q) * uz;
+        const S cf = (S)cx(q) * fx + (S)cy(q) * fy + (S)cz(q) * fz;
+        const S eq_e = w * (rho + (S)4.5 * cu * cu - (S)1.5 * uu);
+        const S eq_o = w * (S)3 * cu;
+        const S fe = (S)0.5 * (f[q] + f[q + 9]);
+        const S fo = (S)0.5 * (f[q] - f[q + 9]);
+        // Luo's term (Eq. LBE_forcetermLuo) split: even w(9 cu cf - 3 u.f), odd 3 w cf,
+        // with the (1 + lambda/2) factors that go with the modified velocity
+        const S Fe = w * ((S)9 * cu * cf - (S)3 * uf);
+        const S Fo = w * (S)3 * cf;
+        const S even = lam_e * (fe - eq_e) + ae * Fe;
+        const S odd = lam_o * (fo - eq_o) + ao * Fo;
+        dst[(long long)q * N + c] = f[q] + even + odd;
+        dst[(long long)(q + 9) * N + c] = f[q + 9] + even - odd;
+    }
+}
+
+// Momentum exchange (Eq. LBMhydrodynForce): one block per sphere scans the
+// fluid cells around it; every link x_F -> x_F + e_q into the sphere adds
+// [2 f~_q(x_F) - 2 w_q (c_q . u_s)/c_s^2] c_q, the torque (x_s - X) x dF.
+// Fixed per-thread order and a fixed reduction tree: deterministic.
+template <class S>
+__global__ void __launch_bounds__(256) k_forces(Grid g, const DParticle* __restrict__ part,
+                                                const int32_t* __restrict__ owner,
+                                                const uint8_t* __restrict__ flags, const S* __restrict__ src,
+                                                double Ex, double Ey, double Ez, double* F, double* T) {
+    __shared__ double sh[32];
+    const int p = blockIdx.x;
+    const DParticle P = part[p];
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) axis_range(g, a, P.x[a], P.x[a], P.R, 1, lo[a], hi[a]);
+    const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
+    const int n = sx * sy * sz;
+    const long long N = g.N;
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int x = wrap_coord(lo[0] + t % sx, g.nx);
+        int y = wrap_coord(lo[1] + (t / sx) % sy, g.ny);
+        int z = wrap_coord(lo[2] + t / (sx * sy), g.nz);
+        long long c = lin(g, x, y, z);
+        if (!(flags[c] & F_NEAR19)) continue;
+#pragma unroll
+        for (int q = 1; q < 19; q++) {
+            long long nb;
+            if (!neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb)) continue;
+            if (owner[nb] != p) continue;
+            int bx = wrap_coord(x + cx(q), g.nx), by = wrap_coord(y + cy(q), g.ny), bz = wrap_coord(z + cz(q), g.nz);
+            double r0 = cell_disp(g, 0, bx, P.x[0]);
+            double r1 = cell_disp(g, 1, by, P.x[1]);
+            double r2 = cell_disp(g, 2, bz, P.x[2]);
+            double us0 = P.v[0] + (P.w[1] * r2 - P.w[2] * r1);
+            double us1 = P.v[1] + (P.w[2] * r0 - P.w[0] * r2);
+            double us2 = P.v[2] + (P.w[0] * r1 - P.w[1] * r0);
+            double cu = cx(q) * us0 + cy(q) * us1 + cz(q) * us2;
+            double fq = (double)src[(long long)q * N + c] + (double)Store<S>::base(q);
+            double m = 2.0 * fq - 6.0 * wq(q) * cu;
+            double d0 = m * cx(q), d1 = m * cy(q), d2 = m * cz(q);
+            acc[0] += d0;
+            acc[1] += d1;
+            acc[2] += d2;
+            acc[3] += r1 * d2 - r2 * d1;
+            acc[4] += r2 * d0 - r0 * d2;
+            acc[5] += r0 * d1 - r1 * d0;
+        }
+    }
+    const double E[3] = {Ex, Ey, Ez};
+    for (int k = 0; k < 6; k++) {
+        double s = block_sum(acc[k], sh);
+        if (threadIdx.x == 0) {
+            if (k < 3)
+                F[3 * p + k] = s + P.qeff * E[k];  // F_C = q E_ext (Sec. 5.6)
+            else
+                T[3 * p + k - 3] = s;
+        }
+    }
+}
+
+// Semi-implicit Euler, dt = 1 (the integrator is a reading: the paper
+// leaves it to the pe engine).
+__global__ void k_advance(int np, DParticle* part, const double* F, const double* T, int px, int py, int pz,
+                          double Lx, double Ly, double Lz) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    DParticle& P = part[p];
+    const int per[3] = {px, py, pz};
+    const double L[3] = {Lx, Ly, Lz};
+    for (int a = 0; a < 3; a++) {
+        P.v[a] += F[3 * p + a] / P.mass;
+        P.x[a] += P.v[a];
+        P.w[a] += T[3 * p + a] / P.inertia;
+        if (per[a]) {
+            if (P.x[a] >= L[a]) P.x[a] -= L[a];
+            if (P.x[a] < 0.0) P.x[a] += L[a];
+        }
+    }
+}
+
+template <class S>
+__global__ void k_fill_rest(long long N, S* a, S* b) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 19 * N) return;
+    int q = (int)(i / N);
+    S v = Store<S>::base(q);
+    a[i] = v;
+    b[i] = v;
+}
+
+template <class S>
+__global__ void k_get_pdf(long long N, const S* src, double* dst) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 19 * N) return;
+    dst[i] = (double)src[i] + (double)Store<S>::base((int)(i / N));
+}
+
+template <class S>
+__global__ void k_set_pdf(long long N, const double* src, S* dst) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 19 * N) return;
+    dst[i] = (S)(src[i] - (double)Store<S>::base((int)(i / N)));
+}
+
+template <class S>
+__global__ void k_moments(long long N, const S* f, const S* fb, double ax, double ay, double az, double* rho,
+                          double* u) {
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+    for (int q = 0; q < 19; q++) {
+        double v = (double)f[(long long)q * N + c] + (double)Store<S>::base(q);
+        r += v;
+        j0 += cx(q) * v;
+        j1 += cy(q) * v;
+        j2 += cz(q) * v;
+    }
+    // collision keeps rho and adds exactly f_b, so u = sum c f - f_b / 2
+    if (rho) rho[c] = r;
+    if (u) {
+        u[c] = j0 - 0.5 * ((double)fb[c] + ax);
+        u[N + c] = j1 - 0.5 * ((double)fb[N + c] + ay);
+        u[2 * N + c] = j2 - 0.5 * ((double)fb[2 * N + c] + az);
+    }
+}
+
+template <class S>
+__global__ void k_copy_fb(long long n, const S* a, double* b) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+template <class S>
+__global__ void k_load_fb(long long n, const double* a, S* b) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (S)a[i];
+}
+
+template <class S>
+__global__ void k_gather(int which, long long N, const long long* idx, int n, const S* cur, const S* last,
+                         const S* fb, const double* psi, const int32_t* owner, const uint8_t* flags, double ax,
+                         double ay, double az, double* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long c = idx[i];
+    switch (which) {
+    case ES_FIELD_PSI: out[i] = psi[c]; break;
+    case ES_FIELD_OWNER: out[i] = (double)owner[c]; break;
+    case ES_FIELD_FLAGS: out[i] = (double)flags[c]; break;
+    case ES_FIELD_FB:
+        for (int k = 0; k < 3; k++) out[(long long)k * n + i] = (double)fb[k * N + c];
+        break;
+    case ES_FIELD_PDF:
+    case ES_FIELD_PDF_LAST: {
+        const S* f = which == ES_FIELD_PDF ? cur : last;
+        for (int q = 0; q < 19; q++) out[(long long)q * n + i] = (double)f[q * N + c] + (double)Store<S>::base(q);
+        break;
+    }
+    case ES_FIELD_RHO:
+    case ES_FIELD_U: {
+        double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+        for (int q = 0; q < 19; q++) {
+            double v = (double)cur[q * N + c] + (double)Store<S>::base(q);
+            r += v;
+            j0 += cx(q) * v;
+            j1 += cy(q) * v;
+            j2 += cz(q) * v;
+        }
+        if (which == ES_FIELD_RHO) {
+            out[i] = r;
+        } else {
+            out[i] = j0 - 0.5 * ((double)fb[c] + ax);
+            out[(long long)n + i] = j1 - 0.5 * ((double)fb[N + c] + ay);
+            out[2LL * n + i] = j2 - 0.5 * ((double)fb[2 * N + c] + az);
+        }
+        break;
+    }
+    }
+}
+
+unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_lbm(es_ctx* c) {
+    const Grid& g = c->g;
+    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    const double* a = c->P.accel;
+    if (mixed(c))
+        k_lbm<float><<<grd, blk, 0, c->stream>>>(g, (const float*)c->pdf[c->cur], (float*)c->pdf[1 - c->cur],
+                                                 c->flags, c->owner, c->part, (const float*)c->fb, (float)a[0],
+                                                 (float)a[1], (float)a[2], (float)c->lambda_e, (float)c->lambda_o);
+    else
+        k_lbm<double><<<grd, blk, 0, c->stream>>>(g, (const double*)c->pdf[c->cur], (double*)c->pdf[1 - c->cur],
+                                                  c->flags, c->owner, c->part, (const double*)c->fb, a[0], a[1],
+                                                  a[2], c->lambda_e, c->lambda_o);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(es_ctx* c) {
+    if (c->np == 0) return cudaSuccess;
+    const double* E = c->P.E_ext;
+    int src = c->last_src >= 0 ? c->last_src : c->cur;
+    if (mixed(c))
+        k_forces<float><<<c->np, 256, 0, c->stream>>>(c->g, c->part, c->owner, c->flags, (const float*)c->pdf[src],
+                                                      E[0], E[1], E[2], c->F, c->T);
+    else
+        k_forces<double><<<c->np, 256, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
+                                                       (const double*)c->pdf[src], E[0], E[1], E[2], c->F, c->T);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(es_ctx* c) {
+    if (c->np == 0) return cudaSuccess;
+    k_advance<<<blocks_for(c->np, 128), 128, 0, c->stream>>>(c->np, c->part, c->F, c->T, c->g.per[0], c->g.per[1],
+                                                             c->g.per[2], (double)c->g.nx, (double)c->g.ny,
+                                                             (double)c->g.nz);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_rest(es_ctx* c) {
+    long long n = 19 * c->g.N;
+    if (mixed(c))
+        k_fill_rest<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, (float*)c->pdf[0], (float*)c->pdf[1]);
+    else
+        k_fill_rest<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, (double*)c->pdf[0], (double*)c->pdf[1]);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_pdf(es_ctx* c, int buf, double* dst) {
+    long long n = 19 * c->g.N;
+    if (mixed(c))
+        k_get_pdf<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, (const float*)c->pdf[buf], dst);
+    else
+        k_get_pdf<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, (const double*)c->pdf[buf], dst);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_pdf(es_ctx* c, const double* src) {
+    long long n = 19 * c->g.N;
+    if (mixed(c))
+        k_set_pdf<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, src, (float*)c->pdf[c->cur]);
+    else
+        k_set_pdf<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, src, (double*)c->pdf[c->cur]);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_moments(es_ctx* c, double* rho, double* u) {
+    const double* a = c->P.accel;
+    if (mixed(c))
+        k_moments<float><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, (const float*)c->pdf[c->cur],
+                                                                         (const float*)c->fb, a[0], a[1], a[2], rho, u);
+    else
+        k_moments<double><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, (const double*)c->pdf[c->cur],
+                                                                          (const double*)c->fb, a[0], a[1], a[2], rho, u);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_fb(es_ctx* c, const double* src) {
+    long long n = 3 * c->g.N;
+    if (mixed(c))
+        k_load_fb<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(n, src, (float*)c->fb);
+    else
+        k_load_fb<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(n, src, (double*)c->fb);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_fb(es_ctx* c, double* dst) {
+    long long n = 3 * c->g.N;
+    if (mixed(c))
+        k_copy_fb<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(n, (const float*)c->fb, dst);
+    else
+        k_copy_fb<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(n, (const double*)c->fb, dst);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(es_ctx* c, int which, const long long* idx, int n, double* out) {
+    const double* a = c->P.accel;
+    int last = c->last_src >= 0 ? c->last_src : c->cur;
+    if (mixed(c))
+        k_gather<float><<<blocks_for(n, 128), 128, 0, c->stream>>>(
+            which, c->g.N, idx, n, (const float*)c->pdf[c->cur], (const float*)c->pdf[last], (const float*)c->fb,
+            c->psi, c->owner, c->flags, a[0], a[1], a[2], out);
+    else
+        k_gather<double><<<blocks_for(n, 128), 128, 0, c->stream>>>(
+            which, c->g.N, idx, n, (const double*)c->pdf[c->cur], (const double*)c->pdf[last],
+            (const double*)c->fb, c->psi, c->owner, c->flags, a[0], a[1], a[2], out);
+    count(c);
+    return cudaGetLastError();
+}
+
+}  // namespace es

@@ -1,0 +1,300 @@
+// es_map.cu -- particle -> grid mapping, PDF reconstruction and potential
+// stencil assembly (a1-a3; Sec. 4.2, Sec. 5.4, Sec. 5.5).
+//
+// The mapping follows the three-phase order of Sec. 5.5 so that spheres
+// with overlapping bounding boxes never clobber each other: one kernel per
+// phase, one thread block per sphere, threads striding over the sphere's
+// bounding box only.
+//   k_clear     cells owned by sphere p at the last mapping -> -2 - p
+//   k_set       cells whose centre lies inside sphere p     -> p (atomicExch
+//               detects a second claimant: overlap)
+//   k_uncover   cells still marked -2 - p were uncovered: PDFs set to
+//               f^eq(rho_0, u_s) of p's state at the last mapping
+//   k_flags     flags / level-0 states of every cell within two cells of
+//               the old or new sphere, and the count of p's fluid faces
+//               (sigma = q / faces for a charged sphere)
+#include "es_device.cuh"
+
+namespace es {
+
+namespace {
+
+__global__ void k_init_flags(Grid g, uint8_t* flags, uint8_t* st0, int32_t* owner) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    long long c = lin(g, x, y, z);
+    owner[c] = -1;
+    bool near19 = false, near7 = false;
+#pragma unroll
+    for (int q = 1; q < 19; q++) {
+        long long nb;
+        if (!neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb)) {
+            near19 = true;
+            if (q <= 3 || (q >= 10 && q <= 12)) near7 = true;
+        }
+    }
+    flags[c] = near19 ? F_NEAR19 : 0;
+    st0[c] = near7 ? ST_NEAR : ST_UNKNOWN;
+}
+
+struct Box {
+    int lo[3], hi[3];
+    __device__ int size(int a) const { return hi[a] - lo[a] + 1; }
+    __device__ int count() const { return size(0) * size(1) * size(2); }
+    __device__ void cell(const Grid& g, int t, int& x, int& y, int& z) const {
+        int sx = size(0), sy = size(1);
+        int i = t % sx;
+        int j = (t / sx) % sy;
+        int k = t / (sx * sy);
+        x = wrap_coord(lo[0] + i, g.nx);
+        y = wrap_coord(lo[1] + j, g.ny);
+        z = wrap_coord(lo[2] + k, g.nz);
+    }
+};
+
+__device__ Box sphere_box(const Grid& g, const double* X, double R, int ext) {
+    Box b;
+    for (int a = 0; a < 3; a++) axis_range(g, a, X[a], X[a], R, ext, b.lo[a], b.hi[a]);
+    return b;
+}
+
+// Union box of the old and the new position; on periodic axes the new
+// position is taken as the image nearest to the old one.
+__device__ Box union_box(const Grid& g, const double* Xo, const double* Xn, double R, int ext) {
+    Box b;
+    for (int a = 0; a < 3; a++) {
+        double xo = Xo[a], xn = Xn[a];
+        if (g.per[a]) {
+            double L = (double)gdim(g, a);
+            if (xn - xo > 0.5 * L) xn -= L;
+            if (xn - xo < -0.5 * L) xn += L;
+        }
+        axis_range(g, a, fmin(xo, xn), fmax(xo, xn), R, ext, b.lo[a], b.hi[a]);
+    }
+    return b;
+}
+
+__global__ void k_clear(Grid g, const DParticle* part, const double* mapped, int32_t* owner) {
+    int p = blockIdx.x;
+    double R = part[p].R;
+    Box b = sphere_box(g, mapped + 9 * p, R, 0);
+    int n = b.count();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int x, y, z;
+        b.cell(g, t, x, y, z);
+        long long c = lin(g, x, y, z);
+        if (owner[c] == p) owner[c] = -2 - p;
+    }
+}
+
+__global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* owner, double* psi,
+                      int* status) {
+    int p = blockIdx.x;
+    DParticle P = part[p];
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; a++)
+            if (!g.per[a] && (P.x[a] - P.R < 0.0 || P.x[a] + P.R > (double)gdim(g, a)))
+                atomicOr(status, DS_WALLCUT);
+    }
+    // boundary value kept in the solution field at boundary cells (Sec. 5.4)
+    double bval = kind[p] == ES_KIND_ZETA ? P.zeta : 0.0;
+    Box b = sphere_box(g, P.x, P.R, 0);
+    int n = b.count();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int x, y, z;
+        b.cell(g, t, x, y, z);
+        if (!cell_inside(g, P, x, y, z)) continue;
+        long long c = lin(g, x, y, z);
+        int old = atomicExch(&owner[c], p);
+        if (old >= 0 && old != p) atomicOr(status, DS_OVERLAP);
+        psi[c] = bval;
+    }
+}
+
+template <class S>
+__global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, int32_t* owner, S* pdf) {
+    int p = blockIdx.x;
+    const double* M = mapped + 9 * p;  // x, v, w at the last mapping
+    Box b = sphere_box(g, M, part[p].R, 0);
+    int n = b.count();
+    constexpr bool shifted = sizeof(S) == 4;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int x, y, z;
+        b.cell(g, t, x, y, z);
+        long long c = lin(g, x, y, z);
+        if (owner[c] != -2 - p) continue;
+        owner[c] = -1;
+        double u[3];
+        surface_velocity(g, M, M + 3, M + 6, x, y, z, u);
+        double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+        for (int q = 0; q < 19; q++) {
+            double cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
+            // f^eq(rho_0 = 1, u_s) of Eq. fequ_Incompr_SRT
+            double dev = wq(q) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            pdf[(long long)q * g.N + c] = shifted ? (S)dev : (S)(wq(q) + dev);
+        }
+    }
+}
+
+// Flags of one cell from the owner field.  Returns the number of D3Q7 faces
+// the cell (if fluid) shares with sphere `p`.
+__device__ int cell_flags(const Grid& g, const int32_t* owner, const int* kind, int x, int y, int z,
+                          int p, uint8_t& fl, uint8_t& st) {
+    long long c = lin(g, x, y, z);
+    int o = owner[c];
+    if (o >= 0) {
+        fl = F_SOLID;
+        st = kind[o] == ES_KIND_ZETA ? ST_DIR : ST_NEU;
+        return 0;
+    }
+    bool near19 = false, near7 = false;
+    int faces = 0;
+#pragma unroll
+    for (int q = 1; q < 19; q++) {
+        long long nb;
+        bool axis = (q <= 3) || (q >= 10 && q <= 12);
+        if (!neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb)) {
+            near19 = true;
+            near7 |= axis;
+            continue;
+        }
+        int on = owner[nb];
+        if (on >= 0) {
+            near19 = true;
+            near7 |= axis;
+            if (axis && on == p) faces++;
+        }
+    }
+    fl = near19 ? F_NEAR19 : 0;
+    st = near7 ? ST_NEAR : ST_UNKNOWN;
+    return faces;
+}
+
+__global__ void k_flags(Grid g, DParticle* part, const double* mapped, const int* kind,
+                        const int32_t* owner, uint8_t* flags, uint8_t* st0, int* nfaces) {
+    __shared__ double sh[32];
+    int p = blockIdx.x;
+    Box b = union_box(g, mapped + 9 * p, part[p].x, part[p].R, 2);
+    int n = b.count();
+    int faces = 0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int x, y, z;
+        b.cell(g, t, x, y, z);
+        uint8_t fl, st;
+        faces += cell_flags(g, owner, kind, x, y, z, p, fl, st);
+        long long c = lin(g, x, y, z);
+        flags[c] = fl;
+        st0[c] = st;
+    }
+    double total = block_sum((double)faces, sh);
+    if (threadIdx.x == 0) {
+        int nf = (int)total;
+        nfaces[p] = nf;
+        // Neumann charge per face: sigma = q / faces, so that the flux over
+        // the staircase surface equals the particle charge.
+        part[p].sigma = nf > 0 ? part[p].q / (double)nf : 0.0;
+    }
+}
+
+__global__ void k_store_mapped(const DParticle* part, double* mapped, int np) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    for (int a = 0; a < 3; a++) {
+        mapped[9 * p + a] = part[p].x[a];
+        mapped[9 * p + 3 + a] = part[p].v[a];
+        mapped[9 * p + 6 + a] = part[p].w[a];
+    }
+}
+
+// Coarse level states (multigrid design): Dirichlet if any child is
+// Dirichlet, else unknown if any child is unknown, else Neumann.
+__global__ void k_coarse_kind(int fx, int fy, int fz, int cxn, int cyn, int czn, const uint8_t* fine,
+                              uint8_t* coarse) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y, k = blockIdx.z;
+    if (i >= cxn) return;
+    bool any_dir = false, any_unknown = false;
+    for (int dk = 0; dk < 2; dk++)
+        for (int dj = 0; dj < 2; dj++)
+            for (int di = 0; di < 2; di++) {
+                uint8_t s = fine[(long long)(2 * i + di) + (long long)fx * ((long long)(2 * j + dj) + (long long)fy * (2 * k + dk))] & ST_KIND;
+                any_dir |= (s == ST_DIR);
+                any_unknown |= (s == ST_UNKNOWN);
+            }
+    coarse[(long long)i + (long long)cxn * ((long long)j + (long long)cyn * k)] =
+        any_dir ? ST_DIR : (any_unknown ? ST_UNKNOWN : ST_NEU);
+    (void)fz;
+    (void)czn;
+}
+
+// Near-boundary bit of an unknown cell: a D3Q7 neighbour that is not an
+// unknown, or a non-periodic domain face.  Only the bit is written; the
+// kind bits neighbours read are unchanged, so updating in place is safe.
+__global__ void k_near_bits(int nx, int ny, int nz, int px, int py, int pz, uint8_t* st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    long long c = (long long)i + (long long)nx * ((long long)j + (long long)ny * k);
+    uint8_t s = st[c];
+    if ((s & ST_KIND) != ST_UNKNOWN) return;
+    bool near = false;
+    int n3[3] = {nx, ny, nz}, p3[3] = {px, py, pz}, v[3] = {i, j, k};
+    for (int a = 0; a < 3 && !near; a++)
+        for (int d = -1; d <= 1 && !near; d += 2) {
+            int w = v[a] + d;
+            if (w < 0 || w >= n3[a]) {
+                if (!p3[a]) {
+                    near = true;
+                    break;
+                }
+                w = w < 0 ? w + n3[a] : w - n3[a];
+            }
+            int q[3] = {v[0], v[1], v[2]};
+            q[a] = w;
+            uint8_t t = st[(long long)q[0] + (long long)nx * ((long long)q[1] + (long long)ny * q[2])] & ST_KIND;
+            if (t != ST_UNKNOWN) near = true;
+        }
+    st[c] = near ? (uint8_t)(ST_UNKNOWN | ST_NEAR) : (uint8_t)ST_UNKNOWN;
+}
+
+}  // namespace
+
+cudaError_t launch_init_flags(es_ctx* c) {
+    const Grid& g = c->g;
+    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    k_init_flags<<<grd, blk, 0, c->stream>>>(g, c->flags, c->st[0], c->owner);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map(es_ctx* c) {
+    if (c->np == 0) return cudaSuccess;
+    const Grid& g = c->g;
+    const int T = 256;
+    k_clear<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner);
+    k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->d_status);
+    if (mixed(c))
+        k_uncover<float><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (float*)c->pdf[c->cur]);
+    else
+        k_uncover<double><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (double*)c->pdf[c->cur]);
+    k_flags<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->kind, c->owner, c->flags, c->st[0], c->nfaces);
+    k_store_mapped<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->part, c->mapped, c->np);
+    count(c, 5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_states(es_ctx* c) {
+    for (int l = 1; l < c->L; l++) {
+        const int* f = c->ln[l - 1];
+        const int* m = c->ln[l];
+        dim3 blk(128), grd((m[0] + 127) / 128, m[1], m[2]);
+        k_coarse_kind<<<grd, blk, 0, c->stream>>>(f[0], f[1], f[2], m[0], m[1], m[2], c->st[l - 1], c->st[l]);
+        k_near_bits<<<grd, blk, 0, c->stream>>>(m[0], m[1], m[2], c->g.per[0], c->g.per[1], c->g.per[2], c->st[l]);
+        count(c, 2);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace es

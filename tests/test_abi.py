@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads without a GPU, exports every function that
+include/es.h declares, and validates parameters before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1708_08741_gb300 as es
+from paper_1708_08741_gb300 import build as es_build
+from paper_1708_08741_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    es_build.build()
+    return es.load()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "es.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(es_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_function(lib):
+    names = declared_functions()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(es.EXPORTED)
+
+
+def test_lattice_is_the_oracle_lattice_up_to_order(lib):
+    c, w = es.lattice()
+    co, wo = oracle.lattice()
+    lib_set = {(tuple(c[q]), round(w[q], 15)) for q in range(19)}
+    or_set = {(tuple(co[q]), round(wo[q], 15)) for q in range(19)}
+    assert lib_set == or_set
+    # opposite pairs q / q+9 of the library's order
+    for q in range(1, 10):
+        assert (c[q] == -c[q + 9]).all()
+
+
+def _create_rc(lib, wl, **over):
+    P = es.make_params(wl, es.ES_FP64, over)
+    parts = es.pack_particles(wl.x, wl.v, wl.w, wl.R, wl.kind, wl.zeta, wl.q)
+    h = ctypes.c_void_p()
+    rc = lib.es_create(ctypes.byref(P), parts, wl.n_particles, None, ctypes.byref(h))
+    return rc, lib.es_last_error(None).decode()
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(tau=0.5), "tau"),
+    (dict(levels=13), "levels"),
+    (dict(levels=7), "multiples"),
+    (dict(levels=6), "even"),
+    (dict(precision=7), "precision"),
+    (dict(omega=2.0), "omega"),
+    (dict(eps=0.0), "eps"),
+])
+def test_invalid_parameters_rejected_before_any_gpu_call(lib, over, needle):
+    rc, msg = _create_rc(lib, W.single_sphere(), **over)
+    assert rc == es.ES_EINVAL and needle in msg
+
+
+def test_invalid_particles_rejected(lib):
+    wl = W.single_sphere(n=16, radius=7.5, levels=1)
+    rc, msg = _create_rc(lib, wl)
+    assert rc == es.ES_EINVAL and "too large" in msg
+    wl2 = W.single_sphere()
+    wl2.kind = np.array([5], dtype=np.int32)
+    rc, msg = _create_rc(lib, wl2)
+    assert rc == es.ES_EINVAL
+
+
+def test_device_bytes_matches_layout(lib):
+    wl = W.suspension(n=512, n_spheres=1, levels=6)
+    b32 = es.device_bytes(wl, es.ES_MIXED32)
+    b64 = es.device_bytes(wl, es.ES_FP64)
+    N = 512 ** 3
+    # two FP32 PDF fields dominate: 2 x 19 x 4 bytes per cell
+    assert 2 * 19 * 4 * N < b32 < 2 * 19 * 4 * N + 40 * N
+    assert 2 * 19 * 8 * N < b64 < 2 * 19 * 8 * N + 60 * N

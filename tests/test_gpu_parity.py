@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.  FP64 bar: 1e-12 relative L2; MIXED32 bar: 1e-4
+relative L2 on velocity, potential and particle position after 100 steps.
+Integer work (the cell-to-sphere mapping) must match exactly."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1708_08741_gb300 as es
+from paper_1708_08741_gb300 import workloads as W
+
+from _pair import Pair, direction_map, rel_l2, to_lib_order, to_oracle_order
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_08741_gb300 import build
+
+    build.build()
+
+
+def _moving(wl, seed=1, vmax=0.05):
+    rng = W.PCG32(seed)
+    wl.v = np.array([[rng.uniform_range(-vmax, vmax) for _ in range(3)] for _ in range(wl.n_particles)])
+    wl.w = np.array([[rng.uniform_range(-0.01, 0.01) for _ in range(3)] for _ in range(wl.n_particles)])
+    return wl
+
+
+CASES = {
+    "single_sphere": lambda: W.single_sphere(),
+    "mixed_ragged": lambda: W.mixed_box(),
+    "channel64": lambda: _moving(W.channel(n=64, n_spheres=8, radius=5.0, levels=4)),
+    "suspension64": lambda: _moving(W.suspension_sample(64, levels=4)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mapping_and_reconstruction_bit_exact(name):
+    wl = CASES[name]()
+    p = Pair(wl)
+    zero = np.zeros((wl.n_particles, 3))
+    for step in range(6):
+        p.o.map_particles()
+        p.g.map_particles()
+        np.testing.assert_array_equal(p.g.field(es.FIELD_OWNER), p.o.owner())
+        flags = p.g.field(es.FIELD_FLAGS)
+        np.testing.assert_array_equal(flags & 1, (p.o.owner() >= 0).astype(np.uint8))
+        # reconstructed PDFs at uncovered cells
+        if step > 0:
+            fo = p.o.field(oracle.FIELD_PDF)
+            fg = to_oracle_order(p.g.field(es.FIELD_PDF))
+            fluid = p.o.owner() < 0
+            assert np.max(np.abs(fg[:, fluid] - fo[:, fluid])) < 1e-15
+        # move the spheres without any fluid update
+        p.o.set_forces(zero, zero)
+        p.g.set_forces(zero, zero)
+        p.o.advance()
+        p.g.advance()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_potential_solve_and_body_force(name):
+    wl = CASES[name]()
+    p = Pair(wl)
+    p.o.map_particles()
+    p.g.map_particles()
+    fluid = p.o.owner() < 0
+    for k in (0, 1, 2, 3):
+        io = p.o.solve(forced_cycles=1 if k else 0)
+        ig = p.g.solve(forced_cycles=1 if k else 0)
+        assert abs(ig["r0"] - io["r0"]) <= 1e-12 * io["r0"]
+        assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < FP64_TOL
+    # tolerance-driven solve takes the same number of cycles
+    io = p.o.solve()
+    ig = p.g.solve()
+    assert ig["cycles"] == io["cycles"] and ig["r"] < ig["tol"]
+    assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < FP64_TOL
+    p.o.body_force()
+    fb_g = p.g.field(es.FIELD_FB)
+    fb_o = p.o.field(oracle.FIELD_FB)
+    assert rel_l2(fb_g[:, fluid], fb_o[:, fluid]) < FP64_TOL
+    assert np.all(fb_g[:, ~fluid] == 0.0)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_lbm_step_forces_and_advance(name):
+    wl = CASES[name]()
+    p = Pair(wl)
+    c, w = oracle.lattice()
+    rng = np.random.Generator(np.random.PCG64(5))
+    shape = (19,) + tuple(wl.dims[::-1])
+    f0 = w[:, None, None, None] * (1.0 + 0.02 * rng.standard_normal(shape))
+    fb = 1e-4 * rng.standard_normal((3,) + tuple(wl.dims[::-1]))
+    p.o.set_field(oracle.FIELD_PDF, f0)
+    p.g.set_field(es.FIELD_PDF, to_lib_order(f0))
+    p.o.map_particles()
+    p.g.map_particles()
+    fluid = p.o.owner() < 0
+    fb[:, ~fluid] = 0.0
+    p.o.set_field(oracle.FIELD_FB, fb)
+    p.g.set_field(es.FIELD_FB, fb)
+    p.o.lbm_step()
+    p.g.lbm_step()
+    fo = p.o.field(oracle.FIELD_PDF)
+    fg = to_oracle_order(p.g.field(es.FIELD_PDF))
+    assert np.max(np.abs(fg[:, fluid] - fo[:, fluid])) < 1e-15
+    assert rel_l2(fg[:, fluid], fo[:, fluid]) < FP64_TOL
+    Fo, To = p.o.forces()
+    Fg, Tg = p.g.forces()
+    if wl.n_particles:
+        assert np.max(np.abs(Fg - Fo)) <= FP64_TOL * np.max(np.abs(Fo))
+        assert np.max(np.abs(Tg - To)) <= FP64_TOL * max(np.max(np.abs(To)), 1e-300) + 1e-15
+    p.o.advance()
+    p.g.advance()
+    pg, po = p.g.particles(), p.o.particles()
+    for k in ("x", "v", "w"):
+        np.testing.assert_allclose(pg[k], po[k], rtol=1e-13, atol=1e-16)
+
+
+def _coupled(wl, steps, precision=es.ES_FP64, overrides=None, forced=True):
+    p = Pair(wl, precision, overrides)
+    for _ in range(steps):
+        info, ginfo, (Fo, To), (Fg, Tg) = p.step(forced=forced)
+        if forced:
+            assert ginfo["cycles"] == info["cycles"]
+    return p, p.compare()
+
+
+def test_coupled_single_sphere_100_steps_fp64():
+    """32^3 periodic box, zeta sphere R = 4, lambda_D = 4, E = 1e-3, 3-level
+    V-cycles to 1e-10, 100 steps (the small case the oracle runs in full)."""
+    p, r = _coupled(W.single_sphere(), 100)
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x", "v"):
+        assert r[k] < FP64_TOL, (k, r[k])
+
+
+def test_coupled_mixed_ragged_fp64():
+    """Non-cubic 40x24x32 box (ragged thread-block tails), walls in z, both
+    sphere kinds, moving and rotating spheres, tau = 0.8."""
+    p, r = _coupled(W.mixed_box(), 20)
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x", "v", "w"):
+        assert r[k] < FP64_TOL, (k, r[k])
+
+
+def test_coupled_channel_fp64():
+    """Channel shape (walls in z, charged spheres) at 64^3, 4 levels."""
+    p, r = _coupled(W.channel(n=64, n_spheres=8, radius=5.0, levels=4), 20)
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x", "v", "w"):
+        assert r[k] < FP64_TOL, (k, r[k])
+
+
+@pytest.mark.parametrize("maker", [lambda: W.single_sphere(),
+                                   lambda: W.channel(n=64, n_spheres=8, radius=5.0, levels=4)])
+def test_mixed32_within_1e4_after_100_steps(maker):
+    """MIXED32 (FP32 PDFs and multigrid cycles, FP64 defect correction and
+    particles) against the FP64 oracle after 100 steps, each side on its own
+    tolerance-driven solver."""
+    p, r = _coupled(maker(), 100, precision=es.ES_MIXED32, forced=False)
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x"):
+        assert r[k] < MIXED_TOL, (k, r[k])
+
+
+def test_overlap_is_reported():
+    wl = W.single_sphere(n=32, radius=4.0)
+    wl.x = np.array([[10.0, 16.0, 16.0], [16.5, 16.0, 16.0]])
+    wl.v = np.zeros((2, 3))
+    wl.w = np.zeros((2, 3))
+    wl.R = np.array([4.0, 4.0])
+    wl.kind = np.array([0, 0], dtype=np.int32)
+    wl.zeta = np.array([1.0, 1.0])
+    wl.q = np.zeros(2)
+    g = es.Simulation(wl)
+    g.map_particles()
+    with pytest.raises(es.EsError) as e:
+        g.solve()
+    assert e.value.code == es.ES_EOVERLAP
+    # the status is cleared once reported
+    g.synchronize()
+
+
+def test_nonconvergence_and_forced_cycles():
+    wl = W.single_sphere(res_rf=1e-12)
+    g = es.Simulation(wl, overrides=dict(max_cycles=2))
+    g.map_particles()
+    r = g.solve(check=False)
+    assert r["status"] == es.ES_ENOTCONVERGED and r["cycles"] == 2
+    r2 = g.solve(forced_cycles=0)
+    assert r2["cycles"] == 0
+
+
+def test_runs_are_deterministic_and_allocator_independent():
+    wl = W.channel(n=64, n_spheres=8, radius=5.0, levels=4)
+    out = []
+    for torch_memory in (True, False, True):
+        g = es.Simulation(wl, es.ES_MIXED32, torch_memory=torch_memory)
+        for _ in range(5):
+            g.step()
+        F, T = g.forces()
+        out.append((g.field(es.FIELD_PSI), g.field(es.FIELD_U), F, T, g.particles()["x"]))
+        g.close()
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(out[0], out[2]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_full_size_suspension_sampled():
+    """512^3 periodic suspension, 2,880 spheres R = 5, MIXED32, 6 levels: the
+    configuration the benchmark times.  Checked on samples the oracle computes
+    one by one and on properties that hold at any size."""
+    import torch
+
+    wl = W.suspension()
+    g = es.Simulation(wl, es.ES_MIXED32)
+    for _ in range(3):
+        info = g.step()
+    assert info["r"] < info["tol"]
+    N = wl.n_cells
+    nx, ny, nz = wl.dims
+    rng = np.random.Generator(np.random.PCG64(9))
+    # (1) sampled collisions: gather the pulled populations of fluid cells away
+    # from spheres and collide them with the oracle on a 1x1x1 periodic
+    # lattice, where streaming maps every population onto itself
+    probe = rng.integers(0, N, 4000)
+    fl = g.gather(es.FIELD_FLAGS, probe)[0]
+    cells = probe[fl == 0][:48]
+    c_lib, _ = es.lattice()
+    perm = direction_map()
+    x, y, z = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    pulled = np.zeros((19, cells.size))
+    for q in range(19):
+        src = ((x - c_lib[q, 0]) % nx) + nx * (((y - c_lib[q, 1]) % ny) + ny * ((z - c_lib[q, 2]) % nz))
+        pulled[q] = g.gather(es.FIELD_PDF_LAST, src)[q]
+    fb = g.gather(es.FIELD_FB, cells)
+    out = g.gather(es.FIELD_PDF, cells)
+    for i in range(cells.size):
+        one = W.Workload(name="cell", dims=[1, 1, 1], periodic=(1, 1, 1), tau=wl.tau, kappa=0.0, eps=1.0,
+                         E_ext=(0.0, 0.0, 0.0), accel=tuple(fb[:, i]), levels=1, coarse_sweeps=1)
+        o = oracle.Oracle(one)
+        fin = np.empty(19)
+        fin[perm] = pulled[:, i]
+        o.set_field(oracle.FIELD_PDF, fin.reshape(19, 1, 1, 1))
+        o.map_particles()
+        o.lbm_step()
+        ref = o.field(oracle.FIELD_PDF).reshape(19)
+        got = np.empty(19)
+        got[perm] = out[:, i]
+        assert np.max(np.abs(got - ref)) < 2e-8
+    # (2) discrete Gauss law: kappa^2 eps sum(psi) over fluid cells = sum q
+    psi = torch.empty(N, dtype=torch.float64, device="cuda")
+    own = torch.empty(N, dtype=torch.int32, device="cuda")
+    g.field_device(es.FIELD_PSI, psi)
+    g.field_device(es.FIELD_OWNER, own)
+    total = (wl.kappa ** 2) * wl.eps * float(psi[own < 0].sum())
+    assert abs(total - wl.q.sum()) < 1e-5 * wl.q.sum()
+    del psi, own
+    # (3) mapping of sampled spheres at their current positions against the
+    # cell-in-sphere definition (centre inside, minimum image), exactly
+    g.map_particles()
+    X = g.particles()["x"]
+    for p in rng.choice(wl.n_particles, 24, replace=False):
+        lo = np.floor(X[p] - 7.0).astype(int)
+        ii, jj, kk = np.meshgrid(*[np.arange(lo[a], lo[a] + 15) for a in range(3)], indexing="ij")
+        cells3 = np.stack([ii % nx, jj % ny, kk % nz], -1).reshape(-1, 3)
+        d = cells3 + 0.5 - X[p]
+        L = np.array([nx, ny, nz], dtype=float)
+        d = np.where(d > L / 2, d - L, d)
+        d = np.where(d < -L / 2, d + L, d)
+        inside = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2] <= wl.R[p] ** 2
+        own = g.gather(es.FIELD_OWNER, cells3[:, 0] + nx * (cells3[:, 1] + ny * cells3[:, 2]))[0]
+        np.testing.assert_array_equal(own == p, inside)
+    g.close()
