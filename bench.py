@@ -50,6 +50,23 @@ def rank_info():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """Largest value over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(cells, steps, world, seconds):
+    """Whole-job MLUPS of `world` replicas that each advanced `cells` cells
+    by `steps` steps, timed by the slowest rank."""
+    return cells * steps * world / seconds / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -224,11 +241,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     t = start.elapsed_time(stop) / 1e3
-    t_all = t
-    if dist is not None:
-        tt = torch.tensor([t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_all = float(tt.item())
+    t_all = max_over_ranks(t, dist, dev)
     lbm_ms = statistics.mean(a.elapsed_time(b) for a, b in lbm_ev)
     phases = {name: statistics.mean(pe[i].elapsed_time(pe[i + 1]) for pe in phase_ev)
               for i, name in enumerate(["map", "solve_and_body_force", "lbm", "forces_advance"])}
@@ -263,11 +276,7 @@ def run_ours(args):
         sim._check(sim.lib.es_advance(sim.h), "es_advance")
         sim._check(sim.lib.es_get_particles(sim.h, parts, wl.n_particles), "es_get_particles")
     torch.cuda.synchronize(dev)
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
     psize = ctypes_sizeof_particle(es)
     h2d = wl.n_particles * psize
     d2h = wl.n_particles * (psize + 48)
@@ -278,7 +287,7 @@ def run_ours(args):
     sim.close()
     if rank != 0:
         return
-    value = N * args.steps * world / t_all / 1e6
+    value = aggregate_throughput(N, args.steps, world, t_all)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
@@ -293,7 +302,7 @@ def run_ours(args):
         "roofline": {"kernel": "k_lbm<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                      "bytes_per_launch": lbm_bytes, "ms_per_launch": lbm_ms},
-        "e2e": {"value": N * e2e_steps * world / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": aggregate_throughput(N, e2e_steps, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,

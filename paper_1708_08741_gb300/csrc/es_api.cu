@@ -88,11 +88,16 @@ DParticle to_device(const es_params& P, const es_particle& s, double sigma) {
     return d;
 }
 
+// Stream stride of the PDF fields: N rounded up to 32 elements plus 1120
+// elements (35 x 128 bytes in FP32), so that the same cell of the 19 streams
+// does not sit at one power-of-two offset apart (DRAM partition camping).
+long long pdf_stride(long long N) { return ((N + 31) / 32) * 32 + 1120; }
+
 size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     long long N = (long long)P->dims[0] * P->dims[1] * P->dims[2];
     size_t s = P->precision == ES_MIXED32 ? 4 : 8;
     size_t b = 0;
-    b += 2 * 19 * N * s;  // pdf ping-pong
+    b += 2 * 19 * pdf_stride(N) * s;  // pdf ping-pong
     b += 3 * N * s;       // body force
     b += N * 8;           // psi
     b += N * 4 + N;       // owner, flags
@@ -180,6 +185,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->g.nz = params->dims[2];
     for (int a = 0; a < 3; a++) c->g.per[a] = params->periodic[a] ? 1 : 0;
     c->g.N = (long long)c->g.nx * c->g.ny * c->g.nz;
+    c->g.ps = pdf_stride(c->g.N);
     for (int f = 0; f < 6; f++) {
         c->S.pot_bc[f] = params->pot_bc[f];
         c->S.pot_val[f] = params->pot_val[f];
@@ -205,8 +211,8 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
         if (!p) ok = false;
         return p;
     };
-    c->pdf[0] = A(19 * N * s);
-    c->pdf[1] = A(19 * N * s);
+    c->pdf[0] = A(19 * c->g.ps * s);
+    c->pdf[1] = A(19 * c->g.ps * s);
     c->fb = A(3 * N * s);
     c->psi = (double*)A(N * 8);
     c->owner = (int32_t*)A(N * 4);

@@ -1,7 +1,7 @@
 // es_internal.cuh -- device data layout and kernel launchers of libes.
 //
 // Layout in HBM (N = nx*ny*nz cells, x fastest):
-//   pdf[2]      19 x N populations, structure of arrays, ping-pong (pull
+//   pdf[2]      19 streams of N populations (stride ps), ping-pong (pull
 //               scheme).  FP64 form: f_q.  MIXED32 form: f_q - w_q as float,
 //               which keeps FP32 resolution for the small deviations.
 //   flags       N bytes: F_SOLID, F_NEAR19 (LBM / gradient fast path switch)
@@ -63,6 +63,8 @@ struct Grid {
     int nx, ny, nz;
     int per[3];
     long long N;
+    long long ps;  // stride between PDF streams: N rounded up plus a pad that keeps
+                   // the 19 streams off a common power-of-two alignment
 };
 
 struct Solver {

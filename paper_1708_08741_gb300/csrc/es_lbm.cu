@@ -17,10 +17,14 @@ namespace es {
 
 namespace {
 
+// Storage forms: FP64 keeps f_q; FP32 keeps f_q - w_q.
 template <class S>
 struct Store {
     static constexpr bool shifted = sizeof(S) == 4;
-    __device__ static S base(int q) { return shifted ? (S)0 : (S)wq(q); }
+    // stored value of the rest state f_q = w_q
+    __device__ static S rest(int q) { return shifted ? (S)0 : (S)wq(q); }
+    // what to add to a stored value to obtain f_q
+    __device__ static double offset(int q) { return shifted ? wq(q) : 0.0; }
 };
 
 template <class S>
@@ -31,7 +35,7 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    const long long N = g.N;
+    const long long N = g.N, ps = g.ps;
     const long long c = lin(g, x, y, z);
     const uint8_t fl = flags[c];
     if (fl & F_SOLID) return;  // obstacle cells are not updated
@@ -45,7 +49,7 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
 #pragma unroll
         for (int q = 0; q < 19; q++) {
             long long s = lin(g, xs[1 + cx(q)], ys[1 + cy(q)], zs[1 + cz(q)]);
-            f[q] = __ldg(src + (long long)q * N + s);
+            f[q] = __ldg(src + (long long)q * ps + s);
         }
     } else {
         f[0] = src[c];
@@ -54,12 +58,12 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
             long long nb;
             if (!neighbour(g, x, y, z, -cx(q), -cy(q), -cz(q), nb)) {
                 // resting no-slip wall half-way outside: bounce back
-                f[q] = src[(long long)opp(q) * N + c];
+                f[q] = src[(long long)opp(q) * ps + c];
                 continue;
             }
             int o = owner[nb];
             if (o < 0) {
-                f[q] = src[(long long)q * N + nb];
+                f[q] = src[(long long)q * ps + nb];
                 continue;
             }
             // moving bounce-back (Eq. LBMMovWall): the population sent from x
@@ -71,7 +75,7 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
             double us[3];
             surface_velocity(g, part[o].x, part[o].v, part[o].w, bx, by, bz, us);
             double cu = cx(q) * us[0] + cy(q) * us[1] + cz(q) * us[2];
-            f[q] = src[(long long)opp(q) * N + c] + (S)(6.0 * wq(q) * cu);
+            f[q] = src[(long long)opp(q) * ps + c] + (S)(6.0 * wq(q) * cu);
         }
     }
 
@@ -117,15 +121,16 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
         const S Fo = w * (S)3 * cf;
         const S even = lam_e * (fe - eq_e) + ae * Fe;
         const S odd = lam_o * (fo - eq_o) + ao * Fo;
-        dst[(long long)q * N + c] = f[q] + even + odd;
-        dst[(long long)(q + 9) * N + c] = f[q + 9] + even - odd;
+        dst[(long long)q * ps + c] = f[q] + even + odd;
+        dst[(long long)(q + 9) * ps + c] = f[q + 9] + even - odd;
     }
 }
 
-// Momentum exchange (Eq. LBMhydrodynForce): one block per sphere scans the
-// fluid cells around it; every link x_F -> x_F + e_q into the sphere adds
+// Momentum exchange (Eq. LBMhydrodynForce): one block per sphere; its
+// threads stride over (cell, direction) pairs of the box around the sphere,
+// and every link x_F -> x_F + e_q into the sphere adds
 // [2 f~_q(x_F) - 2 w_q (c_q . u_s)/c_s^2] c_q, the torque (x_s - X) x dF.
-// Fixed per-thread order and a fixed reduction tree: deterministic.
+// A fixed item order per thread and a fixed reduction tree: deterministic.
 template <class S>
 __global__ void __launch_bounds__(256) k_forces(Grid g, const DParticle* __restrict__ part,
                                                 const int32_t* __restrict__ owner,
@@ -137,38 +142,36 @@ __global__ void __launch_bounds__(256) k_forces(Grid g, const DParticle* __restr
     int lo[3], hi[3];
     for (int a = 0; a < 3; a++) axis_range(g, a, P.x[a], P.x[a], P.R, 1, lo[a], hi[a]);
     const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
-    const int n = sx * sy * sz;
-    const long long N = g.N;
+    const int items = sx * sy * sz * 18;
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        int x = wrap_coord(lo[0] + t % sx, g.nx);
-        int y = wrap_coord(lo[1] + (t / sx) % sy, g.ny);
-        int z = wrap_coord(lo[2] + t / (sx * sy), g.nz);
-        long long c = lin(g, x, y, z);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int t = it / 18, q = it - 18 * t + 1;
+        const int x = wrap_coord(lo[0] + t % sx, g.nx);
+        const int y = wrap_coord(lo[1] + (t / sx) % sy, g.ny);
+        const int z = wrap_coord(lo[2] + t / (sx * sy), g.nz);
+        const long long c = lin(g, x, y, z);
         if (!(flags[c] & F_NEAR19)) continue;
-#pragma unroll
-        for (int q = 1; q < 19; q++) {
-            long long nb;
-            if (!neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb)) continue;
-            if (owner[nb] != p) continue;
-            int bx = wrap_coord(x + cx(q), g.nx), by = wrap_coord(y + cy(q), g.ny), bz = wrap_coord(z + cz(q), g.nz);
-            double r0 = cell_disp(g, 0, bx, P.x[0]);
-            double r1 = cell_disp(g, 1, by, P.x[1]);
-            double r2 = cell_disp(g, 2, bz, P.x[2]);
-            double us0 = P.v[0] + (P.w[1] * r2 - P.w[2] * r1);
-            double us1 = P.v[1] + (P.w[2] * r0 - P.w[0] * r2);
-            double us2 = P.v[2] + (P.w[0] * r1 - P.w[1] * r0);
-            double cu = cx(q) * us0 + cy(q) * us1 + cz(q) * us2;
-            double fq = (double)src[(long long)q * N + c] + (double)Store<S>::base(q);
-            double m = 2.0 * fq - 6.0 * wq(q) * cu;
-            double d0 = m * cx(q), d1 = m * cy(q), d2 = m * cz(q);
-            acc[0] += d0;
-            acc[1] += d1;
-            acc[2] += d2;
-            acc[3] += r1 * d2 - r2 * d1;
-            acc[4] += r2 * d0 - r0 * d2;
-            acc[5] += r0 * d1 - r1 * d0;
-        }
+        const int dx = cx(q), dy = cy(q), dz = cz(q);
+        long long nb;
+        if (!neighbour(g, x, y, z, dx, dy, dz, nb)) continue;
+        if (owner[nb] != p) continue;
+        const int bx = wrap_coord(x + dx, g.nx), by = wrap_coord(y + dy, g.ny), bz = wrap_coord(z + dz, g.nz);
+        const double r0 = cell_disp(g, 0, bx, P.x[0]);
+        const double r1 = cell_disp(g, 1, by, P.x[1]);
+        const double r2 = cell_disp(g, 2, bz, P.x[2]);
+        const double us0 = P.v[0] + (P.w[1] * r2 - P.w[2] * r1);
+        const double us1 = P.v[1] + (P.w[2] * r0 - P.w[0] * r2);
+        const double us2 = P.v[2] + (P.w[0] * r1 - P.w[1] * r0);
+        const double cu = dx * us0 + dy * us1 + dz * us2;
+        const double fq = (double)src[(long long)q * g.ps + c] + Store<S>::offset(q);
+        const double m = 2.0 * fq - 6.0 * wq(q) * cu;
+        const double d0 = m * dx, d1 = m * dy, d2 = m * dz;
+        acc[0] += d0;
+        acc[1] += d1;
+        acc[2] += d2;
+        acc[3] += r1 * d2 - r2 * d1;
+        acc[4] += r2 * d0 - r0 * d2;
+        acc[5] += r0 * d1 - r1 * d0;
     }
     const double E[3] = {Ex, Ey, Ez};
     for (int k = 0; k < 6; k++) {
@@ -203,37 +206,41 @@ __global__ void k_advance(int np, DParticle* part, const double* F, const double
 }
 
 template <class S>
-__global__ void k_fill_rest(long long N, S* a, S* b) {
+__global__ void k_fill_rest(long long N, long long ps, S* a, S* b) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 19 * N) return;
     int q = (int)(i / N);
-    S v = Store<S>::base(q);
-    a[i] = v;
-    b[i] = v;
+    long long j = (long long)q * ps + (i - (long long)q * N);
+    S v = Store<S>::rest(q);
+    a[j] = v;
+    b[j] = v;
 }
 
+// PDFs are exchanged densely (19 x N doubles) and stored with stride ps.
 template <class S>
-__global__ void k_get_pdf(long long N, const S* src, double* dst) {
+__global__ void k_get_pdf(long long N, long long ps, const S* src, double* dst) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 19 * N) return;
-    dst[i] = (double)src[i] + (double)Store<S>::base((int)(i / N));
+    int q = (int)(i / N);
+    dst[i] = (double)src[(long long)q * ps + (i - (long long)q * N)] + Store<S>::offset(q);
 }
 
 template <class S>
-__global__ void k_set_pdf(long long N, const double* src, S* dst) {
+__global__ void k_set_pdf(long long N, long long ps, const double* src, S* dst) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 19 * N) return;
-    dst[i] = (S)(src[i] - (double)Store<S>::base((int)(i / N)));
+    int q = (int)(i / N);
+    dst[(long long)q * ps + (i - (long long)q * N)] = (S)(src[i] - Store<S>::offset(q));
 }
 
 template <class S>
-__global__ void k_moments(long long N, const S* f, const S* fb, double ax, double ay, double az, double* rho,
-                          double* u) {
+__global__ void k_moments(long long N, long long ps, const S* f, const S* fb, double ax, double ay, double az,
+                          double* rho, double* u) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
     for (int q = 0; q < 19; q++) {
-        double v = (double)f[(long long)q * N + c] + (double)Store<S>::base(q);
+        double v = (double)f[(long long)q * ps + c] + Store<S>::offset(q);
         r += v;
         j0 += cx(q) * v;
         j1 += cy(q) * v;
@@ -261,7 +268,7 @@ __global__ void k_load_fb(long long n, const double* a, S* b) {
 }
 
 template <class S>
-__global__ void k_gather(int which, long long N, const long long* idx, int n, const S* cur, const S* last,
+__global__ void k_gather(int which, long long N, long long ps, const long long* idx, int n, const S* cur, const S* last,
                          const S* fb, const double* psi, const int32_t* owner, const uint8_t* flags, double ax,
                          double ay, double az, double* out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,14 +284,14 @@ __global__ void k_gather(int which, long long N, const long long* idx, int n, co
     case ES_FIELD_PDF:
     case ES_FIELD_PDF_LAST: {
         const S* f = which == ES_FIELD_PDF ? cur : last;
-        for (int q = 0; q < 19; q++) out[(long long)q * n + i] = (double)f[q * N + c] + (double)Store<S>::base(q);
+        for (int q = 0; q < 19; q++) out[(long long)q * n + i] = (double)f[q * ps + c] + Store<S>::offset(q);
         break;
     }
     case ES_FIELD_RHO:
     case ES_FIELD_U: {
         double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
         for (int q = 0; q < 19; q++) {
-            double v = (double)cur[q * N + c] + (double)Store<S>::base(q);
+            double v = (double)cur[q * ps + c] + Store<S>::offset(q);
             r += v;
             j0 += cx(q) * v;
             j1 += cy(q) * v;
@@ -348,9 +355,9 @@ cudaError_t launch_advance(es_ctx* c) {
 cudaError_t launch_fill_rest(es_ctx* c) {
     long long n = 19 * c->g.N;
     if (mixed(c))
-        k_fill_rest<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, (float*)c->pdf[0], (float*)c->pdf[1]);
+        k_fill_rest<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (float*)c->pdf[0], (float*)c->pdf[1]);
     else
-        k_fill_rest<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, (double*)c->pdf[0], (double*)c->pdf[1]);
+        k_fill_rest<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (double*)c->pdf[0], (double*)c->pdf[1]);
     count(c);
     return cudaGetLastError();
 }
@@ -358,9 +365,9 @@ cudaError_t launch_fill_rest(es_ctx* c) {
 cudaError_t launch_get_pdf(es_ctx* c, int buf, double* dst) {
     long long n = 19 * c->g.N;
     if (mixed(c))
-        k_get_pdf<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, (const float*)c->pdf[buf], dst);
+        k_get_pdf<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const float*)c->pdf[buf], dst);
     else
-        k_get_pdf<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, (const double*)c->pdf[buf], dst);
+        k_get_pdf<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const double*)c->pdf[buf], dst);
     count(c);
     return cudaGetLastError();
 }
@@ -368,9 +375,9 @@ cudaError_t launch_get_pdf(es_ctx* c, int buf, double* dst) {
 cudaError_t launch_set_pdf(es_ctx* c, const double* src) {
     long long n = 19 * c->g.N;
     if (mixed(c))
-        k_set_pdf<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, src, (float*)c->pdf[c->cur]);
+        k_set_pdf<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, src, (float*)c->pdf[c->cur]);
     else
-        k_set_pdf<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, src, (double*)c->pdf[c->cur]);
+        k_set_pdf<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, src, (double*)c->pdf[c->cur]);
     count(c);
     return cudaGetLastError();
 }
@@ -378,10 +385,10 @@ cudaError_t launch_set_pdf(es_ctx* c, const double* src) {
 cudaError_t launch_get_moments(es_ctx* c, double* rho, double* u) {
     const double* a = c->P.accel;
     if (mixed(c))
-        k_moments<float><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, (const float*)c->pdf[c->cur],
+        k_moments<float><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const float*)c->pdf[c->cur],
                                                                          (const float*)c->fb, a[0], a[1], a[2], rho, u);
     else
-        k_moments<double><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, (const double*)c->pdf[c->cur],
+        k_moments<double><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const double*)c->pdf[c->cur],
                                                                           (const double*)c->fb, a[0], a[1], a[2], rho, u);
     count(c);
     return cudaGetLastError();
@@ -412,11 +419,11 @@ cudaError_t launch_gather(es_ctx* c, int which, const long long* idx, int n, dou
     int last = c->last_src >= 0 ? c->last_src : c->cur;
     if (mixed(c))
         k_gather<float><<<blocks_for(n, 128), 128, 0, c->stream>>>(
-            which, c->g.N, idx, n, (const float*)c->pdf[c->cur], (const float*)c->pdf[last], (const float*)c->fb,
+            which, c->g.N, c->g.ps, idx, n, (const float*)c->pdf[c->cur], (const float*)c->pdf[last], (const float*)c->fb,
             c->psi, c->owner, c->flags, a[0], a[1], a[2], out);
     else
         k_gather<double><<<blocks_for(n, 128), 128, 0, c->stream>>>(
-            which, c->g.N, idx, n, (const double*)c->pdf[c->cur], (const double*)c->pdf[last],
+            which, c->g.N, c->g.ps, idx, n, (const double*)c->pdf[c->cur], (const double*)c->pdf[last],
             (const double*)c->fb, c->psi, c->owner, c->flags, a[0], a[1], a[2], out);
     count(c);
     return cudaGetLastError();

@@ -133,7 +133,7 @@ __global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, i
             double cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
             // f^eq(rho_0 = 1, u_s) of Eq. fequ_Incompr_SRT
             double dev = wq(q) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-            pdf[(long long)q * g.N + c] = shifted ? (S)dev : (S)(wq(q) + dev);
+            pdf[(long long)q * g.ps + c] = shifted ? (S)dev : (S)(wq(q) + dev);
         }
     }
 }
