@@ -50,6 +50,8 @@ int validate(const es_params* P, const es_particle* parts, int n, std::string& w
         if (P->periodic[a] && d > 1 && ((d >> (P->levels - 1)) % 2) != 0)
             return why = "periodic extents must stay even on every level (red-black ordering)", ES_EINVAL;
     }
+    if ((long long)P->dims[0] * P->dims[1] * P->dims[2] >= (1LL << 31))
+        return why = "more than 2^31 - 1 cells (32-bit cell indices)", ES_EINVAL;
     for (int f = 0; f < 6; f++)
         if (P->pot_bc[f] != ES_POT_ZERO_FLUX && P->pot_bc[f] != ES_POT_DIRICHLET)
             return why = "unknown potential boundary kind", ES_EINVAL;
@@ -100,6 +102,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     b += 2 * 19 * pdf_stride(N) * s;  // pdf ping-pong
     b += 3 * N * s;       // body force
     b += N * 8;           // psi
+    if (P->precision == ES_MIXED32) b += N * 4;  // float copy of psi
     b += N * 4 + N;       // owner, flags
     size_t lv = 0;
     for (int l = 0; l < P->levels; l++) {
@@ -201,6 +204,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->cur = 0;
     c->last_src = -1;
     c->red_blocks = 4 * 152;
+    c->mg_rate = 0.15;
 
     const long long N = c->g.N;
     const size_t s = mixed(c) ? 4 : 8;
@@ -215,6 +219,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->pdf[1] = A(19 * c->g.ps * s);
     c->fb = A(3 * N * s);
     c->psi = (double*)A(N * 8);
+    c->psi32 = mixed(c) ? (float*)A(N * 4) : nullptr;
     c->owner = (int32_t*)A(N * 4);
     c->flags = (uint8_t*)A(N);
     for (int l = 0; l < c->L; l++) {
@@ -261,6 +266,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->kind, hk.data(), np1 * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->mapped, hm.data(), np1 * 9 * 8, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->psi, 0, N * 8, c->stream);
+    if (e == cudaSuccess && c->psi32) e = cudaMemsetAsync(c->psi32, 0, N * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fb, 0, 3 * N * s, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->F, 0, np1 * 3 * 8, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->T, 0, np1 * 3 * 8, c->stream);
@@ -329,12 +335,29 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
                 break;
             }
         }
-        ES_CUDA(c, launch_vcycle(c));
+        // V-cycles per FP64 correction: one in the FP64 form (the oracle's
+        // iteration); in MIXED32 as many FP32 cycles, warm-started on the
+        // same defect, as the running rate estimate says will bring the
+        // residual to half the tolerance (at most 6, i.e. within FP32 reach)
+        int k = 1;
+        if (mixed(c) && forced_cycles < 0) {
+            double want = std::log(0.5 * c->tol / norm) / std::log(c->mg_rate);
+            k = (int)std::ceil(want);
+            k = k < 1 ? 1 : (k > 6 ? 6 : k);
+            if (k > c->P.max_cycles - cycles) k = c->P.max_cycles - cycles;
+        }
+        for (int j = 0; j < k; j++) ES_CUDA(c, launch_vcycle(c, j > 0));
         ES_CUDA(c, launch_correct(c));
         ES_CUDA(c, launch_outer_residual(c));
+        const double before = norm;
         rc = read_norm_status(c, &norm, &st);
         if (rc != ES_OK) return rc;
-        cycles++;
+        cycles += k;
+        if (norm > 0.0 && before > 0.0) {
+            double observed = std::pow(norm / before, 1.0 / k);
+            observed = observed < 0.01 ? 0.01 : (observed > 0.9 ? 0.9 : observed);
+            c->mg_rate = std::exp(0.5 * std::log(c->mg_rate) + 0.5 * std::log(observed));
+        }
     }
     if (info) {
         info->cycles = cycles;
@@ -460,6 +483,7 @@ int es_set_field(es_ctx* c, int which, const void* src, size_t bytes, int on_dev
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (which == ES_FIELD_PSI) {
         ES_CUDA(c, cudaMemcpyAsync(c->psi, src, bytes, k, c->stream));
+        ES_CUDA(c, launch_psi32(c));
     } else {
         const double* dsrc = (const double*)src;
         if (!on_device) {

@@ -6,7 +6,8 @@
 //               which keeps FP32 resolution for the small deviations.
 //   flags       N bytes: F_SOLID, F_NEAR19 (LBM / gradient fast path switch)
 //   owner       N int32: sphere index of an obstacle cell, -1 fluid
-//   psi         N doubles: EDL potential (outer FP64 iterate)
+//   psi         N doubles: EDL potential (outer FP64 iterate); MIXED32 also
+//               keeps a float copy psi32 for the FP32 body-force kernel
 //   fb          3 x N body force in the storage type of the PDFs
 //   st[l]       per multigrid level N_l bytes: kind (unknown / Dirichlet /
 //               Neumann) and a "near boundary" bit; the stencil is implied by
@@ -97,6 +98,7 @@ struct es_ctx {
     uint8_t* flags;
     int32_t* owner;
     double* psi;
+    float* psi32;    // MIXED32: float copy of psi for the FP32 body force
     void* fb;
     // multigrid
     int L;
@@ -112,6 +114,7 @@ struct es_ctx {
     int* h_status;   // pinned
     double tol;
     int have_tol;
+    double mg_rate;  // running estimate of the residual reduction per V-cycle
     double lambda_e, lambda_o;
     size_t bytes;
     unsigned long long launches;  // kernels launched by this context
@@ -129,7 +132,8 @@ cudaError_t launch_map(es_ctx* c);
 cudaError_t launch_coarse_states(es_ctx* c);
 // solver (es_solver.cu)
 cudaError_t launch_outer_residual(es_ctx* c);
-cudaError_t launch_vcycle(es_ctx* c);
+cudaError_t launch_vcycle(es_ctx* c, int warm);
+cudaError_t launch_psi32(es_ctx* c);
 cudaError_t launch_correct(es_ctx* c);
 cudaError_t launch_body_force(es_ctx* c);
 // lbm and particles (es_lbm.cu)

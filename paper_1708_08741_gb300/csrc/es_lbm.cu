@@ -32,24 +32,28 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
                                              const uint8_t* __restrict__ flags, const int32_t* __restrict__ owner,
                                              const DParticle* __restrict__ part, const S* __restrict__ fb,
                                              S ax, S ay, S az, S lam_e, S lam_o) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    const long long N = g.N, ps = g.ps;
-    const long long c = lin(g, x, y, z);
+    // 32-bit cell offsets (N < 2^31); stream q starts at src + q * ps
+    const unsigned N = (unsigned)g.N;
+    const size_t ps = (size_t)g.ps;
+    const int nx = g.nx, nxy = g.nx * g.ny;
+    const int c = x + nx * (y + g.ny * z);
     const uint8_t fl = flags[c];
     if (fl & F_SOLID) return;  // obstacle cells are not updated
 
     S f[19];
     if (!(fl & F_NEAR19)) {
-        // all 18 pull sources are fluid cells inside the (periodic) domain
-        const int xs[3] = {x == g.nx - 1 ? 0 : x + 1, x, x == 0 ? g.nx - 1 : x - 1};
-        const int ys[3] = {y == g.ny - 1 ? 0 : y + 1, y, y == 0 ? g.ny - 1 : y - 1};
-        const int zs[3] = {z == g.nz - 1 ? 0 : z + 1, z, z == 0 ? g.nz - 1 : z - 1};
+        // all 18 pull sources are fluid cells inside the (periodic) domain;
+        // the offset of x - e_q is a sum of per-axis steps (wrapped at faces)
+        const int sx[3] = {(x == nx - 1 ? 0 : x + 1) - x, 0, (x == 0 ? nx - 1 : x - 1) - x};
+        const int sy[3] = {((y == g.ny - 1 ? 0 : y + 1) - y) * nx, 0, ((y == 0 ? g.ny - 1 : y - 1) - y) * nx};
+        const int sz[3] = {((z == g.nz - 1 ? 0 : z + 1) - z) * nxy, 0, ((z == 0 ? g.nz - 1 : z - 1) - z) * nxy};
 #pragma unroll
         for (int q = 0; q < 19; q++) {
-            long long s = lin(g, xs[1 + cx(q)], ys[1 + cy(q)], zs[1 + cz(q)]);
-            f[q] = __ldg(src + (long long)q * ps + s);
+            const int s_ = c + sx[1 + cx(q)] + sy[1 + cy(q)] + sz[1 + cz(q)];
+            f[q] = __ldg(src + q * ps + s_);
         }
     } else {
         f[0] = src[c];
@@ -58,12 +62,12 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
             long long nb;
             if (!neighbour(g, x, y, z, -cx(q), -cy(q), -cz(q), nb)) {
                 // resting no-slip wall half-way outside: bounce back
-                f[q] = src[(long long)opp(q) * ps + c];
+                f[q] = src[opp(q) * ps + c];
                 continue;
             }
-            int o = owner[nb];
+            const int o = owner[nb];
             if (o < 0) {
-                f[q] = src[(long long)q * ps + nb];
+                f[q] = src[q * ps + nb];
                 continue;
             }
             // moving bounce-back (Eq. LBMMovWall): the population sent from x
@@ -74,13 +78,13 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
             bz = bz < 0 ? bz + g.nz : (bz >= g.nz ? bz - g.nz : bz);
             double us[3];
             surface_velocity(g, part[o].x, part[o].v, part[o].w, bx, by, bz, us);
-            double cu = cx(q) * us[0] + cy(q) * us[1] + cz(q) * us[2];
-            f[q] = src[(long long)opp(q) * ps + c] + (S)(6.0 * wq(q) * cu);
+            const double cu = cx(q) * us[0] + cy(q) * us[1] + cz(q) * us[2];
+            f[q] = src[opp(q) * ps + c] + (S)(6.0 * wq(q) * cu);
         }
     }
 
     // body force (Sec. 5.6) plus a uniform acceleration
-    const S fx = fb[c] + ax, fy = fb[N + c] + ay, fz = fb[2 * N + c] + az;
+    const S fx = fb[c] + ax, fy = fb[N + c] + ay, fz = fb[2u * N + c] + az;
 
     // moments (Eq. MacroscopVel) with the modified velocity (Eq. modified_velocity)
     S rho = (S)0, jx = (S)0, jy = (S)0, jz = (S)0;
@@ -121,16 +125,17 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
         const S Fo = w * (S)3 * cf;
         const S even = lam_e * (fe - eq_e) + ae * Fe;
         const S odd = lam_o * (fo - eq_o) + ao * Fo;
-        dst[(long long)q * ps + c] = f[q] + even + odd;
-        dst[(long long)(q + 9) * ps + c] = f[q + 9] + even - odd;
+        dst[q * ps + c] = f[q] + even + odd;
+        dst[(q + 9) * ps + c] = f[q + 9] + even - odd;
     }
 }
 
-// Momentum exchange (Eq. LBMhydrodynForce): one block per sphere; its
-// threads stride over (cell, direction) pairs of the box around the sphere,
-// and every link x_F -> x_F + e_q into the sphere adds
-// [2 f~_q(x_F) - 2 w_q (c_q . u_s)/c_s^2] c_q, the torque (x_s - X) x dF.
-// A fixed item order per thread and a fixed reduction tree: deterministic.
+// Momentum exchange (Eq. LBMhydrodynForce): one block per sphere; threads
+// stride over the cells of the box around the sphere, and every link
+// x_F -> x_F + e_q into the sphere adds [2 f~_q(x_F) - 2 w_q (c_q . u_s)/c_s^2] c_q,
+// the torque (x_s - X) x dF.  The 18 owner loads of a near-boundary cell are
+// independent and issued together.  A fixed cell order per thread and a
+// fixed reduction tree make the sums deterministic.
 template <class S>
 __global__ void __launch_bounds__(256) k_forces(Grid g, const DParticle* __restrict__ part,
                                                 const int32_t* __restrict__ owner,
@@ -142,36 +147,44 @@ __global__ void __launch_bounds__(256) k_forces(Grid g, const DParticle* __restr
     int lo[3], hi[3];
     for (int a = 0; a < 3; a++) axis_range(g, a, P.x[a], P.x[a], P.R, 1, lo[a], hi[a]);
     const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
-    const int items = sx * sy * sz * 18;
+    const int n = sx * sy * sz;
+    const size_t ps = (size_t)g.ps;
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int t = it / 18, q = it - 18 * t + 1;
-        const int x = wrap_coord(lo[0] + t % sx, g.nx);
-        const int y = wrap_coord(lo[1] + (t / sx) % sy, g.ny);
-        const int z = wrap_coord(lo[2] + t / (sx * sy), g.nz);
-        const long long c = lin(g, x, y, z);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int tx = t % sx, tyz = t / sx;
+        const int x = wrap_coord(lo[0] + tx, g.nx);
+        const int y = wrap_coord(lo[1] + tyz % sy, g.ny);
+        const int z = wrap_coord(lo[2] + tyz / sy, g.nz);
+        const int c = x + g.nx * (y + g.ny * z);
         if (!(flags[c] & F_NEAR19)) continue;
-        const int dx = cx(q), dy = cy(q), dz = cz(q);
-        long long nb;
-        if (!neighbour(g, x, y, z, dx, dy, dz, nb)) continue;
-        if (owner[nb] != p) continue;
-        const int bx = wrap_coord(x + dx, g.nx), by = wrap_coord(y + dy, g.ny), bz = wrap_coord(z + dz, g.nz);
-        const double r0 = cell_disp(g, 0, bx, P.x[0]);
-        const double r1 = cell_disp(g, 1, by, P.x[1]);
-        const double r2 = cell_disp(g, 2, bz, P.x[2]);
-        const double us0 = P.v[0] + (P.w[1] * r2 - P.w[2] * r1);
-        const double us1 = P.v[1] + (P.w[2] * r0 - P.w[0] * r2);
-        const double us2 = P.v[2] + (P.w[0] * r1 - P.w[1] * r0);
-        const double cu = dx * us0 + dy * us1 + dz * us2;
-        const double fq = (double)src[(long long)q * g.ps + c] + Store<S>::offset(q);
-        const double m = 2.0 * fq - 6.0 * wq(q) * cu;
-        const double d0 = m * dx, d1 = m * dy, d2 = m * dz;
-        acc[0] += d0;
-        acc[1] += d1;
-        acc[2] += d2;
-        acc[3] += r1 * d2 - r2 * d1;
-        acc[4] += r2 * d0 - r0 * d2;
-        acc[5] += r0 * d1 - r1 * d0;
+        int own[19];
+#pragma unroll
+        for (int q = 1; q < 19; q++) {
+            long long nb;
+            own[q] = neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb) ? owner[nb] : -1;
+        }
+#pragma unroll
+        for (int q = 1; q < 19; q++) {
+            if (own[q] != p) continue;
+            const int bx = wrap_coord(x + cx(q), g.nx), by = wrap_coord(y + cy(q), g.ny),
+                      bz = wrap_coord(z + cz(q), g.nz);
+            const double r0 = cell_disp(g, 0, bx, P.x[0]);
+            const double r1 = cell_disp(g, 1, by, P.x[1]);
+            const double r2 = cell_disp(g, 2, bz, P.x[2]);
+            const double us0 = P.v[0] + (P.w[1] * r2 - P.w[2] * r1);
+            const double us1 = P.v[1] + (P.w[2] * r0 - P.w[0] * r2);
+            const double us2 = P.v[2] + (P.w[0] * r1 - P.w[1] * r0);
+            const double cu = cx(q) * us0 + cy(q) * us1 + cz(q) * us2;
+            const double fq = (double)src[q * ps + c] + Store<S>::offset(q);
+            const double m = 2.0 * fq - 6.0 * wq(q) * cu;
+            const double d0 = m * cx(q), d1 = m * cy(q), d2 = m * cz(q);
+            acc[0] += d0;
+            acc[1] += d1;
+            acc[2] += d2;
+            acc[3] += r1 * d2 - r2 * d1;
+            acc[4] += r2 * d0 - r0 * d2;
+            acc[5] += r0 * d1 - r1 * d0;
+        }
     }
     const double E[3] = {Ex, Ey, Ez};
     for (int k = 0; k < 6; k++) {
@@ -206,14 +219,13 @@ __global__ void k_advance(int np, DParticle* part, const double* F, const double
 }
 
 template <class S>
-__global__ void k_fill_rest(long long N, long long ps, S* a, S* b) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 19 * N) return;
-    int q = (int)(i / N);
-    long long j = (long long)q * ps + (i - (long long)q * N);
-    S v = Store<S>::rest(q);
-    a[j] = v;
-    b[j] = v;
+__global__ void k_fill_rest(int N, size_t ps, S* a, S* b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (i >= N) return;
+    const S v = Store<S>::rest(q);
+    a[q * ps + i] = v;
+    b[q * ps + i] = v;
 }
 
 // PDFs are exchanged densely (19 x N doubles) and stored with stride ps.
@@ -353,11 +365,12 @@ cudaError_t launch_advance(es_ctx* c) {
 }
 
 cudaError_t launch_fill_rest(es_ctx* c) {
-    long long n = 19 * c->g.N;
+    const int N = (int)c->g.N;
+    dim3 grd((N + 255) / 256, 19);
     if (mixed(c))
-        k_fill_rest<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (float*)c->pdf[0], (float*)c->pdf[1]);
+        k_fill_rest<float><<<grd, 256, 0, c->stream>>>(N, (size_t)c->g.ps, (float*)c->pdf[0], (float*)c->pdf[1]);
     else
-        k_fill_rest<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (double*)c->pdf[0], (double*)c->pdf[1]);
+        k_fill_rest<double><<<grd, 256, 0, c->stream>>>(N, (size_t)c->g.ps, (double*)c->pdf[0], (double*)c->pdf[1]);
     count(c);
     return cudaGetLastError();
 }

@@ -89,7 +89,7 @@ __global__ void k_clear(Grid g, const DParticle* part, const double* mapped, int
 }
 
 __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* owner, double* psi,
-                      int* status) {
+                      float* psi32, int* status) {
     int p = blockIdx.x;
     DParticle P = part[p];
     if (threadIdx.x == 0) {
@@ -98,7 +98,8 @@ __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* o
                 atomicOr(status, DS_WALLCUT);
     }
     // boundary value kept in the solution field at boundary cells (Sec. 5.4)
-    double bval = kind[p] == ES_KIND_ZETA ? P.zeta : 0.0;
+    const double bval = kind[p] == ES_KIND_ZETA ? P.zeta : 0.0;
+    const float bval32 = (float)bval;
     Box b = sphere_box(g, P.x, P.R, 0);
     int n = b.count();
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -109,6 +110,7 @@ __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* o
         int old = atomicExch(&owner[c], p);
         if (old >= 0 && old != p) atomicOr(status, DS_OVERLAP);
         psi[c] = bval;
+        if (psi32) psi32[c] = bval32;
     }
 }
 
@@ -274,7 +276,7 @@ cudaError_t launch_map(es_ctx* c) {
     const Grid& g = c->g;
     const int T = 256;
     k_clear<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner);
-    k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->d_status);
+    k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->psi32, c->d_status);
     if (mixed(c))
         k_uncover<float><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (float*)c->pdf[c->cur]);
     else

@@ -11,6 +11,11 @@
 //
 // The outer loop runs in FP64 on psi; the V-cycle solves A e = r for the
 // correction in the inner type T (double, or float in the MIXED32 form).
+//
+// GB300 executes FP64 arithmetic (and conversions to and from FP64) on a
+// pipe with 1/64 of the FP32 rate, so the FP32 kernels here carry no double
+// operand at all: level constants come in as T, cell indices are 32-bit
+// (N < 2^31), and the MIXED32 body force reads a float copy of psi.
 #include "es_device.cuh"
 
 namespace es {
@@ -19,20 +24,21 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-struct LevelDesc {
+template <class T>
+struct Level {
     int nx, ny, nz;
     int per[3];
     int pot_bc[6];
-    double h2;    // h_l^2
-    double diag0; // 6 + kappa^2 h_l^2
+    T h2;     // h_l^2
+    T diag0;  // 6 + kappa^2 h_l^2
 };
 
 // Fine-level face contribution for the FP64 outer residual: adds the centre
-// adjustment to diag and the boundary value to b, or returns the neighbour
-// index of an unknown neighbour (>= 0).
-__device__ __forceinline__ long long fine_face(const Grid& g, const Solver& s, const int32_t* owner,
-                                               const DParticle* part, const int* kind, int x, int y,
-                                               int z, int a, int side, double& diag, double& b) {
+// adjustment to diag and the boundary value to b, or returns the index of an
+// unknown neighbour (>= 0).
+__device__ __forceinline__ int fine_face(const Grid& g, const Solver& s, const int32_t* owner,
+                                         const DParticle* part, const int* kind, int x, int y, int z, int a,
+                                         int side, double& diag, double& b) {
     int d[3] = {0, 0, 0};
     d[a] = side;
     long long nb;
@@ -47,7 +53,7 @@ __device__ __forceinline__ long long fine_face(const Grid& g, const Solver& s, c
         return -1;
     }
     int o = owner[nb];
-    if (o < 0) return nb;
+    if (o < 0) return (int)nb;
     if (kind[o] == ES_KIND_ZETA) {
         diag += 1.0;
         b += 2.0 * part[o].zeta;
@@ -59,46 +65,53 @@ __device__ __forceinline__ long long fine_face(const Grid& g, const Solver& s, c
 }
 
 // r = b - A psi on the unknowns (FP64), stored as the V-cycle right-hand
-// side in type T, and per-block partial sums of r^2.
+// side in type T, and per-block partial sums of r^2.  Blocks stride over
+// rows (y, z); threads over x.  At an interior cell this is 5 adds, 2 FMAs
+// and one conversion in FP64.
 template <class T>
-__global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s, const double* psi,
-                                                                const uint8_t* st0, const int32_t* owner,
-                                                                const DParticle* part, const int* kind,
-                                                                T* r_out, double* partial) {
+__global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s, double diag0,
+                                                                const double* __restrict__ psi,
+                                                                const uint8_t* __restrict__ st0,
+                                                                const int32_t* __restrict__ owner,
+                                                                const DParticle* __restrict__ part,
+                                                                const int* __restrict__ kind, T* __restrict__ r_out,
+                                                                double* __restrict__ partial) {
     __shared__ double sh[32];
     double acc = 0.0;
-    const double diag0 = 6.0 + s.kappa * s.kappa;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N; c += stride) {
-        uint8_t st = st0[c];
-        double r = 0.0;
-        if ((st & ST_KIND) == ST_UNKNOWN) {
-            int x = (int)(c % g.nx);
-            long long yz = c / g.nx;
-            int y = (int)(yz % g.ny);
-            int z = (int)(yz / g.ny);
-            double diag = diag0, b = 0.0, off = 0.0;
-            if (!(st & ST_NEAR)) {
-                int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
-                int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-                int zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-                off = psi[lin(g, xm, y, z)];
-                off += psi[lin(g, xp, y, z)];
-                off += psi[lin(g, x, ym, z)];
-                off += psi[lin(g, x, yp, z)];
-                off += psi[lin(g, x, y, zm)];
-                off += psi[lin(g, x, y, zp)];
-            } else {
-                for (int a = 0; a < 3; a++)
-                    for (int side = -1; side <= 1; side += 2) {
-                        long long nb = fine_face(g, s, owner, part, kind, x, y, z, a, side, diag, b);
-                        if (nb >= 0) off += psi[nb];
-                    }
+    const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
+    const int rows = g.ny * g.nz;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int y = row % ny, z = row / ny;
+        const int base = row * nx;
+        const int ym = (y == 0 ? ny - 1 : y - 1) - y, yp = (y == ny - 1 ? 0 : y + 1) - y;
+        const int zm = (z == 0 ? g.nz - 1 : z - 1) - z, zp = (z == g.nz - 1 ? 0 : z + 1) - z;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const int c = base + x;
+            const uint8_t st = st0[c];
+            double r = 0.0;
+            if ((st & ST_KIND) == ST_UNKNOWN) {
+                if (!(st & ST_NEAR)) {
+                    const int xm = (x == 0 ? nx - 1 : x - 1) - x, xp = (x == nx - 1 ? 0 : x + 1) - x;
+                    double off = psi[c + xm];
+                    off += psi[c + xp];
+                    off += psi[c + ym * nx];
+                    off += psi[c + yp * nx];
+                    off += psi[c + zm * nxy];
+                    off += psi[c + zp * nxy];
+                    r = off - diag0 * psi[c];
+                } else {
+                    double diag = diag0, b = 0.0, off = 0.0;
+                    for (int a = 0; a < 3; a++)
+                        for (int side = -1; side <= 1; side += 2) {
+                            int nb = fine_face(g, s, owner, part, kind, x, y, z, a, side, diag, b);
+                            if (nb >= 0) off += psi[nb];
+                        }
+                    r = b - (diag * psi[c] - off);
+                }
+                acc += r * r;
             }
-            r = b - (diag * psi[c] - off);
-            acc += r * r;
+            r_out[c] = (T)r;
         }
-        r_out[c] = (T)r;
     }
     double tot = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
@@ -115,52 +128,50 @@ __global__ void k_finalize_norm(const double* partial, int n, double* out) {
 // Diagonal and off-diagonal sum of level l at an unknown cell.  With
 // READ = false only the diagonal is formed (off = 0, e is not touched).
 template <class T, bool READ = true>
-__device__ __forceinline__ void level_stencil(const LevelDesc& L, const uint8_t* st, const T* e, int x,
-                                              int y, int z, uint8_t s, T& diag, T& off) {
-    long long nxny = (long long)L.nx * L.ny;
-    if (!READ && !(s & ST_NEAR)) {
-        diag = (T)L.diag0;
-        off = (T)0;
-        return;
-    }
+__device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* st, const T* e, int x, int y,
+                                              int z, uint8_t s, T& diag, T& off) {
+    const int nx = L.nx, nxy = L.nx * L.ny;
+    const int c = x + nx * y + nxy * z;
     if (!(s & ST_NEAR)) {
-        int xm = x == 0 ? L.nx - 1 : x - 1, xp = x == L.nx - 1 ? 0 : x + 1;
-        int ym = y == 0 ? L.ny - 1 : y - 1, yp = y == L.ny - 1 ? 0 : y + 1;
-        int zm = z == 0 ? L.nz - 1 : z - 1, zp = z == L.nz - 1 ? 0 : z + 1;
-        long long row = (long long)y * L.nx + (long long)z * nxny;
-        off = e[row + xm];
-        off += e[row + xp];
-        off += e[(long long)ym * L.nx + (long long)z * nxny + x];
-        off += e[(long long)yp * L.nx + (long long)z * nxny + x];
-        off += e[(long long)y * L.nx + (long long)zm * nxny + x];
-        off += e[(long long)y * L.nx + (long long)zp * nxny + x];
-        diag = (T)L.diag0;
+        diag = L.diag0;
+        if (!READ) {
+            off = (T)0;
+            return;
+        }
+        const int xm = (x == 0 ? nx - 1 : x - 1) - x, xp = (x == nx - 1 ? 0 : x + 1) - x;
+        const int ym = (y == 0 ? L.ny - 1 : y - 1) - y, yp = (y == L.ny - 1 ? 0 : y + 1) - y;
+        const int zm = (z == 0 ? L.nz - 1 : z - 1) - z, zp = (z == L.nz - 1 ? 0 : z + 1) - z;
+        T o = e[c + xm];
+        o += e[c + xp];
+        o += e[c + ym * nx];
+        o += e[c + yp * nx];
+        o += e[c + zm * nxy];
+        o += e[c + zp * nxy];
+        off = o;
         return;
     }
-    double dg = L.diag0;
+    T dg = L.diag0;
     T o = (T)0;
-    int v[3] = {x, y, z}, n3[3] = {L.nx, L.ny, L.nz};
+    const int v[3] = {x, y, z}, n3[3] = {L.nx, L.ny, L.nz}, stride[3] = {1, nx, nxy};
     for (int a = 0; a < 3; a++)
         for (int side = -1; side <= 1; side += 2) {
-            int w[3] = {v[0], v[1], v[2]};
             int p = v[a] + side;
             if (p < 0 || p >= n3[a]) {
                 if (!L.per[a]) {
-                    dg += (L.pot_bc[2 * a + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? 1.0 : -1.0;
+                    dg += (L.pot_bc[2 * a + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? (T)1 : (T)-1;
                     continue;
                 }
                 p = p < 0 ? p + n3[a] : p - n3[a];
             }
-            w[a] = p;
-            long long nb = (long long)w[0] + (long long)L.nx * w[1] + nxny * w[2];
-            uint8_t k = st[nb] & ST_KIND;
+            const int nb = c + (p - v[a]) * stride[a];
+            const uint8_t k = st[nb] & ST_KIND;
             if (k == ST_UNKNOWN) {
                 if (READ) o += e[nb];
+            } else {
+                dg += (k == ST_DIR) ? (T)1 : (T)-1;
             }
-            else
-                dg += (k == ST_DIR) ? 1.0 : -1.0;
         }
-    diag = (T)dg;
+    diag = dg;
     off = o;
 }
 
@@ -169,80 +180,80 @@ __device__ __forceinline__ void level_stencil(const LevelDesc& L, const uint8_t*
 // row and updates the one of this colour.  first != 0: the iterate starts
 // at zero, so neighbours are not read and the pair's other cell is zeroed.
 template <class T>
-__global__ void __launch_bounds__(128) k_smooth(LevelDesc L, const uint8_t* st, const T* rhs, T* e,
-                                                int colour, int first, T omega) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y, z = blockIdx.z;
+__global__ void __launch_bounds__(128) k_smooth(Level<T> L, const uint8_t* __restrict__ st,
+                                                const T* __restrict__ rhs, T* __restrict__ e, int colour,
+                                                int first, T omega) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
     if (2 * t >= L.nx) return;
-    int par = (colour + y + z) & 1;
-    int x = 2 * t + par;
-    long long row = (long long)L.nx * ((long long)y + (long long)L.ny * z);
+    const int par = (colour + y + z) & 1;
+    const int x = 2 * t + par;
+    const int row = L.nx * (y + L.ny * z);
     if (first && 2 * t + 1 - par < L.nx) e[row + 2 * t + 1 - par] = (T)0;
     if (x >= L.nx) return;  // odd extent: the last pair has one cell
-    long long c = row + x;
-    uint8_t s = st[c];
-    if ((s & ST_KIND) == ST_UNKNOWN) {
-        T diag, off;
-        if (first) {
-            level_stencil<T, false>(L, st, e, x, y, z, s, diag, off);
-        } else {
-            level_stencil<T>(L, st, e, x, y, z, s, diag, off);
-        }
-        T gs = ((T)L.h2 * rhs[c] + off) / diag;
-        e[c] = first ? omega * gs : ((T)1 - omega) * e[c] + omega * gs;
-    }
+    const int c = row + x;
+    const uint8_t s = st[c];
+    if ((s & ST_KIND) != ST_UNKNOWN) return;
+    T diag, off;
+    if (first)
+        level_stencil<T, false>(L, st, e, x, y, z, s, diag, off);
+    else
+        level_stencil<T, true>(L, st, e, x, y, z, s, diag, off);
+    const T gs = (L.h2 * rhs[c] + off) / diag;
+    e[c] = first ? omega * gs : ((T)1 - omega) * e[c] + omega * gs;
 }
 
 // Residual of level l at its unknown cells, restricted to level l+1 as the
 // mean of the 8 children (children that are not unknowns contribute 0).
 template <class T>
-__global__ void __launch_bounds__(128) k_residual_restrict(LevelDesc L, const uint8_t* st, const T* rhs,
-                                                           const T* e, int cnx, int cny, int cnz,
-                                                           const uint8_t* cst, T* crhs) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y, k = blockIdx.z;
+__global__ void __launch_bounds__(128) k_residual_restrict(Level<T> L, const uint8_t* __restrict__ st,
+                                                           const T* __restrict__ rhs, const T* __restrict__ e,
+                                                           int cnx, int cny, const uint8_t* __restrict__ cst,
+                                                           T* __restrict__ crhs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
     if (i >= cnx) return;
     T sum = (T)0;
     for (int dk = 0; dk < 2; dk++)
         for (int dj = 0; dj < 2; dj++)
             for (int di = 0; di < 2; di++) {
-                int x = 2 * i + di, y = 2 * j + dj, z = 2 * k + dk;
-                long long c = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * z);
-                uint8_t s = st[c];
+                const int x = 2 * i + di, y = 2 * j + dj, z = 2 * k + dk;
+                const int c = x + L.nx * (y + L.ny * z);
+                const uint8_t s = st[c];
                 T r = (T)0;
                 if ((s & ST_KIND) == ST_UNKNOWN) {
                     T diag, off;
                     level_stencil<T>(L, st, e, x, y, z, s, diag, off);
-                    T Ae = (diag * e[c] - off) / (T)L.h2;
+                    const T Ae = (diag * e[c] - off) / L.h2;
                     r = rhs[c] - Ae;
                 }
                 sum += r;
             }
-    long long C = (long long)i + (long long)cnx * ((long long)j + (long long)cny * k);
+    const int C = i + cnx * (j + cny * k);
     crhs[C] = ((cst[C] & ST_KIND) == ST_UNKNOWN) ? sum / (T)8 : (T)0;
-    (void)cnz;
 }
 
 // e_l += e_{l+1}(parent) at unknown cells whose parent is an unknown
 // (piecewise-constant prolongation).
 template <class T>
-__global__ void __launch_bounds__(128) k_prolong(LevelDesc L, const uint8_t* st, T* e, int cnx, int cny,
-                                                 const uint8_t* cst, const T* ce) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y, z = blockIdx.z;
+__global__ void __launch_bounds__(128) k_prolong(Level<T> L, const uint8_t* __restrict__ st, T* __restrict__ e,
+                                                 int cnx, int cny, const uint8_t* __restrict__ cst,
+                                                 const T* __restrict__ ce) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
     if (x >= L.nx) return;
-    long long c = (long long)x + (long long)L.nx * ((long long)y + (long long)L.ny * z);
-    long long C = (long long)(x >> 1) + (long long)cnx * ((long long)(y >> 1) + (long long)cny * (z >> 1));
+    const int c = x + L.nx * (y + L.ny * z);
+    const int C = (x >> 1) + cnx * ((y >> 1) + cny * (z >> 1));
     if ((st[c] & ST_KIND) == ST_UNKNOWN && (cst[C] & ST_KIND) == ST_UNKNOWN) e[c] += ce[C];
 }
 
 // Coarsest level: one thread block holds the level in shared memory and
 // runs `sweeps` red-black sweeps from a zero iterate.
 template <class T>
-__global__ void __launch_bounds__(1024) k_coarse_solve(LevelDesc L, const uint8_t* st, const T* rhs, T* e,
+__global__ void __launch_bounds__(1024) k_coarse_solve(Level<T> L, const uint8_t* st, const T* rhs, T* e,
                                                        int sweeps, T omega) {
     extern __shared__ unsigned char smem[];
-    int n = L.nx * L.ny * L.nz;
+    const int n = L.nx * L.ny * L.nz;
     T* se = (T*)smem;
     T* sr = se + n;
     uint8_t* ss = (uint8_t*)(sr + n);
@@ -255,13 +266,13 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(LevelDesc L, const uint8_
     for (int s = 0; s < sweeps; s++)
         for (int colour = 0; colour < 2; colour++) {
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                int x = i % L.nx, y = (i / L.nx) % L.ny, z = i / (L.nx * L.ny);
+                const int x = i % L.nx, y = (i / L.nx) % L.ny, z = i / (L.nx * L.ny);
                 if (((x + y + z) & 1) != colour) continue;
-                uint8_t k = ss[i];
+                const uint8_t k = ss[i];
                 if ((k & ST_KIND) != ST_UNKNOWN) continue;
                 T diag, off;
                 level_stencil<T>(L, ss, se, x, y, z, k, diag, off);
-                T gs = ((T)L.h2 * sr[i] + off) / diag;
+                const T gs = (L.h2 * sr[i] + off) / diag;
                 se[i] = ((T)1 - omega) * se[i] + omega * gs;
             }
             __syncthreads();
@@ -270,16 +281,26 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(LevelDesc L, const uint8_
 }
 
 template <class T>
-__global__ void k_zero(T* p, long long n) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_zero(T* p, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = (T)0;
 }
 
+// psi += e at unknown cells; the MIXED32 form also refreshes the float copy.
 template <class T>
-__global__ void k_correct(long long N, const uint8_t* st0, const T* e, double* psi) {
-    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_correct(int N, const uint8_t* __restrict__ st0, const T* __restrict__ e, double* __restrict__ psi,
+                          float* __restrict__ psi32) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    if ((st0[c] & ST_KIND) == ST_UNKNOWN) psi[c] += (double)e[c];
+    if ((st0[c] & ST_KIND) != ST_UNKNOWN) return;
+    const double v = psi[c] + (double)e[c];
+    psi[c] = v;
+    if (psi32) psi32[c] = (float)v;
+}
+
+__global__ void k_psi32(int N, const double* __restrict__ psi, float* __restrict__ psi32) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) psi32[c] = (float)psi[c];
 }
 
 // --- EDL field and body force (Sec. 5.6) ---
@@ -287,78 +308,89 @@ __global__ void k_correct(long long N, const uint8_t* st0, const T* e, double* p
 // Value across face (a, side) of unknown cell c for a D3Q7 central
 // difference: neighbour value, or the boundary value extrapolated from the
 // cell (Dirichlet: 2 v - psi_c; Neumann: psi_c + sigma/eps; wall: psi_c).
-__device__ __forceinline__ double face_value(const Grid& g, const Solver& s, const double* psi,
-                                             const int32_t* owner, const DParticle* part, const int* kind,
-                                             int x, int y, int z, double pc, int a, int side) {
+template <class P>
+__device__ __forceinline__ P face_value(const Grid& g, const Solver& s, const P* psi, const int32_t* owner,
+                                        const DParticle* part, const int* kind, int x, int y, int z, P pc, int a,
+                                        int side) {
     int d[3] = {0, 0, 0};
     d[a] = side;
     long long nb;
     if (!neighbour(g, x, y, z, d[0], d[1], d[2], nb)) {
         int face = 2 * a + (side > 0 ? 1 : 0);
-        return s.pot_bc[face] == ES_POT_DIRICHLET ? 2.0 * s.pot_val[face] - pc : pc;
+        return s.pot_bc[face] == ES_POT_DIRICHLET ? (P)(2.0 * s.pot_val[face]) - pc : pc;
     }
     int o = owner[nb];
     if (o < 0) return psi[nb];
-    if (kind[o] == ES_KIND_ZETA) return 2.0 * part[o].zeta - pc;
-    return pc + part[o].sigma / s.eps;
+    if (kind[o] == ES_KIND_ZETA) return (P)(2.0 * part[o].zeta) - pc;
+    return pc + (P)(part[o].sigma / s.eps);
 }
 
-template <class S>
-__global__ void __launch_bounds__(128) k_body_force(Grid g, Solver s, double Ex, double Ey, double Ez,
-                                                    const double* psi, const uint8_t* flags,
-                                                    const int32_t* owner, const DParticle* part,
-                                                    const int* kind, S* fb) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y, z = blockIdx.z;
+// f_b = rho_e (E_ext - grad psi), rho_e = -kappa^2 eps psi (Eq. ChrgDensDHA),
+// computed in the type P of the potential it reads (double, or the float
+// copy in the MIXED32 form) and stored in the PDF storage type S.
+template <class S, class P>
+__global__ void __launch_bounds__(128) k_body_force(Grid g, Solver s, P Ex, P Ey, P Ez, P k2e,
+                                                    const P* __restrict__ psi, const uint8_t* __restrict__ flags,
+                                                    const int32_t* __restrict__ owner,
+                                                    const DParticle* __restrict__ part, const int* __restrict__ kind,
+                                                    S* __restrict__ fb) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    long long c = lin(g, x, y, z);
-    uint8_t fl = flags[c];
-    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    const int nx = g.nx, nxy = g.nx * g.ny;
+    const int c = x + nx * (y + g.ny * z);
+    const uint8_t fl = flags[c];
+    P f0 = (P)0, f1 = (P)0, f2 = (P)0;
     if (!(fl & F_SOLID)) {
-        double pc = psi[c];
-        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        const P pc = psi[c];
+        P g0, g1, g2;
         if (!(fl & F_NEAR19)) {
-            // isotropic D3Q19 gradient (1/c_s^2) sum_q w_q psi(x + e_q) e_q
+            // isotropic D3Q19 gradient (1/c_s^2) sum_q w_q psi(x + e_q) e_q,
+            // taken pairwise: 3 w_q (psi(x + e_q) - psi(x - e_q)) e_q
+            const int dx[3] = {(x == 0 ? nx - 1 : x - 1) - x, 0, (x == nx - 1 ? 0 : x + 1) - x};
+            const int dy[3] = {((y == 0 ? g.ny - 1 : y - 1) - y) * nx, 0, ((y == g.ny - 1 ? 0 : y + 1) - y) * nx};
+            const int dz[3] = {((z == 0 ? g.nz - 1 : z - 1) - z) * nxy, 0, ((z == g.nz - 1 ? 0 : z + 1) - z) * nxy};
+            g0 = (P)0;
+            g1 = (P)0;
+            g2 = (P)0;
 #pragma unroll
-            for (int q = 1; q < 19; q++) {
-                long long nb;
-                neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb);
-                double v = wq(q) * psi[nb];
-                g0 += v * cx(q);
-                g1 += v * cy(q);
-                g2 += v * cz(q);
+            for (int q = 1; q <= 9; q++) {
+                const int op = dx[1 + cx(q)] + dy[1 + cy(q)] + dz[1 + cz(q)];
+                const int om = dx[1 - cx(q)] + dy[1 - cy(q)] + dz[1 - cz(q)];
+                const P d = (P)(3.0 * wq(q)) * (psi[c + op] - psi[c + om]);
+                if (cx(q)) g0 += cx(q) > 0 ? d : -d;
+                if (cy(q)) g1 += cy(q) > 0 ? d : -d;
+                if (cz(q)) g2 += cz(q) > 0 ? d : -d;
             }
-            g0 *= 3.0;
-            g1 *= 3.0;
-            g2 *= 3.0;
         } else {
-            g0 = 0.5 * (face_value(g, s, psi, owner, part, kind, x, y, z, pc, 0, 1) -
-                        face_value(g, s, psi, owner, part, kind, x, y, z, pc, 0, -1));
-            g1 = 0.5 * (face_value(g, s, psi, owner, part, kind, x, y, z, pc, 1, 1) -
-                        face_value(g, s, psi, owner, part, kind, x, y, z, pc, 1, -1));
-            g2 = 0.5 * (face_value(g, s, psi, owner, part, kind, x, y, z, pc, 2, 1) -
-                        face_value(g, s, psi, owner, part, kind, x, y, z, pc, 2, -1));
+            g0 = (P)0.5 * (face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 0, 1) -
+                           face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 0, -1));
+            g1 = (P)0.5 * (face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 1, 1) -
+                           face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 1, -1));
+            g2 = (P)0.5 * (face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 2, 1) -
+                           face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 2, -1));
         }
-        double rho_e = -s.kappa * s.kappa * s.eps * pc;  // Eq. ChrgDensDHA
+        const P rho_e = -k2e * pc;
         f0 = rho_e * (Ex - g0);
         f1 = rho_e * (Ey - g1);
         f2 = rho_e * (Ez - g2);
     }
     fb[c] = (S)f0;
-    fb[g.N + c] = (S)f1;
-    fb[2 * g.N + c] = (S)f2;
+    fb[(long long)g.N + c] = (S)f1;
+    fb[2LL * g.N + c] = (S)f2;
 }
 
-LevelDesc level_desc(const es_ctx* c, int l) {
-    LevelDesc L;
+template <class T>
+Level<T> level_desc(const es_ctx* c, int l) {
+    Level<T> L;
     L.nx = c->ln[l][0];
     L.ny = c->ln[l][1];
     L.nz = c->ln[l][2];
     for (int a = 0; a < 3; a++) L.per[a] = c->g.per[a];
     for (int f = 0; f < 6; f++) L.pot_bc[f] = c->S.pot_bc[f];
     double h = (double)(1 << l);
-    L.h2 = h * h;
-    L.diag0 = 6.0 + c->S.kappa * c->S.kappa * h * h;
+    L.h2 = (T)(h * h);
+    L.diag0 = (T)(6.0 + c->S.kappa * c->S.kappa * h * h);
     return L;
 }
 
@@ -367,14 +399,16 @@ size_t coarse_smem_bytes(const es_ctx* c, size_t tsize) {
     return n * (2 * tsize + 1);
 }
 
+// One V-cycle on level l for A e = rhs.  warm != 0 (level 0 only): e holds a
+// previous iterate and the cycle improves it instead of starting from zero.
 template <class T>
-cudaError_t vcycle_level(es_ctx* c, int l) {
-    LevelDesc L = level_desc(c, l);
+cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
+    Level<T> L = level_desc<T>(c, l);
     T* e = (T*)c->e[l];
     T* rhs = (T*)c->rhs[l];
     const uint8_t* st = c->st[l];
-    T omega = (T)c->P.omega;
-    long long Nl = (long long)L.nx * L.ny * L.nz;
+    const T omega = (T)c->P.omega;
+    const int Nl = L.nx * L.ny * L.nz;
     dim3 blk(128);
     dim3 half(((L.nx + 1) / 2 + 127) / 128, L.ny, L.nz);
     dim3 full((L.nx + 127) / 128, L.ny, L.nz);
@@ -385,7 +419,7 @@ cudaError_t vcycle_level(es_ctx* c, int l) {
             count(c);
         } else {
             count(c, 2 * c->P.coarse_sweeps + (c->P.coarse_sweeps == 0));
-            if (c->P.coarse_sweeps == 0) k_zero<T><<<(unsigned)((Nl + 255) / 256), 256, 0, c->stream>>>(e, Nl);
+            if (c->P.coarse_sweeps == 0) k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
             for (int s = 0; s < c->P.coarse_sweeps; s++) {
                 k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, s == 0, omega);
                 k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
@@ -393,17 +427,18 @@ cudaError_t vcycle_level(es_ctx* c, int l) {
         }
         return cudaGetLastError();
     }
-    count(c, 2 * c->P.nu1 + 2 * c->P.nu2 + 2 + (c->P.nu1 == 0));
-    if (c->P.nu1 == 0) k_zero<T><<<(unsigned)((Nl + 255) / 256), 256, 0, c->stream>>>(e, Nl);
+    const bool zero_start = !warm;
+    count(c, 2 * c->P.nu1 + 2 * c->P.nu2 + 2 + (c->P.nu1 == 0 && zero_start));
+    if (c->P.nu1 == 0 && zero_start) k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
     for (int s = 0; s < c->P.nu1; s++) {
-        k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, s == 0, omega);
+        k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, s == 0 && zero_start, omega);
         k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
     }
     const int* m = c->ln[l + 1];
     dim3 cgrid((m[0] + 127) / 128, m[1], m[2]);
-    k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], m[2], c->st[l + 1],
+    k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], c->st[l + 1],
                                                          (T*)c->rhs[l + 1]);
-    cudaError_t err = vcycle_level<T>(c, l + 1);
+    cudaError_t err = vcycle_level<T>(c, l + 1, 0);
     if (err != cudaSuccess) return err;
     k_prolong<T><<<full, blk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
     for (int s = 0; s < c->P.nu2; s++) {
@@ -423,32 +458,42 @@ void set_coarse_smem(const es_ctx* c) {
 }  // namespace
 
 cudaError_t launch_outer_residual(es_ctx* c) {
+    const double diag0 = 6.0 + c->S.kappa * c->S.kappa;
     if (mixed(c))
         k_outer_residual<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-            c->g, c->S, c->psi, c->st[0], c->owner, c->part, c->kind, (float*)c->rhs[0], c->partial);
+            c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (float*)c->rhs[0], c->partial);
     else
         k_outer_residual<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-            c->g, c->S, c->psi, c->st[0], c->owner, c->part, c->kind, (double*)c->rhs[0], c->partial);
+            c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (double*)c->rhs[0], c->partial);
     k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, c->red_blocks, c->d_norm);
     count(c, 2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_vcycle(es_ctx* c) {
+cudaError_t launch_vcycle(es_ctx* c, int warm) {
     if (mixed(c)) {
         set_coarse_smem<float>(c);
-        return vcycle_level<float>(c, 0);
+        return vcycle_level<float>(c, 0, warm);
     }
     set_coarse_smem<double>(c);
-    return vcycle_level<double>(c, 0);
+    return vcycle_level<double>(c, 0, warm);
 }
 
 cudaError_t launch_correct(es_ctx* c) {
-    unsigned nb = (unsigned)((c->g.N + 255) / 256);
+    const int N = (int)c->g.N;
+    const unsigned nb = (unsigned)((N + 255) / 256);
     if (mixed(c))
-        k_correct<float><<<nb, 256, 0, c->stream>>>(c->g.N, c->st[0], (const float*)c->e[0], c->psi);
+        k_correct<float><<<nb, 256, 0, c->stream>>>(N, c->st[0], (const float*)c->e[0], c->psi, c->psi32);
     else
-        k_correct<double><<<nb, 256, 0, c->stream>>>(c->g.N, c->st[0], (const double*)c->e[0], c->psi);
+        k_correct<double><<<nb, 256, 0, c->stream>>>(N, c->st[0], (const double*)c->e[0], c->psi, nullptr);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psi32(es_ctx* c) {
+    if (!c->psi32) return cudaSuccess;
+    const int N = (int)c->g.N;
+    k_psi32<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->psi, c->psi32);
     count(c);
     return cudaGetLastError();
 }
@@ -457,12 +502,14 @@ cudaError_t launch_body_force(es_ctx* c) {
     const Grid& g = c->g;
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
     const double* E = c->P.E_ext;
+    const double k2e = c->S.kappa * c->S.kappa * c->S.eps;
     if (mixed(c))
-        k_body_force<float><<<grd, blk, 0, c->stream>>>(g, c->S, E[0], E[1], E[2], c->psi, c->flags, c->owner,
-                                                        c->part, c->kind, (float*)c->fb);
+        k_body_force<float, float><<<grd, blk, 0, c->stream>>>(g, c->S, (float)E[0], (float)E[1], (float)E[2],
+                                                               (float)k2e, c->psi32, c->flags, c->owner, c->part,
+                                                               c->kind, (float*)c->fb);
     else
-        k_body_force<double><<<grd, blk, 0, c->stream>>>(g, c->S, E[0], E[1], E[2], c->psi, c->flags, c->owner,
-                                                         c->part, c->kind, (double*)c->fb);
+        k_body_force<double, double><<<grd, blk, 0, c->stream>>>(g, c->S, E[0], E[1], E[2], k2e, c->psi, c->flags,
+                                                                 c->owner, c->part, c->kind, (double*)c->fb);
     count(c);
     return cudaGetLastError();
 }
