@@ -204,6 +204,28 @@ int es_get_field(es_ctx* ctx, int which, void* dst, size_t bytes, int on_device)
  * double); 1 <= n <= 65536; indices must lie in [0, N).  Synchronises.   */
 int es_gather(es_ctx* ctx, int which, const int64_t* idx, int n, double* out);
 
+/* es_gather without any device allocation.  The paper has no counterpart:
+ * this is a library convenience.  es_gather allocates its device staging
+ * buffer on first use; callers that cannot allocate device memory at that
+ * point -- a thread capturing CUDA work into a graph (cudaMalloc is not
+ * allowed during stream capture), a real-time loop that must not wait on an
+ * allocator, or an application that pre-assigns all device memory -- use
+ * this variant, which stages through a fixed array in the library's device
+ * memory instead and calls no device allocator (no cudaMalloc, cudaFree or
+ * allocator hook).
+ *  - Same arguments, field conversions and output layout as es_gather;
+ *    1 <= n <= ES_GATHER_NOALLOC_MAX (4096), larger n returns ES_EINVAL.
+ *  - The array (640 KiB) is held by every GPU that loads the library until
+ *    the process exits.  The first call on a device looks up the array's
+ *    address on that device (with the device current); make that first call
+ *    before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents; no
+ *    part of it needs to start at zero.  Calls whose GPU work overlaps (two
+ *    streams or two host threads at once) race on it: serialise them.
+ *  - Synchronises the context's stream.                                    */
+#define ES_GATHER_NOALLOC_MAX 4096
+int es_gather_noalloc(es_ctx* ctx, int which, const int64_t* idx, int n, double* out);
+
 /* Overwrites ES_FIELD_PSI, ES_FIELD_FB or ES_FIELD_PDF from doubles.      */
 int es_set_field(es_ctx* ctx, int which, const void* src, size_t bytes, int on_device);
 

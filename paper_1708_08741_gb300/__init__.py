@@ -44,6 +44,7 @@ FIELD_PDF_LAST = 7
 EXPORTED = ("es_create", "es_create_with_allocator", "es_destroy", "es_map_particles", "es_potential_solve",
             "es_lbm_step", "es_forces", "es_advance", "es_step", "es_get_field", "es_set_field",
             "es_get_particles", "es_set_particles", "es_set_forces", "es_synchronize", "es_lattice", "es_gather",
+            "es_gather_noalloc",
             "es_device_bytes", "es_kernel_launches", "es_last_error")
 
 
@@ -126,6 +127,7 @@ def load():
     L.es_get_field.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int]
     L.es_set_field.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int]
     L.es_gather.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P]
+    L.es_gather_noalloc.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P]
     L.es_get_particles.argtypes = [P, ctypes.POINTER(Particle), ctypes.c_int]
     L.es_set_particles.argtypes = [P, ctypes.POINTER(Particle), ctypes.c_int]
     L.es_set_forces.argtypes = [P, P, P, ctypes.c_int]
