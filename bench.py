@@ -293,7 +293,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"suspension {args.n}^3 periodic, {wl.n_particles} charged spheres R=5, "
-                               f"lambda_D=4, E=1e-3, MIXED32, {sim.params.levels}-level V(2,2) to RES_RF 1e-8",
+                               f"lambda_D=4, E=1e-3, MIXED32, {sim.params.levels}-level V(2,2) to RES_RF {wl.res_rf:g}",
                    "cells": N, "fluid_cells": n_fluid, "parallelism": f"replicas x{world}",
                    "l2_policy": "inputs larger than L2 (PDF fields 20 GB)"},
         "mflups": n_fluid * args.steps * world / t_all / 1e6,

@@ -229,6 +229,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
         c->rhs[l] = A(Nl * s);
     }
     c->part = (DParticle*)A(np1 * sizeof(DParticle));
+    c->partf = mixed(c) ? (float*)A(np1 * 12 * sizeof(float)) : nullptr;
     c->mapped = (double*)A(np1 * 9 * 8);
     c->kind = (int*)A(np1 * 4);
     c->nfaces = (int*)A(np1 * 4);

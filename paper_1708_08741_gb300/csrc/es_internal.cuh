@@ -88,6 +88,7 @@ struct es_ctx {
     std::vector<void*> allocs;
     // particles
     es::DParticle* part;   // current state
+    float* partf;          // MIXED32: np x 12 floats (x, v, w) for the FP32 stream-collide
     double* mapped;        // np x 9: x, v, w used by the last mapping
     int* kind;
     int* nfaces;

@@ -25,19 +25,39 @@ struct Store {
     __device__ static S rest(int q) { return shifted ? (S)0 : (S)wq(q); }
     // what to add to a stored value to obtain f_q
     __device__ static double offset(int q) { return shifted ? wq(q) : 0.0; }
+    // the same for a direction known only at run time, with weight w
+    __device__ static double offset_rt(int, double w) { return shifted ? w : 0.0; }
 };
 
+// Base pointers of the 19 source and destination streams, so that an access
+// is a 32-bit cell offset from a base (no 64-bit products in the kernel).
 template <class S>
-__global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, S* __restrict__ dst,
+struct Streams {
+    const S* src[19];
+    S* dst[19];
+};
+
+// Float copy of the particle state used by the FP32 stream-collide (centre,
+// velocity, angular velocity), so that its moving-wall term needs no FP64.
+__global__ void k_particles_f32(int np, const DParticle* __restrict__ part, float* __restrict__ pf) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    for (int a = 0; a < 3; a++) {
+        pf[12 * p + a] = (float)part[p].x[a];
+        pf[12 * p + 3 + a] = (float)part[p].v[a];
+        pf[12 * p + 6 + a] = (float)part[p].w[a];
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
                                              const uint8_t* __restrict__ flags, const int32_t* __restrict__ owner,
-                                             const DParticle* __restrict__ part, const S* __restrict__ fb,
-                                             S ax, S ay, S az, S lam_e, S lam_o) {
+                                             const DParticle* __restrict__ part, const float* __restrict__ partf,
+                                             const S* __restrict__ fb, S ax, S ay, S az, S lam_e, S lam_o) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    // 32-bit cell offsets (N < 2^31); stream q starts at src + q * ps
     const unsigned N = (unsigned)g.N;
-    const size_t ps = (size_t)g.ps;
     const int nx = g.nx, nxy = g.nx * g.ny;
     const int c = x + nx * (y + g.ny * z);
     const uint8_t fl = flags[c];
@@ -53,33 +73,52 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
 #pragma unroll
         for (int q = 0; q < 19; q++) {
             const int s_ = c + sx[1 + cx(q)] + sy[1 + cy(q)] + sz[1 + cz(q)];
-            f[q] = __ldg(src + q * ps + s_);
+            f[q] = __ldg(P.src[q] + s_);
         }
     } else {
-        f[0] = src[c];
+        f[0] = P.src[0][c];
 #pragma unroll
         for (int q = 1; q < 19; q++) {
             long long nb;
             if (!neighbour(g, x, y, z, -cx(q), -cy(q), -cz(q), nb)) {
                 // resting no-slip wall half-way outside: bounce back
-                f[q] = src[opp(q) * ps + c];
+                f[q] = P.src[opp(q)][c];
                 continue;
             }
             const int o = owner[nb];
             if (o < 0) {
-                f[q] = src[q * ps + nb];
+                f[q] = P.src[q][nb];
                 continue;
             }
             // moving bounce-back (Eq. LBMMovWall): the population sent from x
             // towards the surface cell returns with 2 w_q rho_0 (c_q . u_s)/c_s^2
-            int bx = x - cx(q), by = y - cy(q), bz = z - cz(q);
-            bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
-            by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
-            bz = bz < 0 ? bz + g.nz : (bz >= g.nz ? bz - g.nz : bz);
-            double us[3];
-            surface_velocity(g, part[o].x, part[o].v, part[o].w, bx, by, bz, us);
-            const double cu = cx(q) * us[0] + cy(q) * us[1] + cz(q) * us[2];
-            f[q] = src[opp(q) * ps + c] + (S)(6.0 * wq(q) * cu);
+            if constexpr (sizeof(S) == 4) {
+                // FP32 form: lever arm from the float copy of the particle
+                const float* pf = partf + 12 * o;
+                float r[3] = {(float)x + 0.5f - (float)cx(q) - pf[0], (float)y + 0.5f - (float)cy(q) - pf[1],
+                              (float)z + 0.5f - (float)cz(q) - pf[2]};
+                const float Lw[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    if (g.per[a]) {
+                        if (r[a] > 0.5f * Lw[a]) r[a] -= Lw[a];
+                        if (r[a] < -0.5f * Lw[a]) r[a] += Lw[a];
+                    }
+                const float u0 = pf[3] + (pf[7] * r[2] - pf[8] * r[1]);
+                const float u1 = pf[4] + (pf[8] * r[0] - pf[6] * r[2]);
+                const float u2 = pf[5] + (pf[6] * r[1] - pf[7] * r[0]);
+                const float cu = (float)cx(q) * u0 + (float)cy(q) * u1 + (float)cz(q) * u2;
+                f[q] = P.src[opp(q)][c] + (float)(6.0 * wq(q)) * cu;
+            } else {
+                int bx = x - cx(q), by = y - cy(q), bz = z - cz(q);
+                bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
+                by = by < 0 ? by + g.ny : (by >= g.ny ? by - g.ny : by);
+                bz = bz < 0 ? bz + g.nz : (bz >= g.nz ? bz - g.nz : bz);
+                double us[3];
+                surface_velocity(g, part[o].x, part[o].v, part[o].w, bx, by, bz, us);
+                const double cu = cx(q) * us[0] + cy(q) * us[1] + cz(q) * us[2];
+                f[q] = P.src[opp(q)][c] + (S)(6.0 * wq(q) * cu);
+            }
         }
     }
 
@@ -107,7 +146,7 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
         const S w0 = (S)wq(0);
         const S eq0 = w0 * (rho - (S)1.5 * uu);
         const S F0 = w0 * ((S)-3 * uf);
-        dst[c] = f[0] + lam_e * (f[0] - eq0) + ae * F0;
+        P.dst[0][c] = f[0] + lam_e * (f[0] - eq0) + ae * F0;
     }
     // pairs (q, q+9): TRT split into even and odd parts (Eq. TRTOp, Eq. EqPDF_TRT)
 #pragma unroll
@@ -125,22 +164,29 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const S* __restrict__ src, 
         const S Fo = w * (S)3 * cf;
         const S even = lam_e * (fe - eq_e) + ae * Fe;
         const S odd = lam_o * (fo - eq_o) + ao * Fo;
-        dst[q * ps + c] = f[q] + even + odd;
-        dst[(q + 9) * ps + c] = f[q + 9] + even - odd;
+        P.dst[q][c] = f[q] + even + odd;
+        P.dst[q + 9][c] = f[q + 9] + even - odd;
     }
 }
 
-// Momentum exchange (Eq. LBMhydrodynForce): one block per sphere; threads
-// stride over the cells of the box around the sphere, and every link
-// x_F -> x_F + e_q into the sphere adds [2 f~_q(x_F) - 2 w_q (c_q . u_s)/c_s^2] c_q,
-// the torque (x_s - X) x dF.  The 18 owner loads of a near-boundary cell are
-// independent and issued together.  A fixed cell order per thread and a
-// fixed reduction tree make the sums deterministic.
+// Momentum exchange (Eq. LBMhydrodynForce): one block per sphere.  Each
+// link x_F -> x_F + e_q into the sphere adds [2 f~_q(x_F) - 2 w_q (c_q . u_s)/c_s^2] c_q
+// and the torque (x_s - X) x dF.  The box around the sphere is scanned 256
+// cells at a time; the links found are compacted into shared memory in
+// (thread, direction) order by a block prefix sum and then summed one link
+// per thread, so the FP64 arithmetic (1/64 rate on GB300) runs on dense
+// warps instead of on divergent lanes.  Fixed order: deterministic.
+constexpr int kForceThreads = 256;
+
 template <class S>
-__global__ void __launch_bounds__(256) k_forces(Grid g, const DParticle* __restrict__ part,
-                                                const int32_t* __restrict__ owner,
-                                                const uint8_t* __restrict__ flags, const S* __restrict__ src,
-                                                double Ex, double Ey, double Ez, double* F, double* T) {
+__global__ void __launch_bounds__(kForceThreads) k_forces(Grid g, const DParticle* __restrict__ part,
+                                                          const int32_t* __restrict__ owner,
+                                                          const uint8_t* __restrict__ flags,
+                                                          const S* __restrict__ src, double Ex, double Ey, double Ez,
+                                                          double* F, double* T) {
+    __shared__ int s_cell[kForceThreads * 18];
+    __shared__ uint8_t s_q[kForceThreads * 18];
+    __shared__ int s_warp[kForceThreads / 32];
     __shared__ double sh[32];
     const int p = blockIdx.x;
     const DParticle P = part[p];
@@ -149,35 +195,73 @@ __global__ void __launch_bounds__(256) k_forces(Grid g, const DParticle* __restr
     const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
     const int n = sx * sy * sz;
     const size_t ps = (size_t)g.ps;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int tx = t % sx, tyz = t / sx;
-        const int x = wrap_coord(lo[0] + tx, g.nx);
-        const int y = wrap_coord(lo[1] + tyz % sy, g.ny);
-        const int z = wrap_coord(lo[2] + tyz / sy, g.nz);
-        const int c = x + g.nx * (y + g.ny * z);
-        if (!(flags[c] & F_NEAR19)) continue;
-        int own[19];
+    for (int base = 0; base < n; base += kForceThreads) {
+        const int t = base + threadIdx.x;
+        unsigned mask = 0;
+        int c = 0;
+        if (t < n) {
+            const int tx = t % sx, tyz = t / sx;
+            const int x = wrap_coord(lo[0] + tx, g.nx);
+            const int y = wrap_coord(lo[1] + tyz % sy, g.ny);
+            const int z = wrap_coord(lo[2] + tyz / sy, g.nz);
+            c = x + g.nx * (y + g.ny * z);
+            if (flags[c] & F_NEAR19) {
 #pragma unroll
-        for (int q = 1; q < 19; q++) {
-            long long nb;
-            own[q] = neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb) ? owner[nb] : -1;
+                for (int q = 1; q < 19; q++) {
+                    long long nb;
+                    if (neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb) && owner[nb] == p) mask |= 1u << q;
+                }
+            }
         }
+        // block-wide exclusive prefix sum of the link counts
+        const int cnt = __popc(mask);
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        int woff = 0, total = 0;
+        for (int w = 0; w < kForceThreads / 32; w++) {
+            if (w < wid) woff += s_warp[w];
+            total += s_warp[w];
+        }
+        int off = woff + incl - cnt;
+        while (mask) {
+            const int q = __ffs(mask) - 1;
+            mask &= mask - 1;
+            s_cell[off] = c;
+            s_q[off] = (uint8_t)q;
+            off++;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < total; i += kForceThreads) {
+            const int cc = s_cell[i], q = s_q[i];
+            const int x = cc % g.nx, yz = cc / g.nx;
+            const int y = yz % g.ny, z = yz / g.ny;
+            int qx = 0, qy = 0, qz = 0;
 #pragma unroll
-        for (int q = 1; q < 19; q++) {
-            if (own[q] != p) continue;
-            const int bx = wrap_coord(x + cx(q), g.nx), by = wrap_coord(y + cy(q), g.ny),
-                      bz = wrap_coord(z + cz(q), g.nz);
+            for (int k = 1; k < 19; k++)
+                if (k == q) {
+                    qx = cx(k);
+                    qy = cy(k);
+                    qz = cz(k);
+                }
+            const int bx = wrap_coord(x + qx, g.nx), by = wrap_coord(y + qy, g.ny), bz = wrap_coord(z + qz, g.nz);
             const double r0 = cell_disp(g, 0, bx, P.x[0]);
             const double r1 = cell_disp(g, 1, by, P.x[1]);
             const double r2 = cell_disp(g, 2, bz, P.x[2]);
             const double us0 = P.v[0] + (P.w[1] * r2 - P.w[2] * r1);
             const double us1 = P.v[1] + (P.w[2] * r0 - P.w[0] * r2);
             const double us2 = P.v[2] + (P.w[0] * r1 - P.w[1] * r0);
-            const double cu = cx(q) * us0 + cy(q) * us1 + cz(q) * us2;
-            const double fq = (double)src[q * ps + c] + Store<S>::offset(q);
-            const double m = 2.0 * fq - 6.0 * wq(q) * cu;
-            const double d0 = m * cx(q), d1 = m * cy(q), d2 = m * cz(q);
+            const double cu = qx * us0 + qy * us1 + qz * us2;
+            const double w = (q <= 3 || (q >= 10 && q <= 12)) ? 1.0 / 18.0 : 1.0 / 36.0;
+            const double fq = (double)src[q * ps + cc] + Store<S>::offset_rt(q, w);
+            const double m = 2.0 * fq - 6.0 * w * cu;
+            const double d0 = m * qx, d1 = m * qy, d2 = m * qz;
             acc[0] += d0;
             acc[1] += d1;
             acc[2] += d2;
@@ -185,6 +269,7 @@ __global__ void __launch_bounds__(256) k_forces(Grid g, const DParticle* __restr
             acc[4] += r2 * d0 - r0 * d2;
             acc[5] += r0 * d1 - r1 * d0;
         }
+        __syncthreads();
     }
     const double E[3] = {Ex, Ey, Ez};
     for (int k = 0; k < 6; k++) {
@@ -325,18 +410,34 @@ unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+template <class S>
+Streams<S> streams(const es_ctx* c) {
+    Streams<S> P;
+    const S* src = (const S*)c->pdf[c->cur];
+    S* dst = (S*)c->pdf[1 - c->cur];
+    for (int q = 0; q < 19; q++) {
+        P.src[q] = src + (size_t)q * (size_t)c->g.ps;
+        P.dst[q] = dst + (size_t)q * (size_t)c->g.ps;
+    }
+    return P;
+}
+
 cudaError_t launch_lbm(es_ctx* c) {
     const Grid& g = c->g;
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
     const double* a = c->P.accel;
-    if (mixed(c))
-        k_lbm<float><<<grd, blk, 0, c->stream>>>(g, (const float*)c->pdf[c->cur], (float*)c->pdf[1 - c->cur],
-                                                 c->flags, c->owner, c->part, (const float*)c->fb, (float)a[0],
-                                                 (float)a[1], (float)a[2], (float)c->lambda_e, (float)c->lambda_o);
-    else
-        k_lbm<double><<<grd, blk, 0, c->stream>>>(g, (const double*)c->pdf[c->cur], (double*)c->pdf[1 - c->cur],
-                                                  c->flags, c->owner, c->part, (const double*)c->fb, a[0], a[1],
-                                                  a[2], c->lambda_e, c->lambda_o);
+    if (mixed(c)) {
+        if (c->np > 0) {
+            k_particles_f32<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->np, c->part, c->partf);
+            count(c);
+        }
+        k_lbm<float><<<grd, blk, 0, c->stream>>>(g, streams<float>(c), c->flags, c->owner, c->part, c->partf,
+                                                 (const float*)c->fb, (float)a[0], (float)a[1], (float)a[2],
+                                                 (float)c->lambda_e, (float)c->lambda_o);
+    } else {
+        k_lbm<double><<<grd, blk, 0, c->stream>>>(g, streams<double>(c), c->flags, c->owner, c->part, nullptr,
+                                                  (const double*)c->fb, a[0], a[1], a[2], c->lambda_e, c->lambda_o);
+    }
     count(c);
     return cudaGetLastError();
 }
@@ -346,10 +447,10 @@ cudaError_t launch_forces(es_ctx* c) {
     const double* E = c->P.E_ext;
     int src = c->last_src >= 0 ? c->last_src : c->cur;
     if (mixed(c))
-        k_forces<float><<<c->np, 256, 0, c->stream>>>(c->g, c->part, c->owner, c->flags, (const float*)c->pdf[src],
+        k_forces<float><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags, (const float*)c->pdf[src],
                                                       E[0], E[1], E[2], c->F, c->T);
     else
-        k_forces<double><<<c->np, 256, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
+        k_forces<double><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
                                                        (const double*)c->pdf[src], E[0], E[1], E[2], c->F, c->T);
     count(c);
     return cudaGetLastError();

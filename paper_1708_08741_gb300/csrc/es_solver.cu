@@ -24,6 +24,16 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
+__device__ __forceinline__ bool wrap_axis(int v, int n, int per, int& out) {
+    if (v < 0 || v >= n) {
+        if (!per) return false;
+        v = v < 0 ? v + n : v - n;
+    }
+    out = v;
+    return true;
+}
+
+
 template <class T>
 struct Level {
     int nx, ny, nz;
@@ -203,6 +213,153 @@ __global__ void __launch_bounds__(128) k_smooth(Level<T> L, const uint8_t* __res
     e[c] = first ? omega * gs : ((T)1 - omega) * e[c] + omega * gs;
 }
 
+template <class T>
+struct Q4 {
+    T v0, v1, v2, v3;
+};
+__device__ __forceinline__ Q4<float> vld(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Q4<double> vld(const double* p) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *(reinterpret_cast<const double2*>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void vst(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void vst(double* p, double a, double b, double c, double d) {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    *(reinterpret_cast<double2*>(p) + 1) = make_double2(c, d);
+}
+#define ES_VLD(arr, off, ptr)      \
+    do {                           \
+        const auto q_ = vld(ptr);  \
+        arr[(off) + 0] = q_.v0;    \
+        arr[(off) + 1] = q_.v1;    \
+        arr[(off) + 2] = q_.v2;    \
+        arr[(off) + 3] = q_.v3;    \
+    } while (0)
+
+// The update of the 4 cells xs + P0 + 2j of a span (indices known at compile
+// time, so the span arrays stay in registers).
+template <class T, int P0, int W>
+__device__ __forceinline__ void span_update(const Level<T>& L, T inv_diag0, const uint8_t* __restrict__ st,
+                                            T (&c)[W + 8], const T (&a)[W], const T (&b)[W], const T (&d)[W],
+                                            const T (&f)[W], const T (&r)[W], uint2 sw, int xs, int y, int z, int row,
+                                            int rym, int ryp, int rzm, int rzp, int first, T omega) {
+#pragma unroll
+    for (int j = 0; j < W / 2; j++) {
+        const int i = P0 + 2 * j;
+        const uint8_t sv = (uint8_t)(((i < 4 ? sw.x : sw.y) >> (8 * (i & 3))) & 0xFF);
+        if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+        T gs;
+        if (!(sv & ST_NEAR)) {
+            T o = c[i + 3];
+            o += c[i + 5];
+            o += a[i];
+            o += b[i];
+            o += d[i];
+            o += f[i];
+            gs = (L.h2 * r[i] + o) * inv_diag0;
+        } else {
+            T dg = L.diag0, o = (T)0;
+            const int gx = xs + i;
+            const int g3[3] = {gx, y, z}, n3[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++)
+#pragma unroll
+                for (int side = -1; side <= 1; side += 2) {
+                    const int q = g3[ax] + side;
+                    if ((q < 0 || q >= n3[ax]) && !L.per[ax]) {
+                        dg += (L.pot_bc[2 * ax + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? (T)1 : (T)-1;
+                        continue;
+                    }
+                    int nb;
+                    T v;
+                    if (ax == 0) {
+                        int wx;
+                        wrap_axis(q, L.nx, L.per[0], wx);
+                        nb = row + wx;
+                        v = c[i + 4 + side];
+                    } else if (ax == 1) {
+                        nb = (side < 0 ? rym : ryp) + gx;
+                        v = side < 0 ? a[i] : b[i];
+                    } else {
+                        nb = (side < 0 ? rzm : rzp) + gx;
+                        v = side < 0 ? d[i] : f[i];
+                    }
+                    const uint8_t kk = st[nb] & ST_KIND;
+                    if (kk == ST_UNKNOWN)
+                        o += v;
+                    else
+                        dg += (kk == ST_DIR) ? (T)1 : (T)-1;
+                }
+            gs = (L.h2 * r[i] + o) / dg;
+        }
+        c[i + 4] = first ? omega * gs : ((T)1 - omega) * c[i + 4] + omega * gs;
+    }
+}
+
+// One red (colour 0) or black (1) half sweep with W-cell spans (W = 4 or 8):
+// a thread owns cells xs .. xs+W-1 of one row, loads its row (xs-4 ..
+// xs+W+3) and the four neighbour rows as aligned 16-byte vectors (the
+// neighbour rows are shared through L1/L2 with the threads that own them),
+// updates the W/2 cells of the colour, and writes the span back with the
+// other colour's values unchanged.  Same per-cell arithmetic as k_smooth;
+// requires nx % W == 0.  first != 0: the iterate starts at zero; nothing is
+// read and the other colour is written as zero.
+template <class T, int W>
+__global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
+                                                  const T* __restrict__ rhs, T* __restrict__ e, int colour,
+                                                  int first, T omega) {
+    const int xs = W * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    if (xs >= L.nx || y >= L.ny) return;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int row = nx * (y + ny * z);
+    int ym, yp, zm, zp, xl, xr;
+    const bool okym = wrap_axis(y - 1, ny, L.per[1], ym), okyp = wrap_axis(y + 1, ny, L.per[1], yp);
+    const bool okzm = wrap_axis(z - 1, nz, L.per[2], zm), okzp = wrap_axis(z + 1, nz, L.per[2], zp);
+    const bool okxl = wrap_axis(xs - 4, nx, L.per[0], xl), okxr = wrap_axis(xs + W, nx, L.per[0], xr);
+    const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
+    const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
+    T c[W + 8], a[W], b[W], d[W], f[W], r[W];
+#pragma unroll
+    for (int i = 0; i < W + 8; i++) c[i] = (T)0;
+#pragma unroll
+    for (int i = 0; i < W; i++) a[i] = b[i] = d[i] = f[i] = (T)0;
+    if (!first) {
+        if (okxl) ES_VLD(c, 0, e + row + xl);
+#pragma unroll
+        for (int v = 0; v < W; v += 4) {
+            ES_VLD(c, 4 + v, e + row + xs + v);
+            if (okym) ES_VLD(a, v, e + rym + xs + v);
+            if (okyp) ES_VLD(b, v, e + ryp + xs + v);
+            if (okzm) ES_VLD(d, v, e + rzm + xs + v);
+            if (okzp) ES_VLD(f, v, e + rzp + xs + v);
+        }
+        if (okxr) ES_VLD(c, W + 4, e + row + xr);
+    }
+#pragma unroll
+    for (int v = 0; v < W; v += 4) ES_VLD(r, v, rhs + row + xs + v);
+    uint2 sw;
+    if (W == 8) {
+        sw = *reinterpret_cast<const uint2*>(st + row + xs);
+    } else {
+        sw.x = *reinterpret_cast<const unsigned*>(st + row + xs);
+        sw.y = 0;
+    }
+    const int p0 = (colour + y + z) & 1;  // xs is even: cells xs + p0 + 2j have the colour
+    if (p0 == 0)
+        span_update<T, 0, W>(L, inv_diag0, st, c, a, b, d, f, r, sw, xs, y, z, row, rym, ryp, rzm, rzp, first, omega);
+    else
+        span_update<T, 1, W>(L, inv_diag0, st, c, a, b, d, f, r, sw, xs, y, z, row, rym, ryp, rzm, rzp, first, omega);
+#pragma unroll
+    for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[4 + v], c[5 + v], c[6 + v], c[7 + v]);
+}
+
 // Residual of level l at its unknown cells, restricted to level l+1 as the
 // mean of the 8 children (children that are not unknowns contribute 0).
 template <class T>
@@ -245,6 +402,140 @@ __global__ void __launch_bounds__(128) k_prolong(Level<T> L, const uint8_t* __re
     const int c = x + L.nx * (y + L.ny * z);
     const int C = (x >> 1) + cnx * ((y >> 1) + cny * (z >> 1));
     if ((st[c] & ST_KIND) == ST_UNKNOWN && (cst[C] & ST_KIND) == ST_UNKNOWN) e[c] += ce[C];
+}
+
+// Vectorized prolongation: a thread owns 4 fine cells of a row (nx % 4 == 0)
+// and adds the correction of their 2 parents.
+template <class T>
+__global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __restrict__ st, T* __restrict__ e,
+                                                   int cnx, int cny, const uint8_t* __restrict__ cst,
+                                                   const T* __restrict__ ce) {
+    const int xs = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    if (xs >= L.nx || y >= L.ny) return;
+    const int c = xs + L.nx * (y + L.ny * z);
+    const int C = (xs >> 1) + cnx * ((y >> 1) + cny * (z >> 1));
+    const unsigned sw = *reinterpret_cast<const unsigned*>(st + c);
+    const uint8_t c0 = cst[C] & ST_KIND, c1 = cst[C + 1] & ST_KIND;
+    const T e0 = ce[C], e1 = ce[C + 1];
+    const auto q = vld(e + c);
+    T v[4] = {q.v0, q.v1, q.v2, q.v3};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const uint8_t sv = (uint8_t)((sw >> (8 * i)) & ST_KIND);
+        const uint8_t pk = i < 2 ? c0 : c1;
+        if (sv == ST_UNKNOWN && pk == ST_UNKNOWN) v[i] += i < 2 ? e0 : e1;
+    }
+    vst(e + c, v[0], v[1], v[2], v[3]);
+}
+
+// Vectorized residual + restriction: a thread owns 2 coarse cells of a
+// coarse row, i.e. a 4 x 2 x 2 block of fine cells (nx % 4 == 0).  For each
+// of its 4 fine rows it loads the row (with one cell of x halo from the
+// neighbouring vectors) and the 4 neighbour rows as 16-byte vectors, forms
+// the residuals and adds them to the coarse sums in the children order
+// (dk, dj, di) of the scalar kernel.
+template <class T>
+__global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T inv_h2, const uint8_t* __restrict__ st,
+                                                    const T* __restrict__ rhs, const T* __restrict__ e, int cnx,
+                                                    int cny, const uint8_t* __restrict__ cst, T* __restrict__ crhs) {
+    const int cxs = 2 * (blockIdx.x * 32 + threadIdx.x);
+    const int cy = blockIdx.y * 8 + threadIdx.y, cz = blockIdx.z;
+    if (cxs >= cnx || cy >= cny) return;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int xs = 2 * cxs;
+    T sum0 = (T)0, sum1 = (T)0;
+#pragma unroll
+    for (int dk = 0; dk < 2; dk++)
+#pragma unroll
+        for (int dj = 0; dj < 2; dj++) {
+            const int y = 2 * cy + dj, z = 2 * cz + dk;
+            const int row = nx * (y + ny * z);
+            int ym, yp, zm, zp, xl, xr;
+            const bool okym = wrap_axis(y - 1, ny, L.per[1], ym), okyp = wrap_axis(y + 1, ny, L.per[1], yp);
+            const bool okzm = wrap_axis(z - 1, nz, L.per[2], zm), okzp = wrap_axis(z + 1, nz, L.per[2], zp);
+            const bool okxl = wrap_axis(xs - 4, nx, L.per[0], xl), okxr = wrap_axis(xs + 4, nx, L.per[0], xr);
+            const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
+            const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
+            T c[12], a[4], b[4], d[4], f[4], r[4];
+#pragma unroll
+            for (int i = 0; i < 12; i++) c[i] = (T)0;
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = b[i] = d[i] = f[i] = (T)0;
+            if (okxl) ES_VLD(c, 0, e + row + xl);
+            ES_VLD(c, 4, e + row + xs);
+            if (okxr) ES_VLD(c, 8, e + row + xr);
+            if (okym) ES_VLD(a, 0, e + rym + xs);
+            if (okyp) ES_VLD(b, 0, e + ryp + xs);
+            if (okzm) ES_VLD(d, 0, e + rzm + xs);
+            if (okzp) ES_VLD(f, 0, e + rzp + xs);
+            ES_VLD(r, 0, rhs + row + xs);
+            const unsigned sw = *reinterpret_cast<const unsigned*>(st + row + xs);
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint8_t sv = (uint8_t)((sw >> (8 * i)) & 0xFF);
+                T res = (T)0;
+                if ((sv & ST_KIND) == ST_UNKNOWN) {
+                    T diag, off;
+                    if (!(sv & ST_NEAR)) {
+                        T o = c[i + 3];
+                        o += c[i + 5];
+                        o += a[i];
+                        o += b[i];
+                        o += d[i];
+                        o += f[i];
+                        diag = L.diag0;
+                        off = o;
+                    } else {
+                        T dg = L.diag0, o = (T)0;
+                        const int gx = xs + i;
+                        const int g3[3] = {gx, y, z}, n3[3] = {nx, ny, nz};
+#pragma unroll
+                        for (int ax = 0; ax < 3; ax++)
+#pragma unroll
+                            for (int side = -1; side <= 1; side += 2) {
+                                const int q = g3[ax] + side;
+                                if ((q < 0 || q >= n3[ax]) && !L.per[ax]) {
+                                    dg += (L.pot_bc[2 * ax + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? (T)1 : (T)-1;
+                                    continue;
+                                }
+                                int nb;
+                                T v;
+                                if (ax == 0) {
+                                    int wx;
+                                    wrap_axis(q, nx, L.per[0], wx);
+                                    nb = row + wx;
+                                    v = c[i + 4 + side];
+                                } else if (ax == 1) {
+                                    nb = (side < 0 ? rym : ryp) + gx;
+                                    v = side < 0 ? a[i] : b[i];
+                                } else {
+                                    nb = (side < 0 ? rzm : rzp) + gx;
+                                    v = side < 0 ? d[i] : f[i];
+                                }
+                                const uint8_t kk = st[nb] & ST_KIND;
+                                if (kk == ST_UNKNOWN)
+                                    o += v;
+                                else
+                                    dg += (kk == ST_DIR) ? (T)1 : (T)-1;
+                            }
+                        diag = dg;
+                        off = o;
+                    }
+                    res = r[i] - (diag * c[i + 4] - off) * inv_h2;
+                }
+                if (i < 2)
+                    sum0 += res;
+                else
+                    sum1 += res;
+            }
+        }
+    const int C = cxs + cnx * (cy + cny * cz);
+    const T v0 = ((cst[C] & ST_KIND) == ST_UNKNOWN) ? sum0 / (T)8 : (T)0;
+    const T v1 = ((cst[C + 1] & ST_KIND) == ST_UNKNOWN) ? sum1 / (T)8 : (T)0;
+    crhs[C] = v0;
+    crhs[C + 1] = v1;
+    (void)inv_diag0;
 }
 
 // Coarsest level: one thread block holds the level in shared memory and
@@ -399,8 +690,9 @@ size_t coarse_smem_bytes(const es_ctx* c, size_t tsize) {
     return n * (2 * tsize + 1);
 }
 
-// One V-cycle on level l for A e = rhs.  warm != 0 (level 0 only): e holds a
-// previous iterate and the cycle improves it instead of starting from zero.
+// One V-cycle on level l for A e = rhs (in place on e[l]).  warm != 0
+// (level 0 only): the current iterate is improved instead of starting from
+// zero.
 template <class T>
 cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     Level<T> L = level_desc<T>(c, l);
@@ -408,43 +700,63 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     T* rhs = (T*)c->rhs[l];
     const uint8_t* st = c->st[l];
     const T omega = (T)c->P.omega;
+    const T inv_diag0 = (T)1 / L.diag0;
     const int Nl = L.nx * L.ny * L.nz;
     dim3 blk(128);
     dim3 half(((L.nx + 1) / 2 + 127) / 128, L.ny, L.nz);
     dim3 full((L.nx + 127) / 128, L.ny, L.nz);
+    const bool vec = (L.nx % 4) == 0;
+    constexpr int W = 4;
+    dim3 vblk(32, 8), vgrd((L.nx / W + 31) / 32, (L.ny + 7) / 8, L.nz);
+    auto sweep = [&](int first) {
+        if (vec) {
+            k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
+            k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
+        } else {
+            k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, first, omega);
+            k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
+        }
+        count(c, 2);
+    };
     if (l == c->L - 1) {
         size_t sm = coarse_smem_bytes(c, sizeof(T));
         if (sm <= 200 * 1024) {
             k_coarse_solve<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
             count(c);
         } else {
-            count(c, 2 * c->P.coarse_sweeps + (c->P.coarse_sweeps == 0));
-            if (c->P.coarse_sweeps == 0) k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
-            for (int s = 0; s < c->P.coarse_sweeps; s++) {
-                k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, s == 0, omega);
-                k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
+            if (c->P.coarse_sweeps == 0) {
+                k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
+                count(c);
             }
+            for (int s = 0; s < c->P.coarse_sweeps; s++) sweep(s == 0);
         }
         return cudaGetLastError();
     }
     const bool zero_start = !warm;
-    count(c, 2 * c->P.nu1 + 2 * c->P.nu2 + 2 + (c->P.nu1 == 0 && zero_start));
-    if (c->P.nu1 == 0 && zero_start) k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
-    for (int s = 0; s < c->P.nu1; s++) {
-        k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, s == 0 && zero_start, omega);
-        k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
+    if (c->P.nu1 == 0 && zero_start) {
+        k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
+        count(c);
     }
+    for (int s = 0; s < c->P.nu1; s++) sweep(s == 0 && zero_start);
     const int* m = c->ln[l + 1];
-    dim3 cgrid((m[0] + 127) / 128, m[1], m[2]);
-    k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], c->st[l + 1],
-                                                         (T*)c->rhs[l + 1]);
+    if (vec) {
+        dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
+        k_restrict_v<T><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, m[0], m[1],
+                                                      c->st[l + 1], (T*)c->rhs[l + 1]);
+    } else {
+        dim3 cgrid((m[0] + 127) / 128, m[1], m[2]);
+        k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], c->st[l + 1],
+                                                             (T*)c->rhs[l + 1]);
+    }
+    count(c);
     cudaError_t err = vcycle_level<T>(c, l + 1, 0);
     if (err != cudaSuccess) return err;
-    k_prolong<T><<<full, blk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
-    for (int s = 0; s < c->P.nu2; s++) {
-        k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, 0, omega);
-        k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
-    }
+    if (vec)
+        k_prolong_v<T><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
+    else
+        k_prolong<T><<<full, blk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
+    count(c);
+    for (int s = 0; s < c->P.nu2; s++) sweep(0);
     return cudaGetLastError();
 }
 
