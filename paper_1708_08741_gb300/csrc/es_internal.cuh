@@ -100,6 +100,8 @@ struct es_ctx {
     int32_t* owner;
     double* psi;
     float* psi32;    // MIXED32: float copy of psi for the FP32 body force
+    double* r64;     // MIXED32: FP64 residual kept between incremental updates
+    float* delta;    // MIXED32: corrections accumulated since psi was last updated
     void* fb;
     // multigrid
     int L;
@@ -135,6 +137,8 @@ cudaError_t launch_coarse_states(es_ctx* c);
 cudaError_t launch_outer_residual(es_ctx* c);
 cudaError_t launch_vcycle(es_ctx* c, int warm);
 cudaError_t launch_psi32(es_ctx* c);
+cudaError_t launch_incremental_residual(es_ctx* c, int first);
+cudaError_t launch_fold_delta(es_ctx* c);
 cudaError_t launch_correct(es_ctx* c);
 cudaError_t launch_body_force(es_ctx* c);
 // lbm and particles (es_lbm.cu)

@@ -85,9 +85,11 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s
                                                                 const int32_t* __restrict__ owner,
                                                                 const DParticle* __restrict__ part,
                                                                 const int* __restrict__ kind, T* __restrict__ r_out,
-                                                                double* __restrict__ partial) {
+                                                                double* __restrict__ r64, double* __restrict__ partial) {
     __shared__ double sh[32];
-    double acc = 0.0;
+    // r^2 is summed per thread in the inner type (the norm only feeds the
+    // tolerance test), then across the block in FP64
+    T acc = (T)0;
     const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
     const int rows = g.ny * g.nz;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -118,13 +120,94 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s
                         }
                     r = b - (diag * psi[c] - off);
                 }
-                acc += r * r;
+                const T rt = (T)r;
+                acc += rt * rt;
             }
             r_out[c] = (T)r;
+            if (r64) r64[c] = r;
         }
     }
-    double tot = block_sum(acc, sh);
+    double tot = block_sum((double)acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// MIXED32 incremental residual: after the V-cycles produced the correction
+// e for the right-hand side r, the new residual is r - A e.  It is formed
+// with A e in FP32 and kept in FP64 (one conversion and one add per cell),
+// e is accumulated into delta (psi is updated once, by k_fold_delta), and
+// the float copy of the residual feeds the next V-cycles.
+__global__ void __launch_bounds__(kRedThreads) k_incr_residual(Grid g, Solver s, float diag0,
+                                                               const uint8_t* __restrict__ st0,
+                                                               const float* __restrict__ e,
+                                                               double* __restrict__ r64, float* __restrict__ r32,
+                                                               float* __restrict__ delta, int first,
+                                                               double* __restrict__ partial) {
+    __shared__ double sh[32];
+    float acc = 0.0f;
+    const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
+    const int rows = g.ny * g.nz;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int y = row % ny, z = row / ny;
+        const int base = row * nx;
+        const int ym = (y == 0 ? ny - 1 : y - 1) - y, yp = (y == ny - 1 ? 0 : y + 1) - y;
+        const int zm = (z == 0 ? g.nz - 1 : z - 1) - z, zp = (z == g.nz - 1 ? 0 : z + 1) - z;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const int c = base + x;
+            const uint8_t st = st0[c];
+            if ((st & ST_KIND) != ST_UNKNOWN) continue;
+            const float ec = e[c];
+            float Ae;
+            if (!(st & ST_NEAR)) {
+                const int xm = (x == 0 ? nx - 1 : x - 1) - x, xp = (x == nx - 1 ? 0 : x + 1) - x;
+                float off = e[c + xm];
+                off += e[c + xp];
+                off += e[c + ym * nx];
+                off += e[c + yp * nx];
+                off += e[c + zm * nxy];
+                off += e[c + zp * nxy];
+                Ae = diag0 * ec - off;
+            } else {
+                float diag = diag0, off = 0.0f;
+                const int v[3] = {x, y, z}, n3[3] = {nx, ny, g.nz}, stride[3] = {1, nx, nxy};
+                for (int a = 0; a < 3; a++)
+                    for (int side = -1; side <= 1; side += 2) {
+                        int p = v[a] + side;
+                        if (p < 0 || p >= n3[a]) {
+                            if (!g.per[a]) {
+                                diag += (s.pot_bc[2 * a + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? 1.0f : -1.0f;
+                                continue;
+                            }
+                            p = p < 0 ? p + n3[a] : p - n3[a];
+                        }
+                        const int nb = c + (p - v[a]) * stride[a];
+                        const uint8_t k = st0[nb] & ST_KIND;
+                        if (k == ST_UNKNOWN)
+                            off += e[nb];
+                        else
+                            diag += (k == ST_DIR) ? 1.0f : -1.0f;
+                    }
+                Ae = diag * ec - off;
+            }
+            const double r = r64[c] - (double)Ae;
+            r64[c] = r;
+            const float rf = (float)r;
+            r32[c] = rf;
+            acc += rf * rf;
+            delta[c] = first ? ec : delta[c] + ec;
+        }
+    }
+    double tot = block_sum((double)acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void k_fold_delta(int N, const uint8_t* __restrict__ st0, const float* __restrict__ delta,
+                             double* __restrict__ psi, float* __restrict__ psi32) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    if ((st0[c] & ST_KIND) != ST_UNKNOWN) return;
+    const double v = psi[c] + (double)delta[c];
+    psi[c] = v;
+    psi32[c] = (float)v;
 }
 
 __global__ void k_finalize_norm(const double* partial, int n, double* out) {
@@ -773,10 +856,11 @@ cudaError_t launch_outer_residual(es_ctx* c) {
     const double diag0 = 6.0 + c->S.kappa * c->S.kappa;
     if (mixed(c))
         k_outer_residual<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-            c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (float*)c->rhs[0], c->partial);
+            c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (float*)c->rhs[0], c->r64, c->partial);
     else
         k_outer_residual<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-            c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (double*)c->rhs[0], c->partial);
+            c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (double*)c->rhs[0], nullptr,
+            c->partial);
     k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, c->red_blocks, c->d_norm);
     count(c, 2);
     return cudaGetLastError();
@@ -798,6 +882,23 @@ cudaError_t launch_correct(es_ctx* c) {
         k_correct<float><<<nb, 256, 0, c->stream>>>(N, c->st[0], (const float*)c->e[0], c->psi, c->psi32);
     else
         k_correct<double><<<nb, 256, 0, c->stream>>>(N, c->st[0], (const double*)c->e[0], c->psi, nullptr);
+    count(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_incremental_residual(es_ctx* c, int first) {
+    const float diag0 = (float)(6.0 + c->S.kappa * c->S.kappa);
+    k_incr_residual<<<c->red_blocks, kRedThreads, 0, c->stream>>>(c->g, c->S, diag0, c->st[0], (const float*)c->e[0],
+                                                                   c->r64, (float*)c->rhs[0], c->delta, first,
+                                                                   c->partial);
+    k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, c->red_blocks, c->d_norm);
+    count(c, 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_delta(es_ctx* c) {
+    const int N = (int)c->g.N;
+    k_fold_delta<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->st[0], c->delta, c->psi, c->psi32);
     count(c);
     return cudaGetLastError();
 }

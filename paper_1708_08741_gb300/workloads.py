@@ -256,9 +256,11 @@ def suspension(n: int = 512, n_spheres: int = 2880, radius: float = 5.0, seed: i
     rng = PCG32(seed)
     centres = place_spheres(n_spheres, radius, dims, periodic, rng)
     q = np.array([1.0 + 0.1 * rng.normal() for _ in range(n_spheres)])
+    # 8 sweeps solve the coarsest level (h = 2^(levels-1), kappa^2 h^2 >> 1,
+    # strongly diagonally dominant) to well below the cycle's contraction
     wl = Workload(name=f"suspension_{dims[0]}x{dims[1]}x{dims[2]}_{n_spheres}xR{radius:g}",
                   dims=dims, periodic=periodic, tau=1.0, kappa=1.0 / debye, eps=1.0,
-                  E_ext=(E, 0.0, 0.0), levels=levels, res_rf=res_rf, steps=steps)
+                  E_ext=(E, 0.0, 0.0), levels=levels, res_rf=res_rf, steps=steps, coarse_sweeps=8)
     return _set_particles(wl, centres, np.full(n_spheres, radius),
                           np.full(n_spheres, KIND_CHARGE), np.zeros(n_spheres), q)
 
