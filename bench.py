@@ -42,6 +42,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=512, help="cells per axis")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer run (default: --steps)")
+    ap.add_argument("--smoother", choices=["fused", "two_pass"], default="two_pass",
+                    help="execution of a red-black sweep (same arithmetic)")
     return ap.parse_args()
 
 
@@ -199,7 +201,8 @@ def run_ours(args):
 
     wl = W.suspension(n=args.n, n_spheres=int(round(2880 * (args.n / 512) ** 3)),
                       levels=6 if args.n % 32 == 0 else 4)
-    sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev))
+    smoother = es.ES_SMOOTH_FUSED if args.smoother == "fused" else es.ES_SMOOTH_TWO_PASS
+    sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev), overrides=dict(smoother=smoother))
     stream = sim.stream
     N = wl.n_cells
 
@@ -217,6 +220,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = sim.kernel_launches()
+    sim.profile_start()
     with torch.cuda.stream(stream):
         start.record(stream)
         for k in range(args.steps):
@@ -236,6 +240,7 @@ def run_ours(args):
             pe[4].record(stream)
         stop.record(stream)
     torch.cuda.synchronize(dev)
+    prof = sim.profile_stop()
     launches = sim.kernel_launches() - launches0
     barrier()
     torch.cuda.synchronize(dev)
@@ -254,7 +259,8 @@ def run_ours(args):
     n_fluid = N - n_solid
     lbm_bytes = LBM_BYTES_FLUID * n_fluid + LBM_BYTES_SOLID * n_solid
     peak, peak_kind = measured_peaks()
-    achieved = lbm_bytes / (lbm_ms / 1e3) / 1e9
+    kernels = kernel_table(prof, lbm_bytes, peak)
+    top = kernels[0]
 
     # end to end through the C ABI with host buffers: the particle state comes
     # in from host memory each step and the new state and forces go back
@@ -299,9 +305,13 @@ def run_ours(args):
         "mflups": n_fluid * args.steps * world / t_all / 1e6,
         "vcycles_per_step": vcycles / args.steps,
         "phases_ms": phases,
-        "roofline": {"kernel": "k_lbm<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                     "bytes_per_launch": lbm_bytes, "ms_per_launch": lbm_ms},
+        "roofline": {"kernel": top["kernel"], "bound": "hbm", "achieved": top["gbs"], "peak": peak,
+                     "unit": "GB/s", "frac": top["frac"], "traffic": TRAFFIC.get(top["kernel"]),
+                     "peak_source": peak_kind, "bytes_per_launch": top["bytes_per_launch"],
+                     "ms_per_launch": top["ms_per_launch"], "launches": top["launches"],
+                     "share_of_timed_kernels": top["share"]},
+        "kernels": kernels,
+        "lbm_step_ms": lbm_ms,
         "e2e": {"value": aggregate_throughput(N, e2e_steps, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -311,6 +321,32 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of each kernel in its current form, by kernel key; a kernel
+# missing here has no capture of its current code.
+TRAFFIC = {}
+
+
+def kernel_table(prof, lbm_bytes, peak):
+    """Per kernel and level, from the library's event timing over the timed
+    steps: launches, mean device time, algorithmic bytes per launch, achieved
+    GB/s and its fraction of the measured peak, share of the kernel time;
+    sorted by total time.  The stream-collide's bytes count fluid cells only
+    (obstacle cells move their flag byte), hence lbm_bytes from the caller."""
+    rows = []
+    total = sum(r["ms"] for r in prof) or 1.0
+    for r in prof:
+        n = max(r["launches"], 1)
+        b = lbm_bytes if r["name"] == "lbm" else r["bytes"] / n
+        ms = r["ms"] / n
+        gbs = b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        key = r["name"] if r["level"] < 0 else f"{r['name']} L{r['level']}"
+        rows.append({"kernel": key, "launches": r["launches"], "ms_per_launch": ms, "bytes_per_launch": b,
+                     "gbs": gbs, "frac": gbs / peak, "share": r["ms"] / total})
+    rows.sort(key=lambda x: -x["share"])
+    return rows
 
 
 def ctypes_sizeof_particle(es):

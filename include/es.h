@@ -51,9 +51,13 @@ extern "C" {
 
 /* arithmetic forms */
 #define ES_FP64 0    /* everything in double precision                           */
-#define ES_MIXED32 1 /* PDFs stored as FP32 deviations from w_q, FP32 collision,
-                        FP32 multigrid cycles inside an FP64 defect correction,
+#define ES_MIXED32 1 /* PDFs stored as FP32 deviations f_q - w_q, FP32 collision,
+                        FP32 multigrid cycles inside a defect correction whose
+                        potential and residual are float-float (two floats,
+                        about 48 significant bits, evaluated on the FP32 pipe),
                         FP64 force/torque sums and rigid-body update           */
+#define ES_MIXED16 2 /* as ES_MIXED32, with the PDFs stored as FP16 relative
+                        deviations (f_q - w_q) / w_q                           */
 
 /* particle electric boundary conditions (Sec. 5.5) */
 #define ES_KIND_ZETA 0   /* prescribed zeta potential: Dirichlet             */
@@ -97,7 +101,15 @@ typedef struct {
     double omega;       /* smoother relaxation (1: Gauss-Seidel; the paper's SOR uses 1.7) */
     double res_rf;      /* residual reduction factor w.r.t. the first solve (Sec. 5.3) */
     int max_cycles;     /* cycle cap per es_potential_solve                        */
+    int smoother;       /* ES_SMOOTH_TWO_PASS (0, default) or ES_SMOOTH_FUSED: how a
+                           red-black sweep is executed; both compute the same sweep */
 } es_params;
+
+/* Execution of one red-black Gauss-Seidel sweep (same arithmetic either way):
+   TWO_PASS runs one in-place pass per colour; FUSED runs red and black in
+   one pass over the level (out of place). */
+#define ES_SMOOTH_TWO_PASS 0
+#define ES_SMOOTH_FUSED 1
 
 typedef struct {
     double x[3]; /* centre                  */
@@ -241,6 +253,29 @@ int es_synchronize(es_ctx* ctx);
 
 /* The library's own D3Q19 velocity (19 x 3 ints) and weight tables. */
 int es_lattice(int* c57, double* w19);
+
+/* ---- Per-kernel device time (instrumentation; the paper has no counterpart) ----
+   Between es_profile_start and es_profile_stop the library brackets each
+   launch of its grid-sized kernels (stream-collide, body force, smoothers,
+   restriction, prolongation, coarse solve, outer residual, correction) with
+   a pair of CUDA events on the context's stream.  es_profile_stop
+   synchronises the stream and writes one record per kernel and multigrid
+   level: launches, summed device time, and summed algorithmic bytes (the
+   least traffic the launches' work needs, every input read once and every
+   output written once; the formulas are stated beside each launch).  The
+   events add two stream commands per bracketed launch and change no
+   result.  es_profile_stop returns ES_EINVAL when profiling was not started;
+   *n receives the number of records (at most max are written). */
+typedef struct {
+    char name[32];   /* kernel                                       */
+    int level;       /* multigrid level; -1 for a fine-grid kernel   */
+    int launches;
+    double ms;       /* summed device time of the launches           */
+    double bytes;    /* summed algorithmic bytes of the launches     */
+} es_kernel_time;
+
+int es_profile_start(es_ctx* ctx);
+int es_profile_stop(es_ctx* ctx, es_kernel_time* out, int max, int* n);
 
 /* Number of CUDA kernels this context has launched so far (telemetry). */
 uint64_t es_kernel_launches(const es_ctx* ctx);

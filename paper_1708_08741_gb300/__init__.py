@@ -30,6 +30,9 @@ ES_EOVERLAP = -6
 
 ES_FP64 = 0
 ES_MIXED32 = 1
+ES_MIXED16 = 2
+ES_SMOOTH_TWO_PASS = 0
+ES_SMOOTH_FUSED = 1
 
 FIELD_PSI = 0
 FIELD_RHO = 1
@@ -45,7 +48,7 @@ EXPORTED = ("es_create", "es_create_with_allocator", "es_destroy", "es_map_parti
             "es_lbm_step", "es_forces", "es_advance", "es_step", "es_get_field", "es_set_field",
             "es_get_particles", "es_set_particles", "es_set_forces", "es_synchronize", "es_lattice", "es_gather",
             "es_gather_noalloc",
-            "es_device_bytes", "es_kernel_launches", "es_last_error")
+            "es_device_bytes", "es_kernel_launches", "es_last_error", "es_profile_start", "es_profile_stop")
 
 
 class Params(ctypes.Structure):
@@ -68,6 +71,7 @@ class Params(ctypes.Structure):
         ("omega", ctypes.c_double),
         ("res_rf", ctypes.c_double),
         ("max_cycles", ctypes.c_int),
+        ("smoother", ctypes.c_int),
     ]
 
 
@@ -89,6 +93,16 @@ class SolveInfo(ctypes.Structure):
         ("r_initial", ctypes.c_double),
         ("r_final", ctypes.c_double),
         ("tol", ctypes.c_double),
+    ]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char * 32),
+        ("level", ctypes.c_int),
+        ("launches", ctypes.c_int),
+        ("ms", ctypes.c_double),
+        ("bytes", ctypes.c_double),
     ]
 
 
@@ -137,6 +151,8 @@ def load():
     L.es_kernel_launches.restype = ctypes.c_uint64
     L.es_device_bytes.argtypes = [ctypes.POINTER(Params), ctypes.c_int]
     L.es_device_bytes.restype = ctypes.c_size_t
+    L.es_profile_start.argtypes = [P]
+    L.es_profile_stop.argtypes = [P, ctypes.POINTER(KernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.es_last_error.argtypes = [P]
     L.es_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -291,6 +307,20 @@ class Simulation:
         info = SolveInfo()
         self._check(self.lib.es_step(self.h, forced_cycles, ctypes.byref(info)), "es_step")
         return {"cycles": info.cycles, "r0": info.r_initial, "r": info.r_final, "tol": info.tol}
+
+    def profile_start(self):
+        """Start bracketing the grid-sized kernel launches with CUDA events."""
+        self._check(self.lib.es_profile_start(self.h), "es_profile_start")
+
+    def profile_stop(self) -> list:
+        """Stop profiling; per kernel and level: launches, summed device ms and
+        summed algorithmic bytes."""
+        cap = 64
+        arr = (KernelTime * cap)()
+        n = ctypes.c_int(0)
+        self._check(self.lib.es_profile_stop(self.h, arr, cap, ctypes.byref(n)), "es_profile_stop")
+        return [{"name": arr[i].name.decode(), "level": arr[i].level, "launches": arr[i].launches,
+                 "ms": arr[i].ms, "bytes": arr[i].bytes} for i in range(min(n.value, cap))]
 
     def kernel_launches(self) -> int:
         return int(self.lib.es_kernel_launches(self.h))

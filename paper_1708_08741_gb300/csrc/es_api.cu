@@ -5,7 +5,7 @@
 #include <cstring>
 #include <new>
 
-#include "es_internal.cuh"
+#include "es_device.cuh"
 
 using namespace es;
 
@@ -35,10 +35,15 @@ int cuda_fail(es_ctx* c, cudaError_t e, const char* where) {
 int validate(const es_params* P, const es_particle* parts, int n, std::string& why) {
     if (!P) return why = "params is NULL", ES_EINVAL;
     if (n < 0 || (n > 0 && !parts)) return why = "bad particle array", ES_EINVAL;
-    if (P->precision != ES_FP64 && P->precision != ES_MIXED32) return why = "unknown precision", ES_EINVAL;
+    if (P->precision != ES_FP64 && P->precision != ES_MIXED32 && P->precision != ES_MIXED16)
+        return why = "unknown precision", ES_EINVAL;
     if (P->levels < 1 || P->levels > ES_MAXLEV) return why = "levels must be in 1..12", ES_EINVAL;
     if (!(P->tau > 0.5)) return why = "tau must exceed 1/2", ES_EINVAL;
     if (!(P->eps > 0.0) || !(P->kappa >= 0.0)) return why = "eps must be > 0 and kappa >= 0", ES_EINVAL;
+    if (P->smoother != ES_SMOOTH_FUSED && P->smoother != ES_SMOOTH_TWO_PASS) {
+        why = "smoother must be ES_SMOOTH_FUSED or ES_SMOOTH_TWO_PASS";
+        return ES_EINVAL;
+    }
     if (P->nu1 < 0 || P->nu2 < 0 || P->coarse_sweeps < 0 || P->max_cycles < 0)
         return why = "negative sweep or cycle count", ES_EINVAL;
     if (!(P->omega > 0.0 && P->omega < 2.0)) return why = "omega must be in (0, 2)", ES_EINVAL;
@@ -97,22 +102,21 @@ long long pdf_stride(long long N) { return ((N + 31) / 32) * 32 + 1120; }
 
 size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     long long N = (long long)P->dims[0] * P->dims[1] * P->dims[2];
-    size_t s = P->precision == ES_MIXED32 ? 4 : 8;
+    const size_t s = P->precision == ES_FP64 ? 8 : 4;  // arithmetic type
     size_t b = 0;
-    b += 2 * 19 * pdf_stride(N) * s;  // pdf ping-pong
+    b += 2 * 19 * pdf_stride(N) * pdf_bytes(P->precision);  // pdf ping-pong
     b += 3 * N * s;       // body force
-    b += N * 8;           // psi
-    if (P->precision == ES_MIXED32) b += N * 16;  // float copy of psi, FP64 residual, FP32 corrections
+    b += N * 8;           // psi: FP64, or float-float high and low parts
     b += N * 4 + N;       // owner, flags
     size_t lv = 0;
     for (int l = 0; l < P->levels; l++) {
         long long Nl = (long long)(P->dims[0] >> l) * (P->dims[1] >> l) * (P->dims[2] >> l);
-        lv += Nl * (1 + 2 * s);
+        lv += Nl * (1 + 3 * s);
     }
     if (per_level) *per_level = lv;
     b += lv;
-    b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8);
-    b += 4096 * 8 + 64;
+    b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8 + 14 * 4);
+    b += (size_t)kResPartials * 8 + 64;
     return b;
 }
 
@@ -145,6 +149,13 @@ void release(es_ctx* c) {
     if (c->h_status) cudaFreeHost(c->h_status);
     c->h_norm = nullptr;
     c->h_status = nullptr;
+    for (auto& r : c->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t ev : c->prof_pool) cudaEventDestroy(ev);
+    c->prof_recs.clear();
+    c->prof_pool.clear();
 }
 
 // Reads the residual norm and the device status word (synchronises).
@@ -164,6 +175,41 @@ int status_error(es_ctx* c, int st) {
 }
 
 }  // namespace
+
+namespace es {
+
+ProfScope::ProfScope(es_ctx* c, const char* name, int level, double bytes) : c_(c), rec_(-1) {
+    if (!c->prof) return;
+    int slot = -1;
+    for (size_t i = 0; i < c->prof_slots.size(); i++)
+        if (c->prof_slots[i].level == level && c->prof_slots[i].name == name) slot = (int)i;
+    if (slot < 0) {
+        c->prof_slots.push_back({name, level, 0, 0.0});
+        slot = (int)c->prof_slots.size() - 1;
+    }
+    c->prof_slots[slot].launches++;
+    c->prof_slots[slot].bytes += bytes;
+    cudaEvent_t ev[2];
+    for (int k = 0; k < 2; k++) {
+        if (!c->prof_pool.empty()) {
+            ev[k] = c->prof_pool.back();
+            c->prof_pool.pop_back();
+        } else if (cudaEventCreate(&ev[k]) != cudaSuccess) {
+            cudaGetLastError();
+            if (k == 1) c->prof_pool.push_back(ev[0]);
+            return;
+        }
+    }
+    cudaEventRecord(ev[0], c->stream);
+    c->prof_recs.push_back({slot, ev[0], ev[1]});
+    rec_ = (int)c->prof_recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (rec_ >= 0) cudaEventRecord(c_->prof_recs[rec_].b, c_->stream);
+}
+
+}  // namespace es
 
 extern "C" {
 
@@ -203,7 +249,16 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->lambda_o = -8.0 * (2.0 - 1.0 / params->tau) / (8.0 - 1.0 / params->tau);
     c->cur = 0;
     c->last_src = -1;
-    c->red_blocks = 4 * 152;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
+            cudaGetLastError();
+            nsm = 152;
+        }
+        c->n_sm = nsm;
+    }
+    c->red_blocks = 4 * c->n_sm;
     c->mg_rate = 0.15;
 
     const long long N = c->g.N;
@@ -215,29 +270,30 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
         if (!p) ok = false;
         return p;
     };
-    c->pdf[0] = A(19 * c->g.ps * s);
-    c->pdf[1] = A(19 * c->g.ps * s);
+    c->pdf[0] = A(19 * c->g.ps * pdf_bytes(c->P.precision));
+    c->pdf[1] = A(19 * c->g.ps * pdf_bytes(c->P.precision));
     c->fb = A(3 * N * s);
-    c->psi = (double*)A(N * 8);
+    c->psi = mixed(c) ? nullptr : (double*)A(N * 8);
     c->psi32 = mixed(c) ? (float*)A(N * 4) : nullptr;
-    c->r64 = mixed(c) ? (double*)A(N * 8) : nullptr;
-    c->delta = mixed(c) ? (float*)A(N * 4) : nullptr;
+    c->psi_lo = mixed(c) ? (float*)A(N * 4) : nullptr;
     c->owner = (int32_t*)A(N * 4);
     c->flags = (uint8_t*)A(N);
     for (int l = 0; l < c->L; l++) {
         long long Nl = (long long)c->ln[l][0] * c->ln[l][1] * c->ln[l][2];
         c->st[l] = (uint8_t*)A(Nl);
         c->e[l] = A(Nl * s);
+        c->e2[l] = A(Nl * s);
         c->rhs[l] = A(Nl * s);
     }
     c->part = (DParticle*)A(np1 * sizeof(DParticle));
     c->partf = mixed(c) ? (float*)A(np1 * 12 * sizeof(float)) : nullptr;
+    c->pbc = mixed(c) ? (float*)A(np1 * 2 * sizeof(float)) : nullptr;
     c->mapped = (double*)A(np1 * 9 * 8);
     c->kind = (int*)A(np1 * 4);
     c->nfaces = (int*)A(np1 * 4);
     c->F = (double*)A(np1 * 3 * 8);
     c->T = (double*)A(np1 * 3 * 8);
-    c->partial = (double*)A(c->red_blocks * 8);
+    c->partial = (double*)A((c->red_blocks > kResPartials ? c->red_blocks : kResPartials) * 8);
     c->d_norm = (double*)A(64);
     c->d_status = (int*)A(64);
     if (!ok) {
@@ -268,8 +324,10 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->part, hp.data(), np1 * sizeof(DParticle), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->kind, hk.data(), np1 * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->mapped, hm.data(), np1 * 9 * 8, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->psi, 0, N * 8, c->stream);
+    if (e == cudaSuccess && c->psi) e = cudaMemsetAsync(c->psi, 0, N * 8, c->stream);
     if (e == cudaSuccess && c->psi32) e = cudaMemsetAsync(c->psi32, 0, N * 4, c->stream);
+    if (e == cudaSuccess && c->psi_lo) e = cudaMemsetAsync(c->psi_lo, 0, N * 4, c->stream);
+    if (e == cudaSuccess && c->pbc) e = cudaMemsetAsync(c->pbc, 0, np1 * 2 * sizeof(float), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fb, 0, 3 * N * s, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->F, 0, np1 * 3 * 8, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->T, 0, np1 * 3 * 8, c->stream);
@@ -324,8 +382,6 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
     }
     int cycles = 0;
     int result = ES_OK;
-    double anchor = norm0;     // norm of the last exact FP64 residual
-    bool pending_fold = false;  // MIXED32: corrections not yet added to psi
     for (;;) {
         if (std::isnan(norm) || std::isinf(norm)) {
             result = fail(c, ES_ENAN, "residual norm is not finite");
@@ -340,7 +396,7 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
                 break;
             }
         }
-        // V-cycles per FP64 correction: one in the FP64 form (the oracle's
+        // V-cycles per correction: one in the FP64 form (the oracle's
         // iteration); in MIXED32 as many FP32 cycles, warm-started on the
         // same defect, as the running rate estimate says will bring the
         // residual to half the tolerance (at most 6, i.e. within FP32 reach)
@@ -352,26 +408,11 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
             if (k > c->P.max_cycles - cycles) k = c->P.max_cycles - cycles;
         }
         for (int j = 0; j < k; j++) ES_CUDA(c, launch_vcycle(c, j > 0));
-        // MIXED32: once the last exact FP64 residual is within 1000x of the
-        // tolerance, the residual is updated as r - A e with A e in FP32: its
-        // error, about 1e-5 of that exact residual, stays below 1 % of tol.
-        // Deeper solves (the first one of a run) recompute it exactly.
-        if (mixed(c) && forced_cycles < 0 && anchor <= 1000.0 * c->tol) {
-            ES_CUDA(c, launch_incremental_residual(c, !pending_fold));
-            pending_fold = true;
-        } else {
-            if (pending_fold) {
-                ES_CUDA(c, launch_fold_delta(c));
-                pending_fold = false;
-            }
-            ES_CUDA(c, launch_correct(c));
-            ES_CUDA(c, launch_outer_residual(c));
-            anchor = -1.0;  // set from the norm below
-        }
+        ES_CUDA(c, launch_correct(c));
+        ES_CUDA(c, launch_outer_residual(c));
         const double before = norm;
         rc = read_norm_status(c, &norm, &st);
         if (rc != ES_OK) return rc;
-        if (anchor < 0.0) anchor = norm;
         cycles += k;
         if (norm > 0.0 && before > 0.0) {
             double observed = std::pow(norm / before, 1.0 / k);
@@ -379,7 +420,6 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
             c->mg_rate = std::exp(0.5 * std::log(c->mg_rate) + 0.5 * std::log(observed));
         }
     }
-    if (pending_fold) ES_CUDA(c, launch_fold_delta(c));
     if (info) {
         info->cycles = cycles;
         info->r_initial = norm0;
@@ -454,7 +494,7 @@ int es_get_field(es_ctx* c, int which, void* dst, size_t bytes, int on_device) {
     if (need == 0 || bytes != need) return fail(c, ES_EINVAL, "unknown field or wrong size");
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const void* srcp = nullptr;
-    if (which == ES_FIELD_PSI) srcp = c->psi;
+    if (which == ES_FIELD_PSI && !mixed(c)) srcp = c->psi;
     if (which == ES_FIELD_OWNER) srcp = c->owner;
     if (which == ES_FIELD_FLAGS) srcp = c->flags;
     if (!srcp) {
@@ -468,6 +508,7 @@ int es_get_field(es_ctx* c, int which, void* dst, size_t bytes, int on_device) {
         if (which == ES_FIELD_RHO) ES_CUDA(c, launch_get_moments(c, buf, nullptr));
         if (which == ES_FIELD_U) ES_CUDA(c, launch_get_moments(c, nullptr, buf));
         if (which == ES_FIELD_FB) ES_CUDA(c, launch_get_fb(c, buf));
+        if (which == ES_FIELD_PSI) ES_CUDA(c, launch_join_psi(c, buf));
         srcp = on_device ? nullptr : buf;
     }
     if (srcp) ES_CUDA(c, cudaMemcpyAsync(dst, srcp, bytes, k, c->stream));
@@ -502,9 +543,8 @@ int es_set_field(es_ctx* c, int which, const void* src, size_t bytes, int on_dev
         return fail(c, ES_EINVAL, "field is read-only");
     if (bytes != field_size(c, which)) return fail(c, ES_EINVAL, "wrong size");
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (which == ES_FIELD_PSI) {
+    if (which == ES_FIELD_PSI && !mixed(c)) {
         ES_CUDA(c, cudaMemcpyAsync(c->psi, src, bytes, k, c->stream));
-        ES_CUDA(c, launch_psi32(c));
     } else {
         const double* dsrc = (const double*)src;
         if (!on_device) {
@@ -515,6 +555,7 @@ int es_set_field(es_ctx* c, int which, const void* src, size_t bytes, int on_dev
         }
         if (which == ES_FIELD_PDF) ES_CUDA(c, launch_set_pdf(c, dsrc));
         if (which == ES_FIELD_FB) ES_CUDA(c, launch_set_fb(c, dsrc));
+        if (which == ES_FIELD_PSI) ES_CUDA(c, launch_split_psi(c, dsrc));
     }
     ES_CUDA(c, cudaStreamSynchronize(c->stream));
     return ES_OK;
@@ -560,6 +601,16 @@ int es_set_particles(es_ctx* c, const es_particle* src, int n) {
     }
     ES_CUDA(c, cudaMemcpyAsync(c->part, hp.data(), n * sizeof(DParticle), cudaMemcpyHostToDevice, c->stream));
     ES_CUDA(c, cudaMemcpyAsync(c->kind, hk.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    std::vector<float> hb;
+    if (c->pbc) {
+        hb.resize(2 * n);
+        for (int p = 0; p < n; p++) {
+            const ff v = ff_from_double(hk[p] == ES_KIND_ZETA ? 2.0 * hp[p].zeta : hp[p].sigma / c->S.eps);
+            hb[2 * p] = v.hi;
+            hb[2 * p + 1] = v.lo;
+        }
+        ES_CUDA(c, cudaMemcpyAsync(c->pbc, hb.data(), 2 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    }
     ES_CUDA(c, cudaStreamSynchronize(c->stream));
     return ES_OK;
 }
@@ -602,6 +653,42 @@ size_t es_device_bytes(const es_params* params, int n) {
     std::string why;
     if (!params || validate(params, nullptr, 0, why) != ES_OK) return 0;
     return field_bytes(params, n, nullptr);
+}
+
+int es_profile_start(es_ctx* c) {
+    if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
+    for (auto& r : c->prof_recs) {
+        c->prof_pool.push_back(r.a);
+        c->prof_pool.push_back(r.b);
+    }
+    c->prof_recs.clear();
+    c->prof_slots.clear();
+    c->prof = true;
+    return ES_OK;
+}
+
+int es_profile_stop(es_ctx* c, es_kernel_time* out, int max, int* n) {
+    if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
+    if (!c->prof) return fail(c, ES_EINVAL, "profiling was not started");
+    c->prof = false;
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<double> ms(c->prof_slots.size(), 0.0);
+    for (auto& r : c->prof_recs) {
+        float t = 0.0f;
+        ES_CUDA(c, cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.slot] += t;
+    }
+    const int ns = (int)c->prof_slots.size();
+    if (n) *n = ns;
+    for (int i = 0; i < ns && i < max && out; i++) {
+        std::memset(&out[i], 0, sizeof(es_kernel_time));
+        std::strncpy(out[i].name, c->prof_slots[i].name.c_str(), sizeof(out[i].name) - 1);
+        out[i].level = c->prof_slots[i].level;
+        out[i].launches = c->prof_slots[i].launches;
+        out[i].ms = ms[i];
+        out[i].bytes = c->prof_slots[i].bytes;
+    }
+    return ES_OK;
 }
 
 const char* es_last_error(const es_ctx* c) {

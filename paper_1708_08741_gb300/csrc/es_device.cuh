@@ -1,6 +1,8 @@
 // es_device.cuh -- small device helpers shared by the libes kernels.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "es_internal.cuh"
 
 namespace es {
@@ -101,6 +103,131 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     if (wid == 0)
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;  // valid in thread 0
+}
+
+// ---- PDF storage forms ----
+// What one stored population holds, and the arithmetic type C of the
+// stream-collide that reads it:
+//   double: f_q (FP64 form, C = double);
+//   float:  f_q - w_q (MIXED32, C = float): the deviation from the rest
+//           state keeps FP32 resolution for the small departures from w_q;
+//   __half: 2^12 (f_q - w_q) / w_q (MIXED16, C = float): the deviation
+//           relative to its weight, so that all 19 streams use FP16 alike,
+//           scaled by 2^12 because FP16 is normal only from 6.1e-5 on while
+//           the relative deviations of slow flows are 1e-6 .. 1e-3 (scaled,
+//           they stay normal down to 1.5e-8; the largest one kept is 16).
+// ld / st convert between a stored value and the collide's working value
+// (f_q for double, f_q - w_q otherwise); to_f / from_f give f_q in double.
+template <class S>
+struct Store;
+
+template <>
+struct Store<double> {
+    using C = double;
+    static constexpr bool shifted = false;
+    __device__ static double ld(int, double s) { return s; }
+    __device__ static double st(int, double v) { return v; }
+    __device__ static double rest(int q) { return wq(q); }
+    __device__ static double to_f(int, double s) { return s; }
+    __device__ static double from_f(int, double f) { return f; }
+    __device__ static double from_dev(int q, double dev) { return wq(q) + dev; }
+};
+
+template <>
+struct Store<float> {
+    using C = float;
+    static constexpr bool shifted = true;
+    __device__ static float ld(int, float s) { return s; }
+    __device__ static float st(int, float v) { return v; }
+    __device__ static float rest(int) { return 0.0f; }
+    __device__ static double to_f(int q, float s) { return (double)s + wq(q); }
+    __device__ static float from_f(int q, double f) { return (float)(f - wq(q)); }
+    __device__ static float from_dev(int, double dev) { return (float)dev; }
+};
+
+constexpr double kHalfScale = 4096.0;
+
+template <>
+struct Store<__half> {
+    using C = float;
+    static constexpr bool shifted = true;
+    __device__ static float ld(int q, __half s) { return __half2float(s) * (float)(wq(q) / kHalfScale); }
+    __device__ static __half st(int q, float v) { return __float2half_rn(v * (float)(kHalfScale / wq(q))); }
+    __device__ static __half rest(int) { return __float2half_rn(0.0f); }
+    __device__ static double to_f(int q, __half s) { return wq(q) + (double)__half2float(s) * (wq(q) / kHalfScale); }
+    __device__ static __half from_f(int q, double f) {
+        return __float2half_rn((float)((f - wq(q)) * (kHalfScale / wq(q))));
+    }
+    __device__ static __half from_dev(int q, double dev) { return __float2half_rn((float)(dev * (kHalfScale / wq(q)))); }
+};
+
+// ---- float-float ("double-single") arithmetic ----
+// A value is held as the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi)/2, about 48 significant bits.  The MIXED32 form keeps psi
+// and the outer residual this way: GB300 runs FP64 arithmetic and FP64
+// conversions at 1/64 of the FP32 rate, while these operations are a handful
+// of FP32 additions and FMAs.  The error-free transformations are Knuth's
+// TwoSum, Dekker's FastTwoSum and the FMA form of TwoProd (Muller et al.,
+// Handbook of Floating-Point Arithmetic, 2nd ed., Sec. 4.3 and 4.4); the
+// explicit _rn intrinsics keep the compiler from contracting or reassociating
+// them.
+struct ff {
+    float hi, lo;
+};
+
+// s + e == a + b exactly, s = fl(a + b)
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// as two_sum, valid when |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// float-float + float-float (the accurate two-TwoSum form)
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    const ff t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+// float-float + float
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    const ff s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// float-float * float-float (lo * lo dropped, below 2^-48 relative)
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+// Sum of terms kept as a float head plus a float tail of rounding errors
+// and low parts; cheaper than a chain of ff_add when terms are only added.
+struct ff_acc {
+    float s, t;
+    __device__ __forceinline__ void add(float hi, float lo) {
+        const ff r = two_sum(s, hi);
+        s = r.hi;
+        t = __fadd_rn(t, __fadd_rn(r.lo, lo));
+    }
+    __device__ __forceinline__ ff value() const { return two_sum(s, t); }
+};
+
+// host-side split of a double into float-float
+__host__ __device__ inline ff ff_from_double(double v) {
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
 }
 
 }  // namespace es

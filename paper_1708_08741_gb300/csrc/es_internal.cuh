@@ -6,8 +6,11 @@
 //               which keeps FP32 resolution for the small deviations.
 //   flags       N bytes: F_SOLID, F_NEAR19 (LBM / gradient fast path switch)
 //   owner       N int32: sphere index of an obstacle cell, -1 fluid
-//   psi         N doubles: EDL potential (outer FP64 iterate); MIXED32 also
-//               keeps a float copy psi32 for the FP32 body-force kernel
+//   psi         EDL potential, the outer iterate.  FP64 form: N doubles.
+//               MIXED32 form: two float arrays psi32 (high part, also what
+//               the FP32 kernels read) and psi_lo, a float-float value of
+//               about 48 bits; the outer residual is formed in float-float
+//               and rounded to the FP32 right-hand side rhs[0]
 //   fb          3 x N body force in the storage type of the PDFs
 //   st[l]       per multigrid level N_l bytes: kind (unknown / Dirichlet /
 //               Neumann) and a "near boundary" bit; the stencil is implied by
@@ -98,10 +101,10 @@ struct es_ctx {
     int cur, last_src;
     uint8_t* flags;
     int32_t* owner;
-    double* psi;
-    float* psi32;    // MIXED32: float copy of psi for the FP32 body force
-    double* r64;     // MIXED32: FP64 residual kept between incremental updates
-    float* delta;    // MIXED32: corrections accumulated since psi was last updated
+    double* psi;     // FP64 form only
+    float* psi32;    // MIXED32: high part of psi
+    float* psi_lo;   // MIXED32: low part of psi
+    float* pbc;      // MIXED32: np x 2, boundary value (2 zeta or sigma / eps) as float-float
     void* fb;
     // multigrid
     int L;
@@ -109,6 +112,9 @@ struct es_ctx {
     uint8_t* st[ES_MAXLEV];
     void* e[ES_MAXLEV];
     void* rhs[ES_MAXLEV];
+    void* e2[ES_MAXLEV];    // second iterate buffer: the fused sweep runs out of place
+    int n_sm;               // multiprocessors of the device
+    int rb_blocks[2];       // resident fused-sweep blocks per SM (float, double); 0 = not queried
     double* partial;
     int red_blocks;
     double* d_norm;
@@ -124,6 +130,21 @@ struct es_ctx {
     void* io;        // lazily allocated staging buffer of 19 N doubles
     void* gather;    // lazily allocated gather scratch (indices + values)
     std::string err;
+    // per-kernel event timing (es_profile_start / es_profile_stop)
+    struct ProfSlot {
+        std::string name;
+        int level;
+        int launches;
+        double bytes;
+    };
+    struct ProfRec {
+        int slot;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    std::vector<ProfSlot> prof_slots;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;  // events of earlier sessions, reused
 };
 
 namespace es {
@@ -136,9 +157,8 @@ cudaError_t launch_coarse_states(es_ctx* c);
 // solver (es_solver.cu)
 cudaError_t launch_outer_residual(es_ctx* c);
 cudaError_t launch_vcycle(es_ctx* c, int warm);
-cudaError_t launch_psi32(es_ctx* c);
-cudaError_t launch_incremental_residual(es_ctx* c, int first);
-cudaError_t launch_fold_delta(es_ctx* c);
+cudaError_t launch_split_psi(es_ctx* c, const double* src);  // MIXED32: psi = src
+cudaError_t launch_join_psi(es_ctx* c, double* dst);         // MIXED32: dst = psi
 cudaError_t launch_correct(es_ctx* c);
 cudaError_t launch_body_force(es_ctx* c);
 // lbm and particles (es_lbm.cu)
@@ -153,7 +173,32 @@ cudaError_t launch_set_fb(es_ctx* c, const double* src);
 cudaError_t launch_get_fb(es_ctx* c, double* dst);
 cudaError_t launch_gather(es_ctx* c, int which, const long long* idx, int n, double* out);
 
-inline bool mixed(const es_ctx* c) { return c->P.precision == ES_MIXED32; }
+// The reduced-precision forms (FP32 arithmetic, float-float psi): MIXED32
+// and MIXED16, which differ only in how the PDFs are stored.
+inline bool mixed(const es_ctx* c) { return c->P.precision == ES_MIXED32 || c->P.precision == ES_MIXED16; }
+
+// Bytes of one stored population.
+inline size_t pdf_bytes(int precision) {
+    return precision == ES_MIXED16 ? 2 : (precision == ES_MIXED32 ? 4 : 8);
+}
+
+// Capacity of the per-block partial-sum array of the residual norm.
+constexpr int kResPartials = 8192;
+
+// Brackets the launches made during its lifetime with CUDA events when the
+// context is profiling (no-op otherwise); bytes: algorithmic bytes of the
+// bracketed work.
+class ProfScope {
+   public:
+    ProfScope(es_ctx* c, const char* name, int level, double bytes);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+   private:
+    es_ctx* c_;
+    int rec_;
+};
 
 // Every launch site adds its kernel count here.
 inline void count(es_ctx* c, unsigned long long n = 1) { c->launches += n; }

@@ -17,18 +17,6 @@ namespace es {
 
 namespace {
 
-// Storage forms: FP64 keeps f_q; FP32 keeps f_q - w_q.
-template <class S>
-struct Store {
-    static constexpr bool shifted = sizeof(S) == 4;
-    // stored value of the rest state f_q = w_q
-    __device__ static S rest(int q) { return shifted ? (S)0 : (S)wq(q); }
-    // what to add to a stored value to obtain f_q
-    __device__ static double offset(int q) { return shifted ? wq(q) : 0.0; }
-    // the same for a direction known only at run time, with weight w
-    __device__ static double offset_rt(int, double w) { return shifted ? w : 0.0; }
-};
-
 // Base pointers of the 19 source and destination streams, so that an access
 // is a 32-bit cell offset from a base (no 64-bit products in the kernel).
 template <class S>
@@ -49,11 +37,12 @@ __global__ void k_particles_f32(int np, const DParticle* __restrict__ part, floa
     }
 }
 
-template <class S>
+template <class S, class C = typename Store<S>::C>
 __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
                                              const uint8_t* __restrict__ flags, const int32_t* __restrict__ owner,
                                              const DParticle* __restrict__ part, const float* __restrict__ partf,
-                                             const S* __restrict__ fb, S ax, S ay, S az, S lam_e, S lam_o) {
+                                             const C* __restrict__ fb, C ax, C ay, C az, C lam_e, C lam_o) {
+    using St = Store<S>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
@@ -63,7 +52,7 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
     const uint8_t fl = flags[c];
     if (fl & F_SOLID) return;  // obstacle cells are not updated
 
-    S f[19];
+    C f[19];
     if (!(fl & F_NEAR19)) {
         // all 18 pull sources are fluid cells inside the (periodic) domain;
         // the offset of x - e_q is a sum of per-axis steps (wrapped at faces)
@@ -73,26 +62,26 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
 #pragma unroll
         for (int q = 0; q < 19; q++) {
             const int s_ = c + sx[1 + cx(q)] + sy[1 + cy(q)] + sz[1 + cz(q)];
-            f[q] = __ldg(P.src[q] + s_);
+            f[q] = St::ld(q, __ldg(P.src[q] + s_));
         }
     } else {
-        f[0] = P.src[0][c];
+        f[0] = St::ld(0, P.src[0][c]);
 #pragma unroll
         for (int q = 1; q < 19; q++) {
             long long nb;
             if (!neighbour(g, x, y, z, -cx(q), -cy(q), -cz(q), nb)) {
                 // resting no-slip wall half-way outside: bounce back
-                f[q] = P.src[opp(q)][c];
+                f[q] = St::ld(opp(q), P.src[opp(q)][c]);
                 continue;
             }
             const int o = owner[nb];
             if (o < 0) {
-                f[q] = P.src[q][nb];
+                f[q] = St::ld(q, P.src[q][nb]);
                 continue;
             }
             // moving bounce-back (Eq. LBMMovWall): the population sent from x
             // towards the surface cell returns with 2 w_q rho_0 (c_q . u_s)/c_s^2
-            if constexpr (sizeof(S) == 4) {
+            if constexpr (sizeof(C) == 4) {
                 // FP32 form: lever arm from the float copy of the particle
                 const float* pf = partf + 12 * o;
                 float r[3] = {(float)x + 0.5f - (float)cx(q) - pf[0], (float)y + 0.5f - (float)cy(q) - pf[1],
@@ -108,7 +97,7 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
                 const float u1 = pf[4] + (pf[8] * r[0] - pf[6] * r[2]);
                 const float u2 = pf[5] + (pf[6] * r[1] - pf[7] * r[0]);
                 const float cu = (float)cx(q) * u0 + (float)cy(q) * u1 + (float)cz(q) * u2;
-                f[q] = P.src[opp(q)][c] + (float)(6.0 * wq(q)) * cu;
+                f[q] = St::ld(opp(q), P.src[opp(q)][c]) + (float)(6.0 * wq(q)) * cu;
             } else {
                 int bx = x - cx(q), by = y - cy(q), bz = z - cz(q);
                 bx = bx < 0 ? bx + g.nx : (bx >= g.nx ? bx - g.nx : bx);
@@ -117,16 +106,16 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
                 double us[3];
                 surface_velocity(g, part[o].x, part[o].v, part[o].w, bx, by, bz, us);
                 const double cu = cx(q) * us[0] + cy(q) * us[1] + cz(q) * us[2];
-                f[q] = P.src[opp(q)][c] + (S)(6.0 * wq(q) * cu);
+                f[q] = St::ld(opp(q), P.src[opp(q)][c]) + (C)(6.0 * wq(q) * cu);
             }
         }
     }
 
     // body force (Sec. 5.6) plus a uniform acceleration
-    const S fx = fb[c] + ax, fy = fb[N + c] + ay, fz = fb[2u * N + c] + az;
+    const C fx = fb[c] + ax, fy = fb[N + c] + ay, fz = fb[2u * N + c] + az;
 
     // moments (Eq. MacroscopVel) with the modified velocity (Eq. modified_velocity)
-    S rho = (S)0, jx = (S)0, jy = (S)0, jz = (S)0;
+    C rho = (C)0, jx = (C)0, jy = (C)0, jz = (C)0;
 #pragma unroll
     for (int q = 0; q < 19; q++) {
         rho += f[q];
@@ -136,36 +125,36 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
     }
     // in the shifted form rho holds rho - 1; w_q * rho below is then the
     // shifted equilibrium directly
-    const S ux = jx + (S)0.5 * fx, uy = jy + (S)0.5 * fy, uz = jz + (S)0.5 * fz;
-    const S uu = ux * ux + uy * uy + uz * uz;
-    const S uf = ux * fx + uy * fy + uz * fz;
-    const S ae = (S)1 + (S)0.5 * lam_e, ao = (S)1 + (S)0.5 * lam_o;
+    const C ux = jx + (C)0.5 * fx, uy = jy + (C)0.5 * fy, uz = jz + (C)0.5 * fz;
+    const C uu = ux * ux + uy * uy + uz * uz;
+    const C uf = ux * fx + uy * fy + uz * fz;
+    const C ae = (C)1 + (C)0.5 * lam_e, ao = (C)1 + (C)0.5 * lam_o;
 
     // rest population: even part only
     {
-        const S w0 = (S)wq(0);
-        const S eq0 = w0 * (rho - (S)1.5 * uu);
-        const S F0 = w0 * ((S)-3 * uf);
-        P.dst[0][c] = f[0] + lam_e * (f[0] - eq0) + ae * F0;
+        const C w0 = (C)wq(0);
+        const C eq0 = w0 * (rho - (C)1.5 * uu);
+        const C F0 = w0 * ((C)-3 * uf);
+        P.dst[0][c] = St::st(0, f[0] + lam_e * (f[0] - eq0) + ae * F0);
     }
     // pairs (q, q+9): TRT split into even and odd parts (Eq. TRTOp, Eq. EqPDF_TRT)
 #pragma unroll
     for (int q = 1; q <= 9; q++) {
-        const S w = (S)wq(q);
-        const S cu = (S)cx(q) * ux + (S)cy(q) * uy + (S)cz(q) * uz;
-        const S cf = (S)cx(q) * fx + (S)cy(q) * fy + (S)cz(q) * fz;
-        const S eq_e = w * (rho + (S)4.5 * cu * cu - (S)1.5 * uu);
-        const S eq_o = w * (S)3 * cu;
-        const S fe = (S)0.5 * (f[q] + f[q + 9]);
-        const S fo = (S)0.5 * (f[q] - f[q + 9]);
+        const C w = (C)wq(q);
+        const C cu = (C)cx(q) * ux + (C)cy(q) * uy + (C)cz(q) * uz;
+        const C cf = (C)cx(q) * fx + (C)cy(q) * fy + (C)cz(q) * fz;
+        const C eq_e = w * (rho + (C)4.5 * cu * cu - (C)1.5 * uu);
+        const C eq_o = w * (C)3 * cu;
+        const C fe = (C)0.5 * (f[q] + f[q + 9]);
+        const C fo = (C)0.5 * (f[q] - f[q + 9]);
         // Luo's term (Eq. LBE_forcetermLuo) split: even w(9 cu cf - 3 u.f), odd 3 w cf,
         // with the (1 + lambda/2) factors that go with the modified velocity
-        const S Fe = w * ((S)9 * cu * cf - (S)3 * uf);
-        const S Fo = w * (S)3 * cf;
-        const S even = lam_e * (fe - eq_e) + ae * Fe;
-        const S odd = lam_o * (fo - eq_o) + ao * Fo;
-        P.dst[q][c] = f[q] + even + odd;
-        P.dst[q + 9][c] = f[q + 9] + even - odd;
+        const C Fe = w * ((C)9 * cu * cf - (C)3 * uf);
+        const C Fo = w * (C)3 * cf;
+        const C even = lam_e * (fe - eq_e) + ae * Fe;
+        const C odd = lam_o * (fo - eq_o) + ao * Fo;
+        P.dst[q][c] = St::st(q, f[q] + even + odd);
+        P.dst[q + 9][c] = St::st(q + 9, f[q + 9] + even - odd);
     }
 }
 
@@ -259,7 +248,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(Grid g, const DParticl
             const double us2 = P.v[2] + (P.w[0] * r1 - P.w[1] * r0);
             const double cu = qx * us0 + qy * us1 + qz * us2;
             const double w = (q <= 3 || (q >= 10 && q <= 12)) ? 1.0 / 18.0 : 1.0 / 36.0;
-            const double fq = (double)src[q * ps + cc] + Store<S>::offset_rt(q, w);
+            const double fq = Store<S>::to_f(q, src[q * ps + cc]);
             const double m = 2.0 * fq - 6.0 * w * cu;
             const double d0 = m * qx, d1 = m * qy, d2 = m * qz;
             acc[0] += d0;
@@ -319,7 +308,7 @@ __global__ void k_get_pdf(long long N, long long ps, const S* src, double* dst) 
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 19 * N) return;
     int q = (int)(i / N);
-    dst[i] = (double)src[(long long)q * ps + (i - (long long)q * N)] + Store<S>::offset(q);
+    dst[i] = Store<S>::to_f(q, src[(long long)q * ps + (i - (long long)q * N)]);
 }
 
 template <class S>
@@ -327,17 +316,17 @@ __global__ void k_set_pdf(long long N, long long ps, const double* src, S* dst) 
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 19 * N) return;
     int q = (int)(i / N);
-    dst[(long long)q * ps + (i - (long long)q * N)] = (S)(src[i] - Store<S>::offset(q));
+    dst[(long long)q * ps + (i - (long long)q * N)] = Store<S>::from_f(q, src[i]);
 }
 
-template <class S>
-__global__ void k_moments(long long N, long long ps, const S* f, const S* fb, double ax, double ay, double az,
+template <class S, class C = typename Store<S>::C>
+__global__ void k_moments(long long N, long long ps, const S* f, const C* fb, double ax, double ay, double az,
                           double* rho, double* u) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
     for (int q = 0; q < 19; q++) {
-        double v = (double)f[(long long)q * ps + c] + Store<S>::offset(q);
+        double v = Store<S>::to_f(q, f[(long long)q * ps + c]);
         r += v;
         j0 += cx(q) * v;
         j1 += cy(q) * v;
@@ -364,15 +353,15 @@ __global__ void k_load_fb(long long n, const double* a, S* b) {
     if (i < n) b[i] = (S)a[i];
 }
 
-template <class S>
+template <class S, class C = typename Store<S>::C>
 __global__ void k_gather(int which, long long N, long long ps, const long long* idx, int n, const S* cur, const S* last,
-                         const S* fb, const double* psi, const int32_t* owner, const uint8_t* flags, double ax,
-                         double ay, double az, double* out) {
+                         const C* fb, const double* psi, const float* psi_hi, const float* psi_lo,
+                         const int32_t* owner, const uint8_t* flags, double ax, double ay, double az, double* out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     long long c = idx[i];
     switch (which) {
-    case ES_FIELD_PSI: out[i] = psi[c]; break;
+    case ES_FIELD_PSI: out[i] = psi ? psi[c] : (double)psi_hi[c] + (double)psi_lo[c]; break;
     case ES_FIELD_OWNER: out[i] = (double)owner[c]; break;
     case ES_FIELD_FLAGS: out[i] = (double)flags[c]; break;
     case ES_FIELD_FB:
@@ -381,14 +370,14 @@ __global__ void k_gather(int which, long long N, long long ps, const long long* 
     case ES_FIELD_PDF:
     case ES_FIELD_PDF_LAST: {
         const S* f = which == ES_FIELD_PDF ? cur : last;
-        for (int q = 0; q < 19; q++) out[(long long)q * n + i] = (double)f[q * ps + c] + Store<S>::offset(q);
+        for (int q = 0; q < 19; q++) out[(long long)q * n + i] = Store<S>::to_f(q, f[q * ps + c]);
         break;
     }
     case ES_FIELD_RHO:
     case ES_FIELD_U: {
         double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
         for (int q = 0; q < 19; q++) {
-            double v = (double)cur[q * ps + c] + Store<S>::offset(q);
+            double v = Store<S>::to_f(q, cur[q * ps + c]);
             r += v;
             j0 += cx(q) * v;
             j1 += cy(q) * v;
@@ -422,22 +411,36 @@ Streams<S> streams(const es_ctx* c) {
     return P;
 }
 
+// Calls fn with a value of the context's PDF storage type (double, float or
+// __half) so that a generic lambda can instantiate the kernel for it.
+template <class Fn>
+void dispatch_store(const es_ctx* c, Fn&& fn) {
+    if (c->P.precision == ES_MIXED16)
+        fn(__half{});
+    else if (mixed(c))
+        fn(0.0f);
+    else
+        fn(0.0);
+}
+
 cudaError_t launch_lbm(es_ctx* c) {
     const Grid& g = c->g;
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
     const double* a = c->P.accel;
-    if (mixed(c)) {
-        if (c->np > 0) {
-            k_particles_f32<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->np, c->part, c->partf);
-            count(c);
-        }
-        k_lbm<float><<<grd, blk, 0, c->stream>>>(g, streams<float>(c), c->flags, c->owner, c->part, c->partf,
-                                                 (const float*)c->fb, (float)a[0], (float)a[1], (float)a[2],
-                                                 (float)c->lambda_e, (float)c->lambda_o);
-    } else {
-        k_lbm<double><<<grd, blk, 0, c->stream>>>(g, streams<double>(c), c->flags, c->owner, c->part, nullptr,
-                                                  (const double*)c->fb, a[0], a[1], a[2], c->lambda_e, c->lambda_o);
+    if (mixed(c) && c->np > 0) {
+        k_particles_f32<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->np, c->part, c->partf);
+        count(c);
     }
+    dispatch_store(c, [&](auto tag) {
+        using S = decltype(tag);
+        using C = typename Store<S>::C;
+        // algorithmic bytes per cell: 19 populations in and out, f_b (3 C)
+        // and the flag byte in
+        ProfScope ps(c, "lbm", -1, (double)g.N * (38.0 * sizeof(S) + 3.0 * sizeof(C) + 1.0));
+        k_lbm<S><<<grd, blk, 0, c->stream>>>(g, streams<S>(c), c->flags, c->owner, c->part, c->partf,
+                                             (const C*)c->fb, (C)a[0], (C)a[1], (C)a[2], (C)c->lambda_e,
+                                             (C)c->lambda_o);
+    });
     count(c);
     return cudaGetLastError();
 }
@@ -446,12 +449,11 @@ cudaError_t launch_forces(es_ctx* c) {
     if (c->np == 0) return cudaSuccess;
     const double* E = c->P.E_ext;
     int src = c->last_src >= 0 ? c->last_src : c->cur;
-    if (mixed(c))
-        k_forces<float><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags, (const float*)c->pdf[src],
-                                                      E[0], E[1], E[2], c->F, c->T);
-    else
-        k_forces<double><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
-                                                       (const double*)c->pdf[src], E[0], E[1], E[2], c->F, c->T);
+    dispatch_store(c, [&](auto tag) {
+        using S = decltype(tag);
+        k_forces<S><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
+                                                            (const S*)c->pdf[src], E[0], E[1], E[2], c->F, c->T);
+    });
     count(c);
     return cudaGetLastError();
 }
@@ -468,42 +470,42 @@ cudaError_t launch_advance(es_ctx* c) {
 cudaError_t launch_fill_rest(es_ctx* c) {
     const int N = (int)c->g.N;
     dim3 grd((N + 255) / 256, 19);
-    if (mixed(c))
-        k_fill_rest<float><<<grd, 256, 0, c->stream>>>(N, (size_t)c->g.ps, (float*)c->pdf[0], (float*)c->pdf[1]);
-    else
-        k_fill_rest<double><<<grd, 256, 0, c->stream>>>(N, (size_t)c->g.ps, (double*)c->pdf[0], (double*)c->pdf[1]);
+    dispatch_store(c, [&](auto tag) {
+        using S = decltype(tag);
+        k_fill_rest<S><<<grd, 256, 0, c->stream>>>(N, (size_t)c->g.ps, (S*)c->pdf[0], (S*)c->pdf[1]);
+    });
     count(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_get_pdf(es_ctx* c, int buf, double* dst) {
     long long n = 19 * c->g.N;
-    if (mixed(c))
-        k_get_pdf<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const float*)c->pdf[buf], dst);
-    else
-        k_get_pdf<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const double*)c->pdf[buf], dst);
+    dispatch_store(c, [&](auto tag) {
+        using S = decltype(tag);
+        k_get_pdf<S><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const S*)c->pdf[buf], dst);
+    });
     count(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_pdf(es_ctx* c, const double* src) {
     long long n = 19 * c->g.N;
-    if (mixed(c))
-        k_set_pdf<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, src, (float*)c->pdf[c->cur]);
-    else
-        k_set_pdf<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, src, (double*)c->pdf[c->cur]);
+    dispatch_store(c, [&](auto tag) {
+        using S = decltype(tag);
+        k_set_pdf<S><<<blocks_for(n, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, src, (S*)c->pdf[c->cur]);
+    });
     count(c);
     return cudaGetLastError();
 }
 
 cudaError_t launch_get_moments(es_ctx* c, double* rho, double* u) {
     const double* a = c->P.accel;
-    if (mixed(c))
-        k_moments<float><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const float*)c->pdf[c->cur],
-                                                                         (const float*)c->fb, a[0], a[1], a[2], rho, u);
-    else
-        k_moments<double><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const double*)c->pdf[c->cur],
-                                                                          (const double*)c->fb, a[0], a[1], a[2], rho, u);
+    dispatch_store(c, [&](auto tag) {
+        using S = decltype(tag);
+        using C = typename Store<S>::C;
+        k_moments<S><<<blocks_for(c->g.N, 256), 256, 0, c->stream>>>(c->g.N, c->g.ps, (const S*)c->pdf[c->cur],
+                                                                     (const C*)c->fb, a[0], a[1], a[2], rho, u);
+    });
     count(c);
     return cudaGetLastError();
 }
@@ -531,14 +533,13 @@ cudaError_t launch_get_fb(es_ctx* c, double* dst) {
 cudaError_t launch_gather(es_ctx* c, int which, const long long* idx, int n, double* out) {
     const double* a = c->P.accel;
     int last = c->last_src >= 0 ? c->last_src : c->cur;
-    if (mixed(c))
-        k_gather<float><<<blocks_for(n, 128), 128, 0, c->stream>>>(
-            which, c->g.N, c->g.ps, idx, n, (const float*)c->pdf[c->cur], (const float*)c->pdf[last], (const float*)c->fb,
-            c->psi, c->owner, c->flags, a[0], a[1], a[2], out);
-    else
-        k_gather<double><<<blocks_for(n, 128), 128, 0, c->stream>>>(
-            which, c->g.N, c->g.ps, idx, n, (const double*)c->pdf[c->cur], (const double*)c->pdf[last],
-            (const double*)c->fb, c->psi, c->owner, c->flags, a[0], a[1], a[2], out);
+    dispatch_store(c, [&](auto tag) {
+        using S = decltype(tag);
+        using C = typename Store<S>::C;
+        k_gather<S><<<blocks_for(n, 128), 128, 0, c->stream>>>(
+            which, c->g.N, c->g.ps, idx, n, (const S*)c->pdf[c->cur], (const S*)c->pdf[last], (const C*)c->fb,
+            c->psi, c->psi32, c->psi_lo, c->owner, c->flags, a[0], a[1], a[2], out);
+    });
     count(c);
     return cudaGetLastError();
 }

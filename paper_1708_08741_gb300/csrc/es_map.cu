@@ -89,7 +89,7 @@ __global__ void k_clear(Grid g, const DParticle* part, const double* mapped, int
 }
 
 __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* owner, double* psi,
-                      float* psi32, int* status) {
+                      float* psi_hi, float* psi_lo, int* status) {
     int p = blockIdx.x;
     DParticle P = part[p];
     if (threadIdx.x == 0) {
@@ -99,7 +99,7 @@ __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* o
     }
     // boundary value kept in the solution field at boundary cells (Sec. 5.4)
     const double bval = kind[p] == ES_KIND_ZETA ? P.zeta : 0.0;
-    const float bval32 = (float)bval;
+    const ff bff = ff_from_double(bval);
     Box b = sphere_box(g, P.x, P.R, 0);
     int n = b.count();
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -109,8 +109,12 @@ __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* o
         long long c = lin(g, x, y, z);
         int old = atomicExch(&owner[c], p);
         if (old >= 0 && old != p) atomicOr(status, DS_OVERLAP);
-        psi[c] = bval;
-        if (psi32) psi32[c] = bval32;
+        if (psi) {
+            psi[c] = bval;
+        } else {
+            psi_hi[c] = bff.hi;
+            psi_lo[c] = bff.lo;
+        }
     }
 }
 
@@ -120,7 +124,6 @@ __global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, i
     const double* M = mapped + 9 * p;  // x, v, w at the last mapping
     Box b = sphere_box(g, M, part[p].R, 0);
     int n = b.count();
-    constexpr bool shifted = sizeof(S) == 4;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         int x, y, z;
         b.cell(g, t, x, y, z);
@@ -135,7 +138,7 @@ __global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, i
             double cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
             // f^eq(rho_0 = 1, u_s) of Eq. fequ_Incompr_SRT
             double dev = wq(q) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-            pdf[(long long)q * g.ps + c] = shifted ? (S)dev : (S)(wq(q) + dev);
+            pdf[(long long)q * g.ps + c] = Store<S>::from_dev(q, dev);
         }
     }
 }
@@ -200,13 +203,22 @@ __global__ void k_flags(Grid g, DParticle* part, const double* mapped, const int
     }
 }
 
-__global__ void k_store_mapped(const DParticle* part, double* mapped, int np) {
+// Keeps the mapped state for the next reconstruction and, in the MIXED32
+// form, the sphere's boundary value for the float-float outer residual:
+// 2 zeta for a Dirichlet sphere, sigma / eps for a charged one (Sec. 5.4).
+__global__ void k_store_mapped(const DParticle* part, const int* kind, double eps, double* mapped, float* pbc,
+                               int np) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     for (int a = 0; a < 3; a++) {
         mapped[9 * p + a] = part[p].x[a];
         mapped[9 * p + 3 + a] = part[p].v[a];
         mapped[9 * p + 6 + a] = part[p].w[a];
+    }
+    if (pbc) {
+        const ff v = ff_from_double(kind[p] == ES_KIND_ZETA ? 2.0 * part[p].zeta : part[p].sigma / eps);
+        pbc[2 * p] = v.hi;
+        pbc[2 * p + 1] = v.lo;
     }
 }
 
@@ -276,13 +288,16 @@ cudaError_t launch_map(es_ctx* c) {
     const Grid& g = c->g;
     const int T = 256;
     k_clear<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner);
-    k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->psi32, c->d_status);
-    if (mixed(c))
+    k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->psi32, c->psi_lo, c->d_status);
+    if (c->P.precision == ES_MIXED16)
+        k_uncover<__half><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (__half*)c->pdf[c->cur]);
+    else if (mixed(c))
         k_uncover<float><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (float*)c->pdf[c->cur]);
     else
         k_uncover<double><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (double*)c->pdf[c->cur]);
     k_flags<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->kind, c->owner, c->flags, c->st[0], c->nfaces);
-    k_store_mapped<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->part, c->mapped, c->np);
+    k_store_mapped<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->part, c->kind, c->S.eps, c->mapped, c->pbc,
+                                                                c->np);
     count(c, 5);
     return cudaGetLastError();
 }

@@ -9,8 +9,10 @@
 // RHS sigma / eps; zero-flux wall: centre -1).  This is the quasi-constant
 // stencil idea of Sec. 5.3 taken to its limit: one byte per cell.
 //
-// The outer loop runs in FP64 on psi; the V-cycle solves A e = r for the
-// correction in the inner type T (double, or float in the MIXED32 form).
+// The outer loop (defect correction) keeps psi and r = b - A psi in FP64,
+// or in the MIXED32 form in float-float (two floats, about 48 bits); the
+// V-cycle solves A e = r for the correction in the inner type T (double, or
+// float in the MIXED32 form).
 //
 // GB300 executes FP64 arithmetic (and conversions to and from FP64) on a
 // pipe with 1/64 of the FP32 rate, so the FP32 kernels here carry no double
@@ -74,22 +76,19 @@ __device__ __forceinline__ int fine_face(const Grid& g, const Solver& s, const i
     return -1;
 }
 
-// r = b - A psi on the unknowns (FP64), stored as the V-cycle right-hand
-// side in type T, and per-block partial sums of r^2.  Blocks stride over
-// rows (y, z); threads over x.  At an interior cell this is 5 adds, 2 FMAs
-// and one conversion in FP64.
-template <class T>
+// r = b - A psi on the unknowns (FP64 form), stored as the V-cycle
+// right-hand side, and per-block partial sums of r^2.  Blocks stride over
+// rows (y, z); threads over x.
 __global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s, double diag0,
                                                                 const double* __restrict__ psi,
                                                                 const uint8_t* __restrict__ st0,
                                                                 const int32_t* __restrict__ owner,
                                                                 const DParticle* __restrict__ part,
-                                                                const int* __restrict__ kind, T* __restrict__ r_out,
-                                                                double* __restrict__ r64, double* __restrict__ partial) {
+                                                                const int* __restrict__ kind,
+                                                                double* __restrict__ r_out,
+                                                                double* __restrict__ partial) {
     __shared__ double sh[32];
-    // r^2 is summed per thread in the inner type (the norm only feeds the
-    // tolerance test), then across the block in FP64
-    T acc = (T)0;
+    double acc = 0.0;
     const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
     const int rows = g.ny * g.nz;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -120,94 +119,214 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s
                         }
                     r = b - (diag * psi[c] - off);
                 }
-                const T rt = (T)r;
-                acc += rt * rt;
+                acc += r * r;
             }
-            r_out[c] = (T)r;
-            if (r64) r64[c] = r;
+            r_out[c] = r;
         }
     }
-    double tot = block_sum((double)acc, sh);
+    double tot = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-// MIXED32 incremental residual: after the V-cycles produced the correction
-// e for the right-hand side r, the new residual is r - A e.  It is formed
-// with A e in FP32 and kept in FP64 (one conversion and one add per cell),
-// e is accumulated into delta (psi is updated once, by k_fold_delta), and
-// the float copy of the residual feeds the next V-cycles.
-__global__ void __launch_bounds__(kRedThreads) k_incr_residual(Grid g, Solver s, float diag0,
-                                                               const uint8_t* __restrict__ st0,
-                                                               const float* __restrict__ e,
-                                                               double* __restrict__ r64, float* __restrict__ r32,
-                                                               float* __restrict__ delta, int first,
-                                                               double* __restrict__ partial) {
+// Wall boundary values 2 * pot_val of a Dirichlet wall, as float-float.
+struct WallFF {
+    float hi[6], lo[6];
+};
+
+// r = b - A psi for the MIXED32 form, with psi = psi_hi + psi_lo in
+// float-float.  The sum that cancels (neighbours + b - diag * psi_c, whose
+// terms are ~1e6 times the residual near convergence) is formed without
+// rounding error in its high parts: the diag * psi_c product is split
+// exactly with an FMA (TwoProd) and the high parts are accumulated with
+// TwoSum, the low parts in plain FP32; the result is then rounded once to
+// the float right-hand side of the V-cycles (the only consumer).  The
+// diagonal 6 + kappa^2 arrives as float-float; a boundary face changes it
+// by +-1 and adds its float-float boundary value to b.  Threads own W = 4
+// consecutive cells of a row (16-byte loads, as the vector smoother) or
+// single cells (W = 1) when nx is not a multiple of 4; blocks of (32, 8)
+// threads stride over z, and each block leaves one partial sum of r^2.
+struct HiSum {
+    float s, e;  // s + e == exact sum of the high parts added so far (e rounded)
+    __device__ __forceinline__ void add(float h) {
+        const ff t = two_sum(s, h);
+        s = t.hi;
+        e = __fadd_rn(e, t.lo);
+    }
+};
+
+template <int W>
+__device__ __forceinline__ void load_span(const float* p, float (&v)[W], int off) {
+    if constexpr (W == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[off + 0] = q.x;
+        v[off + 1] = q.y;
+        v[off + 2] = q.z;
+        v[off + 3] = q.w;
+    } else {
+        v[off] = *p;
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, WallFF wall,
+                                                           const float* __restrict__ psi_hi,
+                                                           const float* __restrict__ psi_lo,
+                                                           const uint8_t* __restrict__ st0,
+                                                           const int32_t* __restrict__ owner,
+                                                           const int* __restrict__ kind,
+                                                           const float2* __restrict__ pbc, int pot_dir_mask,
+                                                           float* __restrict__ r_out,
+                                                           double* __restrict__ partial) {
     __shared__ double sh[32];
     float acc = 0.0f;
-    const int nx = g.nx, ny = g.ny, nxy = g.nx * g.ny;
-    const int rows = g.ny * g.nz;
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int y = row % ny, z = row / ny;
-        const int base = row * nx;
-        const int ym = (y == 0 ? ny - 1 : y - 1) - y, yp = (y == ny - 1 ? 0 : y + 1) - y;
-        const int zm = (z == 0 ? g.nz - 1 : z - 1) - z, zp = (z == g.nz - 1 ? 0 : z + 1) - z;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-            const int c = base + x;
-            const uint8_t st = st0[c];
-            if ((st & ST_KIND) != ST_UNKNOWN) continue;
-            const float ec = e[c];
-            float Ae;
-            if (!(st & ST_NEAR)) {
-                const int xm = (x == 0 ? nx - 1 : x - 1) - x, xp = (x == nx - 1 ? 0 : x + 1) - x;
-                float off = e[c + xm];
-                off += e[c + xp];
-                off += e[c + ym * nx];
-                off += e[c + yp * nx];
-                off += e[c + zm * nxy];
-                off += e[c + zp * nxy];
-                Ae = diag0 * ec - off;
-            } else {
-                float diag = diag0, off = 0.0f;
-                const int v[3] = {x, y, z}, n3[3] = {nx, ny, g.nz}, stride[3] = {1, nx, nxy};
-                for (int a = 0; a < 3; a++)
-                    for (int side = -1; side <= 1; side += 2) {
-                        int p = v[a] + side;
-                        if (p < 0 || p >= n3[a]) {
-                            if (!g.per[a]) {
-                                diag += (s.pot_bc[2 * a + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? 1.0f : -1.0f;
-                                continue;
-                            }
-                            p = p < 0 ? p + n3[a] : p - n3[a];
-                        }
-                        const int nb = c + (p - v[a]) * stride[a];
-                        const uint8_t k = st0[nb] & ST_KIND;
-                        if (k == ST_UNKNOWN)
-                            off += e[nb];
-                        else
-                            diag += (k == ST_DIR) ? 1.0f : -1.0f;
-                    }
-                Ae = diag * ec - off;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = g.nx * g.ny;
+    const int xs = W * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    const bool active = xs < nx && y < ny;
+    int ym = 0, yp = 0, xl = 0, xr = 0;
+    bool okym = false, okyp = false, okxl = false, okxr = false;
+    if (active) {
+        okym = wrap_axis(y - 1, ny, g.per[1], ym);
+        okyp = wrap_axis(y + 1, ny, g.per[1], yp);
+        okxl = wrap_axis(xs - 1, nx, g.per[0], xl);
+        okxr = wrap_axis(xs + W, nx, g.per[0], xr);
+    }
+    for (int z = blockIdx.z; z < nz && active; z += gridDim.z) {
+        const int row = nx * (y + ny * z);
+        int zm = 0, zp = 0;
+        const bool okzm = wrap_axis(z - 1, nz, g.per[2], zm), okzp = wrap_axis(z + 1, nz, g.per[2], zp);
+        uint8_t sv[W];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < W; i++) {
+            sv[i] = st0[row + xs + i];
+            any |= (sv[i] & ST_KIND) == ST_UNKNOWN;
+        }
+        float out[W];
+#pragma unroll
+        for (int i = 0; i < W; i++) out[i] = 0.0f;
+        if (any) {
+            // x row with one neighbour each side, and the four neighbour rows
+            float ch[W + 2], cl[W + 2], ah[W], al[W], bh[W], bl[W], dh[W], dl[W], fh[W], fl[W];
+#pragma unroll
+            for (int i = 0; i < W; i++) ah[i] = al[i] = bh[i] = bl[i] = dh[i] = dl[i] = fh[i] = fl[i] = 0.0f;
+            ch[0] = cl[0] = ch[W + 1] = cl[W + 1] = 0.0f;
+            if (okxl) {
+                ch[0] = psi_hi[row + xl];
+                cl[0] = psi_lo[row + xl];
             }
-            const double r = r64[c] - (double)Ae;
-            r64[c] = r;
-            const float rf = (float)r;
-            r32[c] = rf;
-            acc += rf * rf;
-            delta[c] = first ? ec : delta[c] + ec;
+            if (okxr) {
+                ch[W + 1] = psi_hi[row + xr];
+                cl[W + 1] = psi_lo[row + xr];
+            }
+            {
+                float t[W];
+                load_span<W>(psi_hi + row + xs, t, 0);
+#pragma unroll
+                for (int i = 0; i < W; i++) ch[i + 1] = t[i];
+                load_span<W>(psi_lo + row + xs, t, 0);
+#pragma unroll
+                for (int i = 0; i < W; i++) cl[i + 1] = t[i];
+            }
+            const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
+            const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
+            if (okym) {
+                load_span<W>(psi_hi + rym + xs, ah, 0);
+                load_span<W>(psi_lo + rym + xs, al, 0);
+            }
+            if (okyp) {
+                load_span<W>(psi_hi + ryp + xs, bh, 0);
+                load_span<W>(psi_lo + ryp + xs, bl, 0);
+            }
+            if (okzm) {
+                load_span<W>(psi_hi + rzm + xs, dh, 0);
+                load_span<W>(psi_lo + rzm + xs, dl, 0);
+            }
+            if (okzp) {
+                load_span<W>(psi_hi + rzp + xs, fh, 0);
+                load_span<W>(psi_lo + rzp + xs, fl, 0);
+            }
+#pragma unroll
+            for (int i = 0; i < W; i++) {
+                if ((sv[i] & ST_KIND) != ST_UNKNOWN) continue;
+                const float hc = ch[i + 1], lc = cl[i + 1];
+                HiSum hs = {0.0f, 0.0f};
+                float lo;
+                ff dg = diag0;
+                if (!(sv[i] & ST_NEAR)) {
+                    hs.add(ch[i]);
+                    hs.add(ch[i + 2]);
+                    hs.add(ah[i]);
+                    hs.add(bh[i]);
+                    hs.add(dh[i]);
+                    hs.add(fh[i]);
+                    lo = __fadd_rn(__fadd_rn(__fadd_rn(cl[i], cl[i + 2]), __fadd_rn(al[i], bl[i])),
+                                   __fadd_rn(dl[i], fl[i]));
+                } else {
+                    lo = 0.0f;
+                    int dk = 0;
+                    const int gx = xs + i;
+                    const int g3[3] = {gx, y, z}, n3[3] = {nx, ny, nz};
+                    const float nh[6] = {ch[i], ch[i + 2], ah[i], bh[i], dh[i], fh[i]};
+                    const float nl[6] = {cl[i], cl[i + 2], al[i], bl[i], dl[i], fl[i]};
+                    const int nbr[6] = {row + (gx == 0 ? xl : gx - 1), row + (gx == nx - 1 ? xr : gx + 1),
+                                        rym + gx, ryp + gx, rzm + gx, rzp + gx};
+#pragma unroll
+                    for (int k = 0; k < 6; k++) {
+                        const int ax = k >> 1, side = (k & 1) ? 1 : -1;
+                        const int q = g3[ax] + side;
+                        if ((q < 0 || q >= n3[ax]) && !g.per[ax]) {
+                            const int face = 2 * ax + (side > 0 ? 1 : 0);
+                            if ((pot_dir_mask >> face) & 1) {
+                                dk += 1;
+                                hs.add(wall.hi[face]);
+                                lo = __fadd_rn(lo, wall.lo[face]);
+                            } else {
+                                dk -= 1;
+                            }
+                            continue;
+                        }
+                        const int ow = owner[nbr[k]];
+                        if (ow < 0) {
+                            hs.add(nh[k]);
+                            lo = __fadd_rn(lo, nl[k]);
+                        } else {
+                            dk += kind[ow] == ES_KIND_ZETA ? 1 : -1;
+                            const float2 bv = pbc[ow];
+                            hs.add(bv.x);
+                            lo = __fadd_rn(lo, bv.y);
+                        }
+                    }
+                    dg = ff_add_f(diag0, (float)dk);
+                }
+                // - diag * psi_c: high product split exactly, low terms to lo
+                const float p = __fmul_rn(dg.hi, hc);
+                float t = __fmaf_rn(dg.hi, hc, -p);
+                t = __fmaf_rn(dg.hi, lc, t);
+                t = __fmaf_rn(dg.lo, hc, t);
+                hs.add(-p);
+                lo = __fsub_rn(lo, t);
+                const float r = __fadd_rn(hs.s, __fadd_rn(hs.e, lo));
+                out[i] = r;
+                acc = __fmaf_rn(r, r, acc);
+            }
+        }
+        if constexpr (W == 4) {
+            *reinterpret_cast<float4*>(r_out + row + xs) = make_float4(out[0], out[1], out[2], out[3]);
+        } else {
+            r_out[row + xs] = out[0];
         }
     }
-    double tot = block_sum((double)acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-__global__ void k_fold_delta(int N, const uint8_t* __restrict__ st0, const float* __restrict__ delta,
-                             double* __restrict__ psi, float* __restrict__ psi32) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    if ((st0[c] & ST_KIND) != ST_UNKNOWN) return;
-    const double v = psi[c] + (double)delta[c];
-    psi[c] = v;
-    psi32[c] = (float)v;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    double v = (double)acc;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; w++) tot += sh[w];
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+    }
 }
 
 __global__ void k_finalize_norm(const double* partial, int n, double* out) {
@@ -443,6 +562,264 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
     for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[4 + v], c[5 + v], c[6 + v], c[7 + v]);
 }
 
+// ---- fused red-black sweep ----
+//
+// One full Gauss-Seidel sweep (red half, then black half) in a single pass
+// over the level, out of place (ein -> eout).  A block owns a TX x TY tile of
+// (x, y) and a chunk of z planes and marches up z with a 5-plane ring in
+// shared memory: at plane p it updates the red cells of plane p on the tile
+// plus a one-cell ring, then the black cells of plane p - 1 on the tile
+// (all of whose red neighbours are final by then), and writes plane p - 1.
+// The ring of red cells is recomputed by the neighbouring tiles as well
+// (overlapped tiling), so blocks never wait on one another; every value a
+// block reads comes from ein, which no block writes.  Per cell and sweep
+// the level moves e in and out once, plus rhs and the state byte: half the
+// traffic of two in-place half sweeps.  The per-cell arithmetic is that of
+// k_smooth_v.  Planes are fetched two ahead into registers so the loads of
+// plane p + 2 overlap the updates of planes p and p - 1.
+template <class T, int TX, int TY>
+struct RB {
+    static constexpr int RW = TX + 4, RH = TY + 4;  // tile + 2-cell ring (e, states)
+    static constexpr int QW = TX + 2, QH = TY + 2;  // tile + 1-cell ring (red cells, rhs)
+    static constexpr int NE = RW * RH, NQ = QW * QH;
+    static constexpr int NT = 256;
+    static constexpr int KE = (NE + NT - 1) / NT, KQ = (NQ + NT - 1) / NT;
+    static constexpr int NRED = QH * (QW / 2);
+    static constexpr int KR = (NRED + NT - 1) / NT;
+    static constexpr size_t smem = (size_t)(5 * NE + 3 * NQ) * sizeof(T) + 5 * NE;
+    static_assert(TX % 4 == 0 && (TX / 4) * TY == NT, "one thread per 4 output cells");
+};
+
+__device__ __forceinline__ bool axis_ok(int v, int n, int per, int& w) {
+    if (v >= 0 && v < n) {
+        w = v;
+        return true;
+    }
+    if (!per) return false;
+    w = v % n;
+    if (w < 0) w += n;
+    return true;
+}
+
+// Gauss-Seidel value of one unknown cell from the shared-memory ring.
+// (rr, cc): position in the RH x RW ring; em, e0, ep: planes z-1, z, z+1;
+// sm, s0, sp: their states; g*: unwrapped global coordinates.
+template <class T, int RW>
+__device__ __forceinline__ T rb_update(const Level<T>& L, T inv_diag0, T omega, const T* em, const T* e0,
+                                       const T* ep, const uint8_t* sm, const uint8_t* s0, const uint8_t* sp,
+                                       int rr, int cc, uint8_t sv, T rhsv, int gx, int gy, int gz) {
+    const int i = rr * RW + cc;
+    T gs;
+    if (!(sv & ST_NEAR)) {
+        T o = e0[i - 1];
+        o += e0[i + 1];
+        o += e0[i - RW];
+        o += e0[i + RW];
+        o += em[i];
+        o += ep[i];
+        gs = (L.h2 * rhsv + o) * inv_diag0;
+    } else {
+        T dg = L.diag0, o = (T)0;
+        const int g3[3] = {gx, gy, gz}, n3[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++)
+#pragma unroll
+            for (int side = -1; side <= 1; side += 2) {
+                const int q = g3[ax] + side;
+                if ((q < 0 || q >= n3[ax]) && !L.per[ax]) {
+                    dg += (L.pot_bc[2 * ax + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? (T)1 : (T)-1;
+                    continue;
+                }
+                uint8_t k;
+                T v;
+                if (ax == 0) {
+                    k = s0[i + side];
+                    v = e0[i + side];
+                } else if (ax == 1) {
+                    k = s0[i + side * RW];
+                    v = e0[i + side * RW];
+                } else {
+                    k = side < 0 ? sm[i] : sp[i];
+                    v = side < 0 ? em[i] : ep[i];
+                }
+                k &= ST_KIND;
+                if (k == ST_UNKNOWN)
+                    o += v;
+                else
+                    dg += (k == ST_DIR) ? (T)1 : (T)-1;
+            }
+        gs = (L.h2 * rhsv + o) / dg;
+    }
+    return ((T)1 - omega) * e0[i] + omega * gs;
+}
+
+template <class T, int TX, int TY>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_smooth_rb(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
+                                                   const T* __restrict__ rhs, const T* __restrict__ ein,
+                                                   T* __restrict__ eout, int first, T omega, int zc) {
+    using G = RB<T, TX, TY>;
+    constexpr int RW = G::RW, QW = G::QW, NE = G::NE, NQ = G::NQ, NT = G::NT;
+    extern __shared__ __align__(16) unsigned char rb_smem[];
+    T* se = reinterpret_cast<T*>(rb_smem);                          // [5][NE]
+    T* sr = se + 5 * NE;                                            // [3][NQ]
+    uint8_t* ss = reinterpret_cast<uint8_t*>(sr + 3 * NQ);          // [5][NE]
+    const int tid = threadIdx.x;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int nxy = nx * ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, nz);
+    if (z0 >= nz) return;
+    // slots: plane p lives in e/state slot (p - z0 + 2) % 5 and rhs slot (p - z0 + 1) % 3
+    auto eslot = [&](int p) { return (p - z0 + 2) % 5; };
+    auto rslot = [&](int p) { return (p - z0 + 1) % 3; };
+
+    T ve[G::KE];
+    uint8_t vs[G::KE];
+    T vr[G::KQ];
+    auto fetch_e = [&](int p) {
+        int gz;
+        const bool okz = axis_ok(p, nz, L.per[2], gz);
+#pragma unroll
+        for (int k = 0; k < G::KE; k++) {
+            const int idx = tid + k * NT;
+            T v = (T)0;
+            uint8_t sv = ST_NEU;
+            if (idx < NE && okz) {
+                const int r = idx / RW, q = idx - r * RW;
+                int gx, gy;
+                if (axis_ok(x0 - 2 + q, nx, L.per[0], gx) && axis_ok(y0 - 2 + r, ny, L.per[1], gy)) {
+                    const int off = gx + nx * gy + nxy * gz;
+                    sv = st[off];
+                    if (!first) v = ein[off];
+                }
+            }
+            ve[k] = v;
+            vs[k] = sv;
+        }
+    };
+    auto store_e = [&](int p) {
+        T* d = se + eslot(p) * NE;
+        uint8_t* ds = ss + eslot(p) * NE;
+#pragma unroll
+        for (int k = 0; k < G::KE; k++) {
+            const int idx = tid + k * NT;
+            if (idx < NE) {
+                d[idx] = ve[k];
+                ds[idx] = vs[k];
+            }
+        }
+    };
+    auto fetch_r = [&](int p) {
+        int gz;
+        const bool okz = axis_ok(p, nz, L.per[2], gz);
+#pragma unroll
+        for (int k = 0; k < G::KQ; k++) {
+            const int idx = tid + k * NT;
+            T v = (T)0;
+            if (idx < NQ && okz) {
+                const int r = idx / QW, q = idx - r * QW;
+                int gx, gy;
+                if (axis_ok(x0 - 1 + q, nx, L.per[0], gx) && axis_ok(y0 - 1 + r, ny, L.per[1], gy))
+                    v = rhs[gx + nx * gy + nxy * gz];
+            }
+            vr[k] = v;
+        }
+    };
+    auto store_r = [&](int p) {
+        T* d = sr + rslot(p) * NQ;
+#pragma unroll
+        for (int k = 0; k < G::KQ; k++) {
+            const int idx = tid + k * NT;
+            if (idx < NQ) d[idx] = vr[k];
+        }
+    };
+
+    // prologue: planes z0-2 .. z0 and the rhs of plane z0-1
+    for (int p = z0 - 2; p <= z0; p++) {
+        fetch_e(p);
+        store_e(p);
+    }
+    fetch_r(z0 - 1);
+    store_r(z0 - 1);
+    __syncthreads();
+
+    // output cells of this thread: 4 consecutive x on one tile row
+    const int orow = tid / (TX / 4), ocol = 4 * (tid % (TX / 4));
+    const int ogy = y0 + orow, ogx = x0 + ocol;
+
+    for (int p = z0 - 1; p <= z1; p++) {
+        if (p + 2 <= z1 + 1) fetch_e(p + 2);
+        if (p + 1 <= z1) fetch_r(p + 1);
+        // red cells of plane p on the tile and its 1-cell ring
+        {
+            const T* em = se + eslot(p - 1) * NE;
+            T* e0 = se + eslot(p) * NE;
+            const T* ep = se + eslot(p + 1) * NE;
+            const uint8_t* sm = ss + eslot(p - 1) * NE;
+            const uint8_t* s0 = ss + eslot(p) * NE;
+            const uint8_t* sp = ss + eslot(p + 1) * NE;
+            const T* rq = sr + rslot(p) * NQ;
+#pragma unroll
+            for (int k = 0; k < G::KR; k++) {
+                const int j = tid + k * NT;
+                if (j < G::NRED) {
+                    const int r1 = j / (QW / 2), h = j - r1 * (QW / 2);
+                    const int gy = y0 - 1 + r1;
+                    const int par = (x0 - 1 + gy + p) & 1;
+                    const int c1 = 2 * h + par;  // red: x + y + z even
+                    const int rr = r1 + 1, cc = c1 + 1;
+                    const uint8_t sv = s0[rr * RW + cc];
+                    if ((sv & ST_KIND) == ST_UNKNOWN) {
+                        const T v = rb_update<T, RW>(L, inv_diag0, omega, em, e0, ep, sm, s0, sp, rr, cc, sv,
+                                                     rq[r1 * QW + c1], x0 - 1 + c1, gy, p);
+                        e0[rr * RW + cc] = v;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // black cells of plane p - 1 on the tile, then the plane's output
+        const int pb = p - 1;
+        if (pb >= z0 && pb < z1 && ogy < ny) {
+            const T* em = se + eslot(pb - 1) * NE;
+            const T* e0 = se + eslot(pb) * NE;
+            const T* ep = se + eslot(pb + 1) * NE;
+            const uint8_t* sm = ss + eslot(pb - 1) * NE;
+            const uint8_t* s0 = ss + eslot(pb) * NE;
+            const uint8_t* sp = ss + eslot(pb + 1) * NE;
+            const T* rq = sr + rslot(pb) * NQ;
+            const int rr = orow + 2;
+            T out[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int cc = ocol + u + 2;
+                const int i = rr * RW + cc;
+                T v = e0[i];
+                const int gx = ogx + u;
+                if (((gx + ogy + pb) & 1) == 1) {
+                    const uint8_t sv = s0[i];
+                    if ((sv & ST_KIND) == ST_UNKNOWN)
+                        v = rb_update<T, RW>(L, inv_diag0, omega, em, e0, ep, sm, s0, sp, rr, cc, sv,
+                                             rq[(orow + 1) * QW + ocol + u + 1], gx, ogy, pb);
+                }
+                out[u] = v;
+            }
+            T* dst = eout + (size_t)nxy * pb + (size_t)nx * ogy + ogx;
+            if (ogx + 4 <= nx && (nx & 3) == 0) {
+                vst(dst, out[0], out[1], out[2], out[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (ogx + u < nx) dst[u] = out[u];
+            }
+        }
+        if (p + 2 <= z1 + 1) store_e(p + 2);
+        if (p + 1 <= z1) store_r(p + 1);
+        __syncthreads();
+    }
+}
+
 // Residual of level l at its unknown cells, restricted to level l+1 as the
 // mean of the 8 children (children that are not unknowns contribute 0).
 template <class T>
@@ -660,21 +1037,59 @@ __global__ void k_zero(T* p, int n) {
     if (i < n) p[i] = (T)0;
 }
 
-// psi += e at unknown cells; the MIXED32 form also refreshes the float copy.
-template <class T>
-__global__ void k_correct(int N, const uint8_t* __restrict__ st0, const T* __restrict__ e, double* __restrict__ psi,
-                          float* __restrict__ psi32) {
+// psi += e at unknown cells (FP64 form).
+__global__ void k_correct(int N, const uint8_t* __restrict__ st0, const double* __restrict__ e,
+                          double* __restrict__ psi) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     if ((st0[c] & ST_KIND) != ST_UNKNOWN) return;
-    const double v = psi[c] + (double)e[c];
-    psi[c] = v;
-    if (psi32) psi32[c] = (float)v;
+    psi[c] += e[c];
 }
 
-__global__ void k_psi32(int N, const double* __restrict__ psi, float* __restrict__ psi32) {
+// psi += e at unknown cells, psi in float-float (MIXED32 form); four cells
+// per thread with 16-byte accesses, the last thread also takes the N % 4
+// tail cells one by one.
+__global__ void k_correct_ff(int N, const uint8_t* __restrict__ st0, const float* __restrict__ e,
+                             float* __restrict__ psi_hi, float* __restrict__ psi_lo) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N4 = N >> 2;
+    if (i == N4 - 1 || (N4 == 0 && i == 0))
+        for (int c = 4 * N4; c < N; c++)
+            if ((st0[c] & ST_KIND) == ST_UNKNOWN) {
+                const ff v = ff_add_f({psi_hi[c], psi_lo[c]}, e[c]);
+                psi_hi[c] = v.hi;
+                psi_lo[c] = v.lo;
+            }
+    if (i >= N4) return;
+    const uchar4 st = reinterpret_cast<const uchar4*>(st0)[i];
+    const float4 ev = reinterpret_cast<const float4*>(e)[i];
+    float4 h = reinterpret_cast<float4*>(psi_hi)[i], l = reinterpret_cast<float4*>(psi_lo)[i];
+    const uint8_t sv[4] = {st.x, st.y, st.z, st.w};
+    const float evv[4] = {ev.x, ev.y, ev.z, ev.w};
+    float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if ((sv[k] & ST_KIND) != ST_UNKNOWN) continue;
+        const ff v = ff_add_f({hv[k], lv[k]}, evv[k]);
+        hv[k] = v.hi;
+        lv[k] = v.lo;
+    }
+    reinterpret_cast<float4*>(psi_hi)[i] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    reinterpret_cast<float4*>(psi_lo)[i] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+}
+
+// MIXED32: psi (float-float) from doubles, and back.
+__global__ void k_split_psi(int N, const double* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < N) psi32[c] = (float)psi[c];
+    if (c >= N) return;
+    const ff v = ff_from_double(src[c]);
+    hi[c] = v.hi;
+    lo[c] = v.lo;
+}
+
+__global__ void k_join_psi(int N, const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ dst) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) dst[c] = (double)hi[c] + (double)lo[c];
 }
 
 // --- EDL field and body force (Sec. 5.6) ---
@@ -773,9 +1188,54 @@ size_t coarse_smem_bytes(const es_ctx* c, size_t tsize) {
     return n * (2 * tsize + 1);
 }
 
-// One V-cycle on level l for A e = rhs (in place on e[l]).  warm != 0
+constexpr int kRbTX = 64, kRbTY = 16;
+
+// Launch shape of the fused sweep: tiles of kRbTX x kRbTY columns, and the z
+// extent cut into chunks so that the blocks fill whole waves of the
+// resident-block capacity; each chunk re-reads three planes and recomputes
+// two red planes, so the cost model is (waves rounded up) x (chunk + 2).
+template <class T>
+dim3 rb_launch_shape(es_ctx* c, const Level<T>& L, int& zc) {
+    using G = RB<T, kRbTX, kRbTY>;
+    const int ti = sizeof(T) == 4 ? 0 : 1;
+    if (c->rb_blocks[ti] == 0) {
+        cudaFuncSetAttribute(k_smooth_rb<T, kRbTX, kRbTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_smooth_rb<T, kRbTX, kRbTY>, G::NT, G::smem) !=
+                cudaSuccess ||
+            b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        c->rb_blocks[ti] = b;
+    }
+    const long long cols = (long long)((L.nx + kRbTX - 1) / kRbTX) * ((L.ny + kRbTY - 1) / kRbTY);
+    const long long cap = (long long)c->rb_blocks[ti] * c->n_sm;
+    double best = 1e300;
+    int best_zc = L.nz;
+    for (int chunks = 1; chunks <= L.nz && chunks <= 64; chunks++) {
+        const int z = (L.nz + chunks - 1) / chunks;
+        const long long nb = cols * ((L.nz + z - 1) / z);
+        const double waves = (double)((nb + cap - 1) / cap);
+        const double cost = waves * (z + 2);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_zc = z;
+        }
+    }
+    zc = best_zc;
+    return dim3((unsigned)((L.nx + kRbTX - 1) / kRbTX), (unsigned)((L.ny + kRbTY - 1) / kRbTY),
+                (unsigned)((L.nz + zc - 1) / zc));
+}
+
+// One V-cycle on level l for A e = rhs (the result in e[l]).  warm != 0
 // (level 0 only): the current iterate is improved instead of starting from
-// zero.
+// zero.  Algorithmic bytes of each launch (for es_profile): a fused sweep
+// reads e, rhs and the state byte and writes e once per cell (e is not read
+// on a zero start); a half sweep reads e and the states of all cells and
+// rhs of half of them and writes half of e (all of e on a zero start);
+// restriction and prolongation read the fine e and rhs (or e twice) and
+// states and touch the coarse level once.
 template <class T>
 cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     Level<T> L = level_desc<T>(c, l);
@@ -791,12 +1251,41 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     const bool vec = (L.nx % 4) == 0;
     constexpr int W = 4;
     dim3 vblk(32, 8), vgrd((L.nx / W + 31) / 32, (L.ny + 7) / 8, L.nz);
+    // (a periodic axis of one cell is its own neighbour: no red-black split)
+    const bool use_rb = c->P.smoother == ES_SMOOTH_FUSED && (!L.per[0] || L.nx >= 2) &&
+                        (!L.per[1] || L.ny >= 2) && (!L.per[2] || L.nz >= 2);
+    int rb_zc = 1;
+    dim3 rb_grid(1, 1, 1);
+    if (use_rb) rb_grid = rb_launch_shape<T>(c, L, rb_zc);
+    const double nl = (double)Nl, ts = (double)sizeof(T);
+    const int* mc = l + 1 < c->L ? c->ln[l + 1] : c->ln[l];
+    const double nc = (double)mc[0] * mc[1] * mc[2];
     auto sweep = [&](int first) {
+        if (use_rb) {
+            ProfScope ps(c, "smooth_fused", l, nl * ((first ? 2.0 : 3.0) * ts + 1.0));
+            T* eo = (T*)c->e2[l];
+            k_smooth_rb<T, kRbTX, kRbTY><<<rb_grid, RB<T, kRbTX, kRbTY>::NT, RB<T, kRbTX, kRbTY>::smem, c->stream>>>(
+                L, inv_diag0, st, rhs, e, eo, first, omega, rb_zc);
+            c->e2[l] = c->e[l];
+            c->e[l] = eo;
+            e = eo;
+            count(c);
+            return;
+        }
+        const double b_first = nl * (1.5 * ts + 1.0), b_half = nl * (2.0 * ts + 1.0);
         if (vec) {
-            k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
+            {
+                ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
+                k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
+            }
+            ProfScope ps(c, "smooth_half", l, b_half);
             k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
         } else {
-            k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, first, omega);
+            {
+                ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
+                k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, first, omega);
+            }
+            ProfScope ps(c, "smooth_half", l, b_half);
             k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
         }
         count(c, 2);
@@ -804,6 +1293,7 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     if (l == c->L - 1) {
         size_t sm = coarse_smem_bytes(c, sizeof(T));
         if (sm <= 200 * 1024) {
+            ProfScope ps(c, "coarse_solve", l, nl * (2.0 * ts + 1.0));
             k_coarse_solve<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
             count(c);
         } else {
@@ -822,6 +1312,9 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     }
     for (int s = 0; s < c->P.nu1; s++) sweep(s == 0 && zero_start);
     const int* m = c->ln[l + 1];
+    const double b_grid = nl * (2.0 * ts + 1.0) + nc * (ts + 1.0);
+    {
+    ProfScope ps_r(c, "restrict", l, b_grid);
     if (vec) {
         dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
         k_restrict_v<T><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, m[0], m[1],
@@ -831,13 +1324,17 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
         k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], c->st[l + 1],
                                                              (T*)c->rhs[l + 1]);
     }
+    }
     count(c);
     cudaError_t err = vcycle_level<T>(c, l + 1, 0);
     if (err != cudaSuccess) return err;
-    if (vec)
-        k_prolong_v<T><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
-    else
-        k_prolong<T><<<full, blk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
+    {
+        ProfScope ps(c, "prolong", l, b_grid);
+        if (vec)
+            k_prolong_v<T><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
+        else
+            k_prolong<T><<<full, blk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
+    }
     count(c);
     for (int s = 0; s < c->P.nu2; s++) sweep(0);
     return cudaGetLastError();
@@ -852,15 +1349,41 @@ void set_coarse_smem(const es_ctx* c) {
 
 }  // namespace
 
+// Algorithmic bytes per cell: psi (8: double, or float-float) and the state
+// byte in, r (8) out.
 cudaError_t launch_outer_residual(es_ctx* c) {
     const double diag0 = 6.0 + c->S.kappa * c->S.kappa;
-    if (mixed(c))
-        k_outer_residual<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-            c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (float*)c->rhs[0], c->r64, c->partial);
-    else
-        k_outer_residual<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-            c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (double*)c->rhs[0], nullptr,
-            c->partial);
+    ProfScope ps(c, "outer_residual", -1, (double)c->g.N * 17.0);
+    if (mixed(c)) {
+        WallFF wall;
+        int mask = 0;
+        for (int f = 0; f < 6; f++) {
+            const ff v = ff_from_double(2.0 * c->S.pot_val[f]);
+            wall.hi[f] = v.hi;
+            wall.lo[f] = v.lo;
+            if (c->S.pot_bc[f] == ES_POT_DIRICHLET) mask |= 1 << f;
+        }
+        const int W = (c->g.nx % 4) == 0 ? 4 : 1;
+        const int gx = (c->g.nx / W + 31) / 32, gy = (c->g.ny + 7) / 8;
+        int gz = kResPartials / (gx * gy);
+        gz = gz < 1 ? 1 : (gz > c->g.nz ? c->g.nz : gz);
+        const dim3 grd(gx, gy, gz), blk(32, 8);
+        if (W == 4)
+            k_outer_residual_ff<4><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
+                                                                c->psi_lo, c->st[0], c->owner, c->kind,
+                                                                (const float2*)c->pbc, mask, (float*)c->rhs[0],
+                                                                c->partial);
+        else
+            k_outer_residual_ff<1><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
+                                                                c->psi_lo, c->st[0], c->owner, c->kind,
+                                                                (const float2*)c->pbc, mask, (float*)c->rhs[0],
+                                                                c->partial);
+        k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
+        count(c, 2);
+        return cudaGetLastError();
+    }
+    k_outer_residual<<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (double*)c->rhs[0], c->partial);
     k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, c->red_blocks, c->d_norm);
     count(c, 2);
     return cudaGetLastError();
@@ -875,45 +1398,42 @@ cudaError_t launch_vcycle(es_ctx* c, int warm) {
     return vcycle_level<double>(c, 0, warm);
 }
 
+// Algorithmic bytes per cell: e (s) and the state byte in, psi (8) in and out.
 cudaError_t launch_correct(es_ctx* c) {
     const int N = (int)c->g.N;
-    const unsigned nb = (unsigned)((N + 255) / 256);
-    if (mixed(c))
-        k_correct<float><<<nb, 256, 0, c->stream>>>(N, c->st[0], (const float*)c->e[0], c->psi, c->psi32);
-    else
-        k_correct<double><<<nb, 256, 0, c->stream>>>(N, c->st[0], (const double*)c->e[0], c->psi, nullptr);
+    ProfScope ps(c, "correct", -1, (double)N * ((mixed(c) ? 4.0 : 8.0) + 1.0 + 16.0));
+    if (mixed(c)) {
+        const int n4 = (N >> 2) > 0 ? (N >> 2) : 1;
+        k_correct_ff<<<(n4 + 255) / 256, 256, 0, c->stream>>>(N, c->st[0], (const float*)c->e[0], c->psi32,
+                                                               c->psi_lo);
+    } else {
+        k_correct<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->st[0], (const double*)c->e[0], c->psi);
+    }
     count(c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_incremental_residual(es_ctx* c, int first) {
-    const float diag0 = (float)(6.0 + c->S.kappa * c->S.kappa);
-    k_incr_residual<<<c->red_blocks, kRedThreads, 0, c->stream>>>(c->g, c->S, diag0, c->st[0], (const float*)c->e[0],
-                                                                   c->r64, (float*)c->rhs[0], c->delta, first,
-                                                                   c->partial);
-    k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, c->red_blocks, c->d_norm);
-    count(c, 2);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fold_delta(es_ctx* c) {
+cudaError_t launch_split_psi(es_ctx* c, const double* src) {
     const int N = (int)c->g.N;
-    k_fold_delta<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->st[0], c->delta, c->psi, c->psi32);
+    k_split_psi<<<(N + 255) / 256, 256, 0, c->stream>>>(N, src, c->psi32, c->psi_lo);
     count(c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_psi32(es_ctx* c) {
-    if (!c->psi32) return cudaSuccess;
+cudaError_t launch_join_psi(es_ctx* c, double* dst) {
     const int N = (int)c->g.N;
-    k_psi32<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->psi, c->psi32);
+    k_join_psi<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->psi32, c->psi_lo, dst);
     count(c);
     return cudaGetLastError();
 }
 
+// Algorithmic bytes per cell: psi as the kernel reads it (float in MIXED32,
+// double in FP64) and the flag byte in, f_b (3 s) out.
 cudaError_t launch_body_force(es_ctx* c) {
     const Grid& g = c->g;
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    const double s = mixed(c) ? 4.0 : 8.0;
+    ProfScope ps(c, "body_force", -1, (double)g.N * (s + 1.0 + 3.0 * s));
     const double* E = c->P.E_ext;
     const double k2e = c->S.kappa * c->S.kappa * c->S.eps;
     if (mixed(c))

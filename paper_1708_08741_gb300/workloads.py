@@ -272,10 +272,11 @@ def suspension_sample(n: int, seed: int = 3, radius: float = 5.0, levels: int = 
 
 
 def mixed_box(dims: Sequence[int] = (40, 24, 32), seed: int = 11, levels: int = 3,
-              n_spheres: int = 4, radius: float = 3.5) -> Workload:
-    """Small mixed test case: walls in z, periodic x/y, zeta and charge spheres,
-    random initial velocities, non-cubic extents that leave ragged thread-block tails."""
-    periodic = (1, 1, 0)
+              n_spheres: int = 4, radius: float = 3.5, periodic: Sequence[int] = (1, 1, 0)) -> Workload:
+    """Small mixed test case: walls in z, periodic x/y (by default), zeta and
+    charge spheres, random initial velocities, non-cubic extents that leave
+    ragged thread-block tails."""
+    periodic = tuple(periodic)
     rng = PCG32(seed)
     centres = place_spheres(n_spheres, radius, dims, periodic, rng)
     kind = np.array([KIND_ZETA if i % 2 == 0 else KIND_CHARGE for i in range(n_spheres)])

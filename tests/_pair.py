@@ -36,10 +36,10 @@ def rel_l2(a, b):
 class Pair:
     """A GPU simulation and an oracle simulation of the same workload."""
 
-    def __init__(self, wl, precision=es.ES_FP64, overrides=None):
+    def __init__(self, wl, precision=es.ES_FP64, overrides=None, lib_overrides=None):
         self.wl = wl
         self.o = oracle.Oracle(wl, overrides)
-        self.g = es.Simulation(wl, precision, overrides=overrides)
+        self.g = es.Simulation(wl, precision, overrides={**(overrides or {}), **(lib_overrides or {})})
 
     def step(self, forced=True):
         self.o.map_particles()

@@ -63,6 +63,7 @@ def _create_rc(lib, wl, **over):
     (dict(precision=7), "precision"),
     (dict(omega=2.0), "omega"),
     (dict(eps=0.0), "eps"),
+    (dict(smoother=2), "smoother"),
 ])
 def test_invalid_parameters_rejected_before_any_gpu_call(lib, over, needle):
     rc, msg = _create_rc(lib, W.single_sphere(), **over)
@@ -81,12 +82,16 @@ def test_invalid_particles_rejected(lib):
 
 def test_device_bytes_matches_layout(lib):
     wl = W.suspension(n=512, n_spheres=1, levels=6)
+    b16 = es.device_bytes(wl, es.ES_MIXED16)
     b32 = es.device_bytes(wl, es.ES_MIXED32)
     b64 = es.device_bytes(wl, es.ES_FP64)
     N = 512 ** 3
-    # two PDF fields dominate: 2 x 19 x s bytes per cell; the rest is the body
-    # force (3s), psi (8; MIXED32 adds a float copy, an FP64 residual and FP32
-    # corrections, 16), owner and flags (5) and two s-byte fields plus a byte
-    # per multigrid cell (x 8/7 levels)
-    assert 2 * 19 * 4 * N < b32 < 2 * 19 * 4 * N + 60 * N
-    assert 2 * 19 * 8 * N < b64 < 2 * 19 * 8 * N + 72 * N
+    # two PDF fields dominate: 2 x 19 x s_pdf bytes per cell; the rest is the
+    # body force (3s), psi (8: FP64 or float-float), owner and flags (5) and
+    # three s-byte fields plus a byte per multigrid cell (x 8/7 levels), with
+    # s the arithmetic type (4 in both reduced forms)
+    rest32 = (3 * 4 + 8 + 5 + (3 * 4 + 1) * 8 / 7) * N
+    rest64 = (3 * 8 + 8 + 5 + (3 * 8 + 1) * 8 / 7) * N
+    assert 2 * 19 * 2 * N + rest32 < b16 < 2 * 19 * 2 * N + rest32 + 0.1 * N
+    assert 2 * 19 * 4 * N + rest32 < b32 < 2 * 19 * 4 * N + rest32 + 0.1 * N
+    assert 2 * 19 * 8 * N + rest64 < b64 < 2 * 19 * 8 * N + rest64 + 0.1 * N

@@ -91,6 +91,23 @@ def test_potential_solve_and_body_force(name):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
+def test_fused_smoother(name):
+    """The red-black sweep run as one fused out-of-place pass instead of the
+    default two in-place passes (one per colour): the same V-cycles, so the
+    same iterates as the oracle."""
+    wl = CASES[name]()
+    p = Pair(wl, lib_overrides=dict(smoother=es.ES_SMOOTH_FUSED))
+    p.o.map_particles()
+    p.g.map_particles()
+    fluid = p.o.owner() < 0
+    for k in (0, 2):
+        io = p.o.solve(forced_cycles=k)
+        ig = p.g.solve(forced_cycles=k)
+        assert abs(ig["r0"] - io["r0"]) <= 1e-12 * io["r0"]
+        assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < FP64_TOL
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
 def test_lbm_step_forces_and_advance(name):
     wl = CASES[name]()
     p = Pair(wl)
@@ -174,6 +191,64 @@ def test_mixed32_within_1e4_after_100_steps(maker):
     assert r["owner_equal"]
     for k in ("psi", "u", "x"):
         assert r[k] < MIXED_TOL, (k, r[k])
+
+
+@pytest.mark.parametrize("name", ["single_sphere", "mixed_ragged", "walls_x42"])
+def test_mixed32_defect_correction_reaches_fp64_tolerance(name):
+    """The MIXED32 outer iteration keeps psi and r = b - A psi in float-float
+    (about 48 bits): with FP32 V-cycles it must still reach a relative
+    tolerance of 1e-12, five decades below FP32 resolution, and land on the
+    oracle's FP64 solution.  (A residual formed in FP32 stalls near 1e-7.)
+    Both sides stop at ||r|| < 1e-12 ||r0||; the potential error this leaves
+    is bounded by cond(A) * 1e-12, cond(A) <= (12 + kappa^2) / kappa^2 < 200
+    here, so the two solutions agree to 1e-9."""
+    if name == "walls_x42":  # nx not a multiple of 4: the scalar residual path
+        wl = W.mixed_box(dims=(42, 24, 32), levels=2, periodic=(0, 1, 0))
+    else:
+        wl = CASES[name]()
+    over = dict(res_rf=1e-12, max_cycles=200)
+    p = Pair(wl, es.ES_MIXED32, over)
+    p.o.map_particles()
+    p.g.map_particles()
+    io = p.o.solve()
+    ig = p.g.solve()
+    assert ig["status"] == es.ES_OK and ig["r"] < ig["tol"]
+    assert abs(ig["r0"] - io["r0"]) <= 1e-6 * io["r0"]
+    fluid = p.o.owner() < 0
+    assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < 1e-9
+
+
+def test_mixed32_potential_round_trip():
+    """MIXED32 stores psi as a float-float pair: a double written with
+    es_set_field comes back to within 2^-47 relative."""
+    wl = W.mixed_box()
+    g = es.Simulation(wl, es.ES_MIXED32)
+    rng = np.random.Generator(np.random.PCG64(11))
+    v = rng.standard_normal(wl.n_cells) * np.exp(rng.uniform(-20.0, 20.0, wl.n_cells))
+    g.set_field(es.FIELD_PSI, v)
+    back = g.field(es.FIELD_PSI).ravel()
+    assert np.all(np.abs(back - v) <= 2.0**-47 * np.abs(v))
+    idx = np.arange(0, wl.n_cells, 7, dtype=np.int64)[:4096]
+    assert np.array_equal(g.gather(es.FIELD_PSI, idx)[0], back[idx])
+
+
+# MIXED16 keeps each population as an FP16 number (unit roundoff 2^-11) of
+# its scaled relative deviation: the stored state is re-rounded every step,
+# which leaves a relative error of order 1e-3 in the slow velocity field.
+# The potential and the particles see the PDFs only through the forces.
+MIXED16_U_TOL = 1e-2
+
+
+@pytest.mark.parametrize("maker", [lambda: W.single_sphere(),
+                                   lambda: W.channel(n=64, n_spheres=8, radius=5.0, levels=4)])
+def test_mixed16_after_100_steps(maker):
+    """FP16 relative-deviation PDF storage (FP32 collision, the MIXED32
+    solver) against the FP64 oracle after 100 steps."""
+    p, r = _coupled(maker(), 100, precision=es.ES_MIXED16, forced=False)
+    print("MIXED16 relative L2 after 100 steps:", {k: r[k] for k in ("psi", "u", "x")})
+    assert r["owner_equal"]
+    assert r["psi"] < MIXED_TOL and r["x"] < MIXED_TOL
+    assert r["u"] < MIXED16_U_TOL
 
 
 def test_overlap_is_reported():
