@@ -20,6 +20,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -42,6 +44,12 @@ def parse_args():
     ap.add_argument("--n", type=int, default=512, help="cells per axis")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer run (default: --steps)")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving mode: a stream of independent runs, MIXED32 continuous batching "
+                         "against FP64 one run at a time")
+    ap.add_argument("--requests", type=int, default=24, help="serving: number of requests")
+    ap.add_argument("--slots", type=int, default=8, help="serving: resident runs (MIXED32 server)")
+    ap.add_argument("--max-run-steps", type=int, default=1000, help="serving: step cap per run")
     ap.add_argument("--smoother", choices=["fused", "two_pass"], default="two_pass",
                     help="execution of a red-black sweep (same arithmetic)")
     return ap.parse_args()
@@ -355,10 +363,56 @@ def ctypes_sizeof_particle(es):
     return ctypes.sizeof(es.Particle)
 
 
+def run_serving(args):
+    """Serving: the same seeded request stream (Poisson arrivals at 20/s,
+    grids log-uniform in [32, 96] per axis, 1-200 spheres of radius 3-8,
+    Debye length 2-8, field 5e-4..3e-3, zeta 0.5-2, periodic) served by the
+    MIXED32 continuous-batching server and by FP64 one run at a time; a run
+    ends when its mean particle velocity changes by < 1e-4 (relative) per 100
+    steps or at the step cap."""
+    import torch
+
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import serving as S
+
+    rank, local, world = rank_info()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    reqs = S.request_stream(args.requests, rate=20.0, seed=5, edge_range=(32, 96))
+    kw = dict(check_every=100, rel_tol=1e-4, max_steps=args.max_run_steps)
+    mixed = S.gpu_server(es.ES_MIXED32, slots=args.slots, device=f"cuda:{local}", **kw)
+    r_mixed = mixed.serve(reqs)
+    fp64 = S.gpu_server(es.ES_FP64, slots=1, device=f"cuda:{local}", **kw)
+    r_fp64 = fp64.serve(reqs)
+    s_m, s_f = S.summarize(r_mixed), S.summarize(r_fp64)
+    # accuracy of the served results: final mean particle velocity against FP64
+    errs = [float(np.linalg.norm(a.v_mean - b.v_mean) / max(np.linalg.norm(b.v_mean), 1e-300))
+            for a, b in zip(r_mixed, r_fp64) if a.steps == b.steps]
+    line = {
+        "metric": "served runs/s and p50/p99 time to steady velocity, MIXED32 continuous batching vs FP64 "
+                  "one run at a time",
+        "value": s_m["runs_per_s"], "unit": "runs/s", "higher_is_better": True, "n_gpus": 1,
+        "mixed32_batched": {**s_m, "slots": args.slots, "peak_resident": mixed.peak_resident},
+        "fp64_one_at_a_time": s_f,
+        "speedup_runs_per_s": s_m["runs_per_s"] / s_f["runs_per_s"],
+        "p99_ratio_fp64_over_mixed": s_f["p99_latency_s"] / s_m["p99_latency_s"],
+        "v_mean_rel_err_vs_fp64": {"max": max(errs) if errs else None, "compared_runs": len(errs)},
+        "data": "synthetic",
+        "config": {"workload": f"{args.requests} requests, Poisson 20/s, grid edges log-uniform [32, 96], "
+                               f"1-200 spheres R 3-8 (<= 5 % solid), lambda_D 2-8, E 5e-4..3e-3, zeta 0.5-2, "
+                               f"periodic; steady at 1e-4 per 100 steps, cap {args.max_run_steps} steps",
+                   "res_rf": 1e-8},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serving:
+        run_serving(args)
     else:
         run_ours(args)
 

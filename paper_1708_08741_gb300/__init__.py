@@ -247,11 +247,14 @@ class Simulation:
             parts = pack_particles(wl.x, wl.v, wl.w, wl.R, wl.kind, wl.zeta, wl.q)
             h = ctypes.c_void_p()
             if torch_memory:
+                # blocks are taken on the context's stream, so that the
+                # caching allocator orders their reuse after its work
                 self.allocator = TorchAllocator(self.device)
-                rc = self.lib.es_create_with_allocator(ctypes.byref(self.params), parts, self.np,
-                                                       ctypes.c_void_p(self.stream.cuda_stream),
-                                                       self.allocator.c_alloc, self.allocator.c_free, None,
-                                                       ctypes.byref(h))
+                with torch.cuda.stream(self.stream):
+                    rc = self.lib.es_create_with_allocator(ctypes.byref(self.params), parts, self.np,
+                                                           ctypes.c_void_p(self.stream.cuda_stream),
+                                                           self.allocator.c_alloc, self.allocator.c_free, None,
+                                                           ctypes.byref(h))
             else:
                 self.allocator = None
                 rc = self.lib.es_create(ctypes.byref(self.params), parts, self.np,

@@ -167,46 +167,147 @@ __device__ __forceinline__ void load_span(const float* p, float (&v)[W], int off
     }
 }
 
+// Warp-cooperative processing of rare cells.  Lane l marks its cells with
+// bit i of `bits` (i < W); the marked cells of the warp are dealt out one per
+// lane (in order of i, then of lane), fn(owner_lane, i) computes each one,
+// and the value lands in buf[owner_lane * W + i] (a per-warp buffer of
+// 32 W floats).  A warp whose near-boundary cells sit at different positions
+// of the lanes' spans thus runs the long boundary code once instead of once
+// per position.  Every lane of the warp must call this.
+template <int W, class V, class Fn>
+__device__ __forceinline__ void warp_rare_cells(unsigned bits, V* buf, Fn&& fn) {
+    const int lane = threadIdx.x & 31;
+    unsigned M[W];
+    int P[W + 1];
+    P[0] = 0;
+#pragma unroll
+    for (int i = 0; i < W; i++) {
+        M[i] = __ballot_sync(0xffffffffu, (bits >> i) & 1u);
+        P[i + 1] = P[i] + __popc(M[i]);
+    }
+    for (int k0 = 0; k0 < P[W]; k0 += 32) {
+        const int k = k0 + lane;
+        if (k < P[W]) {
+            int i = 0, pi = 0;
+            unsigned mi = M[0];
+#pragma unroll
+            for (int j = 1; j < W; j++)
+                if (k >= P[j]) {
+                    i = j;
+                    pi = P[j];
+                    mi = M[j];
+                }
+            const int owner = (int)__fns(mi, 0, k - pi + 1);
+            buf[owner * W + i] = fn(owner, i);
+        }
+    }
+    __syncwarp();
+}
+
+// Float-float residual at one near-boundary unknown cell, from global
+// memory: faces to unknown cells add the neighbour's psi, faces to sphere
+// cells add the sphere's boundary value (b) and move the diagonal by +1
+// (Dirichlet) or -1 (Neumann), as read from the neighbour's state byte;
+// faces beyond a non-periodic wall do the same with the wall's condition.
+__device__ __forceinline__ float near_residual_ff(const Grid& g, ff diag0, const WallFF& wall, int pot_dir_mask,
+                                                  const float* __restrict__ psi_hi,
+                                                  const float* __restrict__ psi_lo,
+                                                  const uint8_t* __restrict__ st0,
+                                                  const int32_t* __restrict__ owner,
+                                                  const float2* __restrict__ pbc, int x, int y, int z) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int c = x + nx * (y + ny * z);
+    HiSum hs = {0.0f, 0.0f};
+    float lo = 0.0f;
+    int dk = 0;
+    const int g3[3] = {x, y, z}, n3[3] = {nx, ny, nz}, stride[3] = {1, nx, nx * ny};
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const int ax = k >> 1, side = (k & 1) ? 1 : -1;
+        int q = g3[ax] + side;
+        if (q < 0 || q >= n3[ax]) {
+            if (!g.per[ax]) {
+                const int face = 2 * ax + (side > 0 ? 1 : 0);
+                if ((pot_dir_mask >> face) & 1) {
+                    dk += 1;
+                    hs.add(wall.hi[face]);
+                    lo = __fadd_rn(lo, wall.lo[face]);
+                } else {
+                    dk -= 1;
+                }
+                continue;
+            }
+            q = q < 0 ? q + n3[ax] : q - n3[ax];
+        }
+        const int nb = c + (q - g3[ax]) * stride[ax];
+        const uint8_t kk = st0[nb] & ST_KIND;
+        if (kk == ST_UNKNOWN) {
+            hs.add(psi_hi[nb]);
+            lo = __fadd_rn(lo, psi_lo[nb]);
+        } else {
+            dk += kk == ST_DIR ? 1 : -1;
+            const float2 bv = pbc[owner[nb]];
+            hs.add(bv.x);
+            lo = __fadd_rn(lo, bv.y);
+        }
+    }
+    const ff dg = ff_add_f(diag0, (float)dk);
+    const float hc = psi_hi[c], lc = psi_lo[c];
+    const float p = __fmul_rn(dg.hi, hc);
+    float t = __fmaf_rn(dg.hi, hc, -p);
+    t = __fmaf_rn(dg.hi, lc, t);
+    t = __fmaf_rn(dg.lo, hc, t);
+    hs.add(-p);
+    lo = __fsub_rn(lo, t);
+    return __fadd_rn(hs.s, __fadd_rn(hs.e, lo));
+}
+
 template <int W>
 __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, WallFF wall,
                                                            const float* __restrict__ psi_hi,
                                                            const float* __restrict__ psi_lo,
                                                            const uint8_t* __restrict__ st0,
                                                            const int32_t* __restrict__ owner,
-                                                           const int* __restrict__ kind,
                                                            const float2* __restrict__ pbc, int pot_dir_mask,
                                                            float* __restrict__ r_out,
                                                            double* __restrict__ partial) {
-    __shared__ double sh[32];
+    __shared__ float sbuf[8][32 * W];
+    __shared__ float swarp[8];
     float acc = 0.0f;
-    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = g.nx * g.ny;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int xs = W * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y;
-    const bool active = xs < nx && y < ny;
+    const bool lane_on = xs < nx;
     int ym = 0, yp = 0, xl = 0, xr = 0;
     bool okym = false, okyp = false, okxl = false, okxr = false;
-    if (active) {
+    if (y < ny) {
         okym = wrap_axis(y - 1, ny, g.per[1], ym);
         okyp = wrap_axis(y + 1, ny, g.per[1], yp);
         okxl = wrap_axis(xs - 1, nx, g.per[0], xl);
         okxr = wrap_axis(xs + W, nx, g.per[0], xr);
     }
-    for (int z = blockIdx.z; z < nz && active; z += gridDim.z) {
+    float* buf = sbuf[threadIdx.y];
+    // y is the same for the 32 lanes of a warp, so the loop is warp-uniform
+    for (int z = blockIdx.z; z < nz && y < ny; z += gridDim.z) {
         const int row = nx * (y + ny * z);
         int zm = 0, zp = 0;
         const bool okzm = wrap_axis(z - 1, nz, g.per[2], zm), okzp = wrap_axis(z + 1, nz, g.per[2], zp);
         uint8_t sv[W];
+        unsigned near_bits = 0;
         bool any = false;
 #pragma unroll
         for (int i = 0; i < W; i++) {
-            sv[i] = st0[row + xs + i];
-            any |= (sv[i] & ST_KIND) == ST_UNKNOWN;
+            sv[i] = lane_on ? st0[row + xs + i] : (uint8_t)ST_NEU;
+            const bool unk = (sv[i] & ST_KIND) == ST_UNKNOWN;
+            any |= unk && !(sv[i] & ST_NEAR);
+            if (unk && (sv[i] & ST_NEAR)) near_bits |= 1u << i;
         }
         float out[W];
 #pragma unroll
         for (int i = 0; i < W; i++) out[i] = 0.0f;
         if (any) {
-            // x row with one neighbour each side, and the four neighbour rows
+            // interior cells: the x row with one neighbour each side, and the
+            // four neighbour rows, in registers
             float ch[W + 2], cl[W + 2], ah[W], al[W], bh[W], bl[W], dh[W], dl[W], fh[W], fl[W];
 #pragma unroll
             for (int i = 0; i < W; i++) ah[i] = al[i] = bh[i] = bl[i] = dh[i] = dl[i] = fh[i] = fl[i] = 0.0f;
@@ -248,83 +349,57 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
             }
 #pragma unroll
             for (int i = 0; i < W; i++) {
-                if ((sv[i] & ST_KIND) != ST_UNKNOWN) continue;
+                if ((sv[i] & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
                 const float hc = ch[i + 1], lc = cl[i + 1];
                 HiSum hs = {0.0f, 0.0f};
-                float lo;
-                ff dg = diag0;
-                if (!(sv[i] & ST_NEAR)) {
-                    hs.add(ch[i]);
-                    hs.add(ch[i + 2]);
-                    hs.add(ah[i]);
-                    hs.add(bh[i]);
-                    hs.add(dh[i]);
-                    hs.add(fh[i]);
-                    lo = __fadd_rn(__fadd_rn(__fadd_rn(cl[i], cl[i + 2]), __fadd_rn(al[i], bl[i])),
-                                   __fadd_rn(dl[i], fl[i]));
-                } else {
-                    lo = 0.0f;
-                    int dk = 0;
-                    const int gx = xs + i;
-                    const int g3[3] = {gx, y, z}, n3[3] = {nx, ny, nz};
-                    const float nh[6] = {ch[i], ch[i + 2], ah[i], bh[i], dh[i], fh[i]};
-                    const float nl[6] = {cl[i], cl[i + 2], al[i], bl[i], dl[i], fl[i]};
-                    const int nbr[6] = {row + (gx == 0 ? xl : gx - 1), row + (gx == nx - 1 ? xr : gx + 1),
-                                        rym + gx, ryp + gx, rzm + gx, rzp + gx};
-#pragma unroll
-                    for (int k = 0; k < 6; k++) {
-                        const int ax = k >> 1, side = (k & 1) ? 1 : -1;
-                        const int q = g3[ax] + side;
-                        if ((q < 0 || q >= n3[ax]) && !g.per[ax]) {
-                            const int face = 2 * ax + (side > 0 ? 1 : 0);
-                            if ((pot_dir_mask >> face) & 1) {
-                                dk += 1;
-                                hs.add(wall.hi[face]);
-                                lo = __fadd_rn(lo, wall.lo[face]);
-                            } else {
-                                dk -= 1;
-                            }
-                            continue;
-                        }
-                        const int ow = owner[nbr[k]];
-                        if (ow < 0) {
-                            hs.add(nh[k]);
-                            lo = __fadd_rn(lo, nl[k]);
-                        } else {
-                            dk += kind[ow] == ES_KIND_ZETA ? 1 : -1;
-                            const float2 bv = pbc[ow];
-                            hs.add(bv.x);
-                            lo = __fadd_rn(lo, bv.y);
-                        }
-                    }
-                    dg = ff_add_f(diag0, (float)dk);
-                }
+                hs.add(ch[i]);
+                hs.add(ch[i + 2]);
+                hs.add(ah[i]);
+                hs.add(bh[i]);
+                hs.add(dh[i]);
+                hs.add(fh[i]);
+                float lo = __fadd_rn(__fadd_rn(__fadd_rn(cl[i], cl[i + 2]), __fadd_rn(al[i], bl[i])),
+                                     __fadd_rn(dl[i], fl[i]));
                 // - diag * psi_c: high product split exactly, low terms to lo
-                const float p = __fmul_rn(dg.hi, hc);
-                float t = __fmaf_rn(dg.hi, hc, -p);
-                t = __fmaf_rn(dg.hi, lc, t);
-                t = __fmaf_rn(dg.lo, hc, t);
+                const float p = __fmul_rn(diag0.hi, hc);
+                float t = __fmaf_rn(diag0.hi, hc, -p);
+                t = __fmaf_rn(diag0.hi, lc, t);
+                t = __fmaf_rn(diag0.lo, hc, t);
                 hs.add(-p);
                 lo = __fsub_rn(lo, t);
-                const float r = __fadd_rn(hs.s, __fadd_rn(hs.e, lo));
-                out[i] = r;
-                acc = __fmaf_rn(r, r, acc);
+                out[i] = __fadd_rn(hs.s, __fadd_rn(hs.e, lo));
             }
         }
-        if constexpr (W == 4) {
-            *reinterpret_cast<float4*>(r_out + row + xs) = make_float4(out[0], out[1], out[2], out[3]);
-        } else {
-            r_out[row + xs] = out[0];
+        if (__any_sync(0xffffffffu, near_bits != 0)) {
+            const int xw = W * (blockIdx.x * 32);
+            warp_rare_cells<W>(near_bits, buf, [&](int ln, int i) {
+                return near_residual_ff(g, diag0, wall, pot_dir_mask, psi_hi, psi_lo, st0, owner, pbc,
+                                        xw + W * ln + i, y, z);
+            });
+#pragma unroll
+            for (int i = 0; i < W; i++)
+                if ((near_bits >> i) & 1u) out[i] = buf[(threadIdx.x & 31) * W + i];
+            __syncwarp();
+        }
+#pragma unroll
+        for (int i = 0; i < W; i++) acc = __fmaf_rn(out[i], out[i], acc);
+        if (lane_on) {
+            if constexpr (W == 4) {
+                *reinterpret_cast<float4*>(r_out + row + xs) = make_float4(out[0], out[1], out[2], out[3]);
+            } else {
+                r_out[row + xs] = out[0];
+            }
         }
     }
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    double v = (double)acc;
+    // per-block partial: float within the block (a few thousand terms), one
+    // double per block
+    float v = acc;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    if (threadIdx.x == 0) swarp[threadIdx.y] = v;
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
         double tot = 0.0;
-        for (int w = 0; w < 8; w++) tot += sh[w];
+        for (int w = 0; w < 8; w++) tot += (double)swarp[w];
         partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
     }
 }
@@ -444,64 +519,47 @@ __device__ __forceinline__ void vst(double* p, double a, double b, double c, dou
         arr[(off) + 3] = q_.v3;    \
     } while (0)
 
-// The update of the 4 cells xs + P0 + 2j of a span (indices known at compile
-// time, so the span arrays stay in registers).
+// The update of the interior cells xs + P0 + 2j of a span (indices known at
+// compile time, so the span arrays stay in registers); the near-boundary
+// cells of the colour are only marked in near_bits (bit = span position).
 template <class T, int P0, int W>
-__device__ __forceinline__ void span_update(const Level<T>& L, T inv_diag0, const uint8_t* __restrict__ st,
-                                            T (&c)[W + 8], const T (&a)[W], const T (&b)[W], const T (&d)[W],
-                                            const T (&f)[W], const T (&r)[W], uint2 sw, int xs, int y, int z, int row,
-                                            int rym, int ryp, int rzm, int rzp, int first, T omega) {
+__device__ __forceinline__ void span_update(const Level<T>& L, T inv_diag0, T (&c)[W + 8], const T (&a)[W],
+                                            const T (&b)[W], const T (&d)[W], const T (&f)[W], const T (&r)[W],
+                                            uint2 sw, int first, T omega, unsigned& near_bits) {
 #pragma unroll
     for (int j = 0; j < W / 2; j++) {
         const int i = P0 + 2 * j;
         const uint8_t sv = (uint8_t)(((i < 4 ? sw.x : sw.y) >> (8 * (i & 3))) & 0xFF);
         if ((sv & ST_KIND) != ST_UNKNOWN) continue;
-        T gs;
-        if (!(sv & ST_NEAR)) {
-            T o = c[i + 3];
-            o += c[i + 5];
-            o += a[i];
-            o += b[i];
-            o += d[i];
-            o += f[i];
-            gs = (L.h2 * r[i] + o) * inv_diag0;
-        } else {
-            T dg = L.diag0, o = (T)0;
-            const int gx = xs + i;
-            const int g3[3] = {gx, y, z}, n3[3] = {L.nx, L.ny, L.nz};
-#pragma unroll
-            for (int ax = 0; ax < 3; ax++)
-#pragma unroll
-                for (int side = -1; side <= 1; side += 2) {
-                    const int q = g3[ax] + side;
-                    if ((q < 0 || q >= n3[ax]) && !L.per[ax]) {
-                        dg += (L.pot_bc[2 * ax + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? (T)1 : (T)-1;
-                        continue;
-                    }
-                    int nb;
-                    T v;
-                    if (ax == 0) {
-                        int wx;
-                        wrap_axis(q, L.nx, L.per[0], wx);
-                        nb = row + wx;
-                        v = c[i + 4 + side];
-                    } else if (ax == 1) {
-                        nb = (side < 0 ? rym : ryp) + gx;
-                        v = side < 0 ? a[i] : b[i];
-                    } else {
-                        nb = (side < 0 ? rzm : rzp) + gx;
-                        v = side < 0 ? d[i] : f[i];
-                    }
-                    const uint8_t kk = st[nb] & ST_KIND;
-                    if (kk == ST_UNKNOWN)
-                        o += v;
-                    else
-                        dg += (kk == ST_DIR) ? (T)1 : (T)-1;
-                }
-            gs = (L.h2 * r[i] + o) / dg;
+        if (sv & ST_NEAR) {
+            near_bits |= 1u << i;
+            continue;
         }
+        T o = c[i + 3];
+        o += c[i + 5];
+        o += a[i];
+        o += b[i];
+        o += d[i];
+        o += f[i];
+        const T gs = (L.h2 * r[i] + o) * inv_diag0;
         c[i + 4] = first ? omega * gs : ((T)1 - omega) * c[i + 4] + omega * gs;
     }
+}
+
+// Gauss-Seidel value of one near-boundary unknown cell of level l, read
+// from global memory (the boundary faces per Sec. 5.4 as level_stencil).
+template <class T>
+__device__ __forceinline__ T near_gs(const Level<T>& L, const uint8_t* __restrict__ st, const T* __restrict__ rhs,
+                                     const T* e, int x, int y, int z, int first, T omega) {
+    const int cidx = x + L.nx * (y + L.ny * z);
+    const uint8_t s = st[cidx];
+    T diag, off;
+    if (first)
+        level_stencil<T, false>(L, st, e, x, y, z, s, diag, off);
+    else
+        level_stencil<T, true>(L, st, e, x, y, z, s, diag, off);
+    const T gs = (L.h2 * rhs[cidx] + off) / diag;
+    return first ? omega * gs : ((T)1 - omega) * e[cidx] + omega * gs;
 }
 
 // One red (colour 0) or black (1) half sweep with W-cell spans (W = 4 or 8):
@@ -516,9 +574,12 @@ template <class T, int W>
 __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
                                                   const T* __restrict__ rhs, T* __restrict__ e, int colour,
                                                   int first, T omega) {
-    const int xs = W * (blockIdx.x * 32 + threadIdx.x);
+    __shared__ T sbuf[8][32 * W];
+    const int x_warp = W * (blockIdx.x * 32);
+    const int xs = x_warp + W * threadIdx.x;
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
-    if (xs >= L.nx || y >= L.ny) return;
+    if (y >= L.ny) return;  // whole warps (a warp is one row)
+    const bool lane_on = xs < L.nx;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int row = nx * (y + ny * z);
     int ym, yp, zm, zp, xl, xr;
@@ -532,63 +593,49 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
     for (int i = 0; i < W + 8; i++) c[i] = (T)0;
 #pragma unroll
     for (int i = 0; i < W; i++) a[i] = b[i] = d[i] = f[i] = (T)0;
-    if (!first) {
-        if (okxl) ES_VLD(c, 0, e + row + xl);
+    uint2 sw = make_uint2(0x02020202u, 0x02020202u);  // (Neumann: nothing to update)
+    if (lane_on) {
+        if (!first) {
+            if (okxl) ES_VLD(c, 0, e + row + xl);
 #pragma unroll
-        for (int v = 0; v < W; v += 4) {
-            ES_VLD(c, 4 + v, e + row + xs + v);
-            if (okym) ES_VLD(a, v, e + rym + xs + v);
-            if (okyp) ES_VLD(b, v, e + ryp + xs + v);
-            if (okzm) ES_VLD(d, v, e + rzm + xs + v);
-            if (okzp) ES_VLD(f, v, e + rzp + xs + v);
+            for (int v = 0; v < W; v += 4) {
+                ES_VLD(c, 4 + v, e + row + xs + v);
+                if (okym) ES_VLD(a, v, e + rym + xs + v);
+                if (okyp) ES_VLD(b, v, e + ryp + xs + v);
+                if (okzm) ES_VLD(d, v, e + rzm + xs + v);
+                if (okzp) ES_VLD(f, v, e + rzp + xs + v);
+            }
+            if (okxr) ES_VLD(c, W + 4, e + row + xr);
         }
-        if (okxr) ES_VLD(c, W + 4, e + row + xr);
-    }
 #pragma unroll
-    for (int v = 0; v < W; v += 4) ES_VLD(r, v, rhs + row + xs + v);
-    uint2 sw;
-    if (W == 8) {
-        sw = *reinterpret_cast<const uint2*>(st + row + xs);
-    } else {
-        sw.x = *reinterpret_cast<const unsigned*>(st + row + xs);
-        sw.y = 0;
+        for (int v = 0; v < W; v += 4) ES_VLD(r, v, rhs + row + xs + v);
+        if (W == 8) {
+            sw = *reinterpret_cast<const uint2*>(st + row + xs);
+        } else {
+            sw.x = *reinterpret_cast<const unsigned*>(st + row + xs);
+        }
     }
     const int p0 = (colour + y + z) & 1;  // xs is even: cells xs + p0 + 2j have the colour
+    unsigned near_bits = 0;
     if (p0 == 0)
-        span_update<T, 0, W>(L, inv_diag0, st, c, a, b, d, f, r, sw, xs, y, z, row, rym, ryp, rzm, rzp, first, omega);
+        span_update<T, 0, W>(L, inv_diag0, c, a, b, d, f, r, sw, first, omega, near_bits);
     else
-        span_update<T, 1, W>(L, inv_diag0, st, c, a, b, d, f, r, sw, xs, y, z, row, rym, ryp, rzm, rzp, first, omega);
+        span_update<T, 1, W>(L, inv_diag0, c, a, b, d, f, r, sw, first, omega, near_bits);
+    // near-boundary cells of the colour: dealt out over the warp's lanes
+    if (__any_sync(0xffffffffu, near_bits != 0)) {
+        T* buf = sbuf[threadIdx.y];
+        warp_rare_cells<W>(near_bits, buf, [&](int ln, int i) {
+            return near_gs<T>(L, st, rhs, e, x_warp + W * ln + i, y, z, first, omega);
+        });
 #pragma unroll
-    for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[4 + v], c[5 + v], c[6 + v], c[7 + v]);
+        for (int i = 0; i < W; i++)
+            if ((near_bits >> i) & 1u) c[i + 4] = buf[threadIdx.x * W + i];
+    }
+    if (lane_on) {
+#pragma unroll
+        for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[4 + v], c[5 + v], c[6 + v], c[7 + v]);
+    }
 }
-
-// ---- fused red-black sweep ----
-//
-// One full Gauss-Seidel sweep (red half, then black half) in a single pass
-// over the level, out of place (ein -> eout).  A block owns a TX x TY tile of
-// (x, y) and a chunk of z planes and marches up z with a 5-plane ring in
-// shared memory: at plane p it updates the red cells of plane p on the tile
-// plus a one-cell ring, then the black cells of plane p - 1 on the tile
-// (all of whose red neighbours are final by then), and writes plane p - 1.
-// The ring of red cells is recomputed by the neighbouring tiles as well
-// (overlapped tiling), so blocks never wait on one another; every value a
-// block reads comes from ein, which no block writes.  Per cell and sweep
-// the level moves e in and out once, plus rhs and the state byte: half the
-// traffic of two in-place half sweeps.  The per-cell arithmetic is that of
-// k_smooth_v.  Planes are fetched two ahead into registers so the loads of
-// plane p + 2 overlap the updates of planes p and p - 1.
-template <class T, int TX, int TY>
-struct RB {
-    static constexpr int RW = TX + 4, RH = TY + 4;  // tile + 2-cell ring (e, states)
-    static constexpr int QW = TX + 2, QH = TY + 2;  // tile + 1-cell ring (red cells, rhs)
-    static constexpr int NE = RW * RH, NQ = QW * QH;
-    static constexpr int NT = 256;
-    static constexpr int KE = (NE + NT - 1) / NT, KQ = (NQ + NT - 1) / NT;
-    static constexpr int NRED = QH * (QW / 2);
-    static constexpr int KR = (NRED + NT - 1) / NT;
-    static constexpr size_t smem = (size_t)(5 * NE + 3 * NQ) * sizeof(T) + 5 * NE;
-    static_assert(TX % 4 == 0 && (TX / 4) * TY == NT, "one thread per 4 output cells");
-};
 
 __device__ __forceinline__ bool axis_ok(int v, int n, int per, int& w) {
     if (v >= 0 && v < n) {
@@ -601,223 +648,286 @@ __device__ __forceinline__ bool axis_ok(int v, int n, int per, int& w) {
     return true;
 }
 
-// Gauss-Seidel value of one unknown cell from the shared-memory ring.
-// (rr, cc): position in the RH x RW ring; em, e0, ep: planes z-1, z, z+1;
-// sm, s0, sp: their states; g*: unwrapped global coordinates.
-template <class T, int RW>
-__device__ __forceinline__ T rb_update(const Level<T>& L, T inv_diag0, T omega, const T* em, const T* e0,
-                                       const T* ep, const uint8_t* sm, const uint8_t* s0, const uint8_t* sp,
-                                       int rr, int cc, uint8_t sv, T rhsv, int gx, int gy, int gz) {
-    const int i = rr * RW + cc;
-    T gs;
-    if (!(sv & ST_NEAR)) {
-        T o = e0[i - 1];
-        o += e0[i + 1];
-        o += e0[i - RW];
-        o += e0[i + RW];
-        o += em[i];
-        o += ep[i];
-        gs = (L.h2 * rhsv + o) * inv_diag0;
-    } else {
-        T dg = L.diag0, o = (T)0;
-        const int g3[3] = {gx, gy, gz}, n3[3] = {L.nx, L.ny, L.nz};
+// ---- fused red-black sweep, span form ----
+//
+// One full Gauss-Seidel sweep (red half, then black half) in a single pass
+// over the level, out of place (ein -> eout; no block writes what another
+// reads, so blocks never wait on one another).  A block marches up z: at
+// plane p it updates the red cells of plane p on its tile plus a one-cell
+// ring, then the black cells of plane p - 1 on the tile (all of whose red
+// neighbours are final by then), and writes plane p - 1.  Per cell and sweep
+// the level moves e in and out once, plus rhs and the state byte: half the
+// traffic of two in-place half sweeps.  Layout as in the vector smoother: lane l of row-warp w owns the 4-cell span x0 + 4l .. +3
+// of row y0 - 2 + w, so a block covers 128 x cells and 16 rows, of which
+// rows 2..13 are written (rows 1 and 14 get red updates only, rows 0 and 15
+// are loaded only).  Planes stream into a 7-slot shared-memory ring with
+// cp.async, three planes ahead; the x neighbours just outside the tile
+// (x0 - 1 and x0 + 128) are updated by a 17th "ring" warp, one lane per row
+// and side.  Interior cells use 16-byte shared loads; near-boundary cells
+// read the neighbour states from the ring as well.  Requires nx % 128 == 0.
+constexpr int kRbRows = 16, kRbOut = 12, kRbSpans = 34, kRbSlots = 7;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(pred ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool pred) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(pred ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::); }
+
+template <class T>
+struct RB2 {
+    using Span = T[4];
+    static constexpr size_t e_bytes = (size_t)kRbSlots * kRbRows * kRbSpans * 4 * sizeof(T);
+    static constexpr size_t s_bytes = (size_t)kRbSlots * kRbRows * kRbSpans * 4;
+    static constexpr size_t smem = e_bytes + s_bytes;
+};
+
+// Gauss-Seidel value of one cell from the shared-memory ring, any stencil:
+// jc, jm, jp index the cell in the slots of planes z, z - 1, z + 1 (the
+// state of element j is byte j & 3 of word j >> 2 of the state ring); bit f
+// of `wall` marks face f (x-, x+, y-, y+, z-, z+) as beyond a non-periodic
+// boundary, where the face condition of the potential applies instead.
+template <class T>
+__device__ __forceinline__ T rb2_near(const Level<T>& L, T omega, const T* __restrict__ E,
+                                      const unsigned* __restrict__ S, int jc, int jm, int jp, T rhsv,
+                                      unsigned wall) {
+    constexpr int ROW = kRbSpans * 4;
+    const int nb[6] = {jc - 1, jc + 1, jc - ROW, jc + ROW, jm, jp};
+    T dg = L.diag0, o = (T)0;
 #pragma unroll
-        for (int ax = 0; ax < 3; ax++)
-#pragma unroll
-            for (int side = -1; side <= 1; side += 2) {
-                const int q = g3[ax] + side;
-                if ((q < 0 || q >= n3[ax]) && !L.per[ax]) {
-                    dg += (L.pot_bc[2 * ax + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? (T)1 : (T)-1;
-                    continue;
-                }
-                uint8_t k;
-                T v;
-                if (ax == 0) {
-                    k = s0[i + side];
-                    v = e0[i + side];
-                } else if (ax == 1) {
-                    k = s0[i + side * RW];
-                    v = e0[i + side * RW];
-                } else {
-                    k = side < 0 ? sm[i] : sp[i];
-                    v = side < 0 ? em[i] : ep[i];
-                }
-                k &= ST_KIND;
-                if (k == ST_UNKNOWN)
-                    o += v;
-                else
-                    dg += (k == ST_DIR) ? (T)1 : (T)-1;
-            }
-        gs = (L.h2 * rhsv + o) / dg;
+    for (int f = 0; f < 6; f++) {
+        if ((wall >> f) & 1u) {
+            dg += (L.pot_bc[f] == ES_POT_DIRICHLET) ? (T)1 : (T)-1;
+            continue;
+        }
+        const int j = nb[f];
+        const unsigned kind = (S[j >> 2] >> ((j & 3) << 3)) & ST_KIND;
+        if (kind == ST_UNKNOWN)
+            o += E[j];
+        else
+            dg += (kind == ST_DIR) ? (T)1 : (T)-1;
     }
-    return ((T)1 - omega) * e0[i] + omega * gs;
+    const T gs = (L.h2 * rhsv + o) / dg;
+    return ((T)1 - omega) * E[jc] + omega * gs;
 }
 
-template <class T, int TX, int TY>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_smooth_rb(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
-                                                   const T* __restrict__ rhs, const T* __restrict__ ein,
-                                                   T* __restrict__ eout, int first, T omega, int zc) {
-    using G = RB<T, TX, TY>;
-    constexpr int RW = G::RW, QW = G::QW, NE = G::NE, NQ = G::NQ, NT = G::NT;
-    extern __shared__ __align__(16) unsigned char rb_smem[];
-    T* se = reinterpret_cast<T*>(rb_smem);                          // [5][NE]
-    T* sr = se + 5 * NE;                                            // [3][NQ]
-    uint8_t* ss = reinterpret_cast<uint8_t*>(sr + 3 * NQ);          // [5][NE]
-    const int tid = threadIdx.x;
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int nxy = nx * ny;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(z0 + zc, nz);
-    if (z0 >= nz) return;
-    // slots: plane p lives in e/state slot (p - z0 + 2) % 5 and rhs slot (p - z0 + 1) % 3
-    auto eslot = [&](int p) { return (p - z0 + 2) % 5; };
-    auto rslot = [&](int p) { return (p - z0 + 1) % 3; };
+// Faces of cell (gx, gy, gz) that lie beyond a non-periodic boundary.
+template <class T>
+__device__ __forceinline__ unsigned wall_faces(const Level<T>& L, int gx, int gy, int gz) {
+    unsigned m = 0;
+    if (!L.per[0]) m |= (gx == 0 ? 1u : 0u) | (gx == L.nx - 1 ? 2u : 0u);
+    if (!L.per[1]) m |= (gy == 0 ? 4u : 0u) | (gy == L.ny - 1 ? 8u : 0u);
+    if (!L.per[2]) m |= (gz == 0 ? 16u : 0u) | (gz == L.nz - 1 ? 32u : 0u);
+    return m;
+}
 
-    T ve[G::KE];
-    uint8_t vs[G::KE];
-    T vr[G::KQ];
-    auto fetch_e = [&](int p) {
-        int gz;
-        const bool okz = axis_ok(p, nz, L.per[2], gz);
+template <class T>
+__global__ void __launch_bounds__(32 * (kRbRows + 1), sizeof(T) == 4 ? 2 : 1) k_smooth_rb2(Level<T> L, T inv_diag0,
+                                                                  const uint8_t* __restrict__ st,
+                                                                  const T* __restrict__ rhs,
+                                                                  const T* __restrict__ ein, T* __restrict__ eout,
+                                                                  int first, T omega, int zc) {
+    extern __shared__ __align__(16) unsigned char rb2_smem[];
+    __shared__ T sbuf[kRbRows][32 * 4];
+    constexpr int SE = kRbRows * kRbSpans * 4;  // elements of one plane slot
+    constexpr int SS = kRbRows * kRbSpans;      // state words of one plane slot
+    constexpr int ROW = kRbSpans * 4;           // elements of one ring row
+    T* E = reinterpret_cast<T*>(rb2_smem);
+    unsigned* S = reinterpret_cast<unsigned*>(rb2_smem + RB2<T>::e_bytes);
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const bool ring = w == kRbRows;
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nxy = nx * ny;
+    const int x0 = blockIdx.x * 128, y0 = blockIdx.y * kRbOut;
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
+    // what this thread loads: a row warp its span of row w, the ring warp the
+    // left (lanes 0-15) or right ring span of row lane % 16
+    const int lrow = ring ? (lane & 15) : w;
+    const int lspan = ring ? ((lane >> 4) ? kRbSpans - 1 : 0) : lane + 1;
+    const int lidx = lrow * kRbSpans + lspan;
+    int gy_l = 0, gx_l = 0;
+    const bool xy_ok = axis_ok(y0 - 2 + lrow, ny, L.per[1], gy_l) && axis_ok(x0 - 4 + 4 * lspan, nx, L.per[0], gx_l);
+    const int goff = gx_l + nx * gy_l;
+    auto wrap7 = [](int v) { return v >= kRbSlots ? v - kRbSlots : (v < 0 ? v + kRbSlots : v); };
+    auto plane = [&](int p, int& gz) { return axis_ok(p, nz, L.per[2], gz); };
+    auto issue = [&](int p, int sl) {
+        int gz = 0;
+        const bool ok = xy_ok && p <= z1 + 1 && plane(p, gz);
+        const int off = ok ? goff + nxy * gz : 0;
+        T* de = E + sl * SE + lidx * 4;
 #pragma unroll
-        for (int k = 0; k < G::KE; k++) {
-            const int idx = tid + k * NT;
-            T v = (T)0;
-            uint8_t sv = ST_NEU;
-            if (idx < NE && okz) {
-                const int r = idx / RW, q = idx - r * RW;
-                int gx, gy;
-                if (axis_ok(x0 - 2 + q, nx, L.per[0], gx) && axis_ok(y0 - 2 + r, ny, L.per[1], gy)) {
-                    const int off = gx + nx * gy + nxy * gz;
-                    sv = st[off];
-                    if (!first) v = ein[off];
-                }
-            }
-            ve[k] = v;
-            vs[k] = sv;
+        for (int h = 0; h < (int)(4 * sizeof(T) / 16); h++)
+            cp_async16(reinterpret_cast<unsigned char*>(de) + 16 * h,
+                       reinterpret_cast<const unsigned char*>(ein + off) + 16 * h, ok && !first);
+        cp_async4(S + sl * SS + lidx, st + off, ok);
+        cp_async_commit();
+    };
+    // right-hand sides in registers, two planes ahead: a row warp keeps its
+    // span, the ring warp the one cell it updates
+    const int rk = ring ? ((lane >> 4) ? 128 : -1) : 4 * lane;
+    int rgx = 0;
+    const bool rx_ok = axis_ok(x0 + rk, nx, L.per[0], rgx);
+    auto fetch_rhs = [&](int p, T (&r)[4]) {
+        int gz = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) r[i] = (T)0;
+        if (!(p >= z0 - 1 && p <= z1 && xy_ok && plane(p, gz))) return;
+        const T* src = rhs + (nxy * gz + nx * gy_l);
+        if (!ring) {
+            const auto q = vld(src + x0 + rk);
+            r[0] = q.v0;
+            r[1] = q.v1;
+            r[2] = q.v2;
+            r[3] = q.v3;
+        } else if (rx_ok) {
+            r[0] = src[rgx];
         }
     };
-    auto store_e = [&](int p) {
-        T* d = se + eslot(p) * NE;
-        uint8_t* ds = ss + eslot(p) * NE;
+    T r_m1[4], r_0[4], r_p1[4], r_p2[4];
+    for (int p = z0 - 2; p <= z0 + 1; p++) issue(p, wrap7(p - z0 + 3));
+    fetch_rhs(z0 - 1, r_0);
+    fetch_rhs(z0, r_p1);
 #pragma unroll
-        for (int k = 0; k < G::KE; k++) {
-            const int idx = tid + k * NT;
-            if (idx < NE) {
-                d[idx] = ve[k];
-                ds[idx] = vs[k];
-            }
-        }
-    };
-    auto fetch_r = [&](int p) {
-        int gz;
-        const bool okz = axis_ok(p, nz, L.per[2], gz);
-#pragma unroll
-        for (int k = 0; k < G::KQ; k++) {
-            const int idx = tid + k * NT;
-            T v = (T)0;
-            if (idx < NQ && okz) {
-                const int r = idx / QW, q = idx - r * QW;
-                int gx, gy;
-                if (axis_ok(x0 - 1 + q, nx, L.per[0], gx) && axis_ok(y0 - 1 + r, ny, L.per[1], gy))
-                    v = rhs[gx + nx * gy + nxy * gz];
-            }
-            vr[k] = v;
-        }
-    };
-    auto store_r = [&](int p) {
-        T* d = sr + rslot(p) * NQ;
-#pragma unroll
-        for (int k = 0; k < G::KQ; k++) {
-            const int idx = tid + k * NT;
-            if (idx < NQ) d[idx] = vr[k];
-        }
-    };
+    for (int i = 0; i < 4; i++) r_m1[i] = (T)0;
 
-    // prologue: planes z0-2 .. z0 and the rhs of plane z0-1
-    for (int p = z0 - 2; p <= z0; p++) {
-        fetch_e(p);
-        store_e(p);
-    }
-    fetch_r(z0 - 1);
-    store_r(z0 - 1);
-    __syncthreads();
-
-    // output cells of this thread: 4 consecutive x on one tile row
-    const int orow = tid / (TX / 4), ocol = 4 * (tid % (TX / 4));
-    const int ogy = y0 + orow, ogx = x0 + ocol;
-
+    const int ry = y0 - 2 + w;  // row of a row warp (unwrapped)
+    int gry = 0;
+    const bool row_ok = !ring && axis_ok(ry, ny, L.per[1], gry);
+    const bool red_row = row_ok && w >= 1 && w <= kRbRows - 2;
+    const bool out_row = !ring && w >= 2 && w < 2 + kRbOut && ry < ny;
+    const int own = (w * kRbSpans + lane + 1) * 4;  // own span, element offset within a slot
+    T* buf = sbuf[ring ? 0 : w];
+    int sl = 2;  // slot of plane p (p = z0 - 1)
     for (int p = z0 - 1; p <= z1; p++) {
-        if (p + 2 <= z1 + 1) fetch_e(p + 2);
-        if (p + 1 <= z1) fetch_r(p + 1);
-        // red cells of plane p on the tile and its 1-cell ring
-        {
-            const T* em = se + eslot(p - 1) * NE;
-            T* e0 = se + eslot(p) * NE;
-            const T* ep = se + eslot(p + 1) * NE;
-            const uint8_t* sm = ss + eslot(p - 1) * NE;
-            const uint8_t* s0 = ss + eslot(p) * NE;
-            const uint8_t* sp = ss + eslot(p + 1) * NE;
-            const T* rq = sr + rslot(p) * NQ;
+        const int s_m2 = wrap7(sl - 2), s_m1 = wrap7(sl - 1), s_p1 = wrap7(sl + 1);
+        issue(p + 3, wrap7(sl + 3));
+        fetch_rhs(p + 2, r_p2);
+        cp_async_wait2();
+        __syncthreads();
+        int gz = 0;
+        const bool zok = plane(p, gz);
+        // red cells of plane p: rows 1..14 and the ring cells
+        if (!ring) {
+            unsigned near = 0;
+            const int jc = sl * SE + own;
+            if (zok && red_row) {
+                const auto c = vld(E + jc);
+                const T cm = E[jc - 1], cp = E[jc + 4];
+                const auto u = vld(E + jc - ROW);
+                const auto d = vld(E + jc + ROW);
+                const auto zm = vld(E + s_m1 * SE + own);
+                const auto zp = vld(E + s_p1 * SE + own);
+                const unsigned sw = S[jc >> 2];
+                const T cc[6] = {cm, c.v0, c.v1, c.v2, c.v3, cp};
+                const T uu[4] = {u.v0, u.v1, u.v2, u.v3}, dd[4] = {d.v0, d.v1, d.v2, d.v3};
+                const T mm[4] = {zm.v0, zm.v1, zm.v2, zm.v3}, pp[4] = {zp.v0, zp.v1, zp.v2, zp.v3};
+                const int p0 = (ry + p) & 1;  // red cells at span positions p0 and p0 + 2
 #pragma unroll
-            for (int k = 0; k < G::KR; k++) {
-                const int j = tid + k * NT;
-                if (j < G::NRED) {
-                    const int r1 = j / (QW / 2), h = j - r1 * (QW / 2);
-                    const int gy = y0 - 1 + r1;
-                    const int par = (x0 - 1 + gy + p) & 1;
-                    const int c1 = 2 * h + par;  // red: x + y + z even
-                    const int rr = r1 + 1, cc = c1 + 1;
-                    const uint8_t sv = s0[rr * RW + cc];
-                    if ((sv & ST_KIND) == ST_UNKNOWN) {
-                        const T v = rb_update<T, RW>(L, inv_diag0, omega, em, e0, ep, sm, s0, sp, rr, cc, sv,
-                                                     rq[r1 * QW + c1], x0 - 1 + c1, gy, p);
-                        e0[rr * RW + cc] = v;
+                for (int i = 0; i < 4; i++) {
+                    if ((i & 1) != p0) continue;
+                    const unsigned sv = (sw >> (8 * i)) & 0xFFu;
+                    if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+                    if (sv & ST_NEAR) {
+                        near |= 1u << i;
+                        continue;
                     }
+                    T o = cc[i];
+                    o += cc[i + 2];
+                    o += uu[i];
+                    o += dd[i];
+                    o += mm[i];
+                    o += pp[i];
+                    const T gs = (L.h2 * r_0[i] + o) * inv_diag0;
+                    E[jc + i] = ((T)1 - omega) * cc[i + 1] + omega * gs;
                 }
+            }
+            if (__any_sync(0xffffffffu, near != 0)) {
+                const int jw = sl * SE + w * ROW + 4, jwm = s_m1 * SE + w * ROW + 4, jwp = s_p1 * SE + w * ROW + 4;
+                warp_rare_cells<4>(near, buf, [&](int ln, int i) {
+                    const int k = 4 * ln + i;
+                    return rb2_near<T>(L, omega, E, S, jw + k, jwm + k, jwp + k,
+                                       rhs[nxy * gz + nx * gry + x0 + k], wall_faces(L, x0 + k, gry, gz));
+                });
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if ((near >> i) & 1u) E[jc + i] = buf[lane * 4 + i];
+            }
+        } else if (zok) {
+            const int rw = lane & 15, k = rk;
+            const int yy = y0 - 2 + rw;
+            int gyy = 0;
+            if (rw >= 1 && rw <= kRbRows - 2 && rx_ok && axis_ok(yy, ny, L.per[1], gyy) &&
+                ((x0 + k + yy + p) & 1) == 0) {
+                const int jc = sl * SE + rw * ROW + k + 4;
+                const unsigned sv = (S[jc >> 2] >> ((jc & 3) << 3)) & 0xFFu;
+                if ((sv & ST_KIND) == ST_UNKNOWN)
+                    E[jc] = rb2_near<T>(L, omega, E, S, jc, s_m1 * SE + rw * ROW + k + 4, s_p1 * SE + rw * ROW + k + 4,
+                                        r_0[0], wall_faces(L, rgx, gyy, gz));
             }
         }
         __syncthreads();
-        // black cells of plane p - 1 on the tile, then the plane's output
+        // black cells of plane p - 1 on the output rows, then the span out
         const int pb = p - 1;
-        if (pb >= z0 && pb < z1 && ogy < ny) {
-            const T* em = se + eslot(pb - 1) * NE;
-            const T* e0 = se + eslot(pb) * NE;
-            const T* ep = se + eslot(pb + 1) * NE;
-            const uint8_t* sm = ss + eslot(pb - 1) * NE;
-            const uint8_t* s0 = ss + eslot(pb) * NE;
-            const uint8_t* sp = ss + eslot(pb + 1) * NE;
-            const T* rq = sr + rslot(pb) * NQ;
-            const int rr = orow + 2;
-            T out[4];
+        if (out_row && pb >= z0 && pb < z1) {  // warp-uniform
+            const int jc = s_m1 * SE + own;
+            const auto c = vld(E + jc);
+            const T cm = E[jc - 1], cp = E[jc + 4];
+            const auto u = vld(E + jc - ROW);
+            const auto d = vld(E + jc + ROW);
+            const auto zm = vld(E + s_m2 * SE + own);
+            const auto zp = vld(E + sl * SE + own);
+            const unsigned sw = S[jc >> 2];
+            const T cc[6] = {cm, c.v0, c.v1, c.v2, c.v3, cp};
+            const T uu[4] = {u.v0, u.v1, u.v2, u.v3}, dd[4] = {d.v0, d.v1, d.v2, d.v3};
+            const T mm[4] = {zm.v0, zm.v1, zm.v2, zm.v3}, pp[4] = {zp.v0, zp.v1, zp.v2, zp.v3};
+            T out[4] = {c.v0, c.v1, c.v2, c.v3};
+            unsigned near = 0;
+            const int p0 = (ry + pb + 1) & 1;  // black cells at span positions p0 and p0 + 2
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int cc = ocol + u + 2;
-                const int i = rr * RW + cc;
-                T v = e0[i];
-                const int gx = ogx + u;
-                if (((gx + ogy + pb) & 1) == 1) {
-                    const uint8_t sv = s0[i];
-                    if ((sv & ST_KIND) == ST_UNKNOWN)
-                        v = rb_update<T, RW>(L, inv_diag0, omega, em, e0, ep, sm, s0, sp, rr, cc, sv,
-                                             rq[(orow + 1) * QW + ocol + u + 1], gx, ogy, pb);
+            for (int i = 0; i < 4; i++) {
+                if ((i & 1) != p0) continue;
+                const unsigned sv = (sw >> (8 * i)) & 0xFFu;
+                if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+                if (sv & ST_NEAR) {
+                    near |= 1u << i;
+                    continue;
                 }
-                out[u] = v;
+                T o = cc[i];
+                o += cc[i + 2];
+                o += uu[i];
+                o += dd[i];
+                o += mm[i];
+                o += pp[i];
+                const T gs = (L.h2 * r_m1[i] + o) * inv_diag0;
+                out[i] = ((T)1 - omega) * cc[i + 1] + omega * gs;
             }
-            T* dst = eout + (size_t)nxy * pb + (size_t)nx * ogy + ogx;
-            if (ogx + 4 <= nx && (nx & 3) == 0) {
-                vst(dst, out[0], out[1], out[2], out[3]);
-            } else {
+            if (__any_sync(0xffffffffu, near != 0)) {
+                const int jw = s_m1 * SE + w * ROW + 4, jwm = s_m2 * SE + w * ROW + 4, jwp = sl * SE + w * ROW + 4;
+                warp_rare_cells<4>(near, buf, [&](int ln, int i) {
+                    const int k = 4 * ln + i;
+                    return rb2_near<T>(L, omega, E, S, jw + k, jwm + k, jwp + k, rhs[nxy * pb + nx * ry + x0 + k],
+                                       wall_faces(L, x0 + k, ry, pb));
+                });
 #pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (ogx + u < nx) dst[u] = out[u];
+                for (int i = 0; i < 4; i++)
+                    if ((near >> i) & 1u) out[i] = buf[lane * 4 + i];
             }
+            vst(eout + (nxy * pb + nx * ry + x0 + rk), out[0], out[1], out[2], out[3]);
         }
-        if (p + 2 <= z1 + 1) store_e(p + 2);
-        if (p + 1 <= z1) store_r(p + 1);
-        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            r_m1[i] = r_0[i];
+            r_0[i] = r_p1[i];
+            r_p1[i] = r_p2[i];
+        }
+        sl = s_p1;
     }
+    asm volatile("cp.async.wait_all;\n" ::);
 }
 
 // Residual of level l at its unknown cells, restricted to level l+1 as the
@@ -896,12 +1006,25 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
 // the residuals and adds them to the coarse sums in the children order
 // (dk, dj, di) of the scalar kernel.
 template <class T>
+__device__ __forceinline__ T near_residual(const Level<T>& L, const uint8_t* __restrict__ st,
+                                           const T* __restrict__ rhs, const T* __restrict__ e, int x, int y, int z,
+                                           T inv_h2) {
+    const int cidx = x + L.nx * (y + L.ny * z);
+    T diag, off;
+    level_stencil<T, true>(L, st, e, x, y, z, st[cidx], diag, off);
+    return rhs[cidx] - (diag * e[cidx] - off) * inv_h2;
+}
+
+template <class T>
 __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T inv_h2, const uint8_t* __restrict__ st,
                                                     const T* __restrict__ rhs, const T* __restrict__ e, int cnx,
                                                     int cny, const uint8_t* __restrict__ cst, T* __restrict__ crhs) {
-    const int cxs = 2 * (blockIdx.x * 32 + threadIdx.x);
+    __shared__ T sbuf[8][32 * 4];
+    const int cx_warp = 2 * (blockIdx.x * 32);
+    const int cxs = cx_warp + 2 * threadIdx.x;
     const int cy = blockIdx.y * 8 + threadIdx.y, cz = blockIdx.z;
-    if (cxs >= cnx || cy >= cny) return;
+    if (cy >= cny) return;  // whole warps
+    const bool lane_on = cxs < cnx;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int xs = 2 * cxs;
     T sum0 = (T)0, sum1 = (T)0;
@@ -921,75 +1044,52 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
 #pragma unroll
             for (int i = 0; i < 12; i++) c[i] = (T)0;
 #pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = b[i] = d[i] = f[i] = (T)0;
-            if (okxl) ES_VLD(c, 0, e + row + xl);
-            ES_VLD(c, 4, e + row + xs);
-            if (okxr) ES_VLD(c, 8, e + row + xr);
-            if (okym) ES_VLD(a, 0, e + rym + xs);
-            if (okyp) ES_VLD(b, 0, e + ryp + xs);
-            if (okzm) ES_VLD(d, 0, e + rzm + xs);
-            if (okzp) ES_VLD(f, 0, e + rzp + xs);
-            ES_VLD(r, 0, rhs + row + xs);
-            const unsigned sw = *reinterpret_cast<const unsigned*>(st + row + xs);
+            for (int i = 0; i < 4; i++) a[i] = b[i] = d[i] = f[i] = r[i] = (T)0;
+            unsigned sw = 0x02020202u;  // (Neumann: no residual)
+            if (lane_on) {
+                if (okxl) ES_VLD(c, 0, e + row + xl);
+                ES_VLD(c, 4, e + row + xs);
+                if (okxr) ES_VLD(c, 8, e + row + xr);
+                if (okym) ES_VLD(a, 0, e + rym + xs);
+                if (okyp) ES_VLD(b, 0, e + ryp + xs);
+                if (okzm) ES_VLD(d, 0, e + rzm + xs);
+                if (okzp) ES_VLD(f, 0, e + rzp + xs);
+                ES_VLD(r, 0, rhs + row + xs);
+                sw = *reinterpret_cast<const unsigned*>(st + row + xs);
+            }
+            T res[4];
+            unsigned near_bits = 0;
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const uint8_t sv = (uint8_t)((sw >> (8 * i)) & 0xFF);
-                T res = (T)0;
-                if ((sv & ST_KIND) == ST_UNKNOWN) {
-                    T diag, off;
-                    if (!(sv & ST_NEAR)) {
-                        T o = c[i + 3];
-                        o += c[i + 5];
-                        o += a[i];
-                        o += b[i];
-                        o += d[i];
-                        o += f[i];
-                        diag = L.diag0;
-                        off = o;
-                    } else {
-                        T dg = L.diag0, o = (T)0;
-                        const int gx = xs + i;
-                        const int g3[3] = {gx, y, z}, n3[3] = {nx, ny, nz};
-#pragma unroll
-                        for (int ax = 0; ax < 3; ax++)
-#pragma unroll
-                            for (int side = -1; side <= 1; side += 2) {
-                                const int q = g3[ax] + side;
-                                if ((q < 0 || q >= n3[ax]) && !L.per[ax]) {
-                                    dg += (L.pot_bc[2 * ax + (side > 0 ? 1 : 0)] == ES_POT_DIRICHLET) ? (T)1 : (T)-1;
-                                    continue;
-                                }
-                                int nb;
-                                T v;
-                                if (ax == 0) {
-                                    int wx;
-                                    wrap_axis(q, nx, L.per[0], wx);
-                                    nb = row + wx;
-                                    v = c[i + 4 + side];
-                                } else if (ax == 1) {
-                                    nb = (side < 0 ? rym : ryp) + gx;
-                                    v = side < 0 ? a[i] : b[i];
-                                } else {
-                                    nb = (side < 0 ? rzm : rzp) + gx;
-                                    v = side < 0 ? d[i] : f[i];
-                                }
-                                const uint8_t kk = st[nb] & ST_KIND;
-                                if (kk == ST_UNKNOWN)
-                                    o += v;
-                                else
-                                    dg += (kk == ST_DIR) ? (T)1 : (T)-1;
-                            }
-                        diag = dg;
-                        off = o;
-                    }
-                    res = r[i] - (diag * c[i + 4] - off) * inv_h2;
+                res[i] = (T)0;
+                if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+                if (sv & ST_NEAR) {
+                    near_bits |= 1u << i;
+                    continue;
                 }
-                if (i < 2)
-                    sum0 += res;
-                else
-                    sum1 += res;
+                T o = c[i + 3];
+                o += c[i + 5];
+                o += a[i];
+                o += b[i];
+                o += d[i];
+                o += f[i];
+                res[i] = r[i] - (L.diag0 * c[i + 4] - o) * inv_h2;
             }
+            if (__any_sync(0xffffffffu, near_bits != 0)) {
+                T* buf = sbuf[threadIdx.y];
+                warp_rare_cells<4>(near_bits, buf, [&](int ln, int i) {
+                    return near_residual<T>(L, st, rhs, e, 2 * (cx_warp + 2 * ln) + i, y, z, inv_h2);
+                });
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if ((near_bits >> i) & 1u) res[i] = buf[threadIdx.x * 4 + i];
+                __syncwarp();
+            }
+            sum0 += res[0] + res[1];
+            sum1 += res[2] + res[3];
         }
+    if (!lane_on) return;
     const int C = cxs + cnx * (cy + cny * cz);
     const T v0 = ((cst[C] & ST_KIND) == ST_UNKNOWN) ? sum0 / (T)8 : (T)0;
     const T v1 = ((cst[C + 1] & ST_KIND) == ST_UNKNOWN) ? sum1 / (T)8 : (T)0;
@@ -1114,15 +1214,38 @@ __device__ __forceinline__ P face_value(const Grid& g, const Solver& s, const P*
     return pc + (P)(part[o].sigma / s.eps);
 }
 
+// The same ghost values in FP32 for the reduced forms: the sphere's
+// boundary value (2 zeta or sigma / eps) comes from its float-float record
+// (high part), a Dirichlet wall's 2 * value from wall2.
+struct WallF {
+    float v2[6];
+};
+__device__ __forceinline__ float face_value_f(const Grid& g, const Solver& s, const WallF& wall2,
+                                              const float* psi, const int32_t* owner, const uint8_t* st0,
+                                              const float2* pbc, int x, int y, int z, float pc, int a, int side) {
+    int d[3] = {0, 0, 0};
+    d[a] = side;
+    long long nb;
+    if (!neighbour(g, x, y, z, d[0], d[1], d[2], nb)) {
+        const int face = 2 * a + (side > 0 ? 1 : 0);
+        return s.pot_bc[face] == ES_POT_DIRICHLET ? wall2.v2[face] - pc : pc;
+    }
+    const uint8_t k = st0[nb] & ST_KIND;
+    if (k == ST_UNKNOWN) return psi[nb];
+    const float b = pbc[owner[nb]].x;
+    return k == ST_DIR ? b - pc : pc + b;
+}
+
 // f_b = rho_e (E_ext - grad psi), rho_e = -kappa^2 eps psi (Eq. ChrgDensDHA),
 // computed in the type P of the potential it reads (double, or the float
-// copy in the MIXED32 form) and stored in the PDF storage type S.
+// high part of psi in the reduced forms) and stored in the type S of f_b.
 template <class S, class P>
 __global__ void __launch_bounds__(128) k_body_force(Grid g, Solver s, P Ex, P Ey, P Ez, P k2e,
                                                     const P* __restrict__ psi, const uint8_t* __restrict__ flags,
                                                     const int32_t* __restrict__ owner,
                                                     const DParticle* __restrict__ part, const int* __restrict__ kind,
-                                                    S* __restrict__ fb) {
+                                                    const uint8_t* __restrict__ st0, const float2* __restrict__ pbc,
+                                                    WallF wall2, S* __restrict__ fb) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
@@ -1151,6 +1274,13 @@ __global__ void __launch_bounds__(128) k_body_force(Grid g, Solver s, P Ex, P Ey
                 if (cy(q)) g1 += cy(q) > 0 ? d : -d;
                 if (cz(q)) g2 += cz(q) > 0 ? d : -d;
             }
+        } else if constexpr (sizeof(P) == 4) {
+            g0 = 0.5f * (face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 0, 1) -
+                         face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 0, -1));
+            g1 = 0.5f * (face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 1, 1) -
+                         face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 1, -1));
+            g2 = 0.5f * (face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 2, 1) -
+                         face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 2, -1));
         } else {
             g0 = (P)0.5 * (face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 0, 1) -
                            face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 0, -1));
@@ -1188,20 +1318,17 @@ size_t coarse_smem_bytes(const es_ctx* c, size_t tsize) {
     return n * (2 * tsize + 1);
 }
 
-constexpr int kRbTX = 64, kRbTY = 16;
-
-// Launch shape of the fused sweep: tiles of kRbTX x kRbTY columns, and the z
-// extent cut into chunks so that the blocks fill whole waves of the
-// resident-block capacity; each chunk re-reads three planes and recomputes
-// two red planes, so the cost model is (waves rounded up) x (chunk + 2).
+// Launch shape of the fused sweep: 128 x 12 output tiles, and the z extent
+// cut into chunks so that the blocks fill whole waves of the resident-block
+// capacity; a chunk re-reads three planes and recomputes two red planes, so
+// the cost model is (waves rounded up) x (chunk + 2).
 template <class T>
 dim3 rb_launch_shape(es_ctx* c, const Level<T>& L, int& zc) {
-    using G = RB<T, kRbTX, kRbTY>;
     const int ti = sizeof(T) == 4 ? 0 : 1;
     if (c->rb_blocks[ti] == 0) {
-        cudaFuncSetAttribute(k_smooth_rb<T, kRbTX, kRbTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+        cudaFuncSetAttribute(k_smooth_rb2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RB2<T>::smem);
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_smooth_rb<T, kRbTX, kRbTY>, G::NT, G::smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_smooth_rb2<T>, 32 * (kRbRows + 1), RB2<T>::smem) !=
                 cudaSuccess ||
             b < 1) {
             cudaGetLastError();
@@ -1209,7 +1336,7 @@ dim3 rb_launch_shape(es_ctx* c, const Level<T>& L, int& zc) {
         }
         c->rb_blocks[ti] = b;
     }
-    const long long cols = (long long)((L.nx + kRbTX - 1) / kRbTX) * ((L.ny + kRbTY - 1) / kRbTY);
+    const long long cols = (long long)(L.nx / 128) * ((L.ny + kRbOut - 1) / kRbOut);
     const long long cap = (long long)c->rb_blocks[ti] * c->n_sm;
     double best = 1e300;
     int best_zc = L.nz;
@@ -1224,8 +1351,7 @@ dim3 rb_launch_shape(es_ctx* c, const Level<T>& L, int& zc) {
         }
     }
     zc = best_zc;
-    return dim3((unsigned)((L.nx + kRbTX - 1) / kRbTX), (unsigned)((L.ny + kRbTY - 1) / kRbTY),
-                (unsigned)((L.nz + zc - 1) / zc));
+    return dim3((unsigned)(L.nx / 128), (unsigned)((L.ny + kRbOut - 1) / kRbOut), (unsigned)((L.nz + zc - 1) / zc));
 }
 
 // One V-cycle on level l for A e = rhs (the result in e[l]).  warm != 0
@@ -1251,9 +1377,10 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     const bool vec = (L.nx % 4) == 0;
     constexpr int W = 4;
     dim3 vblk(32, 8), vgrd((L.nx / W + 31) / 32, (L.ny + 7) / 8, L.nz);
-    // (a periodic axis of one cell is its own neighbour: no red-black split)
-    const bool use_rb = c->P.smoother == ES_SMOOTH_FUSED && (!L.per[0] || L.nx >= 2) &&
-                        (!L.per[1] || L.ny >= 2) && (!L.per[2] || L.nz >= 2);
+    // (the span form needs whole 128-cell tiles in x; a periodic axis of
+    // one cell is its own neighbour: no red-black split)
+    const bool use_rb = c->P.smoother == ES_SMOOTH_FUSED && (L.nx % 128) == 0 && (!L.per[1] || L.ny >= 2) &&
+                        (!L.per[2] || L.nz >= 2);
     int rb_zc = 1;
     dim3 rb_grid(1, 1, 1);
     if (use_rb) rb_grid = rb_launch_shape<T>(c, L, rb_zc);
@@ -1264,8 +1391,8 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
         if (use_rb) {
             ProfScope ps(c, "smooth_fused", l, nl * ((first ? 2.0 : 3.0) * ts + 1.0));
             T* eo = (T*)c->e2[l];
-            k_smooth_rb<T, kRbTX, kRbTY><<<rb_grid, RB<T, kRbTX, kRbTY>::NT, RB<T, kRbTX, kRbTY>::smem, c->stream>>>(
-                L, inv_diag0, st, rhs, e, eo, first, omega, rb_zc);
+            k_smooth_rb2<T><<<rb_grid, dim3(32, kRbRows + 1), RB2<T>::smem, c->stream>>>(L, inv_diag0, st, rhs, e,
+                                                                                          eo, first, omega, rb_zc);
             c->e2[l] = c->e[l];
             c->e[l] = eo;
             e = eo;
@@ -1370,12 +1497,12 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         const dim3 grd(gx, gy, gz), blk(32, 8);
         if (W == 4)
             k_outer_residual_ff<4><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
-                                                                c->psi_lo, c->st[0], c->owner, c->kind,
+                                                                c->psi_lo, c->st[0], c->owner,
                                                                 (const float2*)c->pbc, mask, (float*)c->rhs[0],
                                                                 c->partial);
         else
             k_outer_residual_ff<1><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
-                                                                c->psi_lo, c->st[0], c->owner, c->kind,
+                                                                c->psi_lo, c->st[0], c->owner,
                                                                 (const float2*)c->pbc, mask, (float*)c->rhs[0],
                                                                 c->partial);
         k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
@@ -1436,13 +1563,17 @@ cudaError_t launch_body_force(es_ctx* c) {
     ProfScope ps(c, "body_force", -1, (double)g.N * (s + 1.0 + 3.0 * s));
     const double* E = c->P.E_ext;
     const double k2e = c->S.kappa * c->S.kappa * c->S.eps;
+    WallF wall2;
+    for (int f = 0; f < 6; f++) wall2.v2[f] = (float)(2.0 * c->S.pot_val[f]);
     if (mixed(c))
         k_body_force<float, float><<<grd, blk, 0, c->stream>>>(g, c->S, (float)E[0], (float)E[1], (float)E[2],
                                                                (float)k2e, c->psi32, c->flags, c->owner, c->part,
-                                                               c->kind, (float*)c->fb);
+                                                               c->kind, c->st[0], (const float2*)c->pbc, wall2,
+                                                               (float*)c->fb);
     else
         k_body_force<double, double><<<grd, blk, 0, c->stream>>>(g, c->S, E[0], E[1], E[2], k2e, c->psi, c->flags,
-                                                                 c->owner, c->part, c->kind, (double*)c->fb);
+                                                                 c->owner, c->part, c->kind, c->st[0], nullptr,
+                                                                 wall2, (double*)c->fb);
     count(c);
     return cudaGetLastError();
 }

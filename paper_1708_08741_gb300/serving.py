@@ -1,0 +1,257 @@
+"""Serving independent electrophoresis runs on one GPU with continuous batching.
+
+A request is a complete run: a seeded workload (grid, spheres, Debye length,
+field) stepped until the mean particle velocity is steady.  The server keeps
+a fixed number of slots; a request is admitted as soon as a slot is free and
+the device memory the library reports for it (``es_device_bytes``) fits in
+the budget next to the runs already resident, so requests that arrive while
+others run join them.  Each admitted run lives in its own library context on
+its own CUDA stream, driven by its own host thread (the library releases
+Python's lock while it waits on the GPU), so the kernels of all resident runs
+overlap on the device.  Runs are independent and deterministic, so a run's
+result does not depend on what else is resident (tested).
+
+Request mix (the serving configuration): Poisson arrivals; grid edges
+log-uniform per axis; 1-200 spheres of one radius in [3, 8] (capped at 5 %
+solid volume so that the non-overlapping placement exists); Debye length in
+[2, 8]; field in [5e-4, 3e-3] along x; zeta potentials in [0.5, 2]; periodic
+boundaries.  Steady: the mean particle velocity changes by less than
+``rel_tol`` of its magnitude over ``check_every`` steps, capped at
+``max_steps``.  The potential is solved to RES_RF 1e-8 (the configuration
+names none): looser solves leave potential errors of cond(A) x RES_RF, which
+at 1e-6 already move particle velocities by ~1e-4 between two correct runs.
+
+The scheduler, admission and statistics are plain Python and take a
+simulation factory, so they are tested on the CPU with a stand-in simulation.
+"""
+from __future__ import annotations
+
+import math
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import workloads as W
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float  # seconds after the start of the stream
+    wl: W.Workload
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    steps: int
+    steady: bool
+    v_mean: np.ndarray
+    v: np.ndarray = field(repr=False, default=None)
+    x: np.ndarray = field(repr=False, default=None)
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def _round_edge(e: float, mult: int, lo: int, hi: int) -> int:
+    v = int(round(e / mult)) * mult
+    return max(lo, min(hi, v))
+
+
+def request_workload(rid: int, seed: int = 5, edge_range=(32, 192), max_spheres: int = 200,
+                     radius_range=(3.0, 8.0), debye_range=(2.0, 8.0), field_range=(5e-4, 3e-3),
+                     zeta_range=(0.5, 2.0), max_solid: float = 0.05, res_rf: float = 1e-8) -> W.Workload:
+    """The workload of request ``rid`` (its own PCG32 stream)."""
+    rng = W.PCG32(seed, stream=1000 + rid)
+    lo, hi = edge_range
+    raw = [math.exp(rng.uniform_range(math.log(lo), math.log(hi))) for _ in range(3)]
+    levels = 3 if min(raw) < 64 else 4
+    mult = 1 << levels  # every extent stays even on the coarsest level
+    dims = [_round_edge(e, mult, lo, hi) for e in raw]
+    radius = rng.uniform_range(*radius_range)
+    n = 1 + int(rng.uniform() * max_spheres)
+    vol = dims[0] * dims[1] * dims[2]
+    n = max(1, min(n, int(max_solid * vol / (4.0 / 3.0 * math.pi * radius ** 3))))
+    debye = rng.uniform_range(*debye_range)
+    E = rng.uniform_range(*field_range)
+    periodic = (1, 1, 1)
+    centres = W.place_spheres(n, radius, dims, periodic, rng)
+    zeta = np.array([rng.uniform_range(*zeta_range) for _ in range(n)])
+    wl = W.Workload(name=f"req{rid}_{dims[0]}x{dims[1]}x{dims[2]}_{n}xR{radius:.2f}", dims=dims,
+                    periodic=periodic, tau=1.0, kappa=1.0 / debye, eps=1.0, E_ext=(E, 0.0, 0.0),
+                    levels=levels, res_rf=res_rf, steps=0)
+    return W._set_particles(wl, centres, np.full(n, radius), np.full(n, W.KIND_ZETA), zeta, np.zeros(n))
+
+
+def request_stream(n: int = 256, rate: float = 20.0, seed: int = 5, **kw) -> List[Request]:
+    """``n`` requests with Poisson arrivals at ``rate`` per second."""
+    rng = W.PCG32(seed, stream=7)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += -math.log(1.0 - rng.uniform()) / rate
+        out.append(Request(i, t, request_workload(i, seed=seed, **kw)))
+    return out
+
+
+def percentile(values: Sequence[float], p: float) -> float:
+    """Linear-interpolation percentile (p in [0, 100])."""
+    v = sorted(values)
+    if not v:
+        return float("nan")
+    k = (len(v) - 1) * p / 100.0
+    f = int(math.floor(k))
+    c = min(f + 1, len(v) - 1)
+    return v[f] + (v[c] - v[f]) * (k - f)
+
+
+def run_to_steady(sim, check_every: int = 100, rel_tol: float = 1e-4, max_steps: int = 20000):
+    """Steps ``sim`` until the mean particle velocity changes by less than
+    rel_tol of its magnitude over check_every steps (or max_steps)."""
+    steps = 0
+    prev = None
+    while True:
+        for _ in range(check_every):
+            sim.step()
+        steps += check_every
+        p = sim.particles()
+        vm = np.mean(p["v"], axis=0)
+        if prev is not None:
+            if np.linalg.norm(vm - prev) <= rel_tol * max(np.linalg.norm(vm), 1e-300):
+                return steps, True, vm, p
+        if steps >= max_steps:
+            return steps, False, vm, p
+        prev = vm
+
+
+class Server:
+    """Continuous-batching scheduler.
+
+    sim_factory(workload, stream_index) -> simulation with step(),
+    particles() and close(); bytes_of(workload) -> device bytes of a run.
+    """
+
+    def __init__(self, sim_factory: Callable, bytes_of: Callable, slots: int, budget_bytes: int,
+                 check_every: int = 100, rel_tol: float = 1e-4, max_steps: int = 20000,
+                 clock: Callable[[], float] = time.perf_counter):
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
+        self.sim_factory = sim_factory
+        self.bytes_of = bytes_of
+        self.slots = slots
+        self.budget = budget_bytes
+        self.check_every = check_every
+        self.rel_tol = rel_tol
+        self.max_steps = max_steps
+        self.clock = clock
+        self.peak_resident = 0
+        self.peak_bytes = 0
+
+    def serve(self, requests: Sequence[Request], time_scale: float = 1.0) -> List[Result]:
+        """Replays the arrivals (times multiplied by time_scale) and returns
+        one Result per request, in request order."""
+        for r in requests:
+            if self.bytes_of(r.wl) > self.budget:
+                raise ValueError(f"request {r.rid} needs more device memory than the budget")
+        lock = threading.Condition()
+        pending: List[Request] = []
+        results: Dict[int, Result] = {}
+        state = {"resident": 0, "bytes": 0, "errors": []}
+        free_slots = list(range(self.slots))
+        t0 = self.clock()
+
+        def worker(req: Request, slot: int, need: int, admitted: float):
+            try:
+                sim = self.sim_factory(req.wl, slot)
+                try:
+                    steps, steady, vm, p = run_to_steady(sim, self.check_every, self.rel_tol, self.max_steps)
+                finally:
+                    sim.close()
+                res = Result(req.rid, req.arrival * time_scale, admitted, self.clock() - t0, steps, steady, vm,
+                             p["v"], p["x"])
+            except Exception as e:  # reported after the stream
+                res = None
+                with lock:
+                    state["errors"].append((req.rid, e))
+            with lock:
+                if res is not None:
+                    results[req.rid] = res
+                state["resident"] -= 1
+                state["bytes"] -= need
+                free_slots.append(slot)
+                lock.notify_all()
+
+        def admit_ready():
+            # first fit in arrival order among the requests that have arrived
+            i = 0
+            while i < len(pending) and free_slots:
+                need = self.bytes_of(pending[i].wl)
+                if state["bytes"] + need <= self.budget:
+                    req = pending.pop(i)
+                    slot = free_slots.pop(0)
+                    state["resident"] += 1
+                    state["bytes"] += need
+                    self.peak_resident = max(self.peak_resident, state["resident"])
+                    self.peak_bytes = max(self.peak_bytes, state["bytes"])
+                    th = threading.Thread(target=worker, args=(req, slot, need, self.clock() - t0), daemon=True)
+                    th.start()
+                else:
+                    i += 1
+
+        queue = sorted(requests, key=lambda r: r.arrival)
+        k = 0
+        with lock:
+            while k < len(queue) or pending or state["resident"] > 0:
+                now = self.clock() - t0
+                while k < len(queue) and queue[k].arrival * time_scale <= now:
+                    pending.append(queue[k])
+                    k += 1
+                admit_ready()
+                if k < len(queue):
+                    wait = queue[k].arrival * time_scale - (self.clock() - t0)
+                    if wait > 0:
+                        lock.wait(timeout=wait)
+                elif pending or state["resident"] > 0:
+                    lock.wait(timeout=0.05)
+        if state["errors"]:
+            rid, e = state["errors"][0]
+            raise RuntimeError(f"request {rid} failed: {e}") from e
+        return [results[r.rid] for r in requests]
+
+
+def summarize(results: Sequence[Result]) -> dict:
+    lat = [r.latency for r in results]
+    makespan = max(r.finished for r in results) - min(r.arrival for r in results)
+    return {"runs": len(results), "runs_per_s": len(results) / makespan if makespan > 0 else float("nan"),
+            "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
+            "makespan_s": makespan, "steady": sum(1 for r in results if r.steady),
+            "steps_total": sum(r.steps for r in results)}
+
+
+def gpu_server(precision: int, slots: int, device: str = "cuda:0", budget_fraction: float = 0.8,
+               overrides: Optional[dict] = None, **kw) -> Server:
+    """A Server whose runs are library contexts on their own CUDA streams."""
+    import torch
+
+    import paper_1708_08741_gb300 as es
+
+    dev = torch.device(device)
+    streams = [torch.cuda.Stream(dev) for _ in range(slots)]
+    free, _ = torch.cuda.mem_get_info(dev)
+
+    def factory(wl, slot):
+        torch.cuda.set_device(dev)
+        return es.Simulation(wl, precision, device=device, stream=streams[slot], overrides=overrides)
+
+    def bytes_of(wl):
+        return es.device_bytes(wl, precision, overrides)
+
+    return Server(factory, bytes_of, slots, int(budget_fraction * free), **kw)

@@ -1,0 +1,115 @@
+"""Electrophoretic velocity of a single sphere against Henry's solution.
+
+The paper's validation (Sec. 6, Tab. ValidElectrophoresis) moves one sphere
+of fixed zeta potential through a large box under an applied field, takes
+the terminal velocity U* from the second half of the run, and compares it
+with Henry's velocity for an unbounded electrolyte (Eq. ElPhorVelSphere,
+with Ohshima's approximation of Henry's function, Eq. ElPhorMobilitySphere):
+
+    U_EP = 2 eps zeta E / (3 mu) * (1 + 1 / (2 [1 + 2.5 / (kR (1 + 2 exp(-kR)))]^3)).
+
+The confinement is taken out as the paper does: the relative deviation from
+Stokes' velocity of the same sphere in the same box under a plain force,
+Delta_r U_Stokes, is subtracted from the electrophoretic deviation
+Delta_r U = (U* - U_EP) / U_EP.
+
+Here the box is periodic (the paper's free-slip walls are not built), so
+both runs are the periodic-array setting: the sphere's own force is balanced
+by a uniform counter-force on the fluid, and velocities are measured
+relative to the mean fluid velocity.  The Stokes run uses kappa = 0, where
+the charge density -kappa^2 eps psi vanishes and the sphere carries only the
+force q E (q from Eq. SurfChrgZetaRelationDebHuck at kappa = 0).  Lattice
+units: dx = dt = rho = eps = 1, mu = (tau - 1/2) / 3.
+
+    python -m paper_1708_08741_gb300.validation [--n 128] [--radius 4] [--kR 0.5]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+
+import paper_1708_08741_gb300 as es
+from paper_1708_08741_gb300 import workloads as W
+
+
+def henry_velocity(zeta: float, E: float, eps: float, mu: float, kR: float) -> float:
+    """Henry's electrophoretic velocity with Ohshima's Henry function."""
+    g = 1.0 + 2.5 / (kR * (1.0 + 2.0 * math.exp(-kR)))
+    return 2.0 * eps * zeta * E / (3.0 * mu) * (1.0 + 1.0 / (2.0 * g ** 3))
+
+
+def sphere_charge(zeta: float, R: float, kappa: float, eps: float = 1.0) -> float:
+    """q_s = 4 pi R^2 sigma_s with sigma_s = zeta eps (1 + kappa R) / R."""
+    return 4.0 * math.pi * R * zeta * eps * (1.0 + kappa * R)
+
+
+def _box(n, R, tau, kappa, E, zeta, accel, levels):
+    wl = W.Workload(name=f"henry_{n}_R{R:g}", dims=[n, n, n], periodic=(1, 1, 1), tau=tau, kappa=kappa,
+                    eps=1.0, E_ext=(E, 0.0, 0.0), accel=accel, levels=levels, res_rf=1e-8, max_cycles=200)
+    c = np.array([[n / 2.0, n / 2.0, n / 2.0]])
+    return W._set_particles(wl, c, np.array([float(R)]), np.array([W.KIND_ZETA]), np.array([zeta]), np.zeros(1))
+
+
+def terminal_velocity(wl, steps: int, sample_every: int = 50, precision: int = es.ES_MIXED32,
+                      device: str = "cuda:0") -> dict:
+    """Runs ``steps`` steps and returns the mean sphere velocity relative to
+    the mean fluid velocity over the second half of the samples, and the
+    relative spread (max - min) / mean of that window."""
+    sim = es.Simulation(wl, precision, device=device)
+    samples = []
+    try:
+        for s in range(1, steps + 1):
+            sim.step()
+            if s % sample_every == 0:
+                up = sim.particles()["v"][0, 0]
+                fluid = sim.field(es.FIELD_OWNER) < 0
+                uf = sim.field(es.FIELD_U)[0][fluid].mean()
+                samples.append(up - uf)
+    finally:
+        sim.close()
+    tail = np.array(samples[len(samples) // 2:])
+    mean = float(tail.mean())
+    return {"U": mean, "spread": float((tail.max() - tail.min()) / abs(mean)) if mean else float("nan"),
+            "samples": len(samples)}
+
+
+def validate(n: int = 128, R: float = 4.0, kR: float = 0.5, tau: float = 6.0, zeta: float = 1.0,
+             E: float = 2.5e-3, steps: int = 12000, levels: int = 5, device: str = "cuda:0") -> dict:
+    """One point of the validation: Henry deviation of the electrophoretic
+    run, the Stokes deviation of the matching plain-force run, and their
+    difference (the corrected deviation of Tab. ValidElectrophoresis)."""
+    mu = (tau - 0.5) / 3.0
+    kappa = kR / R
+    n_fluid = n ** 3 - (4.0 / 3.0) * math.pi * R ** 3  # counter-force spread (continuous volume)
+    # electrophoresis: the EDL carries about -q, so the net force is ~0; the
+    # residual is removed with the mean fluid velocity
+    ep = terminal_velocity(_box(n, R, tau, kappa, E, zeta, (0.0, 0.0, 0.0), levels), steps, device=device)
+    u_henry = henry_velocity(zeta, E, 1.0, mu, kR)
+    # Stokes: kappa = 0, force q0 E on the sphere, balanced on the fluid
+    F = sphere_charge(zeta, R, 0.0) * E
+    st = terminal_velocity(_box(n, R, tau, 0.0, E, zeta, (-F / n_fluid, 0.0, 0.0), levels), steps, device=device)
+    u_stokes = F / (6.0 * math.pi * mu * R)
+    d_ep = (ep["U"] - u_henry) / u_henry
+    d_st = (st["U"] - u_stokes) / u_stokes
+    return {"n": n, "R": R, "kR": kR, "tau": tau, "zeta": zeta, "E": E, "steps": steps,
+            "U_henry": u_henry, "U_sim": ep["U"], "spread": ep["spread"], "dU": d_ep,
+            "U_stokes": u_stokes, "U_sim_stokes": st["U"], "dU_stokes": d_st, "dU_corrected": d_ep - d_st}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--radius", type=float, nargs="+", default=[4.0])
+    ap.add_argument("--kR", type=float, nargs="+", default=[0.265, 0.5, 0.8])
+    ap.add_argument("--steps", type=int, default=12000)
+    a = ap.parse_args()
+    for R in a.radius:
+        for kR in a.kR:
+            print(json.dumps(validate(a.n, R, kR, steps=a.steps)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,42 @@
+"""Serving on the GPU: a run's result is the same alone and in a mix of runs
+that share the device (separate contexts, streams and host threads), and
+the MIXED32 server's results match the FP64 server's within 1e-4."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_08741_gb300 import build
+
+    build.build()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_alone_equals_in_the_mix_and_mixed_matches_fp64():
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import serving as S
+
+    reqs = S.request_stream(5, rate=200.0, seed=21, edge_range=(32, 56), max_spheres=8)
+    # rel_tol = 0: every run takes exactly max_steps, so that runs compare step for step
+    kw = dict(check_every=50, rel_tol=0.0, max_steps=300)
+    srv = S.gpu_server(es.ES_MIXED32, slots=5, **kw)
+    mix = srv.serve(reqs)
+    assert srv.peak_resident > 1  # the runs overlapped on the device
+    for r in reqs:
+        alone = S.gpu_server(es.ES_MIXED32, slots=1, **kw).serve([r])[0]
+        m = mix[r.rid]
+        assert alone.steps == m.steps == 300
+        np.testing.assert_array_equal(alone.v, m.v)
+        np.testing.assert_array_equal(alone.x, m.x)
+    ref = S.gpu_server(es.ES_FP64, slots=1, **kw).serve(reqs[:3])
+    for a, b in zip(ref, mix[:3]):
+        assert _rel(b.v, a.v) < 1e-4 and _rel(b.x, a.x) < 1e-4
