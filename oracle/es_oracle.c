@@ -599,7 +599,10 @@ static double outer_residual(or_ctx* c, double* r) {
 
 /* Debye-Hueckel solve of Sec. 5.3: while the residual L2 norm is at least
  * tol = RES_RF * (norm at the first solve of the run), apply a V-cycle to the
- * defect and correct.  forced_cycles >= 0 applies exactly that many cycles.
+ * defect and correct.  A residual of exactly zero is an exact solution and
+ * stops the loop too (with a zero first residual, tol is zero and the test
+ * alone would never end it).  forced_cycles >= 0 applies exactly that many
+ * cycles.
  * info: [cycles, norm before, norm after, tol].                              */
 int or_solve(or_ctx* c, int forced_cycles, double* info) {
     double* r = c->rhs[0];
@@ -619,7 +622,7 @@ int or_solve(or_ctx* c, int forced_cycles, double* info) {
         if (forced_cycles >= 0) {
             if (cycles >= forced_cycles) break;
         } else {
-            if (!(norm >= c->tol)) break;
+            if (norm == 0.0 || !(norm >= c->tol)) break;
             if (cycles >= c->P.max_cycles) {
                 status = OR_ENOTCONVERGED;
                 break;

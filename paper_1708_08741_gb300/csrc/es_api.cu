@@ -390,7 +390,9 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
         if (forced_cycles >= 0) {
             if (cycles >= forced_cycles) break;
         } else {
-            if (!(norm >= c->tol)) break;
+            // (an exactly zero residual is an exact solution; with a zero
+            // first residual tol is zero and the test alone never ends)
+            if (norm == 0.0 || !(norm >= c->tol)) break;
             if (cycles >= c->P.max_cycles) {
                 result = fail(c, ES_ENOTCONVERGED, "max_cycles reached above tolerance");
                 break;

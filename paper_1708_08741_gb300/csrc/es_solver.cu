@@ -278,26 +278,38 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
     const int xs = W * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y;
     const bool lane_on = xs < nx;
-    int ym = 0, yp = 0, xl = 0, xr = 0;
-    bool okym = false, okyp = false, okxl = false, okxr = false;
+    const int xq = lane_on ? xs : 0;  // (inactive lanes read a valid span)
+    // unguarded loads: beyond a wall only near-boundary cells would read,
+    // and those are formed from memory by near_residual_ff
+    int ym = y, yp = y, xl = xq, xr = xq;
     if (y < ny) {
-        okym = wrap_axis(y - 1, ny, g.per[1], ym);
-        okyp = wrap_axis(y + 1, ny, g.per[1], yp);
-        okxl = wrap_axis(xs - 1, nx, g.per[0], xl);
-        okxr = wrap_axis(xs + W, nx, g.per[0], xr);
+        if (!wrap_axis(y - 1, ny, g.per[1], ym)) ym = y;
+        if (!wrap_axis(y + 1, ny, g.per[1], yp)) yp = y;
+        if (!wrap_axis(xq - 1, nx, g.per[0], xl)) xl = xq;
+        if (!wrap_axis(xq + W, nx, g.per[0], xr)) xr = xq;
     }
     float* buf = sbuf[threadIdx.y];
     // y is the same for the 32 lanes of a warp, so the loop is warp-uniform
     for (int z = blockIdx.z; z < nz && y < ny; z += gridDim.z) {
         const int row = nx * (y + ny * z);
-        int zm = 0, zp = 0;
-        const bool okzm = wrap_axis(z - 1, nz, g.per[2], zm), okzp = wrap_axis(z + 1, nz, g.per[2], zp);
+        int zm, zp;
+        if (!wrap_axis(z - 1, nz, g.per[2], zm)) zm = z;
+        if (!wrap_axis(z + 1, nz, g.per[2], zp)) zp = z;
         uint8_t sv[W];
+        if constexpr (W == 4) {
+            const uchar4 s4 = *reinterpret_cast<const uchar4*>(st0 + row + xq);
+            sv[0] = s4.x;
+            sv[1] = s4.y;
+            sv[2] = s4.z;
+            sv[3] = s4.w;
+        } else {
+            sv[0] = st0[row + xq];
+        }
         unsigned near_bits = 0;
         bool any = false;
 #pragma unroll
         for (int i = 0; i < W; i++) {
-            sv[i] = lane_on ? st0[row + xs + i] : (uint8_t)ST_NEU;
+            if (!lane_on) sv[i] = (uint8_t)ST_NEU;
             const bool unk = (sv[i] & ST_KIND) == ST_UNKNOWN;
             any |= unk && !(sv[i] & ST_NEAR);
             if (unk && (sv[i] & ST_NEAR)) near_bits |= 1u << i;
@@ -309,44 +321,29 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
             // interior cells: the x row with one neighbour each side, and the
             // four neighbour rows, in registers
             float ch[W + 2], cl[W + 2], ah[W], al[W], bh[W], bl[W], dh[W], dl[W], fh[W], fl[W];
-#pragma unroll
-            for (int i = 0; i < W; i++) ah[i] = al[i] = bh[i] = bl[i] = dh[i] = dl[i] = fh[i] = fl[i] = 0.0f;
-            ch[0] = cl[0] = ch[W + 1] = cl[W + 1] = 0.0f;
-            if (okxl) {
-                ch[0] = psi_hi[row + xl];
-                cl[0] = psi_lo[row + xl];
-            }
-            if (okxr) {
-                ch[W + 1] = psi_hi[row + xr];
-                cl[W + 1] = psi_lo[row + xr];
-            }
+            ch[0] = psi_hi[row + xl];
+            cl[0] = psi_lo[row + xl];
+            ch[W + 1] = psi_hi[row + xr];
+            cl[W + 1] = psi_lo[row + xr];
             {
                 float t[W];
-                load_span<W>(psi_hi + row + xs, t, 0);
+                load_span<W>(psi_hi + row + xq, t, 0);
 #pragma unroll
                 for (int i = 0; i < W; i++) ch[i + 1] = t[i];
-                load_span<W>(psi_lo + row + xs, t, 0);
+                load_span<W>(psi_lo + row + xq, t, 0);
 #pragma unroll
                 for (int i = 0; i < W; i++) cl[i + 1] = t[i];
             }
             const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
             const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
-            if (okym) {
-                load_span<W>(psi_hi + rym + xs, ah, 0);
-                load_span<W>(psi_lo + rym + xs, al, 0);
-            }
-            if (okyp) {
-                load_span<W>(psi_hi + ryp + xs, bh, 0);
-                load_span<W>(psi_lo + ryp + xs, bl, 0);
-            }
-            if (okzm) {
-                load_span<W>(psi_hi + rzm + xs, dh, 0);
-                load_span<W>(psi_lo + rzm + xs, dl, 0);
-            }
-            if (okzp) {
-                load_span<W>(psi_hi + rzp + xs, fh, 0);
-                load_span<W>(psi_lo + rzp + xs, fl, 0);
-            }
+            load_span<W>(psi_hi + rym + xq, ah, 0);
+            load_span<W>(psi_lo + rym + xq, al, 0);
+            load_span<W>(psi_hi + ryp + xq, bh, 0);
+            load_span<W>(psi_lo + ryp + xq, bl, 0);
+            load_span<W>(psi_hi + rzm + xq, dh, 0);
+            load_span<W>(psi_lo + rzm + xq, dl, 0);
+            load_span<W>(psi_hi + rzp + xq, fh, 0);
+            load_span<W>(psi_lo + rzp + xq, fl, 0);
 #pragma unroll
             for (int i = 0; i < W; i++) {
                 if ((sv[i] & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
@@ -523,9 +520,9 @@ __device__ __forceinline__ void vst(double* p, double a, double b, double c, dou
 // compile time, so the span arrays stay in registers); the near-boundary
 // cells of the colour are only marked in near_bits (bit = span position).
 template <class T, int P0, int W>
-__device__ __forceinline__ void span_update(const Level<T>& L, T inv_diag0, T (&c)[W + 8], const T (&a)[W],
+__device__ __forceinline__ void span_update(const Level<T>& L, T inv_diag0, T (&c)[W + 2], const T (&a)[W],
                                             const T (&b)[W], const T (&d)[W], const T (&f)[W], const T (&r)[W],
-                                            uint2 sw, int first, T omega, unsigned& near_bits) {
+                                            uint2 sw, T omega, unsigned& near_bits) {
 #pragma unroll
     for (int j = 0; j < W / 2; j++) {
         const int i = P0 + 2 * j;
@@ -535,14 +532,14 @@ __device__ __forceinline__ void span_update(const Level<T>& L, T inv_diag0, T (&
             near_bits |= 1u << i;
             continue;
         }
-        T o = c[i + 3];
-        o += c[i + 5];
+        T o = c[i];
+        o += c[i + 2];
         o += a[i];
         o += b[i];
         o += d[i];
         o += f[i];
         const T gs = (L.h2 * r[i] + o) * inv_diag0;
-        c[i + 4] = first ? omega * gs : ((T)1 - omega) * c[i + 4] + omega * gs;
+        c[i + 1] = ((T)1 - omega) * c[i + 1] + omega * gs;
     }
 }
 
@@ -582,33 +579,43 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
     const bool lane_on = xs < L.nx;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int row = nx * (y + ny * z);
+    // Neighbour rows and columns wrap on periodic axes.  Beyond a wall no
+    // interior cell reads them (a cell next to a wall is a near-boundary
+    // cell, updated from global memory below), so any valid index does
+    // there and the loads need no guards.
     int ym, yp, zm, zp, xl, xr;
-    const bool okym = wrap_axis(y - 1, ny, L.per[1], ym), okyp = wrap_axis(y + 1, ny, L.per[1], yp);
-    const bool okzm = wrap_axis(z - 1, nz, L.per[2], zm), okzp = wrap_axis(z + 1, nz, L.per[2], zp);
-    const bool okxl = wrap_axis(xs - 4, nx, L.per[0], xl), okxr = wrap_axis(xs + W, nx, L.per[0], xr);
+    if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
+    if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
+    if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
+    if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
+    if (!wrap_axis(xs - 1, nx, L.per[0], xl)) xl = xs;
+    if (!wrap_axis(xs + W, nx, L.per[0], xr)) xr = xs;
     const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
     const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
-    T c[W + 8], a[W], b[W], d[W], f[W], r[W];
-#pragma unroll
-    for (int i = 0; i < W + 8; i++) c[i] = (T)0;
-#pragma unroll
-    for (int i = 0; i < W; i++) a[i] = b[i] = d[i] = f[i] = (T)0;
+    T c[W + 2], a[W], b[W], d[W], f[W], r[W];
     uint2 sw = make_uint2(0x02020202u, 0x02020202u);  // (Neumann: nothing to update)
-    if (lane_on) {
-        if (!first) {
-            if (okxl) ES_VLD(c, 0, e + row + xl);
+    const int xq = lane_on ? xs : 0;                   // (inactive lanes read a valid span)
+    if (!first) {
+        c[0] = e[row + (lane_on ? xl : 0)];
+        c[W + 1] = e[row + (lane_on ? xr : 0)];
 #pragma unroll
-            for (int v = 0; v < W; v += 4) {
-                ES_VLD(c, 4 + v, e + row + xs + v);
-                if (okym) ES_VLD(a, v, e + rym + xs + v);
-                if (okyp) ES_VLD(b, v, e + ryp + xs + v);
-                if (okzm) ES_VLD(d, v, e + rzm + xs + v);
-                if (okzp) ES_VLD(f, v, e + rzp + xs + v);
-            }
-            if (okxr) ES_VLD(c, W + 4, e + row + xr);
+        for (int v = 0; v < W; v += 4) {
+            ES_VLD(c, 1 + v, e + row + xq + v);
+            ES_VLD(a, v, e + rym + xq + v);
+            ES_VLD(b, v, e + ryp + xq + v);
+            ES_VLD(d, v, e + rzm + xq + v);
+            ES_VLD(f, v, e + rzp + xq + v);
         }
+    } else {
+        // the iterate starts at zero
 #pragma unroll
-        for (int v = 0; v < W; v += 4) ES_VLD(r, v, rhs + row + xs + v);
+        for (int i = 0; i < W + 2; i++) c[i] = (T)0;
+#pragma unroll
+        for (int i = 0; i < W; i++) a[i] = b[i] = d[i] = f[i] = (T)0;
+    }
+#pragma unroll
+    for (int v = 0; v < W; v += 4) ES_VLD(r, v, rhs + row + xq + v);
+    if (lane_on) {
         if (W == 8) {
             sw = *reinterpret_cast<const uint2*>(st + row + xs);
         } else {
@@ -618,9 +625,9 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
     const int p0 = (colour + y + z) & 1;  // xs is even: cells xs + p0 + 2j have the colour
     unsigned near_bits = 0;
     if (p0 == 0)
-        span_update<T, 0, W>(L, inv_diag0, c, a, b, d, f, r, sw, first, omega, near_bits);
+        span_update<T, 0, W>(L, inv_diag0, c, a, b, d, f, r, sw, omega, near_bits);
     else
-        span_update<T, 1, W>(L, inv_diag0, c, a, b, d, f, r, sw, first, omega, near_bits);
+        span_update<T, 1, W>(L, inv_diag0, c, a, b, d, f, r, sw, omega, near_bits);
     // near-boundary cells of the colour: dealt out over the warp's lanes
     if (__any_sync(0xffffffffu, near_bits != 0)) {
         T* buf = sbuf[threadIdx.y];
@@ -629,11 +636,11 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
         });
 #pragma unroll
         for (int i = 0; i < W; i++)
-            if ((near_bits >> i) & 1u) c[i + 4] = buf[threadIdx.x * W + i];
+            if ((near_bits >> i) & 1u) c[i + 1] = buf[threadIdx.x * W + i];
     }
     if (lane_on) {
 #pragma unroll
-        for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[4 + v], c[5 + v], c[6 + v], c[7 + v]);
+        for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[1 + v], c[2 + v], c[3 + v], c[4 + v]);
     }
 }
 
@@ -1034,29 +1041,28 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
         for (int dj = 0; dj < 2; dj++) {
             const int y = 2 * cy + dj, z = 2 * cz + dk;
             const int row = nx * (y + ny * z);
+            // unguarded loads, as in k_smooth_v: beyond a wall only
+            // near-boundary cells would read, and those come from memory below
             int ym, yp, zm, zp, xl, xr;
-            const bool okym = wrap_axis(y - 1, ny, L.per[1], ym), okyp = wrap_axis(y + 1, ny, L.per[1], yp);
-            const bool okzm = wrap_axis(z - 1, nz, L.per[2], zm), okzp = wrap_axis(z + 1, nz, L.per[2], zp);
-            const bool okxl = wrap_axis(xs - 4, nx, L.per[0], xl), okxr = wrap_axis(xs + 4, nx, L.per[0], xr);
+            if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
+            if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
+            if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
+            if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
+            const int xq = lane_on ? xs : 0;
+            if (!wrap_axis(xq - 1, nx, L.per[0], xl)) xl = xq;
+            if (!wrap_axis(xq + 4, nx, L.per[0], xr)) xr = xq;
             const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
             const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
-            T c[12], a[4], b[4], d[4], f[4], r[4];
-#pragma unroll
-            for (int i = 0; i < 12; i++) c[i] = (T)0;
-#pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = b[i] = d[i] = f[i] = r[i] = (T)0;
-            unsigned sw = 0x02020202u;  // (Neumann: no residual)
-            if (lane_on) {
-                if (okxl) ES_VLD(c, 0, e + row + xl);
-                ES_VLD(c, 4, e + row + xs);
-                if (okxr) ES_VLD(c, 8, e + row + xr);
-                if (okym) ES_VLD(a, 0, e + rym + xs);
-                if (okyp) ES_VLD(b, 0, e + ryp + xs);
-                if (okzm) ES_VLD(d, 0, e + rzm + xs);
-                if (okzp) ES_VLD(f, 0, e + rzp + xs);
-                ES_VLD(r, 0, rhs + row + xs);
-                sw = *reinterpret_cast<const unsigned*>(st + row + xs);
-            }
+            T c[6], a[4], b[4], d[4], f[4], r[4];
+            c[0] = e[row + xl];
+            c[5] = e[row + xr];
+            ES_VLD(c, 1, e + row + xq);
+            ES_VLD(a, 0, e + rym + xq);
+            ES_VLD(b, 0, e + ryp + xq);
+            ES_VLD(d, 0, e + rzm + xq);
+            ES_VLD(f, 0, e + rzp + xq);
+            ES_VLD(r, 0, rhs + row + xq);
+            const unsigned sw = lane_on ? *reinterpret_cast<const unsigned*>(st + row + xs) : 0x02020202u;
             T res[4];
             unsigned near_bits = 0;
 #pragma unroll
@@ -1068,13 +1074,13 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
                     near_bits |= 1u << i;
                     continue;
                 }
-                T o = c[i + 3];
-                o += c[i + 5];
+                T o = c[i];
+                o += c[i + 2];
                 o += a[i];
                 o += b[i];
                 o += d[i];
                 o += f[i];
-                res[i] = r[i] - (L.diag0 * c[i + 4] - o) * inv_h2;
+                res[i] = r[i] - (L.diag0 * c[i + 1] - o) * inv_h2;
             }
             if (__any_sync(0xffffffffu, near_bits != 0)) {
                 T* buf = sbuf[threadIdx.y];
@@ -1377,6 +1383,10 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     const bool vec = (L.nx % 4) == 0;
     constexpr int W = 4;
     dim3 vblk(32, 8), vgrd((L.nx / W + 31) / 32, (L.ny + 7) / 8, L.nz);
+    // the smoother takes 8-cell spans where the extent allows (half the
+    // per-cell index work of 4-cell spans)
+    const bool vec8 = (L.nx % 8) == 0;
+    dim3 vgrd8((L.nx / 8 + 31) / 32, (L.ny + 7) / 8, L.nz);
     // (the span form needs whole 128-cell tiles in x; a periodic axis of
     // one cell is its own neighbour: no red-black split)
     const bool use_rb = c->P.smoother == ES_SMOOTH_FUSED && (L.nx % 128) == 0 && (!L.per[1] || L.ny >= 2) &&
@@ -1400,7 +1410,14 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
             return;
         }
         const double b_first = nl * (1.5 * ts + 1.0), b_half = nl * (2.0 * ts + 1.0);
-        if (vec) {
+        if (vec8) {
+            {
+                ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
+                k_smooth_v<T, 8><<<vgrd8, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
+            }
+            ProfScope ps(c, "smooth_half", l, b_half);
+            k_smooth_v<T, 8><<<vgrd8, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
+        } else if (vec) {
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
                 k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
@@ -1477,10 +1494,10 @@ void set_coarse_smem(const es_ctx* c) {
 }  // namespace
 
 // Algorithmic bytes per cell: psi (8: double, or float-float) and the state
-// byte in, r (8) out.
+// byte in, r out (8 as double, 4 as the float right-hand side).
 cudaError_t launch_outer_residual(es_ctx* c) {
     const double diag0 = 6.0 + c->S.kappa * c->S.kappa;
-    ProfScope ps(c, "outer_residual", -1, (double)c->g.N * 17.0);
+    ProfScope ps(c, "outer_residual", -1, (double)c->g.N * (mixed(c) ? 13.0 : 17.0));
     if (mixed(c)) {
         WallFF wall;
         int mask = 0;

@@ -14,8 +14,10 @@ result does not depend on what else is resident (tested).
 Request mix (the serving configuration): Poisson arrivals; grid edges
 log-uniform per axis; 1-200 spheres of one radius in [3, 8] (capped at 5 %
 solid volume so that the non-overlapping placement exists); Debye length in
-[2, 8]; field in [5e-4, 3e-3] along x; zeta potentials in [0.5, 2]; periodic
-boundaries.  Steady: the mean particle velocity changes by less than
+[2, 8]; field in [5e-4, 3e-3] along x; one zeta potential in [0.5, 2] per run
+(equal spheres drift together; the method has no collision response, so a
+run whose spheres meet stops with ES_EOVERLAP and is reported as failed);
+periodic boundaries.  Steady: the mean particle velocity changes by less than
 ``rel_tol`` of its magnitude over ``check_every`` steps, capped at
 ``max_steps``.  The potential is solved to RES_RF 1e-8 (the configuration
 names none): looser solves leave potential errors of cond(A) x RES_RF, which
@@ -55,6 +57,7 @@ class Result:
     v_mean: np.ndarray
     v: np.ndarray = field(repr=False, default=None)
     x: np.ndarray = field(repr=False, default=None)
+    error: Optional[str] = None  # the run stopped with an error (e.g. two spheres overlapped)
 
     @property
     def latency(self) -> float:
@@ -84,7 +87,7 @@ def request_workload(rid: int, seed: int = 5, edge_range=(32, 192), max_spheres:
     E = rng.uniform_range(*field_range)
     periodic = (1, 1, 1)
     centres = W.place_spheres(n, radius, dims, periodic, rng)
-    zeta = np.array([rng.uniform_range(*zeta_range) for _ in range(n)])
+    zeta = np.full(n, rng.uniform_range(*zeta_range))  # one zeta per run: the spheres keep their spacing
     wl = W.Workload(name=f"req{rid}_{dims[0]}x{dims[1]}x{dims[2]}_{n}xR{radius:.2f}", dims=dims,
                     periodic=periodic, tau=1.0, kappa=1.0 / debye, eps=1.0, E_ext=(E, 0.0, 0.0),
                     levels=levels, res_rf=res_rf, steps=0)
@@ -171,16 +174,20 @@ class Server:
         def worker(req: Request, slot: int, need: int, admitted: float):
             try:
                 sim = self.sim_factory(req.wl, slot)
-                try:
-                    steps, steady, vm, p = run_to_steady(sim, self.check_every, self.rel_tol, self.max_steps)
-                finally:
-                    sim.close()
-                res = Result(req.rid, req.arrival * time_scale, admitted, self.clock() - t0, steps, steady, vm,
-                             p["v"], p["x"])
-            except Exception as e:  # reported after the stream
-                res = None
+            except Exception as e:  # cannot run at all: reported after the stream
+                sim, res = None, None
                 with lock:
                     state["errors"].append((req.rid, e))
+            if sim is not None:
+                try:
+                    steps, steady, vm, p = run_to_steady(sim, self.check_every, self.rel_tol, self.max_steps)
+                    res = Result(req.rid, req.arrival * time_scale, admitted, self.clock() - t0, steps, steady,
+                                 vm, p["v"], p["x"])
+                except Exception as e:  # the run itself failed (e.g. overlap): a failed result
+                    res = Result(req.rid, req.arrival * time_scale, admitted, self.clock() - t0, -1, False,
+                                 np.full(3, np.nan), error=f"{type(e).__name__}: {e}")
+                finally:
+                    sim.close()
             with lock:
                 if res is not None:
                     results[req.rid] = res
@@ -228,12 +235,15 @@ class Server:
 
 
 def summarize(results: Sequence[Result]) -> dict:
-    lat = [r.latency for r in results]
+    """runs/s counts the completed runs (failed ones are listed apart)."""
+    ok = [r for r in results if r.error is None]
+    lat = [r.latency for r in ok]
     makespan = max(r.finished for r in results) - min(r.arrival for r in results)
-    return {"runs": len(results), "runs_per_s": len(results) / makespan if makespan > 0 else float("nan"),
+    return {"runs": len(ok), "failed": len(results) - len(ok),
+            "runs_per_s": len(ok) / makespan if makespan > 0 else float("nan"),
             "p50_latency_s": percentile(lat, 50), "p99_latency_s": percentile(lat, 99),
-            "makespan_s": makespan, "steady": sum(1 for r in results if r.steady),
-            "steps_total": sum(r.steps for r in results)}
+            "makespan_s": makespan, "steady": sum(1 for r in ok if r.steady),
+            "steps_total": sum(r.steps for r in ok)}
 
 
 def gpu_server(precision: int, slots: int, device: str = "cuda:0", budget_fraction: float = 0.8,

@@ -9,17 +9,23 @@ with Ohshima's approximation of Henry's function, Eq. ElPhorMobilitySphere):
     U_EP = 2 eps zeta E / (3 mu) * (1 + 1 / (2 [1 + 2.5 / (kR (1 + 2 exp(-kR)))]^3)).
 
 The confinement is taken out as the paper does: the relative deviation from
-Stokes' velocity of the same sphere in the same box under a plain force,
-Delta_r U_Stokes, is subtracted from the electrophoretic deviation
-Delta_r U = (U* - U_EP) / U_EP.
+Stokes' velocity of the same sphere in the same box, Delta_r U_Stokes, is
+subtracted from the electrophoretic deviation Delta_r U = (U* - U_EP) / U_EP.
 
 Here the box is periodic (the paper's free-slip walls are not built), so
-both runs are the periodic-array setting: the sphere's own force is balanced
-by a uniform counter-force on the fluid, and velocities are measured
-relative to the mean fluid velocity.  The Stokes run uses kappa = 0, where
-the charge density -kappa^2 eps psi vanishes and the sphere carries only the
-force q E (q from Eq. SurfChrgZetaRelationDebHuck at kappa = 0).  Lattice
-units: dx = dt = rho = eps = 1, mu = (tau - 1/2) / 3.
+both runs are the periodic-array setting, with velocities measured relative
+to the mean fluid velocity.  The electrophoretic run needs no balancing
+force: the double layer carries the opposite of the sphere's charge.  The
+Stokes run holds an uncharged sphere (zeta = 0, so psi = 0 and no field
+force) in place with a very large density and drives the fluid past it with
+a uniform body force g.  The mean flow of the whole box approaches its
+steady value only on the time N_fluid / (6 pi mu R K), far longer than the
+run, but the disturbance around the sphere follows the mean flow within a
+few hundred steps, so the drag coefficient K = F / (6 pi mu R U) is read at
+every sample from the momentum-exchange force F and the mean fluid velocity
+U, and Delta_r U_Stokes = 1 / K - 1 (the velocity the same force would give
+relative to Stokes' F / (6 pi mu R)).
+Lattice units: dx = dt = rho = eps = 1, mu = (tau - 1/2) / 3.
 
     python -m paper_1708_08741_gb300.validation [--n 128] [--radius 4] [--kR 0.5]
 """
@@ -46,34 +52,49 @@ def sphere_charge(zeta: float, R: float, kappa: float, eps: float = 1.0) -> floa
     return 4.0 * math.pi * R * zeta * eps * (1.0 + kappa * R)
 
 
-def _box(n, R, tau, kappa, E, zeta, accel, levels):
+def _box(n, R, tau, kappa, E, zeta, accel, levels, rho_p_ratio=1.195):
     wl = W.Workload(name=f"henry_{n}_R{R:g}", dims=[n, n, n], periodic=(1, 1, 1), tau=tau, kappa=kappa,
-                    eps=1.0, E_ext=(E, 0.0, 0.0), accel=accel, levels=levels, res_rf=1e-8, max_cycles=200)
+                    eps=1.0, E_ext=(E, 0.0, 0.0), accel=accel, levels=levels, res_rf=1e-8, max_cycles=200,
+                    rho_p_ratio=rho_p_ratio)
     c = np.array([[n / 2.0, n / 2.0, n / 2.0]])
     return W._set_particles(wl, c, np.array([float(R)]), np.array([W.KIND_ZETA]), np.array([zeta]), np.zeros(1))
 
 
-def terminal_velocity(wl, steps: int, sample_every: int = 50, precision: int = es.ES_MIXED32,
+def _solid_mask(wl):
+    """Cells whose centre lies in the sphere (the mapping rule, Sec. 4.2)."""
+    n = wl.dims[0]
+    c = np.arange(n) + 0.5
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    x0 = wl.x[0]
+    return (X - x0[0]) ** 2 + (Y - x0[1]) ** 2 + (Z - x0[2]) ** 2 <= wl.R[0] ** 2
+
+
+def terminal_velocity(wl, steps: int, sample_every: int = 100, precision: int = es.ES_MIXED32,
                       device: str = "cuda:0") -> dict:
-    """Runs ``steps`` steps and returns the mean sphere velocity relative to
-    the mean fluid velocity over the second half of the samples, and the
-    relative spread (max - min) / mean of that window."""
+    """Runs ``steps`` steps; over the second half of the samples returns the
+    mean sphere velocity relative to the mean fluid velocity (U), its
+    relative spread (max - min) / mean, and the mean of F_x / U_rel with F_x
+    the hydrodynamic force on the sphere (drag per unit relative velocity)."""
     sim = es.Simulation(wl, precision, device=device)
-    samples = []
+    samples, drag = [], []
     try:
+        fluid = None
         for s in range(1, steps + 1):
             sim.step()
             if s % sample_every == 0:
                 up = sim.particles()["v"][0, 0]
                 fluid = sim.field(es.FIELD_OWNER) < 0
                 uf = sim.field(es.FIELD_U)[0][fluid].mean()
+                F, _ = sim.forces()
                 samples.append(up - uf)
+                drag.append(F[0, 0] / (uf - up) if uf != up else float("nan"))
     finally:
         sim.close()
-    tail = np.array(samples[len(samples) // 2:])
+    h = len(samples) // 2
+    tail = np.array(samples[h:])
     mean = float(tail.mean())
     return {"U": mean, "spread": float((tail.max() - tail.min()) / abs(mean)) if mean else float("nan"),
-            "samples": len(samples)}
+            "drag_per_velocity": float(np.mean(drag[h:])), "samples": len(samples)}
 
 
 def validate(n: int = 128, R: float = 4.0, kR: float = 0.5, tau: float = 6.0, zeta: float = 1.0,
@@ -83,20 +104,23 @@ def validate(n: int = 128, R: float = 4.0, kR: float = 0.5, tau: float = 6.0, ze
     difference (the corrected deviation of Tab. ValidElectrophoresis)."""
     mu = (tau - 0.5) / 3.0
     kappa = kR / R
-    n_fluid = n ** 3 - (4.0 / 3.0) * math.pi * R ** 3  # counter-force spread (continuous volume)
-    # electrophoresis: the EDL carries about -q, so the net force is ~0; the
-    # residual is removed with the mean fluid velocity
+    # electrophoresis: the EDL carries about -q, so the net force is ~0; what
+    # is left is removed with the mean fluid velocity
     ep = terminal_velocity(_box(n, R, tau, kappa, E, zeta, (0.0, 0.0, 0.0), levels), steps, device=device)
     u_henry = henry_velocity(zeta, E, 1.0, mu, kR)
-    # Stokes: kappa = 0, force q0 E on the sphere, balanced on the fluid
-    F = sphere_charge(zeta, R, 0.0) * E
-    st = terminal_velocity(_box(n, R, tau, 0.0, E, zeta, (-F / n_fluid, 0.0, 0.0), levels), steps, device=device)
-    u_stokes = F / (6.0 * math.pi * mu * R)
+    # Stokes: fixed uncharged sphere, fluid driven by g with about the
+    # electrophoretic speed
+    sim_wl = _box(n, R, tau, kappa, 0.0, 0.0, (0.0, 0.0, 0.0), levels, rho_p_ratio=1e12)
+    n_fluid = n ** 3 - int(np.count_nonzero(_solid_mask(sim_wl)))
+    g = u_henry * 6.0 * math.pi * mu * R / n_fluid
+    sim_wl.accel = (g, 0.0, 0.0)
+    st = terminal_velocity(sim_wl, steps, device=device)
+    K = st["drag_per_velocity"] / (6.0 * math.pi * mu * R)
     d_ep = (ep["U"] - u_henry) / u_henry
-    d_st = (st["U"] - u_stokes) / u_stokes
+    d_st = 1.0 / K - 1.0
     return {"n": n, "R": R, "kR": kR, "tau": tau, "zeta": zeta, "E": E, "steps": steps,
             "U_henry": u_henry, "U_sim": ep["U"], "spread": ep["spread"], "dU": d_ep,
-            "U_stokes": u_stokes, "U_sim_stokes": st["U"], "dU_stokes": d_st, "dU_corrected": d_ep - d_st}
+            "K_stokes": K, "dU_stokes": d_st, "dU_corrected": d_ep - d_st}
 
 
 def main():

@@ -260,6 +260,48 @@ def test_mixed16_after_100_steps(maker):
     assert r["u"] < MIXED16_U_TOL
 
 
+@pytest.mark.parametrize("n", [16, 32])
+def test_sor_variant(n):
+    """The paper's own solver, red-black SOR with omega = 1.7 (Sec. 6.1):
+    one level, so a "cycle" is coarse_sweeps SOR sweeps on the defect (the
+    same iterates as SOR on psi, the sweeps being affine).  16^3 runs in the
+    one-block shared-memory solver, 32^3 in the sweep kernels."""
+    wl = W.single_sphere(n=n, radius=4.0 if n == 32 else 3.0, levels=1, res_rf=1e-8)
+    over = dict(omega=1.7, coarse_sweeps=10, max_cycles=400)
+    p = Pair(wl, overrides=over)
+    p.o.map_particles()
+    p.g.map_particles()
+    fluid = p.o.owner() < 0
+    io = p.o.solve(forced_cycles=3)
+    ig = p.g.solve(forced_cycles=3)
+    assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < FP64_TOL
+    io = p.o.solve()
+    ig = p.g.solve()
+    assert ig["cycles"] == io["cycles"] and ig["r"] < ig["tol"]
+    assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < FP64_TOL
+
+
+@pytest.mark.parametrize("tau", [6.0, 6.5])
+def test_coupled_paper_relaxation_times(tau):
+    """The paper's relaxation times (tau = 6 for the validation and scaling
+    runs, 6.5 for the micro-channel run; Sec. 6.1), FP64, 20 coupled steps."""
+    wl = W.mixed_box()
+    wl.tau = tau
+    p, r = _coupled(wl, 20)
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x", "v", "w"):
+        assert r[k] < FP64_TOL, (k, r[k])
+
+
+def test_zero_right_hand_side_is_solved_without_cycles():
+    wl = W.single_sphere(n=16, radius=3.0, levels=2, res_rf=1e-8)
+    wl.zeta = np.zeros(1)
+    g = es.Simulation(wl, es.ES_MIXED32, overrides=dict(max_cycles=3))
+    g.map_particles()
+    info = g.solve()
+    assert info["cycles"] == 0 and info["r0"] == 0.0 and info["status"] == es.ES_OK
+
+
 def test_overlap_is_reported():
     wl = W.single_sphere(n=32, radius=4.0)
     wl.x = np.array([[10.0, 16.0, 16.0], [16.5, 16.0, 16.0]])

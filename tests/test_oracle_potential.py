@@ -206,6 +206,18 @@ def test_solver_stops_on_tolerance_and_reports_nonconvergence():
     assert res["status"] == oracle.OR_ENOTCONVERGED and res["cycles"] == 1
 
 
+def test_zero_right_hand_side_is_solved_without_cycles():
+    """An uncharged sphere (zeta = 0) and zero-flux walls: b = 0, psi = 0 is
+    exact, the first residual is zero and the solve returns at once."""
+    wl = W.single_sphere(n=16, radius=3.0, levels=2, res_rf=1e-8)
+    wl.zeta = np.zeros(1)
+    o = oracle.Oracle(wl, dict(max_cycles=3))
+    o.map_particles()
+    info = o.solve()
+    assert info["status"] == oracle.OR_OK and info["cycles"] == 0 and info["r0"] == 0.0
+    assert np.all(o.field(oracle.FIELD_PSI) == 0.0)
+
+
 def test_gradient_exact_for_linear_potential():
     """Both the D3Q19 stencil (Eq. ElPotGradComp) and the D3Q7 central
     differences with linearly extrapolated Dirichlet values are exact for a
