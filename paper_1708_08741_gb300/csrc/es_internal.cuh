@@ -113,6 +113,9 @@ struct es_ctx {
     void* e[ES_MAXLEV];
     void* rhs[ES_MAXLEV];
     void* e2[ES_MAXLEV];    // second iterate buffer: the fused sweep runs out of place
+    int* near_list[ES_MAXLEV];  // near-boundary unknown cells per level: red ones, then black ones
+    int near_cap[ES_MAXLEV];    // capacity of each colour's part
+    int* near_count;            // device: 2 counts per level (red, black)
     int n_sm;               // multiprocessors of the device
     int rb_blocks[2];       // resident fused-sweep blocks per SM (float, double); 0 = not queried
     double* partial;
@@ -154,6 +157,7 @@ namespace es {
 cudaError_t launch_init_flags(es_ctx* c);
 cudaError_t launch_map(es_ctx* c);
 cudaError_t launch_coarse_states(es_ctx* c);
+cudaError_t launch_near_lists(es_ctx* c);
 // solver (es_solver.cu)
 cudaError_t launch_outer_residual(es_ctx* c);
 cudaError_t launch_vcycle(es_ctx* c, int warm);

@@ -262,6 +262,27 @@ __device__ __forceinline__ float near_residual_ff(const Grid& g, ff diag0, const
     return __fadd_rn(hs.s, __fadd_rn(hs.e, lo));
 }
 
+// The float-float residual at the near-boundary unknown cells of level 0,
+// from the near-cell list (both colours), written to r_out before the main
+// pass, which reads them back into its norm sum.
+__global__ void __launch_bounds__(256) k_outer_residual_near_ff(Grid g, ff diag0, WallFF wall, int pot_dir_mask,
+                                                                const float* __restrict__ psi_hi,
+                                                                const float* __restrict__ psi_lo,
+                                                                const uint8_t* __restrict__ st0,
+                                                                const int32_t* __restrict__ owner,
+                                                                const float2* __restrict__ pbc,
+                                                                const int* __restrict__ list,
+                                                                const int* __restrict__ count, int cap,
+                                                                float* __restrict__ r_out) {
+    const int n0 = count[0], n1 = count[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0 + n1; i += gridDim.x * blockDim.x) {
+        const int c = i < n0 ? list[i] : list[cap + i - n0];
+        const int x = c % g.nx, yz = c / g.nx;
+        r_out[c] = near_residual_ff(g, diag0, wall, pot_dir_mask, psi_hi, psi_lo, st0, owner, pbc, x, yz % g.ny,
+                                    yz / g.ny);
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, WallFF wall,
                                                            const float* __restrict__ psi_hi,
@@ -271,7 +292,6 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
                                                            const float2* __restrict__ pbc, int pot_dir_mask,
                                                            float* __restrict__ r_out,
                                                            double* __restrict__ partial) {
-    __shared__ float sbuf[8][32 * W];
     __shared__ float swarp[8];
     float acc = 0.0f;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -288,7 +308,6 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
         if (!wrap_axis(xq - 1, nx, g.per[0], xl)) xl = xq;
         if (!wrap_axis(xq + W, nx, g.per[0], xr)) xr = xq;
     }
-    float* buf = sbuf[threadIdx.y];
     // y is the same for the 32 lanes of a warp, so the loop is warp-uniform
     for (int z = blockIdx.z; z < nz && y < ny; z += gridDim.z) {
         const int row = nx * (y + ny * z);
@@ -367,17 +386,10 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
                 out[i] = __fadd_rn(hs.s, __fadd_rn(hs.e, lo));
             }
         }
-        if (__any_sync(0xffffffffu, near_bits != 0)) {
-            const int xw = W * (blockIdx.x * 32);
-            warp_rare_cells<W>(near_bits, buf, [&](int ln, int i) {
-                return near_residual_ff(g, diag0, wall, pot_dir_mask, psi_hi, psi_lo, st0, owner, pbc,
-                                        xw + W * ln + i, y, z);
-            });
+        // near-boundary cells: formed by k_outer_residual_near_ff just before
 #pragma unroll
-            for (int i = 0; i < W; i++)
-                if ((near_bits >> i) & 1u) out[i] = buf[(threadIdx.x & 31) * W + i];
-            __syncwarp();
-        }
+        for (int i = 0; i < W; i++)
+            if ((near_bits >> i) & 1u) out[i] = r_out[row + xs + i];
 #pragma unroll
         for (int i = 0; i < W; i++) acc = __fmaf_rn(out[i], out[i], acc);
         if (lane_on) {
@@ -559,6 +571,21 @@ __device__ __forceinline__ T near_gs(const Level<T>& L, const uint8_t* __restric
     return first ? omega * gs : ((T)1 - omega) * e[cidx] + omega * gs;
 }
 
+// The near-boundary unknown cells of one colour of a level, from the list
+// built at mapping (a grid-stride loop over the device-side count).
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_near(Level<T> L, const uint8_t* __restrict__ st,
+                                                     const T* __restrict__ rhs, T* __restrict__ e,
+                                                     const int* __restrict__ list, const int* __restrict__ count,
+                                                     int first, T omega) {
+    const int n = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = list[i];
+        const int x = c % L.nx, yz = c / L.nx;
+        e[c] = near_gs<T>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, first, omega);
+    }
+}
+
 // One red (colour 0) or black (1) half sweep with W-cell spans (W = 4 or 8):
 // a thread owns cells xs .. xs+W-1 of one row, loads its row (xs-4 ..
 // xs+W+3) and the four neighbour rows as aligned 16-byte vectors (the
@@ -566,16 +593,16 @@ __device__ __forceinline__ T near_gs(const Level<T>& L, const uint8_t* __restric
 // updates the W/2 cells of the colour, and writes the span back with the
 // other colour's values unchanged.  Same per-cell arithmetic as k_smooth;
 // requires nx % W == 0.  first != 0: the iterate starts at zero; nothing is
-// read and the other colour is written as zero.
+// read and the other colour is written as zero.  Near-boundary cells are
+// skipped here and updated by k_smooth_near right after (same colour, so
+// the two passes do not depend on each other).
 template <class T, int W>
 __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
                                                   const T* __restrict__ rhs, T* __restrict__ e, int colour,
                                                   int first, T omega) {
-    __shared__ T sbuf[8][32 * W];
-    const int x_warp = W * (blockIdx.x * 32);
-    const int xs = x_warp + W * threadIdx.x;
+    const int xs = W * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
-    if (y >= L.ny) return;  // whole warps (a warp is one row)
+    if (y >= L.ny) return;
     const bool lane_on = xs < L.nx;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int row = nx * (y + ny * z);
@@ -628,16 +655,8 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
         span_update<T, 0, W>(L, inv_diag0, c, a, b, d, f, r, sw, omega, near_bits);
     else
         span_update<T, 1, W>(L, inv_diag0, c, a, b, d, f, r, sw, omega, near_bits);
-    // near-boundary cells of the colour: dealt out over the warp's lanes
-    if (__any_sync(0xffffffffu, near_bits != 0)) {
-        T* buf = sbuf[threadIdx.y];
-        warp_rare_cells<W>(near_bits, buf, [&](int ln, int i) {
-            return near_gs<T>(L, st, rhs, e, x_warp + W * ln + i, y, z, first, omega);
-        });
-#pragma unroll
-        for (int i = 0; i < W; i++)
-            if ((near_bits >> i) & 1u) c[i + 1] = buf[threadIdx.x * W + i];
-    }
+    // (near-boundary cells of the colour are left to k_smooth_near)
+    (void)near_bits;
     if (lane_on) {
 #pragma unroll
         for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[1 + v], c[2 + v], c[3 + v], c[4 + v]);
@@ -1022,11 +1041,27 @@ __device__ __forceinline__ T near_residual(const Level<T>& L, const uint8_t* __r
     return rhs[cidx] - (diag * e[cidx] - off) * inv_h2;
 }
 
+// The residual at the near-boundary unknown cells of a level, from its
+// near-cell list (both colours), into a scratch array that the restriction
+// then reads for those children.
+template <class T>
+__global__ void __launch_bounds__(256) k_near_residual(Level<T> L, const uint8_t* __restrict__ st,
+                                                       const T* __restrict__ rhs, const T* __restrict__ e,
+                                                       const int* __restrict__ list, const int* __restrict__ count,
+                                                       int cap, T inv_h2, T* __restrict__ out) {
+    const int n0 = count[0], n1 = count[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0 + n1; i += gridDim.x * blockDim.x) {
+        const int c = i < n0 ? list[i] : list[cap + i - n0];
+        const int x = c % L.nx, yz = c / L.nx;
+        out[c] = near_residual<T>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, inv_h2);
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T inv_h2, const uint8_t* __restrict__ st,
-                                                    const T* __restrict__ rhs, const T* __restrict__ e, int cnx,
+                                                    const T* __restrict__ rhs, const T* __restrict__ e,
+                                                    const T* __restrict__ near_res, int cnx,
                                                     int cny, const uint8_t* __restrict__ cst, T* __restrict__ crhs) {
-    __shared__ T sbuf[8][32 * 4];
     const int cx_warp = 2 * (blockIdx.x * 32);
     const int cxs = cx_warp + 2 * threadIdx.x;
     const int cy = blockIdx.y * 8 + threadIdx.y, cz = blockIdx.z;
@@ -1082,16 +1117,10 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
                 o += f[i];
                 res[i] = r[i] - (L.diag0 * c[i + 1] - o) * inv_h2;
             }
-            if (__any_sync(0xffffffffu, near_bits != 0)) {
-                T* buf = sbuf[threadIdx.y];
-                warp_rare_cells<4>(near_bits, buf, [&](int ln, int i) {
-                    return near_residual<T>(L, st, rhs, e, 2 * (cx_warp + 2 * ln) + i, y, z, inv_h2);
-                });
+            // near-boundary children: formed by k_near_residual just before
 #pragma unroll
-                for (int i = 0; i < 4; i++)
-                    if ((near_bits >> i) & 1u) res[i] = buf[threadIdx.x * 4 + i];
-                __syncwarp();
-            }
+            for (int i = 0; i < 4; i++)
+                if ((near_bits >> i) & 1u) res[i] = near_res[row + xq + i];
             sum0 += res[0] + res[1];
             sum1 += res[2] + res[3];
         }
@@ -1383,10 +1412,7 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     const bool vec = (L.nx % 4) == 0;
     constexpr int W = 4;
     dim3 vblk(32, 8), vgrd((L.nx / W + 31) / 32, (L.ny + 7) / 8, L.nz);
-    // the smoother takes 8-cell spans where the extent allows (half the
-    // per-cell index work of 4-cell spans)
-    const bool vec8 = (L.nx % 8) == 0;
-    dim3 vgrd8((L.nx / 8 + 31) / 32, (L.ny + 7) / 8, L.nz);
+
     // (the span form needs whole 128-cell tiles in x; a periodic axis of
     // one cell is its own neighbour: no red-black split)
     const bool use_rb = c->P.smoother == ES_SMOOTH_FUSED && (L.nx % 128) == 0 && (!L.per[1] || L.ny >= 2) &&
@@ -1410,20 +1436,26 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
             return;
         }
         const double b_first = nl * (1.5 * ts + 1.0), b_half = nl * (2.0 * ts + 1.0);
-        if (vec8) {
-            {
-                ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
-                k_smooth_v<T, 8><<<vgrd8, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
-            }
-            ProfScope ps(c, "smooth_half", l, b_half);
-            k_smooth_v<T, 8><<<vgrd8, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
-        } else if (vec) {
+        if (vec) {
+            const int* cnt = c->near_count + 2 * l;
+            const int* list = c->near_list[l];
+            const int cap = c->near_cap[l];
+            const unsigned nb = (unsigned)(16 * c->n_sm);
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
                 k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
             }
-            ProfScope ps(c, "smooth_half", l, b_half);
-            k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
+            {
+                ProfScope ps(c, "smooth_near", l, 0.0);
+                k_smooth_near<T><<<nb, 256, 0, c->stream>>>(L, st, rhs, e, list, cnt, first, omega);
+            }
+            {
+                ProfScope ps(c, "smooth_half", l, b_half);
+                k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
+            }
+            ProfScope ps(c, "smooth_near", l, 0.0);
+            k_smooth_near<T><<<nb, 256, 0, c->stream>>>(L, st, rhs, e, list + cap, cnt + 1, 0, omega);
+            count(c, 2);
         } else {
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
@@ -1461,8 +1493,13 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     ProfScope ps_r(c, "restrict", l, b_grid);
     if (vec) {
         dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
-        k_restrict_v<T><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, m[0], m[1],
+        T* scratch = (T*)c->e2[l];  // (the fused sweep's second iterate; free between sweeps)
+        k_near_residual<T><<<16 * c->n_sm, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l],
+                                                                 c->near_count + 2 * l, c->near_cap[l],
+                                                                 (T)1 / L.h2, scratch);
+        k_restrict_v<T><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1],
                                                       c->st[l + 1], (T*)c->rhs[l + 1]);
+        count(c);
     } else {
         dim3 cgrid((m[0] + 127) / 128, m[1], m[2]);
         k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], c->st[l + 1],
@@ -1512,6 +1549,9 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         int gz = kResPartials / (gx * gy);
         gz = gz < 1 ? 1 : (gz > c->g.nz ? c->g.nz : gz);
         const dim3 grd(gx, gy, gz), blk(32, 8);
+        k_outer_residual_near_ff<<<16 * c->n_sm, 256, 0, c->stream>>>(
+            c->g, ff_from_double(diag0), wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner, (const float2*)c->pbc,
+            c->near_list[0], c->near_count, c->near_cap[0], (float*)c->rhs[0]);
         if (W == 4)
             k_outer_residual_ff<4><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
                                                                 c->psi_lo, c->st[0], c->owner,
@@ -1523,7 +1563,7 @@ cudaError_t launch_outer_residual(es_ctx* c) {
                                                                 (const float2*)c->pbc, mask, (float*)c->rhs[0],
                                                                 c->partial);
         k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
-        count(c, 2);
+        count(c, 3);
         return cudaGetLastError();
     }
     k_outer_residual<<<c->red_blocks, kRedThreads, 0, c->stream>>>(

@@ -247,8 +247,10 @@ def summarize(results: Sequence[Result]) -> dict:
 
 
 def gpu_server(precision: int, slots: int, device: str = "cuda:0", budget_fraction: float = 0.8,
-               overrides: Optional[dict] = None, **kw) -> Server:
-    """A Server whose runs are library contexts on their own CUDA streams."""
+               overrides: Optional[dict] = None, tuner=None, **kw) -> Server:
+    """A Server whose runs are library contexts on their own CUDA streams.
+    With a tuner (autotune.Autotuner), each run takes the smoothing schedule
+    chosen for its workload class (tuned once per class, at admission)."""
     import torch
 
     import paper_1708_08741_gb300 as es
@@ -256,10 +258,15 @@ def gpu_server(precision: int, slots: int, device: str = "cuda:0", budget_fracti
     dev = torch.device(device)
     streams = [torch.cuda.Stream(dev) for _ in range(slots)]
     free, _ = torch.cuda.mem_get_info(dev)
+    tune_lock = threading.Lock()
 
     def factory(wl, slot):
         torch.cuda.set_device(dev)
-        return es.Simulation(wl, precision, device=device, stream=streams[slot], overrides=overrides)
+        ov = dict(overrides or {})
+        if tuner is not None:
+            with tune_lock:
+                ov.update(tuner.tune(wl))
+        return es.Simulation(wl, precision, device=device, stream=streams[slot], overrides=ov)
 
     def bytes_of(wl):
         return es.device_bytes(wl, precision, overrides)

@@ -40,3 +40,21 @@ def test_alone_equals_in_the_mix_and_mixed_matches_fp64():
     ref = S.gpu_server(es.ES_FP64, slots=1, **kw).serve(reqs[:3])
     for a, b in zip(ref, mix[:3]):
         assert _rel(b.v, a.v) < 1e-4 and _rel(b.x, a.x) < 1e-4
+
+
+def test_autotuner_on_the_gpu_picks_a_schedule_that_meets_the_tolerance():
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import autotune as A
+    from paper_1708_08741_gb300 import workloads as W
+
+    wl = W.suspension_sample(64)
+    tuner = A.Autotuner(A.gpu_measure(es.ES_MIXED32, steps=3, warmup=2))
+    best = tuner.tune(wl)
+    assert best in A.candidates(wl)
+    times = [t for _, t in tuner.log[A.class_key(wl)]]
+    assert all(t > 0 for t in times) and min(times) < float("inf")
+    sim = es.Simulation(wl, es.ES_MIXED32, overrides=best)
+    for _ in range(3):
+        info = sim.step()
+        assert info["r"] < info["tol"]
+    sim.close()
