@@ -111,7 +111,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     size_t lv = 0;
     for (int l = 0; l < P->levels; l++) {
         long long Nl = (long long)(P->dims[0] >> l) * (P->dims[1] >> l) * (P->dims[2] >> l);
-        lv += Nl * (1 + 3 * s + 4);  // states, e, e2, rhs, near-cell lists
+        lv += Nl * (1 + 3 * s + 4);  // states, e, e2, rhs, near-cell lists (+ one row per segment)
     }
     if (per_level) *per_level = lv;
     b += lv;
@@ -283,8 +283,12 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
         c->st[l] = (uint8_t*)A(Nl);
         c->e[l] = A(Nl * s);
         c->e2[l] = A(Nl * s);
-        c->near_cap[l] = (int)((Nl + 1) / 2);
-        c->near_list[l] = (int*)A((size_t)2 * c->near_cap[l] * 4);
+        {
+            const long long rows = (long long)c->ln[l][1] * c->ln[l][2];
+            // a segment holds one colour of rows = seg (mod kNearSegs)
+            c->near_cap[l] = (int)(((rows + kNearSegs - 1) / kNearSegs) * ((c->ln[l][0] + 1) / 2));
+            c->near_list[l] = (int*)A((size_t)2 * kNearSegs * c->near_cap[l] * 4);
+        }
         c->rhs[l] = A(Nl * s);
     }
     c->part = (DParticle*)A(np1 * sizeof(DParticle));
@@ -297,7 +301,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->T = (double*)A(np1 * 3 * 8);
     c->partial = (double*)A((c->red_blocks > kResPartials ? c->red_blocks : kResPartials) * 8);
     c->d_norm = (double*)A(64);
-    c->near_count = (int*)A(2 * ES_MAXLEV * 4);
+    c->near_count = (int*)A(2 * kNearSegs * ES_MAXLEV * 4);
     c->d_status = (int*)A(64);
     if (!ok) {
         release(c);

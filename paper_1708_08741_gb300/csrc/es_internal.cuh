@@ -113,9 +113,9 @@ struct es_ctx {
     void* e[ES_MAXLEV];
     void* rhs[ES_MAXLEV];
     void* e2[ES_MAXLEV];    // second iterate buffer: the fused sweep runs out of place
-    int* near_list[ES_MAXLEV];  // near-boundary unknown cells per level: red ones, then black ones
-    int near_cap[ES_MAXLEV];    // capacity of each colour's part
-    int* near_count;            // device: 2 counts per level (red, black)
+    int* near_list[ES_MAXLEV];  // near-boundary unknown cells per level: red segments, then black ones
+    int near_cap[ES_MAXLEV];    // capacity of one segment
+    int* near_count;            // device: 2 kNearSegs counts per level (red segments, then black)
     int n_sm;               // multiprocessors of the device
     int rb_blocks[2];       // resident fused-sweep blocks per SM (float, double); 0 = not queried
     double* partial;
@@ -185,6 +185,11 @@ inline bool mixed(const es_ctx* c) { return c->P.precision == ES_MIXED32 || c->P
 inline size_t pdf_bytes(int precision) {
     return precision == ES_MIXED16 ? 2 : (precision == ES_MIXED32 ? 4 : 8);
 }
+
+// Near-cell lists are split by colour and by row (y + ny z) mod kNearSegs,
+// each segment with its own counter, so that the list builder's atomics
+// spread over that many addresses.
+constexpr int kNearSegs = 64;
 
 // Capacity of the per-block partial-sum array of the residual norm.
 constexpr int kResPartials = 8192;

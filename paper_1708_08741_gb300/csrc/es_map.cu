@@ -273,40 +273,40 @@ __global__ void k_near_bits(int nx, int ny, int nz, int px, int py, int pz, uint
     st[c] = near ? (uint8_t)(ST_UNKNOWN | ST_NEAR) : (uint8_t)ST_UNKNOWN;
 }
 
-// Lists the near-boundary unknown cells of a level by colour ((x + y + z)
-// mod 2), for the smoother's separate near-cell pass.  The order within a
-// list depends on the atomics' order; the cells of one colour are updated
-// independently of each other, so results do not.
+// Lists the near-boundary unknown cells of a level, by colour, for the
+// separate near-cell passes of the smoother, residual and restriction.  A
+// row (y, z) goes to segment row mod kNearSegs of each colour; a warp walks its row 32 cells at a time with
+// one atomic per step on the segment's counter.  The order within a
+// segment depends on the atomics' order; the consumers write each cell's
+// value to its own place, so results do not.
 __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const uint8_t* __restrict__ st,
                                                    int cap, int* list, int* count) {
-    // warps stride over rows and walk each row 32 cells at a time: one
-    // atomic per warp step and colour, and the warp's cells stay in x order
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < ny * nz; row += warps) {
-        const int y = row % ny, z = row / ny;
-        for (int x0 = 0; x0 < nx; x0 += 32) {
-            const int x = x0 + lane;
-            const int c = x + nx * row;
-            bool take = false;
-            if (x < nx) {
-                const uint8_t s = st[c];
-                take = (s & ST_KIND) == ST_UNKNOWN && (s & ST_NEAR);
-            }
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= ny * nz) return;  // whole warps
+    const int seg = row % kNearSegs;
+    const int y = row % ny, z = row / ny;
+    for (int x0 = 0; x0 < nx; x0 += 32) {
+        const int x = x0 + lane;
+        bool take = false;
+        if (x < nx) {
+            const uint8_t s = st[x + nx * row];
+            take = (s & ST_KIND) == ST_UNKNOWN && (s & ST_NEAR);
+        }
 #pragma unroll
-            for (int colour = 0; colour < 2; colour++) {
-                const bool mine = take && ((x + y + z) & 1) == colour;
-                const unsigned m = __ballot_sync(0xffffffffu, mine);
-                if (!m) continue;
-                const int leader = __ffs(m) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&count[colour], __popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (mine) {
-                    const int i = base + __popc(m & lt);
-                    if (i < cap) list[colour * cap + i] = c;
-                }
+        for (int colour = 0; colour < 2; colour++) {
+            const bool mine = take && ((x + y + z) & 1) == colour;
+            const unsigned m = __ballot_sync(0xffffffffu, mine);
+            if (!m) continue;
+            const int k = colour * kNearSegs + seg;
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&count[k], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (mine) {
+                const int i = base + __popc(m & lt);
+                if (i < cap) list[(size_t)k * cap + i] = x + nx * row;
             }
         }
     }
@@ -315,14 +315,14 @@ __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const
 }  // namespace
 
 cudaError_t launch_near_lists(es_ctx* c) {
-    cudaError_t e = cudaMemsetAsync(c->near_count, 0, 2 * ES_MAXLEV * sizeof(int), c->stream);
+    cudaError_t e = cudaMemsetAsync(c->near_count, 0, 2 * kNearSegs * ES_MAXLEV * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     for (int l = 0; l < c->L; l++) {
         const int* n = c->ln[l];
         const int rows = n[1] * n[2];
         const int nb = (rows + 7) / 8;  // a warp per row: every row in flight at once
         k_near_list<<<nb, 256, 0, c->stream>>>(n[0], n[1], n[2], c->st[l], c->near_cap[l], c->near_list[l],
-                                                c->near_count + 2 * l);
+                                                c->near_count + 2 * kNearSegs * l);
         count(c);
     }
     return cudaGetLastError();

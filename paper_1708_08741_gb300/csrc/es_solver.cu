@@ -274,9 +274,11 @@ __global__ void __launch_bounds__(256) k_outer_residual_near_ff(Grid g, ff diag0
                                                                 const int* __restrict__ list,
                                                                 const int* __restrict__ count, int cap,
                                                                 float* __restrict__ r_out) {
-    const int n0 = count[0], n1 = count[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0 + n1; i += gridDim.x * blockDim.x) {
-        const int c = i < n0 ? list[i] : list[cap + i - n0];
+    // blockIdx.y: list segment
+    const int n = count[blockIdx.y];
+    const int* seg = list + (size_t)blockIdx.y * cap;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = seg[i];
         const int x = c % g.nx, yz = c / g.nx;
         r_out[c] = near_residual_ff(g, diag0, wall, pot_dir_mask, psi_hi, psi_lo, st0, owner, pbc, x, yz % g.ny,
                                     yz / g.ny);
@@ -571,16 +573,17 @@ __device__ __forceinline__ T near_gs(const Level<T>& L, const uint8_t* __restric
     return first ? omega * gs : ((T)1 - omega) * e[cidx] + omega * gs;
 }
 
-// The near-boundary unknown cells of one colour of a level, from the list
-// built at mapping (a grid-stride loop over the device-side count).
+// The near-boundary unknown cells of one colour of a level, from that
+// colour's segments of the level's near-cell list (blockIdx.y: segment).
 template <class T>
 __global__ void __launch_bounds__(256) k_smooth_near(Level<T> L, const uint8_t* __restrict__ st,
                                                      const T* __restrict__ rhs, T* __restrict__ e,
                                                      const int* __restrict__ list, const int* __restrict__ count,
-                                                     int first, T omega) {
-    const int n = *count;
+                                                     int cap, int first, T omega) {
+    const int n = count[blockIdx.y];
+    const int* seg = list + (size_t)blockIdx.y * cap;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int c = list[i];
+        const int c = seg[i];
         const int x = c % L.nx, yz = c / L.nx;
         e[c] = near_gs<T>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, first, omega);
     }
@@ -1049,9 +1052,11 @@ __global__ void __launch_bounds__(256) k_near_residual(Level<T> L, const uint8_t
                                                        const T* __restrict__ rhs, const T* __restrict__ e,
                                                        const int* __restrict__ list, const int* __restrict__ count,
                                                        int cap, T inv_h2, T* __restrict__ out) {
-    const int n0 = count[0], n1 = count[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0 + n1; i += gridDim.x * blockDim.x) {
-        const int c = i < n0 ? list[i] : list[cap + i - n0];
+    // blockIdx.y: list segment
+    const int n = count[blockIdx.y];
+    const int* seg = list + (size_t)blockIdx.y * cap;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = seg[i];
         const int x = c % L.nx, yz = c / L.nx;
         out[c] = near_residual<T>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, inv_h2);
     }
@@ -1437,24 +1442,25 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
         }
         const double b_first = nl * (1.5 * ts + 1.0), b_half = nl * (2.0 * ts + 1.0);
         if (vec) {
-            const int* cnt = c->near_count + 2 * l;
-            const int* list = c->near_list[l];
-            const int cap = c->near_cap[l];
-            const unsigned nb = (unsigned)(16 * c->n_sm);
+            const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, kNearSegs);
+            const int* cnt = c->near_count + 2 * kNearSegs * l;
+            const size_t half = (size_t)kNearSegs * c->near_cap[l];
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
                 k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
             }
             {
                 ProfScope ps(c, "smooth_near", l, 0.0);
-                k_smooth_near<T><<<nb, 256, 0, c->stream>>>(L, st, rhs, e, list, cnt, first, omega);
+                k_smooth_near<T><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l],
+                                                              first, omega);
             }
             {
                 ProfScope ps(c, "smooth_half", l, b_half);
                 k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
             }
             ProfScope ps(c, "smooth_near", l, 0.0);
-            k_smooth_near<T><<<nb, 256, 0, c->stream>>>(L, st, rhs, e, list + cap, cnt + 1, 0, omega);
+            k_smooth_near<T><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l] + half, cnt + kNearSegs,
+                                                          c->near_cap[l], 0, omega);
             count(c, 2);
         } else {
             {
@@ -1494,8 +1500,8 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     if (vec) {
         dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
         T* scratch = (T*)c->e2[l];  // (the fused sweep's second iterate; free between sweeps)
-        k_near_residual<T><<<16 * c->n_sm, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l],
-                                                                 c->near_count + 2 * l, c->near_cap[l],
+        k_near_residual<T><<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs), 256, 0, c->stream>>>(
+            L, st, rhs, e, c->near_list[l], c->near_count + 2 * kNearSegs * l, c->near_cap[l],
                                                                  (T)1 / L.h2, scratch);
         k_restrict_v<T><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1],
                                                       c->st[l + 1], (T*)c->rhs[l + 1]);
@@ -1549,7 +1555,8 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         int gz = kResPartials / (gx * gy);
         gz = gz < 1 ? 1 : (gz > c->g.nz ? c->g.nz : gz);
         const dim3 grd(gx, gy, gz), blk(32, 8);
-        k_outer_residual_near_ff<<<16 * c->n_sm, 256, 0, c->stream>>>(
+        k_outer_residual_near_ff<<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs), 256, 0,
+                                   c->stream>>>(
             c->g, ff_from_double(diag0), wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner, (const float2*)c->pbc,
             c->near_list[0], c->near_count, c->near_cap[0], (float*)c->rhs[0]);
         if (W == 4)
