@@ -108,6 +108,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     b += 3 * N * s;       // body force
     b += N * 8;           // psi: FP64, or float-float high and low parts
     b += N * 4 + N;       // owner, flags
+    b += N * 4;           // list of fluid cells next to obstacles (body force)
     size_t lv = 0;
     for (int l = 0; l < P->levels; l++) {
         long long Nl = (long long)(P->dims[0] >> l) * (P->dims[1] >> l) * (P->dims[2] >> l);
@@ -302,6 +303,12 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->partial = (double*)A((c->red_blocks > kResPartials ? c->red_blocks : kResPartials) * 8);
     c->d_norm = (double*)A(64);
     c->near_count = (int*)A(2 * kNearSegs * ES_MAXLEV * 4);
+    {
+        const long long rows = (long long)c->g.ny * c->g.nz;
+        c->bf_cap = (int)(((rows + kNearSegs - 1) / kNearSegs) * c->g.nx);
+        c->bf_list = (int*)A((size_t)kNearSegs * c->bf_cap * 4);
+        c->bf_count = (int*)A(kNearSegs * 4);
+    }
     c->d_status = (int*)A(64);
     if (!ok) {
         release(c);

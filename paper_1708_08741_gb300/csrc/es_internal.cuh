@@ -116,6 +116,9 @@ struct es_ctx {
     int* near_list[ES_MAXLEV];  // near-boundary unknown cells per level: red segments, then black ones
     int near_cap[ES_MAXLEV];    // capacity of one segment
     int* near_count;            // device: 2 kNearSegs counts per level (red segments, then black)
+    int* bf_list;               // fluid cells with a non-fluid D3Q19 neighbour (level 0), kNearSegs segments
+    int bf_cap;                 // capacity of one segment
+    int* bf_count;              // device: kNearSegs counts
     int n_sm;               // multiprocessors of the device
     int rb_blocks[2];       // resident fused-sweep blocks per SM (float, double); 0 = not queried
     double* partial;

@@ -312,6 +312,36 @@ __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const
     }
 }
 
+// Lists the fluid cells with a non-fluid D3Q19 neighbour (F_NEAR19), which
+// the body force treats with the D3Q7 ghost-value gradient, in kNearSegs
+// row segments as k_near_list does.
+__global__ void __launch_bounds__(256) k_near19_list(int nx, int ny, int nz, const uint8_t* __restrict__ flags,
+                                                     int cap, int* list, int* count) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= ny * nz) return;  // whole warps
+    const int seg = row % kNearSegs;
+    for (int x0 = 0; x0 < nx; x0 += 32) {
+        const int x = x0 + lane;
+        bool take = false;
+        if (x < nx) {
+            const uint8_t f = flags[x + nx * row];
+            take = (f & F_NEAR19) && !(f & F_SOLID);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&count[seg], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (take) {
+            const int i = base + __popc(m & lt);
+            if (i < cap) list[(size_t)seg * cap + i] = x + nx * row;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_near_lists(es_ctx* c) {
@@ -325,6 +355,11 @@ cudaError_t launch_near_lists(es_ctx* c) {
                                                 c->near_count + 2 * kNearSegs * l);
         count(c);
     }
+    e = cudaMemsetAsync(c->bf_count, 0, kNearSegs * sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    k_near19_list<<<(c->g.ny * c->g.nz + 7) / 8, 256, 0, c->stream>>>(c->g.nx, c->g.ny, c->g.nz, c->flags,
+                                                                      c->bf_cap, c->bf_list, c->bf_count);
+    count(c);
     return cudaGetLastError();
 }
 

@@ -597,12 +597,14 @@ __global__ void __launch_bounds__(256) k_smooth_near(Level<T> L, const uint8_t* 
 // other colour's values unchanged.  Same per-cell arithmetic as k_smooth;
 // requires nx % W == 0.  first != 0: the iterate starts at zero; nothing is
 // read and the other colour is written as zero.  Near-boundary cells are
-// skipped here and updated by k_smooth_near right after (same colour, so
-// the two passes do not depend on each other).
-template <class T, int W>
+// updated in the kernel (INLINE_NEAR) or skipped and updated by
+// k_smooth_near right after (same colour, so the two passes do not depend
+// on each other).
+template <class T, int W, bool INLINE_NEAR>
 __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
                                                   const T* __restrict__ rhs, T* __restrict__ e, int colour,
                                                   int first, T omega) {
+    static_assert(W == 4, "the near-cell path reads the span's states from one word");
     const int xs = W * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
     if (y >= L.ny) return;
@@ -658,8 +660,51 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
         span_update<T, 0, W>(L, inv_diag0, c, a, b, d, f, r, sw, omega, near_bits);
     else
         span_update<T, 1, W>(L, inv_diag0, c, a, b, d, f, r, sw, omega, near_bits);
-    // (near-boundary cells of the colour are left to k_smooth_near)
-    (void)near_bits;
+    if constexpr (INLINE_NEAR) {
+        // Near-boundary cells of the colour, on small levels (where a separate
+        // pass would cost more in launch time than it saves): the neighbour
+        // values are already in registers; the neighbours' state bytes decide
+        // which of them enter the sum and how the diagonal moves (Sec. 5.4:
+        // Dirichlet +1, Neumann -1); a face beyond a non-periodic boundary
+        // takes the domain condition.  Only warps holding such a cell load
+        // the states.
+        if (__any_sync(0xffffffffu, near_bits != 0)) {
+            const int xq2 = lane_on ? xs : 0;
+            const unsigned su = *reinterpret_cast<const unsigned*>(st + rym + xq2);
+            const unsigned sd = *reinterpret_cast<const unsigned*>(st + ryp + xq2);
+            const unsigned sm = *reinterpret_cast<const unsigned*>(st + rzm + xq2);
+            const unsigned sp = *reinterpret_cast<const unsigned*>(st + rzp + xq2);
+            const unsigned sl = st[row + (lane_on ? xl : 0)], sr = st[row + (lane_on ? xr : 0)];
+            const bool wy0 = !L.per[1] && y == 0, wy1 = !L.per[1] && y == ny - 1;
+            const bool wz0 = !L.per[2] && z == 0, wz1 = !L.per[2] && z == nz - 1;
+            auto wd = [&](int f) { return L.pot_bc[f] == ES_POT_DIRICHLET ? (T)1 : (T)-1; };
+#pragma unroll
+            for (int i = 0; i < W; i++) {
+                if (!((near_bits >> i) & 1u)) continue;
+                const int gx = xs + i;
+                T dg = L.diag0, o = (T)0;
+                auto face = [&](bool wall, T wdv, unsigned kind, T v) {
+                    if (wall)
+                        dg += wdv;
+                    else if (kind == ST_UNKNOWN)
+                        o += v;
+                    else
+                        dg += kind == ST_DIR ? (T)1 : (T)-1;
+                };
+                face(!L.per[0] && gx == 0, wd(0), (i == 0 ? sl : (sw.x >> (8 * (i - 1)))) & ST_KIND, c[i]);
+                face(!L.per[0] && gx == nx - 1, wd(1), (i == W - 1 ? sr : (sw.x >> (8 * (i + 1)))) & ST_KIND,
+                     c[i + 2]);
+                face(wy0, wd(2), (su >> (8 * i)) & ST_KIND, a[i]);
+                face(wy1, wd(3), (sd >> (8 * i)) & ST_KIND, b[i]);
+                face(wz0, wd(4), (sm >> (8 * i)) & ST_KIND, d[i]);
+                face(wz1, wd(5), (sp >> (8 * i)) & ST_KIND, f[i]);
+                const T gs = (L.h2 * r[i] + o) / dg;
+                c[i + 1] = ((T)1 - omega) * c[i + 1] + omega * gs;
+            }
+        }
+    } else {
+        (void)near_bits;  // left to k_smooth_near
+    }
     if (lane_on) {
 #pragma unroll
         for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[1 + v], c[2 + v], c[3 + v], c[4 + v]);
@@ -1339,6 +1384,109 @@ __global__ void __launch_bounds__(128) k_body_force(Grid g, Solver s, P Ex, P Ey
     fb[2LL * g.N + c] = (S)f2;
 }
 
+// Body force of the reduced forms, 4-cell spans (16-byte loads of the nine
+// rows the D3Q19 gradient touches).  Interior fluid cells take the
+// isotropic gradient (Eq. ElPotGradComp, pairwise as in k_body_force);
+// obstacle cells get 0; cells with a non-fluid D3Q19 neighbour are written
+// again right after by k_body_force_near with the D3Q7 ghost-value gradient.
+__global__ void __launch_bounds__(256) k_body_force_v(Grid g, float Ex, float Ey, float Ez, float k2e,
+                                                      const float* __restrict__ psi,
+                                                      const uint8_t* __restrict__ flags, float* __restrict__ fb) {
+    const int xs = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    if (xs >= g.nx || y >= g.ny) return;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    // periodic wrap; beyond a wall the cells are near cells (rewritten), so
+    // any valid index does
+    const int xl = xs == 0 ? (g.per[0] ? nx - 1 : 0) : xs - 1;
+    const int xr = xs + 4 == nx ? (g.per[0] ? 0 : nx - 1) : xs + 4;
+    const int ym = y == 0 ? (g.per[1] ? ny - 1 : 0) : y - 1, yp = y == ny - 1 ? (g.per[1] ? 0 : y) : y + 1;
+    const int zm = z == 0 ? (g.per[2] ? nz - 1 : 0) : z - 1, zp = z == nz - 1 ? (g.per[2] ? 0 : z) : z + 1;
+    auto rowp = [&](int yy, int zz) { return psi + nx * (yy + ny * zz); };
+    auto span6 = [&](const float* r, float (&v)[6]) {
+        const float4 q = *reinterpret_cast<const float4*>(r + xs);
+        v[0] = r[xl];
+        v[1] = q.x;
+        v[2] = q.y;
+        v[3] = q.z;
+        v[4] = q.w;
+        v[5] = r[xr];
+    };
+    auto span4 = [&](const float* r, float (&v)[4]) {
+        const float4 q = *reinterpret_cast<const float4*>(r + xs);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    };
+    float c0[6], ym0[6], yp0[6], zm0[6], zp0[6], mm[4], pm[4], mp[4], pp[4];
+    span6(rowp(y, z), c0);
+    span6(rowp(ym, z), ym0);
+    span6(rowp(yp, z), yp0);
+    span6(rowp(y, zm), zm0);
+    span6(rowp(y, zp), zp0);
+    span4(rowp(ym, zm), mm);  // (y-1, z-1)
+    span4(rowp(yp, zm), pm);  // (y+1, z-1)
+    span4(rowp(ym, zp), mp);  // (y-1, z+1)
+    span4(rowp(yp, zp), pp);  // (y+1, z+1)
+    const int row = nx * (y + ny * z);
+    const uchar4 f4 = *reinterpret_cast<const uchar4*>(flags + row + xs);
+    const uint8_t fl[4] = {f4.x, f4.y, f4.z, f4.w};
+    const float a = (float)(3.0 / 18.0), b = (float)(3.0 / 36.0);
+    float o0[4], o1[4], o2[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int j = i + 1;  // index in the 6-wide rows
+        float g0 = a * (c0[j + 1] - c0[j - 1]);
+        float g1 = a * (yp0[j] - ym0[j]);
+        float g2 = a * (zp0[j] - zm0[j]);
+        const float dxy1 = b * (yp0[j + 1] - ym0[j - 1]), dxy2 = b * (ym0[j + 1] - yp0[j - 1]);
+        const float dxz1 = b * (zp0[j + 1] - zm0[j - 1]), dxz2 = b * (zm0[j + 1] - zp0[j - 1]);
+        const float dyz1 = b * (pp[i] - mm[i]), dyz2 = b * (pm[i] - mp[i]);
+        g0 += dxy1 + dxy2 + dxz1 + dxz2;
+        g1 += dxy1 - dxy2 + dyz1 + dyz2;
+        g2 += dxz1 - dxz2 + dyz1 - dyz2;
+        const float rho_e = -k2e * c0[j];
+        const bool solid = fl[i] & F_SOLID;
+        o0[i] = solid ? 0.0f : rho_e * (Ex - g0);
+        o1[i] = solid ? 0.0f : rho_e * (Ey - g1);
+        o2[i] = solid ? 0.0f : rho_e * (Ez - g2);
+    }
+    const size_t N = (size_t)g.N;
+    *reinterpret_cast<float4*>(fb + row + xs) = make_float4(o0[0], o0[1], o0[2], o0[3]);
+    *reinterpret_cast<float4*>(fb + N + row + xs) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+    *reinterpret_cast<float4*>(fb + 2 * N + row + xs) = make_float4(o2[0], o2[1], o2[2], o2[3]);
+}
+
+// The fluid cells with a non-fluid D3Q19 neighbour: D3Q7 gradient with the
+// ghost values of face_value_f (list of cells, kNearSegs segments).
+__global__ void __launch_bounds__(256) k_body_force_near(Grid g, Solver s, float Ex, float Ey, float Ez, float k2e,
+                                                         const float* __restrict__ psi,
+                                                         const int32_t* __restrict__ owner,
+                                                         const uint8_t* __restrict__ st0,
+                                                         const float2* __restrict__ pbc, WallF wall2,
+                                                         const int* __restrict__ list,
+                                                         const int* __restrict__ count, int cap,
+                                                         float* __restrict__ fb) {
+    const int n = count[blockIdx.y];
+    const int* seg = list + (size_t)blockIdx.y * cap;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = seg[i];
+        const int x = c % g.nx, yz = c / g.nx, y = yz % g.ny, z = yz / g.ny;
+        const float pc = psi[c];
+        const float g0 = 0.5f * (face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 0, 1) -
+                                 face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 0, -1));
+        const float g1 = 0.5f * (face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 1, 1) -
+                                 face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 1, -1));
+        const float g2 = 0.5f * (face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 2, 1) -
+                                 face_value_f(g, s, wall2, psi, owner, st0, pbc, x, y, z, pc, 2, -1));
+        const float rho_e = -k2e * pc;
+        fb[c] = rho_e * (Ex - g0);
+        fb[(size_t)g.N + c] = rho_e * (Ey - g1);
+        fb[2 * (size_t)g.N + c] = rho_e * (Ez - g2);
+    }
+}
+
 template <class T>
 Level<T> level_desc(const es_ctx* c, int l) {
     Level<T> L;
@@ -1357,6 +1505,10 @@ size_t coarse_smem_bytes(const es_ctx* c, size_t tsize) {
     size_t n = (size_t)c->ln[c->L - 1][0] * c->ln[c->L - 1][1] * c->ln[c->L - 1][2];
     return n * (2 * tsize + 1);
 }
+
+// Levels up to this many cells update their near-boundary cells inside the
+// smoothing kernel; larger ones in a separate pass over the near-cell list.
+constexpr int kInlineNearCells = 1 << 21;
 
 // Launch shape of the fused sweep: 128 x 12 output tiles, and the z extent
 // cut into chunks so that the blocks fill whole waves of the resident-block
@@ -1442,12 +1594,22 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
         }
         const double b_first = nl * (1.5 * ts + 1.0), b_half = nl * (2.0 * ts + 1.0);
         if (vec) {
+            if (Nl <= kInlineNearCells) {
+                {
+                    ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
+                    k_smooth_v<T, W, true><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
+                }
+                ProfScope ps(c, "smooth_half", l, b_half);
+                k_smooth_v<T, W, true><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
+                count(c, 2);
+                return;
+            }
             const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, kNearSegs);
             const int* cnt = c->near_count + 2 * kNearSegs * l;
             const size_t half = (size_t)kNearSegs * c->near_cap[l];
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
-                k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
+                k_smooth_v<T, W, false><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
             }
             {
                 ProfScope ps(c, "smooth_near", l, 0.0);
@@ -1456,7 +1618,7 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
             }
             {
                 ProfScope ps(c, "smooth_half", l, b_half);
-                k_smooth_v<T, W><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
+                k_smooth_v<T, W, false><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
             }
             ProfScope ps(c, "smooth_near", l, 0.0);
             k_smooth_near<T><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l] + half, cnt + kNearSegs,
@@ -1629,7 +1791,15 @@ cudaError_t launch_body_force(es_ctx* c) {
     const double k2e = c->S.kappa * c->S.kappa * c->S.eps;
     WallF wall2;
     for (int f = 0; f < 6; f++) wall2.v2[f] = (float)(2.0 * c->S.pot_val[f]);
-    if (mixed(c))
+    if (mixed(c) && g.nx % 4 == 0) {
+        dim3 vgrd((g.nx / 4 + 31) / 32, (g.ny + 7) / 8, g.nz);
+        k_body_force_v<<<vgrd, dim3(32, 8), 0, c->stream>>>(g, (float)E[0], (float)E[1], (float)E[2], (float)k2e,
+                                                            c->psi32, c->flags, (float*)c->fb);
+        k_body_force_near<<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * 4, kNearSegs), 256, 0, c->stream>>>(
+            g, c->S, (float)E[0], (float)E[1], (float)E[2], (float)k2e, c->psi32, c->owner, c->st[0],
+            (const float2*)c->pbc, wall2, c->bf_list, c->bf_count, c->bf_cap, (float*)c->fb);
+        count(c);
+    } else if (mixed(c))
         k_body_force<float, float><<<grd, blk, 0, c->stream>>>(g, c->S, (float)E[0], (float)E[1], (float)E[2],
                                                                (float)k2e, c->psi32, c->flags, c->owner, c->part,
                                                                c->kind, c->st[0], (const float2*)c->pbc, wall2,

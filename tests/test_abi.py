@@ -87,12 +87,12 @@ def test_device_bytes_matches_layout(lib):
     b64 = es.device_bytes(wl, es.ES_FP64)
     N = 512 ** 3
     # two PDF fields dominate: 2 x 19 x s_pdf bytes per cell; the rest is the
-    # body force (3s), psi (8: FP64 or float-float), owner and flags (5) and,
-    # per multigrid cell (x 8/7 levels), three s-byte fields, a state byte and
-    # a 4-byte near-cell list entry, with s the arithmetic type (4 in both
-    # reduced forms)
-    rest32 = (3 * 4 + 8 + 5 + (3 * 4 + 1 + 4) * 8 / 7) * N
-    rest64 = (3 * 8 + 8 + 5 + (3 * 8 + 1 + 4) * 8 / 7) * N
+    # body force (3s), psi (8: FP64 or float-float), owner and flags (5), the
+    # list of fluid cells next to obstacles (4) and, per multigrid cell (x 8/7
+    # levels), three s-byte fields, a state byte and a 4-byte near-cell list
+    # entry, with s the arithmetic type (4 in both reduced forms)
+    rest32 = (3 * 4 + 8 + 5 + 4 + (3 * 4 + 1 + 4) * 8 / 7) * N
+    rest64 = (3 * 8 + 8 + 5 + 4 + (3 * 8 + 1 + 4) * 8 / 7) * N
     assert 2 * 19 * 2 * N + rest32 < b16 < 2 * 19 * 2 * N + rest32 + 0.1 * N
     assert 2 * 19 * 4 * N + rest32 < b32 < 2 * 19 * 4 * N + rest32 + 0.1 * N
     assert 2 * 19 * 8 * N + rest64 < b64 < 2 * 19 * 8 * N + rest64 + 0.1 * N
