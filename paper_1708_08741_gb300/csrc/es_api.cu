@@ -380,6 +380,10 @@ int es_map_particles(es_ctx* c) {
     return ES_OK;
 }
 
+// MIXED32/16: the FP32 V-cycles per correction are predicted to bring the
+// residual to this fraction of the tolerance (a margin for the rate estimate).
+constexpr double kCycleTarget = 0.85;
+
 int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
     if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
     double norm;
@@ -417,10 +421,11 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
         // V-cycles per correction: one in the FP64 form (the oracle's
         // iteration); in MIXED32 as many FP32 cycles, warm-started on the
         // same defect, as the running rate estimate says will bring the
-        // residual to half the tolerance (at most 6, i.e. within FP32 reach)
+        // residual below kCycleTarget x tolerance (at most 6, i.e. within
+        // FP32 reach)
         int k = 1;
         if (mixed(c) && forced_cycles < 0) {
-            double want = std::log(0.5 * c->tol / norm) / std::log(c->mg_rate);
+            double want = std::log(kCycleTarget * c->tol / norm) / std::log(c->mg_rate);
             k = (int)std::ceil(want);
             k = k < 1 ? 1 : (k > 6 ? 6 : k);
             if (k > c->P.max_cycles - cycles) k = c->P.max_cycles - cycles;

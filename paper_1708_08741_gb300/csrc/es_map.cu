@@ -342,12 +342,83 @@ __global__ void __launch_bounds__(256) k_near19_list(int nx, int ny, int nz, con
     }
 }
 
+// Level 0 in one pass: both lists (near-boundary unknown cells by colour,
+// and fluid cells next to obstacles) from 4 cells per lane (x extent a
+// multiple of 4), with warp prefix sums so that each warp step costs one
+// atomic per list.
+__device__ __forceinline__ int warp_excl_scan(int v, int& total) {
+    const int lane = threadIdx.x & 31;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - v;
+}
+
+__global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const uint8_t* __restrict__ st,
+                                                  const uint8_t* __restrict__ flags, int cap, int* list,
+                                                  int* count, int bf_cap, int* bf_list, int* bf_count) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= ny * nz) return;  // whole warps
+    const int seg = row % kNearSegs;
+    const int y = row % ny, z = row / ny;
+    for (int x0 = 0; x0 < nx; x0 += 128) {
+        const int xs = x0 + 4 * lane;
+        unsigned sw = 0x02020202u, fw = 0x01010101u;  // (Neumann / obstacle: not listed)
+        if (xs < nx) {
+            sw = *reinterpret_cast<const unsigned*>(st + xs + nx * row);
+            fw = *reinterpret_cast<const unsigned*>(flags + xs + nx * row);
+        }
+        unsigned m_near[2] = {0, 0}, m_bf = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const unsigned s8 = (sw >> (8 * i)) & 0xFFu, f8 = (fw >> (8 * i)) & 0xFFu;
+            if ((s8 & ST_KIND) == ST_UNKNOWN && (s8 & ST_NEAR)) m_near[(xs + i + y + z) & 1] |= 1u << i;
+            if ((f8 & F_NEAR19) && !(f8 & F_SOLID)) m_bf |= 1u << i;
+        }
+#pragma unroll
+        for (int t = 0; t < 3; t++) {
+            const unsigned m = t < 2 ? m_near[t] : m_bf;
+            int total;
+            const int excl = warp_excl_scan(__popc(m), total);
+            if (total == 0) continue;
+            int* cnt = t < 2 ? &count[t * kNearSegs + seg] : &bf_count[seg];
+            int base = 0;
+            if (lane == 0) base = atomicAdd(cnt, total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int* out = t < 2 ? list + (size_t)(t * kNearSegs + seg) * cap : bf_list + (size_t)seg * bf_cap;
+            const int c_out = t < 2 ? cap : bf_cap;
+            int k = base + excl;
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if ((m >> i) & 1u) {
+                    if (k < c_out) out[k] = xs + i + nx * row;
+                    k++;
+                }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_near_lists(es_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->near_count, 0, 2 * kNearSegs * ES_MAXLEV * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
-    for (int l = 0; l < c->L; l++) {
+    e = cudaMemsetAsync(c->bf_count, 0, kNearSegs * sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    int l0 = 0;
+    if (c->g.nx % 4 == 0) {
+        k_lists_l0<<<(c->g.ny * c->g.nz + 7) / 8, 256, 0, c->stream>>>(c->g.nx, c->g.ny, c->g.nz, c->st[0], c->flags,
+                                                                      c->near_cap[0], c->near_list[0], c->near_count,
+                                                                      c->bf_cap, c->bf_list, c->bf_count);
+        count(c);
+        l0 = 1;
+    }
+    for (int l = l0; l < c->L; l++) {
         const int* n = c->ln[l];
         const int rows = n[1] * n[2];
         const int nb = (rows + 7) / 8;  // a warp per row: every row in flight at once
@@ -355,11 +426,11 @@ cudaError_t launch_near_lists(es_ctx* c) {
                                                 c->near_count + 2 * kNearSegs * l);
         count(c);
     }
-    e = cudaMemsetAsync(c->bf_count, 0, kNearSegs * sizeof(int), c->stream);
-    if (e != cudaSuccess) return e;
-    k_near19_list<<<(c->g.ny * c->g.nz + 7) / 8, 256, 0, c->stream>>>(c->g.nx, c->g.ny, c->g.nz, c->flags,
-                                                                      c->bf_cap, c->bf_list, c->bf_count);
-    count(c);
+    if (l0 == 0) {
+        k_near19_list<<<(c->g.ny * c->g.nz + 7) / 8, 256, 0, c->stream>>>(c->g.nx, c->g.ny, c->g.nz, c->flags,
+                                                                          c->bf_cap, c->bf_list, c->bf_count);
+        count(c);
+    }
     return cudaGetLastError();
 }
 
