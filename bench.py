@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--max-run-steps", type=int, default=1000, help="serving: step cap per run")
     ap.add_argument("--smoother", choices=["fused", "two_pass"], default="two_pass",
                     help="execution of a red-black sweep (same arithmetic)")
+    ap.add_argument("--mg-storage", choices=["native", "fp16"], default="native",
+                    help="storage of the finest level's multigrid correction")
     return ap.parse_args()
 
 
@@ -210,7 +212,8 @@ def run_ours(args):
     wl = W.suspension(n=args.n, n_spheres=int(round(2880 * (args.n / 512) ** 3)),
                       levels=6 if args.n % 32 == 0 else 4)
     smoother = es.ES_SMOOTH_FUSED if args.smoother == "fused" else es.ES_SMOOTH_TWO_PASS
-    sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev), overrides=dict(smoother=smoother))
+    mg = es.ES_MG_FP16 if args.mg_storage == "fp16" else es.ES_MG_NATIVE
+    sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev), overrides=dict(smoother=smoother, mg_storage=mg))
     stream = sim.stream
     N = wl.n_cells
 
@@ -317,7 +320,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"suspension {args.n}^3 periodic, {wl.n_particles} charged spheres R=5, "
-                               f"lambda_D=4, E=1e-3, MIXED32, {sim.params.levels}-level V(2,2) to RES_RF {wl.res_rf:g}",
+                               f"lambda_D=4, E=1e-3, MIXED32, {sim.params.levels}-level V(2,2) to RES_RF {wl.res_rf:g}"
+                               + (", FP16 finest-level correction" if mg == es.ES_MG_FP16 else ""),
                    "cells": N, "fluid_cells": n_fluid, "parallelism": f"replicas x{world}",
                    "l2_policy": "inputs larger than L2 (PDF fields 20 GB)"},
         "mflups": n_fluid * args.steps * world / t_all / 1e6,

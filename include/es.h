@@ -103,6 +103,8 @@ typedef struct {
     int max_cycles;     /* cycle cap per es_potential_solve                        */
     int smoother;       /* ES_SMOOTH_TWO_PASS (0, default) or ES_SMOOTH_FUSED: how a
                            red-black sweep is executed; both compute the same sweep */
+    int mg_storage;     /* ES_MG_NATIVE (0, default) or ES_MG_FP16: storage of the
+                           finest level's multigrid correction (see below)        */
 } es_params;
 
 /* Execution of one red-black Gauss-Seidel sweep (same arithmetic either way):
@@ -110,6 +112,17 @@ typedef struct {
    one pass over the level (out of place). */
 #define ES_SMOOTH_TWO_PASS 0
 #define ES_SMOOTH_FUSED 1
+
+/* Storage of the finest level's correction e inside the V-cycle.  NATIVE:
+   the solver's arithmetic type (double in ES_FP64, float otherwise).  FP16
+   (reduced precisions only; two-pass smoother; dims[0] % 4 == 0; levels >=
+   2): e is held as FP16 values s * e with s = sqrt(N) / ||r|| fixed for the
+   V-cycles of one correction, and every operation still computes in float.
+   The outer defect correction forms the residual of psi in float-float, so
+   the rounding of the stored correction only slows the outer iteration; it
+   does not move the converged potential. */
+#define ES_MG_NATIVE 0
+#define ES_MG_FP16 1
 
 typedef struct {
     double x[3]; /* centre                  */

@@ -33,6 +33,8 @@ ES_MIXED32 = 1
 ES_MIXED16 = 2
 ES_SMOOTH_TWO_PASS = 0
 ES_SMOOTH_FUSED = 1
+ES_MG_NATIVE = 0
+ES_MG_FP16 = 1
 
 FIELD_PSI = 0
 FIELD_RHO = 1
@@ -72,6 +74,7 @@ class Params(ctypes.Structure):
         ("res_rf", ctypes.c_double),
         ("max_cycles", ctypes.c_int),
         ("smoother", ctypes.c_int),
+        ("mg_storage", ctypes.c_int),
     ]
 
 

@@ -44,6 +44,14 @@ int validate(const es_params* P, const es_particle* parts, int n, std::string& w
         why = "smoother must be ES_SMOOTH_FUSED or ES_SMOOTH_TWO_PASS";
         return ES_EINVAL;
     }
+    if (P->mg_storage != ES_MG_NATIVE && P->mg_storage != ES_MG_FP16)
+        return why = "mg_storage must be ES_MG_NATIVE or ES_MG_FP16", ES_EINVAL;
+    if (P->mg_storage == ES_MG_FP16) {
+        if (P->precision == ES_FP64) return why = "ES_MG_FP16 needs a reduced precision", ES_EINVAL;
+        if (P->smoother != ES_SMOOTH_TWO_PASS) return why = "ES_MG_FP16 needs the two-pass smoother", ES_EINVAL;
+        if (P->dims[0] % 4 != 0) return why = "ES_MG_FP16 needs dims[0] % 4 == 0", ES_EINVAL;
+        if (P->levels < 2) return why = "ES_MG_FP16 needs levels >= 2", ES_EINVAL;
+    }
     if (P->nu1 < 0 || P->nu2 < 0 || P->coarse_sweeps < 0 || P->max_cycles < 0)
         return why = "negative sweep or cycle count", ES_EINVAL;
     if (!(P->omega > 0.0 && P->omega < 2.0)) return why = "omega must be in (0, 2)", ES_EINVAL;
@@ -113,6 +121,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     for (int l = 0; l < P->levels; l++) {
         long long Nl = (long long)(P->dims[0] >> l) * (P->dims[1] >> l) * (P->dims[2] >> l);
         lv += Nl * (1 + 3 * s + 4);  // states, e, e2, rhs, near-cell lists (+ one row per segment)
+        if (l == 0 && P->mg_storage == ES_MG_FP16) lv -= Nl * (s - 2);  // e as FP16
     }
     if (per_level) *per_level = lv;
     b += lv;
@@ -261,6 +270,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     }
     c->red_blocks = 4 * c->n_sm;
     c->mg_rate = 0.15;
+    c->e_scale = 1.0f;
 
     const long long N = c->g.N;
     const size_t s = mixed(c) ? 4 : 8;
@@ -282,7 +292,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     for (int l = 0; l < c->L; l++) {
         long long Nl = (long long)c->ln[l][0] * c->ln[l][1] * c->ln[l][2];
         c->st[l] = (uint8_t*)A(Nl);
-        c->e[l] = A(Nl * s);
+        c->e[l] = A(Nl * (l == 0 && c->P.mg_storage == ES_MG_FP16 ? 2 : s));
         c->e2[l] = A(Nl * s);
         {
             const long long rows = (long long)c->ln[l][1] * c->ln[l][2];
@@ -429,6 +439,12 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
             k = (int)std::ceil(want);
             k = k < 1 ? 1 : (k > 6 ? 6 : k);
             if (k > c->P.max_cycles - cycles) k = c->P.max_cycles - cycles;
+        }
+        if (c->P.mg_storage == ES_MG_FP16) {
+            // the FP16 correction holds s * e, s = sqrt(N) / ||r|| (the
+            // residual's RMS scaled to one), fixed for this correction
+            const double sc = norm > 0.0 ? std::sqrt((double)c->g.N) / norm : 1.0;
+            c->e_scale = (float)(sc < 1e-30 ? 1e-30 : (sc > 1e30 ? 1e30 : sc));
         }
         for (int j = 0; j < k; j++) ES_CUDA(c, launch_vcycle(c, j > 0));
         ES_CUDA(c, launch_correct(c));

@@ -130,6 +130,7 @@ struct es_ctx {
     double tol;
     int have_tol;
     double mg_rate;  // running estimate of the residual reduction per V-cycle
+    float e_scale;   // ES_MG_FP16: scale of the finest level's stored correction
     double lambda_e, lambda_o;
     size_t bytes;
     unsigned long long launches;  // kernels launched by this context

@@ -18,6 +18,8 @@
 // pipe with 1/64 of the FP32 rate, so the FP32 kernels here carry no double
 // operand at all: level constants come in as T, cell indices are 32-bit
 // (N < 2^31), and the MIXED32 body force reads a float copy of psi.
+#include <type_traits>
+
 #include "es_device.cuh"
 
 namespace es {
@@ -423,11 +425,83 @@ __global__ void k_finalize_norm(const double* partial, int n, double* out) {
     if (threadIdx.x == 0) out[0] = sqrt(tot);
 }
 
+template <class T>
+struct Q4 {
+    T v0, v1, v2, v3;
+};
+__device__ __forceinline__ Q4<float> vld(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Q4<double> vld(const double* p) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *(reinterpret_cast<const double2*>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void vst(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void vst(double* p, double a, double b, double c, double d) {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    *(reinterpret_cast<double2*>(p) + 1) = make_double2(c, d);
+}
+#define ES_VLD(arr, off, ptr)      \
+    do {                           \
+        const auto q_ = vld(ptr);  \
+        arr[(off) + 0] = q_.v0;    \
+        arr[(off) + 1] = q_.v1;    \
+        arr[(off) + 2] = q_.v2;    \
+        arr[(off) + 3] = q_.v3;    \
+    } while (0)
+
+// Access to a level's correction e stored as E: the arithmetic type T
+// itself, or (finest level, ES_MG_FP16) FP16 holding s * e, with the scale
+// s = sqrt(N) / ||r|| set per correction so that the stored values sit near
+// 1 in FP16's normal range; loads return e in T.
+template <class T, class E>
+struct EAcc;
+template <class T>
+struct EAcc<T, T> {
+    T s, is;
+    __device__ __forceinline__ T ld(const T* p) const { return *p; }
+    __device__ __forceinline__ void st(T* p, T v) const { *p = v; }
+    __device__ __forceinline__ Q4<T> ld4(const T* p) const { return vld(p); }
+    __device__ __forceinline__ void st4(T* p, T a, T b, T c, T d) const { vst(p, a, b, c, d); }
+};
+template <>
+struct EAcc<float, __half> {
+    float s, is;
+    __device__ __forceinline__ float ld(const __half* p) const { return __half2float(*p) * is; }
+    __device__ __forceinline__ void st(__half* p, float v) const { *p = __float2half_rn(v * s); }
+    __device__ __forceinline__ Q4<float> ld4(const __half* p) const {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        return {a.x * is, a.y * is, b.x * is, b.y * is};
+    }
+    __device__ __forceinline__ void st4(__half* p, float a, float b, float c, float d) const {
+        const __half2 h0 = __floats2half2_rn(a * s, b * s), h1 = __floats2half2_rn(c * s, d * s);
+        uint2 u;
+        u.x = *reinterpret_cast<const unsigned*>(&h0);
+        u.y = *reinterpret_cast<const unsigned*>(&h1);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+};
+#define ES_ELD(acc, arr, off, ptr)    \
+    do {                              \
+        const auto q_ = (acc).ld4(ptr); \
+        arr[(off) + 0] = q_.v0;       \
+        arr[(off) + 1] = q_.v1;       \
+        arr[(off) + 2] = q_.v2;       \
+        arr[(off) + 3] = q_.v3;       \
+    } while (0)
+
 // Diagonal and off-diagonal sum of level l at an unknown cell.  With
 // READ = false only the diagonal is formed (off = 0, e is not touched).
-template <class T, bool READ = true>
-__device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* st, const T* e, int x, int y,
-                                              int z, uint8_t s, T& diag, T& off) {
+template <class T, bool READ = true, class E = T>
+__device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* st, const E* e, int x, int y,
+                                              int z, uint8_t s, T& diag, T& off,
+                                              const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}) {
     const int nx = L.nx, nxy = L.nx * L.ny;
     const int c = x + nx * y + nxy * z;
     if (!(s & ST_NEAR)) {
@@ -439,12 +513,12 @@ __device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* 
         const int xm = (x == 0 ? nx - 1 : x - 1) - x, xp = (x == nx - 1 ? 0 : x + 1) - x;
         const int ym = (y == 0 ? L.ny - 1 : y - 1) - y, yp = (y == L.ny - 1 ? 0 : y + 1) - y;
         const int zm = (z == 0 ? L.nz - 1 : z - 1) - z, zp = (z == L.nz - 1 ? 0 : z + 1) - z;
-        T o = e[c + xm];
-        o += e[c + xp];
-        o += e[c + ym * nx];
-        o += e[c + yp * nx];
-        o += e[c + zm * nxy];
-        o += e[c + zp * nxy];
+        T o = A.ld(e + c + xm);
+        o += A.ld(e + c + xp);
+        o += A.ld(e + c + ym * nx);
+        o += A.ld(e + c + yp * nx);
+        o += A.ld(e + c + zm * nxy);
+        o += A.ld(e + c + zp * nxy);
         off = o;
         return;
     }
@@ -464,7 +538,7 @@ __device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* 
             const int nb = c + (p - v[a]) * stride[a];
             const uint8_t k = st[nb] & ST_KIND;
             if (k == ST_UNKNOWN) {
-                if (READ) o += e[nb];
+                if (READ) o += A.ld(e + nb);
             } else {
                 dg += (k == ST_DIR) ? (T)1 : (T)-1;
             }
@@ -501,34 +575,6 @@ __global__ void __launch_bounds__(128) k_smooth(Level<T> L, const uint8_t* __res
     e[c] = first ? omega * gs : ((T)1 - omega) * e[c] + omega * gs;
 }
 
-template <class T>
-struct Q4 {
-    T v0, v1, v2, v3;
-};
-__device__ __forceinline__ Q4<float> vld(const float* p) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    return {v.x, v.y, v.z, v.w};
-}
-__device__ __forceinline__ Q4<double> vld(const double* p) {
-    const double2 a = *reinterpret_cast<const double2*>(p);
-    const double2 b = *(reinterpret_cast<const double2*>(p) + 1);
-    return {a.x, a.y, b.x, b.y};
-}
-__device__ __forceinline__ void vst(float* p, float a, float b, float c, float d) {
-    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
-}
-__device__ __forceinline__ void vst(double* p, double a, double b, double c, double d) {
-    *reinterpret_cast<double2*>(p) = make_double2(a, b);
-    *(reinterpret_cast<double2*>(p) + 1) = make_double2(c, d);
-}
-#define ES_VLD(arr, off, ptr)      \
-    do {                           \
-        const auto q_ = vld(ptr);  \
-        arr[(off) + 0] = q_.v0;    \
-        arr[(off) + 1] = q_.v1;    \
-        arr[(off) + 2] = q_.v2;    \
-        arr[(off) + 3] = q_.v3;    \
-    } while (0)
 
 // The update of the interior cells xs + P0 + 2j of a span (indices known at
 // compile time, so the span arrays stay in registers); the near-boundary
@@ -559,33 +605,34 @@ __device__ __forceinline__ void span_update(const Level<T>& L, T inv_diag0, T (&
 
 // Gauss-Seidel value of one near-boundary unknown cell of level l, read
 // from global memory (the boundary faces per Sec. 5.4 as level_stencil).
-template <class T>
+template <class T, class E = T>
 __device__ __forceinline__ T near_gs(const Level<T>& L, const uint8_t* __restrict__ st, const T* __restrict__ rhs,
-                                     const T* e, int x, int y, int z, int first, T omega) {
+                                     const E* e, int x, int y, int z, int first, T omega,
+                                     const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}) {
     const int cidx = x + L.nx * (y + L.ny * z);
     const uint8_t s = st[cidx];
     T diag, off;
     if (first)
-        level_stencil<T, false>(L, st, e, x, y, z, s, diag, off);
+        level_stencil<T, false, E>(L, st, e, x, y, z, s, diag, off, A);
     else
-        level_stencil<T, true>(L, st, e, x, y, z, s, diag, off);
+        level_stencil<T, true, E>(L, st, e, x, y, z, s, diag, off, A);
     const T gs = (L.h2 * rhs[cidx] + off) / diag;
-    return first ? omega * gs : ((T)1 - omega) * e[cidx] + omega * gs;
+    return first ? omega * gs : ((T)1 - omega) * A.ld(e + cidx) + omega * gs;
 }
 
 // The near-boundary unknown cells of one colour of a level, from that
 // colour's segments of the level's near-cell list (blockIdx.y: segment).
-template <class T>
+template <class T, class E>
 __global__ void __launch_bounds__(256) k_smooth_near(Level<T> L, const uint8_t* __restrict__ st,
-                                                     const T* __restrict__ rhs, T* __restrict__ e,
+                                                     const T* __restrict__ rhs, E* __restrict__ e,
                                                      const int* __restrict__ list, const int* __restrict__ count,
-                                                     int cap, int first, T omega) {
+                                                     int cap, int first, T omega, EAcc<T, E> A) {
     const int n = count[blockIdx.y];
     const int* seg = list + (size_t)blockIdx.y * cap;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = seg[i];
         const int x = c % L.nx, yz = c / L.nx;
-        e[c] = near_gs<T>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, first, omega);
+        A.st(e + c, near_gs<T, E>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, first, omega, A));
     }
 }
 
@@ -600,10 +647,10 @@ __global__ void __launch_bounds__(256) k_smooth_near(Level<T> L, const uint8_t* 
 // updated in the kernel (INLINE_NEAR) or skipped and updated by
 // k_smooth_near right after (same colour, so the two passes do not depend
 // on each other).
-template <class T, int W, bool INLINE_NEAR>
+template <class T, int W, bool INLINE_NEAR, class E = T>
 __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
-                                                  const T* __restrict__ rhs, T* __restrict__ e, int colour,
-                                                  int first, T omega) {
+                                                  const T* __restrict__ rhs, E* __restrict__ e, int colour,
+                                                  int first, T omega, EAcc<T, E> A) {
     static_assert(W == 4, "the near-cell path reads the span's states from one word");
     const int xs = W * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
@@ -628,15 +675,15 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
     uint2 sw = make_uint2(0x02020202u, 0x02020202u);  // (Neumann: nothing to update)
     const int xq = lane_on ? xs : 0;                   // (inactive lanes read a valid span)
     if (!first) {
-        c[0] = e[row + (lane_on ? xl : 0)];
-        c[W + 1] = e[row + (lane_on ? xr : 0)];
+        c[0] = A.ld(e + row + (lane_on ? xl : 0));
+        c[W + 1] = A.ld(e + row + (lane_on ? xr : 0));
 #pragma unroll
         for (int v = 0; v < W; v += 4) {
-            ES_VLD(c, 1 + v, e + row + xq + v);
-            ES_VLD(a, v, e + rym + xq + v);
-            ES_VLD(b, v, e + ryp + xq + v);
-            ES_VLD(d, v, e + rzm + xq + v);
-            ES_VLD(f, v, e + rzp + xq + v);
+            ES_ELD(A, c, 1 + v, e + row + xq + v);
+            ES_ELD(A, a, v, e + rym + xq + v);
+            ES_ELD(A, b, v, e + ryp + xq + v);
+            ES_ELD(A, d, v, e + rzm + xq + v);
+            ES_ELD(A, f, v, e + rzp + xq + v);
         }
     } else {
         // the iterate starts at zero
@@ -707,7 +754,7 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
     }
     if (lane_on) {
 #pragma unroll
-        for (int v = 0; v < W; v += 4) vst(e + row + xs + v, c[1 + v], c[2 + v], c[3 + v], c[4 + v]);
+        for (int v = 0; v < W; v += 4) A.st4(e + row + xs + v, c[1 + v], c[2 + v], c[3 + v], c[4 + v]);
     }
 }
 
@@ -1050,10 +1097,10 @@ __global__ void __launch_bounds__(128) k_prolong(Level<T> L, const uint8_t* __re
 
 // Vectorized prolongation: a thread owns 4 fine cells of a row (nx % 4 == 0)
 // and adds the correction of their 2 parents.
-template <class T>
-__global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __restrict__ st, T* __restrict__ e,
+template <class T, class E>
+__global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __restrict__ st, E* __restrict__ e,
                                                    int cnx, int cny, const uint8_t* __restrict__ cst,
-                                                   const T* __restrict__ ce) {
+                                                   const T* __restrict__ ce, EAcc<T, E> A) {
     const int xs = 4 * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
     if (xs >= L.nx || y >= L.ny) return;
@@ -1062,7 +1109,7 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
     const unsigned sw = *reinterpret_cast<const unsigned*>(st + c);
     const uint8_t c0 = cst[C] & ST_KIND, c1 = cst[C + 1] & ST_KIND;
     const T e0 = ce[C], e1 = ce[C + 1];
-    const auto q = vld(e + c);
+    const auto q = A.ld4(e + c);
     T v[4] = {q.v0, q.v1, q.v2, q.v3};
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -1070,7 +1117,7 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
         const uint8_t pk = i < 2 ? c0 : c1;
         if (sv == ST_UNKNOWN && pk == ST_UNKNOWN) v[i] += i < 2 ? e0 : e1;
     }
-    vst(e + c, v[0], v[1], v[2], v[3]);
+    A.st4(e + c, v[0], v[1], v[2], v[3]);
 }
 
 // Vectorized residual + restriction: a thread owns 2 coarse cells of a
@@ -1079,39 +1126,40 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
 // neighbouring vectors) and the 4 neighbour rows as 16-byte vectors, forms
 // the residuals and adds them to the coarse sums in the children order
 // (dk, dj, di) of the scalar kernel.
-template <class T>
+template <class T, class E = T>
 __device__ __forceinline__ T near_residual(const Level<T>& L, const uint8_t* __restrict__ st,
-                                           const T* __restrict__ rhs, const T* __restrict__ e, int x, int y, int z,
-                                           T inv_h2) {
+                                           const T* __restrict__ rhs, const E* __restrict__ e, int x, int y, int z,
+                                           T inv_h2, const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}) {
     const int cidx = x + L.nx * (y + L.ny * z);
     T diag, off;
-    level_stencil<T, true>(L, st, e, x, y, z, st[cidx], diag, off);
-    return rhs[cidx] - (diag * e[cidx] - off) * inv_h2;
+    level_stencil<T, true, E>(L, st, e, x, y, z, st[cidx], diag, off, A);
+    return rhs[cidx] - (diag * A.ld(e + cidx) - off) * inv_h2;
 }
 
 // The residual at the near-boundary unknown cells of a level, from its
 // near-cell list (both colours), into a scratch array that the restriction
 // then reads for those children.
-template <class T>
+template <class T, class E>
 __global__ void __launch_bounds__(256) k_near_residual(Level<T> L, const uint8_t* __restrict__ st,
-                                                       const T* __restrict__ rhs, const T* __restrict__ e,
+                                                       const T* __restrict__ rhs, const E* __restrict__ e,
                                                        const int* __restrict__ list, const int* __restrict__ count,
-                                                       int cap, T inv_h2, T* __restrict__ out) {
+                                                       int cap, T inv_h2, T* __restrict__ out, EAcc<T, E> A) {
     // blockIdx.y: list segment
     const int n = count[blockIdx.y];
     const int* seg = list + (size_t)blockIdx.y * cap;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = seg[i];
         const int x = c % L.nx, yz = c / L.nx;
-        out[c] = near_residual<T>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, inv_h2);
+        out[c] = near_residual<T, E>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, inv_h2, A);
     }
 }
 
-template <class T>
+template <class T, class E>
 __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T inv_h2, const uint8_t* __restrict__ st,
-                                                    const T* __restrict__ rhs, const T* __restrict__ e,
+                                                    const T* __restrict__ rhs, const E* __restrict__ e,
                                                     const T* __restrict__ near_res, int cnx,
-                                                    int cny, const uint8_t* __restrict__ cst, T* __restrict__ crhs) {
+                                                    int cny, const uint8_t* __restrict__ cst, T* __restrict__ crhs,
+                                                    EAcc<T, E> A) {
     const int cx_warp = 2 * (blockIdx.x * 32);
     const int cxs = cx_warp + 2 * threadIdx.x;
     const int cy = blockIdx.y * 8 + threadIdx.y, cz = blockIdx.z;
@@ -1139,13 +1187,13 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
             const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
             const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
             T c[6], a[4], b[4], d[4], f[4], r[4];
-            c[0] = e[row + xl];
-            c[5] = e[row + xr];
-            ES_VLD(c, 1, e + row + xq);
-            ES_VLD(a, 0, e + rym + xq);
-            ES_VLD(b, 0, e + ryp + xq);
-            ES_VLD(d, 0, e + rzm + xq);
-            ES_VLD(f, 0, e + rzp + xq);
+            c[0] = A.ld(e + row + xl);
+            c[5] = A.ld(e + row + xr);
+            ES_ELD(A, c, 1, e + row + xq);
+            ES_ELD(A, a, 0, e + rym + xq);
+            ES_ELD(A, b, 0, e + ryp + xq);
+            ES_ELD(A, d, 0, e + rzm + xq);
+            ES_ELD(A, f, 0, e + rzp + xq);
             ES_VLD(r, 0, rhs + row + xq);
             const unsigned sw = lane_on ? *reinterpret_cast<const unsigned*>(st + row + xs) : 0x02020202u;
             T res[4];
@@ -1234,23 +1282,24 @@ __global__ void k_correct(int N, const uint8_t* __restrict__ st0, const double* 
 // psi += e at unknown cells, psi in float-float (MIXED32 form); four cells
 // per thread with 16-byte accesses, the last thread also takes the N % 4
 // tail cells one by one.
-__global__ void k_correct_ff(int N, const uint8_t* __restrict__ st0, const float* __restrict__ e,
-                             float* __restrict__ psi_hi, float* __restrict__ psi_lo) {
+template <class E>
+__global__ void k_correct_ff(int N, const uint8_t* __restrict__ st0, const E* __restrict__ e,
+                             float* __restrict__ psi_hi, float* __restrict__ psi_lo, EAcc<float, E> A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int N4 = N >> 2;
     if (i == N4 - 1 || (N4 == 0 && i == 0))
         for (int c = 4 * N4; c < N; c++)
             if ((st0[c] & ST_KIND) == ST_UNKNOWN) {
-                const ff v = ff_add_f({psi_hi[c], psi_lo[c]}, e[c]);
+                const ff v = ff_add_f({psi_hi[c], psi_lo[c]}, A.ld(e + c));
                 psi_hi[c] = v.hi;
                 psi_lo[c] = v.lo;
             }
     if (i >= N4) return;
     const uchar4 st = reinterpret_cast<const uchar4*>(st0)[i];
-    const float4 ev = reinterpret_cast<const float4*>(e)[i];
+    const auto ev = A.ld4(e + 4 * (size_t)i);
     float4 h = reinterpret_cast<float4*>(psi_hi)[i], l = reinterpret_cast<float4*>(psi_lo)[i];
     const uint8_t sv[4] = {st.x, st.y, st.z, st.w};
-    const float evv[4] = {ev.x, ev.y, ev.z, ev.w};
+    const float evv[4] = {ev.v0, ev.v1, ev.v2, ev.v3};
     float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -1555,14 +1604,23 @@ dim3 rb_launch_shape(es_ctx* c, const Level<T>& L, int& zc) {
 // restriction and prolongation read the fine e and rhs (or e twice) and
 // states and touch the coarse level once.
 template <class T>
-cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
+cudaError_t vcycle_level(es_ctx* c, int l, int warm);
+
+// One level of the V-cycle with the level's correction stored as E (T, or
+// FP16 on the finest level under ES_MG_FP16: two-pass vector smoother,
+// never the coarsest level; the parameters are checked at creation).
+template <class T, class E>
+cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
+    constexpr bool kNative = std::is_same<T, E>::value;
     Level<T> L = level_desc<T>(c, l);
-    T* e = (T*)c->e[l];
+    E* e = (E*)c->e[l];
     T* rhs = (T*)c->rhs[l];
     const uint8_t* st = c->st[l];
     const T omega = (T)c->P.omega;
     const T inv_diag0 = (T)1 / L.diag0;
     const int Nl = L.nx * L.ny * L.nz;
+    EAcc<T, E> A{(T)1, (T)1};
+    if constexpr (!kNative) A = EAcc<T, E>{(T)c->e_scale, (T)1 / (T)c->e_scale};
     dim3 blk(128);
     dim3 half(((L.nx + 1) / 2 + 127) / 128, L.ny, L.nz);
     dim3 full((L.nx + 127) / 128, L.ny, L.nz);
@@ -1572,35 +1630,40 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
 
     // (the span form needs whole 128-cell tiles in x; a periodic axis of
     // one cell is its own neighbour: no red-black split)
-    const bool use_rb = c->P.smoother == ES_SMOOTH_FUSED && (L.nx % 128) == 0 && (!L.per[1] || L.ny >= 2) &&
-                        (!L.per[2] || L.nz >= 2);
+    const bool use_rb = kNative && c->P.smoother == ES_SMOOTH_FUSED && (L.nx % 128) == 0 &&
+                        (!L.per[1] || L.ny >= 2) && (!L.per[2] || L.nz >= 2);
     int rb_zc = 1;
     dim3 rb_grid(1, 1, 1);
     if (use_rb) rb_grid = rb_launch_shape<T>(c, L, rb_zc);
-    const double nl = (double)Nl, ts = (double)sizeof(T);
+    const double nl = (double)Nl, ts = (double)sizeof(T), es = (double)sizeof(E);
     const int* mc = l + 1 < c->L ? c->ln[l + 1] : c->ln[l];
     const double nc = (double)mc[0] * mc[1] * mc[2];
     auto sweep = [&](int first) {
-        if (use_rb) {
-            ProfScope ps(c, "smooth_fused", l, nl * ((first ? 2.0 : 3.0) * ts + 1.0));
-            T* eo = (T*)c->e2[l];
-            k_smooth_rb2<T><<<rb_grid, dim3(32, kRbRows + 1), RB2<T>::smem, c->stream>>>(L, inv_diag0, st, rhs, e,
-                                                                                          eo, first, omega, rb_zc);
-            c->e2[l] = c->e[l];
-            c->e[l] = eo;
-            e = eo;
-            count(c);
-            return;
+        if constexpr (kNative) {
+            if (use_rb) {
+                ProfScope ps(c, "smooth_fused", l, nl * ((first ? 2.0 : 3.0) * ts + 1.0));
+                T* eo = (T*)c->e2[l];
+                k_smooth_rb2<T><<<rb_grid, dim3(32, kRbRows + 1), RB2<T>::smem, c->stream>>>(
+                    L, inv_diag0, st, rhs, e, eo, first, omega, rb_zc);
+                c->e2[l] = c->e[l];
+                c->e[l] = eo;
+                e = eo;
+                count(c);
+                return;
+            }
         }
-        const double b_first = nl * (1.5 * ts + 1.0), b_half = nl * (2.0 * ts + 1.0);
+        // per half sweep: e of every cell in, the colour's e out, its rhs
+        // and state bytes in
+        const double b_first = nl * (0.5 * es + 0.5 * ts + 1.0), b_half = nl * (1.5 * es + 0.5 * ts + 1.0);
         if (vec) {
             if (Nl <= kInlineNearCells) {
                 {
                     ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
-                    k_smooth_v<T, W, true><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
+                    k_smooth_v<T, W, true, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first,
+                                                                             omega, A);
                 }
                 ProfScope ps(c, "smooth_half", l, b_half);
-                k_smooth_v<T, W, true><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
+                k_smooth_v<T, W, true, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega, A);
                 count(c, 2);
                 return;
             }
@@ -1609,84 +1672,99 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
             const size_t half = (size_t)kNearSegs * c->near_cap[l];
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
-                k_smooth_v<T, W, false><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first, omega);
+                k_smooth_v<T, W, false, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first,
+                                                                          omega, A);
             }
             {
                 ProfScope ps(c, "smooth_near", l, 0.0);
-                k_smooth_near<T><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l],
-                                                              first, omega);
+                k_smooth_near<T, E><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l], cnt,
+                                                                 c->near_cap[l], first, omega, A);
             }
             {
                 ProfScope ps(c, "smooth_half", l, b_half);
-                k_smooth_v<T, W, false><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega);
+                k_smooth_v<T, W, false, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega,
+                                                                          A);
             }
             ProfScope ps(c, "smooth_near", l, 0.0);
-            k_smooth_near<T><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l] + half, cnt + kNearSegs,
-                                                          c->near_cap[l], 0, omega);
-            count(c, 2);
-        } else {
+            k_smooth_near<T, E><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l] + half,
+                                                             cnt + kNearSegs, c->near_cap[l], 0, omega, A);
+            count(c, 4);
+            return;
+        }
+        if constexpr (kNative) {
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
                 k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, first, omega);
             }
             ProfScope ps(c, "smooth_half", l, b_half);
             k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
+            count(c, 2);
         }
-        count(c, 2);
     };
-    if (l == c->L - 1) {
-        size_t sm = coarse_smem_bytes(c, sizeof(T));
-        if (sm <= 200 * 1024) {
-            ProfScope ps(c, "coarse_solve", l, nl * (2.0 * ts + 1.0));
-            k_coarse_solve<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
-            count(c);
-        } else {
-            if (c->P.coarse_sweeps == 0) {
-                k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
+    if constexpr (kNative) {
+        if (l == c->L - 1) {
+            size_t sm = coarse_smem_bytes(c, sizeof(T));
+            if (sm <= 200 * 1024) {
+                ProfScope ps(c, "coarse_solve", l, nl * (2.0 * ts + 1.0));
+                k_coarse_solve<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
                 count(c);
+            } else {
+                if (c->P.coarse_sweeps == 0) {
+                    k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
+                    count(c);
+                }
+                for (int s = 0; s < c->P.coarse_sweeps; s++) sweep(s == 0);
             }
-            for (int s = 0; s < c->P.coarse_sweeps; s++) sweep(s == 0);
+            return cudaGetLastError();
         }
-        return cudaGetLastError();
     }
     const bool zero_start = !warm;
     if (c->P.nu1 == 0 && zero_start) {
-        k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
-        count(c);
+        cudaError_t err = cudaMemsetAsync(e, 0, (size_t)Nl * sizeof(E), c->stream);  // (0 in every E)
+        if (err != cudaSuccess) return err;
     }
     for (int s = 0; s < c->P.nu1; s++) sweep(s == 0 && zero_start);
     const int* m = c->ln[l + 1];
-    const double b_grid = nl * (2.0 * ts + 1.0) + nc * (ts + 1.0);
+    const double b_grid = nl * (es + ts + 1.0) + nc * (ts + 1.0);
     {
-    ProfScope ps_r(c, "restrict", l, b_grid);
-    if (vec) {
-        dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
-        T* scratch = (T*)c->e2[l];  // (the fused sweep's second iterate; free between sweeps)
-        k_near_residual<T><<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs), 256, 0, c->stream>>>(
-            L, st, rhs, e, c->near_list[l], c->near_count + 2 * kNearSegs * l, c->near_cap[l],
-                                                                 (T)1 / L.h2, scratch);
-        k_restrict_v<T><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1],
-                                                      c->st[l + 1], (T*)c->rhs[l + 1]);
-        count(c);
-    } else {
-        dim3 cgrid((m[0] + 127) / 128, m[1], m[2]);
-        k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], c->st[l + 1],
-                                                             (T*)c->rhs[l + 1]);
+        ProfScope ps_r(c, "restrict", l, b_grid);
+        if (vec) {
+            dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
+            T* scratch = (T*)c->e2[l];  // (the fused sweep's second iterate; free between sweeps)
+            k_near_residual<T, E><<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs), 256, 0,
+                                    c->stream>>>(L, st, rhs, e, c->near_list[l],
+                                                 c->near_count + 2 * kNearSegs * l, c->near_cap[l],
+                                                 (T)1 / L.h2, scratch, A);
+            k_restrict_v<T, E><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch, m[0],
+                                                             m[1], c->st[l + 1], (T*)c->rhs[l + 1], A);
+            count(c, 2);
+        } else if constexpr (kNative) {
+            dim3 cgrid((m[0] + 127) / 128, m[1], m[2]);
+            k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], c->st[l + 1],
+                                                                 (T*)c->rhs[l + 1]);
+            count(c);
+        }
     }
-    }
-    count(c);
     cudaError_t err = vcycle_level<T>(c, l + 1, 0);
     if (err != cudaSuccess) return err;
     {
-        ProfScope ps(c, "prolong", l, b_grid);
+        ProfScope ps(c, "prolong", l, nl * (2.0 * es + 1.0) + nc * (ts + 1.0));
         if (vec)
-            k_prolong_v<T><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
-        else
+            k_prolong_v<T, E><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1],
+                                                            (const T*)c->e[l + 1], A);
+        else if constexpr (kNative)
             k_prolong<T><<<full, blk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
     }
     count(c);
     for (int s = 0; s < c->P.nu2; s++) sweep(0);
     return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
+    if constexpr (std::is_same<T, float>::value)
+        if (l == 0 && c->P.mg_storage == ES_MG_FP16) return vcycle_impl<float, __half>(c, l, warm);
+    return vcycle_impl<T, T>(c, l, warm);
 }
 
 template <class T>
@@ -1754,11 +1832,17 @@ cudaError_t launch_vcycle(es_ctx* c, int warm) {
 // Algorithmic bytes per cell: e (s) and the state byte in, psi (8) in and out.
 cudaError_t launch_correct(es_ctx* c) {
     const int N = (int)c->g.N;
-    ProfScope ps(c, "correct", -1, (double)N * ((mixed(c) ? 4.0 : 8.0) + 1.0 + 16.0));
+    const double es = c->P.mg_storage == ES_MG_FP16 ? 2.0 : (mixed(c) ? 4.0 : 8.0);
+    ProfScope ps(c, "correct", -1, (double)N * (es + 1.0 + 16.0));
     if (mixed(c)) {
         const int n4 = (N >> 2) > 0 ? (N >> 2) : 1;
-        k_correct_ff<<<(n4 + 255) / 256, 256, 0, c->stream>>>(N, c->st[0], (const float*)c->e[0], c->psi32,
-                                                               c->psi_lo);
+        if (c->P.mg_storage == ES_MG_FP16)
+            k_correct_ff<__half><<<(n4 + 255) / 256, 256, 0, c->stream>>>(
+                N, c->st[0], (const __half*)c->e[0], c->psi32, c->psi_lo,
+                EAcc<float, __half>{c->e_scale, 1.0f / c->e_scale});
+        else
+            k_correct_ff<float><<<(n4 + 255) / 256, 256, 0, c->stream>>>(
+                N, c->st[0], (const float*)c->e[0], c->psi32, c->psi_lo, EAcc<float, float>{1.0f, 1.0f});
     } else {
         k_correct<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->st[0], (const double*)c->e[0], c->psi);
     }

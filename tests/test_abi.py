@@ -64,6 +64,8 @@ def _create_rc(lib, wl, **over):
     (dict(omega=2.0), "omega"),
     (dict(eps=0.0), "eps"),
     (dict(smoother=2), "smoother"),
+    (dict(mg_storage=2), "mg_storage"),
+    (dict(mg_storage=1), "reduced precision"),  # (the helper creates FP64 contexts)
 ])
 def test_invalid_parameters_rejected_before_any_gpu_call(lib, over, needle):
     rc, msg = _create_rc(lib, W.single_sphere(), **over)
@@ -96,3 +98,6 @@ def test_device_bytes_matches_layout(lib):
     assert 2 * 19 * 2 * N + rest32 < b16 < 2 * 19 * 2 * N + rest32 + 0.1 * N
     assert 2 * 19 * 4 * N + rest32 < b32 < 2 * 19 * 4 * N + rest32 + 0.1 * N
     assert 2 * 19 * 8 * N + rest64 < b64 < 2 * 19 * 8 * N + rest64 + 0.1 * N
+    # FP16 storage of the finest level's correction: 2 bytes a cell less
+    b32h = es.device_bytes(wl, es.ES_MIXED32, dict(mg_storage=es.ES_MG_FP16))
+    assert b32 - b32h == 2 * N

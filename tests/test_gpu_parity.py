@@ -227,6 +227,40 @@ def test_mixed32_defect_correction_reaches_fp64_tolerance(name):
     assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < 1e-9
 
 
+@pytest.mark.parametrize("maker", [lambda: W.single_sphere(),
+                                   lambda: W.channel(n=64, n_spheres=8, radius=5.0, levels=4)])
+def test_mg_fp16_within_1e4_after_100_steps(maker):
+    """MIXED32 with the finest level's multigrid correction stored as FP16
+    (scaled by sqrt(N) / ||r||) against the FP64 oracle after 100 steps."""
+    wl = maker()
+    p = Pair(wl, es.ES_MIXED32, lib_overrides=dict(mg_storage=es.ES_MG_FP16))
+    for _ in range(100):
+        _, ginfo, _, _ = p.step(forced=False)
+        assert ginfo["status"] == es.ES_OK and ginfo["r"] < ginfo["tol"]
+    r = p.compare()
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x"):
+        assert r[k] < MIXED_TOL, (k, r[k])
+
+
+@pytest.mark.parametrize("name", ["single_sphere", "mixed_ragged"])
+def test_mg_fp16_defect_correction_reaches_fp64_tolerance(name):
+    """The FP16 correction's rounding (unit roundoff 2^-11 of the scaled
+    values) only slows the float-float outer iteration: it still reaches
+    1e-12 relative and the oracle's FP64 solution, as in the MIXED32 test
+    above."""
+    wl = CASES[name]()
+    over = dict(res_rf=1e-12, max_cycles=300)
+    p = Pair(wl, es.ES_MIXED32, over, lib_overrides=dict(mg_storage=es.ES_MG_FP16))
+    p.o.map_particles()
+    p.g.map_particles()
+    p.o.solve()
+    ig = p.g.solve()
+    assert ig["status"] == es.ES_OK and ig["r"] < ig["tol"]
+    fluid = p.o.owner() < 0
+    assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < 1e-9
+
+
 def test_mixed32_potential_round_trip():
     """MIXED32 stores psi as a float-float pair: a double written with
     es_set_field comes back to within 2^-47 relative."""
