@@ -105,6 +105,9 @@ typedef struct {
                            red-black sweep is executed; both compute the same sweep */
     int mg_storage;     /* ES_MG_NATIVE (0, default) or ES_MG_FP16: storage of the
                            finest level's multigrid correction (see below)        */
+    int wall_slip[6];   /* LBM condition per face of a non-periodic axis (order of
+                           pot_bc): 0 no-slip (resting bounce-back), 1 free-slip
+                           (specular reflection; Sec. 4.1 uses both)             */
 } es_params;
 
 /* Execution of one red-black Gauss-Seidel sweep (same arithmetic either way):

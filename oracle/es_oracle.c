@@ -68,6 +68,7 @@ typedef struct {
     int levels, nu1, nu2, coarse_sweeps;
     double omega, res_rf;
     int max_cycles;
+    int wall_slip[6]; /* per face of a non-periodic axis: 0 no-slip, 1 free-slip */
 } or_params;
 
 typedef struct {
@@ -232,6 +233,8 @@ int or_create(const or_params* P, const or_particle* parts, int np, or_ctx** out
         /* red-black ordering needs an even extent on periodic axes (coarsest too) */
         if (P->periodic[a] && ((d >> (P->levels - 1)) % 2 != 0) && d > 1) return OR_EINVAL;
     }
+    for (int f = 0; f < 6; f++)
+        if (P->wall_slip[f] != 0 && P->wall_slip[f] != 1) return OR_EINVAL;
     for (int p = 0; p < np; p++) {
         if (!(parts[p].R > 0.0)) return OR_EINVAL;
         for (int a = 0; a < 3; a++)
@@ -763,6 +766,44 @@ static void collide_cell(const or_ctx* c, const double fin[19], const double fbv
     }
 }
 
+/* Direction index of the lattice vector (x, y, z).                          */
+static int dir_of(int x, int y, int z) {
+    for (int q = 0; q < 19; q++)
+        if (CV[q][0] == x && CV[q][1] == y && CV[q][2] == z) return q;
+    return -1;
+}
+
+/* Population q of fluid cell (i,j,k) whose pull source x - e_q lies beyond a
+ * non-periodic face (Sec. 4.1 uses both wall kinds).  No-slip: resting
+ * bounce-back, the cell's own post-collision population of the opposite
+ * direction.  Free-slip (all crossed faces free-slip): specular reflection.
+ * The population arriving with velocity e_q left the fluid cell s towards
+ * the face with the crossed components of e_q reversed, and s is x minus the
+ * components of e_q that stay parallel to the crossed faces.  Where s is an
+ * obstacle cell, bounce-back is used instead.                                */
+static double wall_population(const or_ctx* c, const double* src, int i, int j, int k, int q, long id) {
+    const int x[3] = {i, j, k};
+    int m[3], s[3];
+    int slip = 1;
+    for (int a = 0; a < 3; a++) {
+        int v = x[a] - CV[q][a];
+        if (CV[q][a] != 0 && !c->P.periodic[a] && (v < 0 || v >= c->n[a])) {
+            int face = 2 * a + (v >= c->n[a] ? 1 : 0);
+            if (!c->P.wall_slip[face]) slip = 0;
+            m[a] = -CV[q][a];
+            s[a] = x[a];
+        } else {
+            m[a] = CV[q][a];
+            s[a] = (v + c->n[a]) % c->n[a];
+        }
+    }
+    if (slip) {
+        long sid = cidx(c, s[0], s[1], s[2]);
+        if (c->owner[sid] < 0) return src[(long)dir_of(m[0], m[1], m[2]) * c->N + sid];
+    }
+    return src[(long)opposite(q) * c->N + id];
+}
+
 int or_lbm(or_ctx* c) {
     const double* src = c->f[c->cur];
     double* dst = c->f[1 - c->cur];
@@ -777,7 +818,7 @@ int or_lbm(or_ctx* c) {
                     int o = opposite(q);
                     /* stream step (Eq. LBMstreamStep), pulled from x - e_q */
                     if (!neighbour(c->n, c->P.periodic, i, j, k, -CV[q][0], -CV[q][1], -CV[q][2], nb, NULL)) {
-                        fin[q] = src[o * c->N + id]; /* resting no-slip wall: bounce back */
+                        fin[q] = wall_population(c, src, i, j, k, q, id);
                         continue;
                     }
                     long nid = cidx(c, nb[0], nb[1], nb[2]);

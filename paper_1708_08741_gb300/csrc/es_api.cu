@@ -68,6 +68,8 @@ int validate(const es_params* P, const es_particle* parts, int n, std::string& w
     for (int f = 0; f < 6; f++)
         if (P->pot_bc[f] != ES_POT_ZERO_FLUX && P->pot_bc[f] != ES_POT_DIRICHLET)
             return why = "unknown potential boundary kind", ES_EINVAL;
+    for (int f = 0; f < 6; f++)
+        if (P->wall_slip[f] != 0 && P->wall_slip[f] != 1) return why = "wall_slip entries must be 0 or 1", ES_EINVAL;
     for (int p = 0; p < n; p++) {
         if (!(parts[p].R > 0.0)) return why = "particle radius must be > 0", ES_EINVAL;
         if (parts[p].kind != ES_KIND_ZETA && parts[p].kind != ES_KIND_CHARGE)
@@ -243,6 +245,9 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->g.ny = params->dims[1];
     c->g.nz = params->dims[2];
     for (int a = 0; a < 3; a++) c->g.per[a] = params->periodic[a] ? 1 : 0;
+    c->slip = 0;
+    for (int f = 0; f < 6; f++)
+        if (!c->g.per[f / 2] && params->wall_slip[f]) c->slip |= 1 << f;
     c->g.N = (long long)c->g.nx * c->g.ny * c->g.nz;
     c->g.ps = pdf_stride(c->g.N);
     for (int f = 0; f < 6; f++) {

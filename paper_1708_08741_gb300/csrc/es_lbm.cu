@@ -37,11 +37,59 @@ __global__ void k_particles_f32(int np, const DParticle* __restrict__ part, floa
     }
 }
 
-template <class S, class C = typename Store<S>::C>
+// A population whose pull source lies beyond a non-periodic face (walls
+// half-way outside the first and last layer): the direction and cell it is
+// taken from.  No-slip face: resting bounce-back, the cell's own population
+// of the opposite direction.  Free-slip (every crossed face free-slip):
+// specular reflection; the population arriving with e_q left the fluid cell
+// s = x - (the components of e_q parallel to the crossed faces) in the
+// direction with the crossed components reversed.  An obstacle cell at s
+// falls back to bounce-back.  Either direction has the weight of q.
+struct WallSrc {
+    int q;
+    long long cell;
+};
+
+__device__ __forceinline__ WallSrc wall_source(const Grid& g, int slip_faces, const int32_t* __restrict__ owner,
+                                               int x, int y, int z, int q, long long c) {
+    const int cv[3] = {cx(q), cy(q), cz(q)};
+    const int p[3] = {x, y, z};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    int m[3], s[3];
+    bool slip = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int v = p[a] - cv[a];
+        if (cv[a] != 0 && !g.per[a] && (v < 0 || v >= n[a])) {
+            slip = slip && ((slip_faces >> (2 * a + (v >= n[a] ? 1 : 0))) & 1);
+            m[a] = -cv[a];
+            s[a] = p[a];
+        } else {
+            m[a] = cv[a];
+            s[a] = v < 0 ? v + n[a] : (v >= n[a] ? v - n[a] : v);
+        }
+    }
+    if (slip) {
+        const long long sc = lin(g, s[0], s[1], s[2]);
+        if (owner[sc] < 0) {
+            int qm = 0;
+#pragma unroll
+            for (int k = 1; k < 19; k++)
+                if (cx(k) == m[0] && cy(k) == m[1] && cz(k) == m[2]) qm = k;
+            return WallSrc{qm, sc};
+        }
+    }
+    return WallSrc{opp(q), c};
+}
+
+// SLIP: the grid has free-slip faces (a separate instance, so that the
+// common no-slip/periodic form keeps its register count).
+template <class S, bool SLIP, class C = typename Store<S>::C>
 __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
                                              const uint8_t* __restrict__ flags, const int32_t* __restrict__ owner,
                                              const DParticle* __restrict__ part, const float* __restrict__ partf,
-                                             const C* __restrict__ fb, C ax, C ay, C az, C lam_e, C lam_o) {
+                                             const C* __restrict__ fb, C ax, C ay, C az, C lam_e, C lam_o,
+                                             int slip_faces) {
     using St = Store<S>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -70,8 +118,12 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
         for (int q = 1; q < 19; q++) {
             long long nb;
             if (!neighbour(g, x, y, z, -cx(q), -cy(q), -cz(q), nb)) {
-                // resting no-slip wall half-way outside: bounce back
-                f[q] = St::ld(opp(q), P.src[opp(q)][c]);
+                if constexpr (SLIP) {
+                    const WallSrc w = wall_source(g, slip_faces, owner, x, y, z, q, c);
+                    f[q] = St::ld(q, P.src[w.q][w.cell]);
+                } else {
+                    f[q] = St::ld(opp(q), P.src[opp(q)][c]);  // resting no-slip wall: bounce back
+                }
                 continue;
             }
             const int o = owner[nb];
@@ -437,9 +489,14 @@ cudaError_t launch_lbm(es_ctx* c) {
         // algorithmic bytes per cell: 19 populations in and out, f_b (3 C)
         // and the flag byte in
         ProfScope ps(c, "lbm", -1, (double)g.N * (38.0 * sizeof(S) + 3.0 * sizeof(C) + 1.0));
-        k_lbm<S><<<grd, blk, 0, c->stream>>>(g, streams<S>(c), c->flags, c->owner, c->part, c->partf,
-                                             (const C*)c->fb, (C)a[0], (C)a[1], (C)a[2], (C)c->lambda_e,
-                                             (C)c->lambda_o);
+        if (c->slip)
+            k_lbm<S, true><<<grd, blk, 0, c->stream>>>(g, streams<S>(c), c->flags, c->owner, c->part, c->partf,
+                                                       (const C*)c->fb, (C)a[0], (C)a[1], (C)a[2],
+                                                       (C)c->lambda_e, (C)c->lambda_o, c->slip);
+        else
+            k_lbm<S, false><<<grd, blk, 0, c->stream>>>(g, streams<S>(c), c->flags, c->owner, c->part, c->partf,
+                                                        (const C*)c->fb, (C)a[0], (C)a[1], (C)a[2],
+                                                        (C)c->lambda_e, (C)c->lambda_o, 0);
     });
     count(c);
     return cudaGetLastError();

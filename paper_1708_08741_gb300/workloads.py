@@ -93,6 +93,7 @@ class Workload:
     max_cycles: int = 100
     steps: int = 100
     pot_bc: Sequence[int] = (0, 0, 0, 0, 0, 0)
+    wall_slip: Sequence[int] = (0, 0, 0, 0, 0, 0)  # per face of a non-periodic axis: 1 = free-slip
     pot_val: Sequence[float] = (0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
     # particle arrays
     x: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))

@@ -190,6 +190,42 @@ def test_coupled_channel_fp64():
         assert r[k] < FP64_TOL, (k, r[k])
 
 
+def _slip(wl, faces):
+    wl.wall_slip = faces
+    return wl
+
+
+SLIP_CASES = {
+    # walls in z, both free-slip; moving and rotating spheres of both kinds
+    "mixed_box_z_free": lambda: _slip(W.mixed_box(), (0, 0, 0, 0, 1, 1)),
+    # x walls no-slip, z walls free-slip: edges fall back to bounce-back
+    "x_noslip_z_free": lambda: _slip(_moving(W.mixed_box(dims=(40, 24, 32), levels=2, periodic=(0, 1, 0))),
+                                     (0, 0, 0, 0, 1, 1)),
+    # x and z walls free-slip: populations at the edges reflect off both
+    "xz_free": lambda: _slip(_moving(W.mixed_box(dims=(40, 24, 32), levels=2, periodic=(0, 1, 0))),
+                             (1, 1, 0, 0, 1, 1)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SLIP_CASES))
+def test_coupled_free_slip_walls_fp64(name):
+    """Free-slip walls (specular reflection) in the stream step, coupled
+    with moving spheres, against the oracle: FP64 bar."""
+    p, r = _coupled(SLIP_CASES[name](), 20)
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x", "v", "w"):
+        assert r[k] < FP64_TOL, (k, r[k])
+
+
+@pytest.mark.parametrize("precision", [es.ES_MIXED32, es.ES_MIXED16])
+def test_free_slip_reduced_precision_after_100_steps(precision):
+    wl = _slip(W.channel(n=64, n_spheres=8, radius=5.0, levels=4), (0, 0, 0, 0, 1, 1))
+    p, r = _coupled(wl, 100, precision=precision, forced=False)
+    assert r["owner_equal"]
+    assert r["psi"] < MIXED_TOL and r["x"] < MIXED_TOL
+    assert r["u"] < (MIXED_TOL if precision == es.ES_MIXED32 else MIXED16_U_TOL)
+
+
 @pytest.mark.parametrize("maker", [lambda: W.single_sphere(),
                                    lambda: W.channel(n=64, n_spheres=8, radius=5.0, levels=4)])
 def test_mixed32_within_1e4_after_100_steps(maker):

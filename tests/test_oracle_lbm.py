@@ -147,3 +147,104 @@ def test_shear_wave_decay_sets_viscosity():
     rate = -np.polyfit(np.arange(len(amps)), np.log(amps), 1)[0]
     nu = (tau - 0.5) / 3.0
     assert abs(rate / (nu * k * k) - 1.0) < 2e-3
+
+
+@pytest.mark.parametrize("tau,H", [(1.0, 8), (0.8, 6)])
+def test_free_slip_half_channel_is_half_of_the_no_slip_channel(tau, H):
+    """No-slip wall below the first layer, free-slip wall above the last: a
+    specular wall is a mirror plane, so the steady profile is the lower half
+    of the Poiseuille channel of height 2H, u(z) = g/(2 nu) (z + 1/2)(2H - 1/2 - z),
+    which the TRT scheme with half-way bounce-back reproduces exactly."""
+    g = 1e-6
+    wl = _box((1, 1, H), (1, 1, 0), tau=tau, accel=(g, 0.0, 0.0))
+    wl.wall_slip = (0, 0, 0, 0, 0, 1)
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    nu = (tau - 0.5) / 3.0
+    z = np.arange(H) + 0.0
+    exact = g / (2.0 * nu) * (z + 0.5) * (2 * H - 0.5 - z)
+    steps = int(40 * (2 * H) ** 2 / nu) + 2000
+    for _ in range(steps):
+        o.lbm_step()
+    u = o.field(oracle.FIELD_U)[0, :, 0, 0]
+    assert np.max(np.abs(u / exact - 1.0)) < 1e-10
+    np.testing.assert_allclose(o.field(oracle.FIELD_U)[1:], 0.0, atol=1e-15)
+
+
+def _momentum(f, c):
+    return np.array([f.sum()] + [np.tensordot(c[:, a].astype(float), f, axes=(0, 0)).sum() for a in range(3)])
+
+
+@pytest.mark.parametrize("slip", [(0, 0, 0, 0, 1, 1), (1, 1, 0, 0, 1, 1)])
+def test_free_slip_walls_conserve_tangential_momentum(slip):
+    """A free-slip wall reverses only the normal component of a population's
+    velocity, so the total mass and the total momentum along every axis that
+    has no wall are invariant; at an edge of two free-slip walls a
+    population reflects off both.  A uniform flow plus random populations,
+    no forcing, no spheres.  With no-slip walls the same momentum decays (the test sees the
+    difference)."""
+    dims = (8, 6, 10)
+    per = tuple(0 if slip[2 * a] else 1 for a in range(3))
+    rng = np.random.Generator(np.random.PCG64(17))
+    c, w = oracle.lattice()
+    cu = (c.astype(float) @ np.array([0.02, -0.015, 0.01]))[:, None, None, None]
+    f = w[:, None, None, None] * (1.0 + 3.0 * cu + 0.05 * rng.standard_normal((19, dims[2], dims[1], dims[0])))
+    out = {}
+    for kind in ("slip", "noslip"):
+        wl = _box(dims, per, tau=0.9)
+        wl.wall_slip = slip if kind == "slip" else (0,) * 6
+        o = oracle.Oracle(wl)
+        o.set_field(oracle.FIELD_PDF, f)
+        o.map_particles()
+        m0 = _momentum(o.field(oracle.FIELD_PDF), c)
+        for _ in range(30):
+            o.lbm_step()
+        out[kind] = (m0, _momentum(o.field(oracle.FIELD_PDF), c))
+    m0, m1 = out["slip"]
+    free = [1 + a for a in range(3) if per[a]]
+    scale = np.abs(f).sum()
+    assert abs(m1[0] - m0[0]) < 1e-14 * scale
+    for k in free:
+        assert abs(m1[k] - m0[k]) < 1e-14 * scale
+        assert abs(m0[k]) > 1e-4 * scale  # the random state carries momentum there
+    m0n, m1n = out["noslip"]
+    assert max(abs(m1n[k] - m0n[k]) for k in free) > 1e-3 * max(abs(m0n[k]) for k in free)
+
+
+@pytest.mark.parametrize("slip", [(0, 0, 0, 0, 1, 1), (1, 1, 0, 0, 1, 1)])
+def test_free_slip_walls_are_mirror_planes(slip):
+    """A state that is uniform across the free-slip walls and has no velocity
+    normal to them is its own mirror image, so the walls act like periodic
+    faces: the run matches the fully periodic run cell by cell.  The flow
+    varies along the walls, which checks that a reflected population comes
+    from the tangentially displaced cell (and, with two free-slip walls,
+    that a population reflected at the edge comes back from the cell
+    itself)."""
+    dims = (12, 10, 6)
+    walls = [a for a in range(3) if slip[2 * a]]
+    c, w = oracle.lattice()
+    X, Y, Z = np.meshgrid(*[np.arange(n) + 0.5 for n in dims], indexing="ij")
+    k = [2.0 * np.pi / n for n in dims]
+    u = np.zeros((3,) + X.shape)
+    rho = 1.0 + 0.01 * np.cos(k[1] * Y)
+    if 0 in walls:  # uniform in x and z, flow along y only
+        u[1] = 0.01 * np.sin(k[1] * Y)
+    else:
+        u[0] = 0.01 * np.sin(k[1] * Y)
+        u[1] = 0.008 * np.cos(k[0] * X)
+        rho = rho + 0.01 * np.sin(k[0] * X)
+    f = _equilibrium(c, w, rho, u).transpose(0, 3, 2, 1)  # (q, z, y, x)
+    res = {}
+    for kind in ("slip", "periodic"):
+        per = tuple(0 if (kind == "slip" and a in walls) else 1 for a in range(3))
+        wl = _box(dims, per, tau=0.7)
+        wl.wall_slip = slip if kind == "slip" else (0,) * 6
+        o = oracle.Oracle(wl)
+        o.set_field(oracle.FIELD_PDF, f)
+        o.map_particles()
+        for _ in range(25):
+            o.lbm_step()
+        res[kind] = o.field(oracle.FIELD_PDF)
+    assert np.max(np.abs(res["slip"] - res["periodic"])) < 1e-15
+    # (bounce-back walls give a different flow)
+    assert np.max(np.abs(res["periodic"] - f)) > 1e-5
