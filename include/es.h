@@ -108,6 +108,15 @@ typedef struct {
     int wall_slip[6];   /* LBM condition per face of a non-periodic axis (order of
                            pot_bc): 0 no-slip (resting bounce-back), 1 free-slip
                            (specular reflection; Sec. 4.1 uses both)             */
+    double phi_t;       /* thermal voltage k_B T / (z e).  0 (default): the
+                           Debye-Hueckel equation.  > 0: the symmetric nonlinear
+                           Poisson-Boltzmann equation (Eq. SPBE),
+                           -lap psi + kappa^2 phi_t sinh(psi / phi_t) = 0, solved by
+                           Newton steps whose linear systems get coarse_sweeps
+                           red-black SOR sweeps on the stencil re-linearised about
+                           the current psi (Sec. 5.3); needs ES_FP64, levels == 1.
+                           The charge density becomes -eps kappa^2 phi_t
+                           sinh(psi / phi_t).                                      */
 } es_params;
 
 /* Execution of one red-black Gauss-Seidel sweep (same arithmetic either way):

@@ -71,6 +71,7 @@ class OrParams(ctypes.Structure):
         ("res_rf", ctypes.c_double),
         ("max_cycles", ctypes.c_int),
         ("wall_slip", ctypes.c_int * 6),
+        ("phi_t", ctypes.c_double),
     ]
 
 
@@ -163,7 +164,7 @@ class Oracle:
                  tau=wl.tau, kappa=wl.kappa, eps=wl.eps, E_ext=wl.E_ext, accel=wl.accel,
                  rho_p_ratio=wl.rho_p_ratio, levels=wl.levels, nu1=wl.nu1, nu2=wl.nu2,
                  coarse_sweeps=wl.coarse_sweeps, omega=wl.omega, res_rf=wl.res_rf,
-                 max_cycles=wl.max_cycles, wall_slip=wl.wall_slip)
+                 max_cycles=wl.max_cycles, wall_slip=wl.wall_slip, phi_t=wl.phi_t)
         if params_override:
             d.update(params_override)
         for k, v in d.items():

@@ -15,7 +15,9 @@
  *                 cells, assembly of the potential stencil and RHS
  *                 (Sec. 4.2, Sec. 5.4, Sec. 5.5)
  *   or_solve      Debye-Hueckel solve by multigrid V-cycles inside a residual
- *                 loop (Sec. 5.3; Eq. DiscrFV and the 7-point stencil of Sec. 4.3)
+ *                 loop (Sec. 5.3; Eq. DiscrFV and the 7-point stencil of Sec. 4.3);
+ *                 optionally the nonlinear Poisson-Boltzmann equation (Eq. SPBE)
+ *                 by SOR sweeps on the stencil re-linearised every iteration
  *   or_body_force EDL field, charge density and electric body force (Sec. 5.6)
  *   or_lbm        fused stream-collide TRT step with Luo forcing and moving
  *                 bounce-back (Sec. 4.1, Eq. LBMMovWall)
@@ -69,6 +71,7 @@ typedef struct {
     double omega, res_rf;
     int max_cycles;
     int wall_slip[6]; /* per face of a non-periodic axis: 0 no-slip, 1 free-slip */
+    double phi_t;     /* thermal voltage k_B T / (z e); 0: Debye-Hueckel, > 0: nonlinear PB */
 } or_params;
 
 typedef struct {
@@ -96,6 +99,7 @@ typedef struct {
     int ln[OR_MAXLEV][3];
     unsigned char *state[OR_MAXLEV];
     double *diag[OR_MAXLEV];
+    double *dlin; /* nonlinear PB: level-0 diagonal linearised about the current psi */
     double *e[OR_MAXLEV], *rhs[OR_MAXLEV], *res[OR_MAXLEV];
     double tol;
     int have_tol;
@@ -211,6 +215,7 @@ void or_destroy(or_ctx* c) {
     free(c->T);
     free(c->nfaces);
     free(c->sigma);
+    free(c->dlin);
     for (int l = 0; l < OR_MAXLEV; l++) {
         free(c->state[l]);
         free(c->diag[l]);
@@ -235,6 +240,8 @@ int or_create(const or_params* P, const or_particle* parts, int np, or_ctx** out
     }
     for (int f = 0; f < 6; f++)
         if (P->wall_slip[f] != 0 && P->wall_slip[f] != 1) return OR_EINVAL;
+    /* the nonlinear Poisson-Boltzmann form runs the paper's SOR solver only */
+    if (!(P->phi_t >= 0.0) || (P->phi_t > 0.0 && P->levels != 1)) return OR_EINVAL;
     for (int p = 0; p < np; p++) {
         if (!(parts[p].R > 0.0)) return OR_EINVAL;
         for (int a = 0; a < 3; a++)
@@ -263,8 +270,9 @@ int or_create(const or_params* P, const or_particle* parts, int np, or_ctx** out
     c->T = (double*)calloc(3 * (np > 0 ? np : 1), sizeof(double));
     c->nfaces = (int*)calloc(np > 0 ? np : 1, sizeof(int));
     c->sigma = (double*)calloc(np > 0 ? np : 1, sizeof(double));
+    c->dlin = (double*)calloc(c->N, sizeof(double));
     if (!c->part || !c->mapped || !c->f[0] || !c->f[1] || !c->owner || !c->owner_prev || !c->psi ||
-        !c->b || !c->fb || !c->F || !c->T || !c->nfaces || !c->sigma) {
+        !c->b || !c->fb || !c->F || !c->T || !c->nfaces || !c->sigma || !c->dlin) {
         or_destroy(c);
         return OR_ENOMEM;
     }
@@ -514,7 +522,8 @@ static void rb_half_sweep(or_ctx* c, int l, int colour) {
                 if (((i + j + k) & 1) != colour) continue;
                 long id = (long)i + (long)m[0] * ((long)j + (long)m[1] * k);
                 if (c->state[l][id] != ST_UNKNOWN) continue;
-                double gs = (h2 * c->rhs[l][id] + level_offsum(c, l, c->e[l], i, j, k)) / c->diag[l][id];
+                double d = (l == 0 && c->P.phi_t > 0.0) ? c->dlin[id] : c->diag[l][id];
+                double gs = (h2 * c->rhs[l][id] + level_offsum(c, l, c->e[l], i, j, k)) / d;
                 c->e[l][id] = (1.0 - w) * c->e[l][id] + w * gs;
             }
 }
@@ -582,7 +591,20 @@ static void vcycle(or_ctx* c, int l) {
     }
 }
 
-/* Outer residual r = b - A psi on the unknowns and its Euclidean norm. */
+/* Screening term of the potential equation at one cell, kappa^2 psi for the
+ * Debye-Hueckel form (Eq. DebyHuckApproxPot), and for the symmetric
+ * Poisson-Boltzmann equation (Eq. SPBE) written with kappa^2 =
+ * 2 z^2 e^2 n / (eps k_B T) and phi_t = k_B T / (z e):
+ * kappa^2 phi_t sinh(psi / phi_t), which tends to kappa^2 psi as phi_t grows. */
+static double screening(const or_ctx* c, double psi) {
+    double k2 = c->P.kappa * c->P.kappa;
+    if (c->P.phi_t > 0.0) return k2 * c->P.phi_t * sinh(psi / c->P.phi_t);
+    return k2 * psi;
+}
+
+/* Outer residual r = b - A psi on the unknowns and its Euclidean norm.  For
+ * the nonlinear form A psi holds the screening term above in place of the
+ * kappa^2 psi that the assembled diagonal carries.                          */
 static double outer_residual(or_ctx* c, double* r) {
     double ss = 0.0;
     for (int k = 0; k < c->n[2]; k++)
@@ -594,18 +616,23 @@ static double outer_residual(or_ctx* c, double* r) {
                     continue;
                 }
                 double Apsi = c->diag[0][id] * c->psi[id] - level_offsum(c, 0, c->psi, i, j, k);
+                if (c->P.phi_t > 0.0)
+                    Apsi += screening(c, c->psi[id]) - c->P.kappa * c->P.kappa * c->psi[id];
                 r[id] = c->b[id] - Apsi;
                 ss += r[id] * r[id];
             }
     return sqrt(ss);
 }
 
-/* Debye-Hueckel solve of Sec. 5.3: while the residual L2 norm is at least
+/* Potential solve of Sec. 5.3: while the residual L2 norm is at least
  * tol = RES_RF * (norm at the first solve of the run), apply a V-cycle to the
  * defect and correct.  A residual of exactly zero is an exact solution and
  * stops the loop too (with a zero first residual, tol is zero and the test
  * alone would never end it).  forced_cycles >= 0 applies exactly that many
- * cycles.
+ * cycles.  With phi_t > 0 the residual is the nonlinear one and each
+ * iteration is one Newton step whose linear system is smoothed by the
+ * single-level red-black SOR sweeps (the paper's solver for varying
+ * stencils; levels == 1 is required).
  * info: [cycles, norm before, norm after, tol].                              */
 int or_solve(or_ctx* c, int forced_cycles, double* info) {
     double* r = c->rhs[0];
@@ -630,6 +657,15 @@ int or_solve(or_ctx* c, int forced_cycles, double* info) {
                 status = OR_ENOTCONVERGED;
                 break;
             }
+        }
+        if (c->P.phi_t > 0.0) {
+            /* nonlinear PB (Sec. 5.3: stencils re-set at the beginning of each
+             * iteration): the centre entry linearised about the current psi,
+             * d = diag + kappa^2 (cosh(psi / phi_t) - 1), the derivative of the
+             * screening term; the sweeps below then solve J e = r (Newton) */
+            double k2 = c->P.kappa * c->P.kappa;
+            for (long i = 0; i < c->N; i++)
+                c->dlin[i] = c->diag[0][i] + k2 * (cosh(c->psi[i] / c->P.phi_t) - 1.0);
         }
         vcycle(c, 0); /* solves A e = r with e = 0 initially (rhs[0] holds r) */
         for (long i = 0; i < c->N; i++)
@@ -707,7 +743,9 @@ void or_gradient(const or_ctx* c, double* g_out) {
 }
 
 /* f_b = rho_e (E_ext - grad psi) with rho_e = -kappa^2 eps psi
- * (Eq. ChrgDensDHA) at every fluid cell; zero elsewhere.
+ * (Eq. ChrgDensDHA), or -eps kappa^2 phi_t sinh(psi / phi_t) for the
+ * nonlinear form (the right-hand side of Eq. SPBE times eps), at every fluid
+ * cell; zero elsewhere.
  * READING: every unknown cell carries the body force, near-boundary included. */
 int or_body_force(or_ctx* c) {
     for (int k = 0; k < c->n[2]; k++)
@@ -720,7 +758,8 @@ int or_body_force(or_ctx* c) {
                 }
                 double g[3];
                 gradient_at(c, i, j, k, g);
-                double rho_e = -c->P.kappa * c->P.kappa * c->P.eps * c->psi[id];
+                double rho_e = c->P.phi_t > 0.0 ? -c->P.eps * screening(c, c->psi[id])
+                                                : -c->P.kappa * c->P.kappa * c->P.eps * c->psi[id];
                 for (int a = 0; a < 3; a++) c->fb[a * c->N + id] = rho_e * (c->P.E_ext[a] - g[a]);
             }
     return OR_OK;

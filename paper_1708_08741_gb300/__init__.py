@@ -76,6 +76,7 @@ class Params(ctypes.Structure):
         ("smoother", ctypes.c_int),
         ("mg_storage", ctypes.c_int),
         ("wall_slip", ctypes.c_int * 6),
+        ("phi_t", ctypes.c_double),
     ]
 
 
@@ -176,7 +177,8 @@ def make_params(wl, precision: int = ES_FP64, overrides: Optional[dict] = None) 
     d = dict(dims=wl.dims, periodic=wl.periodic, pot_bc=wl.pot_bc, pot_val=wl.pot_val, tau=wl.tau,
              kappa=wl.kappa, eps=wl.eps, E_ext=wl.E_ext, accel=wl.accel, rho_p_ratio=wl.rho_p_ratio,
              precision=precision, levels=wl.levels, nu1=wl.nu1, nu2=wl.nu2, coarse_sweeps=wl.coarse_sweeps,
-             omega=wl.omega, res_rf=wl.res_rf, max_cycles=wl.max_cycles, wall_slip=wl.wall_slip)
+             omega=wl.omega, res_rf=wl.res_rf, max_cycles=wl.max_cycles, wall_slip=wl.wall_slip,
+             phi_t=wl.phi_t)
     if overrides:
         d.update(overrides)
     for k, v in d.items():

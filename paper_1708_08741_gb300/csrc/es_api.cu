@@ -70,6 +70,9 @@ int validate(const es_params* P, const es_particle* parts, int n, std::string& w
             return why = "unknown potential boundary kind", ES_EINVAL;
     for (int f = 0; f < 6; f++)
         if (P->wall_slip[f] != 0 && P->wall_slip[f] != 1) return why = "wall_slip entries must be 0 or 1", ES_EINVAL;
+    if (!(P->phi_t >= 0.0) || std::isinf(P->phi_t)) return why = "phi_t must be finite and >= 0", ES_EINVAL;
+    if (P->phi_t > 0.0 && (P->precision != ES_FP64 || P->levels != 1))
+        return why = "the nonlinear Poisson-Boltzmann form (phi_t > 0) needs ES_FP64 and levels == 1", ES_EINVAL;
     for (int p = 0; p < n; p++) {
         if (!(parts[p].R > 0.0)) return why = "particle radius must be > 0", ES_EINVAL;
         if (parts[p].kind != ES_KIND_ZETA && parts[p].kind != ES_KIND_CHARGE)
@@ -125,6 +128,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
         lv += Nl * (1 + 3 * s + 4);  // states, e, e2, rhs, near-cell lists (+ one row per segment)
         if (l == 0 && P->mg_storage == ES_MG_FP16) lv -= Nl * (s - 2);  // e as FP16
     }
+    if (P->phi_t > 0.0) b += N * 8;  // linearised diagonal of the Poisson-Boltzmann stencil
     if (per_level) *per_level = lv;
     b += lv;
     b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8 + 14 * 4);
@@ -292,6 +296,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->psi = mixed(c) ? nullptr : (double*)A(N * 8);
     c->psi32 = mixed(c) ? (float*)A(N * 4) : nullptr;
     c->psi_lo = mixed(c) ? (float*)A(N * 4) : nullptr;
+    c->dk = c->P.phi_t > 0.0 ? (double*)A(N * 8) : nullptr;
     c->owner = (int32_t*)A(N * 4);
     c->flags = (uint8_t*)A(N);
     for (int l = 0; l < c->L; l++) {
@@ -356,6 +361,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     if (e == cudaSuccess && c->psi) e = cudaMemsetAsync(c->psi, 0, N * 8, c->stream);
     if (e == cudaSuccess && c->psi32) e = cudaMemsetAsync(c->psi32, 0, N * 4, c->stream);
     if (e == cudaSuccess && c->psi_lo) e = cudaMemsetAsync(c->psi_lo, 0, N * 4, c->stream);
+    if (e == cudaSuccess && c->dk) e = cudaMemsetAsync(c->dk, 0, N * 8, c->stream);
     if (e == cudaSuccess && c->pbc) e = cudaMemsetAsync(c->pbc, 0, np1 * 2 * sizeof(float), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fb, 0, 3 * N * s, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->F, 0, np1 * 3 * 8, c->stream);

@@ -104,6 +104,7 @@ struct es_ctx {
     double* psi;     // FP64 form only
     float* psi32;    // MIXED32: high part of psi
     float* psi_lo;   // MIXED32: low part of psi
+    double* dk;      // phi_t > 0: kappa^2 (cosh(psi / phi_t) - 1), the Newton diagonal shift
     float* pbc;      // MIXED32: np x 2, boundary value (2 zeta or sigma / eps) as float-float
     void* fb;
     // multigrid

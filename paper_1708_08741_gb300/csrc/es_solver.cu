@@ -80,8 +80,15 @@ __device__ __forceinline__ int fine_face(const Grid& g, const Solver& s, const i
 
 // r = b - A psi on the unknowns (FP64 form), stored as the V-cycle
 // right-hand side, and per-block partial sums of r^2.  Blocks stride over
-// rows (y, z); threads over x.
-__global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s, double diag0,
+// rows (y, z); threads over x.  PB: the nonlinear Poisson-Boltzmann form
+// (Eq. SPBE): the screening term kappa^2 psi of A psi becomes
+// kappa^2 phi_t sinh(psi / phi_t), and the kernel also leaves the shift of
+// the stencil's centre entry linearised about psi, kappa^2 (cosh(psi /
+// phi_t) - 1), for the sweeps of this iteration (Sec. 5.3: the stencils are
+// re-set at the start of every iteration).
+template <bool PB>
+__global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s, double diag0, double k2,
+                                                                double phi_t, double* __restrict__ dk,
                                                                 const double* __restrict__ psi,
                                                                 const uint8_t* __restrict__ st0,
                                                                 const int32_t* __restrict__ owner,
@@ -120,6 +127,11 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s
                             if (nb >= 0) off += psi[nb];
                         }
                     r = b - (diag * psi[c] - off);
+                }
+                if constexpr (PB) {
+                    const double pc = psi[c], u = pc / phi_t;
+                    r += k2 * pc - k2 * phi_t * sinh(u);
+                    dk[c] = k2 * (cosh(u) - 1.0);
                 }
                 acc += r * r;
             }
@@ -554,7 +566,7 @@ __device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* 
 template <class T>
 __global__ void __launch_bounds__(128) k_smooth(Level<T> L, const uint8_t* __restrict__ st,
                                                 const T* __restrict__ rhs, T* __restrict__ e, int colour,
-                                                int first, T omega) {
+                                                int first, T omega, const T* __restrict__ dk = nullptr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (2 * t >= L.nx) return;
@@ -571,6 +583,7 @@ __global__ void __launch_bounds__(128) k_smooth(Level<T> L, const uint8_t* __res
         level_stencil<T, false>(L, st, e, x, y, z, s, diag, off);
     else
         level_stencil<T, true>(L, st, e, x, y, z, s, diag, off);
+    if (dk) diag += dk[c];  // (nonlinear Poisson-Boltzmann: the linearised centre entry)
     const T gs = (L.h2 * rhs[c] + off) / diag;
     e[c] = first ? omega * gs : ((T)1 - omega) * e[c] + omega * gs;
 }
@@ -1374,7 +1387,7 @@ __device__ __forceinline__ float face_value_f(const Grid& g, const Solver& s, co
 // computed in the type P of the potential it reads (double, or the float
 // high part of psi in the reduced forms) and stored in the type S of f_b.
 template <class S, class P>
-__global__ void __launch_bounds__(128) k_body_force(Grid g, Solver s, P Ex, P Ey, P Ez, P k2e,
+__global__ void __launch_bounds__(128) k_body_force(Grid g, Solver s, P Ex, P Ey, P Ez, P k2e, P phi_t,
                                                     const P* __restrict__ psi, const uint8_t* __restrict__ flags,
                                                     const int32_t* __restrict__ owner,
                                                     const DParticle* __restrict__ part, const int* __restrict__ kind,
@@ -1423,7 +1436,8 @@ __global__ void __launch_bounds__(128) k_body_force(Grid g, Solver s, P Ex, P Ey
             g2 = (P)0.5 * (face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 2, 1) -
                            face_value<P>(g, s, psi, owner, part, kind, x, y, z, pc, 2, -1));
         }
-        const P rho_e = -k2e * pc;
+        // (phi_t > 0: the nonlinear Poisson-Boltzmann charge density)
+        const P rho_e = phi_t > (P)0 ? -k2e * phi_t * sinh(pc / phi_t) : -k2e * pc;
         f0 = rho_e * (Ex - g0);
         f1 = rho_e * (Ey - g1);
         f2 = rho_e * (Ez - g2);
@@ -1702,6 +1716,24 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
         }
     };
     if constexpr (kNative) {
+        if (l == c->L - 1 && c->dk) {
+            // nonlinear Poisson-Boltzmann (one level): red-black SOR sweeps on
+            // the Newton system with the linearised centre entries
+            for (int s = 0; s < c->P.coarse_sweeps; s++) {
+                {
+                    ProfScope ps(c, "smooth_half", l, nl * (2.0 * ts + 1.0));
+                    k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, s == 0, omega, (const T*)c->dk);
+                }
+                ProfScope ps(c, "smooth_half", l, nl * (2.0 * ts + 1.0));
+                k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega, (const T*)c->dk);
+                count(c, 2);
+            }
+            if (c->P.coarse_sweeps == 0) {
+                cudaError_t err = cudaMemsetAsync(e, 0, (size_t)Nl * sizeof(T), c->stream);
+                if (err != cudaSuccess) return err;
+            }
+            return cudaGetLastError();
+        }
         if (l == c->L - 1) {
             size_t sm = coarse_smem_bytes(c, sizeof(T));
             if (sm <= 200 * 1024) {
@@ -1813,8 +1845,15 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         count(c, 3);
         return cudaGetLastError();
     }
-    k_outer_residual<<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-        c->g, c->S, diag0, c->psi, c->st[0], c->owner, c->part, c->kind, (double*)c->rhs[0], c->partial);
+    const double k2 = c->S.kappa * c->S.kappa;
+    if (c->P.phi_t > 0.0)
+        k_outer_residual<true><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+            c->g, c->S, diag0, k2, c->P.phi_t, c->dk, c->psi, c->st[0], c->owner, c->part, c->kind,
+            (double*)c->rhs[0], c->partial);
+    else
+        k_outer_residual<false><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+            c->g, c->S, diag0, k2, 0.0, nullptr, c->psi, c->st[0], c->owner, c->part, c->kind,
+            (double*)c->rhs[0], c->partial);
     k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, c->red_blocks, c->d_norm);
     count(c, 2);
     return cudaGetLastError();
@@ -1885,11 +1924,12 @@ cudaError_t launch_body_force(es_ctx* c) {
         count(c);
     } else if (mixed(c))
         k_body_force<float, float><<<grd, blk, 0, c->stream>>>(g, c->S, (float)E[0], (float)E[1], (float)E[2],
-                                                               (float)k2e, c->psi32, c->flags, c->owner, c->part,
+                                                               (float)k2e, 0.0f, c->psi32, c->flags, c->owner, c->part,
                                                                c->kind, c->st[0], (const float2*)c->pbc, wall2,
                                                                (float*)c->fb);
     else
-        k_body_force<double, double><<<grd, blk, 0, c->stream>>>(g, c->S, E[0], E[1], E[2], k2e, c->psi, c->flags,
+        k_body_force<double, double><<<grd, blk, 0, c->stream>>>(g, c->S, E[0], E[1], E[2], k2e, c->P.phi_t,
+                                                                 c->psi, c->flags,
                                                                  c->owner, c->part, c->kind, c->st[0], nullptr,
                                                                  wall2, (double*)c->fb);
     count(c);

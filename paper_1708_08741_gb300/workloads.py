@@ -94,6 +94,7 @@ class Workload:
     steps: int = 100
     pot_bc: Sequence[int] = (0, 0, 0, 0, 0, 0)
     wall_slip: Sequence[int] = (0, 0, 0, 0, 0, 0)  # per face of a non-periodic axis: 1 = free-slip
+    phi_t: float = 0.0  # thermal voltage k_B T / (z e): 0 = Debye-Hueckel, > 0 = nonlinear Poisson-Boltzmann
     pot_val: Sequence[float] = (0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
     # particle arrays
     x: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))

@@ -226,6 +226,30 @@ def test_free_slip_reduced_precision_after_100_steps(precision):
     assert r["u"] < (MIXED_TOL if precision == es.ES_MIXED32 else MIXED16_U_TOL)
 
 
+def _pb(wl, phi_t, sweeps=2, omega=1.5):
+    wl.phi_t, wl.levels, wl.coarse_sweeps, wl.omega, wl.max_cycles = phi_t, 1, sweeps, omega, 5000
+    return wl
+
+
+PB_CASES = {
+    # zeta = 4 phi_t: far outside the Debye-Hueckel regime
+    "sphere_zeta": lambda: _pb(W.single_sphere(n=24, radius=4.0, zeta=2.0), 0.5),
+    # walls in z (Dirichlet and zero-flux faces), zeta and charged spheres, moving
+    "mixed_walls": lambda: _pb(W.mixed_box(dims=(24, 16, 20)), 0.6, sweeps=1, omega=1.7),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PB_CASES))
+def test_coupled_nonlinear_poisson_boltzmann_fp64(name):
+    """The nonlinear Poisson-Boltzmann form (SOR-Newton with the stencil
+    re-linearised each iteration, sinh charge density in the body force),
+    coupled with the LBM and the particles, against the oracle: FP64 bar."""
+    p, r = _coupled(PB_CASES[name](), 8)
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x", "v"):
+        assert r[k] < FP64_TOL, (k, r[k])
+
+
 @pytest.mark.parametrize("maker", [lambda: W.single_sphere(),
                                    lambda: W.channel(n=64, n_spheres=8, radius=5.0, levels=4)])
 def test_mixed32_within_1e4_after_100_steps(maker):

@@ -277,3 +277,116 @@ def test_uniform_potential_body_force():
     fb = o.field(oracle.FIELD_FB)
     for d in range(3):
         np.testing.assert_allclose(fb[d], -0.25 * 0.7 * wl.E_ext[d], rtol=1e-14)
+
+
+# ---- nonlinear Poisson-Boltzmann form (Eq. SPBE) ---------------------------
+# With kappa^2 = 2 z^2 e^2 n / (eps k_B T) and phi_t = k_B T / (z e), Eq. SPBE
+# reads -lap psi + kappa^2 phi_t sinh(psi / phi_t) = 0 in the electrolyte; the
+# oracle solves it with the paper's SOR sweeps on the stencil re-linearised at
+# every iteration (levels == 1).
+
+
+def _pb(wl, phi_t, sweeps=1, omega=1.0):
+    wl.phi_t = phi_t
+    wl.levels = 1
+    wl.coarse_sweeps = sweeps
+    wl.omega = omega
+    return wl
+
+
+def _dense_newton(A, b, kappa, phi_t, iters=60):
+    """Newton's method on the dense finite-volume system with the screening
+    term replaced: F(x) = (A - kappa^2 I) x + kappa^2 phi_t sinh(x / phi_t) - b."""
+    k2 = kappa * kappa
+    L = A - k2 * np.eye(len(b))
+    x = np.linalg.solve(A, b)
+    for _ in range(iters):
+        F = L @ x + k2 * phi_t * np.sinh(x / phi_t) - b
+        J = L + np.diag(k2 * np.cosh(x / phi_t))
+        dx = np.linalg.solve(J, -F)
+        x = x + dx
+        if np.max(np.abs(dx)) < 1e-15 * max(1.0, np.max(np.abs(x))):
+            break
+    return x
+
+
+@pytest.mark.parametrize("case", ["periodic_zeta", "mixed"])
+def test_pb_matches_dense_newton_8cubed(case):
+    """The oracle's SOR-Newton iteration converges to the solution of the
+    nonlinear finite-volume system assembled directly (as in the dense
+    Debye-Hueckel test) and solved by Newton's method with dense linear
+    algebra.  zeta up to 4 phi_t: far outside the linear regime."""
+    if case == "periodic_zeta":
+        wl = _wl((8, 8, 8), (1, 1, 1), 0.4, [((4.0, 4.0, 4.0), 1.6, W.KIND_ZETA, 2.0, 0.0)])
+        phi_t = 0.5
+    else:
+        wl = _wl((8, 8, 8), (0, 1, 1), 0.5, [((2.5, 2.5, 3.0), 1.2, W.KIND_ZETA, -1.2, 0.0),
+                                              ((5.6, 5.5, 5.5), 1.5, W.KIND_CHARGE, 0.0, -2.5)],
+                 pot_bc=(1, 0, 0, 0, 0, 0), pot_val=(0.9, 0, 0, 0, 0, 0))
+        phi_t = 0.3
+    wl = _pb(wl, phi_t, sweeps=2, omega=1.4)
+    wl.max_cycles = 2000
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    info = o.solve()
+    assert info["status"] == 0 and info["r"] < info["tol"]
+    owner = o.owner()
+    A, b, idx, _ = _dense_system(wl.dims, wl.periodic, wl.kappa, owner, wl.kind, wl.zeta, wl.q,
+                                 wl.pot_bc, wl.pot_val)
+    x = _dense_newton(A, b, wl.kappa, phi_t)
+    lin = np.linalg.solve(A, b)
+    psi = o.field(oracle.FIELD_PSI)
+    got, ref = psi[owner < 0], x[idx[owner < 0]]
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-11
+    # (and it is not the Debye-Hueckel solution)
+    assert np.max(np.abs(lin[idx[owner < 0]] - ref)) > 1e-2 * np.max(np.abs(ref))
+
+
+def test_pb_gouy_chapman_profile_and_electroneutrality():
+    """Flat Dirichlet wall at z = 0 (zeta = 3 phi_t), zero flux far away: the
+    continuum solution is Gouy-Chapman's psi = 4 phi_t artanh(tanh(zeta /
+    (4 phi_t)) exp(-kappa d)), d the distance from the wall (cell centres at
+    d = k + 1/2).  The finite-volume solution approaches it as kappa h falls:
+    the error must drop at least 2.5-fold when kappa h halves.  At convergence
+    the double layer's charge, the sum of rho_e over the column (read back
+    from f_b = rho_e E_x with a field along the wall), balances the wall
+    flux eps (psi_ghost - psi_0) = 2 eps (zeta - psi_0) exactly."""
+    phi_t, zeta, E = 0.4, 1.2, 1e-3
+    errs = []
+    for kappa, H in ((0.2, 80), (0.1, 160)):
+        wl = _wl((1, 1, H), (1, 1, 0), kappa, pot_bc=(0, 0, 0, 0, 1, 0),
+                 pot_val=(0, 0, 0, 0, zeta, 0), E=(E, 0.0, 0.0), max_cycles=20000)
+        wl = _pb(wl, phi_t, sweeps=4, omega=1.9)
+        o = oracle.Oracle(wl)
+        o.map_particles()
+        info = o.solve()
+        assert info["status"] == 0 and info["r"] < info["tol"]
+        psi = o.field(oracle.FIELD_PSI)[:, 0, 0]
+        d = np.arange(H) + 0.5
+        gc = 4.0 * phi_t * np.arctanh(np.tanh(zeta / (4.0 * phi_t)) * np.exp(-kappa * d))
+        near = d * kappa < 3.0
+        errs.append(np.max(np.abs(psi[near] - gc[near])) / zeta)
+        o.body_force()
+        rho = o.field(oracle.FIELD_FB)[0][:, 0, 0] / E
+        assert abs(rho.sum() + 2.0 * (zeta - psi[0])) < 1e-10 * zeta
+    assert errs[0] < 2e-2 and errs[1] < 0.4 * errs[0]
+
+
+def test_pb_tends_to_debye_hueckel_for_large_thermal_voltage():
+    """sinh(x) = x + x^3/6 + ...: with phi_t = 1e3 |psi| the nonlinear solve
+    lands on the Debye-Hueckel solution to ~1e-7."""
+    wl = _wl((8, 8, 8), (1, 1, 1), 0.4, [((4.0, 4.0, 4.0), 1.6, W.KIND_ZETA, 0.8, 0.0)])
+    wl.coarse_sweeps = 2
+    wl.omega = 1.4
+    wl.max_cycles = 2000
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    o.solve()
+    lin = o.field(oracle.FIELD_PSI)
+    o2 = oracle.Oracle(_pb(wl, 800.0, sweeps=2, omega=1.4))
+    o2.map_particles()
+    o2.solve()
+    nl = o2.field(oracle.FIELD_PSI)
+    fluid = o.owner() < 0
+    d = np.max(np.abs(nl[fluid] - lin[fluid])) / np.max(np.abs(lin[fluid]))
+    assert 1e-12 < d < 1e-6
