@@ -117,6 +117,9 @@ typedef struct {
                            the current psi (Sec. 5.3); needs ES_FP64, levels == 1.
                            The charge density becomes -eps kappa^2 phi_t
                            sinh(psi / phi_t).                                      */
+    int fine_layout;    /* ES_LAYOUT_AUTO (0, default) or ES_LAYOUT_NATURAL: storage of
+                           the finest level's multigrid correction and right-hand
+                           side (see below); both give the same iteration          */
 } es_params;
 
 /* Execution of one red-black Gauss-Seidel sweep (same arithmetic either way):
@@ -135,6 +138,15 @@ typedef struct {
    does not move the converged potential. */
 #define ES_MG_NATIVE 0
 #define ES_MG_FP16 1
+
+/* AUTO: in the reduced precisions, with the two-pass smoother, native
+   correction storage, levels >= 2 and dims[0] % 8 == 0, the finest level's
+   e and rhs are stored colour-split (all cells of colour (x+y+z) % 2 = 0,
+   then all of colour 1, each in natural order), so that a red or black half
+   sweep streams only its own colour; otherwise, and with NATURAL, cell
+   x + nx (y + ny z) is element x + nx (y + ny z). */
+#define ES_LAYOUT_AUTO 0
+#define ES_LAYOUT_NATURAL 1
 
 typedef struct {
     double x[3]; /* centre                  */

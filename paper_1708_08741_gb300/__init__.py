@@ -35,6 +35,8 @@ ES_SMOOTH_TWO_PASS = 0
 ES_SMOOTH_FUSED = 1
 ES_MG_NATIVE = 0
 ES_MG_FP16 = 1
+ES_LAYOUT_AUTO = 0
+ES_LAYOUT_NATURAL = 1
 
 FIELD_PSI = 0
 FIELD_RHO = 1
@@ -77,6 +79,7 @@ class Params(ctypes.Structure):
         ("mg_storage", ctypes.c_int),
         ("wall_slip", ctypes.c_int * 6),
         ("phi_t", ctypes.c_double),
+        ("fine_layout", ctypes.c_int),
     ]
 
 

@@ -71,6 +71,8 @@ int validate(const es_params* P, const es_particle* parts, int n, std::string& w
     for (int f = 0; f < 6; f++)
         if (P->wall_slip[f] != 0 && P->wall_slip[f] != 1) return why = "wall_slip entries must be 0 or 1", ES_EINVAL;
     if (!(P->phi_t >= 0.0) || std::isinf(P->phi_t)) return why = "phi_t must be finite and >= 0", ES_EINVAL;
+    if (P->fine_layout != ES_LAYOUT_AUTO && P->fine_layout != ES_LAYOUT_NATURAL)
+        return why = "fine_layout must be ES_LAYOUT_AUTO or ES_LAYOUT_NATURAL", ES_EINVAL;
     if (P->phi_t > 0.0 && (P->precision != ES_FP64 || P->levels != 1))
         return why = "the nonlinear Poisson-Boltzmann form (phi_t > 0) needs ES_FP64 and levels == 1", ES_EINVAL;
     for (int p = 0; p < n; p++) {
@@ -249,6 +251,9 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->g.ny = params->dims[1];
     c->g.nz = params->dims[2];
     for (int a = 0; a < 3; a++) c->g.per[a] = params->periodic[a] ? 1 : 0;
+    c->rb0 = (params->precision != ES_FP64) && params->dims[0] % 8 == 0 &&
+             params->smoother == ES_SMOOTH_TWO_PASS && params->mg_storage == ES_MG_NATIVE && params->levels >= 2 &&
+             params->fine_layout == ES_LAYOUT_AUTO;
     c->slip = 0;
     for (int f = 0; f < 6; f++)
         if (!c->g.per[f / 2] && params->wall_slip[f]) c->slip |= 1 << f;

@@ -133,6 +133,7 @@ struct es_ctx {
     double mg_rate;  // running estimate of the residual reduction per V-cycle
     float e_scale;   // ES_MG_FP16: scale of the finest level's stored correction
     int slip;        // bit f: face f (x-lo, x-hi, y-lo, ...) of a non-periodic axis is free-slip
+    bool rb0;        // the finest level's e and rhs in the colour-split layout (reduced forms)
     double lambda_e, lambda_o;
     size_t bytes;
     unsigned long long launches;  // kernels launched by this context

@@ -142,6 +142,15 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_residual(Grid g, Solver s
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
+// Stores natural cells c .. c+3 (c % 4 == 0, cell c of colour col) of a
+// float field in the colour-split layout (cells c, c+2 of colour col sit at
+// c/2, c/2+1 of half col; cells c+1, c+3 at the same places of the other).
+__device__ __forceinline__ void rb_st4(float* base, int half, int c, int col, float v0, float v1, float v2,
+                                       float v3) {
+    *reinterpret_cast<float2*>(base + col * half + (c >> 1)) = make_float2(v0, v2);
+    *reinterpret_cast<float2*>(base + (col ^ 1) * half + (c >> 1)) = make_float2(v1, v3);
+}
+
 // Wall boundary values 2 * pot_val of a Dirichlet wall, as float-float.
 struct WallFF {
     float hi[6], lo[6];
@@ -279,6 +288,7 @@ __device__ __forceinline__ float near_residual_ff(const Grid& g, ff diag0, const
 // The float-float residual at the near-boundary unknown cells of level 0,
 // from the near-cell list (both colours), written to r_out before the main
 // pass, which reads them back into its norm sum.
+template <class M>
 __global__ void __launch_bounds__(256) k_outer_residual_near_ff(Grid g, ff diag0, WallFF wall, int pot_dir_mask,
                                                                 const float* __restrict__ psi_hi,
                                                                 const float* __restrict__ psi_lo,
@@ -287,19 +297,21 @@ __global__ void __launch_bounds__(256) k_outer_residual_near_ff(Grid g, ff diag0
                                                                 const float2* __restrict__ pbc,
                                                                 const int* __restrict__ list,
                                                                 const int* __restrict__ count, int cap,
-                                                                float* __restrict__ r_out) {
+                                                                float* __restrict__ r_out, M m) {
     // blockIdx.y: list segment
     const int n = count[blockIdx.y];
     const int* seg = list + (size_t)blockIdx.y * cap;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = seg[i];
         const int x = c % g.nx, yz = c / g.nx;
-        r_out[c] = near_residual_ff(g, diag0, wall, pot_dir_mask, psi_hi, psi_lo, st0, owner, pbc, x, yz % g.ny,
-                                    yz / g.ny);
+        const int y = yz % g.ny, z = yz / g.ny;
+        r_out[m(c, (x + y + z) & 1)] =
+            near_residual_ff(g, diag0, wall, pot_dir_mask, psi_hi, psi_lo, st0, owner, pbc, x, y, z);
     }
 }
 
-template <int W>
+// SPLIT: r is stored in the colour-split layout (W == 4).
+template <int W, bool SPLIT>
 __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, WallFF wall,
                                                            const float* __restrict__ psi_hi,
                                                            const float* __restrict__ psi_lo,
@@ -308,7 +320,9 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
                                                            const float2* __restrict__ pbc, int pot_dir_mask,
                                                            float* __restrict__ r_out,
                                                            double* __restrict__ partial) {
+    static_assert(!SPLIT || W == 4, "the split store takes 4-cell spans");
     __shared__ float swarp[8];
+    const int half = (int)(g.N >> 1);
     float acc = 0.0f;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int xs = W * (blockIdx.x * 32 + threadIdx.x);
@@ -403,13 +417,21 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
             }
         }
         // near-boundary cells: formed by k_outer_residual_near_ff just before
+        const int col0 = (xs + y + z) & 1;
 #pragma unroll
         for (int i = 0; i < W; i++)
-            if ((near_bits >> i) & 1u) out[i] = r_out[row + xs + i];
+            if ((near_bits >> i) & 1u) {
+                if constexpr (SPLIT)
+                    out[i] = r_out[((col0 + i) & 1) * half + ((row + xs + i) >> 1)];
+                else
+                    out[i] = r_out[row + xs + i];
+            }
 #pragma unroll
         for (int i = 0; i < W; i++) acc = __fmaf_rn(out[i], out[i], acc);
         if (lane_on) {
-            if constexpr (W == 4) {
+            if constexpr (SPLIT) {
+                rb_st4(r_out, half, row + xs, col0, out[0], out[1], out[2], out[3]);
+            } else if constexpr (W == 4) {
                 *reinterpret_cast<float4*>(r_out + row + xs) = make_float4(out[0], out[1], out[2], out[3]);
             } else {
                 r_out[row + xs] = out[0];
@@ -466,6 +488,14 @@ __device__ __forceinline__ void vst(double* p, double a, double b, double c, dou
         arr[(off) + 3] = q_.v3;    \
     } while (0)
 
+// Loads natural cells c .. c+3 of a float field in the colour-split layout
+// (the placement of rb_st4; 8-byte loads).
+__device__ __forceinline__ Q4<float> rb_ld4(const float* base, int half, int c, int col) {
+    const float2 a = *reinterpret_cast<const float2*>(base + col * half + (c >> 1));
+    const float2 b = *reinterpret_cast<const float2*>(base + (col ^ 1) * half + (c >> 1));
+    return {a.x, b.x, a.y, b.y};
+}
+
 // Access to a level's correction e stored as E: the arithmetic type T
 // itself, or (finest level, ES_MG_FP16) FP16 holding s * e, with the scale
 // s = sqrt(N) / ||r|| set per correction so that the stored values sit near
@@ -508,14 +538,29 @@ struct EAcc<float, __half> {
         arr[(off) + 3] = q_.v3;       \
     } while (0)
 
+// Storage index of a level's e and rhs: the natural index (x + nx (y + ny z)),
+// or the colour-split layout of the finest level in the reduced forms
+// (nx % 8 == 0): the cells of colour (x + y + z) % 2 = k are stored
+// contiguously in half k, cell c at k * N/2 + c / 2 (c / 2 = x / 2 +
+// nx/2 (y + ny z) for even nx), so that a half sweep streams only its own
+// colour and reads the other one.  col is the cell's colour.
+struct NatMap {
+    __device__ __forceinline__ int operator()(int c, int) const { return c; }
+};
+struct RbMap {
+    int half;
+    __device__ __forceinline__ int operator()(int c, int col) const { return col * half + (c >> 1); }
+};
+
 // Diagonal and off-diagonal sum of level l at an unknown cell.  With
 // READ = false only the diagonal is formed (off = 0, e is not touched).
-template <class T, bool READ = true, class E = T>
+template <class T, bool READ = true, class E = T, class M = NatMap>
 __device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* st, const E* e, int x, int y,
                                               int z, uint8_t s, T& diag, T& off,
-                                              const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}) {
+                                              const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}, M m = M{}) {
     const int nx = L.nx, nxy = L.nx * L.ny;
     const int c = x + nx * y + nxy * z;
+    const int ncol = 1 - ((x + y + z) & 1);  // (the six neighbours have the other colour)
     if (!(s & ST_NEAR)) {
         diag = L.diag0;
         if (!READ) {
@@ -525,12 +570,12 @@ __device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* 
         const int xm = (x == 0 ? nx - 1 : x - 1) - x, xp = (x == nx - 1 ? 0 : x + 1) - x;
         const int ym = (y == 0 ? L.ny - 1 : y - 1) - y, yp = (y == L.ny - 1 ? 0 : y + 1) - y;
         const int zm = (z == 0 ? L.nz - 1 : z - 1) - z, zp = (z == L.nz - 1 ? 0 : z + 1) - z;
-        T o = A.ld(e + c + xm);
-        o += A.ld(e + c + xp);
-        o += A.ld(e + c + ym * nx);
-        o += A.ld(e + c + yp * nx);
-        o += A.ld(e + c + zm * nxy);
-        o += A.ld(e + c + zp * nxy);
+        T o = A.ld(e + m(c + xm, ncol));
+        o += A.ld(e + m(c + xp, ncol));
+        o += A.ld(e + m(c + ym * nx, ncol));
+        o += A.ld(e + m(c + yp * nx, ncol));
+        o += A.ld(e + m(c + zm * nxy, ncol));
+        o += A.ld(e + m(c + zp * nxy, ncol));
         off = o;
         return;
     }
@@ -550,7 +595,7 @@ __device__ __forceinline__ void level_stencil(const Level<T>& L, const uint8_t* 
             const int nb = c + (p - v[a]) * stride[a];
             const uint8_t k = st[nb] & ST_KIND;
             if (k == ST_UNKNOWN) {
-                if (READ) o += A.ld(e + nb);
+                if (READ) o += A.ld(e + m(nb, ncol));
             } else {
                 dg += (k == ST_DIR) ? (T)1 : (T)-1;
             }
@@ -618,34 +663,39 @@ __device__ __forceinline__ void span_update(const Level<T>& L, T inv_diag0, T (&
 
 // Gauss-Seidel value of one near-boundary unknown cell of level l, read
 // from global memory (the boundary faces per Sec. 5.4 as level_stencil).
-template <class T, class E = T>
+// first: 0 the iterate is read; 1 the iterate starts at zero (nothing is
+// read); 2 the cell's own old value is zero but its neighbours are read
+// (the second colour of a sweep from zero in the colour-split layout).
+template <class T, class E = T, class M = NatMap>
 __device__ __forceinline__ T near_gs(const Level<T>& L, const uint8_t* __restrict__ st, const T* __restrict__ rhs,
                                      const E* e, int x, int y, int z, int first, T omega,
-                                     const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}) {
+                                     const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}, M m = M{}) {
     const int cidx = x + L.nx * (y + L.ny * z);
+    const int col = (x + y + z) & 1;
     const uint8_t s = st[cidx];
     T diag, off;
-    if (first)
-        level_stencil<T, false, E>(L, st, e, x, y, z, s, diag, off, A);
+    if (first == 1)
+        level_stencil<T, false, E, M>(L, st, e, x, y, z, s, diag, off, A, m);
     else
-        level_stencil<T, true, E>(L, st, e, x, y, z, s, diag, off, A);
-    const T gs = (L.h2 * rhs[cidx] + off) / diag;
-    return first ? omega * gs : ((T)1 - omega) * A.ld(e + cidx) + omega * gs;
+        level_stencil<T, true, E, M>(L, st, e, x, y, z, s, diag, off, A, m);
+    const T gs = (L.h2 * rhs[m(cidx, col)] + off) / diag;
+    return first ? omega * gs : ((T)1 - omega) * A.ld(e + m(cidx, col)) + omega * gs;
 }
 
 // The near-boundary unknown cells of one colour of a level, from that
 // colour's segments of the level's near-cell list (blockIdx.y: segment).
-template <class T, class E>
+template <class T, class E, class M = NatMap>
 __global__ void __launch_bounds__(256) k_smooth_near(Level<T> L, const uint8_t* __restrict__ st,
                                                      const T* __restrict__ rhs, E* __restrict__ e,
                                                      const int* __restrict__ list, const int* __restrict__ count,
-                                                     int cap, int first, T omega, EAcc<T, E> A) {
+                                                     int cap, int first, T omega, EAcc<T, E> A, M m = M{}) {
     const int n = count[blockIdx.y];
     const int* seg = list + (size_t)blockIdx.y * cap;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = seg[i];
         const int x = c % L.nx, yz = c / L.nx;
-        A.st(e + c, near_gs<T, E>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, first, omega, A));
+        const int y = yz % L.ny, z = yz / L.ny;
+        A.st(e + m(c, (x + y + z) & 1), near_gs<T, E, M>(L, st, rhs, e, x, y, z, first, omega, A, m));
     }
 }
 
@@ -769,6 +819,99 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
 #pragma unroll
         for (int v = 0; v < W; v += 4) A.st4(e + row + xs + v, c[1 + v], c[2 + v], c[3 + v], c[4 + v]);
     }
+}
+
+// The update of a 4-cell span of one colour in the colour-split layout
+// (interior cells only; O: offset of the colour's cells in the row, x = 2i + O).
+// ox[j] holds the other colour at compact index i0 - 1 + j, so the x
+// neighbours of cell i0 + k are ox[k + O] (left) and ox[k + 1 + O] (right).
+template <class T, int O>
+__device__ __forceinline__ void rb_span_update(T inv_diag0, T h2, T (&c)[4], const T (&ox)[6], const T (&a)[4],
+                                               const T (&b)[4], const T (&d)[4], const T (&f)[4],
+                                               const T (&r)[4], uint2 sw, int first, T omega) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int bit = 2 * k + O;  // natural position in the 8-cell state span
+        const unsigned sv = ((bit < 4 ? sw.x : sw.y) >> (8 * (bit & 3))) & 0xFFu;
+        if ((sv & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;  // (c[k] is 0 when first)
+        T o = ox[k + O];
+        o += ox[k + 1 + O];
+        o += a[k];
+        o += b[k];
+        o += d[k];
+        o += f[k];
+        const T gs = (h2 * r[k] + o) * inv_diag0;
+        c[k] = first ? omega * gs : ((T)1 - omega) * c[k] + omega * gs;
+    }
+}
+
+// One red (colour 0) or black (1) half sweep of the finest level in the
+// colour-split layout (reduced forms, nx % 8 == 0): a thread owns 4
+// consecutive cells of the colour in one row (8 natural cells), loads them,
+// the other colour at the same compact places of its own row (plus one
+// halo value) and of the four neighbour rows, and its right-hand side, as
+// 16-byte vectors, and writes back only its own colour.  Per cell and half
+// sweep that moves e of both colours once, rhs and e of the colour
+// once and the state bytes: 9 bytes instead of the 13 of the interleaved
+// layout, whose spans also stream the other colour's e and rhs.  Same
+// per-cell arithmetic as k_smooth_v; near-boundary cells are left to
+// k_smooth_near.  first: 1 the iterate starts at zero (nothing is read;
+// the colour's cells that are not updated are written as zero), 2 the
+// colour's old values are zero (the second colour of a sweep from zero; its
+// other cells are written as zero too), so the other colour never needs
+// clearing.
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
+                                                   const T* __restrict__ rhs, T* __restrict__ e, int colour,
+                                                   int first, T omega, int half) {
+    const int nxh = L.nx >> 1;
+    const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    if (y >= L.ny) return;
+    const bool lane_on = i0 < nxh;
+    const int iq = lane_on ? i0 : 0;  // (inactive lanes read a valid span)
+    const int ny = L.ny, nz = L.nz;
+    const int O = (colour + y + z) & 1;  // the colour's cells in this row: x = 2 i + O
+    const T* eo = e + (colour ^ 1) * half;
+    T* es = e + colour * half;
+    // unguarded wrapped loads, as in k_smooth_v: beyond a wall only
+    // near-boundary cells would read, and those are updated from the list
+    int ym, yp, zm, zp, il, ir;
+    if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
+    if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
+    if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
+    if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
+    if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
+    if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
+    const int rowh = nxh * (y + ny * z);
+    T c[4], ox[6], a[4], b[4], d[4], f[4], r[4];
+    if (first == 1) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) c[k] = a[k] = b[k] = d[k] = f[k] = (T)0;
+#pragma unroll
+        for (int k = 0; k < 6; k++) ox[k] = (T)0;
+    } else {
+        if (first == 2) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) c[k] = (T)0;
+        } else {
+            ES_VLD(c, 0, es + rowh + iq);
+        }
+        ES_VLD(ox, 1, eo + rowh + iq);
+        ox[0] = O == 0 ? eo[rowh + il] : (T)0;
+        ox[5] = O == 1 ? eo[rowh + ir] : (T)0;
+        ES_VLD(a, 0, eo + nxh * (ym + ny * z) + iq);
+        ES_VLD(b, 0, eo + nxh * (yp + ny * z) + iq);
+        ES_VLD(d, 0, eo + nxh * (y + ny * zm) + iq);
+        ES_VLD(f, 0, eo + nxh * (y + ny * zp) + iq);
+    }
+    ES_VLD(r, 0, rhs + colour * half + rowh + iq);
+    const uint2 sw = *reinterpret_cast<const uint2*>(st + L.nx * (y + ny * z) + 2 * iq);
+    if (O == 0)
+        rb_span_update<T, 0>(inv_diag0, L.h2, c, ox, a, b, d, f, r, sw, first == 1, omega);
+    else
+        rb_span_update<T, 1>(inv_diag0, L.h2, c, ox, a, b, d, f, r, sw, first == 1, omega);
+    if (lane_on) vst(es + rowh + i0, c[0], c[1], c[2], c[3]);
 }
 
 __device__ __forceinline__ bool axis_ok(int v, int n, int per, int& w) {
@@ -1110,10 +1253,10 @@ __global__ void __launch_bounds__(128) k_prolong(Level<T> L, const uint8_t* __re
 
 // Vectorized prolongation: a thread owns 4 fine cells of a row (nx % 4 == 0)
 // and adds the correction of their 2 parents.
-template <class T, class E>
+template <class T, class E, bool SPLIT = false>
 __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __restrict__ st, E* __restrict__ e,
                                                    int cnx, int cny, const uint8_t* __restrict__ cst,
-                                                   const T* __restrict__ ce, EAcc<T, E> A) {
+                                                   const T* __restrict__ ce, EAcc<T, E> A, int half = 0) {
     const int xs = 4 * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
     if (xs >= L.nx || y >= L.ny) return;
@@ -1122,7 +1265,12 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
     const unsigned sw = *reinterpret_cast<const unsigned*>(st + c);
     const uint8_t c0 = cst[C] & ST_KIND, c1 = cst[C + 1] & ST_KIND;
     const T e0 = ce[C], e1 = ce[C + 1];
-    const auto q = A.ld4(e + c);
+    const int col0 = (xs + y + z) & 1;
+    Q4<T> q;
+    if constexpr (SPLIT)
+        q = rb_ld4(e, half, c, col0);
+    else
+        q = A.ld4(e + c);
     T v[4] = {q.v0, q.v1, q.v2, q.v3};
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -1130,7 +1278,10 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
         const uint8_t pk = i < 2 ? c0 : c1;
         if (sv == ST_UNKNOWN && pk == ST_UNKNOWN) v[i] += i < 2 ? e0 : e1;
     }
-    A.st4(e + c, v[0], v[1], v[2], v[3]);
+    if constexpr (SPLIT)
+        rb_st4(e, half, c, col0, v[0], v[1], v[2], v[3]);
+    else
+        A.st4(e + c, v[0], v[1], v[2], v[3]);
 }
 
 // Vectorized residual + restriction: a thread owns 2 coarse cells of a
@@ -1139,40 +1290,43 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
 // neighbouring vectors) and the 4 neighbour rows as 16-byte vectors, forms
 // the residuals and adds them to the coarse sums in the children order
 // (dk, dj, di) of the scalar kernel.
-template <class T, class E = T>
+template <class T, class E = T, class M = NatMap>
 __device__ __forceinline__ T near_residual(const Level<T>& L, const uint8_t* __restrict__ st,
                                            const T* __restrict__ rhs, const E* __restrict__ e, int x, int y, int z,
-                                           T inv_h2, const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}) {
+                                           T inv_h2, const EAcc<T, E>& A = EAcc<T, E>{(T)1, (T)1}, M m = M{}) {
     const int cidx = x + L.nx * (y + L.ny * z);
+    const int sc = m(cidx, (x + y + z) & 1);
     T diag, off;
-    level_stencil<T, true, E>(L, st, e, x, y, z, st[cidx], diag, off, A);
-    return rhs[cidx] - (diag * A.ld(e + cidx) - off) * inv_h2;
+    level_stencil<T, true, E, M>(L, st, e, x, y, z, st[cidx], diag, off, A, m);
+    return rhs[sc] - (diag * A.ld(e + sc) - off) * inv_h2;
 }
 
 // The residual at the near-boundary unknown cells of a level, from its
 // near-cell list (both colours), into a scratch array that the restriction
 // then reads for those children.
-template <class T, class E>
+template <class T, class E, class M = NatMap>
 __global__ void __launch_bounds__(256) k_near_residual(Level<T> L, const uint8_t* __restrict__ st,
                                                        const T* __restrict__ rhs, const E* __restrict__ e,
                                                        const int* __restrict__ list, const int* __restrict__ count,
-                                                       int cap, T inv_h2, T* __restrict__ out, EAcc<T, E> A) {
+                                                       int cap, T inv_h2, T* __restrict__ out, EAcc<T, E> A,
+                                                       M m = M{}) {
     // blockIdx.y: list segment
     const int n = count[blockIdx.y];
     const int* seg = list + (size_t)blockIdx.y * cap;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = seg[i];
         const int x = c % L.nx, yz = c / L.nx;
-        out[c] = near_residual<T, E>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, inv_h2, A);
+        out[c] = near_residual<T, E, M>(L, st, rhs, e, x, yz % L.ny, yz / L.ny, inv_h2, A, m);  // (natural)
     }
 }
 
-template <class T, class E>
+// SPLIT: e and rhs of this level in the colour-split layout (float).
+template <class T, class E, bool SPLIT = false>
 __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T inv_h2, const uint8_t* __restrict__ st,
                                                     const T* __restrict__ rhs, const E* __restrict__ e,
                                                     const T* __restrict__ near_res, int cnx,
                                                     int cny, const uint8_t* __restrict__ cst, T* __restrict__ crhs,
-                                                    EAcc<T, E> A) {
+                                                    EAcc<T, E> A, int half = 0) {
     const int cx_warp = 2 * (blockIdx.x * 32);
     const int cxs = cx_warp + 2 * threadIdx.x;
     const int cy = blockIdx.y * 8 + threadIdx.y, cz = blockIdx.z;
@@ -1200,14 +1354,34 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
             const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
             const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
             T c[6], a[4], b[4], d[4], f[4], r[4];
-            c[0] = A.ld(e + row + xl);
-            c[5] = A.ld(e + row + xr);
-            ES_ELD(A, c, 1, e + row + xq);
-            ES_ELD(A, a, 0, e + rym + xq);
-            ES_ELD(A, b, 0, e + ryp + xq);
-            ES_ELD(A, d, 0, e + rzm + xq);
-            ES_ELD(A, f, 0, e + rzp + xq);
-            ES_VLD(r, 0, rhs + row + xq);
+            if constexpr (SPLIT) {
+                static_assert(std::is_same<T, float>::value && std::is_same<E, float>::value, "float split layout");
+                const RbMap mp{half};
+                const int yz = y + z, col0 = (xq + yz) & 1;
+                c[0] = e[mp(row + xl, (xl + yz) & 1)];
+                c[5] = e[mp(row + xr, (xr + yz) & 1)];
+                auto put = [](T* v, int o, Q4<T> q) {
+                    v[o] = q.v0;
+                    v[o + 1] = q.v1;
+                    v[o + 2] = q.v2;
+                    v[o + 3] = q.v3;
+                };
+                put(c, 1, rb_ld4(e, half, row + xq, col0));
+                put(a, 0, rb_ld4(e, half, rym + xq, (xq + ym + z) & 1));
+                put(b, 0, rb_ld4(e, half, ryp + xq, (xq + yp + z) & 1));
+                put(d, 0, rb_ld4(e, half, rzm + xq, (xq + y + zm) & 1));
+                put(f, 0, rb_ld4(e, half, rzp + xq, (xq + y + zp) & 1));
+                put(r, 0, rb_ld4(rhs, half, row + xq, col0));
+            } else {
+                c[0] = A.ld(e + row + xl);
+                c[5] = A.ld(e + row + xr);
+                ES_ELD(A, c, 1, e + row + xq);
+                ES_ELD(A, a, 0, e + rym + xq);
+                ES_ELD(A, b, 0, e + ryp + xq);
+                ES_ELD(A, d, 0, e + rzm + xq);
+                ES_ELD(A, f, 0, e + rzp + xq);
+                ES_VLD(r, 0, rhs + row + xq);
+            }
             const unsigned sw = lane_on ? *reinterpret_cast<const unsigned*>(st + row + xs) : 0x02020202u;
             T res[4];
             unsigned near_bits = 0;
@@ -1295,9 +1469,12 @@ __global__ void k_correct(int N, const uint8_t* __restrict__ st0, const double* 
 // psi += e at unknown cells, psi in float-float (MIXED32 form); four cells
 // per thread with 16-byte accesses, the last thread also takes the N % 4
 // tail cells one by one.
-template <class E>
+// SPLIT: e in the colour-split layout (nx % 8 == 0, so N % 4 == 0 and a
+// 4-cell group never wraps a row; its colour follows from its position).
+template <class E, bool SPLIT = false>
 __global__ void k_correct_ff(int N, const uint8_t* __restrict__ st0, const E* __restrict__ e,
-                             float* __restrict__ psi_hi, float* __restrict__ psi_lo, EAcc<float, E> A) {
+                             float* __restrict__ psi_hi, float* __restrict__ psi_lo, EAcc<float, E> A,
+                             int nx = 0, int ny = 0) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int N4 = N >> 2;
     if (i == N4 - 1 || (N4 == 0 && i == 0))
@@ -1309,7 +1486,13 @@ __global__ void k_correct_ff(int N, const uint8_t* __restrict__ st0, const E* __
             }
     if (i >= N4) return;
     const uchar4 st = reinterpret_cast<const uchar4*>(st0)[i];
-    const auto ev = A.ld4(e + 4 * (size_t)i);
+    Q4<float> ev;
+    if constexpr (SPLIT) {
+        const int c = 4 * i, row = c / nx;  // (row = y + ny z)
+        ev = rb_ld4(e, N >> 1, c, (c - row * nx + row % ny + row / ny) & 1);
+    } else {
+        ev = A.ld4(e + 4 * (size_t)i);
+    }
     float4 h = reinterpret_cast<float4*>(psi_hi)[i], l = reinterpret_cast<float4*>(psi_lo)[i];
     const uint8_t sv[4] = {st.x, st.y, st.z, st.w};
     const float evv[4] = {ev.v0, ev.v1, ev.v2, ev.v3};
@@ -1646,6 +1829,9 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
     // one cell is its own neighbour: no red-black split)
     const bool use_rb = kNative && c->P.smoother == ES_SMOOTH_FUSED && (L.nx % 128) == 0 &&
                         (!L.per[1] || L.ny >= 2) && (!L.per[2] || L.nz >= 2);
+    // the finest level of the reduced forms in the colour-split layout
+    const bool split = kNative && std::is_same<T, float>::value && l == 0 && c->rb0;
+    const RbMap rb{Nl / 2};
     int rb_zc = 1;
     dim3 rb_grid(1, 1, 1);
     if (use_rb) rb_grid = rb_launch_shape<T>(c, L, rb_zc);
@@ -1669,6 +1855,30 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
         // per half sweep: e of every cell in, the colour's e out, its rhs
         // and state bytes in
         const double b_first = nl * (0.5 * es + 0.5 * ts + 1.0), b_half = nl * (1.5 * es + 0.5 * ts + 1.0);
+        if constexpr (kNative && std::is_same<T, float>::value) {
+            if (split) {
+                // colour-split finest level: interior pass, then the colour's
+                // near-boundary cells from the list
+                const dim3 sgrd((L.nx / 8 + 31) / 32, (L.ny + 7) / 8, L.nz);
+                const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, kNearSegs);
+                const int* cnt = c->near_count + 2 * kNearSegs * l;
+                const size_t hl = (size_t)kNearSegs * c->near_cap[l];
+                for (int col = 0; col < 2; col++) {
+                    const int fs = first ? (col == 0 ? 1 : 2) : 0;
+                    {
+                        ProfScope ps(c, "smooth_half", l, col == 0 && first ? b_first : b_half);
+                        k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, col, fs, omega,
+                                                                     rb.half);
+                    }
+                    ProfScope ps(c, "smooth_near", l, 0.0);
+                    k_smooth_near<T, E, RbMap><<<ngrd, 256, 0, c->stream>>>(
+                        L, st, rhs, e, c->near_list[l] + col * hl, cnt + col * kNearSegs, c->near_cap[l], fs, omega,
+                        A, rb);
+                }
+                count(c, 4);
+                return;
+            }
+        }
         if (vec) {
             if (Nl <= kInlineNearCells) {
                 {
@@ -1763,12 +1973,25 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
         if (vec) {
             dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
             T* scratch = (T*)c->e2[l];  // (the fused sweep's second iterate; free between sweeps)
-            k_near_residual<T, E><<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs), 256, 0,
-                                    c->stream>>>(L, st, rhs, e, c->near_list[l],
-                                                 c->near_count + 2 * kNearSegs * l, c->near_cap[l],
-                                                 (T)1 / L.h2, scratch, A);
-            k_restrict_v<T, E><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch, m[0],
-                                                             m[1], c->st[l + 1], (T*)c->rhs[l + 1], A);
+            const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs);
+            const int* cnt = c->near_count + 2 * kNearSegs * l;
+            bool done = false;
+            if constexpr (kNative && std::is_same<T, float>::value) {
+                if (split) {
+                    k_near_residual<T, E, RbMap><<<ngrd, 256, 0, c->stream>>>(
+                        L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
+                    k_restrict_v<T, E, true><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e,
+                                                                           scratch, m[0], m[1], c->st[l + 1],
+                                                                           (T*)c->rhs[l + 1], A, rb.half);
+                    done = true;
+                }
+            }
+            if (!done) {
+                k_near_residual<T, E><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l], cnt,
+                                                                   c->near_cap[l], (T)1 / L.h2, scratch, A);
+                k_restrict_v<T, E><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch,
+                                                                 m[0], m[1], c->st[l + 1], (T*)c->rhs[l + 1], A);
+            }
             count(c, 2);
         } else if constexpr (kNative) {
             dim3 cgrid((m[0] + 127) / 128, m[1], m[2]);
@@ -1781,7 +2004,16 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
     if (err != cudaSuccess) return err;
     {
         ProfScope ps(c, "prolong", l, nl * (2.0 * es + 1.0) + nc * (ts + 1.0));
-        if (vec)
+        bool done = false;
+        if constexpr (kNative && std::is_same<T, float>::value) {
+            if (split) {
+                k_prolong_v<T, E, true><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1],
+                                                                      (const T*)c->e[l + 1], A, rb.half);
+                done = true;
+            }
+        }
+        if (done) {
+        } else if (vec)
             k_prolong_v<T, E><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1],
                                                             (const T*)c->e[l + 1], A);
         else if constexpr (kNative)
@@ -1827,20 +2059,33 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         int gz = kResPartials / (gx * gy);
         gz = gz < 1 ? 1 : (gz > c->g.nz ? c->g.nz : gz);
         const dim3 grd(gx, gy, gz), blk(32, 8);
-        k_outer_residual_near_ff<<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs), 256, 0,
-                                   c->stream>>>(
-            c->g, ff_from_double(diag0), wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner, (const float2*)c->pbc,
-            c->near_list[0], c->near_count, c->near_cap[0], (float*)c->rhs[0]);
-        if (W == 4)
-            k_outer_residual_ff<4><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
-                                                                c->psi_lo, c->st[0], c->owner,
-                                                                (const float2*)c->pbc, mask, (float*)c->rhs[0],
-                                                                c->partial);
-        else
-            k_outer_residual_ff<1><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
-                                                                c->psi_lo, c->st[0], c->owner,
-                                                                (const float2*)c->pbc, mask, (float*)c->rhs[0],
-                                                                c->partial);
+        const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs);
+        if (c->rb0) {
+            // r goes to the colour-split right-hand side of the finest level
+            k_outer_residual_near_ff<RbMap><<<ngrd, 256, 0, c->stream>>>(
+                c->g, ff_from_double(diag0), wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner,
+                (const float2*)c->pbc, c->near_list[0], c->near_count, c->near_cap[0], (float*)c->rhs[0],
+                RbMap{(int)(c->g.N / 2)});
+            k_outer_residual_ff<4, true><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
+                                                                      c->psi_lo, c->st[0], c->owner,
+                                                                      (const float2*)c->pbc, mask,
+                                                                      (float*)c->rhs[0], c->partial);
+        } else {
+            k_outer_residual_near_ff<NatMap><<<ngrd, 256, 0, c->stream>>>(
+                c->g, ff_from_double(diag0), wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner,
+                (const float2*)c->pbc, c->near_list[0], c->near_count, c->near_cap[0], (float*)c->rhs[0],
+                NatMap{});
+            if (W == 4)
+                k_outer_residual_ff<4, false><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall,
+                                                                           c->psi32, c->psi_lo, c->st[0], c->owner,
+                                                                           (const float2*)c->pbc, mask,
+                                                                           (float*)c->rhs[0], c->partial);
+            else
+                k_outer_residual_ff<1, false><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall,
+                                                                           c->psi32, c->psi_lo, c->st[0], c->owner,
+                                                                           (const float2*)c->pbc, mask,
+                                                                           (float*)c->rhs[0], c->partial);
+        }
         k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
         count(c, 3);
         return cudaGetLastError();
@@ -1879,6 +2124,10 @@ cudaError_t launch_correct(es_ctx* c) {
             k_correct_ff<__half><<<(n4 + 255) / 256, 256, 0, c->stream>>>(
                 N, c->st[0], (const __half*)c->e[0], c->psi32, c->psi_lo,
                 EAcc<float, __half>{c->e_scale, 1.0f / c->e_scale});
+        else if (c->rb0)
+            k_correct_ff<float, true><<<(n4 + 255) / 256, 256, 0, c->stream>>>(
+                N, c->st[0], (const float*)c->e[0], c->psi32, c->psi_lo, EAcc<float, float>{1.0f, 1.0f}, c->g.nx,
+                c->g.ny);
         else
             k_correct_ff<float><<<(n4 + 255) / 256, 256, 0, c->stream>>>(
                 N, c->st[0], (const float*)c->e[0], c->psi32, c->psi_lo, EAcc<float, float>{1.0f, 1.0f});

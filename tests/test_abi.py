@@ -68,6 +68,7 @@ def _create_rc(lib, wl, **over):
     (dict(mg_storage=1), "reduced precision"),  # (the helper creates FP64 contexts)
     (dict(phi_t=-1.0), "phi_t"),
     (dict(phi_t=0.5, levels=2), "levels == 1"),
+    (dict(fine_layout=2), "fine_layout"),
 ])
 def test_invalid_parameters_rejected_before_any_gpu_call(lib, over, needle):
     rc, msg = _create_rc(lib, W.single_sphere(), **over)
