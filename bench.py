@@ -54,6 +54,8 @@ def parse_args():
                     help="execution of a red-black sweep (same arithmetic)")
     ap.add_argument("--mg-storage", choices=["native", "fp16"], default="native",
                     help="storage of the finest level's multigrid correction")
+    ap.add_argument("--fine-layout", choices=["auto", "natural"], default="auto",
+                    help="finest-level layout of the multigrid correction and right-hand side")
     return ap.parse_args()
 
 
@@ -213,7 +215,9 @@ def run_ours(args):
                       levels=6 if args.n % 32 == 0 else 4)
     smoother = es.ES_SMOOTH_FUSED if args.smoother == "fused" else es.ES_SMOOTH_TWO_PASS
     mg = es.ES_MG_FP16 if args.mg_storage == "fp16" else es.ES_MG_NATIVE
-    sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev), overrides=dict(smoother=smoother, mg_storage=mg))
+    lay = es.ES_LAYOUT_NATURAL if args.fine_layout == "natural" else es.ES_LAYOUT_AUTO
+    sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev),
+                        overrides=dict(smoother=smoother, mg_storage=mg, fine_layout=lay))
     stream = sim.stream
     N = wl.n_cells
 

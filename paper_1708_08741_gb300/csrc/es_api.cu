@@ -285,6 +285,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->red_blocks = 4 * c->n_sm;
     c->mg_rate = 0.15;
     c->e_scale = 1.0f;
+    c->mapped_once = false;
 
     const long long N = c->g.N;
     const size_t s = mixed(c) ? 4 : 8;

@@ -57,6 +57,35 @@ __device__ __forceinline__ bool cell_inside(const Grid& g, const DParticle& p, i
     return d2 <= __dmul_rn(p.R, p.R);
 }
 
+// FP32 distances from a sphere centre to the cells of a box [blo, bhi], for deciding
+// cheaply which cells need work: the centre relative to the box origin is
+// formed once in FP64 and rounded to float, so the FP32 squared distance of
+// a cell (local index i, j, k) is within ~1e-6 relative of the FP64 one.
+// ok is false where a periodic axis is too short for the unwrapped distance
+// to be the minimum image everywhere in the box (callers then take the slow
+// path for every cell).
+struct BallF {
+    float c[3], r2, margin;
+    bool ok;
+    __device__ void init(const Grid& g, const double* X, double R, const int* blo, const int* bhi) {
+        ok = true;
+        for (int a = 0; a < 3; a++) {
+            c[a] = (float)(X[a] - ((double)blo[a] + 0.5));
+            if (g.per[a]) {
+                const double half = 0.5 * (double)gdim(g, a);
+                const double lo = (double)blo[a] + 0.5 - X[a], hi = (double)bhi[a] + 0.5 - X[a];
+                if (!(lo > -half + 1.0 && hi < half - 1.0)) ok = false;
+            }
+        }
+        r2 = (float)(R * R);
+        margin = 1e-5f * (r2 + 100.0f);  // far above the FP32 rounding of d^2
+    }
+    __device__ float d2(int i, int j, int k) const {
+        const float dx = (float)i - c[0], dy = (float)j - c[1], dz = (float)k - c[2];
+        return dx * dx + dy * dy + dz * dz;
+    }
+};
+
 // Surface velocity u_s = V + Omega x (x_s - X) at the centre of a cell.
 __device__ __forceinline__ void surface_velocity(const Grid& g, const double* X, const double* V,
                                                  const double* W, int x, int y, int z, double u[3]) {

@@ -134,6 +134,7 @@ struct es_ctx {
     float e_scale;   // ES_MG_FP16: scale of the finest level's stored correction
     int slip;        // bit f: face f (x-lo, x-hi, y-lo, ...) of a non-periodic axis is free-slip
     bool rb0;        // the finest level's e and rhs in the colour-split layout (reduced forms)
+    bool mapped_once;  // the particles were mapped at least once (flags valid outside their shells)
     double lambda_e, lambda_o;
     size_t bytes;
     unsigned long long launches;  // kernels launched by this context

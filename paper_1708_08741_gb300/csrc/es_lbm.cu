@@ -11,6 +11,8 @@
 //
 // MIXED32 stores f_q - w_q in float: the collision is linear in f, and the
 // weights cancel in every term except the density, which becomes 1 + sum.
+#include <type_traits>
+
 #include "es_device.cuh"
 
 namespace es {
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(Grid g, const DParticl
                                                           const int32_t* __restrict__ owner,
                                                           const uint8_t* __restrict__ flags,
                                                           const S* __restrict__ src, double Ex, double Ey, double Ez,
-                                                          double* F, double* T) {
+                                                          const double* __restrict__ mapped, double* F, double* T) {
     __shared__ int s_cell[kForceThreads * 18];
     __shared__ uint8_t s_q[kForceThreads * 18];
     __shared__ int s_warp[kForceThreads / 32];
@@ -234,6 +236,14 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(Grid g, const DParticl
     int lo[3], hi[3];
     for (int a = 0; a < 3; a++) axis_range(g, a, P.x[a], P.x[a], P.R, 1, lo[a], hi[a]);
     const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
+    // A link runs from a fluid cell to a cell of p within sqrt 2, and p's
+    // cells are those within R of its centre at the last mapping, so only
+    // cells between R - 1 and R + 1.5 of that centre are scanned (FP32
+    // distances; the bounds are far outside their rounding).
+    BallF ball;
+    ball.init(g, mapped + 9 * p, P.R, lo, hi);
+    const float rin = (float)P.R - 1.0f, rout = (float)P.R + 1.5f;
+    const float in2 = rin > 0.0f ? rin * rin : -1.0f, out2 = rout * rout;
     const int n = sx * sy * sz;
     const size_t ps = (size_t)g.ps;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -242,7 +252,12 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(Grid g, const DParticl
         const int t = base + threadIdx.x;
         unsigned mask = 0;
         int c = 0;
-        if (t < n) {
+        bool scan = t < n;
+        if (scan && ball.ok) {
+            const float d2 = ball.d2(t % sx, (t / sx) % sy, t / (sx * sy));
+            scan = d2 >= in2 && d2 <= out2;
+        }
+        if (scan) {
             const int tx = t % sx, tyz = t / sx;
             const int x = wrap_coord(lo[0] + tx, g.nx);
             const int y = wrap_coord(lo[1] + tyz % sy, g.ny);
@@ -320,6 +335,217 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(Grid g, const DParticl
                 F[3 * p + k] = s + P.qeff * E[k];  // F_C = q E_ext (Sec. 5.6)
             else
                 T[3 * p + k - 3] = s;
+        }
+    }
+}
+
+// Momentum exchange of the reduced forms (float or FP16 populations, stored
+// as deviations f - w_q).  Same links and sums as k_forces, arranged so that
+// no FP64 arithmetic runs per link (GB300's FP64 rate is a small fraction
+// of its FP32 rate).  With f~ = w_q + dev the link term is
+// [2 w_q + m'] c_q, m' = 2 dev - 6 w_q (c_q . u_s):
+//  * the m' part (small) is summed in FP32 per thread, with lever arms in
+//    FP32, and over the block in float-float;
+//  * the 2 w_q part is summed exactly: per direction, the number of links
+//    and the integer sums of the surface cells' coordinates (relative to the
+//    box origin, unwrapped), from which thread 0 forms sum 2 w_q c_q and
+//    sum 2 w_q (x_s - X) x c_q in FP64 at the end.
+// Near-surface scan as in k_forces (cells between R - 1 and R + 1.5 of the
+// centre at the last mapping).  Deterministic: fixed summation order.
+template <class S>
+__global__ void __launch_bounds__(kForceThreads) k_forces_f32(Grid g, const DParticle* __restrict__ part,
+                                                              const int32_t* __restrict__ owner,
+                                                              const uint8_t* __restrict__ flags,
+                                                              const S* __restrict__ src, double Ex, double Ey,
+                                                              double Ez, const double* __restrict__ mapped,
+                                                              double* F, double* T) {
+    using St = Store<S>;
+    __shared__ int s_cell[kForceThreads * 18];
+    __shared__ uint8_t s_q[kForceThreads * 18];
+    __shared__ int s_warp[kForceThreads / 32];
+    __shared__ int s_lo[3], s_n[3];
+    __shared__ BallF s_ball;
+    __shared__ float s_X[3], s_V[3], s_W[3], s_band[2];
+    __shared__ int s_cnt[19], s_sum[19][3];
+    __shared__ float s_red[kForceThreads / 32][12];
+    const int p = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const DParticle& P = part[p];
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; a++) {
+            axis_range(g, a, P.x[a], P.x[a], P.R, 1, lo[a], hi[a]);
+            s_lo[a] = lo[a];
+            s_n[a] = hi[a] - lo[a] + 1;
+            // centre relative to the box origin's cell centre: r = i - s_X for
+            // the cell with local index i (exact to FP32 rounding of s_X)
+            s_X[a] = (float)(P.x[a] - ((double)lo[a] + 0.5));
+            s_V[a] = (float)P.v[a];
+            s_W[a] = (float)P.w[a];
+        }
+        s_ball.init(g, mapped + 9 * p, P.R, lo, hi);
+        const float rin = (float)P.R - 1.0f, rout = (float)P.R + 1.5f;
+        s_band[0] = rin > 0.0f ? rin * rin : -1.0f;
+        s_band[1] = rout * rout;
+    }
+    if (threadIdx.x < 19) {
+        s_cnt[threadIdx.x] = 0;
+        s_sum[threadIdx.x][0] = s_sum[threadIdx.x][1] = s_sum[threadIdx.x][2] = 0;
+    }
+    __syncthreads();
+    const int sx = s_n[0], sy = s_n[1], sz = s_n[2];
+    const int n = sx * sy * sz;
+    const BallF ball = s_ball;
+    const float in2 = s_band[0], out2 = s_band[1];
+    const float Xr[3] = {s_X[0], s_X[1], s_X[2]}, V[3] = {s_V[0], s_V[1], s_V[2]}, W[3] = {s_W[0], s_W[1], s_W[2]};
+    const int L[3] = {g.nx, g.ny, g.nz};
+    const size_t ps = (size_t)g.ps;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int base = 0; base < n; base += kForceThreads) {
+        const int t = base + threadIdx.x;
+        unsigned mask = 0;
+        int c = 0;
+        bool scan = t < n;
+        if (scan && ball.ok) {
+            const float d2 = ball.d2(t % sx, (t / sx) % sy, t / (sx * sy));
+            scan = d2 >= in2 && d2 <= out2;
+        }
+        if (scan) {
+            const int tx = t % sx, tyz = t / sx;
+            const int x = wrap_coord(s_lo[0] + tx, g.nx);
+            const int y = wrap_coord(s_lo[1] + tyz % sy, g.ny);
+            const int z = wrap_coord(s_lo[2] + tyz / sy, g.nz);
+            c = x + g.nx * (y + g.ny * z);
+            if (flags[c] & F_NEAR19) {
+#pragma unroll
+                for (int q = 1; q < 19; q++) {
+                    long long nb;
+                    if (neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb) && owner[nb] == p) mask |= 1u << q;
+                }
+            }
+        }
+        const int cnt = __popc(mask);
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        int woff = 0, total = 0;
+        for (int w = 0; w < kForceThreads / 32; w++) {
+            if (w < wid) woff += s_warp[w];
+            total += s_warp[w];
+        }
+        int off = woff + incl - cnt;
+        while (mask) {
+            const int q = __ffs(mask) - 1;
+            mask &= mask - 1;
+            s_cell[off] = c;
+            s_q[off] = (uint8_t)q;
+            off++;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < total; i += kForceThreads) {
+            const int cc = s_cell[i], q = s_q[i];
+            const int x = cc % g.nx, yz = cc / g.nx;
+            const int y = yz % g.ny, z = yz / g.ny;
+            int qv[3] = {0, 0, 0};
+#pragma unroll
+            for (int k = 1; k < 19; k++)
+                if (k == q) {
+                    qv[0] = cx(k);
+                    qv[1] = cy(k);
+                    qv[2] = cz(k);
+                }
+            // surface cell x_s = x_F + c_q, unwrapped into the box (minimum image)
+            const int xs3[3] = {x + qv[0], y + qv[1], z + qv[2]};
+            int rel[3];
+            float r[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                int u = xs3[a] - s_lo[a];  // local index, up to a multiple of the extent
+                if (g.per[a]) {
+                    if (u < 0) u += L[a];
+                    if (u >= L[a]) u -= L[a];
+                    if ((float)u - Xr[a] > 0.5f * (float)L[a]) u -= L[a];
+                    if ((float)u - Xr[a] < -0.5f * (float)L[a]) u += L[a];
+                }
+                rel[a] = u;
+                r[a] = (float)u - Xr[a];
+            }
+            const float us0 = V[0] + (W[1] * r[2] - W[2] * r[1]);
+            const float us1 = V[1] + (W[2] * r[0] - W[0] * r[2]);
+            const float us2 = V[2] + (W[0] * r[1] - W[1] * r[0]);
+            const float cu = (float)qv[0] * us0 + (float)qv[1] * us1 + (float)qv[2] * us2;
+            const float w = (q <= 3 || (q >= 10 && q <= 12)) ? 1.0f / 18.0f : 1.0f / 36.0f;
+            float dev;  // f~ - w_q
+            if constexpr (std::is_same<S, __half>::value)
+                dev = __half2float(src[q * ps + cc]) * (w * (float)(1.0 / kHalfScale));  // (Store<__half>::ld in FP32)
+            else
+                dev = St::ld(q, src[q * ps + cc]);
+            const float m = 2.0f * dev - 6.0f * w * cu;
+            const float d0 = m * (float)qv[0], d1 = m * (float)qv[1], d2 = m * (float)qv[2];
+            acc[0] += d0;
+            acc[1] += d1;
+            acc[2] += d2;
+            acc[3] += r[1] * d2 - r[2] * d1;
+            acc[4] += r[2] * d0 - r[0] * d2;
+            acc[5] += r[0] * d1 - r[1] * d0;
+            atomicAdd(&s_cnt[q], 1);
+            atomicAdd(&s_sum[q][0], rel[0]);
+            atomicAdd(&s_sum[q][1], rel[1]);
+            atomicAdd(&s_sum[q][2], rel[2]);
+        }
+        __syncthreads();
+    }
+    // block sum of the six FP32 partials in float-float (fixed order)
+    ff v[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = {acc[k], 0.0f};
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            const ff u = {__shfl_down_sync(0xffffffffu, v[k].hi, o), __shfl_down_sync(0xffffffffu, v[k].lo, o)};
+            v[k] = ff_add(v[k], u);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            s_red[wid][2 * k] = v[k].hi;
+            s_red[wid][2 * k + 1] = v[k].lo;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const DParticle& P = part[p];
+        double sum[6];
+        for (int k = 0; k < 6; k++) {
+            ff a = {s_red[0][2 * k], s_red[0][2 * k + 1]};
+            for (int w = 1; w < kForceThreads / 32; w++) a = ff_add(a, ff{s_red[w][2 * k], s_red[w][2 * k + 1]});
+            sum[k] = (double)a.hi + (double)a.lo;
+        }
+        // the 2 w_q part: sum 2 w_q c_q and sum 2 w_q (x_s - X) x c_q, with
+        // x_s - X = rel + (lo + 1/2 - X)
+        double off[3];
+        for (int a = 0; a < 3; a++) off[a] = (double)s_lo[a] + 0.5 - P.x[a];
+        for (int q = 1; q < 19; q++) {
+            if (s_cnt[q] == 0) continue;
+            const double w2 = 2.0 * ((q <= 3 || (q >= 10 && q <= 12)) ? 1.0 / 18.0 : 1.0 / 36.0);
+            const double nq = (double)s_cnt[q];
+            const double c3[3] = {(double)cx(q), (double)cy(q), (double)cz(q)};
+            double rs[3];  // sum over the links of x_s - X
+            for (int a = 0; a < 3; a++) rs[a] = (double)s_sum[q][a] + nq * off[a];
+            sum[0] += w2 * nq * c3[0];
+            sum[1] += w2 * nq * c3[1];
+            sum[2] += w2 * nq * c3[2];
+            sum[3] += w2 * (rs[1] * c3[2] - rs[2] * c3[1]);
+            sum[4] += w2 * (rs[2] * c3[0] - rs[0] * c3[2]);
+            sum[5] += w2 * (rs[0] * c3[1] - rs[1] * c3[0]);
+        }
+        const double E[3] = {Ex, Ey, Ez};
+        for (int k = 0; k < 3; k++) {
+            F[3 * p + k] = sum[k] + P.qeff * E[k];  // F_C = q E_ext (Sec. 5.6)
+            T[3 * p + k] = sum[3 + k];
         }
     }
 }
@@ -506,10 +732,17 @@ cudaError_t launch_forces(es_ctx* c) {
     if (c->np == 0) return cudaSuccess;
     const double* E = c->P.E_ext;
     int src = c->last_src >= 0 ? c->last_src : c->cur;
+    ProfScope ps(c, "forces", -1, 0.0);
     dispatch_store(c, [&](auto tag) {
         using S = decltype(tag);
-        k_forces<S><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
-                                                            (const S*)c->pdf[src], E[0], E[1], E[2], c->F, c->T);
+        if constexpr (std::is_same<S, double>::value)
+            k_forces<S><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
+                                                                (const S*)c->pdf[src], E[0], E[1], E[2], c->mapped,
+                                                                c->F, c->T);
+        else
+            k_forces_f32<S><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
+                                                                    (const S*)c->pdf[src], E[0], E[1], E[2],
+                                                                    c->mapped, c->F, c->T);
     });
     count(c);
     return cudaGetLastError();
@@ -517,6 +750,7 @@ cudaError_t launch_forces(es_ctx* c) {
 
 cudaError_t launch_advance(es_ctx* c) {
     if (c->np == 0) return cudaSuccess;
+    ProfScope ps(c, "advance", -1, 0.0);
     k_advance<<<blocks_for(c->np, 128), 128, 0, c->stream>>>(c->np, c->part, c->F, c->T, c->g.per[0], c->g.per[1],
                                                              c->g.per[2], (double)c->g.nx, (double)c->g.ny,
                                                              (double)c->g.nz);

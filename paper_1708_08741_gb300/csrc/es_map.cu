@@ -75,10 +75,17 @@ __device__ Box union_box(const Grid& g, const double* Xo, const double* Xn, doub
     return b;
 }
 
+// GB300 runs FP64 arithmetic at a small fraction of the FP32 rate, so the
+// per-sphere kernels form their FP64 set-up (box, FP32 ball) once per block
+// in thread 0 and share it; per cell they work in integers and FP32 and
+// fall back to the FP64 cell-in-sphere test only where FP32 cannot decide.
+
 __global__ void k_clear(Grid g, const DParticle* part, const double* mapped, int32_t* owner) {
+    __shared__ Box sb;
     int p = blockIdx.x;
-    double R = part[p].R;
-    Box b = sphere_box(g, mapped + 9 * p, R, 0);
+    if (threadIdx.x == 0) sb = sphere_box(g, mapped + 9 * p, part[p].R, 0);
+    __syncthreads();
+    const Box b = sb;
     int n = b.count();
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         int x, y, z;
@@ -90,39 +97,60 @@ __global__ void k_clear(Grid g, const DParticle* part, const double* mapped, int
 
 __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* owner, double* psi,
                       float* psi_hi, float* psi_lo, int* status) {
+    __shared__ Box sb;
+    __shared__ BallF sball;
+    __shared__ double sbval;
+    __shared__ float sbhi, sblo;
     int p = blockIdx.x;
-    DParticle P = part[p];
+    const DParticle& P = part[p];
     if (threadIdx.x == 0) {
         for (int a = 0; a < 3; a++)
             if (!g.per[a] && (P.x[a] - P.R < 0.0 || P.x[a] + P.R > (double)gdim(g, a)))
                 atomicOr(status, DS_WALLCUT);
+        // boundary value kept in the solution field at boundary cells (Sec. 5.4)
+        sbval = kind[p] == ES_KIND_ZETA ? P.zeta : 0.0;
+        const ff bff = ff_from_double(sbval);
+        sbhi = bff.hi;
+        sblo = bff.lo;
+        sb = sphere_box(g, P.x, P.R, 0);
+        sball.init(g, P.x, P.R, sb.lo, sb.hi);
     }
-    // boundary value kept in the solution field at boundary cells (Sec. 5.4)
-    const double bval = kind[p] == ES_KIND_ZETA ? P.zeta : 0.0;
-    const ff bff = ff_from_double(bval);
-    Box b = sphere_box(g, P.x, P.R, 0);
+    __syncthreads();
+    const Box b = sb;
+    const BallF ball = sball;
     int n = b.count();
+    const int sx = b.size(0), sy = b.size(1);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        // decided in FP32 away from the surface, by the FP64 test near it
+        int in = -1;
+        if (ball.ok) {
+            const float d2 = ball.d2(t % sx, (t / sx) % sy, t / (sx * sy));
+            if (d2 > ball.r2 + ball.margin) continue;
+            if (d2 < ball.r2 - ball.margin) in = 1;
+        }
         int x, y, z;
         b.cell(g, t, x, y, z);
-        if (!cell_inside(g, P, x, y, z)) continue;
+        if (in < 0 && !cell_inside(g, P, x, y, z)) continue;
         long long c = lin(g, x, y, z);
         int old = atomicExch(&owner[c], p);
         if (old >= 0 && old != p) atomicOr(status, DS_OVERLAP);
         if (psi) {
-            psi[c] = bval;
+            psi[c] = sbval;
         } else {
-            psi_hi[c] = bff.hi;
-            psi_lo[c] = bff.lo;
+            psi_hi[c] = sbhi;
+            psi_lo[c] = sblo;
         }
     }
 }
 
 template <class S>
 __global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, int32_t* owner, S* pdf) {
+    __shared__ Box sb;
     int p = blockIdx.x;
     const double* M = mapped + 9 * p;  // x, v, w at the last mapping
-    Box b = sphere_box(g, M, part[p].R, 0);
+    if (threadIdx.x == 0) sb = sphere_box(g, M, part[p].R, 0);
+    __syncthreads();
+    const Box b = sb;
     int n = b.count();
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         int x, y, z;
@@ -177,14 +205,61 @@ __device__ int cell_flags(const Grid& g, const int32_t* owner, const int* kind, 
     return faces;
 }
 
+// all_cells = 0 skips the cells whose flags cannot have changed.  With D
+// the displacement since the last mapping, a cell that changed owner lies
+// within D of the old surface in its old distance and within D of the new
+// surface in its new distance; a cell whose D3Q19 neighbours (within
+// sqrt 2) include one is therefore within D + sqrt 2 of both.  A cell
+// outside either band keeps its flags, and it has no D3Q7 face to the new
+// sphere unless it is within 1 of the new surface.  So a cell is visited
+// when it is within 2.5 of the new surface, or within 2.5 + D of both.
+// The first mapping of a context visits every cell (all_cells = 1).
 __global__ void k_flags(Grid g, DParticle* part, const double* mapped, const int* kind,
-                        const int32_t* owner, uint8_t* flags, uint8_t* st0, int* nfaces) {
-    __shared__ double sh[32];
+                        const int32_t* owner, uint8_t* flags, uint8_t* st0, int* nfaces, int all_cells) {
+    __shared__ Box sb;
+    __shared__ BallF sbo, sbn;
+    __shared__ float sband[5];  // lo1, hi1, lo2, hi2, skip_ok
+    __shared__ int sw[32];
     int p = blockIdx.x;
-    Box b = union_box(g, mapped + 9 * p, part[p].x, part[p].R, 2);
+    if (threadIdx.x == 0) {
+        const double* Xo = mapped + 9 * p;
+        const double R = part[p].R;
+        sb = union_box(g, Xo, part[p].x, R, 2);
+        sbo.init(g, Xo, R, sb.lo, sb.hi);
+        sbn.init(g, part[p].x, R, sb.lo, sb.hi);
+        float D2 = 0.0f;
+        for (int a = 0; a < 3; a++) {
+            double d = part[p].x[a] - Xo[a];
+            if (g.per[a]) {
+                const double L = (double)gdim(g, a);
+                if (d > 0.5 * L) d -= L;
+                if (d < -0.5 * L) d += L;
+            }
+            D2 += (float)d * (float)d;
+        }
+        const float rf = (float)R, w1 = 2.5f, w2 = 2.5f + sqrtf(D2) * 1.001f;
+        sband[0] = rf > w1 ? (rf - w1) * (rf - w1) : -1.0f;
+        sband[1] = (rf + w1) * (rf + w1);
+        sband[2] = rf > w2 ? (rf - w2) * (rf - w2) : -1.0f;
+        sband[3] = (rf + w2) * (rf + w2);
+        sband[4] = (!all_cells && sbo.ok && sbn.ok) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    const Box b = sb;
+    const BallF bo = sbo, bn = sbn;
+    const float lo1 = sband[0], hi1 = sband[1], lo2 = sband[2], hi2 = sband[3];
+    const bool skip_ok = sband[4] != 0.0f;
     int n = b.count();
+    const int sx = b.size(0), sy = b.size(1);
     int faces = 0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        if (skip_ok) {
+            const int i = t % sx, j = (t / sx) % sy, k = t / (sx * sy);
+            const float dn = bn.d2(i, j, k), dol = bo.d2(i, j, k);
+            const bool near_new = dn >= lo1 && dn <= hi1;
+            const bool near_both = dn >= lo2 && dn <= hi2 && dol >= lo2 && dol <= hi2;
+            if (!near_new && !near_both) continue;
+        }
         int x, y, z;
         b.cell(g, t, x, y, z);
         uint8_t fl, st;
@@ -193,9 +268,13 @@ __global__ void k_flags(Grid g, DParticle* part, const double* mapped, const int
         flags[c] = fl;
         st0[c] = st;
     }
-    double total = block_sum((double)faces, sh);
+    // block sum of the face counts (integers: exact in any order)
+    for (int o = 16; o > 0; o >>= 1) faces += __shfl_down_sync(0xffffffffu, faces, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = faces;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        int nf = (int)total;
+        int nf = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) nf += sw[w];
         nfaces[p] = nf;
         // Neumann charge per face: sigma = q / faces, so that the flux over
         // the staircase surface equals the particle charge.
@@ -412,6 +491,7 @@ cudaError_t launch_near_lists(es_ctx* c) {
     if (e != cudaSuccess) return e;
     int l0 = 0;
     if (c->g.nx % 4 == 0) {
+        ProfScope ps(c, "cell_lists", 0, 2.0 * (double)c->g.N);
         k_lists_l0<<<(c->g.ny * c->g.nz + 7) / 8, 256, 0, c->stream>>>(c->g.nx, c->g.ny, c->g.nz, c->st[0], c->flags,
                                                                       c->near_cap[0], c->near_list[0], c->near_count,
                                                                       c->bf_cap, c->bf_list, c->bf_count);
@@ -422,6 +502,7 @@ cudaError_t launch_near_lists(es_ctx* c) {
         const int* n = c->ln[l];
         const int rows = n[1] * n[2];
         const int nb = (rows + 7) / 8;  // a warp per row: every row in flight at once
+        ProfScope ps(c, "cell_lists", l, (double)rows * n[0]);
         k_near_list<<<nb, 256, 0, c->stream>>>(n[0], n[1], n[2], c->st[l], c->near_cap[l], c->near_list[l],
                                                 c->near_count + 2 * kNearSegs * l);
         count(c);
@@ -446,15 +527,29 @@ cudaError_t launch_map(es_ctx* c) {
     if (c->np == 0) return cudaSuccess;
     const Grid& g = c->g;
     const int T = 256;
-    k_clear<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner);
-    k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->psi32, c->psi_lo, c->d_status);
-    if (c->P.precision == ES_MIXED16)
-        k_uncover<__half><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (__half*)c->pdf[c->cur]);
-    else if (mixed(c))
-        k_uncover<float><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (float*)c->pdf[c->cur]);
-    else
-        k_uncover<double><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (double*)c->pdf[c->cur]);
-    k_flags<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->kind, c->owner, c->flags, c->st[0], c->nfaces);
+    {
+        ProfScope ps(c, "map_clear", -1, 0.0);
+        k_clear<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner);
+    }
+    {
+        ProfScope ps(c, "map_set", -1, 0.0);
+        k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->psi32, c->psi_lo, c->d_status);
+    }
+    {
+        ProfScope ps(c, "map_uncover", -1, 0.0);
+        if (c->P.precision == ES_MIXED16)
+            k_uncover<__half><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (__half*)c->pdf[c->cur]);
+        else if (mixed(c))
+            k_uncover<float><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (float*)c->pdf[c->cur]);
+        else
+            k_uncover<double><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (double*)c->pdf[c->cur]);
+    }
+    {
+        ProfScope ps(c, "map_flags", -1, 0.0);
+        k_flags<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->kind, c->owner, c->flags, c->st[0],
+                                            c->nfaces, c->mapped_once ? 0 : 1);
+        c->mapped_once = true;
+    }
     k_store_mapped<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->part, c->kind, c->S.eps, c->mapped, c->pbc,
                                                                 c->np);
     count(c, 5);
@@ -466,6 +561,8 @@ cudaError_t launch_coarse_states(es_ctx* c) {
         const int* f = c->ln[l - 1];
         const int* m = c->ln[l];
         dim3 blk(128), grd((m[0] + 127) / 128, m[1], m[2]);
+        const double nc = (double)m[0] * m[1] * m[2];
+        ProfScope ps(c, "coarse_states", l, 8.0 * nc + nc + 2.0 * nc);
         k_coarse_kind<<<grd, blk, 0, c->stream>>>(f[0], f[1], f[2], m[0], m[1], m[2], c->st[l - 1], c->st[l]);
         k_near_bits<<<grd, blk, 0, c->stream>>>(m[0], m[1], m[2], c->g.per[0], c->g.per[1], c->g.per[2], c->st[l]);
         count(c, 2);

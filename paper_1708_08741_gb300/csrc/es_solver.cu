@@ -1418,6 +1418,119 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
     (void)inv_diag0;
 }
 
+// Residual + restriction from the colour-split finest level (float,
+// nx % 8 == 0).  A block of 32 x 8 threads covers 128 coarse cells of two
+// coarse rows; the 4 warps of a coarse row take one fine row of the
+// children each (threadIdx.y = 4 * row + 2 dk + dj), so a thread forms the
+// residuals of 8 fine cells: in a fine row, the two children of coarse
+// cell X are the compact cells X of the two colours (x = 2X and 2X+1), so
+// it loads 4 compact cells of each colour, the same places of the four
+// neighbour rows (where the colours swap), one halo value per colour and
+// the right-hand sides, all as 16-byte vectors.  The four partial sums of
+// a coarse cell are then added through shared memory in the order of
+// k_restrict_v (dk outer, dj inner), whose arithmetic this repeats exactly;
+// near-boundary children come from k_near_residual.
+__global__ void __launch_bounds__(256) k_restrict_rb(Level<float> L, float inv_h2, const uint8_t* __restrict__ st,
+                                                     const float* __restrict__ rhs, const float* __restrict__ e,
+                                                     const float* __restrict__ near_res, int cnx, int cny,
+                                                     const uint8_t* __restrict__ cst, float* __restrict__ crhs,
+                                                     int half) {
+    __shared__ float4 part[8][32];
+    const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int crow = threadIdx.y >> 2, sub = threadIdx.y & 3;
+    const int cy = blockIdx.y * 2 + crow, cz = blockIdx.z;
+    const bool row_on = cy < cny;
+    const bool lane_on = X0 < cnx && row_on;
+    const int Xq = X0 < cnx ? X0 : 0;
+    const int cyq = row_on ? cy : 0;  // (rows past the end compute on a valid row; nothing is stored)
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nxh = nx >> 1;
+    const int dk = sub >> 1, dj = sub & 1;
+    const int y = 2 * cyq + dj, z = 2 * cz + dk;
+    int ym, yp, zm, zp, il, ir;
+    if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
+    if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
+    if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
+    if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
+    if (!wrap_axis(Xq - 1, nxh, L.per[0], il)) il = Xq;
+    if (!wrap_axis(Xq + 4, nxh, L.per[0], ir)) ir = Xq;
+    const int pe = (y + z) & 1;  // colour of the even-x cells of this row
+    const float* E0 = e + pe * half;        // x = 2X of this row; x = 2X + 1 of the neighbour rows
+    const float* E1 = e + (pe ^ 1) * half;  // x = 2X + 1 of this row; x = 2X of the neighbour rows
+    const int rowh = nxh * (y + ny * z);
+    const int hym = nxh * (ym + ny * z), hyp = nxh * (yp + ny * z);
+    const int hzm = nxh * (y + ny * zm), hzp = nxh * (y + ny * zp);
+    float A[4], B[4], r[4], a[4], b[4], d[4], f[4];
+    ES_VLD(A, 0, E0 + rowh + Xq);
+    ES_VLD(B, 0, E1 + rowh + Xq);
+    const float hl = E1[rowh + il], hr = E0[rowh + ir];
+    const uint2 sw = *reinterpret_cast<const uint2*>(st + nx * (y + ny * z) + 2 * Xq);
+    float res[8];
+    // even-x children (A): x neighbours B[k-1] (or the halo), B[k]
+    ES_VLD(r, 0, rhs + pe * half + rowh + Xq);
+    ES_VLD(a, 0, E1 + hym + Xq);
+    ES_VLD(b, 0, E1 + hyp + Xq);
+    ES_VLD(d, 0, E1 + hzm + Xq);
+    ES_VLD(f, 0, E1 + hzp + Xq);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const unsigned sv = ((k < 2 ? sw.x : sw.y) >> (16 * (k & 1))) & 0xFFu;
+        res[2 * k] = 0.0f;
+        if ((sv & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
+        float o = k == 0 ? hl : B[k - 1];
+        o += B[k];
+        o += a[k];
+        o += b[k];
+        o += d[k];
+        o += f[k];
+        res[2 * k] = r[k] - (L.diag0 * A[k] - o) * inv_h2;
+    }
+    // odd-x children (B): x neighbours A[k], A[k+1] (or the halo)
+    ES_VLD(r, 0, rhs + (pe ^ 1) * half + rowh + Xq);
+    ES_VLD(a, 0, E0 + hym + Xq);
+    ES_VLD(b, 0, E0 + hyp + Xq);
+    ES_VLD(d, 0, E0 + hzm + Xq);
+    ES_VLD(f, 0, E0 + hzp + Xq);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const unsigned sv = ((k < 2 ? sw.x : sw.y) >> (16 * (k & 1) + 8)) & 0xFFu;
+        res[2 * k + 1] = 0.0f;
+        if ((sv & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
+        float o = A[k];
+        o += k == 3 ? hr : A[k + 1];
+        o += a[k];
+        o += b[k];
+        o += d[k];
+        o += f[k];
+        res[2 * k + 1] = r[k] - (L.diag0 * B[k] - o) * inv_h2;
+    }
+    // near-boundary children: formed by k_near_residual just before
+    const int rown = nx * (y + ny * z) + 2 * Xq;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const unsigned sv = ((j < 4 ? sw.x : sw.y) >> (8 * (j & 3))) & 0xFFu;
+        if ((sv & (ST_KIND | ST_NEAR)) == (ST_UNKNOWN | ST_NEAR)) res[j] = near_res[rown + j];
+    }
+    part[threadIdx.y][threadIdx.x] = make_float4(res[0] + res[1], res[2] + res[3], res[4] + res[5], res[6] + res[7]);
+    __syncthreads();
+    if (sub != 0 || !lane_on) return;
+    float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < 4; q++) {  // q = 2 dk + dj: dk outer, dj inner
+        const float4 p = part[4 * crow + q][threadIdx.x];
+        sum[0] += p.x;
+        sum[1] += p.y;
+        sum[2] += p.z;
+        sum[3] += p.w;
+    }
+    const int C = X0 + cnx * (cy + cny * cz);
+    const uchar4 cs = *reinterpret_cast<const uchar4*>(cst + C);
+    const uint8_t ck[4] = {cs.x, cs.y, cs.z, cs.w};
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = ((ck[k] & ST_KIND) == ST_UNKNOWN) ? sum[k] / 8.0f : 0.0f;
+    *reinterpret_cast<float4*>(crhs + C) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
 // Coarsest level: one thread block holds the level in shared memory and
 // runs `sweeps` red-black sweeps from a zero iterate.
 template <class T>
@@ -1980,9 +2093,9 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                 if (split) {
                     k_near_residual<T, E, RbMap><<<ngrd, 256, 0, c->stream>>>(
                         L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
-                    k_restrict_v<T, E, true><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e,
-                                                                           scratch, m[0], m[1], c->st[l + 1],
-                                                                           (T*)c->rhs[l + 1], A, rb.half);
+                    const dim3 qgrd((m[0] / 4 + 31) / 32, (m[1] + 1) / 2, m[2]);
+                    k_restrict_rb<<<qgrd, vblk, 0, c->stream>>>(L, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1],
+                                                                c->st[l + 1], (T*)c->rhs[l + 1], rb.half);
                     done = true;
                 }
             }
