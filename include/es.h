@@ -278,7 +278,9 @@ int es_gather_noalloc(es_ctx* ctx, int which, const int64_t* idx, int n, double*
 /* Overwrites ES_FIELD_PSI, ES_FIELD_FB or ES_FIELD_PDF from doubles.      */
 int es_set_field(es_ctx* ctx, int which, const void* src, size_t bytes, int on_device);
 
-/* Host copies of the particle state (n must equal the context's count). */
+/* Host copies of the particle state (n must equal the context's count).
+   es_set_particles changes positions, velocities, spins, zeta and charge;
+   a sphere's radius and kind are fixed after creation (ES_EINVAL). */
 int es_get_particles(es_ctx* ctx, es_particle* dst, int n);
 int es_set_particles(es_ctx* ctx, const es_particle* src, int n);
 

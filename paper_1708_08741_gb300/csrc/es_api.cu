@@ -355,6 +355,8 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     for (int p = 0; p < n; p++) {
         hp[p] = to_device(*params, parts[p], 0.0);
         hk[p] = parts[p].kind;
+        c->h_R.push_back(parts[p].R);
+        c->h_kind.push_back(parts[p].kind);
         for (int a = 0; a < 3; a++) {
             hm[9 * p + a] = parts[p].x[a];
             hm[9 * p + 3 + a] = parts[p].v[a];
@@ -645,6 +647,10 @@ int es_set_particles(es_ctx* c, const es_particle* src, int n) {
     int v = validate(&c->P, src, n, why);
     if (v != ES_OK) return fail(c, v, why);
     if (n == 0) return ES_OK;
+    // (the mapping updates flags and states near each sphere's surface only)
+    for (int p = 0; p < n; p++)
+        if (src[p].R != c->h_R[p] || src[p].kind != c->h_kind[p])
+            return fail(c, ES_EINVAL, "a sphere's radius and kind are fixed after creation");
     // sigma is recomputed by the next mapping; keep the current one meanwhile
     std::vector<DParticle> cur(n);
     ES_CUDA(c, cudaMemcpyAsync(cur.data(), c->part, n * sizeof(DParticle), cudaMemcpyDeviceToHost, c->stream));

@@ -86,6 +86,78 @@ struct BallF {
     }
 };
 
+// The owner field over a box [lo - 1, hi + 1] (the box and a one-cell
+// halo) in shared memory, x fastest; cells beyond a non-periodic face read
+// kOwnerOutside.  Per-sphere kernels read a cell's D3Q19 neighbours from it
+// with fixed offsets instead of wrapping indices per neighbour.
+constexpr int kOwnerOutside = -0x7fffffff;
+constexpr int kOwnerTileMax = 8192;  // ints of shared memory per block
+
+struct OwnerTile {
+    int n[3];  // box extents (the tile is (n + 2)^3)
+    __device__ int tx() const { return n[0] + 2; }
+    __device__ int txy() const { return (n[0] + 2) * (n[1] + 2); }
+    __device__ bool fits(int max_ints = kOwnerTileMax) const { return (n[0] + 2) * (n[1] + 2) * (n[2] + 2) <= max_ints; }
+    // tile index of the box cell with local index (i, j, k)
+    __device__ int at(int i, int j, int k) const { return (i + 1) + tx() * (j + 1) + txy() * (k + 1); }
+    // offset of the D3Q19 neighbour in direction q
+    __device__ int step(int q) const { return cx(q) + tx() * cy(q) + txy() * cz(q); }
+};
+
+// Local indices (i, j, k) of the cells t, t + step, t + 2 step, ... of a box
+// of extents sx x sy x ..., x fastest, advanced without integer division.
+struct BoxWalk {
+    int i, j, k, si, sj, sk, sx, sy;
+    __device__ __forceinline__ void start(int t0, int step, int sx_, int sy_) {
+        sx = sx_;
+        sy = sy_;
+        i = t0 % sx;
+        j = (t0 / sx) % sy;
+        k = t0 / (sx * sy);
+        si = step % sx;
+        sj = (step / sx) % sy;
+        sk = step / (sx * sy);
+    }
+    __device__ __forceinline__ void next() {
+        i += si;
+        j += sj;
+        k += sk;
+        if (i >= sx) {
+            i -= sx;
+            j++;
+        }
+        if (j >= sy) {
+            j -= sy;
+            k++;
+        }
+    }
+};
+
+// v in [-n, 2n) into [0, n) (a box never spans more than one period).
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ void load_owner_tile(const Grid& g, const int32_t* __restrict__ owner, const int* lo,
+                                                const OwnerTile& T, int* tile) {
+    const int sx = T.n[0] + 2, sy = T.n[1] + 2, n = sx * sy * (T.n[2] + 2);
+    const int dim[3] = {g.nx, g.ny, g.nz};
+    BoxWalk w;
+    w.start(threadIdx.x, blockDim.x, sx, sy);
+    for (int t = threadIdx.x; t < n; t += blockDim.x, w.next()) {
+        int v[3] = {lo[0] - 1 + w.i, lo[1] - 1 + w.j, lo[2] - 1 + w.k};
+        bool out = false;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (v[a] < 0 || v[a] >= dim[a]) {
+                if (!g.per[a])
+                    out = true;
+                else
+                    v[a] = wrap1(v[a], dim[a]);
+            }
+        }
+        tile[t] = out ? kOwnerOutside : owner[lin(g, v[0], v[1], v[2])];
+    }
+}
+
 // Surface velocity u_s = V + Omega x (x_s - X) at the centre of a cell.
 __device__ __forceinline__ void surface_velocity(const Grid& g, const double* X, const double* V,
                                                  const double* W, int x, int y, int z, double u[3]) {

@@ -360,6 +360,8 @@ __global__ void __launch_bounds__(kForceThreads) k_forces_f32(Grid g, const DPar
                                                               double Ez, const double* __restrict__ mapped,
                                                               double* F, double* T) {
     using St = Store<S>;
+    constexpr int kTile = 4096;  // (with the link lists below, within 48 KB of static shared memory)
+    __shared__ int tile[kTile];
     __shared__ int s_cell[kForceThreads * 18];
     __shared__ uint8_t s_q[kForceThreads * 18];
     __shared__ int s_warp[kForceThreads / 32];
@@ -395,34 +397,52 @@ __global__ void __launch_bounds__(kForceThreads) k_forces_f32(Grid g, const DPar
     const int sx = s_n[0], sy = s_n[1], sz = s_n[2];
     const int n = sx * sy * sz;
     const BallF ball = s_ball;
+    const OwnerTile TL{{sx, sy, sz}};
+    const bool use_tile = TL.fits(kTile);
+    if (use_tile) {
+        const int lo3[3] = {s_lo[0], s_lo[1], s_lo[2]};
+        load_owner_tile(g, owner, lo3, TL, tile);
+        __syncthreads();
+    }
     const float in2 = s_band[0], out2 = s_band[1];
     const float Xr[3] = {s_X[0], s_X[1], s_X[2]}, V[3] = {s_V[0], s_V[1], s_V[2]}, W[3] = {s_W[0], s_W[1], s_W[2]};
     const int L[3] = {g.nx, g.ny, g.nz};
     const size_t ps = (size_t)g.ps;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    for (int base = 0; base < n; base += kForceThreads) {
+    BoxWalk bw;
+    bw.start(threadIdx.x, kForceThreads, sx, sy);
+    for (int base = 0; base < n; base += kForceThreads, bw.next()) {
         const int t = base + threadIdx.x;
         unsigned mask = 0;
         int c = 0;
         bool scan = t < n;
         if (scan && ball.ok) {
-            const float d2 = ball.d2(t % sx, (t / sx) % sy, t / (sx * sy));
+            const float d2 = ball.d2(bw.i, bw.j, bw.k);
             scan = d2 >= in2 && d2 <= out2;
         }
         if (scan) {
-            const int tx = t % sx, tyz = t / sx;
-            const int x = wrap_coord(s_lo[0] + tx, g.nx);
-            const int y = wrap_coord(s_lo[1] + tyz % sy, g.ny);
-            const int z = wrap_coord(s_lo[2] + tyz / sy, g.nz);
-            c = x + g.nx * (y + g.ny * z);
-            if (flags[c] & F_NEAR19) {
+            if (use_tile) {
+                const int ti = TL.at(bw.i, bw.j, bw.k);
+                if (tile[ti] < 0 && tile[ti] != kOwnerOutside) {
 #pragma unroll
-                for (int q = 1; q < 19; q++) {
-                    long long nb;
-                    if (neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb) && owner[nb] == p) mask |= 1u << q;
+                    for (int q = 1; q < 19; q++)
+                        if (tile[ti + TL.step(q)] == p) mask |= 1u << q;
+                }
+            } else {
+                const int x = wrap1(s_lo[0] + bw.i, g.nx);
+                const int y = wrap1(s_lo[1] + bw.j, g.ny);
+                const int z = wrap1(s_lo[2] + bw.k, g.nz);
+                const int cg = x + g.nx * (y + g.ny * z);
+                if (flags[cg] & F_NEAR19) {
+#pragma unroll
+                    for (int q = 1; q < 19; q++) {
+                        long long nb;
+                        if (neighbour(g, x, y, z, cx(q), cy(q), cz(q), nb) && owner[nb] == p) mask |= 1u << q;
+                    }
                 }
             }
+            c = bw.i | (bw.j << 10) | (bw.k << 20);  // local indices of x_F (a box is < 1024 cells a side)
         }
         const int cnt = __popc(mask);
         int incl = cnt;
@@ -447,9 +467,10 @@ __global__ void __launch_bounds__(kForceThreads) k_forces_f32(Grid g, const DPar
         }
         __syncthreads();
         for (int i = threadIdx.x; i < total; i += kForceThreads) {
-            const int cc = s_cell[i], q = s_q[i];
-            const int x = cc % g.nx, yz = cc / g.nx;
-            const int y = yz % g.ny, z = yz / g.ny;
+            const int pk = s_cell[i], q = s_q[i];
+            const int li[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
+            const int cc = wrap1(s_lo[0] + li[0], g.nx) +
+                           g.nx * (wrap1(s_lo[1] + li[1], g.ny) + g.ny * wrap1(s_lo[2] + li[2], g.nz));
             int qv[3] = {0, 0, 0};
 #pragma unroll
             for (int k = 1; k < 19; k++)
@@ -458,16 +479,14 @@ __global__ void __launch_bounds__(kForceThreads) k_forces_f32(Grid g, const DPar
                     qv[1] = cy(k);
                     qv[2] = cz(k);
                 }
-            // surface cell x_s = x_F + c_q, unwrapped into the box (minimum image)
-            const int xs3[3] = {x + qv[0], y + qv[1], z + qv[2]};
+            // surface cell x_s = x_F + c_q in the box's unwrapped frame
+            // (minimum image where a periodic box spans the whole axis)
             int rel[3];
             float r[3];
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                int u = xs3[a] - s_lo[a];  // local index, up to a multiple of the extent
+                int u = li[a] + qv[a];
                 if (g.per[a]) {
-                    if (u < 0) u += L[a];
-                    if (u >= L[a]) u -= L[a];
                     if ((float)u - Xr[a] > 0.5f * (float)L[a]) u -= L[a];
                     if ((float)u - Xr[a] < -0.5f * (float)L[a]) u += L[a];
                 }
@@ -735,7 +754,11 @@ cudaError_t launch_forces(es_ctx* c) {
     ProfScope ps(c, "forces", -1, 0.0);
     dispatch_store(c, [&](auto tag) {
         using S = decltype(tag);
-        if constexpr (std::is_same<S, double>::value)
+        // (the FP32 form packs box-local indices in 10 bits per axis)
+        double rmax = 0.0;
+        for (double r : c->h_R) rmax = r > rmax ? r : rmax;
+        const bool small_boxes = 2.0 * rmax + 8.0 < 1024.0;
+        if (std::is_same<S, double>::value || !small_boxes)
             k_forces<S><<<c->np, kForceThreads, 0, c->stream>>>(c->g, c->part, c->owner, c->flags,
                                                                 (const S*)c->pdf[src], E[0], E[1], E[2], c->mapped,
                                                                 c->F, c->T);

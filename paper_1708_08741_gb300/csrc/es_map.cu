@@ -42,6 +42,12 @@ struct Box {
     int lo[3], hi[3];
     __device__ int size(int a) const { return hi[a] - lo[a] + 1; }
     __device__ int count() const { return size(0) * size(1) * size(2); }
+    // global coordinates of the cell with local index (i, j, k)
+    __device__ __forceinline__ void at(const Grid& g, int i, int j, int k, int& x, int& y, int& z) const {
+        x = wrap1(lo[0] + i, g.nx);
+        y = wrap1(lo[1] + j, g.ny);
+        z = wrap1(lo[2] + k, g.nz);
+    }
     __device__ void cell(const Grid& g, int t, int& x, int& y, int& z) const {
         int sx = size(0), sy = size(1);
         int i = t % sx;
@@ -87,9 +93,11 @@ __global__ void k_clear(Grid g, const DParticle* part, const double* mapped, int
     __syncthreads();
     const Box b = sb;
     int n = b.count();
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    BoxWalk w;
+    w.start(threadIdx.x, blockDim.x, b.size(0), b.size(1));
+    for (int t = threadIdx.x; t < n; t += blockDim.x, w.next()) {
         int x, y, z;
-        b.cell(g, t, x, y, z);
+        b.at(g, w.i, w.j, w.k, x, y, z);
         long long c = lin(g, x, y, z);
         if (owner[c] == p) owner[c] = -2 - p;
     }
@@ -119,17 +127,18 @@ __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* o
     const Box b = sb;
     const BallF ball = sball;
     int n = b.count();
-    const int sx = b.size(0), sy = b.size(1);
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    BoxWalk w;
+    w.start(threadIdx.x, blockDim.x, b.size(0), b.size(1));
+    for (int t = threadIdx.x; t < n; t += blockDim.x, w.next()) {
         // decided in FP32 away from the surface, by the FP64 test near it
         int in = -1;
         if (ball.ok) {
-            const float d2 = ball.d2(t % sx, (t / sx) % sy, t / (sx * sy));
+            const float d2 = ball.d2(w.i, w.j, w.k);
             if (d2 > ball.r2 + ball.margin) continue;
             if (d2 < ball.r2 - ball.margin) in = 1;
         }
         int x, y, z;
-        b.cell(g, t, x, y, z);
+        b.at(g, w.i, w.j, w.k, x, y, z);
         if (in < 0 && !cell_inside(g, P, x, y, z)) continue;
         long long c = lin(g, x, y, z);
         int old = atomicExch(&owner[c], p);
@@ -152,9 +161,11 @@ __global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, i
     __syncthreads();
     const Box b = sb;
     int n = b.count();
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    BoxWalk w;
+    w.start(threadIdx.x, blockDim.x, b.size(0), b.size(1));
+    for (int t = threadIdx.x; t < n; t += blockDim.x, w.next()) {
         int x, y, z;
-        b.cell(g, t, x, y, z);
+        b.at(g, w.i, w.j, w.k, x, y, z);
         long long c = lin(g, x, y, z);
         if (owner[c] != -2 - p) continue;
         owner[c] = -1;
@@ -216,6 +227,7 @@ __device__ int cell_flags(const Grid& g, const int32_t* owner, const int* kind, 
 // The first mapping of a context visits every cell (all_cells = 1).
 __global__ void k_flags(Grid g, DParticle* part, const double* mapped, const int* kind,
                         const int32_t* owner, uint8_t* flags, uint8_t* st0, int* nfaces, int all_cells) {
+    __shared__ int tile[kOwnerTileMax];
     __shared__ Box sb;
     __shared__ BallF sbo, sbn;
     __shared__ float sband[5];  // lo1, hi1, lo2, hi2, skip_ok
@@ -237,7 +249,9 @@ __global__ void k_flags(Grid g, DParticle* part, const double* mapped, const int
             }
             D2 += (float)d * (float)d;
         }
-        const float rf = (float)R, w1 = 2.5f, w2 = 2.5f + sqrtf(D2) * 1.001f;
+        // (bands: faces need the new surface's outer layer, R .. R + 1;
+        // changed flags lie within sqrt 2 + D of both surfaces; 0.05 margin)
+        const float rf = (float)R, w1 = 1.05f, w2 = 1.47f + sqrtf(D2) * 1.001f;
         sband[0] = rf > w1 ? (rf - w1) * (rf - w1) : -1.0f;
         sband[1] = (rf + w1) * (rf + w1);
         sband[2] = rf > w2 ? (rf - w2) * (rf - w2) : -1.0f;
@@ -249,21 +263,51 @@ __global__ void k_flags(Grid g, DParticle* part, const double* mapped, const int
     const BallF bo = sbo, bn = sbn;
     const float lo1 = sband[0], hi1 = sband[1], lo2 = sband[2], hi2 = sband[3];
     const bool skip_ok = sband[4] != 0.0f;
+    const OwnerTile T{{b.size(0), b.size(1), b.size(2)}};
+    const bool use_tile = T.fits();
+    if (use_tile) {
+        load_owner_tile(g, owner, b.lo, T, tile);
+        __syncthreads();
+    }
     int n = b.count();
-    const int sx = b.size(0), sy = b.size(1);
     int faces = 0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    BoxWalk w;
+    w.start(threadIdx.x, blockDim.x, b.size(0), b.size(1));
+    for (int t = threadIdx.x; t < n; t += blockDim.x, w.next()) {
         if (skip_ok) {
-            const int i = t % sx, j = (t / sx) % sy, k = t / (sx * sy);
-            const float dn = bn.d2(i, j, k), dol = bo.d2(i, j, k);
+            const float dn = bn.d2(w.i, w.j, w.k), dol = bo.d2(w.i, w.j, w.k);
             const bool near_new = dn >= lo1 && dn <= hi1;
             const bool near_both = dn >= lo2 && dn <= hi2 && dol >= lo2 && dol <= hi2;
             if (!near_new && !near_both) continue;
         }
         int x, y, z;
-        b.cell(g, t, x, y, z);
+        b.at(g, w.i, w.j, w.k, x, y, z);
         uint8_t fl, st;
-        faces += cell_flags(g, owner, kind, x, y, z, p, fl, st);
+        if (use_tile) {
+            // cell_flags from the tile
+            const int ti = T.at(w.i, w.j, w.k);
+            const int o = tile[ti];
+            if (o >= 0) {
+                fl = F_SOLID;
+                st = kind[o] == ES_KIND_ZETA ? ST_DIR : ST_NEU;
+            } else {
+                bool near19 = false, near7 = false;
+#pragma unroll
+                for (int q = 1; q < 19; q++) {
+                    const int on = tile[ti + T.step(q)];
+                    const bool axis = (q <= 3) || (q >= 10 && q <= 12);
+                    if (on >= 0 || on == kOwnerOutside) {
+                        near19 = true;
+                        near7 |= axis;
+                        if (axis && on == p) faces++;
+                    }
+                }
+                fl = near19 ? F_NEAR19 : 0;
+                st = near7 ? ST_NEAR : ST_UNKNOWN;
+            }
+        } else {
+            faces += cell_flags(g, owner, kind, x, y, z, p, fl, st);
+        }
         long long c = lin(g, x, y, z);
         flags[c] = fl;
         st0[c] = st;
