@@ -366,6 +366,80 @@ __global__ void k_coarse_kind(int fx, int fy, int fz, int cxn, int cyn, int czn,
     (void)czn;
 }
 
+// Coarse kinds, four coarse cells per thread (coarse nx % 4 == 0): the 8
+// fine cells of a fine row segment arrive as one 8-byte load per child row.
+__global__ void __launch_bounds__(256) k_coarse_kind_v(int fx, int fy, int cxn, int cyn,
+                                                       const uint8_t* __restrict__ fine,
+                                                       uint8_t* __restrict__ coarse) {
+    const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i0 >= cxn || j >= cyn) return;
+    unsigned any_dir = 0, any_unk = 0;  // bit per coarse cell
+#pragma unroll
+    for (int dk = 0; dk < 2; dk++)
+#pragma unroll
+        for (int dj = 0; dj < 2; dj++) {
+            const uint2 v = *reinterpret_cast<const uint2*>(
+                fine + (size_t)2 * i0 + (size_t)fx * ((size_t)(2 * j + dj) + (size_t)fy * (2 * k + dk)));
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const unsigned s = ((b < 4 ? v.x : v.y) >> (8 * (b & 3))) & ST_KIND;
+                if (s == ST_DIR) any_dir |= 1u << (b >> 1);
+                if (s == ST_UNKNOWN) any_unk |= 1u << (b >> 1);
+            }
+        }
+    unsigned out = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const unsigned kind = ((any_dir >> q) & 1u) ? ST_DIR : (((any_unk >> q) & 1u) ? ST_UNKNOWN : ST_NEU);
+        out |= kind << (8 * q);
+    }
+    *reinterpret_cast<unsigned*>(coarse + (size_t)i0 + (size_t)cxn * ((size_t)j + (size_t)cyn * k)) = out;
+}
+
+// Near-boundary bits of a level (as k_near_bits), four cells per thread
+// (nx % 4 == 0), in place: a thread rewrites its 4-byte word with the same
+// kind bits, and neighbours read only kind bits, so every read sees the
+// kinds whether or not the word was rewritten yet.
+__global__ void __launch_bounds__(256) k_near_bits_v(int nx, int ny, int nz, int px, int py, int pz, uint8_t* st) {
+    const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i0 >= nx || j >= ny) return;
+    const size_t row = (size_t)nx * ((size_t)j + (size_t)ny * k);
+    const unsigned own = *reinterpret_cast<const unsigned*>(st + row + i0);
+    // the kinds of the four neighbour rows at the same x, and the x halo
+    // (a missing neighbour beyond a wall counts as not unknown)
+    const unsigned kOut = 0x02020202u;  // (Neumann: not unknown)
+    auto row_at = [&](int jj, int kk) -> unsigned {
+        return *reinterpret_cast<const unsigned*>(st + (size_t)nx * ((size_t)jj + (size_t)ny * kk) + i0);
+    };
+    unsigned ym = kOut, yp = kOut, zm = kOut, zp = kOut;
+    if (j > 0) ym = row_at(j - 1, k); else if (py) ym = row_at(ny - 1, k);
+    if (j < ny - 1) yp = row_at(j + 1, k); else if (py) yp = row_at(0, k);
+    if (k > 0) zm = row_at(j, k - 1); else if (pz) zm = row_at(j, nz - 1);
+    if (k < nz - 1) zp = row_at(j, k + 1); else if (pz) zp = row_at(j, 0);
+    unsigned xl = 2u, xr = 2u;
+    if (i0 > 0) xl = st[row + i0 - 1]; else if (px) xl = st[row + nx - 1];
+    if (i0 + 4 < nx) xr = st[row + i0 + 4]; else if (px) xr = st[row];
+    unsigned res = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const unsigned s = (own >> (8 * q)) & ST_KIND;
+        unsigned v = s;
+        if (s == ST_UNKNOWN) {
+            const unsigned l = q == 0 ? (xl & ST_KIND) : ((own >> (8 * (q - 1))) & ST_KIND);
+            const unsigned r = q == 3 ? (xr & ST_KIND) : ((own >> (8 * (q + 1))) & ST_KIND);
+            const bool near = l != ST_UNKNOWN || r != ST_UNKNOWN || ((ym >> (8 * q)) & ST_KIND) != ST_UNKNOWN ||
+                              ((yp >> (8 * q)) & ST_KIND) != ST_UNKNOWN ||
+                              ((zm >> (8 * q)) & ST_KIND) != ST_UNKNOWN ||
+                              ((zp >> (8 * q)) & ST_KIND) != ST_UNKNOWN;
+            v = near ? (ST_UNKNOWN | ST_NEAR) : ST_UNKNOWN;
+        }
+        res |= v << (8 * q);
+    }
+    *reinterpret_cast<unsigned*>(st + row + i0) = res;
+}
+
 // Near-boundary bit of an unknown cell: a D3Q7 neighbour that is not an
 // unknown, or a non-periodic domain face.  Only the bit is written; the
 // kind bits neighbours read are unchanged, so updating in place is safe.
@@ -503,12 +577,14 @@ __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const 
             if ((s8 & ST_KIND) == ST_UNKNOWN && (s8 & ST_NEAR)) m_near[(xs + i + y + z) & 1] |= 1u << i;
             if ((f8 & F_NEAR19) && !(f8 & F_SOLID)) m_bf |= 1u << i;
         }
+        // (most 128-cell spans hold no listed cell: one vote skips them)
+        if (!__any_sync(0xffffffffu, (m_near[0] | m_near[1] | m_bf) != 0)) continue;
 #pragma unroll
         for (int t = 0; t < 3; t++) {
             const unsigned m = t < 2 ? m_near[t] : m_bf;
+            if (!__any_sync(0xffffffffu, m != 0)) continue;
             int total;
             const int excl = warp_excl_scan(__popc(m), total);
-            if (total == 0) continue;
             int* cnt = t < 2 ? &count[t * kNearSegs + seg] : &bf_count[seg];
             int base = 0;
             if (lane == 0) base = atomicAdd(cnt, total);
@@ -607,8 +683,16 @@ cudaError_t launch_coarse_states(es_ctx* c) {
         dim3 blk(128), grd((m[0] + 127) / 128, m[1], m[2]);
         const double nc = (double)m[0] * m[1] * m[2];
         ProfScope ps(c, "coarse_states", l, 8.0 * nc + nc + 2.0 * nc);
-        k_coarse_kind<<<grd, blk, 0, c->stream>>>(f[0], f[1], f[2], m[0], m[1], m[2], c->st[l - 1], c->st[l]);
-        k_near_bits<<<grd, blk, 0, c->stream>>>(m[0], m[1], m[2], c->g.per[0], c->g.per[1], c->g.per[2], c->st[l]);
+        if (m[0] % 4 == 0) {
+            const dim3 vblk(32, 8), vgrd((m[0] / 4 + 31) / 32, (m[1] + 7) / 8, m[2]);
+            k_coarse_kind_v<<<vgrd, vblk, 0, c->stream>>>(f[0], f[1], m[0], m[1], c->st[l - 1], c->st[l]);
+            k_near_bits_v<<<vgrd, vblk, 0, c->stream>>>(m[0], m[1], m[2], c->g.per[0], c->g.per[1], c->g.per[2],
+                                                         c->st[l]);
+        } else {
+            k_coarse_kind<<<grd, blk, 0, c->stream>>>(f[0], f[1], f[2], m[0], m[1], m[2], c->st[l - 1], c->st[l]);
+            k_near_bits<<<grd, blk, 0, c->stream>>>(m[0], m[1], m[2], c->g.per[0], c->g.per[1], c->g.per[2],
+                                                    c->st[l]);
+        }
         count(c, 2);
     }
     return cudaGetLastError();
