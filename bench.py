@@ -232,6 +232,7 @@ def run_ours(args):
     lbm_ev = [(ev(), ev()) for _ in range(args.steps)]
     phase_ev = [[ev() for _ in range(5)] for _ in range(args.steps)]
     cycles = []
+    start_ratio = []  # residual norm at the start of each solve / tolerance
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = sim.kernel_launches()
@@ -246,6 +247,7 @@ def run_ours(args):
             pe[1].record(stream)
             info = sim.solve()
             cycles.append(info["cycles"])
+            start_ratio.append(info["r0"] / info["tol"] if info["tol"] > 0 else 0.0)
             pe[2].record(stream)
             lbm_ev[k][0].record(stream)
             sim.lbm_step()
@@ -330,6 +332,7 @@ def run_ours(args):
                    "l2_policy": "inputs larger than L2 (PDF fields 20 GB)"},
         "mflups": n_fluid * args.steps * world / t_all / 1e6,
         "vcycles_per_step": vcycles / args.steps,
+        "start_residual_over_tol": sorted(round(x, 1) for x in start_ratio),
         "phases_ms": phases,
         "roofline": {"kernel": top["kernel"], "bound": "hbm", "achieved": top["gbs"], "peak": peak,
                      "unit": "GB/s", "frac": top["frac"], "traffic": TRAFFIC.get(top["kernel"]),

@@ -412,6 +412,13 @@ int es_map_particles(es_ctx* c) {
 // MIXED32/16: the FP32 V-cycles per correction are predicted to bring the
 // residual to this fraction of the tolerance (a margin for the rate estimate).
 constexpr double kCycleTarget = 0.85;
+// The residual after a correction is updated in FP32 (r - A e) when the
+// residual before it is within this factor of the tolerance.  The update
+// forms A e from differences e_c - e_nb, so its rounding is ~1e-6 of the
+// residual before the correction rather than of e (up to 1/kappa^2 larger);
+// at 5000 x tol that stays near 0.5 % of the tolerance, inside the margin
+// kCycleTarget leaves.
+constexpr double kFastUpdate = 5000.0;
 
 int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
     if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
@@ -466,11 +473,27 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
             c->e_scale = (float)(sc < 1e-30 ? 1e-30 : (sc > 1e30 ? 1e30 : sc));
         }
         for (int j = 0; j < k; j++) ES_CUDA(c, launch_vcycle(c, j > 0));
-        ES_CUDA(c, launch_correct(c));
-        ES_CUDA(c, launch_outer_residual(c));
         const double before = norm;
-        rc = read_norm_status(c, &norm, &st);
-        if (rc != ES_OK) return rc;
+        if (c->rb0 && forced_cycles < 0 && norm <= kFastUpdate * c->tol) {
+            // near the tolerance: psi += e, then r -= A e (FP32 update, error
+            // ~1e-6 of the residual before the correction); the float-float
+            // residual is formed again only if the updated one is not yet
+            // below the tolerance
+            ES_CUDA(c, launch_residual_update(c));
+            ES_CUDA(c, launch_correct(c));
+            rc = read_norm_status(c, &norm, &st);
+            if (rc != ES_OK) return rc;
+            if (!(norm < c->tol)) {
+                ES_CUDA(c, launch_outer_residual(c));
+                rc = read_norm_status(c, &norm, &st);
+                if (rc != ES_OK) return rc;
+            }
+        } else {
+            ES_CUDA(c, launch_correct(c));
+            ES_CUDA(c, launch_outer_residual(c));
+            rc = read_norm_status(c, &norm, &st);
+            if (rc != ES_OK) return rc;
+        }
         cycles += k;
         if (norm > 0.0 && before > 0.0) {
             double observed = std::pow(norm / before, 1.0 / k);

@@ -174,6 +174,7 @@ cudaError_t launch_vcycle(es_ctx* c, int warm);
 cudaError_t launch_split_psi(es_ctx* c, const double* src);  // MIXED32: psi = src
 cudaError_t launch_join_psi(es_ctx* c, double* dst);         // MIXED32: dst = psi
 cudaError_t launch_correct(es_ctx* c);
+cudaError_t launch_residual_update(es_ctx* c);
 cudaError_t launch_body_force(es_ctx* c);
 // lbm and particles (es_lbm.cu)
 cudaError_t launch_lbm(es_ctx* c);

@@ -1531,6 +1531,115 @@ __global__ void __launch_bounds__(256) k_restrict_rb(Level<float> L, float inv_h
     *reinterpret_cast<float4*>(crhs + C) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// The residual of the corrected potential on the colour-split finest level
+// (reduced forms), r <- r - A e in FP32, formed by updating the previous
+// residual instead of recomputing b - A psi (psi += e is k_correct_ff's).
+// A e h^2 = sum over the faces of (e_c - e_nb) + kappa^2 h^2 e_c: the
+// differences carry no rounding of the smooth part of e, which dominates e
+// near convergence (|e| up to 1/kappa^2 times |r|).  A thread owns 8
+// natural cells of a row (the compact cells X0 .. X0+3 of both colours),
+// loaded as in k_restrict_rb; near-boundary cells take r - A e from
+// k_near_residual's scratch (natural index); other cells keep r = 0.
+// Blocks stride over z and leave per-block partial sums of r^2.
+__global__ void __launch_bounds__(256) k_residual_update_rb(Level<float> L, float inv_h2,
+                                                            const uint8_t* __restrict__ st, float* __restrict__ rhs,
+                                                            const float* __restrict__ e,
+                                                            const float* __restrict__ near_res, int half,
+                                                            double* __restrict__ partial) {
+    __shared__ float swarp[8];
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nxh = nx >> 1;
+    const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    const bool lane_on = X0 < nxh;
+    const int Xq = lane_on ? X0 : 0;
+    const float k2h2 = L.diag0 - 6.0f;  // (exact: diag0 in [6, 12))
+    float acc = 0.0f;
+    int ym = y, yp = y, il = Xq, ir = Xq;
+    if (y < ny) {
+        if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
+        if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
+        if (!wrap_axis(Xq - 1, nxh, L.per[0], il)) il = Xq;
+        if (!wrap_axis(Xq + 4, nxh, L.per[0], ir)) ir = Xq;
+    }
+    for (int z = blockIdx.z; z < nz && y < ny; z += gridDim.z) {
+        int zm, zp;
+        if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
+        if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
+        const int pe = (y + z) & 1;
+        const float* E0 = e + pe * half;
+        const float* E1 = e + (pe ^ 1) * half;
+        const int rowh = nxh * (y + ny * z), rown = nx * (y + ny * z) + 2 * Xq;
+        const int hym = nxh * (ym + ny * z), hyp = nxh * (yp + ny * z);
+        const int hzm = nxh * (y + ny * zm), hzp = nxh * (y + ny * zp);
+        float A[4], B[4], r[4], a[4], b[4], d[4], f[4], out[8];
+        ES_VLD(A, 0, E0 + rowh + Xq);
+        ES_VLD(B, 0, E1 + rowh + Xq);
+        const float hl = E1[rowh + il], hr = E0[rowh + ir];
+        const uint2 sw = *reinterpret_cast<const uint2*>(st + rown);
+        ES_VLD(r, 0, rhs + pe * half + rowh + Xq);
+        ES_VLD(a, 0, E1 + hym + Xq);
+        ES_VLD(b, 0, E1 + hyp + Xq);
+        ES_VLD(d, 0, E1 + hzm + Xq);
+        ES_VLD(f, 0, E1 + hzp + Xq);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const unsigned sv = ((k < 2 ? sw.x : sw.y) >> (16 * (k & 1))) & 0xFFu;
+            out[2 * k] = r[k];  // (0 at non-unknown cells)
+            if ((sv & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
+            const float ec = A[k];
+            float o = ec - (k == 0 ? hl : B[k - 1]);
+            o += ec - B[k];
+            o += ec - a[k];
+            o += ec - b[k];
+            o += ec - d[k];
+            o += ec - f[k];
+            o += k2h2 * ec;
+            out[2 * k] = r[k] - o * inv_h2;
+        }
+        ES_VLD(r, 0, rhs + (pe ^ 1) * half + rowh + Xq);
+        ES_VLD(a, 0, E0 + hym + Xq);
+        ES_VLD(b, 0, E0 + hyp + Xq);
+        ES_VLD(d, 0, E0 + hzm + Xq);
+        ES_VLD(f, 0, E0 + hzp + Xq);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const unsigned sv = ((k < 2 ? sw.x : sw.y) >> (16 * (k & 1) + 8)) & 0xFFu;
+            out[2 * k + 1] = r[k];
+            if ((sv & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
+            const float ec = B[k];
+            float o = ec - A[k];
+            o += ec - (k == 3 ? hr : A[k + 1]);
+            o += ec - a[k];
+            o += ec - b[k];
+            o += ec - d[k];
+            o += ec - f[k];
+            o += k2h2 * ec;
+            out[2 * k + 1] = r[k] - o * inv_h2;
+        }
+        // near-boundary cells from the scratch
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const unsigned sv = ((j < 4 ? sw.x : sw.y) >> (8 * (j & 3))) & 0xFFu;
+            if ((sv & (ST_KIND | ST_NEAR)) == (ST_UNKNOWN | ST_NEAR)) out[j] = near_res[rown + j];
+        }
+        if (lane_on) {
+#pragma unroll
+            for (int j = 0; j < 8; j++) acc = __fmaf_rn(out[j], out[j], acc);
+            vst(rhs + pe * half + rowh + X0, out[0], out[2], out[4], out[6]);
+            vst(rhs + (pe ^ 1) * half + rowh + X0, out[1], out[3], out[5], out[7]);
+        }
+    }
+    float v = acc;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) swarp[threadIdx.y] = v;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; w++) tot += (double)swarp[w];
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+    }
+}
+
 // Coarsest level: one thread block holds the level in shared memory and
 // runs `sweeps` red-black sweeps from a zero iterate.
 template <class T>
@@ -2248,6 +2357,28 @@ cudaError_t launch_correct(es_ctx* c) {
         k_correct<<<(N + 255) / 256, 256, 0, c->stream>>>(N, c->st[0], (const double*)c->e[0], c->psi);
     }
     count(c);
+    return cudaGetLastError();
+}
+
+// The FP32 residual update of the colour-split finest level (reduced
+// forms), after k_correct_ff.  Algorithmic bytes per cell: e (4), r in and
+// out (8), the state byte.
+cudaError_t launch_residual_update(es_ctx* c) {
+    Level<float> L = level_desc<float>(c, 0);
+    const int N = (int)c->g.N, nxh = L.nx / 2;
+    ProfScope ps(c, "residual_update", -1, (double)N * 13.0);
+    float* scratch = (float*)c->e2[0];
+    const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs);
+    k_near_residual<float, float, RbMap><<<ngrd, 256, 0, c->stream>>>(
+        L, c->st[0], (const float*)c->rhs[0], (const float*)c->e[0], c->near_list[0], c->near_count,
+        c->near_cap[0], 1.0f / L.h2, scratch, EAcc<float, float>{1.0f, 1.0f}, RbMap{N / 2});
+    const int gx = (nxh / 4 + 31) / 32, gy = (L.ny + 7) / 8;
+    int gz = kResPartials / (gx * gy);
+    gz = gz < 1 ? 1 : (gz > L.nz ? L.nz : gz);
+    k_residual_update_rb<<<dim3(gx, gy, gz), dim3(32, 8), 0, c->stream>>>(
+        L, 1.0f / L.h2, c->st[0], (float*)c->rhs[0], (const float*)c->e[0], scratch, N / 2, c->partial);
+    k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
+    count(c, 3);
     return cudaGetLastError();
 }
 
