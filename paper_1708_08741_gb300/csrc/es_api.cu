@@ -419,6 +419,10 @@ constexpr double kCycleTarget = 0.85;
 // at 5000 x tol that stays near 0.5 % of the tolerance, inside the margin
 // kCycleTarget leaves.
 constexpr double kFastUpdate = 5000.0;
+// (on small grids the float-float residual costs about a launch and the
+// update's occasional second norm read costs a host round trip: the update
+// is used from 2^21 cells on)
+constexpr long long kFastUpdateCells = 1LL << 21;
 
 int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
     if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
@@ -474,7 +478,7 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
         }
         for (int j = 0; j < k; j++) ES_CUDA(c, launch_vcycle(c, j > 0));
         const double before = norm;
-        if (c->rb0 && forced_cycles < 0 && norm <= kFastUpdate * c->tol) {
+        if (c->rb0 && forced_cycles < 0 && c->g.N >= kFastUpdateCells && norm <= kFastUpdate * c->tol) {
             // near the tolerance: psi += e, then r -= A e (FP32 update, error
             // ~1e-6 of the residual before the correction); the float-float
             // residual is formed again only if the updated one is not yet
