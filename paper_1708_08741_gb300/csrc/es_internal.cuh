@@ -201,6 +201,9 @@ inline size_t pdf_bytes(int precision) {
 // each segment with its own counter, so that the list builder's atomics
 // spread over that many addresses.
 constexpr int kNearSegs = 64;
+// blocks per segment and per 64 SMs of a near-cell list pass (the passes are
+// bound by the latency of their scattered loads: more threads in flight)
+constexpr int kNearBlocks = 16;
 
 // Capacity of the per-block partial-sum array of the residual norm.
 constexpr int kResPartials = 8192;

@@ -2082,7 +2082,7 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                 // colour-split finest level: interior pass, then the colour's
                 // near-boundary cells from the list
                 const dim3 sgrd((L.nx / 8 + 31) / 32, (L.ny + 7) / 8, L.nz);
-                const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, kNearSegs);
+                const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, kNearSegs);
                 const int* cnt = c->near_count + 2 * kNearSegs * l;
                 const size_t hl = (size_t)kNearSegs * c->near_cap[l];
                 for (int col = 0; col < 2; col++) {
@@ -2113,7 +2113,7 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                 count(c, 2);
                 return;
             }
-            const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, kNearSegs);
+            const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, kNearSegs);
             const int* cnt = c->near_count + 2 * kNearSegs * l;
             const size_t half = (size_t)kNearSegs * c->near_cap[l];
             {
@@ -2195,7 +2195,7 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
         if (vec) {
             dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
             T* scratch = (T*)c->e2[l];  // (the fused sweep's second iterate; free between sweeps)
-            const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs);
+            const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, 2 * kNearSegs);
             const int* cnt = c->near_count + 2 * kNearSegs * l;
             bool done = false;
             if constexpr (kNative && std::is_same<T, float>::value) {
@@ -2281,7 +2281,7 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         int gz = kResPartials / (gx * gy);
         gz = gz < 1 ? 1 : (gz > c->g.nz ? c->g.nz : gz);
         const dim3 grd(gx, gy, gz), blk(32, 8);
-        const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs);
+        const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, 2 * kNearSegs);
         if (c->rb0) {
             // r goes to the colour-split right-hand side of the finest level
             k_outer_residual_near_ff<RbMap><<<ngrd, 256, 0, c->stream>>>(
@@ -2368,7 +2368,7 @@ cudaError_t launch_residual_update(es_ctx* c) {
     const int N = (int)c->g.N, nxh = L.nx / 2;
     ProfScope ps(c, "residual_update", -1, (double)N * 13.0);
     float* scratch = (float*)c->e2[0];
-    const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * 4, 2 * kNearSegs);
+    const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, 2 * kNearSegs);
     k_near_residual<float, float, RbMap><<<ngrd, 256, 0, c->stream>>>(
         L, c->st[0], (const float*)c->rhs[0], (const float*)c->e[0], c->near_list[0], c->near_count,
         c->near_cap[0], 1.0f / L.h2, scratch, EAcc<float, float>{1.0f, 1.0f}, RbMap{N / 2});
@@ -2411,7 +2411,7 @@ cudaError_t launch_body_force(es_ctx* c) {
         dim3 vgrd((g.nx / 4 + 31) / 32, (g.ny + 7) / 8, g.nz);
         k_body_force_v<<<vgrd, dim3(32, 8), 0, c->stream>>>(g, (float)E[0], (float)E[1], (float)E[2], (float)k2e,
                                                             c->psi32, c->flags, (float*)c->fb);
-        k_body_force_near<<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * 4, kNearSegs), 256, 0, c->stream>>>(
+        k_body_force_near<<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, kNearSegs), 256, 0, c->stream>>>(
             g, c->S, (float)E[0], (float)E[1], (float)E[2], (float)k2e, c->psi32, c->owner, c->st[0],
             (const float2*)c->pbc, wall2, c->bf_list, c->bf_count, c->bf_cap, (float*)c->fb);
         count(c);
