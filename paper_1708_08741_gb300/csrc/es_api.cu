@@ -174,6 +174,11 @@ void release(es_ctx* c) {
     for (cudaEvent_t ev : c->prof_pool) cudaEventDestroy(ev);
     c->prof_recs.clear();
     c->prof_pool.clear();
+    for (int w = 0; w < 2; w++)
+        if (c->vgraph[w]) {
+            cudaGraphExecDestroy(c->vgraph[w]);
+            c->vgraph[w] = nullptr;
+        }
 }
 
 // Reads the residual norm and the device status word (synchronises).

@@ -135,6 +135,9 @@ struct es_ctx {
     int slip;        // bit f: face f (x-lo, x-hi, y-lo, ...) of a non-periodic axis is free-slip
     bool rb0;        // the finest level's e and rhs in the colour-split layout (reduced forms)
     bool mapped_once;  // the particles were mapped at least once (flags valid outside their shells)
+    cudaGraphExec_t vgraph[2];          // the V-cycle from zero / warm-started, captured on first use
+    unsigned long long vgraph_kernels[2];  // kernel launches in each graph
+    bool vgraph_off;                    // capture failed once: launch directly
     std::vector<double> h_R;  // radii and kinds as created (fixed for the context's life)
     std::vector<int> h_kind;
     double lambda_e, lambda_o;

@@ -2326,13 +2326,60 @@ cudaError_t launch_outer_residual(es_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_vcycle(es_ctx* c, int warm) {
-    if (mixed(c)) {
-        set_coarse_smem<float>(c);
-        return vcycle_level<float>(c, 0, warm);
-    }
-    set_coarse_smem<double>(c);
+namespace {
+cudaError_t vcycle_direct(es_ctx* c, int warm) {
+    if (mixed(c)) return vcycle_level<float>(c, 0, warm);
     return vcycle_level<double>(c, 0, warm);
+}
+}  // namespace
+
+// The V-cycle's launches depend only on the context's shapes, buffers and
+// on `warm` (device-side data such as the near-cell lists and their counts
+// are read at run time), so each of the two sequences is captured once into
+// a CUDA graph and replayed: the many small coarse-level kernels then follow
+// each other without a host launch apiece.  Launched directly instead while
+// per-kernel profiling brackets launches with events, with the fused sweep
+// (it swaps iterate buffers between cycles), with the FP16 correction (its
+// scale changes per correction), on the legacy default stream (no capture
+// there), or after a capture failed.
+cudaError_t launch_vcycle(es_ctx* c, int warm) {
+    if (mixed(c))
+        set_coarse_smem<float>(c);
+    else
+        set_coarse_smem<double>(c);
+    const bool graph = !c->prof && !c->vgraph_off && c->stream != nullptr &&
+                       c->P.smoother == ES_SMOOTH_TWO_PASS && c->P.mg_storage == ES_MG_NATIVE;
+    if (!graph) return vcycle_direct(c, warm);
+    const int w = warm ? 1 : 0;
+    if (!c->vgraph[w]) {
+        const unsigned long long before = c->launches;
+        cudaError_t err = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            c->vgraph_off = true;
+            return vcycle_direct(c, warm);
+        }
+        const cudaError_t cerr = vcycle_direct(c, warm);
+        cudaGraph_t gph = nullptr;
+        err = cudaStreamEndCapture(c->stream, &gph);
+        cudaGraphExec_t ge = nullptr;
+        if (cerr == cudaSuccess && err == cudaSuccess && gph)
+            err = cudaGraphInstantiate(&ge, gph, 0);
+        if (gph) cudaGraphDestroy(gph);
+        // (the launches counted while capturing are the graph's kernels; they
+        // run at each replay)
+        const unsigned long long captured = c->launches - before;
+        c->launches = before;
+        if (cerr != cudaSuccess || err != cudaSuccess || !ge) {
+            cudaGetLastError();
+            c->vgraph_off = true;
+            return vcycle_direct(c, warm);
+        }
+        c->vgraph[w] = ge;
+        c->vgraph_kernels[w] = captured;
+    }
+    count(c, c->vgraph_kernels[w]);
+    return cudaGraphLaunch(c->vgraph[w], c->stream);
 }
 
 // Algorithmic bytes per cell: e (s) and the state byte in, psi (8) in and out.
