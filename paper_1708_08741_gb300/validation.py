@@ -12,9 +12,17 @@ The confinement is taken out as the paper does: the relative deviation from
 Stokes' velocity of the same sphere in the same box, Delta_r U_Stokes, is
 subtracted from the electrophoretic deviation Delta_r U = (U* - U_EP) / U_EP.
 
-Here the box is periodic (the paper's free-slip walls are not built), so
-both runs are the periodic-array setting, with velocities measured relative
-to the mean fluid velocity.  The electrophoretic run needs no balancing
+Two settings.  Periodic box (``validate``): both runs are the
+periodic-array setting, with velocities measured relative to the mean fluid
+velocity (the Stokes half is described below).  Free-slip box
+(``validate_free_slip``, the paper's setting): all six faces are free-slip
+walls with zero-flux potential, velocities are absolute (the box holds no
+net flow), and the Stokes run drags the same sphere, uncharged, with a
+constant external force F_0 = 6 pi mu R U_Henry added to its hydrodynamic
+force every step (es_forces, then es_set_forces, then es_advance), so that
+Delta_r U_Stokes = U*_Stokes / U_Henry - 1.
+
+In the periodic box:  The electrophoretic run needs no balancing
 force: the double layer carries the opposite of the sphere's charge.  The
 Stokes run holds an uncharged sphere (zeta = 0, so psi = 0 and no field
 force) in place with a very large density and drives the fluid past it with
@@ -27,7 +35,7 @@ U, and Delta_r U_Stokes = 1 / K - 1 (the velocity the same force would give
 relative to Stokes' F / (6 pi mu R)).
 Lattice units: dx = dt = rho = eps = 1, mu = (tau - 1/2) / 3.
 
-    python -m paper_1708_08741_gb300.validation [--n 128] [--radius 4] [--kR 0.5]
+    python -m paper_1708_08741_gb300.validation [--n 128] [--radius 4] [--kR 0.5] [--walls free-slip]
 """
 from __future__ import annotations
 
@@ -52,10 +60,12 @@ def sphere_charge(zeta: float, R: float, kappa: float, eps: float = 1.0) -> floa
     return 4.0 * math.pi * R * zeta * eps * (1.0 + kappa * R)
 
 
-def _box(n, R, tau, kappa, E, zeta, accel, levels, rho_p_ratio=1.195):
-    wl = W.Workload(name=f"henry_{n}_R{R:g}", dims=[n, n, n], periodic=(1, 1, 1), tau=tau, kappa=kappa,
-                    eps=1.0, E_ext=(E, 0.0, 0.0), accel=accel, levels=levels, res_rf=1e-8, max_cycles=200,
-                    rho_p_ratio=rho_p_ratio)
+def _box(n, R, tau, kappa, E, zeta, accel, levels, rho_p_ratio=1.195, walls=False):
+    wl = W.Workload(name=f"henry_{n}_R{R:g}", dims=[n, n, n], periodic=(0, 0, 0) if walls else (1, 1, 1),
+                    tau=tau, kappa=kappa, eps=1.0, E_ext=(E, 0.0, 0.0), accel=accel, levels=levels, res_rf=1e-8,
+                    max_cycles=200, rho_p_ratio=rho_p_ratio)
+    if walls:
+        wl.wall_slip = (1, 1, 1, 1, 1, 1)
     c = np.array([[n / 2.0, n / 2.0, n / 2.0]])
     return W._set_particles(wl, c, np.array([float(R)]), np.array([W.KIND_ZETA]), np.array([zeta]), np.zeros(1))
 
@@ -70,11 +80,12 @@ def _solid_mask(wl):
 
 
 def terminal_velocity(wl, steps: int, sample_every: int = 100, precision: int = es.ES_MIXED32,
-                      device: str = "cuda:0") -> dict:
+                      device: str = "cuda:0", relative: bool = True) -> dict:
     """Runs ``steps`` steps; over the second half of the samples returns the
-    mean sphere velocity relative to the mean fluid velocity (U), its
-    relative spread (max - min) / mean, and the mean of F_x / U_rel with F_x
-    the hydrodynamic force on the sphere (drag per unit relative velocity)."""
+    mean sphere velocity relative to the mean fluid velocity (U; absolute
+    with relative=False), its relative spread (max - min) / mean, and the
+    mean of F_x / U_rel with F_x the hydrodynamic force on the sphere (drag
+    per unit relative velocity)."""
     sim = es.Simulation(wl, precision, device=device)
     samples, drag = [], []
     try:
@@ -83,8 +94,10 @@ def terminal_velocity(wl, steps: int, sample_every: int = 100, precision: int = 
             sim.step()
             if s % sample_every == 0:
                 up = sim.particles()["v"][0, 0]
-                fluid = sim.field(es.FIELD_OWNER) < 0
-                uf = sim.field(es.FIELD_U)[0][fluid].mean()
+                uf = 0.0
+                if relative:
+                    fluid = sim.field(es.FIELD_OWNER) < 0
+                    uf = sim.field(es.FIELD_U)[0][fluid].mean()
                 F, _ = sim.forces()
                 samples.append(up - uf)
                 drag.append(F[0, 0] / (uf - up) if uf != up else float("nan"))
@@ -123,16 +136,66 @@ def validate(n: int = 128, R: float = 4.0, kR: float = 0.5, tau: float = 6.0, ze
             "K_stokes": K, "dU_stokes": d_st, "dU_corrected": d_ep - d_st}
 
 
+def dragged_velocity(wl, f0: float, steps: int, sample_every: int = 100, precision: int = es.ES_MIXED32,
+                     device: str = "cuda:0") -> dict:
+    """The first sphere of ``wl`` (uncharged) moved by the constant force
+    (f0, 0, 0) on top of its hydrodynamic force; mean x velocity over the
+    second half of the samples."""
+    sim = es.Simulation(wl, precision, device=device)
+    samples = []
+    try:
+        for s in range(1, steps + 1):
+            sim.map_particles()
+            sim.solve()
+            sim.lbm_step()
+            F, T = sim.forces()
+            F = F.copy()
+            F[0, 0] += f0
+            sim.set_forces(F, T)
+            sim.advance()
+            if s % sample_every == 0:
+                samples.append(sim.particles()["v"][0, 0])
+    finally:
+        sim.close()
+    tail = np.array(samples[len(samples) // 2:])
+    mean = float(tail.mean())
+    return {"U": mean, "spread": float((tail.max() - tail.min()) / abs(mean)) if mean else float("nan"),
+            "samples": len(samples)}
+
+
+def validate_free_slip(n: int = 128, R: float = 4.0, kR: float = 0.5, tau: float = 6.0, zeta: float = 1.0,
+                       E: float = 2.5e-3, steps: int = 12000, levels: int = 5, device: str = "cuda:0") -> dict:
+    """The validation in a box with free-slip walls on all faces (the
+    paper's setting): Henry deviation of the electrophoretic run, the Stokes
+    deviation of the same sphere without a double layer (kappa = 0, moved by
+    F = q E), and their difference."""
+    mu = (tau - 0.5) / 3.0
+    ep = terminal_velocity(_box(n, R, tau, kR / R, E, zeta, (0.0, 0.0, 0.0), levels, walls=True), steps,
+                           device=device, relative=False)
+    u_henry = henry_velocity(zeta, E, 1.0, mu, kR)
+    f0 = 6.0 * math.pi * mu * R * u_henry
+    st = dragged_velocity(_box(n, R, tau, kR / R, 0.0, 0.0, (0.0, 0.0, 0.0), levels, walls=True), f0, steps,
+                          device=device)
+    u0 = u_henry
+    d_ep = (ep["U"] - u_henry) / u_henry
+    d_st = st["U"] / u0 - 1.0
+    return {"walls": "free-slip", "n": n, "R": R, "kR": kR, "tau": tau, "zeta": zeta, "E": E, "steps": steps,
+            "U_henry": u_henry, "U_sim": ep["U"], "spread": ep["spread"], "dU": d_ep, "U_stokes": st["U"],
+            "U0": u0, "dU_stokes": d_st, "dU_corrected": d_ep - d_st}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--radius", type=float, nargs="+", default=[4.0])
     ap.add_argument("--kR", type=float, nargs="+", default=[0.265, 0.5, 0.8])
     ap.add_argument("--steps", type=int, default=12000)
+    ap.add_argument("--walls", choices=["periodic", "free-slip"], default="periodic")
     a = ap.parse_args()
+    run = validate_free_slip if a.walls == "free-slip" else validate
     for R in a.radius:
         for kR in a.kR:
-            print(json.dumps(validate(a.n, R, kR, steps=a.steps)), flush=True)
+            print(json.dumps(run(a.n, R, kR, steps=a.steps)), flush=True)
 
 
 if __name__ == "__main__":

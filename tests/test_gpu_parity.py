@@ -522,3 +522,18 @@ def test_full_size_suspension_sampled():
         own = g.gather(es.FIELD_OWNER, cells3[:, 0] + nx * (cells3[:, 1] + ny * cells3[:, 2]))[0]
         np.testing.assert_array_equal(own == p, inside)
     g.close()
+
+
+def test_radius_and_kind_fixed_after_creation():
+    """es_set_particles moves spheres but rejects a change of radius or kind
+    (the mapping updates flags only near each sphere's surface)."""
+    wl = W.mixed_box()
+    g = es.Simulation(wl, es.ES_MIXED32)
+    for R, kind in ((wl.R * 1.1, wl.kind), (wl.R, 1 - wl.kind)):
+        parts = es.pack_particles(wl.x, wl.v, wl.w, R, kind, wl.zeta, wl.q)
+        rc = g.lib.es_set_particles(g.h, parts, wl.n_particles)
+        assert rc == es.ES_EINVAL and "fixed after creation" in g.lib.es_last_error(g.h).decode()
+    g.set_particles(wl.x + 0.25, wl.v, wl.w)
+    info = g.step()
+    assert info["r"] < info["tol"]
+    g.close()
