@@ -55,7 +55,9 @@ extern "C" {
                         FP32 multigrid cycles inside a defect correction whose
                         potential and residual are float-float (two floats,
                         about 48 significant bits, evaluated on the FP32 pipe),
-                        FP64 force/torque sums and rigid-body update           */
+                        force/torque from FP32 link terms with the constant
+                        2 w_q c_q part summed exactly (es_forces), FP64
+                        rigid-body update                                     */
 #define ES_MIXED16 2 /* as ES_MIXED32, with the PDFs stored as FP16 relative
                         deviations (f_q - w_q) / w_q                           */
 
@@ -84,8 +86,8 @@ extern "C" {
 
 typedef struct {
     int dims[3];        /* cells per axis; each a multiple of 2^(levels-1)          */
-    int periodic[3];    /* 1: periodic axis; 0: no-slip walls half-way outside the
-                           first and last layer (LBM) with pot_bc on both faces     */
+    int periodic[3];    /* 1: periodic axis; 0: walls half-way outside the first
+                           and last layer (LBM: wall_slip) with pot_bc on both faces */
     int pot_bc[6];      /* faces x-lo, x-hi, y-lo, y-hi, z-lo, z-hi of non-periodic axes */
     double pot_val[6];  /* Dirichlet values of those faces                          */
     double tau;         /* LBM relaxation time, nu = (tau - 1/2)/3 (Eq. kinVisc); > 1/2 */
@@ -94,7 +96,7 @@ typedef struct {
     double E_ext[3];    /* applied field (Sec. 5.6)                               */
     double accel[3];    /* additional uniform body force density on the fluid      */
     double rho_p_ratio; /* particle / fluid density (1.195 in Sec. 6.1)           */
-    int precision;      /* ES_FP64 or ES_MIXED32                                  */
+    int precision;      /* ES_FP64, ES_MIXED32 or ES_MIXED16                      */
     int levels;         /* multigrid levels, 1..12                                */
     int nu1, nu2;       /* pre- and post-smoothing red-black sweeps per level     */
     int coarse_sweeps;  /* red-black sweeps on the coarsest level                 */
@@ -202,10 +204,14 @@ int es_destroy(es_ctx* ctx);
 int es_map_particles(es_ctx* ctx);
 
 /* Algorithm 1, "while residual >= tol: iterate" and the coupling block
- * (Sec. 5.3, Sec. 5.6): r = b - A psi in FP64 with the 7-point
- * finite-volume stencil of Sec. 4.3 and the boundary treatment of Sec. 5.4;
- * tol = res_rf * ||r|| of the first solve of the run; while ||r|| >= tol,
- * psi += V-cycle(r).  forced_cycles >= 0 applies exactly that many cycles
+ * (Sec. 5.3, Sec. 5.6): r = b - A psi with the 7-point finite-volume
+ * stencil of Sec. 4.3 and the boundary treatment of Sec. 5.4 (FP64, or
+ * float-float in the reduced forms); tol = res_rf * ||r|| of the first
+ * solve of the run; while ||r|| >= tol, psi += V-cycle(r) (reduced forms:
+ * several warm-started FP32 V-cycles per correction, and, on grids of 2^21
+ * cells or more starting within 5000 x tol, the residual after a correction
+ * updated in FP32 as r - A e, re-formed in float-float if that is not yet
+ * below tol).  forced_cycles >= 0 applies exactly that many cycles
  * and skips the tolerance test.  Then computes the EDL field grad psi
  * (Eq. ElPotGradComp), the charge density -kappa^2 eps psi (Eq.
  * ChrgDensDHA) and the body force f_b = rho_e (E_ext - grad psi).
@@ -219,13 +225,15 @@ int es_potential_solve(es_ctx* ctx, int forced_cycles, es_solve_info* info);
  * (Eq. LBMcollideStep), incompressible equilibrium (Eq. EqPDF_TRT), Luo
  * forcing with the modified velocity (Eq. LBE_forcetermLuo, Eq.
  * modified_velocity) and velocity bounce-back at moving sphere cells (Eq.
- * LBMMovWall) and at resting walls.                                       */
+ * LBMMovWall), resting bounce-back at no-slip walls and specular
+ * reflection at free-slip walls (wall_slip).                              */
 int es_lbm_step(es_ctx* ctx);
 
 /* Algorithm 1, "apply hydrodynamic force to particles" (Sec. 4.2, Eq.
  * LBMhydrodynForce, torque by the same sum with (x_s - X) x dF) plus the
- * electrostatic force F_C = q E_ext (Sec. 5.6), summed in FP64 in a fixed
- * order (deterministic).  Uses the populations bounced by the last
+ * electrostatic force F_C = q E_ext (Sec. 5.6), summed in a fixed order
+ * (deterministic): in FP64, or in the reduced forms from FP32 link terms
+ * (float-float block sums) plus the exactly summed constant part.  Uses the populations bounced by the last
  * es_lbm_step.  F and T receive n x 3 doubles each (particle major); either
  * may be NULL.  on_device != 0: F/T are device pointers (no
  * synchronisation); 0: host pointers (synchronises).  The sums are also
