@@ -1326,7 +1326,7 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
                                                     const T* __restrict__ rhs, const E* __restrict__ e,
                                                     const T* __restrict__ near_res, int cnx,
                                                     int cny, const uint8_t* __restrict__ cst, T* __restrict__ crhs,
-                                                    EAcc<T, E> A, int half = 0) {
+                                                    EAcc<T, E> A, int half = 0, int red_only = 0) {
     const int cx_warp = 2 * (blockIdx.x * 32);
     const int cxs = cx_warp + 2 * threadIdx.x;
     const int cy = blockIdx.y * 8 + threadIdx.y, cz = blockIdx.z;
@@ -1406,6 +1406,13 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
 #pragma unroll
             for (int i = 0; i < 4; i++)
                 if ((near_bits >> i) & 1u) res[i] = near_res[row + xq + i];
+            if (red_only) {
+                // (after a Gauss-Seidel black half sweep the black residuals
+                // vanish: see k_restrict_red_rb)
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if ((xq + i + y + z) & 1) res[i] = (T)0;
+            }
             sum0 += res[0] + res[1];
             sum1 += res[2] + res[3];
         }
@@ -1638,6 +1645,96 @@ __global__ void __launch_bounds__(256) k_residual_update_rb(Level<float> L, floa
         for (int w = 0; w < 8; w++) tot += (double)swarp[w];
         partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
     }
+}
+
+// Residual + restriction right after a black Gauss-Seidel half sweep
+// (omega = 1) on the colour-split finest level.  That half sweep solved
+// every black cell's equation exactly for the red values around it, which
+// it does not change, so the black residuals vanish (up to rounding) and
+// the restricted residual is the mean of the 4 red children's residuals
+// (the 4 black children count as 0).  Laid out as k_smooth_rb for the red
+// colour: a thread forms the residuals of 4 red cells of one fine row
+// (compact cells X0 .. X0+3, the red children of coarse cells X0 .. X0+3),
+// reading the red e and rhs and the black e around them (7 bytes per fine
+// cell instead of 9); the 4 fine rows of a coarse row are the block's 4
+// warps, added in the order of k_restrict_v (dk outer, dj inner).
+// Near-boundary red children come from k_near_residual (red segments).
+__global__ void __launch_bounds__(128) k_restrict_red_rb(Level<float> L, float inv_h2,
+                                                         const uint8_t* __restrict__ st,
+                                                         const float* __restrict__ rhs,
+                                                         const float* __restrict__ e,
+                                                         const float* __restrict__ near_res, int cnx, int cny,
+                                                         const uint8_t* __restrict__ cst, float* __restrict__ crhs,
+                                                         int half) {
+    __shared__ float4 part[4][32];
+    const int nxh = L.nx >> 1, ny = L.ny, nz = L.nz;
+    const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int cy = blockIdx.y, cz = blockIdx.z;
+    const int dj = threadIdx.y & 1, dk = threadIdx.y >> 1;
+    const int y = 2 * cy + dj, z = 2 * cz + dk;
+    const bool lane_on = X0 < cnx;
+    const int iq = lane_on ? X0 : 0;
+    const int O = (y + z) & 1;  // red cells of this row: x = 2 i + O
+    const float* eo = e + half;  // black
+    int ym, yp, zm, zp, il, ir;
+    if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
+    if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
+    if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
+    if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
+    if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
+    if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
+    const int rowh = nxh * (y + ny * z), rown = L.nx * (y + ny * z) + 2 * iq;
+    float c[4], ox[6], a[4], b[4], d[4], f[4], r[4];
+    ES_VLD(c, 0, e + rowh + iq);
+    ES_VLD(ox, 1, eo + rowh + iq);
+    ox[0] = O == 0 ? eo[rowh + il] : 0.0f;
+    ox[5] = O == 1 ? eo[rowh + ir] : 0.0f;
+    ES_VLD(a, 0, eo + nxh * (ym + ny * z) + iq);
+    ES_VLD(b, 0, eo + nxh * (yp + ny * z) + iq);
+    ES_VLD(d, 0, eo + nxh * (y + ny * zm) + iq);
+    ES_VLD(f, 0, eo + nxh * (y + ny * zp) + iq);
+    ES_VLD(r, 0, rhs + rowh + iq);
+    const uint2 sw = *reinterpret_cast<const uint2*>(st + rown);
+    float res[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int bit = 2 * k + O;
+        const unsigned sv = ((bit < 4 ? sw.x : sw.y) >> (8 * (bit & 3))) & 0xFFu;
+        res[k] = 0.0f;
+        if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+        if (sv & ST_NEAR) {
+            res[k] = near_res[rown + bit];
+            continue;
+        }
+        float o = O == 0 ? ox[k] : ox[k + 1];  // (left, right, y-, y+, z-, z+ as k_restrict_v)
+        o += O == 0 ? ox[k + 1] : ox[k + 2];
+        o += a[k];
+        o += b[k];
+        o += d[k];
+        o += f[k];
+        res[k] = r[k] - (L.diag0 * c[k] - o) * inv_h2;
+    }
+    part[threadIdx.y][threadIdx.x] = make_float4(res[0], res[1], res[2], res[3]);
+    __syncthreads();
+    if (threadIdx.y != 0 || !lane_on) return;
+    // per fine row k_restrict_v adds (even child + odd child), one of them
+    // the black child (0): the red residual plus 0, i.e. the red residual
+    float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float4 p = part[q][threadIdx.x];
+        sum[0] += p.x;
+        sum[1] += p.y;
+        sum[2] += p.z;
+        sum[3] += p.w;
+    }
+    const int C = X0 + cnx * (cy + cny * cz);
+    const uchar4 cs = *reinterpret_cast<const uchar4*>(cst + C);
+    const uint8_t ck[4] = {cs.x, cs.y, cs.z, cs.w};
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = ((ck[k] & ST_KIND) == ST_UNKNOWN) ? sum[k] / 8.0f : 0.0f;
+    *reinterpret_cast<float4*>(crhs + C) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // Coarsest level: one thread block holds the level in shared memory and
@@ -2054,6 +2151,10 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
     // the finest level of the reduced forms in the colour-split layout
     const bool split = kNative && std::is_same<T, float>::value && l == 0 && c->rb0;
     const RbMap rb{Nl / 2};
+    // reduced forms, Gauss-Seidel: the pre-smoothing ends with a black half
+    // sweep, after which only red residuals remain (the restriction adds the
+    // red children only; the same in both finest-level layouts)
+    const bool red_only = kNative && std::is_same<T, float>::value && c->P.omega == 1.0 && c->P.nu1 >= 1;
     int rb_zc = 1;
     dim3 rb_grid(1, 1, 1);
     if (use_rb) rb_grid = rb_launch_shape<T>(c, L, rb_zc);
@@ -2199,7 +2300,16 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             const int* cnt = c->near_count + 2 * kNearSegs * l;
             bool done = false;
             if constexpr (kNative && std::is_same<T, float>::value) {
-                if (split) {
+                if (split && red_only) {
+                    // (red near cells only: the first kNearSegs segments)
+                    k_near_residual<T, E, RbMap><<<dim3(ngrd.x, kNearSegs), 256, 0, c->stream>>>(
+                        L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
+                    const dim3 qgrd((m[0] / 4 + 31) / 32, m[1], m[2]);
+                    k_restrict_red_rb<<<qgrd, dim3(32, 4), 0, c->stream>>>(L, (T)1 / L.h2, st, rhs, e, scratch,
+                                                                           m[0], m[1], c->st[l + 1],
+                                                                           (T*)c->rhs[l + 1], rb.half);
+                    done = true;
+                } else if (split) {
                     k_near_residual<T, E, RbMap><<<ngrd, 256, 0, c->stream>>>(
                         L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
                     const dim3 qgrd((m[0] / 4 + 31) / 32, (m[1] + 1) / 2, m[2]);
@@ -2212,7 +2322,8 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                 k_near_residual<T, E><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l], cnt,
                                                                    c->near_cap[l], (T)1 / L.h2, scratch, A);
                 k_restrict_v<T, E><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch,
-                                                                 m[0], m[1], c->st[l + 1], (T*)c->rhs[l + 1], A);
+                                                                 m[0], m[1], c->st[l + 1], (T*)c->rhs[l + 1], A, 0,
+                                                                 red_only ? 1 : 0);
             }
             count(c, 2);
         } else if constexpr (kNative) {
