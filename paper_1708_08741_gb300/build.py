@@ -2,7 +2,7 @@
 
 Each .cu file is compiled by its own nvcc process in parallel, then linked
 into ``paper_1708_08741_gb300/_build/libes.so``.  The CUDA runtime is linked
-statically, so the library needs only the driver at run time.
+statically, so the library needs only the CUDA driver at run time.
 """
 from __future__ import annotations
 

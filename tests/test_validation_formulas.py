@@ -1,5 +1,5 @@
 """Henry's electrophoretic velocity (Eq. ElPhorVelSphere with Ohshima's
-Henry function, Eq. ElPhorMobilitySphere) as the validation driver uses it:
+Henry function, Eq. ElPhorMobilitySphere) as paper_1708_08741_gb300.validation uses it:
 its two classical limits, and the velocities the paper prints for its
 validation spheres (tests/golden/henry_velocities.txt)."""
 import math
