@@ -390,3 +390,37 @@ def test_pb_tends_to_debye_hueckel_for_large_thermal_voltage():
     fluid = o.owner() < 0
     d = np.max(np.abs(nl[fluid] - lin[fluid])) / np.max(np.abs(lin[fluid]))
     assert 1e-12 < d < 1e-6
+
+
+@pytest.mark.parametrize("case", ["periodic_zeta", "mixed"])
+def test_black_residuals_vanish_after_a_gauss_seidel_sweep(case):
+    """After a red-black Gauss-Seidel sweep (omega = 1; red, then black) of
+    A e = r, every black cell's equation holds for the red values around it,
+    which the black half sweep does not change: the black residuals vanish
+    and only red ones remain (what lets a restriction after pre-smoothing
+    add the red children only).  A is the finite-volume system assembled
+    directly (the dense-solve test's assembly), not the oracle's."""
+    if case == "periodic_zeta":
+        wl = _wl((8, 8, 8), (1, 1, 1), 0.4, [((4.0, 4.0, 4.0), 1.6, W.KIND_ZETA, 0.8, 0.0)])
+    else:
+        wl = _wl((8, 8, 8), (0, 1, 1), 0.5, [((2.5, 2.5, 3.0), 1.2, W.KIND_ZETA, -0.6, 0.0),
+                                              ((5.6, 5.5, 5.5), 1.5, W.KIND_CHARGE, 0.0, -0.9)],
+                 pot_bc=(1, 0, 0, 0, 0, 0), pot_val=(0.3, 0, 0, 0, 0, 0))
+    o = oracle.Oracle(wl)
+    o.map_particles()
+    owner = o.owner()
+    A, _, idx, _ = _dense_system(wl.dims, wl.periodic, wl.kappa, owner, wl.kind, wl.zeta, wl.q,
+                                 wl.pot_bc, wl.pot_val)
+    rng = np.random.Generator(np.random.PCG64(5))
+    fluid = owner < 0
+    r = np.where(fluid, rng.standard_normal(owner.shape), 0.0)
+    e = o.smooth(r, np.zeros(owner.shape), 1)
+    # residual cell by cell in the dense system's unknown order
+    cells = np.argwhere(fluid)  # (k, j, i) in C order, as the dense assembly numbers them
+    ev = np.array([e[k, j, i] for k, j, i in cells])
+    rv = np.array([r[k, j, i] for k, j, i in cells])
+    res = rv - A @ ev
+    colour = (cells[:, 0] + cells[:, 1] + cells[:, 2]) % 2
+    scale = np.max(np.abs(rv))
+    assert np.max(np.abs(res[colour == 1])) < 1e-13 * scale
+    assert np.max(np.abs(res[colour == 0])) > 1e-3 * scale
