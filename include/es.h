@@ -122,7 +122,27 @@ typedef struct {
     int fine_layout;    /* ES_LAYOUT_AUTO (0, default) or ES_LAYOUT_NATURAL: storage of
                            the finest level's multigrid correction and right-hand
                            side (see below); both give the same iteration          */
+    int near_list_cells; /* multigrid levels (dims[0] % 4 == 0 on the level) with more
+                           cells than this smooth their near-boundary cells in
+                           separate passes over per-colour cell lists, the others
+                           inside the smoothing kernel; the same sweep either way.
+                           0 selects the default ES_NEAR_LIST_CELLS; < 0 is
+                           ES_EINVAL.  (The colour-split finest level always uses
+                           the lists.)                                             */
+    int fast_update_cells; /* reduced forms with the colour-split finest level: on
+                           grids of at least this many cells a tolerance-driven
+                           solve that starts within 5000 x tol updates the
+                           residual after a correction in FP32 as r - A e (Sec.
+                           5.3 defect correction, see es_potential_solve).  0
+                           selects the default ES_FAST_UPDATE_CELLS; < 0 is
+                           ES_EINVAL.                                              */
 } es_params;
+
+/* Defaults of near_list_cells and fast_update_cells (2^21 cells): below this
+   size the separate passes cost more in launches and host round trips than
+   they save. */
+#define ES_NEAR_LIST_CELLS (1 << 21)
+#define ES_FAST_UPDATE_CELLS (1 << 21)
 
 /* Execution of one red-black Gauss-Seidel sweep (same arithmetic either way):
    TWO_PASS runs one in-place pass per colour; FUSED runs red and black in
@@ -208,10 +228,10 @@ int es_map_particles(es_ctx* ctx);
  * stencil of Sec. 4.3 and the boundary treatment of Sec. 5.4 (FP64, or
  * float-float in the reduced forms); tol = res_rf * ||r|| of the first
  * solve of the run; while ||r|| >= tol, psi += V-cycle(r) (reduced forms:
- * several warm-started FP32 V-cycles per correction, and, on grids of 2^21
- * cells or more starting within 5000 x tol, the residual after a correction
- * updated in FP32 as r - A e, re-formed in float-float if that is not yet
- * below tol).  forced_cycles >= 0 applies exactly that many cycles
+ * several warm-started FP32 V-cycles per correction, and, on grids of at
+ * least fast_update_cells cells starting within 5000 x tol, the residual
+ * after a correction updated in FP32 as r - A e, re-formed in float-float if
+ * that is not yet below tol).  forced_cycles >= 0 applies exactly that many cycles
  * and skips the tolerance test.  Then computes the EDL field grad psi
  * (Eq. ElPotGradComp), the charge density -kappa^2 eps psi (Eq.
  * ChrgDensDHA) and the body force f_b = rho_e (E_ext - grad psi).
@@ -263,23 +283,25 @@ int es_gather(es_ctx* ctx, int which, const int64_t* idx, int n, double* out);
 
 /* es_gather without any device allocation.  The paper has no counterpart:
  * this is a library convenience.  es_gather allocates its device staging
- * buffer on first use; callers that cannot allocate device memory at that
- * point -- a thread capturing CUDA work into a graph (cudaMalloc is not
- * allowed during stream capture), a real-time loop that must not wait on an
- * allocator, or an application that pre-assigns all device memory -- use
- * this variant, which stages through a fixed array in the library's device
- * memory instead and calls no device allocator (no cudaMalloc, cudaFree or
- * allocator hook).
- *  - Same arguments, field conversions and output layout as es_gather;
- *    1 <= n <= ES_GATHER_NOALLOC_MAX (4096), larger n returns ES_EINVAL.
+ * buffer on first use; callers that must not allocate device memory when
+ * they read values back -- a real-time loop that cannot wait on an
+ * allocator, or an application that hands out all device memory up front --
+ * use this variant, which stages through a fixed array in the library's
+ * device memory instead and calls no device allocator (no cudaMalloc,
+ * cudaFree or allocator hook).
+ *  - Same arguments, checks, field conversions and output layout as
+ *    es_gather; 1 <= n <= ES_GATHER_NOALLOC_MAX (4096), larger n returns
+ *    ES_EINVAL.
+ *  - The context's device must be the current device (ES_EINVAL otherwise).
  *  - The array (640 KiB) is held by every GPU that loads the library until
  *    the process exits.  The first call on a device looks up the array's
- *    address on that device (with the device current); make that first call
- *    before any stream capture.
+ *    address on that device; make that first call before any stream
+ *    capture.
  *  - All calls share the array and it keeps the last call's contents; no
  *    part of it needs to start at zero.  Calls whose GPU work overlaps (two
  *    streams or two host threads at once) race on it: serialise them.
- *  - Synchronises the context's stream.                                    */
+ *  - Copies the indices from the caller's (pageable) host array and
+ *    synchronises the context's stream, like es_gather.                    */
 #define ES_GATHER_NOALLOC_MAX 4096
 int es_gather_noalloc(es_ctx* ctx, int which, const int64_t* idx, int n, double* out);
 

@@ -80,6 +80,8 @@ class Params(ctypes.Structure):
         ("wall_slip", ctypes.c_int * 6),
         ("phi_t", ctypes.c_double),
         ("fine_layout", ctypes.c_int),
+        ("near_list_cells", ctypes.c_int),
+        ("fast_update_cells", ctypes.c_int),
     ]
 
 

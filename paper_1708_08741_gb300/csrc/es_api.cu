@@ -73,6 +73,8 @@ int validate(const es_params* P, const es_particle* parts, int n, std::string& w
     if (!(P->phi_t >= 0.0) || std::isinf(P->phi_t)) return why = "phi_t must be finite and >= 0", ES_EINVAL;
     if (P->fine_layout != ES_LAYOUT_AUTO && P->fine_layout != ES_LAYOUT_NATURAL)
         return why = "fine_layout must be ES_LAYOUT_AUTO or ES_LAYOUT_NATURAL", ES_EINVAL;
+    if (P->near_list_cells < 0 || P->fast_update_cells < 0)
+        return why = "near_list_cells and fast_update_cells must be >= 0", ES_EINVAL;
     if (P->phi_t > 0.0 && (P->precision != ES_FP64 || P->levels != 1))
         return why = "the nonlinear Poisson-Boltzmann form (phi_t > 0) needs ES_FP64 and levels == 1", ES_EINVAL;
     for (int p = 0; p < n; p++) {
@@ -115,6 +117,12 @@ DParticle to_device(const es_params& P, const es_particle& s, double sigma) {
 // does not sit at one power-of-two offset apart (DRAM partition camping).
 long long pdf_stride(long long N) { return ((N + 31) / 32) * 32 + 1120; }
 
+// The finest level's e and rhs are stored colour-split (see es.h, fine_layout).
+bool colour_split(const es_params* P) {
+    return P->precision != ES_FP64 && P->dims[0] % 8 == 0 && P->smoother == ES_SMOOTH_TWO_PASS &&
+           P->mg_storage == ES_MG_NATIVE && P->levels >= 2 && P->fine_layout == ES_LAYOUT_AUTO;
+}
+
 size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     long long N = (long long)P->dims[0] * P->dims[1] * P->dims[2];
     const size_t s = P->precision == ES_FP64 ? 8 : 4;  // arithmetic type
@@ -124,6 +132,8 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     b += N * 8;           // psi: FP64, or float-float high and low parts
     b += N * 4 + N;       // owner, flags
     b += N * 4;           // list of fluid cells next to obstacles (body force)
+    if (colour_split(P))  // per-colour update masks of the finest level
+        b += (size_t)2 * P->dims[1] * P->dims[2] * ((P->dims[0] + 63) / 64) * 4;
     size_t lv = 0;
     for (int l = 0; l < P->levels; l++) {
         long long Nl = (long long)(P->dims[0] >> l) * (P->dims[1] >> l) * (P->dims[2] >> l);
@@ -232,6 +242,22 @@ ProfScope::~ProfScope() {
     if (rec_ >= 0) cudaEventRecord(c_->prof_recs[rec_].b, c_->stream);
 }
 
+int field_components(int which) {
+    if (which == ES_FIELD_PDF || which == ES_FIELD_PDF_LAST) return 19;
+    if (which == ES_FIELD_U || which == ES_FIELD_FB) return 3;
+    return 1;
+}
+
+int check_gather_args(es_ctx* c, int which, const int64_t* idx, int n, int max_n, const double* out) {
+    if (!c || !idx || !out) return fail(c, ES_EINVAL, "NULL argument");
+    if (n < 1 || n > max_n) return fail(c, ES_EINVAL, "n must be in 1.." + std::to_string(max_n));
+    if (which < ES_FIELD_PSI || which > ES_FIELD_PDF_LAST) return fail(c, ES_EINVAL, "unknown field");
+    if (which == ES_FIELD_PDF_LAST && c->last_src < 0) return fail(c, ES_EINVAL, "no LBM step yet");
+    for (int i = 0; i < n; i++)
+        if (idx[i] < 0 || idx[i] >= c->g.N) return fail(c, ES_EINVAL, "cell index out of range");
+    return ES_OK;
+}
+
 }  // namespace es
 
 extern "C" {
@@ -256,9 +282,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->g.ny = params->dims[1];
     c->g.nz = params->dims[2];
     for (int a = 0; a < 3; a++) c->g.per[a] = params->periodic[a] ? 1 : 0;
-    c->rb0 = (params->precision != ES_FP64) && params->dims[0] % 8 == 0 &&
-             params->smoother == ES_SMOOTH_TWO_PASS && params->mg_storage == ES_MG_NATIVE && params->levels >= 2 &&
-             params->fine_layout == ES_LAYOUT_AUTO;
+    c->rb0 = colour_split(params);
     c->slip = 0;
     for (int f = 0; f < 6; f++)
         if (!c->g.per[f / 2] && params->wall_slip[f]) c->slip |= 1 << f;
@@ -286,6 +310,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
             nsm = 152;
         }
         c->n_sm = nsm;
+        c->device = dev;
     }
     c->red_blocks = 4 * c->n_sm;
     c->mg_rate = 0.15;
@@ -341,6 +366,8 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
         c->bf_count = (int*)A(kNearSegs * 4);
     }
     c->d_status = (int*)A(64);
+    c->rb_wpr = (c->g.nx + 63) / 64;
+    c->rbmask = c->rb0 ? (uint32_t*)A((size_t)2 * c->g.ny * c->g.nz * c->rb_wpr * 4) : nullptr;
     if (!ok) {
         release(c);
         delete c;
@@ -426,8 +453,10 @@ constexpr double kCycleTarget = 0.85;
 constexpr double kFastUpdate = 5000.0;
 // (on small grids the float-float residual costs about a launch and the
 // update's occasional second norm read costs a host round trip: the update
-// is used from 2^21 cells on)
-constexpr long long kFastUpdateCells = 1LL << 21;
+// is used from fast_update_cells cells on, default 2^21)
+long long fast_update_cells(const es_ctx* c) {
+    return c->P.fast_update_cells > 0 ? (long long)c->P.fast_update_cells : (long long)ES_FAST_UPDATE_CELLS;
+}
 
 int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
     if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
@@ -483,7 +512,7 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
         }
         for (int j = 0; j < k; j++) ES_CUDA(c, launch_vcycle(c, j > 0));
         const double before = norm;
-        if (c->rb0 && forced_cycles < 0 && c->g.N >= kFastUpdateCells && norm <= kFastUpdate * c->tol) {
+        if (c->rb0 && forced_cycles < 0 && c->g.N >= fast_update_cells(c) && norm <= kFastUpdate * c->tol) {
             // near the tolerance: psi += e, then r -= A e (FP32 update, error
             // ~1e-6 of the residual before the correction); the float-float
             // residual is formed again only if the updated one is not yet
@@ -607,19 +636,14 @@ int es_get_field(es_ctx* c, int which, void* dst, size_t bytes, int on_device) {
 }
 
 int es_gather(es_ctx* c, int which, const int64_t* idx, int n, double* out) {
-    if (!c || !idx || !out) return fail(c, ES_EINVAL, "NULL argument");
-    if (n < 1 || n > 65536) return fail(c, ES_EINVAL, "n must be in 1..65536");
-    if (field_size(c, which) == 0) return fail(c, ES_EINVAL, "unknown field");
-    if (which == ES_FIELD_PDF_LAST && c->last_src < 0) return fail(c, ES_EINVAL, "no LBM step yet");
-    for (int i = 0; i < n; i++)
-        if (idx[i] < 0 || idx[i] >= c->g.N) return fail(c, ES_EINVAL, "cell index out of range");
+    const int rc = check_gather_args(c, which, idx, n, 65536, out);
+    if (rc != ES_OK) return rc;
     const size_t kmax = 65536;
     if (!c->gather) c->gather = dev_alloc(c, kmax * 8 + 19 * kmax * 8);
     if (!c->gather) return fail(c, ES_ENOMEM, "gather scratch allocation failed");
     long long* didx = (long long*)c->gather;
     double* dout = (double*)((char*)c->gather + kmax * 8);
-    int comps = (which == ES_FIELD_PDF || which == ES_FIELD_PDF_LAST) ? 19
-                : (which == ES_FIELD_U || which == ES_FIELD_FB) ? 3 : 1;
+    const int comps = field_components(which);
     ES_CUDA(c, cudaMemcpyAsync(didx, idx, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
     ES_CUDA(c, launch_gather(c, which, didx, n, dout));
     ES_CUDA(c, cudaMemcpyAsync(out, dout, (size_t)comps * n * 8, cudaMemcpyDeviceToHost, c->stream));

@@ -117,9 +117,13 @@ struct es_ctx {
     int* near_list[ES_MAXLEV];  // near-boundary unknown cells per level: red segments, then black ones
     int near_cap[ES_MAXLEV];    // capacity of one segment
     int* near_count;            // device: 2 kNearSegs counts per level (red segments, then black)
+    uint32_t* rbmask;           // colour-split finest level: per colour, one bit per cell (compact order,
+                                // each row padded to rb_wpr words): 1 = interior unknown cell
+    int rb_wpr;                 // mask words per row: ceil(nx / 64)
     int* bf_list;               // fluid cells with a non-fluid D3Q19 neighbour (level 0), kNearSegs segments
     int bf_cap;                 // capacity of one segment
     int* bf_count;              // device: kNearSegs counts
+    int device;             // the CUDA device current at creation (the context's device)
     int n_sm;               // multiprocessors of the device
     int rb_blocks[2];       // resident fused-sweep blocks per SM (float, double); 0 = not queried
     double* partial;
@@ -190,6 +194,12 @@ cudaError_t launch_get_moments(es_ctx* c, double* rho, double* u);
 cudaError_t launch_set_fb(es_ctx* c, const double* src);
 cudaError_t launch_get_fb(es_ctx* c, double* dst);
 cudaError_t launch_gather(es_ctx* c, int which, const long long* idx, int n, double* out);
+
+// Argument checks shared by es_gather and es_gather_noalloc (host only, no
+// device work): ES_OK, or ES_EINVAL with the reason in c->err.
+int check_gather_args(es_ctx* c, int which, const int64_t* idx, int n, int max_n, const double* out);
+// Values per cell of a field (19 for the PDFs, 3 for U and FB, else 1).
+int field_components(int which);
 
 // The reduced-precision forms (FP32 arithmetic, float-float psi): MIXED32
 // and MIXED16, which differ only in how the PDFs are stored.

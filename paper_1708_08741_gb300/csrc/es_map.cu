@@ -555,9 +555,13 @@ __device__ __forceinline__ int warp_excl_scan(int v, int& total) {
     return incl - v;
 }
 
+// With rbmask (the colour-split finest level), also the per-colour update
+// masks of the half sweeps: bit j of colour k's row (wpr words, compact
+// index j = x / 2) is set iff that cell is an interior unknown cell.
 __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const uint8_t* __restrict__ st,
                                                   const uint8_t* __restrict__ flags, int cap, int* list,
-                                                  int* count, int bf_cap, int* bf_list, int* bf_count) {
+                                                  int* count, int bf_cap, int* bf_list, int* bf_count,
+                                                  uint32_t* __restrict__ rbmask, int wpr) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= ny * nz) return;  // whole warps
@@ -569,6 +573,25 @@ __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const 
         if (xs < nx) {
             sw = *reinterpret_cast<const unsigned*>(st + xs + nx * row);
             fw = *reinterpret_cast<const unsigned*>(flags + xs + nx * row);
+        }
+        if (rbmask) {
+            // lane's cells of colour k: xs + O and xs + 2 + O, O = (k + y + z) & 1,
+            // at compact places xs / 2 and xs / 2 + 1 (bits 2 lane, 2 lane + 1
+            // of this span's 64)
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int O = (k + y + z) & 1;
+                const unsigned s0 = (sw >> (8 * O)) & 0xFFu, s1 = (sw >> (8 * (2 + O))) & 0xFFu;
+                const unsigned v = (((s0 & (ST_KIND | ST_NEAR)) == ST_UNKNOWN) ? 1u : 0u) |
+                                   (((s1 & (ST_KIND | ST_NEAR)) == ST_UNKNOWN) ? 2u : 0u);
+                const unsigned sh = (xs < nx ? v : 0u) << ((2 * lane) & 31);
+                const unsigned lo = __reduce_or_sync(0xffffffffu, lane < 16 ? sh : 0u);
+                const unsigned hi = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : sh);
+                const int w0 = x0 / 64;  // (x0 is a multiple of 128)
+                uint32_t* m = rbmask + (size_t)k * ((size_t)ny * nz * wpr) + (size_t)wpr * row;
+                if (lane == 0) m[w0] = lo;
+                if (lane == 16 && w0 + 1 < wpr) m[w0 + 1] = hi;
+            }
         }
         unsigned m_near[2] = {0, 0}, m_bf = 0;
 #pragma unroll
@@ -614,7 +637,8 @@ cudaError_t launch_near_lists(es_ctx* c) {
         ProfScope ps(c, "cell_lists", 0, 2.0 * (double)c->g.N);
         k_lists_l0<<<(c->g.ny * c->g.nz + 7) / 8, 256, 0, c->stream>>>(c->g.nx, c->g.ny, c->g.nz, c->st[0], c->flags,
                                                                       c->near_cap[0], c->near_list[0], c->near_count,
-                                                                      c->bf_cap, c->bf_list, c->bf_count);
+                                                                      c->bf_cap, c->bf_list, c->bf_count,
+                                                                      c->rbmask, c->rb_wpr);
         count(c);
         l0 = 1;
     }

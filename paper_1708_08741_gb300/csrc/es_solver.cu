@@ -828,12 +828,10 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
 template <class T, int O>
 __device__ __forceinline__ void rb_span_update(T inv_diag0, T h2, T (&c)[4], const T (&ox)[6], const T (&a)[4],
                                                const T (&b)[4], const T (&d)[4], const T (&f)[4],
-                                               const T (&r)[4], uint2 sw, int first, T omega) {
+                                               const T (&r)[4], unsigned upd, int first, T omega) {
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        const int bit = 2 * k + O;  // natural position in the 8-cell state span
-        const unsigned sv = ((bit < 4 ? sw.x : sw.y) >> (8 * (bit & 3))) & 0xFFu;
-        if ((sv & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;  // (c[k] is 0 when first)
+        if (!((upd >> k) & 1u)) continue;  // not an interior unknown cell (c[k] is 0 when first)
         T o = ox[k + O];
         o += ox[k + 1 + O];
         o += a[k];
@@ -845,28 +843,67 @@ __device__ __forceinline__ void rb_span_update(T inv_diag0, T h2, T (&c)[4], con
     }
 }
 
+// The near-boundary cells of the colour-split finest level, by colour: the
+// level's near-cell list and the state bytes their stencils need, and how
+// many leading z planes of blocks of a half sweep's grid work on them.
+struct NearWork {
+    const uint8_t* st;
+    const int* list;
+    const int* count;
+    int cap;
+    int planes;
+};
+
 // One red (colour 0) or black (1) half sweep of the finest level in the
-// colour-split layout (reduced forms, nx % 8 == 0): a thread owns 4
-// consecutive cells of the colour in one row (8 natural cells), loads them,
-// the other colour at the same compact places of its own row (plus one
-// halo value) and of the four neighbour rows, and its right-hand side, as
-// 16-byte vectors, and writes back only its own colour.  Per cell and half
-// sweep that moves e of both colours once, rhs and e of the colour
-// once and the state bytes: 9 bytes instead of the 13 of the interleaved
-// layout, whose spans also stream the other colour's e and rhs.  Same
-// per-cell arithmetic as k_smooth_v; near-boundary cells are left to
-// k_smooth_near.  first: 1 the iterate starts at zero (nothing is read;
-// the colour's cells that are not updated are written as zero), 2 the
-// colour's old values are zero (the second colour of a sweep from zero; its
-// other cells are written as zero too), so the other colour never needs
-// clearing.
+// colour-split layout (reduced forms, nx % 8 == 0), interior and
+// near-boundary cells in one launch.  The two sets are disjoint and both
+// read only the other colour, so they need no order:
+//  * the first nw.planes z planes of blocks update the colour's
+//    near-boundary cells from the near-cell list (Gauss-Seidel values with
+//    the boundary faces of Sec. 5.4, as k_smooth_near); scheduled first,
+//    their scattered, latency-bound loads overlap the streaming blocks;
+//  * in the other blocks a thread owns 4 consecutive cells of the colour in
+//    one row (8 natural cells), loads the other colour at the same compact
+//    places of its own row (plus one halo value) and of the four neighbour
+//    rows, and its right-hand side, as 16-byte vectors, and stores the
+//    cells it updates.  Which cells those are (the interior unknown cells)
+//    it reads from the colour's bit mask (one bit per cell, rows padded to
+//    whole 32-bit words), not from the state bytes.  A Gauss-Seidel update
+//    (omega = 1) does not need the cell's old value, so the colour's own e
+//    is read only for omega != 1.
+// Per cell and half sweep the interior moves the other colour's e in, the
+// colour's e out and its rhs in: 6 bytes, plus 1/16 byte of mask (against 9
+// with the state bytes and the colour's old values, and 13 in the
+// interleaved layout).  Cells that are not unknown are never written: no
+// kernel reads e there.  Same per-cell arithmetic as k_smooth_v.  first: 1
+// the iterate starts at zero (nothing is read), 2 the colour's old values
+// are zero (the second colour of a sweep from zero).
 template <class T>
-__global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
-                                                   const T* __restrict__ rhs, T* __restrict__ e, int colour,
-                                                   int first, T omega, int half) {
+__global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, const uint32_t* __restrict__ mask,
+                                                   int wpr, const T* __restrict__ rhs, T* __restrict__ e,
+                                                   int colour, int first, T omega, int half, NearWork nw) {
+    if ((int)blockIdx.z < nw.planes) {
+        // block b of the near part serves segment b % kNearSegs of the colour
+        const int nblk = nw.planes * (int)(gridDim.x * gridDim.y);
+        const int b = ((int)blockIdx.z * (int)gridDim.y + (int)blockIdx.y) * (int)gridDim.x + (int)blockIdx.x;
+        const int seg = b % kNearSegs, sb = b / kNearSegs;
+        const int nsb = (nblk - seg + kNearSegs - 1) / kNearSegs;  // blocks on this segment
+        const int k = colour * kNearSegs + seg;
+        const int n = nw.count[k];
+        const int* list = nw.list + (size_t)k * nw.cap;
+        const RbMap rb{half};
+        const EAcc<T, T> A{(T)1, (T)1};
+        for (int i = sb * 256 + (int)(threadIdx.y * 32 + threadIdx.x); i < n; i += nsb * 256) {
+            const int cc = list[i];
+            const int x = cc % L.nx, yz = cc / L.nx;
+            const int y = yz % L.ny, z = yz / L.ny;
+            e[rb(cc, colour)] = near_gs<T, T, RbMap>(L, nw.st, rhs, e, x, y, z, first, omega, A, rb);
+        }
+        return;
+    }
     const int nxh = L.nx >> 1;
     const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
-    const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y * 8 + threadIdx.y, z = (int)blockIdx.z - nw.planes;
     if (y >= L.ny) return;
     const bool lane_on = i0 < nxh;
     const int iq = lane_on ? i0 : 0;  // (inactive lanes read a valid span)
@@ -884,6 +921,11 @@ __global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, cons
     if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
     if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
     const int rowh = nxh * (y + ny * z);
+    // the colour's update bits of this span (4 bits of one mask word)
+    const unsigned upd = (mask[(size_t)colour * ((size_t)ny * nz * wpr) + (size_t)wpr * (y + ny * z) + (iq >> 5)] >>
+                          (iq & 31)) & 0xFu;
+    if (!lane_on || upd == 0u) return;
+    const bool gs = omega == (T)1;
     T c[4], ox[6], a[4], b[4], d[4], f[4], r[4];
     if (first == 1) {
 #pragma unroll
@@ -891,9 +933,9 @@ __global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, cons
 #pragma unroll
         for (int k = 0; k < 6; k++) ox[k] = (T)0;
     } else {
-        if (first == 2) {
+        if (first == 2 || gs) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) c[k] = (T)0;
+            for (int k = 0; k < 4; k++) c[k] = (T)0;  // (gs: not read, never used)
         } else {
             ES_VLD(c, 0, es + rowh + iq);
         }
@@ -906,12 +948,18 @@ __global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, cons
         ES_VLD(f, 0, eo + nxh * (y + ny * zp) + iq);
     }
     ES_VLD(r, 0, rhs + colour * half + rowh + iq);
-    const uint2 sw = *reinterpret_cast<const uint2*>(st + L.nx * (y + ny * z) + 2 * iq);
     if (O == 0)
-        rb_span_update<T, 0>(inv_diag0, L.h2, c, ox, a, b, d, f, r, sw, first == 1, omega);
+        rb_span_update<T, 0>(inv_diag0, L.h2, c, ox, a, b, d, f, r, upd, first == 1, omega);
     else
-        rb_span_update<T, 1>(inv_diag0, L.h2, c, ox, a, b, d, f, r, sw, first == 1, omega);
-    if (lane_on) vst(es + rowh + i0, c[0], c[1], c[2], c[3]);
+        rb_span_update<T, 1>(inv_diag0, L.h2, c, ox, a, b, d, f, r, upd, first == 1, omega);
+    if (upd == 0xFu) {
+        vst(es + rowh + i0, c[0], c[1], c[2], c[3]);
+    } else {
+        // (the colour's near-boundary cells belong to the near blocks)
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if ((upd >> k) & 1u) es[rowh + i0 + k] = c[k];
+    }
 }
 
 __device__ __forceinline__ bool axis_ok(int v, int n, int per, int& w) {
@@ -2071,9 +2119,12 @@ size_t coarse_smem_bytes(const es_ctx* c, size_t tsize) {
     return n * (2 * tsize + 1);
 }
 
-// Levels up to this many cells update their near-boundary cells inside the
-// smoothing kernel; larger ones in a separate pass over the near-cell list.
-constexpr int kInlineNearCells = 1 << 21;
+// Levels up to this many cells (near_list_cells, default 2^21) update their
+// near-boundary cells inside the smoothing kernel; larger ones in a separate
+// pass over the near-cell list.
+long long inline_near_cells(const es_ctx* c) {
+    return c->P.near_list_cells > 0 ? (long long)c->P.near_list_cells : (long long)ES_NEAR_LIST_CELLS;
+}
 
 // Launch shape of the fused sweep: 128 x 12 output tiles, and the z extent
 // cut into chunks so that the blocks fill whole waves of the resident-block
@@ -2182,28 +2233,34 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             if (split) {
                 // colour-split finest level: interior pass, then the colour's
                 // near-boundary cells from the list
-                const dim3 sgrd((L.nx / 8 + 31) / 32, (L.ny + 7) / 8, L.nz);
-                const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, kNearSegs);
+                // leading z planes of near-cell blocks: at least one block per
+                // list segment, about two per SM
+                const int gx = (L.nx / 8 + 31) / 32, gy = (L.ny + 7) / 8;
+                const int want = 2 * c->n_sm > kNearSegs ? 2 * c->n_sm : kNearSegs;
+                const int near_planes = (want + gx * gy - 1) / (gx * gy);
+                const dim3 sgrd(gx, gy, L.nz + near_planes);
                 const int* cnt = c->near_count + 2 * kNearSegs * l;
-                const size_t hl = (size_t)kNearSegs * c->near_cap[l];
+                // per cell: the other colour's e in, the colour's e out, its
+                // rhs in (from zero: rhs in, e out), the mask bits; the
+                // colour's old e in as well unless omega = 1 (the
+                // near-boundary cells' scattered loads are not counted)
+                const double own = c->P.omega == 1.0 ? 0.0 : 0.5 * es;
+                const double b_rb_first = nl * (0.5 * es + 0.5 * ts + 0.0625);
+                const double b_rb_half = nl * (1.0 * es + own + 0.5 * ts + 0.0625);
+                const NearWork nw{st, c->near_list[l], cnt, c->near_cap[l], near_planes};
                 for (int col = 0; col < 2; col++) {
                     const int fs = first ? (col == 0 ? 1 : 2) : 0;
-                    {
-                        ProfScope ps(c, "smooth_half", l, col == 0 && first ? b_first : b_half);
-                        k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, col, fs, omega,
-                                                                     rb.half);
-                    }
-                    ProfScope ps(c, "smooth_near", l, 0.0);
-                    k_smooth_near<T, E, RbMap><<<ngrd, 256, 0, c->stream>>>(
-                        L, st, rhs, e, c->near_list[l] + col * hl, cnt + col * kNearSegs, c->near_cap[l], fs, omega,
-                        A, rb);
+                    ProfScope ps(c, "smooth_half", l,
+                                 !first ? b_rb_half : (col == 0 ? b_rb_first : b_rb_half - nl * own));
+                    k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, c->rbmask, c->rb_wpr, rhs, e, col,
+                                                                 fs, omega, rb.half, nw);
                 }
-                count(c, 4);
+                count(c, 2);
                 return;
             }
         }
         if (vec) {
-            if (Nl <= kInlineNearCells) {
+            if (Nl <= inline_near_cells(c)) {
                 {
                     ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
                     k_smooth_v<T, W, true, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first,

@@ -40,6 +40,8 @@ class Pair:
         self.wl = wl
         self.o = oracle.Oracle(wl, overrides)
         self.g = es.Simulation(wl, precision, overrides={**(overrides or {}), **(lib_overrides or {})})
+        self.x0 = np.array(wl.x, dtype=np.float64).reshape(-1, 3).copy()
+        self.last_forces = None
 
     def step(self, forced=True):
         self.o.map_particles()
@@ -53,11 +55,30 @@ class Pair:
         Fg, Tg = self.g.forces()
         self.o.advance()
         self.g.advance()
+        self.last_forces = ((Fo, To), (Fg, Tg))
         return info, ginfo, (Fo, To), (Fg, Tg)
+
+    def displacement(self, x):
+        """x - x0 per sphere, by minimum image on periodic axes (a sphere
+        that crossed a periodic face is wrapped back into the box)."""
+        d = np.asarray(x, dtype=np.float64) - self.x0
+        for a in range(3):
+            if self.wl.periodic[a]:
+                n = float(self.wl.dims[a])
+                d[:, a] -= n * np.round(d[:, a] / n)
+        return d
 
     def compare(self):
         """Relative L2 differences of potential (unknown cells), velocity
-        (fluid cells) and particle state, plus owner equality."""
+        (fluid cells) and particle state, plus owner equality.
+
+        x: the absolute positions; "disp": the displacements since the start
+        (x - x0, minimum image), the quantity the forces actually move and
+        the one a reduced-precision bar must be set on (absolute coordinates
+        of 16 to 60 cells hide errors of a few thousandths of a cell).
+        F, T: the force and torque of the last step (Pair.step).  A torque
+        that vanishes by symmetry (a centred sphere in an axial field) is
+        measured against R times the force instead of its own norm."""
         own_o = self.o.owner()
         own_g = self.g.field(es.FIELD_OWNER)
         fluid = own_o < 0
@@ -69,6 +90,14 @@ class Pair:
         if self.wl.n_particles:
             pg, po = self.g.particles(), self.o.particles()
             res["x"] = rel_l2(pg["x"], po["x"])
+            res["disp"] = rel_l2(self.displacement(pg["x"]), self.displacement(po["x"]))
             res["v"] = rel_l2(pg["v"], po["v"]) if np.linalg.norm(po["v"]) > 0 else 0.0
             res["w"] = np.linalg.norm(pg["w"] - po["w"]) / max(np.linalg.norm(po["w"]), 1e-300)
+            if self.last_forces is not None:
+                (Fo, To), (Fg, Tg) = self.last_forces
+                res["F"] = rel_l2(Fg, Fo)
+                arm = float(np.mean(self.wl.R)) * np.linalg.norm(Fo)
+                nT = np.linalg.norm(To)
+                res["T"] = float(np.linalg.norm(np.asarray(Tg) - np.asarray(To)) /
+                                 (nT if nT > 1e-6 * arm else max(arm, 1e-300)))
         return res

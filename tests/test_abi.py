@@ -69,6 +69,8 @@ def _create_rc(lib, wl, **over):
     (dict(phi_t=-1.0), "phi_t"),
     (dict(phi_t=0.5, levels=2), "levels == 1"),
     (dict(fine_layout=2), "fine_layout"),
+    (dict(near_list_cells=-1), "near_list_cells"),
+    (dict(fast_update_cells=-5), "fast_update_cells"),
 ])
 def test_invalid_parameters_rejected_before_any_gpu_call(lib, over, needle):
     rc, msg = _create_rc(lib, W.single_sphere(), **over)
@@ -95,12 +97,14 @@ def test_device_bytes_matches_layout(lib):
     # body force (3s), psi (8: FP64 or float-float), owner and flags (5), the
     # list of fluid cells next to obstacles (4) and, per multigrid cell (x 8/7
     # levels), three s-byte fields, a state byte and a 4-byte near-cell list
-    # entry, with s the arithmetic type (4 in both reduced forms)
-    rest32 = (3 * 4 + 8 + 5 + 4 + (3 * 4 + 1 + 4) * 8 / 7) * N
+    # entry, with s the arithmetic type (4 in both reduced forms); the reduced
+    # forms' colour-split finest level adds its update masks (1/8 byte a cell)
+    rest32 = (3 * 4 + 8 + 5 + 4 + (3 * 4 + 1 + 4) * 8 / 7 + 0.125) * N
     rest64 = (3 * 8 + 8 + 5 + 4 + (3 * 8 + 1 + 4) * 8 / 7) * N
     assert 2 * 19 * 2 * N + rest32 < b16 < 2 * 19 * 2 * N + rest32 + 0.1 * N
     assert 2 * 19 * 4 * N + rest32 < b32 < 2 * 19 * 4 * N + rest32 + 0.1 * N
     assert 2 * 19 * 8 * N + rest64 < b64 < 2 * 19 * 8 * N + rest64 + 0.1 * N
     # FP16 storage of the finest level's correction: 2 bytes a cell less
     b32h = es.device_bytes(wl, es.ES_MIXED32, dict(mg_storage=es.ES_MG_FP16))
-    assert b32 - b32h == 2 * N
+    # (and the colour-split layout, with its masks, is off under FP16 storage)
+    assert b32 - b32h == 2 * N + 2 * 512 * 512 * (512 // 64) * 4

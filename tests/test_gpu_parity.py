@@ -15,6 +15,18 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-4
+# the quantities every reduced-precision comparison bars: potential (unknown
+# cells), velocity (fluid cells), particle displacement, velocity, force and
+# torque of the last step
+REDUCED_KEYS = ("psi", "u", "disp", "v", "F", "T")
+
+
+def _assert_reduced(r, bars=None):
+    """Every quantity below MIXED_TOL, or below its entry in bars."""
+    print("relative L2 against the oracle:", {k: float(r.get(k)) for k in REDUCED_KEYS})
+    assert r["owner_equal"]
+    for k in REDUCED_KEYS:
+        assert r[k] < (bars or {}).get(k, MIXED_TOL), (k, r[k])
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -114,6 +126,80 @@ def test_fused_smoother(name):
         ig = p.g.solve(forced_cycles=k)
         assert abs(ig["r0"] - io["r0"]) <= 1e-12 * io["r0"]
         assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < FP64_TOL
+
+
+# The solver paths the 512^3 workload takes but small grids do not: levels
+# above near_list_cells (default 2^21) smooth their near-boundary cells in
+# separate list passes, and grids from fast_update_cells (default 2^21) on
+# update the residual after a correction in FP32.  Setting both thresholds to
+# one cell forces those paths on 64^3 grids the oracle runs in seconds.
+BENCH_PATHS = dict(near_list_cells=1, fast_update_cells=1)
+LIST_CASES = {
+    "channel64": lambda: _moving(W.channel(n=64, n_spheres=8, radius=5.0, levels=4)),
+    "suspension64": lambda: _moving(W.suspension_sample(64, levels=4)),
+}
+
+
+def _profiled_names(g, steps):
+    """Kernel records (name, level) -> launches over `steps` coupled steps."""
+    g.profile_start()
+    for _ in range(steps):
+        g.step()
+    return {(r["name"], r["level"]): r["launches"] for r in g.profile_stop()}
+
+
+@pytest.mark.parametrize("name", sorted(LIST_CASES))
+def test_list_passes_fp64_forced_cycles(name):
+    """FP64 with every level but the coarsest on the list-driven near passes
+    (k_smooth_v without inline near cells + k_smooth_near): forced V-cycles
+    against the oracle at 1e-12, then 10 coupled steps."""
+    wl = LIST_CASES[name]()
+    p = Pair(wl, lib_overrides=BENCH_PATHS)
+    p.o.map_particles()
+    p.g.map_particles()
+    fluid = p.o.owner() < 0
+    for k in (0, 1, 2, 3):
+        io = p.o.solve(forced_cycles=1 if k else 0)
+        ig = p.g.solve(forced_cycles=1 if k else 0)
+        assert abs(ig["r0"] - io["r0"]) <= 1e-12 * io["r0"]
+        assert rel_l2(p.g.field(es.FIELD_PSI)[fluid], p.o.field(oracle.FIELD_PSI)[fluid]) < FP64_TOL
+    p.o.body_force()
+    p.o.lbm_step()
+    p.g.lbm_step()
+    p.o.forces()
+    p.g.forces()
+    p.o.advance()
+    p.g.advance()
+    for _ in range(10):
+        info, ginfo, _, _ = p.step()
+        assert ginfo["cycles"] == info["cycles"]
+    r = p.compare()
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x", "v", "w"):
+        assert r[k] < FP64_TOL, (k, r[k])
+    # the list passes did run on the levels between the finest and the coarsest
+    seen = _profiled_names(p.g, 2)
+    assert all(seen.get(("smooth_near", l), 0) > 0 for l in range(wl.levels - 1))
+
+
+@pytest.mark.parametrize("name", sorted(LIST_CASES))
+def test_bench_solver_paths_mixed32_after_100_steps(name):
+    """MIXED32 with the near-cell list passes on every level and the FP32
+    residual update (r - A e after a correction near the tolerance) on: the
+    paths of the 512^3 workload, at 64^3, tolerance-driven on both sides,
+    against the oracle after 100 steps at 1e-4."""
+    wl = LIST_CASES[name]()
+    p = Pair(wl, es.ES_MIXED32, lib_overrides=BENCH_PATHS)
+    for _ in range(100):
+        _, ginfo, _, _ = p.step(forced=False)
+        assert ginfo["status"] == es.ES_OK and ginfo["r"] < ginfo["tol"]
+    _assert_reduced(p.compare())
+    seen = _profiled_names(p.g, 6)
+    # (the colour-split finest level updates its near-boundary cells inside
+    # the half-sweep launches; the levels below it in separate list passes)
+    assert all(seen.get(("smooth_near", l), 0) > 0 for l in range(1, wl.levels - 1))
+    updates = seen.get(("residual_update", -1), 0)
+    assert updates > 0, "the FP32 residual update never ran"
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -221,9 +307,7 @@ def test_coupled_free_slip_walls_fp64(name):
 def test_free_slip_reduced_precision_after_100_steps(precision):
     wl = _slip(W.channel(n=64, n_spheres=8, radius=5.0, levels=4), (0, 0, 0, 0, 1, 1))
     p, r = _coupled(wl, 100, precision=precision, forced=False)
-    assert r["owner_equal"]
-    assert r["psi"] < MIXED_TOL and r["x"] < MIXED_TOL
-    assert r["u"] < (MIXED_TOL if precision == es.ES_MIXED32 else MIXED16_U_TOL)
+    _assert_reduced(r, None if precision == es.ES_MIXED32 else MIXED16_BARS)
 
 
 def _pb(wl, phi_t, sweeps=2, omega=1.5):
@@ -257,9 +341,7 @@ def test_mixed32_within_1e4_after_100_steps(maker):
     particles) against the FP64 oracle after 100 steps, each side on its own
     tolerance-driven solver."""
     p, r = _coupled(maker(), 100, precision=es.ES_MIXED32, forced=False)
-    assert r["owner_equal"]
-    for k in ("psi", "u", "x"):
-        assert r[k] < MIXED_TOL, (k, r[k])
+    _assert_reduced(r)
 
 
 @pytest.mark.parametrize("name", ["single_sphere", "mixed_ragged", "walls_x42"])
@@ -297,10 +379,7 @@ def test_mg_fp16_within_1e4_after_100_steps(maker):
     for _ in range(100):
         _, ginfo, _, _ = p.step(forced=False)
         assert ginfo["status"] == es.ES_OK and ginfo["r"] < ginfo["tol"]
-    r = p.compare()
-    assert r["owner_equal"]
-    for k in ("psi", "u", "x"):
-        assert r[k] < MIXED_TOL, (k, r[k])
+    _assert_reduced(p.compare())
 
 
 @pytest.mark.parametrize("name", ["single_sphere", "mixed_ragged"])
@@ -353,9 +432,17 @@ def test_mixed32_potential_round_trip():
 
 # MIXED16 keeps each population as an FP16 number (unit roundoff 2^-11) of
 # its scaled relative deviation: the stored state is re-rounded every step,
-# which leaves a relative error of order 1e-3 in the slow velocity field.
-# The potential and the particles see the PDFs only through the forces.
-MIXED16_U_TOL = 1e-2
+# which leaves a relative error of about 1.3e-4 in the slow velocity field
+# (measured, and flat from 100 to 1,000 steps), and the momentum exchange of
+# one step sums that rounding over every boundary link.  MIXED16 misses the
+# 1e-4 bar on the fluid velocity and on the force and torque of a single
+# step; the particles integrate the force noise out (displacement and
+# velocity stay within 1e-4), and the potential sees the PDFs only through
+# them.  Its bars here are about twice the largest errors measured on these
+# cases after 100 steps (u 6.2e-4 in the single-sphere box, F 6.3e-3 there,
+# T 2.7e-2 in the free-slip channel; displacement and particle velocity at
+# most 8.6e-5).
+MIXED16_BARS = {"u": 1.3e-3, "F": 1.3e-2, "T": 6e-2}
 
 
 @pytest.mark.parametrize("maker", [lambda: W.single_sphere(),
@@ -364,10 +451,7 @@ def test_mixed16_after_100_steps(maker):
     """FP16 relative-deviation PDF storage (FP32 collision, the MIXED32
     solver) against the FP64 oracle after 100 steps."""
     p, r = _coupled(maker(), 100, precision=es.ES_MIXED16, forced=False)
-    print("MIXED16 relative L2 after 100 steps:", {k: r[k] for k in ("psi", "u", "x")})
-    assert r["owner_equal"]
-    assert r["psi"] < MIXED_TOL and r["x"] < MIXED_TOL
-    assert r["u"] < MIXED16_U_TOL
+    _assert_reduced(r, MIXED16_BARS)
 
 
 @pytest.mark.parametrize("n", [16, 32])
