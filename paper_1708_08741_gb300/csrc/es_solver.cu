@@ -825,24 +825,6 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
 // (interior cells only; O: offset of the colour's cells in the row, x = 2i + O).
 // ox[j] holds the other colour at compact index i0 - 1 + j, so the x
 // neighbours of cell i0 + k are ox[k + O] (left) and ox[k + 1 + O] (right).
-template <class T, int O>
-__device__ __forceinline__ void rb_span_update(T inv_diag0, T h2, T (&c)[4], const T (&ox)[6], const T (&a)[4],
-                                               const T (&b)[4], const T (&d)[4], const T (&f)[4],
-                                               const T (&r)[4], unsigned upd, int first, T omega) {
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        if (!((upd >> k) & 1u)) continue;  // not an interior unknown cell (c[k] is 0 when first)
-        T o = ox[k + O];
-        o += ox[k + 1 + O];
-        o += a[k];
-        o += b[k];
-        o += d[k];
-        o += f[k];
-        const T gs = (h2 * r[k] + o) * inv_diag0;
-        c[k] = first ? omega * gs : ((T)1 - omega) * c[k] + omega * gs;
-    }
-}
-
 // The near-boundary cells of the colour-split finest level, by colour: the
 // level's near-cell list and the state bytes their stencils need, and how
 // many leading z planes of blocks of a half sweep's grid work on them.
@@ -854,6 +836,118 @@ struct NearWork {
     int planes;
 };
 
+// The interior unknown cells of one colour of the colour-split finest
+// level, for a 4-cell span of compact places iq .. iq+3 in row y and the
+// planes z0 .. z1-1 (see k_smooth_rb).  The other colour's rows of the
+// planes z-1, z and z+1 at row y roll through registers (the row z+1 of one
+// plane is the row z of the next and the row z-1 of the one after), so a
+// plane loads three new rows of e (z+1, y-1, y+1), one halo value, its
+// right-hand side and its mask word; the loads of plane z+1 are issued
+// before plane z is updated.  FIRST: 1 the iterate starts at zero (no e is
+// read), 2 the colour's old values are zero; GS: omega = 1 (the old value
+// is not needed).  A cell's update sums its neighbours in the order of
+// k_smooth_v's span_update (x left, x right, y-1, y+1, z-1, z+1), so both
+// finest-level layouts give the same bits.
+template <class T, int FIRST, bool GS>
+__device__ __forceinline__ void rb_march(const Level<T>& L, T inv_diag0, const uint32_t* __restrict__ mcol, int wpr,
+                                         const T* __restrict__ rcol, const T* __restrict__ eo, T* __restrict__ es,
+                                         int colour, T omega, int iq, int y, int z0, int z1) {
+    const int nxh = L.nx >> 1, ny = L.ny, nz = L.nz;
+    int ym, yp, il, ir;
+    if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
+    if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
+    if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
+    if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
+    const int msh = iq & 31, mw = iq >> 5;
+    auto zwrap = [&](int z) {
+        int w;
+        if (!wrap_axis(z, nz, L.per[2], w)) w = z < 0 ? 0 : nz - 1;  // (beyond a wall: any valid row)
+        return w;
+    };
+    // plane z's loads: rows (y, z+1), (y-1, z), (y+1, z), the halo of row
+    // (y, z), rhs and the mask word
+    T F[4], A[4], B[4], R[4], h = (T)0;
+    unsigned m = 0;
+    auto load = [&](int z, T (&f)[4], T (&a)[4], T (&b)[4], T (&r)[4], T& hv, unsigned& mv) {
+        const int rz = nxh * (y + ny * z);
+        mv = (mcol[(size_t)wpr * (y + ny * z) + mw] >> msh) & 0xFu;
+        ES_VLD(r, 0, rcol + rz + iq);
+        if constexpr (FIRST != 1) {
+            const int zp = zwrap(z + 1);
+            ES_VLD(f, 0, eo + nxh * (y + ny * zp) + iq);
+            ES_VLD(a, 0, eo + nxh * (ym + ny * z) + iq);
+            ES_VLD(b, 0, eo + nxh * (yp + ny * z) + iq);
+            hv = ((colour + y + z) & 1) == 0 ? eo[rz + il] : eo[rz + ir];
+        } else {
+            // (the iterate starts at zero: every neighbour is zero)
+#pragma unroll
+            for (int k = 0; k < 4; k++) f[k] = a[k] = b[k] = (T)0;
+            hv = (T)0;
+        }
+    };
+    T D[4] = {(T)0, (T)0, (T)0, (T)0}, X[4] = {(T)0, (T)0, (T)0, (T)0};
+    if constexpr (FIRST != 1) {
+        ES_VLD(D, 0, eo + nxh * (y + ny * zwrap(z0 - 1)) + iq);
+        ES_VLD(X, 0, eo + nxh * (y + ny * z0) + iq);
+    }
+    load(z0, F, A, B, R, h, m);
+    for (int z = z0; z < z1; z++) {
+        T nF[4], nA[4], nB[4], nR[4], nh = (T)0;
+        unsigned nm = 0;
+        if (z + 1 < z1) load(z + 1, nF, nA, nB, nR, nh, nm);
+        if (m) {
+            const int rz = nxh * (y + ny * z) + iq;
+            T C[4] = {(T)0, (T)0, (T)0, (T)0};
+            if constexpr (FIRST == 0 && !GS) ES_VLD(C, 0, es + rz);
+            const int O = (colour + y + z) & 1;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (!((m >> k) & 1u)) continue;
+                T left, right;
+                if (O == 0) {
+                    left = k == 0 ? h : X[k - 1];
+                    right = X[k];
+                } else {
+                    left = X[k];
+                    right = k == 3 ? h : X[k + 1];
+                }
+                T o = left;
+                o += right;
+                o += A[k];
+                o += B[k];
+                o += D[k];
+                o += F[k];
+                const T gs = (L.h2 * R[k] + o) * inv_diag0;
+                if constexpr (FIRST != 0)
+                    C[k] = omega * gs;
+                else if constexpr (GS)
+                    C[k] = gs;
+                else
+                    C[k] = ((T)1 - omega) * C[k] + omega * gs;
+            }
+            if (m == 0xFu) {
+                vst(es + rz, C[0], C[1], C[2], C[3]);
+            } else {
+                // (the colour's near-boundary cells belong to the near blocks)
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if ((m >> k) & 1u) es[rz + k] = C[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            D[k] = X[k];
+            X[k] = F[k];
+            F[k] = nF[k];
+            A[k] = nA[k];
+            B[k] = nB[k];
+            R[k] = nR[k];
+        }
+        h = nh;
+        m = nm;
+    }
+}
+
 // One red (colour 0) or black (1) half sweep of the finest level in the
 // colour-split layout (reduced forms, nx % 8 == 0), interior and
 // near-boundary cells in one launch.  The two sets are disjoint and both
@@ -862,15 +956,14 @@ struct NearWork {
 //    near-boundary cells from the near-cell list (Gauss-Seidel values with
 //    the boundary faces of Sec. 5.4, as k_smooth_near); scheduled first,
 //    their scattered, latency-bound loads overlap the streaming blocks;
-//  * in the other blocks a thread owns 4 consecutive cells of the colour in
-//    one row (8 natural cells), loads the other colour at the same compact
-//    places of its own row (plus one halo value) and of the four neighbour
-//    rows, and its right-hand side, as 16-byte vectors, and stores the
-//    cells it updates.  Which cells those are (the interior unknown cells)
-//    it reads from the colour's bit mask (one bit per cell, rows padded to
-//    whole 32-bit words), not from the state bytes.  A Gauss-Seidel update
-//    (omega = 1) does not need the cell's old value, so the colour's own e
-//    is read only for omega != 1.
+//  * in the other blocks a thread owns 4 consecutive compact places of the
+//    colour in one row (8 natural cells) and marches through zc planes
+//    (rb_march), loading the other colour's rows and its right-hand side
+//    as 16-byte vectors and storing the cells it updates.  Which cells
+//    those are (the interior unknown cells) it reads from the colour's bit
+//    mask (one bit per cell, rows padded to whole 32-bit words), not from
+//    the state bytes.  A Gauss-Seidel update (omega = 1) does not need the
+//    cell's old value, so the colour's own e is read only for omega != 1.
 // Per cell and half sweep the interior moves the other colour's e in, the
 // colour's e out and its rhs in: 6 bytes, plus 1/16 byte of mask (against 9
 // with the state bytes and the colour's old values, and 13 in the
@@ -881,7 +974,7 @@ struct NearWork {
 template <class T>
 __global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, const uint32_t* __restrict__ mask,
                                                    int wpr, const T* __restrict__ rhs, T* __restrict__ e,
-                                                   int colour, int first, T omega, int half, NearWork nw) {
+                                                   int colour, int first, T omega, int half, NearWork nw, int zc) {
     if ((int)blockIdx.z < nw.planes) {
         // block b of the near part serves segment b % kNearSegs of the colour
         const int nblk = nw.planes * (int)(gridDim.x * gridDim.y);
@@ -901,65 +994,23 @@ __global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, cons
         }
         return;
     }
-    const int nxh = L.nx >> 1;
     const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
-    const int y = blockIdx.y * 8 + threadIdx.y, z = (int)blockIdx.z - nw.planes;
-    if (y >= L.ny) return;
-    const bool lane_on = i0 < nxh;
-    const int iq = lane_on ? i0 : 0;  // (inactive lanes read a valid span)
-    const int ny = L.ny, nz = L.nz;
-    const int O = (colour + y + z) & 1;  // the colour's cells in this row: x = 2 i + O
-    const T* eo = e + (colour ^ 1) * half;
-    T* es = e + colour * half;
-    // unguarded wrapped loads, as in k_smooth_v: beyond a wall only
-    // near-boundary cells would read, and those are updated from the list
-    int ym, yp, zm, zp, il, ir;
-    if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
-    if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
-    if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
-    if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
-    if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
-    if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
-    const int rowh = nxh * (y + ny * z);
-    // the colour's update bits of this span (4 bits of one mask word)
-    const unsigned upd = (mask[(size_t)colour * ((size_t)ny * nz * wpr) + (size_t)wpr * (y + ny * z) + (iq >> 5)] >>
-                          (iq & 31)) & 0xFu;
-    if (!lane_on || upd == 0u) return;
-    const bool gs = omega == (T)1;
-    T c[4], ox[6], a[4], b[4], d[4], f[4], r[4];
-    if (first == 1) {
-#pragma unroll
-        for (int k = 0; k < 4; k++) c[k] = a[k] = b[k] = d[k] = f[k] = (T)0;
-#pragma unroll
-        for (int k = 0; k < 6; k++) ox[k] = (T)0;
-    } else {
-        if (first == 2 || gs) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) c[k] = (T)0;  // (gs: not read, never used)
-        } else {
-            ES_VLD(c, 0, es + rowh + iq);
-        }
-        ES_VLD(ox, 1, eo + rowh + iq);
-        ox[0] = O == 0 ? eo[rowh + il] : (T)0;
-        ox[5] = O == 1 ? eo[rowh + ir] : (T)0;
-        ES_VLD(a, 0, eo + nxh * (ym + ny * z) + iq);
-        ES_VLD(b, 0, eo + nxh * (yp + ny * z) + iq);
-        ES_VLD(d, 0, eo + nxh * (y + ny * zm) + iq);
-        ES_VLD(f, 0, eo + nxh * (y + ny * zp) + iq);
-    }
-    ES_VLD(r, 0, rhs + colour * half + rowh + iq);
-    if (O == 0)
-        rb_span_update<T, 0>(inv_diag0, L.h2, c, ox, a, b, d, f, r, upd, first == 1, omega);
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (y >= L.ny || i0 >= (L.nx >> 1)) return;
+    const int z0 = ((int)blockIdx.z - nw.planes) * zc;
+    const int z1 = z0 + zc < L.nz ? z0 + zc : L.nz;
+    const uint32_t* mcol = mask + (size_t)colour * ((size_t)L.ny * L.nz * wpr);
+    const T* rcol = rhs + (size_t)colour * half;
+    const T* eo = e + (size_t)(colour ^ 1) * half;
+    T* es = e + (size_t)colour * half;
+    if (first == 1)
+        rb_march<T, 1, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
+    else if (first == 2)
+        rb_march<T, 2, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
+    else if (omega == (T)1)
+        rb_march<T, 0, true>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
     else
-        rb_span_update<T, 1>(inv_diag0, L.h2, c, ox, a, b, d, f, r, upd, first == 1, omega);
-    if (upd == 0xFu) {
-        vst(es + rowh + i0, c[0], c[1], c[2], c[3]);
-    } else {
-        // (the colour's near-boundary cells belong to the near blocks)
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            if ((upd >> k) & 1u) es[rowh + i0 + k] = c[k];
-    }
+        rb_march<T, 0, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
 }
 
 __device__ __forceinline__ bool axis_ok(int v, int n, int per, int& w) {
@@ -2238,7 +2289,11 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                 const int gx = (L.nx / 8 + 31) / 32, gy = (L.ny + 7) / 8;
                 const int want = 2 * c->n_sm > kNearSegs ? 2 * c->n_sm : kNearSegs;
                 const int near_planes = (want + gx * gy - 1) / (gx * gy);
-                const dim3 sgrd(gx, gy, L.nz + near_planes);
+                // planes per interior block: up to 16, keeping about eight
+                // blocks per SM in all
+                int zc = (int)((long long)gx * gy * L.nz / (8LL * c->n_sm));
+                zc = zc < 1 ? 1 : (zc > 16 ? 16 : zc);
+                const dim3 sgrd(gx, gy, (L.nz + zc - 1) / zc + near_planes);
                 const int* cnt = c->near_count + 2 * kNearSegs * l;
                 // per cell: the other colour's e in, the colour's e out, its
                 // rhs in (from zero: rhs in, e out), the mask bits; the
@@ -2253,7 +2308,7 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                     ProfScope ps(c, "smooth_half", l,
                                  !first ? b_rb_half : (col == 0 ? b_rb_first : b_rb_half - nl * own));
                     k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, c->rbmask, c->rb_wpr, rhs, e, col,
-                                                                 fs, omega, rb.half, nw);
+                                                                 fs, omega, rb.half, nw, zc);
                 }
                 count(c, 2);
                 return;
