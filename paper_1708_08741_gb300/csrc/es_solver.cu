@@ -826,14 +826,12 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
 // ox[j] holds the other colour at compact index i0 - 1 + j, so the x
 // neighbours of cell i0 + k are ox[k + O] (left) and ox[k + 1 + O] (right).
 // The near-boundary cells of the colour-split finest level, by colour: the
-// level's near-cell list and the state bytes their stencils need, and how
-// many leading z planes of blocks of a half sweep's grid work on them.
+// level's near-cell list and the state bytes their stencils need.
 struct NearWork {
     const uint8_t* st;
     const int* list;
     const int* count;
     int cap;
-    int planes;
 };
 
 // The interior unknown cells of one colour of the colour-split finest
@@ -952,65 +950,72 @@ __device__ __forceinline__ void rb_march(const Level<T>& L, T inv_diag0, const u
 // colour-split layout (reduced forms, nx % 8 == 0), interior and
 // near-boundary cells in one launch.  The two sets are disjoint and both
 // read only the other colour, so they need no order:
-//  * the first nw.planes z planes of blocks update the colour's
-//    near-boundary cells from the near-cell list (Gauss-Seidel values with
-//    the boundary faces of Sec. 5.4, as k_smooth_near); scheduled first,
-//    their scattered, latency-bound loads overlap the streaming blocks;
-//  * in the other blocks a thread owns 4 consecutive compact places of the
-//    colour in one row (8 natural cells) and marches through zc planes
-//    (rb_march), loading the other colour's rows and its right-hand side
-//    as 16-byte vectors and storing the cells it updates.  Which cells
-//    those are (the interior unknown cells) it reads from the colour's bit
-//    mask (one bit per cell, rows padded to whole 32-bit words), not from
-//    the state bytes.  A Gauss-Seidel update (omega = 1) does not need the
-//    cell's old value, so the colour's own e is read only for omega != 1.
+//  * a thread owns 4 consecutive compact places of the colour in one row
+//    (8 natural cells) and marches through zc planes (rb_march), loading
+//    the other colour's rows and its right-hand side as 16-byte vectors and
+//    storing the cells it updates.  Which cells those are (the interior
+//    unknown cells) it reads from the colour's bit mask (one bit per cell,
+//    rows padded to whole 32-bit words), not from the state bytes.  A
+//    Gauss-Seidel update (omega = 1) does not need the cell's old value, so
+//    the colour's own e is read only for omega != 1;
+//  * then every block takes its share of the colour's near-boundary cells
+//    from the near-cell list (Gauss-Seidel values with the boundary faces of
+//    Sec. 5.4, as k_smooth_near): about half a cell per thread on large
+//    grids, whose scattered, latency-bound loads overlap the streaming of
+//    the blocks still marching.
 // Per cell and half sweep the interior moves the other colour's e in, the
 // colour's e out and its rhs in: 6 bytes, plus 1/16 byte of mask (against 9
 // with the state bytes and the colour's old values, and 13 in the
 // interleaved layout).  Cells that are not unknown are never written: no
 // kernel reads e there.  Same per-cell arithmetic as k_smooth_v.  first: 1
 // the iterate starts at zero (nothing is read), 2 the colour's old values
-// are zero (the second colour of a sweep from zero).
+// are zero (the second colour of a sweep from zero).  Four blocks per SM:
+// the register cap keeps enough loads in flight to stream at the HBM rate.
 template <class T>
-__global__ void __launch_bounds__(256) k_smooth_rb(Level<T> L, T inv_diag0, const uint32_t* __restrict__ mask,
-                                                   int wpr, const T* __restrict__ rhs, T* __restrict__ e,
-                                                   int colour, int first, T omega, int half, NearWork nw, int zc) {
-    if ((int)blockIdx.z < nw.planes) {
-        // block b of the near part serves segment b % kNearSegs of the colour
-        const int nblk = nw.planes * (int)(gridDim.x * gridDim.y);
-        const int b = ((int)blockIdx.z * (int)gridDim.y + (int)blockIdx.y) * (int)gridDim.x + (int)blockIdx.x;
-        const int seg = b % kNearSegs, sb = b / kNearSegs;
-        const int nsb = (nblk - seg + kNearSegs - 1) / kNearSegs;  // blocks on this segment
+__global__ void __launch_bounds__(256, 4) k_smooth_rb(Level<T> L, T inv_diag0, const uint32_t* __restrict__ mask,
+                                                      int wpr, const T* __restrict__ rhs, T* __restrict__ e,
+                                                      int colour, int first, T omega, int half, NearWork nw,
+                                                      int zc) {
+    const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (y < L.ny && i0 < (L.nx >> 1)) {
+        const int z0 = (int)blockIdx.z * zc;
+        const int z1 = z0 + zc < L.nz ? z0 + zc : L.nz;
+        const uint32_t* mcol = mask + (size_t)colour * ((size_t)L.ny * L.nz * wpr);
+        const T* rcol = rhs + (size_t)colour * half;
+        const T* eo = e + (size_t)(colour ^ 1) * half;
+        T* es = e + (size_t)colour * half;
+        if (first == 1)
+            rb_march<T, 1, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
+        else if (first == 2)
+            rb_march<T, 2, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
+        else if (omega == (T)1)
+            rb_march<T, 0, true>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
+        else
+            rb_march<T, 0, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
+    }
+    // the near-boundary cells: with at least kNearSegs blocks, block b
+    // serves segment b % kNearSegs together with the other blocks of that
+    // residue; with fewer, block b serves segments b, b + nblk, ...
+    const int nblk = (int)(gridDim.x * gridDim.y * gridDim.z);
+    const int b = ((int)blockIdx.z * (int)gridDim.y + (int)blockIdx.y) * (int)gridDim.x + (int)blockIdx.x;
+    const bool many = nblk >= kNearSegs;
+    const RbMap rb{half};
+    const EAcc<T, T> A{(T)1, (T)1};
+    const int tid = (int)(threadIdx.y * blockDim.x + threadIdx.x), nth = (int)(blockDim.x * blockDim.y);
+    for (int seg = many ? b % kNearSegs : b; seg < kNearSegs; seg += many ? kNearSegs : nblk) {
+        const int sb = many ? b / kNearSegs : 0;
+        const int nsb = many ? (nblk - seg + kNearSegs - 1) / kNearSegs : 1;  // blocks on this segment
         const int k = colour * kNearSegs + seg;
         const int n = nw.count[k];
         const int* list = nw.list + (size_t)k * nw.cap;
-        const RbMap rb{half};
-        const EAcc<T, T> A{(T)1, (T)1};
-        for (int i = sb * 256 + (int)(threadIdx.y * 32 + threadIdx.x); i < n; i += nsb * 256) {
+        for (int i = sb * nth + tid; i < n; i += nsb * nth) {
             const int cc = list[i];
             const int x = cc % L.nx, yz = cc / L.nx;
-            const int y = yz % L.ny, z = yz / L.ny;
-            e[rb(cc, colour)] = near_gs<T, T, RbMap>(L, nw.st, rhs, e, x, y, z, first, omega, A, rb);
+            const int yy = yz % L.ny, zz = yz / L.ny;
+            e[rb(cc, colour)] = near_gs<T, T, RbMap>(L, nw.st, rhs, e, x, yy, zz, first, omega, A, rb);
         }
-        return;
     }
-    const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
-    const int y = blockIdx.y * 8 + threadIdx.y;
-    if (y >= L.ny || i0 >= (L.nx >> 1)) return;
-    const int z0 = ((int)blockIdx.z - nw.planes) * zc;
-    const int z1 = z0 + zc < L.nz ? z0 + zc : L.nz;
-    const uint32_t* mcol = mask + (size_t)colour * ((size_t)L.ny * L.nz * wpr);
-    const T* rcol = rhs + (size_t)colour * half;
-    const T* eo = e + (size_t)(colour ^ 1) * half;
-    T* es = e + (size_t)colour * half;
-    if (first == 1)
-        rb_march<T, 1, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
-    else if (first == 2)
-        rb_march<T, 2, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
-    else if (omega == (T)1)
-        rb_march<T, 0, true>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
-    else
-        rb_march<T, 0, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
 }
 
 __device__ __forceinline__ bool axis_ok(int v, int n, int per, int& w) {
@@ -2284,16 +2289,12 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             if (split) {
                 // colour-split finest level: interior pass, then the colour's
                 // near-boundary cells from the list
-                // leading z planes of near-cell blocks: at least one block per
-                // list segment, about two per SM
+                // planes per block: up to 16, keeping about eight blocks per
+                // SM in all
                 const int gx = (L.nx / 8 + 31) / 32, gy = (L.ny + 7) / 8;
-                const int want = 2 * c->n_sm > kNearSegs ? 2 * c->n_sm : kNearSegs;
-                const int near_planes = (want + gx * gy - 1) / (gx * gy);
-                // planes per interior block: up to 16, keeping about eight
-                // blocks per SM in all
                 int zc = (int)((long long)gx * gy * L.nz / (8LL * c->n_sm));
                 zc = zc < 1 ? 1 : (zc > 16 ? 16 : zc);
-                const dim3 sgrd(gx, gy, (L.nz + zc - 1) / zc + near_planes);
+                const dim3 sgrd(gx, gy, (L.nz + zc - 1) / zc);
                 const int* cnt = c->near_count + 2 * kNearSegs * l;
                 // per cell: the other colour's e in, the colour's e out, its
                 // rhs in (from zero: rhs in, e out), the mask bits; the
@@ -2302,7 +2303,7 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                 const double own = c->P.omega == 1.0 ? 0.0 : 0.5 * es;
                 const double b_rb_first = nl * (0.5 * es + 0.5 * ts + 0.0625);
                 const double b_rb_half = nl * (1.0 * es + own + 0.5 * ts + 0.0625);
-                const NearWork nw{st, c->near_list[l], cnt, c->near_cap[l], near_planes};
+                const NearWork nw{st, c->near_list[l], cnt, c->near_cap[l]};
                 for (int col = 0; col < 2; col++) {
                     const int fs = first ? (col == 0 ? 1 : 2) : 0;
                     ProfScope ps(c, "smooth_half", l,
