@@ -29,9 +29,10 @@ if ROOT not in sys.path:
 METRIC = "coupled-step MLUPS & %HBM roofline at 512^3; served runs/s, p99 latency mixed vs FP64"
 UNIT = "MLUPS"
 # algorithmic bytes per fluid cell of the stream-collide kernel in the MIXED32
-# form: 19 FP32 populations read + 19 written, 3 FP32 body-force components,
-# 1 flag byte; obstacle cells only read their flag byte
-LBM_BYTES_FLUID = 2 * 19 * 4 + 3 * 4 + 1
+# form: 19 FP32 populations read + 19 written, the FP32 potential (the body
+# force is formed in the kernel from psi at the cell and, from cache, its
+# neighbours), 1 flag byte; obstacle cells only read their flag byte
+LBM_BYTES_FLUID = 2 * 19 * 4 + 4 + 1
 LBM_BYTES_SOLID = 1
 
 

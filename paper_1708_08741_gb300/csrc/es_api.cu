@@ -283,6 +283,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->g.nz = params->dims[2];
     for (int a = 0; a < 3; a++) c->g.per[a] = params->periodic[a] ? 1 : 0;
     c->rb0 = colour_split(params);
+    c->fb_lazy = false;
     c->slip = 0;
     for (int f = 0; f < 6; f++)
         if (!c->g.per[f / 2] && params->wall_slip[f]) c->slip |= 1 << f;

@@ -138,6 +138,9 @@ struct es_ctx {
     float e_scale;   // ES_MG_FP16: scale of the finest level's stored correction
     int slip;        // bit f: face f (x-lo, x-hi, y-lo, ...) of a non-periodic axis is free-slip
     bool rb0;        // the finest level's e and rhs in the colour-split layout (reduced forms)
+    bool fb_lazy;    // f_b is derived from psi by the stream-collide (set by a solve when
+                     // fb_fused); the stored field then holds it only after a read or
+                     // at the cells next to obstacles
     bool mapped_once;  // the particles were mapped at least once (flags valid outside their shells)
     cudaGraphExec_t vgraph[2];          // the V-cycle from zero / warm-started, captured on first use
     unsigned long long vgraph_kernels[2];  // kernel launches in each graph
@@ -183,6 +186,9 @@ cudaError_t launch_join_psi(es_ctx* c, double* dst);         // MIXED32: dst = p
 cudaError_t launch_correct(es_ctx* c);
 cudaError_t launch_residual_update(es_ctx* c);
 cudaError_t launch_body_force(es_ctx* c);
+cudaError_t launch_body_force_near(es_ctx* c);      // f_b at the listed cells next to obstacles
+cudaError_t materialize_body_force(es_ctx* c);      // the whole stored f_b, when it is evaluated on the fly
+bool fb_fused(const es_ctx* c);                     // the stream-collide evaluates f_b from psi
 // lbm and particles (es_lbm.cu)
 cudaError_t launch_lbm(es_ctx* c);
 cudaError_t launch_forces(es_ctx* c);

@@ -84,14 +84,27 @@ __device__ __forceinline__ WallSrc wall_source(const Grid& g, int slip_faces, co
     return WallSrc{opp(q), c};
 }
 
+// The electric body force evaluated inside the stream-collide (reduced
+// forms): psi (the float potential), E_ext and kappa^2 eps.
+struct FbPsi {
+    const float* psi;
+    float Ex, Ey, Ez, k2e;
+};
+
 // SLIP: the grid has free-slip faces (a separate instance, so that the
-// common no-slip/periodic form keeps its register count).
-template <class S, bool SLIP, class C = typename Store<S>::C>
+// common no-slip/periodic form keeps its register count).  FBPSI: the body
+// force of an interior fluid cell (no obstacle or wall among its D3Q19
+// neighbours) is formed here from the potential at the cell and its 18
+// neighbours (body_force_iso, Sec. 5.6), so f_b makes no round trip through
+// HBM: the cell reads 4 bytes of psi (the neighbours' come from cache)
+// instead of 12 of stored f_b.  Cells next to obstacles or walls read the
+// stored field (their D3Q7 ghost-value gradient, k_body_force_near).
+template <class S, bool SLIP, bool FBPSI = false, class C = typename Store<S>::C>
 __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
                                              const uint8_t* __restrict__ flags, const int32_t* __restrict__ owner,
                                              const DParticle* __restrict__ part, const float* __restrict__ partf,
                                              const C* __restrict__ fb, C ax, C ay, C az, C lam_e, C lam_o,
-                                             int slip_faces) {
+                                             int slip_faces, FbPsi fp) {
     using St = Store<S>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -103,18 +116,54 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
     if (fl & F_SOLID) return;  // obstacle cells are not updated
 
     C f[19];
+    C fx, fy, fz;  // body force (Sec. 5.6) plus the uniform acceleration
     if (!(fl & F_NEAR19)) {
         // all 18 pull sources are fluid cells inside the (periodic) domain;
         // the offset of x - e_q is a sum of per-axis steps (wrapped at faces)
         const int sx[3] = {(x == nx - 1 ? 0 : x + 1) - x, 0, (x == 0 ? nx - 1 : x - 1) - x};
         const int sy[3] = {((y == g.ny - 1 ? 0 : y + 1) - y) * nx, 0, ((y == 0 ? g.ny - 1 : y - 1) - y) * nx};
         const int sz[3] = {((z == g.nz - 1 ? 0 : z + 1) - z) * nxy, 0, ((z == 0 ? g.nz - 1 : z - 1) - z) * nxy};
+        if constexpr (FBPSI) {
+            // psi(x + d) at offset sx[1 - dx] + sy[1 - dy] + sz[1 - dz]
+            const float* ps = fp.psi + c;
+            const Psi19 p{__ldg(ps),
+                          __ldg(ps + sx[0]),
+                          __ldg(ps + sx[2]),
+                          __ldg(ps + sy[0]),
+                          __ldg(ps + sy[2]),
+                          __ldg(ps + sz[0]),
+                          __ldg(ps + sz[2]),
+                          __ldg(ps + sx[0] + sy[0]),
+                          __ldg(ps + sx[2] + sy[2]),
+                          __ldg(ps + sx[0] + sy[2]),
+                          __ldg(ps + sx[2] + sy[0]),
+                          __ldg(ps + sx[0] + sz[0]),
+                          __ldg(ps + sx[2] + sz[2]),
+                          __ldg(ps + sx[0] + sz[2]),
+                          __ldg(ps + sx[2] + sz[0]),
+                          __ldg(ps + sy[0] + sz[0]),
+                          __ldg(ps + sy[2] + sz[2]),
+                          __ldg(ps + sy[0] + sz[2]),
+                          __ldg(ps + sy[2] + sz[0])};
+            float f0, f1, f2;
+            body_force_iso(p, fp.Ex, fp.Ey, fp.Ez, fp.k2e, f0, f1, f2);
+            fx = f0 + ax;
+            fy = f1 + ay;
+            fz = f2 + az;
+        } else {
+            fx = fb[c] + ax;
+            fy = fb[N + c] + ay;
+            fz = fb[2u * N + c] + az;
+        }
 #pragma unroll
         for (int q = 0; q < 19; q++) {
             const int s_ = c + sx[1 + cx(q)] + sy[1 + cy(q)] + sz[1 + cz(q)];
             f[q] = St::ld(q, __ldg(P.src[q] + s_));
         }
     } else {
+        fx = fb[c] + ax;
+        fy = fb[N + c] + ay;
+        fz = fb[2u * N + c] + az;
         f[0] = St::ld(0, P.src[0][c]);
 #pragma unroll
         for (int q = 1; q < 19; q++) {
@@ -164,9 +213,6 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
             }
         }
     }
-
-    // body force (Sec. 5.6) plus a uniform acceleration
-    const C fx = fb[c] + ax, fy = fb[N + c] + ay, fz = fb[2u * N + c] + az;
 
     // moments (Eq. MacroscopVel) with the modified velocity (Eq. modified_velocity)
     C rho = (C)0, jx = (C)0, jy = (C)0, jz = (C)0;
@@ -728,20 +774,41 @@ cudaError_t launch_lbm(es_ctx* c) {
         k_particles_f32<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->np, c->part, c->partf);
         count(c);
     }
+    // the body force evaluated in the stream-collide: first the stored values
+    // of the cells next to obstacles and walls
+    const bool lazy = c->fb_lazy;
+    if (lazy) {
+        const cudaError_t e = launch_body_force_near(c);
+        if (e != cudaSuccess) return e;
+    }
+    const double k2e = c->S.kappa * c->S.kappa * c->S.eps;
+    const FbPsi fp{c->psi32, (float)c->P.E_ext[0], (float)c->P.E_ext[1], (float)c->P.E_ext[2], (float)k2e};
     dispatch_store(c, [&](auto tag) {
         using S = decltype(tag);
         using C = typename Store<S>::C;
         // algorithmic bytes per cell: 19 populations in and out, f_b (3 C)
-        // and the flag byte in
-        ProfScope ps(c, "lbm", -1, (double)g.N * (38.0 * sizeof(S) + 3.0 * sizeof(C) + 1.0));
+        // or psi (4) and the flag byte in
+        ProfScope ps(c, "lbm", -1, (double)g.N * (38.0 * sizeof(S) + (lazy ? 4.0 : 3.0 * sizeof(C)) + 1.0));
+        auto run = [&](auto slip, auto fused) {
+            k_lbm<S, decltype(slip)::value, decltype(fused)::value><<<grd, blk, 0, c->stream>>>(
+                g, streams<S>(c), c->flags, c->owner, c->part, c->partf, (const C*)c->fb, (C)a[0], (C)a[1], (C)a[2],
+                (C)c->lambda_e, (C)c->lambda_o, c->slip, fp);
+        };
+        using T_ = std::true_type;
+        using F_ = std::false_type;
+        if constexpr (std::is_same<C, float>::value) {
+            if (lazy) {
+                if (c->slip)
+                    run(T_{}, T_{});
+                else
+                    run(F_{}, T_{});
+                return;
+            }
+        }
         if (c->slip)
-            k_lbm<S, true><<<grd, blk, 0, c->stream>>>(g, streams<S>(c), c->flags, c->owner, c->part, c->partf,
-                                                       (const C*)c->fb, (C)a[0], (C)a[1], (C)a[2],
-                                                       (C)c->lambda_e, (C)c->lambda_o, c->slip);
+            run(T_{}, F_{});
         else
-            k_lbm<S, false><<<grd, blk, 0, c->stream>>>(g, streams<S>(c), c->flags, c->owner, c->part, c->partf,
-                                                        (const C*)c->fb, (C)a[0], (C)a[1], (C)a[2],
-                                                        (C)c->lambda_e, (C)c->lambda_o, 0);
+            run(F_{}, F_{});
     });
     count(c);
     return cudaGetLastError();
@@ -813,6 +880,8 @@ cudaError_t launch_set_pdf(es_ctx* c, const double* src) {
 }
 
 cudaError_t launch_get_moments(es_ctx* c, double* rho, double* u) {
+    const cudaError_t err = materialize_body_force(c);
+    if (err != cudaSuccess) return err;
     const double* a = c->P.accel;
     dispatch_store(c, [&](auto tag) {
         using S = decltype(tag);
@@ -825,6 +894,7 @@ cudaError_t launch_get_moments(es_ctx* c, double* rho, double* u) {
 }
 
 cudaError_t launch_set_fb(es_ctx* c, const double* src) {
+    c->fb_lazy = false;  // (the given field is used until the next solve)
     long long n = 3 * c->g.N;
     if (mixed(c))
         k_load_fb<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(n, src, (float*)c->fb);
@@ -835,6 +905,8 @@ cudaError_t launch_set_fb(es_ctx* c, const double* src) {
 }
 
 cudaError_t launch_get_fb(es_ctx* c, double* dst) {
+    const cudaError_t err = materialize_body_force(c);
+    if (err != cudaSuccess) return err;
     long long n = 3 * c->g.N;
     if (mixed(c))
         k_copy_fb<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(n, (const float*)c->fb, dst);
@@ -845,6 +917,10 @@ cudaError_t launch_get_fb(es_ctx* c, double* dst) {
 }
 
 cudaError_t launch_gather(es_ctx* c, int which, const long long* idx, int n, double* out) {
+    if (which == ES_FIELD_FB || which == ES_FIELD_U) {
+        const cudaError_t err = materialize_body_force(c);
+        if (err != cudaSuccess) return err;
+    }
     const double* a = c->P.accel;
     int last = c->last_src >= 0 ? c->last_src : c->cur;
     dispatch_store(c, [&](auto tag) {

@@ -2101,25 +2101,19 @@ __global__ void __launch_bounds__(256) k_body_force_v(Grid g, float Ex, float Ey
     const int row = nx * (y + ny * z);
     const uchar4 f4 = *reinterpret_cast<const uchar4*>(flags + row + xs);
     const uint8_t fl[4] = {f4.x, f4.y, f4.z, f4.w};
-    const float a = (float)(3.0 / 18.0), b = (float)(3.0 / 36.0);
     float o0[4], o1[4], o2[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int j = i + 1;  // index in the 6-wide rows
-        float g0 = a * (c0[j + 1] - c0[j - 1]);
-        float g1 = a * (yp0[j] - ym0[j]);
-        float g2 = a * (zp0[j] - zm0[j]);
-        const float dxy1 = b * (yp0[j + 1] - ym0[j - 1]), dxy2 = b * (ym0[j + 1] - yp0[j - 1]);
-        const float dxz1 = b * (zp0[j + 1] - zm0[j - 1]), dxz2 = b * (zm0[j + 1] - zp0[j - 1]);
-        const float dyz1 = b * (pp[i] - mm[i]), dyz2 = b * (pm[i] - mp[i]);
-        g0 += dxy1 + dxy2 + dxz1 + dxz2;
-        g1 += dxy1 - dxy2 + dyz1 + dyz2;
-        g2 += dxz1 - dxz2 + dyz1 - dyz2;
-        const float rho_e = -k2e * c0[j];
+        const Psi19 p{c0[j],      c0[j + 1],  c0[j - 1],  yp0[j],     ym0[j],     zp0[j],     zm0[j],
+                      yp0[j + 1], ym0[j - 1], ym0[j + 1], yp0[j - 1], zp0[j + 1], zm0[j - 1], zm0[j + 1],
+                      zp0[j - 1], pp[i],      mm[i],      pm[i],      mp[i]};
+        float f0, f1, f2;
+        body_force_iso(p, Ex, Ey, Ez, k2e, f0, f1, f2);
         const bool solid = fl[i] & F_SOLID;
-        o0[i] = solid ? 0.0f : rho_e * (Ex - g0);
-        o1[i] = solid ? 0.0f : rho_e * (Ey - g1);
-        o2[i] = solid ? 0.0f : rho_e * (Ez - g2);
+        o0[i] = solid ? 0.0f : f0;
+        o1[i] = solid ? 0.0f : f1;
+        o2[i] = solid ? 0.0f : f2;
     }
     const size_t N = (size_t)g.N;
     *reinterpret_cast<float4*>(fb + row + xs) = make_float4(o0[0], o0[1], o0[2], o0[3]);
@@ -2667,26 +2661,51 @@ cudaError_t launch_join_psi(es_ctx* c, double* dst) {
     return cudaGetLastError();
 }
 
-// Algorithmic bytes per cell: psi as the kernel reads it (float in MIXED32,
-// double in FP64) and the flag byte in, f_b (3 s) out.
-cudaError_t launch_body_force(es_ctx* c) {
+// The reduced forms on grids with nx % 4 == 0 evaluate f_b inside the
+// stream-collide (body_force_iso at interior fluid cells, the stored field
+// at cells next to obstacles and walls): the solve only marks the body force
+// as derived from psi.
+bool fb_fused(const es_ctx* c) { return mixed(c) && c->g.nx % 4 == 0; }
+
+// f_b of the fluid cells with a non-fluid D3Q19 neighbour (the D3Q7
+// ghost-value gradient; list of cells), into the stored field.
+cudaError_t launch_body_force_near(es_ctx* c) {
     const Grid& g = c->g;
-    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
-    const double s = mixed(c) ? 4.0 : 8.0;
-    ProfScope ps(c, "body_force", -1, (double)g.N * (s + 1.0 + 3.0 * s));
     const double* E = c->P.E_ext;
     const double k2e = c->S.kappa * c->S.kappa * c->S.eps;
     WallF wall2;
     for (int f = 0; f < 6; f++) wall2.v2[f] = (float)(2.0 * c->S.pot_val[f]);
-    if (mixed(c) && g.nx % 4 == 0) {
-        dim3 vgrd((g.nx / 4 + 31) / 32, (g.ny + 7) / 8, g.nz);
-        k_body_force_v<<<vgrd, dim3(32, 8), 0, c->stream>>>(g, (float)E[0], (float)E[1], (float)E[2], (float)k2e,
-                                                            c->psi32, c->flags, (float*)c->fb);
-        k_body_force_near<<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, kNearSegs), 256, 0, c->stream>>>(
-            g, c->S, (float)E[0], (float)E[1], (float)E[2], (float)k2e, c->psi32, c->owner, c->st[0],
-            (const float2*)c->pbc, wall2, c->bf_list, c->bf_count, c->bf_cap, (float*)c->fb);
-        count(c);
-    } else if (mixed(c))
+    ProfScope ps(c, "body_force_near", -1, 0.0);
+    k_body_force_near<<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, kNearSegs), 256, 0, c->stream>>>(
+        g, c->S, (float)E[0], (float)E[1], (float)E[2], (float)k2e, c->psi32, c->owner, c->st[0],
+        (const float2*)c->pbc, wall2, c->bf_list, c->bf_count, c->bf_cap, (float*)c->fb);
+    count(c);
+    return cudaGetLastError();
+}
+
+// Algorithmic bytes per cell: psi as the kernel reads it (float in MIXED32,
+// double in FP64) and the flag byte in, f_b (3 s) out.  Writes the whole
+// field (the fused forms call it when the field is read).
+cudaError_t launch_body_force_full(es_ctx* c) {
+    const Grid& g = c->g;
+    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    const double s = mixed(c) ? 4.0 : 8.0;
+    const double* E = c->P.E_ext;
+    const double k2e = c->S.kappa * c->S.kappa * c->S.eps;
+    WallF wall2;
+    for (int f = 0; f < 6; f++) wall2.v2[f] = (float)(2.0 * c->S.pot_val[f]);
+    if (fb_fused(c)) {
+        {
+            ProfScope ps(c, "body_force", -1, (double)g.N * (s + 1.0 + 3.0 * s));
+            dim3 vgrd((g.nx / 4 + 31) / 32, (g.ny + 7) / 8, g.nz);
+            k_body_force_v<<<vgrd, dim3(32, 8), 0, c->stream>>>(g, (float)E[0], (float)E[1], (float)E[2],
+                                                                (float)k2e, c->psi32, c->flags, (float*)c->fb);
+            count(c);
+        }
+        return launch_body_force_near(c);
+    }
+    ProfScope ps(c, "body_force", -1, (double)g.N * (s + 1.0 + 3.0 * s));
+    if (mixed(c))
         k_body_force<float, float><<<grd, blk, 0, c->stream>>>(g, c->S, (float)E[0], (float)E[1], (float)E[2],
                                                                (float)k2e, 0.0f, c->psi32, c->flags, c->owner, c->part,
                                                                c->kind, c->st[0], (const float2*)c->pbc, wall2,
@@ -2699,5 +2718,20 @@ cudaError_t launch_body_force(es_ctx* c) {
     count(c);
     return cudaGetLastError();
 }
+
+// The body force after a solve: computed and stored here (FP64, and reduced
+// forms with nx % 4 != 0), or left to the stream-collide (fb_fused).
+cudaError_t launch_body_force(es_ctx* c) {
+    if (fb_fused(c)) {
+        c->fb_lazy = true;
+        return cudaSuccess;
+    }
+    c->fb_lazy = false;
+    return launch_body_force_full(c);
+}
+
+// Before the stored field is read (FB, U and the stream-collide's cells next
+// to obstacles): the values of a body force that is evaluated on the fly.
+cudaError_t materialize_body_force(es_ctx* c) { return c->fb_lazy ? launch_body_force_full(c) : cudaSuccess; }
 
 }  // namespace es
