@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=512, help="cells per axis")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer run (default: --steps)")
     ap.add_argument("--serving", action="store_true",
                     help="serving mode: a stream of independent runs, MIXED32 continuous batching "
@@ -141,52 +142,72 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(steps_timed=1, n=128):
-    """The FP64 oracle as it stands, single-threaded on a host core, on a
-    sub-box of the same suspension (same sphere density, radius, charges,
-    Debye length and field).  One untimed step (the cold solve), then timed
-    steps; value in MLUPS."""
+def _oracle_mlups(wl, steps, warmup, omp):
+    """MLUPS of the FP64 oracle as it stands on wl: `warmup` untimed steps,
+    then `steps` timed ones."""
+    import oracle
+
+    o = oracle.Oracle(wl, omp=omp)
+    for _ in range(warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step()
+    dt = time.perf_counter() - t0
+    return wl.n_cells * steps / dt / 1e6, dt
+
+
+def cpu_baseline(n=128):
+    """The FP64 oracle as it stands (plain C, -O3, no FMA contraction) on the
+    host cores, bounded to ~15 s of CPU work:
+    * value: the all-core OpenMP build (same source and bits, independent
+      cells shared out) on an n^3 sub-box of the suspension (same sphere
+      density, radius, charges, Debye length and field), 1 untimed + 5 timed
+      steps;
+    * single_thread: the serial build on the same sub-box, 1 + 2 steps;
+    * c1_full: the 32^3 single-sphere case in full (100 steps), serial."""
     import oracle
     from paper_1708_08741_gb300 import workloads as W
 
+    nproc = os.cpu_count() or 1
     wl = W.suspension_sample(n)
-    o = oracle.Oracle(wl)
-    o.step()
-    t0 = time.perf_counter()
-    for _ in range(steps_timed):
-        o.step()
-    dt = time.perf_counter() - t0
-    return {"value": wl.n_cells * steps_timed / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n}^3 periodic sub-box, {wl.n_particles} spheres R=5 (same density as 2,880 in 512^3), "
-                      f"FP64 C oracle, {steps_timed} timed step(s) after 1 untimed step, 1 thread",
-            "seconds": dt}
+    v_all, dt_all = _oracle_mlups(wl, 5, 1, omp=True)
+    v_one, dt_one = _oracle_mlups(wl, 2, 1, omp=False)
+    c1 = W.single_sphere()
+    v_c1, dt_c1 = _oracle_mlups(c1, 100, 0, omp=False)
+    return {"value": v_all, "unit": UNIT, "cores": oracle.threads(True), "kind": "oracle",
+            "sample": f"{n}^3 periodic sub-box of the suspension, {wl.n_particles} spheres R=5 (the density of "
+                      f"2,880 in 512^3), FP64 C oracle built with OpenMP (all host cores), 5 timed steps after 1 "
+                      f"untimed step",
+            "seconds": dt_all, "nproc": nproc,
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1, "seconds": dt_one,
+                              "sample": f"the same {n}^3 sub-box, serial build, 2 timed steps after 1 untimed"},
+            "c1_full": {"value": v_c1, "unit": UNIT, "cores": 1, "seconds": dt_c1,
+                        "sample": "32^3 periodic box, one zeta sphere R=4, 3-level V-cycles to 1e-10, "
+                                  "all 100 steps, serial build"}}
 
 
 def run_reference(args):
+    """The oracle as it stands, on the host cores (OpenMP build), each step
+    one oracle step of an n^3 sub-box of the suspension; rank 0 only."""
     rank, _, world = rank_info()
     if rank != 0:
         return
-    n = 128 if (args.steps + args.warmup) <= 14 else 64
     import oracle
     from paper_1708_08741_gb300 import workloads as W
 
+    n = 128 if (args.steps + args.warmup) <= 24 else 64
     wl = W.suspension_sample(n)
-    o = oracle.Oracle(wl)
-    for _ in range(args.warmup):
-        o.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.step()
-    dt = time.perf_counter() - t0
-    value = wl.n_cells * args.steps / dt / 1e6
+    value, dt = _oracle_mlups(wl, args.steps, args.warmup, omp=True)
+    cores = oracle.threads(True)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"suspension sample {n}^3, {wl.n_particles} spheres R=5 (density of 2,880 in 512^3)",
-                   "parallelism": "host core"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step one oracle step of the {n}^3 sub-box"},
+                   "parallelism": f"host cores x{cores}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step one oracle step of the {n}^3 sub-box (OpenMP build, all host cores)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -267,8 +288,9 @@ def run_ours(args):
     # durations for the roofline; the event records cost host time, which
     # is why the step time comes from region 1)
     sim.profile_start()
+    pcycles = 0
     for k in range(args.steps):
-        sim.step()
+        pcycles += sim.step()["cycles"]
     prof = sim.profile_stop()
     barrier()
     torch.cuda.synchronize(dev)
@@ -315,10 +337,16 @@ def run_ours(args):
     h2d = wl.n_particles * psize
     d2h = wl.n_particles * (psize + 48)
 
+    levels = sim.params.levels
+    sim.close()
+    del sim
+    torch.cuda.synchronize(dev)
+    fp64 = None
+    if not args.no_fp64:
+        fp64 = measure_fp64(args, dev, barrier)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
-    sim.close()
     if rank != 0:
         return
     value = aggregate_throughput(N, args.steps, world, t_all)
@@ -327,12 +355,13 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"suspension {args.n}^3 periodic, {wl.n_particles} charged spheres R=5, "
-                               f"lambda_D=4, E=1e-3, MIXED32, {sim.params.levels}-level V(2,2) to RES_RF {wl.res_rf:g}"
+                               f"lambda_D=4, E=1e-3, MIXED32, {levels}-level V(2,2) to RES_RF {wl.res_rf:g}"
                                + (", FP16 finest-level correction" if mg == es.ES_MG_FP16 else ""),
                    "cells": N, "fluid_cells": n_fluid, "parallelism": f"replicas x{world}",
                    "l2_policy": "inputs larger than L2 (PDF fields 20 GB)"},
         "mflups": n_fluid * args.steps * world / t_all / 1e6,
         "vcycles_per_step": vcycles / args.steps,
+        **vcycle_stats(prof, pcycles),
         "start_residual_over_tol": sorted(round(x, 1) for x in start_ratio),
         "phases_ms": phases,
         "roofline": {"kernel": top["kernel"], "bound": "hbm", "achieved": top["gbs"], "peak": peak,
@@ -347,20 +376,18 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": base,
+        "fp64_form": fp64,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of each kernel in its current form, by kernel key; a kernel
-# missing here has no capture of its current code.
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# kernels that can lead the table, from one ncu --set full capture of the
-# same workload at 320^3 (bench.py --n 320), scaled by the cell count to
-# 512^3; None for the others.
-TRAFFIC = {"smooth_half L0": 276.18e6 * 4.096, "lbm": 5439.6e6 * 4.096}
+# kernels that can lead the table, from one ncu capture of each kernel in its
+# current form, by kernel key; a kernel missing here has no capture of its
+# current code (traffic null).
+TRAFFIC = {}
 
 
 def kernel_table(prof, lbm_bytes, peak):
@@ -381,6 +408,76 @@ def kernel_table(prof, lbm_bytes, peak):
                      "gbs": gbs, "frac": gbs / peak, "share": r["ms"] / total})
     rows.sort(key=lambda x: -x["share"])
     return rows
+
+
+# kernels that make up a V-cycle (per level)
+VCYCLE_KERNELS = ("smooth_half", "smooth_near", "smooth_fused", "restrict", "prolong", "coarse_solve")
+# floating-point operations of the stream-collide per interior fluid cell,
+# counted from k_lbm with an FMA as two: moments 45, modified velocity, u.u,
+# u.f and constants 23, rest population 10, nine TRT pairs with Luo forcing
+# 264 (axis pairs 28 each, diagonal pairs 30)
+LBM_FLOPS = 342
+
+
+def vcycle_stats(prof, cycles):
+    """Device time of one V-cycle (all levels) from the per-kernel event
+    timing of a region that ran `cycles` V-cycles."""
+    ms = sum(r["ms"] for r in prof if r["name"] in VCYCLE_KERNELS)
+    if cycles <= 0 or ms <= 0:
+        return {"vcycle_ms": None, "vcycles_per_s": None}
+    v = ms / cycles
+    return {"vcycle_ms": v, "vcycles_per_s": 1e3 / v, "vcycle_kernel_ms_total": ms, "vcycles_profiled": cycles}
+
+
+def measure_fp64(args, dev, barrier):
+    """The FP64 form on the same workload: step time, V-cycle time, and the
+    stream-collide against the measured FP64 FMA peak (the form is bound by
+    GB300's FP64 pipe, not by HBM)."""
+    import torch
+
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import workloads as W
+
+    wl = W.suspension(n=args.n, n_spheres=int(round(2880 * (args.n / 512) ** 3)),
+                      levels=6 if args.n % 32 == 0 else 4)
+    peak = es.alu_peak(es.ES_FP64)
+    sim = es.Simulation(wl, es.ES_FP64, device=str(dev))
+    for _ in range(2):
+        sim.step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    a, b = ev(), ev()
+    steps = 3
+    cyc = 0
+    with torch.cuda.stream(sim.stream):
+        a.record(sim.stream)
+        for _ in range(steps):
+            cyc += sim.step()["cycles"]
+        b.record(sim.stream)
+    torch.cuda.synchronize(dev)
+    t = a.elapsed_time(b) / 1e3
+    sim.profile_start()
+    pc = 0
+    for _ in range(2):
+        pc += sim.step()["cycles"]
+    prof = sim.profile_stop()
+    own = torch.empty(wl.n_cells, dtype=torch.int32, device=dev)
+    sim.field_device(es.FIELD_OWNER, own)
+    n_fluid = int((own < 0).sum().item())
+    del own
+    sim.close()
+    lbm = [r for r in prof if r["name"] == "lbm"][0]
+    lbm_ms = lbm["ms"] / max(lbm["launches"], 1)
+    achieved = LBM_FLOPS * n_fluid / (lbm_ms / 1e3) / 1e9
+    top = sorted(prof, key=lambda r: -r["ms"])[:6]
+    return {"ms_per_step": t / steps * 1e3, "mlups": wl.n_cells * steps / t / 1e6, "steps": steps,
+            "vcycles_per_step": cyc / steps, **vcycle_stats(prof, pc),
+            "roofline": {"kernel": "lbm", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                         "frac": achieved / peak, "flops_per_fluid_cell": LBM_FLOPS, "ms_per_launch": lbm_ms,
+                         "peak_source": "es_alu_peak FP64 FMA probe, CUDA events"},
+            "top_kernels_ms": {(r["name"] if r["level"] < 0 else f"{r['name']} L{r['level']}"):
+                               r["ms"] / max(r["launches"], 1) for r in top}}
 
 
 def ctypes_sizeof_particle(es):

@@ -346,6 +346,16 @@ typedef struct {
 int es_profile_start(es_ctx* ctx);
 int es_profile_stop(es_ctx* ctx, es_kernel_time* out, int max, int* n);
 
+/* Measured fused multiply-add throughput of the current device in GFLOP/s
+ * (2 flops per FMA), the denominator of the arithmetic roofline of kernels
+ * bound by their FP64 (precision ES_FP64) or FP32 (ES_MIXED32) pipe; the
+ * paper has no counterpart (instrumentation).  Runs register-resident FMA
+ * chains on every SM for a few milliseconds, timed with CUDA events on a
+ * private stream; allocates and frees a small device buffer.  Synchronises
+ * that stream.  ES_EINVAL for another precision or a NULL gflops, ES_ECUDA
+ * if a CUDA call fails. */
+int es_alu_peak(int precision, double* gflops);
+
 /* Number of CUDA kernels this context has launched so far (telemetry). */
 uint64_t es_kernel_launches(const es_ctx* ctx);
 

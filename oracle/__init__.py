@@ -38,17 +38,24 @@ FIELD_DIAG = 6
 FIELD_PDF_LAST = 7
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, so that decisions taken
-    in floating point, such as the cell-in-sphere test, are reproducible)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
+_LIB_OMP = os.path.join(_HERE, "_build", "libesoracle_omp.so")
+
+
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc -O3 (no FMA contraction, so that decisions
+    taken in floating point, such as the cell-in-sphere test, are
+    reproducible).  omp: the same source with OpenMP, a separate library used
+    only to time the oracle on all host cores (same results bit for bit)."""
+    target = _LIB_OMP if omp else _LIB
+    os.makedirs(os.path.dirname(target), exist_ok=True)
+    if force or not os.path.exists(target) or os.path.getmtime(target) < os.path.getmtime(_SRC):
+        tmp = target + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O3", "-std=c99", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC"]
+        cmd += ["-fopenmp"] if omp else []
+        cmd += ["-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, target)
+    return target
 
 
 class OrParams(ctypes.Structure):
@@ -87,13 +94,13 @@ class OrParticle(ctypes.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = build()
+def lib(omp: bool = False):
+    """The oracle library (serial), or its OpenMP build."""
+    if omp not in _libs:
+        path = build(omp=omp)
         L = ctypes.CDLL(path)
         P = ctypes.c_void_p
         dp = ctypes.POINTER(ctypes.c_double)
@@ -122,10 +129,17 @@ def lib():
         L.or_tolerance.restype = ctypes.c_double
         L.or_num_cells.argtypes = [P]
         L.or_num_cells.restype = ctypes.c_long
+        L.or_threads.argtypes = []
+        L.or_threads.restype = ctypes.c_int
         L.or_q_from_zeta.argtypes = [ctypes.c_double] * 4
         L.or_q_from_zeta.restype = ctypes.c_double
-        _lib = L
-    return _lib
+        _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(omp: bool = False) -> int:
+    """Threads the oracle's shared-out loops run on (1 for the serial build)."""
+    return int(lib(omp).or_threads())
 
 
 def _dptr(a: np.ndarray):
@@ -157,8 +171,9 @@ class OracleError(RuntimeError):
 class Oracle:
     """One oracle simulation; mirrors the C-ABI call sequence of the library."""
 
-    def __init__(self, wl, params_override: Optional[dict] = None):
+    def __init__(self, wl, params_override: Optional[dict] = None, omp: bool = False):
         self.wl = wl
+        self.L = lib(omp)
         P = OrParams()
         d = dict(dims=wl.dims, periodic=wl.periodic, pot_bc=wl.pot_bc, pot_val=wl.pot_val,
                  tau=wl.tau, kappa=wl.kappa, eps=wl.eps, E_ext=wl.E_ext, accel=wl.accel,
@@ -178,11 +193,11 @@ class Oracle:
         self.np = wl.n_particles
         parts = self._pack(wl.x, wl.v, wl.w, wl.R, wl.kind, wl.zeta, wl.q)
         h = ctypes.c_void_p()
-        rc = lib().or_create(ctypes.byref(P), parts, self.np, ctypes.byref(h))
+        rc = self.L.or_create(ctypes.byref(P), parts, self.np, ctypes.byref(h))
         if rc != OR_OK:
             raise OracleError(rc, "or_create")
         self.h = h
-        self.N = int(lib().or_num_cells(h))
+        self.N = int(self.L.or_num_cells(h))
         self.dims = tuple(int(x) for x in wl.dims)
 
     def _pack(self, x, v, w, R, kind, zeta, q):
@@ -201,7 +216,7 @@ class Oracle:
     def __del__(self):
         h = getattr(self, "h", None)
         if h is not None and h.value:
-            lib().or_destroy(h)
+            self.L.or_destroy(h)
             self.h = None
 
     def _check(self, rc, where):
@@ -210,29 +225,29 @@ class Oracle:
 
     # --- Algorithm 1 steps ---
     def map_particles(self):
-        self._check(lib().or_map(self.h), "or_map")
+        self._check(self.L.or_map(self.h), "or_map")
 
     def solve(self, forced_cycles: int = -1, check: bool = True):
         info = np.zeros(4)
-        rc = lib().or_solve(self.h, forced_cycles, _dptr(info))
+        rc = self.L.or_solve(self.h, forced_cycles, _dptr(info))
         if check:
             self._check(rc, "or_solve")
         return {"cycles": int(info[0]), "r0": info[1], "r": info[2], "tol": info[3], "status": rc}
 
     def body_force(self):
-        self._check(lib().or_body_force(self.h), "or_body_force")
+        self._check(self.L.or_body_force(self.h), "or_body_force")
 
     def lbm_step(self):
-        self._check(lib().or_lbm(self.h), "or_lbm")
+        self._check(self.L.or_lbm(self.h), "or_lbm")
 
     def forces(self):
         F = np.zeros(3 * max(1, self.np))
         T = np.zeros(3 * max(1, self.np))
-        self._check(lib().or_forces(self.h, _dptr(F), _dptr(T)), "or_forces")
+        self._check(self.L.or_forces(self.h, _dptr(F), _dptr(T)), "or_forces")
         return F[: 3 * self.np].reshape(-1, 3), T[: 3 * self.np].reshape(-1, 3)
 
     def advance(self):
-        self._check(lib().or_advance(self.h), "or_advance")
+        self._check(self.L.or_advance(self.h), "or_advance")
 
     def step(self, forced_cycles: int = -1):
         self.map_particles()
@@ -247,7 +262,7 @@ class Oracle:
     def field(self, which: int) -> np.ndarray:
         comps = {FIELD_U: 3, FIELD_FB: 3, FIELD_PDF: 19, FIELD_PDF_LAST: 19}.get(which, 1)
         out = np.zeros(comps * self.N)
-        self._check(lib().or_get_field(self.h, which, _dptr(out)), "or_get_field")
+        self._check(self.L.or_get_field(self.h, which, _dptr(out)), "or_get_field")
         nx, ny, nz = self.dims
         if comps == 1:
             return out.reshape(nz, ny, nx)
@@ -255,22 +270,22 @@ class Oracle:
 
     def set_field(self, which: int, values: np.ndarray):
         v = np.ascontiguousarray(values, dtype=np.float64).ravel()
-        self._check(lib().or_set_field(self.h, which, _dptr(v)), "or_set_field")
+        self._check(self.L.or_set_field(self.h, which, _dptr(v)), "or_set_field")
 
     def owner(self) -> np.ndarray:
         out = np.zeros(self.N, dtype=np.int32)
-        lib().or_get_owner(self.h, _iptr(out))
+        self.L.or_get_owner(self.h, _iptr(out))
         nx, ny, nz = self.dims
         return out.reshape(nz, ny, nx)
 
     def nfaces(self) -> np.ndarray:
         out = np.zeros(max(1, self.np), dtype=np.int32)
-        lib().or_get_nfaces(self.h, _iptr(out))
+        self.L.or_get_nfaces(self.h, _iptr(out))
         return out[: self.np]
 
     def particles(self) -> dict:
         arr = (OrParticle * max(1, self.np))()
-        lib().or_get_particles(self.h, arr)
+        self.L.or_get_particles(self.h, arr)
         return {
             "x": np.array([list(arr[i].x) for i in range(self.np)]).reshape(-1, 3),
             "v": np.array([list(arr[i].v) for i in range(self.np)]).reshape(-1, 3),
@@ -280,36 +295,36 @@ class Oracle:
     def set_particles(self, x, v, w):
         wl = self.wl
         arr = self._pack(x, v, w, wl.R, wl.kind, wl.zeta, wl.q)
-        lib().or_set_particles(self.h, arr)
+        self.L.or_set_particles(self.h, arr)
 
     def set_forces(self, F, T):
         F = np.ascontiguousarray(F, dtype=np.float64).ravel()
         T = np.ascontiguousarray(T, dtype=np.float64).ravel()
-        lib().or_set_forces(self.h, _dptr(F), _dptr(T))
+        self.L.or_set_forces(self.h, _dptr(F), _dptr(T))
 
     def vcycle(self, rhs: np.ndarray) -> np.ndarray:
         r = np.ascontiguousarray(rhs, dtype=np.float64).ravel()
         e = np.zeros(self.N)
-        lib().or_vcycle(self.h, _dptr(r), _dptr(e))
+        self.L.or_vcycle(self.h, _dptr(r), _dptr(e))
         return e.reshape(self.dims[::-1])
 
     def smooth(self, rhs: np.ndarray, e0: np.ndarray, sweeps: int) -> np.ndarray:
         r = np.ascontiguousarray(rhs, dtype=np.float64).ravel()
         e_in = np.ascontiguousarray(e0, dtype=np.float64).ravel()
         e = np.zeros(self.N)
-        lib().or_smooth(self.h, _dptr(r), _dptr(e_in), sweeps, _dptr(e))
+        self.L.or_smooth(self.h, _dptr(r), _dptr(e_in), sweeps, _dptr(e))
         return e.reshape(self.dims[::-1])
 
     def residual(self) -> Tuple[float, np.ndarray]:
         r = np.zeros(self.N)
-        n = lib().or_residual(self.h, _dptr(r))
+        n = self.L.or_residual(self.h, _dptr(r))
         return n, r.reshape(self.dims[::-1])
 
     def gradient(self) -> np.ndarray:
         g = np.zeros(3 * self.N)
-        lib().or_gradient(self.h, _dptr(g))
+        self.L.or_gradient(self.h, _dptr(g))
         nx, ny, nz = self.dims
         return g.reshape(3, nz, ny, nx)
 
     def tolerance(self) -> float:
-        return lib().or_tolerance(self.h)
+        return self.L.or_tolerance(self.h)

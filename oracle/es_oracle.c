@@ -9,8 +9,14 @@
  * benchmark may load it; the product path never does.  It shares no code,
  * header, table or constant with the CUDA sources.
  *
- * Everything is double precision, single threaded, plain loops, in the order
- * of Algorithm 1 (Sec. 5.7):
+ * Everything is double precision, plain loops, in the order of Algorithm 1
+ * (Sec. 5.7).  Built with OpenMP (a separate build used only to time the
+ * oracle on all host cores) the loops whose cells are independent -- the
+ * stream-collide, the red-black half sweeps, the level residual, the
+ * restriction and prolongation, the body force -- are shared out among
+ * threads; every cell is still computed by the same arithmetic and every
+ * sum is taken in the same order by one thread, so both builds give the
+ * same bits.  The functions are:
  *   or_map        particle -> grid mapping, PDF reconstruction at uncovered
  *                 cells, assembly of the potential stencil and RHS
  *                 (Sec. 4.2, Sec. 5.4, Sec. 5.5)
@@ -38,6 +44,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_EINVAL -1
@@ -516,6 +525,7 @@ static void rb_half_sweep(or_ctx* c, int l, int colour) {
     const int* m = c->ln[l];
     double h2 = (double)(1 << l) * (double)(1 << l);
     double w = c->P.omega;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < m[2]; k++)
         for (int j = 0; j < m[1]; j++)
             for (int i = 0; i < m[0]; i++) {
@@ -532,6 +542,7 @@ static void rb_half_sweep(or_ctx* c, int l, int colour) {
 static void level_residual(or_ctx* c, int l, double* r) {
     const int* m = c->ln[l];
     double h2 = (double)(1 << l) * (double)(1 << l);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < m[2]; k++)
         for (int j = 0; j < m[1]; j++)
             for (int i = 0; i < m[0]; i++) {
@@ -563,6 +574,7 @@ static void vcycle(or_ctx* c, int l) {
     level_residual(c, l, c->res[l]);
     /* restriction: mean of the 8 children (boundary children carry r = 0) */
     const int* M = c->ln[l + 1];
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < M[2]; k++)
         for (int j = 0; j < M[1]; j++)
             for (int i = 0; i < M[0]; i++) {
@@ -577,6 +589,7 @@ static void vcycle(or_ctx* c, int l) {
     vcycle(c, l + 1);
     /* prolongation: piecewise-constant injection of the coarse correction
      * into unknown cells whose parent is an unknown                          */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < m[2]; k++)
         for (int j = 0; j < m[1]; j++)
             for (int i = 0; i < m[0]; i++) {
@@ -748,6 +761,7 @@ void or_gradient(const or_ctx* c, double* g_out) {
  * cell; zero elsewhere.
  * READING: every unknown cell carries the body force, near-boundary included. */
 int or_body_force(or_ctx* c) {
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < c->n[2]; k++)
         for (int j = 0; j < c->n[1]; j++)
             for (int i = 0; i < c->n[0]; i++) {
@@ -846,6 +860,7 @@ static double wall_population(const or_ctx* c, const double* src, int i, int j, 
 int or_lbm(or_ctx* c) {
     const double* src = c->f[c->cur];
     double* dst = c->f[1 - c->cur];
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < c->n[2]; k++)
         for (int j = 0; j < c->n[1]; j++)
             for (int i = 0; i < c->n[0]; i++) {
@@ -972,6 +987,15 @@ int or_advance(or_ctx* c) {
 #define OR_FIELD_PDF_LAST 7 /* 19 N: field the last step pulled from */
 
 long or_num_cells(const or_ctx* c) { return c->N; }
+
+/* Threads the shared-out loops run on (1 in the serial build). */
+int or_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* Density and velocity of the stored (post-collision) state.  Collision keeps
  * rho and adds exactly f_b of momentum, so u = sum_q c_q f_q - f_b / 2 equals

@@ -52,7 +52,8 @@ EXPORTED = ("es_create", "es_create_with_allocator", "es_destroy", "es_map_parti
             "es_lbm_step", "es_forces", "es_advance", "es_step", "es_get_field", "es_set_field",
             "es_get_particles", "es_set_particles", "es_set_forces", "es_synchronize", "es_lattice", "es_gather",
             "es_gather_noalloc",
-            "es_device_bytes", "es_kernel_launches", "es_last_error", "es_profile_start", "es_profile_stop")
+            "es_device_bytes", "es_kernel_launches", "es_last_error", "es_profile_start", "es_profile_stop",
+            "es_alu_peak")
 
 
 class Params(ctypes.Structure):
@@ -163,10 +164,20 @@ def load():
     L.es_device_bytes.restype = ctypes.c_size_t
     L.es_profile_start.argtypes = [P]
     L.es_profile_stop.argtypes = [P, ctypes.POINTER(KernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.es_alu_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.es_last_error.argtypes = [P]
     L.es_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
+
+
+def alu_peak(precision: int = ES_FP64) -> float:
+    """Measured FMA throughput of the current device in GFLOP/s (es_alu_peak)."""
+    v = ctypes.c_double(0.0)
+    rc = load().es_alu_peak(precision, ctypes.byref(v))
+    if rc != ES_OK:
+        raise EsError(rc, "es_alu_peak", "FMA probe failed")
+    return v.value
 
 
 def lattice() -> Tuple[np.ndarray, np.ndarray]:

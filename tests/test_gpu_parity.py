@@ -645,3 +645,14 @@ def test_radius_and_kind_fixed_after_creation():
     info = g.step()
     assert info["r"] < info["tol"]
     g.close()
+
+
+def test_alu_peak_probe():
+    """es_alu_peak measures FMA throughput: positive, FP32 well above FP64
+    on GB300 (its FP64 pipe runs at a small fraction of the FP32 rate)."""
+    f64 = es.alu_peak(es.ES_FP64)
+    f32 = es.alu_peak(es.ES_MIXED32)
+    print("FMA peaks GFLOP/s: fp64", f64, "fp32", f32)
+    assert f64 > 10.0 and f32 > 4.0 * f64
+    rc = es.load().es_alu_peak(es.ES_MIXED16, None)
+    assert rc == es.ES_EINVAL
