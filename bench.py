@@ -45,6 +45,7 @@ def parse_args():
     ap.add_argument("--n", type=int, default=512, help="cells per axis")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement")
+    ap.add_argument("--no-channel", action="store_true", help="skip the 128^3 channel measurement")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer run (default: --steps)")
     ap.add_argument("--serving", action="store_true",
                     help="serving mode: a stream of independent runs, MIXED32 continuous batching "
@@ -344,6 +345,7 @@ def run_ours(args):
     fp64 = None
     if not args.no_fp64:
         fp64 = measure_fp64(args, dev, barrier)
+    chan = None if args.no_channel else measure_channel(dev)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
@@ -377,6 +379,7 @@ def run_ours(args):
         "clocks": clk,
         "cpu_baseline": base,
         "fp64_form": fp64,
+        "channel128": chan,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -479,6 +482,39 @@ def measure_fp64(args, dev, barrier):
                          "peak_source": "es_alu_peak FP64 FMA probe, CUDA events"},
             "top_kernels_ms": {(r["name"] if r["level"] < 0 else f"{r['name']} L{r['level']}"):
                                r["ms"] / max(r["launches"], 1) for r in top}}
+
+
+def measure_channel(dev, steps=20, warmup=3):
+    """The channel configuration at its own size (128^3, walls at the z
+    faces, 64 charged spheres R=6, lambda_D=3, E=2e-3, 4-level V-cycles to
+    1e-8) in the FP64 and MIXED32 forms: ms per step and MLUPS with CUDA
+    events over `steps` steps after `warmup`."""
+    import torch
+
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import workloads as W
+
+    out = {}
+    for prec, name in ((es.ES_FP64, "fp64"), (es.ES_MIXED32, "mixed32")):
+        wl = W.channel()
+        sim = es.Simulation(wl, prec, device=str(dev))
+        for _ in range(warmup):
+            sim.step()
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        a, b = ev(), ev()
+        cyc = 0
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(sim.stream):
+            a.record(sim.stream)
+            for _ in range(steps):
+                cyc += sim.step()["cycles"]
+            b.record(sim.stream)
+        torch.cuda.synchronize(dev)
+        t = a.elapsed_time(b) / 1e3
+        sim.close()
+        out[name] = {"ms_per_step": t / steps * 1e3, "mlups": wl.n_cells * steps / t / 1e6,
+                     "vcycles_per_step": cyc / steps, "steps": steps}
+    return out
 
 
 def ctypes_sizeof_particle(es):

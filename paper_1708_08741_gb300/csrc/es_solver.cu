@@ -1874,6 +1874,94 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(Level<T> L, const uint8_t
     for (int i = threadIdx.x; i < n; i += blockDim.x) e[i] = se[i];
 }
 
+// Coarsest level, one block, from shared memory, with the unknown cells of
+// each colour packed into a list: every lane of a half sweep updates a cell
+// of that colour, so no lane idles on the other colour or past a short row
+// (the FP64 form is bound by one SM's FP64 pipe here).  Set-up, once per
+// launch: for each unknown cell a 4-byte record (x, y, z and a mask of its
+// unknown neighbours) goes to its colour's list (shared-memory atomics; the
+// order within a colour does not matter, its cells depend only on the other
+// colour), and its inverse diagonal comes from a table of 1 / (diag0 + k),
+// k = #Dirichlet - #Neumann faces (Sec. 5.4, as in level_stencil).  A sweep
+// then needs no index division, no state lookup and no division.  A masked
+// neighbour adds +0, so the sum is taken in level_stencil's order.
+// Records hold coordinates in 8 bits: nx, ny, nz <= 256.
+template <class T>
+__global__ void __launch_bounds__(1024) k_coarse_lists(Level<T> L, const uint8_t* __restrict__ st,
+                                                       const T* __restrict__ rhs, T* __restrict__ e, int sweeps,
+                                                       T omega) {
+    extern __shared__ unsigned char smem[];
+    __shared__ T inv_tab[13];  // 1 / (diag0 + k), k = -6 .. 6
+    __shared__ int cnt[2];
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nxy = nx * ny, n = nxy * nz;
+    T* se = (T*)smem;
+    T* sr = se + n;
+    T* sinv = sr + n;
+    unsigned* rec = (unsigned*)(sinv + n);  // colour 0 from the front, colour 1 from the back
+    if (threadIdx.x < 13) inv_tab[threadIdx.x] = (T)1 / (L.diag0 + (T)((int)threadIdx.x - 6));
+    if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int x = i % nx, y = (i / nx) % ny, z = i / nxy;
+        const uint8_t k = st[i];
+        se[i] = (T)0;
+        sr[i] = rhs[i];
+        T inv = (T)0;
+        if ((k & ST_KIND) == ST_UNKNOWN) {
+            int dk = 0;
+            unsigned m = 0;
+            const int v[3] = {x, y, z}, n3[3] = {nx, ny, nz}, stride[3] = {1, nx, nxy};
+            for (int a = 0; a < 3; a++)
+                for (int sd = 0; sd < 2; sd++) {
+                    int p = v[a] + (sd ? 1 : -1);
+                    if (p < 0 || p >= n3[a]) {
+                        if (!L.per[a]) {
+                            dk += L.pot_bc[2 * a + sd] == ES_POT_DIRICHLET ? 1 : -1;
+                            continue;
+                        }
+                        p = p < 0 ? p + n3[a] : p - n3[a];
+                    }
+                    const uint8_t kn = st[i + (p - v[a]) * stride[a]] & ST_KIND;
+                    if (kn == ST_UNKNOWN)
+                        m |= 1u << (2 * a + sd);
+                    else
+                        dk += kn == ST_DIR ? 1 : -1;
+                }
+            inv = inv_tab[dk + 6];
+            const int col = (x + y + z) & 1;
+            const int pos = atomicAdd(&cnt[col], 1);
+            rec[col == 0 ? pos : n - 1 - pos] = (unsigned)x | ((unsigned)y << 8) | ((unsigned)z << 16) | (m << 24);
+        }
+        sinv[i] = inv;
+    }
+    __syncthreads();
+    const int c0 = cnt[0], c1 = cnt[1];
+    for (int s = 0; s < sweeps; s++)
+        for (int colour = 0; colour < 2; colour++) {
+            const int m_ = colour == 0 ? c0 : c1;
+            for (int j = threadIdx.x; j < m_; j += blockDim.x) {
+                const unsigned r = rec[colour == 0 ? j : n - 1 - j];
+                const int x = r & 0xFF, y = (r >> 8) & 0xFF, z = (r >> 16) & 0xFF;
+                const unsigned m = r >> 24;
+                const int i = x + nx * y + nxy * z;
+                const int xm = x == 0 ? nx - 1 : -1, xp = x == nx - 1 ? 1 - nx : 1;
+                const int ym = y == 0 ? (ny - 1) * nx : -nx, yp = y == ny - 1 ? (1 - ny) * nx : nx;
+                const int zm = z == 0 ? (nz - 1) * nxy : -nxy, zp = z == nz - 1 ? (1 - nz) * nxy : nxy;
+                T o = (T)0;
+                o += (m & 1) ? se[i + xm] : (T)0;
+                o += (m & 2) ? se[i + xp] : (T)0;
+                o += (m & 4) ? se[i + ym] : (T)0;
+                o += (m & 8) ? se[i + yp] : (T)0;
+                o += (m & 16) ? se[i + zm] : (T)0;
+                o += (m & 32) ? se[i + zp] : (T)0;
+                const T gs = (L.h2 * sr[i] + o) * sinv[i];
+                se[i] = ((T)1 - omega) * se[i] + omega * gs;
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) e[i] = se[i];
+}
+
 template <class T>
 __global__ void k_zero(T* p, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2164,9 +2252,19 @@ Level<T> level_desc(const es_ctx* c, int l) {
     return L;
 }
 
+// The coarsest level runs in one block from shared memory: from packed
+// per-colour lists (k_coarse_lists: e, rhs, inverse diagonal, one 4-byte
+// record per cell) when that fits, else k_coarse_solve (e, rhs, states).
+size_t coarse_cells(const es_ctx* c) { return (size_t)c->ln[c->L - 1][0] * c->ln[c->L - 1][1] * c->ln[c->L - 1][2]; }
+
+bool coarse_by_lists(const es_ctx* c, size_t tsize) {
+    const int* m = c->ln[c->L - 1];
+    return m[0] <= 256 && m[1] <= 256 && m[2] <= 256 && coarse_cells(c) * (3 * tsize + 4) <= 200 * 1024;
+}
+
 size_t coarse_smem_bytes(const es_ctx* c, size_t tsize) {
-    size_t n = (size_t)c->ln[c->L - 1][0] * c->ln[c->L - 1][1] * c->ln[c->L - 1][2];
-    return n * (2 * tsize + 1);
+    const size_t n = coarse_cells(c);
+    return coarse_by_lists(c, tsize) ? n * (3 * tsize + 4) : n * (2 * tsize + 1);
 }
 
 // Levels up to this many cells (near_list_cells, default 2^21) update their
@@ -2378,7 +2476,10 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             size_t sm = coarse_smem_bytes(c, sizeof(T));
             if (sm <= 200 * 1024) {
                 ProfScope ps(c, "coarse_solve", l, nl * (2.0 * ts + 1.0));
-                k_coarse_solve<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
+                if (coarse_by_lists(c, sizeof(T)))
+                    k_coarse_lists<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
+                else
+                    k_coarse_solve<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
                 count(c);
             } else {
                 if (c->P.coarse_sweeps == 0) {
@@ -2474,8 +2575,10 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
 template <class T>
 void set_coarse_smem(const es_ctx* c) {
     size_t sm = coarse_smem_bytes(c, sizeof(T));
-    if (sm > 48 * 1024 && sm <= 200 * 1024)
+    if (sm > 48 * 1024 && sm <= 200 * 1024) {
         cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_coarse_lists<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    }
 }
 
 }  // namespace

@@ -35,7 +35,14 @@ U, and Delta_r U_Stokes = 1 / K - 1 (the velocity the same force would give
 relative to Stokes' F / (6 pi mu R)).
 Lattice units: dx = dt = rho = eps = 1, mu = (tau - 1/2) / 3.
 
+A third way (``box_extrapolated``) takes the box out with the
+electrophoretic sphere itself: periodic runs at several box sizes,
+extrapolated to an unbounded box in (R/L)^3, the order in which the
+periodic images of a force-free sphere with its screened double layer act
+on it.
+
     python -m paper_1708_08741_gb300.validation [--n 128] [--radius 4] [--kR 0.5] [--walls free-slip]
+    python -m paper_1708_08741_gb300.validation --extrapolate 64 96 128 [--kR 0.265 0.5 0.8]
 """
 from __future__ import annotations
 
@@ -140,7 +147,7 @@ def dragged_velocity(wl, f0: float, steps: int, sample_every: int = 100, precisi
                      device: str = "cuda:0") -> dict:
     """The first sphere of ``wl`` (uncharged) moved by the constant force
     (f0, 0, 0) on top of its hydrodynamic force; mean x velocity over the
-    second half of the samples."""
+    second half of the samples, and every sample."""
     sim = es.Simulation(wl, precision, device=device)
     samples = []
     try:
@@ -160,7 +167,33 @@ def dragged_velocity(wl, f0: float, steps: int, sample_every: int = 100, precisi
     tail = np.array(samples[len(samples) // 2:])
     mean = float(tail.mean())
     return {"U": mean, "spread": float((tail.max() - tail.min()) / abs(mean)) if mean else float("nan"),
-            "samples": len(samples)}
+            "samples": len(samples), "U_samples": [float(v) for v in samples]}
+
+
+def box_extrapolated(R: float = 4.0, kR: float = 0.5, sizes=(64, 96, 128), tau: float = 6.0, zeta: float = 1.0,
+                     E: float = 2.5e-3, steps: int = 12000, device: str = "cuda:0") -> dict:
+    """Henry deviation of the electrophoretic sphere with the box taken out
+    by the sphere's own runs instead of a Stokes-drag run: the periodic
+    electrophoretic run (velocity relative to the mean fluid velocity) at
+    several box sizes L, fitted by least squares to U(L) = U_inf + b (R/L)^3
+    -- the far field of an electrophoretic sphere decays like that of a
+    dipole, 1/r^3, so its periodic images shift it by O((R/L)^3), where a
+    dragged sphere's Stokeslet images shift it by O(R/L) -- and Delta_r U_inf
+    = (U_inf - U_EP) / U_EP."""
+    mu = (tau - 0.5) / 3.0
+    kappa = kR / R
+    u_henry = henry_velocity(zeta, E, 1.0, mu, kR)
+    runs = []
+    for n in sizes:
+        levels = 5 if n % 32 == 0 else 4
+        r = terminal_velocity(_box(n, R, tau, kappa, E, zeta, (0.0, 0.0, 0.0), levels), steps, device=device)
+        runs.append({"n": n, "U": r["U"], "spread": r["spread"], "dU": (r["U"] - u_henry) / u_henry})
+    x = np.array([(R / r["n"]) ** 3 for r in runs])
+    y = np.array([r["U"] for r in runs])
+    A = np.stack([np.ones_like(x), x], 1)
+    (u_inf, b), *_ = np.linalg.lstsq(A, y, rcond=None)
+    return {"R": R, "kR": kR, "tau": tau, "zeta": zeta, "E": E, "steps": steps, "U_henry": u_henry,
+            "boxes": runs, "U_inf": float(u_inf), "b": float(b), "dU_inf": float((u_inf - u_henry) / u_henry)}
 
 
 def validate_free_slip(n: int = 128, R: float = 4.0, kR: float = 0.5, tau: float = 6.0, zeta: float = 1.0,
@@ -191,11 +224,16 @@ def main():
     ap.add_argument("--kR", type=float, nargs="+", default=[0.265, 0.5, 0.8])
     ap.add_argument("--steps", type=int, default=12000)
     ap.add_argument("--walls", choices=["periodic", "free-slip"], default="periodic")
+    ap.add_argument("--extrapolate", type=int, nargs="+", default=None, metavar="L",
+                    help="box sizes of the periodic electrophoretic runs extrapolated to an unbounded box")
     a = ap.parse_args()
-    run = validate_free_slip if a.walls == "free-slip" else validate
     for R in a.radius:
         for kR in a.kR:
-            print(json.dumps(run(a.n, R, kR, steps=a.steps)), flush=True)
+            if a.extrapolate:
+                res = box_extrapolated(R, kR, sizes=a.extrapolate, steps=a.steps)
+            else:
+                res = (validate_free_slip if a.walls == "free-slip" else validate)(a.n, R, kR, steps=a.steps)
+            print(json.dumps(res), flush=True)
 
 
 if __name__ == "__main__":

@@ -36,9 +36,10 @@ def rel_l2(a, b):
 class Pair:
     """A GPU simulation and an oracle simulation of the same workload."""
 
-    def __init__(self, wl, precision=es.ES_FP64, overrides=None, lib_overrides=None):
+    def __init__(self, wl, precision=es.ES_FP64, overrides=None, lib_overrides=None, omp=False):
         self.wl = wl
-        self.o = oracle.Oracle(wl, overrides)
+        # (omp: the oracle's OpenMP build, the same bits on all host cores)
+        self.o = oracle.Oracle(wl, overrides, omp=omp)
         self.g = es.Simulation(wl, precision, overrides={**(overrides or {}), **(lib_overrides or {})})
         self.x0 = np.array(wl.x, dtype=np.float64).reshape(-1, 3).copy()
         self.last_forces = None

@@ -300,6 +300,32 @@ def test_coupled_channel_fp64():
         assert r[k] < FP64_TOL, (k, r[k])
 
 
+def test_channel_128_full_size_fp64():
+    """The channel configuration at its own size: 128^3, no-slip and
+    zero-flux walls at the z faces, periodic x and y, 64 moving spheres of
+    radius 6 with charges in [0.5, 1.5], lambda_D = 3, E = 2e-3, 4 levels to
+    1e-8.  FP64 against the oracle (its OpenMP build), 5 coupled steps with
+    the oracle's cycle counts: 1e-12."""
+    p = Pair(_moving(W.channel()), omp=True)
+    for _ in range(5):
+        info, ginfo, _, _ = p.step()
+        assert ginfo["cycles"] == info["cycles"]
+    r = p.compare()
+    assert r["owner_equal"]
+    for k in ("psi", "u", "x", "v", "w", "F", "T"):
+        assert r[k] < FP64_TOL, (k, r[k])
+
+
+def test_channel_128_full_size_mixed32():
+    """The same 128^3 channel in MIXED32, each side on its own
+    tolerance-driven solver, 20 steps: 1e-4 on every quantity."""
+    p = Pair(_moving(W.channel()), es.ES_MIXED32, omp=True)
+    for _ in range(20):
+        _, ginfo, _, _ = p.step(forced=False)
+        assert ginfo["status"] == es.ES_OK and ginfo["r"] < ginfo["tol"]
+    _assert_reduced(p.compare())
+
+
 def _slip(wl, faces):
     wl.wall_slip = faces
     return wl
