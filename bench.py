@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=24, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="serving: resident runs (MIXED32 server)")
     ap.add_argument("--max-run-steps", type=int, default=1000, help="serving: step cap per run")
+    ap.add_argument("--max-edge", type=int, default=96, help="serving: largest grid edge of the request mix")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving measurement")
     ap.add_argument("--smoother", choices=["fused", "two_pass"], default="two_pass",
                     help="execution of a red-black sweep (same arithmetic)")
     ap.add_argument("--mg-storage", choices=["native", "fp16"], default="native",
@@ -346,6 +348,9 @@ def run_ours(args):
     if not args.no_fp64:
         fp64 = measure_fp64(args, dev, barrier)
     chan = None if args.no_channel else measure_channel(dev)
+    serv = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serv = serving_measure(12, 8, 600, (32, 64), str(dev))
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
@@ -380,6 +385,7 @@ def run_ours(args):
         "cpu_baseline": base,
         "fp64_form": fp64,
         "channel128": chan,
+        "serving": serv,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -523,54 +529,68 @@ def ctypes_sizeof_particle(es):
     return ctypes.sizeof(es.Particle)
 
 
-def run_serving(args):
-    """Serving: the same seeded request stream (Poisson arrivals at 20/s,
-    grids log-uniform in [32, 96] per axis, 1-200 spheres of radius 3-8,
-    Debye length 2-8, field 5e-4..3e-3, zeta 0.5-2, periodic) served by the
-    MIXED32 continuous-batching server and by FP64 one run at a time; a run
-    ends when its mean particle velocity changes by < 1e-4 (relative) per 100
-    steps or at the step cap."""
-    import torch
-
-    import paper_1708_08741_gb300 as es
+def serving_measure(n_requests, slots, max_steps, edge_range, device, seed=5):
+    """One seeded request stream (Poisson arrivals at 20/s, grid edges
+    log-uniform in edge_range per axis, 1-200 spheres of radius 3-8, Debye
+    length 2-8, field 5e-4..3e-3, zeta 0.5-2, periodic; a run ends when its
+    mean particle velocity changes by < 1e-4 relative per 100 steps, or at
+    the step cap) served four ways, so that batching and precision are seen
+    apart: MIXED32 with `slots` runs resident (each on its own host thread
+    and stream), MIXED32 with `slots` runs stepped in lockstep and their
+    stream-collides batched into one launch, MIXED32 one run at a time, and
+    FP64 one run at a time.  Accuracy: every server's final mean particle
+    velocities against FP64's."""
     from paper_1708_08741_gb300 import serving as S
+
+    reqs = S.request_stream(n_requests, rate=20.0, seed=seed, edge_range=edge_range)
+    kw = dict(check_every=100, rel_tol=1e-4, max_steps=max_steps)
+    import paper_1708_08741_gb300 as es
+
+    servers = {
+        f"mixed32_{slots}_slots": S.gpu_server(es.ES_MIXED32, slots=slots, device=device, **kw),
+        f"mixed32_{slots}_slots_batched": S.gpu_batch_server(es.ES_MIXED32, slots=slots, device=device, **kw),
+        "mixed32_1_slot": S.gpu_server(es.ES_MIXED32, slots=1, device=device, **kw),
+        "fp64_1_slot": S.gpu_server(es.ES_FP64, slots=1, device=device, **kw),
+    }
+    results = {name: srv.serve(reqs) for name, srv in servers.items()}
+    ref = results["fp64_1_slot"]
+    out = {}
+    for name, res in results.items():
+        summ = S.summarize(res)
+        errs = []
+        for a, b in zip(res, ref):
+            if a.steps == b.steps and a.error is None and b.error is None:
+                errs.append(float(np.linalg.norm(a.v_mean - b.v_mean) / max(np.linalg.norm(b.v_mean), 1e-300)))
+        summ["v_mean_rel_err_vs_fp64"] = {"median": float(np.median(errs)) if errs else None,
+                                          "max": max(errs) if errs else None, "compared_runs": len(errs)}
+        summ["peak_resident"] = servers[name].peak_resident
+        out[name] = summ
+    base = out["fp64_1_slot"]
+    for name, summ in out.items():
+        summ["runs_per_s_over_fp64"] = summ["runs_per_s"] / base["runs_per_s"]
+        summ["p99_fp64_over_this"] = base["p99_latency_s"] / summ["p99_latency_s"]
+    return {"config": {"requests": n_requests, "rate_per_s": 20.0, "grid_edges": list(edge_range),
+                       "spheres": "1-200, R 3-8 (<= 5 % solid)", "lambda_D": "2-8", "E": "5e-4..3e-3",
+                       "zeta": "0.5-2", "steady": "1e-4 per 100 steps", "step_cap": max_steps, "res_rf": 1e-8,
+                       "seed": seed},
+            "servers": out}
+
+
+def run_serving(args):
+    """Serving mode: one JSON line with the four servers of serving_measure."""
+    import torch
 
     rank, local, world = rank_info()
     if rank != 0:
         return
     torch.cuda.set_device(local)
-    reqs = S.request_stream(args.requests, rate=20.0, seed=5, edge_range=(32, 96))
-    kw = dict(check_every=100, rel_tol=1e-4, max_steps=args.max_run_steps)
-    mixed = S.gpu_server(es.ES_MIXED32, slots=args.slots, device=f"cuda:{local}", **kw)
-    r_mixed = mixed.serve(reqs)
-    fp64 = S.gpu_server(es.ES_FP64, slots=1, device=f"cuda:{local}", **kw)
-    r_fp64 = fp64.serve(reqs)
-    s_m, s_f = S.summarize(r_mixed), S.summarize(r_fp64)
-    # accuracy of the served results: final mean particle velocity against FP64
-    errs, worst = [], []
-    for q, a, b in zip(reqs, r_mixed, r_fp64):
-        if a.steps == b.steps and a.error is None and b.error is None:
-            e = float(np.linalg.norm(a.v_mean - b.v_mean) / max(np.linalg.norm(b.v_mean), 1e-300))
-            errs.append(e)
-            worst.append({"rid": q.rid, "rel_err": e, "dims": list(q.wl.dims), "spheres": q.wl.n_particles,
-                          "steps": a.steps})
-    worst.sort(key=lambda d: -d["rel_err"])
+    m = serving_measure(args.requests, args.slots, args.max_run_steps, (32, args.max_edge), f"cuda:{local}")
+    best = m["servers"][f"mixed32_{args.slots}_slots"]
     line = {
         "metric": "served runs/s and p50/p99 time to steady velocity, MIXED32 continuous batching vs FP64 "
                   "one run at a time",
-        "value": s_m["runs_per_s"], "unit": "runs/s", "higher_is_better": True, "n_gpus": 1,
-        "mixed32_batched": {**s_m, "slots": args.slots, "peak_resident": mixed.peak_resident},
-        "fp64_one_at_a_time": s_f,
-        "speedup_runs_per_s": s_m["runs_per_s"] / s_f["runs_per_s"],
-        "p99_ratio_fp64_over_mixed": s_f["p99_latency_s"] / s_m["p99_latency_s"],
-        "v_mean_rel_err_vs_fp64": {"max": max(errs) if errs else None,
-                                   "median": float(np.median(errs)) if errs else None,
-                                   "compared_runs": len(errs), "worst": worst[:3]},
-        "data": "synthetic",
-        "config": {"workload": f"{args.requests} requests, Poisson 20/s, grid edges log-uniform [32, 96], "
-                               f"1-200 spheres R 3-8 (<= 5 % solid), lambda_D 2-8, E 5e-4..3e-3, zeta 0.5-2, "
-                               f"periodic; steady at 1e-4 per 100 steps, cap {args.max_run_steps} steps",
-                   "res_rf": 1e-8},
+        "value": best["runs_per_s"], "unit": "runs/s", "higher_is_better": True, "n_gpus": 1,
+        "data": "synthetic", **m,
     }
     print(json.dumps(line), flush=True)
 

@@ -129,6 +129,10 @@ typedef struct {
                            0 selects the default ES_NEAR_LIST_CELLS; < 0 is
                            ES_EINVAL.  (The colour-split finest level always uses
                            the lists.)                                             */
+    int lbm_block[2];   /* thread-block shape of the stream-collide: cells along x
+                           (a multiple of 32 in 32..256) by rows along y, at most
+                           256 threads; {0, 0} selects {128, 1}.  The same result
+                           for every shape (the autotuner times them).         */
     int fast_update_cells; /* reduced forms with the colour-split finest level: on
                            grids of at least this many cells a tolerance-driven
                            solve that starts within 5000 x tol updates the
@@ -248,6 +252,19 @@ int es_potential_solve(es_ctx* ctx, int forced_cycles, es_solve_info* info);
  * LBMMovWall), resting bounce-back at no-slip walls and specular
  * reflection at free-slip walls (wall_slip).                              */
 int es_lbm_step(es_ctx* ctx);
+
+/* es_lbm_step for n resident runs at once (the paper has no counterpart:
+ * serving many small independent runs).  One persistent launch steps every
+ * run's stream-collide from a work table of the runs' fields and parameters
+ * (tiles of 32 cells x 4 rows, any mix of grid sizes), each cell exactly as
+ * es_lbm_step computes it, so a run gives the same bits alone and batched.
+ * The launch goes on ctxs[0]'s stream after the work already issued on every
+ * context's stream, and each context's later work waits for it (CUDA
+ * events), so the contexts stay stream-ordered.  1 <= n <= ES_LBM_BATCH_MAX;
+ * all contexts on one device, of one precision, without free-slip faces, no
+ * context twice (ES_EINVAL otherwise). */
+#define ES_LBM_BATCH_MAX 32
+int es_lbm_step_batch(es_ctx* const* ctxs, int n);
 
 /* Algorithm 1, "apply hydrodynamic force to particles" (Sec. 4.2, Eq.
  * LBMhydrodynForce, torque by the same sum with (x_s - X) x dF) plus the

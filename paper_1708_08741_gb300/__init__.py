@@ -53,7 +53,7 @@ EXPORTED = ("es_create", "es_create_with_allocator", "es_destroy", "es_map_parti
             "es_get_particles", "es_set_particles", "es_set_forces", "es_synchronize", "es_lattice", "es_gather",
             "es_gather_noalloc",
             "es_device_bytes", "es_kernel_launches", "es_last_error", "es_profile_start", "es_profile_stop",
-            "es_alu_peak")
+            "es_alu_peak", "es_lbm_step_batch")
 
 
 class Params(ctypes.Structure):
@@ -82,6 +82,7 @@ class Params(ctypes.Structure):
         ("phi_t", ctypes.c_double),
         ("fine_layout", ctypes.c_int),
         ("near_list_cells", ctypes.c_int),
+        ("lbm_block", ctypes.c_int * 2),
         ("fast_update_cells", ctypes.c_int),
     ]
 
@@ -165,6 +166,7 @@ def load():
     L.es_profile_start.argtypes = [P]
     L.es_profile_stop.argtypes = [P, ctypes.POINTER(KernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.es_alu_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.es_lbm_step_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
     L.es_last_error.argtypes = [P]
     L.es_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -397,6 +399,16 @@ class Simulation:
         F = np.ascontiguousarray(F, dtype=np.float64).ravel()
         T = np.ascontiguousarray(T, dtype=np.float64).ravel()
         self._check(self.lib.es_set_forces(self.h, F.ctypes.data, T.ctypes.data, self.np), "es_set_forces")
+
+
+def lbm_step_batch(sims) -> None:
+    """One stream-collide step of every simulation in one launch
+    (es_lbm_step_batch); the same result as sim.lbm_step() on each."""
+    sims = list(sims)
+    arr = (ctypes.c_void_p * len(sims))(*[s.h.value for s in sims])
+    rc = load().es_lbm_step_batch(arr, len(sims))
+    if rc != ES_OK:
+        raise EsError(rc, "es_lbm_step_batch", load().es_last_error(sims[0].h if sims else None).decode())
 
 
 def device_bytes(wl, precision: int = ES_FP64, overrides: Optional[dict] = None) -> int:

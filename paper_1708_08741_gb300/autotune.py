@@ -1,14 +1,19 @@
-"""Autotuner for the multigrid smoothing schedule of a workload.
+"""Autotuner for the multigrid smoothing schedule and the stream-collide's
+block shape of a workload.
 
 The V-cycle's pre- and post-smoothing sweep counts (nu1, nu2) and the way a
 red-black sweep is executed (two in-place passes, or one fused pass on
 levels whose x extent is a multiple of 128) trade cycles per step against
 time per cycle.  Every candidate solves to the same tolerance (the
 workload's RES_RF), so the fastest candidate per step is chosen at equal
-accuracy.  Each candidate runs ``warmup`` untimed steps and ``steps`` timed
-steps from the same initial state on the GPU, timed with CUDA events on the
-run's stream.  Results are cached per grid shape, level count and sphere
-count class, so a server tunes a request class once.
+accuracy.  Then, with that schedule, the stream-collide's thread-block
+shape (es_params.lbm_block: cells along x by rows along y) is timed: a
+128-wide row leaves most threads idle on a 40-cell grid, where 32 x 4 keeps
+them busy; every shape gives the same bits.  Each candidate runs ``warmup``
+untimed steps and ``steps`` timed steps from the same initial state on the
+GPU, timed with CUDA events on the run's stream.  Results are cached per
+grid shape, level count and sphere count class, so a server tunes a request
+class once.
 """
 from __future__ import annotations
 
@@ -29,6 +34,17 @@ def candidates(wl, nus: Sequence[Tuple[int, int]] = DEFAULT_NU) -> list:
     if int(wl.dims[0]) % 128 == 0:
         smoothers.append(es.ES_SMOOTH_FUSED)
     return [dict(nu1=a, nu2=b, smoother=s) for (a, b), s in itertools.product(nus, smoothers)]
+
+
+# stream-collide block shapes (x cells, y rows); (0, 0) is the library default 128 x 1
+DEFAULT_SHAPES = ((0, 0), (32, 4), (64, 2), (32, 8))
+
+
+def block_shapes(wl, shapes: Sequence[Tuple[int, int]] = DEFAULT_SHAPES) -> list:
+    """The stream-collide block shapes worth trying for a workload (those no
+    wider than its x extent rounded up to a warp, plus the default)."""
+    nx = int(wl.dims[0])
+    return [dict(lbm_block=tuple(s)) for s in shapes if s == (0, 0) or s[0] <= max(32, ((nx + 31) // 32) * 32)]
 
 
 def choose(times: Dict[int, float]) -> int:
@@ -59,26 +75,35 @@ class Autotuner:
     fails, e.g. does not converge within max_cycles).
     """
 
-    def __init__(self, measure: Callable, cands: Optional[Callable] = None):
+    def __init__(self, measure: Callable, cands: Optional[Callable] = None, shapes: Optional[Callable] = None):
         self.measure = measure
         self.cands = cands or candidates
+        self.shapes = shapes if shapes is not None else block_shapes
         self.cache: Dict[tuple, dict] = {}
         self.log: Dict[tuple, list] = {}
 
-    def tune(self, wl) -> dict:
-        key = class_key(wl)
-        if key in self.cache:
-            return self.cache[key]
-        cs = self.cands(wl)
+    def _best(self, wl, cs, log):
         times = {}
         for i, ov in enumerate(cs):
             try:
                 times[i] = float(self.measure(wl, ov))
             except Exception:
                 times[i] = math.inf
-        best = cs[choose(times)]
+            log.append((cs[i], times[i]))
+        return cs[choose(times)]
+
+    def tune(self, wl) -> dict:
+        """The schedule first, then (with it) the block shape."""
+        key = class_key(wl)
+        if key in self.cache:
+            return self.cache[key]
+        log: list = []
+        best = self._best(wl, self.cands(wl), log)
+        shapes = self.shapes(wl) if self.shapes else []
+        if len(shapes) > 1:
+            best = self._best(wl, [{**best, **sh} for sh in shapes], log)
         self.cache[key] = best
-        self.log[key] = [(cs[i], times[i]) for i in range(len(cs))]
+        self.log[key] = log
         return best
 
 

@@ -73,6 +73,11 @@ int validate(const es_params* P, const es_particle* parts, int n, std::string& w
     if (!(P->phi_t >= 0.0) || std::isinf(P->phi_t)) return why = "phi_t must be finite and >= 0", ES_EINVAL;
     if (P->fine_layout != ES_LAYOUT_AUTO && P->fine_layout != ES_LAYOUT_NATURAL)
         return why = "fine_layout must be ES_LAYOUT_AUTO or ES_LAYOUT_NATURAL", ES_EINVAL;
+    if (P->lbm_block[0] != 0 || P->lbm_block[1] != 0) {
+        const int bx = P->lbm_block[0], by = P->lbm_block[1];
+        if (bx < 32 || bx > 256 || bx % 32 != 0 || by < 1 || bx * by > 256)
+            return why = "lbm_block must be 0 x 0 or x in 32..256 (a multiple of 32) with x * y <= 256", ES_EINVAL;
+    }
     if (P->near_list_cells < 0 || P->fast_update_cells < 0)
         return why = "near_list_cells and fast_update_cells must be >= 0", ES_EINVAL;
     if (P->phi_t > 0.0 && (P->precision != ES_FP64 || P->levels != 1))
@@ -189,6 +194,10 @@ void release(es_ctx* c) {
             cudaGraphExecDestroy(c->vgraph[w]);
             c->vgraph[w] = nullptr;
         }
+    if (c->ev_sync) {
+        cudaEventDestroy(c->ev_sync);
+        c->ev_sync = nullptr;
+    }
 }
 
 // Reads the residual norm and the device status word (synchronises).
@@ -555,6 +564,26 @@ int es_lbm_step(es_ctx* c) {
     ES_CUDA(c, launch_lbm(c));
     c->last_src = c->cur;
     c->cur = 1 - c->cur;
+    return ES_OK;
+}
+
+int es_lbm_step_batch(es_ctx* const* ctxs, int n) {
+    if (!ctxs || n < 1 || n > ES_LBM_BATCH_MAX) return fail(nullptr, ES_EINVAL, "need 1..ES_LBM_BATCH_MAX contexts");
+    for (int i = 0; i < n; i++) {
+        es_ctx* c = ctxs[i];
+        if (!c) return fail(nullptr, ES_EINVAL, "a context is NULL");
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == c) return fail(c, ES_EINVAL, "a context appears twice in the batch");
+        if (c->P.precision != ctxs[0]->P.precision) return fail(c, ES_EINVAL, "the contexts differ in precision");
+        if (c->device != ctxs[0]->device) return fail(c, ES_EINVAL, "the contexts are on different devices");
+        if (c->slip) return fail(c, ES_EINVAL, "free-slip walls are not batched");
+    }
+    const cudaError_t e = launch_lbm_batch(ctxs, n);
+    if (e != cudaSuccess) return cuda_fail(ctxs[0], e, "es_lbm_step_batch");
+    for (int i = 0; i < n; i++) {
+        ctxs[i]->last_src = ctxs[i]->cur;
+        ctxs[i]->cur = 1 - ctxs[i]->cur;
+    }
     return ES_OK;
 }
 

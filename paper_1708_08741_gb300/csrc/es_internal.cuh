@@ -145,6 +145,7 @@ struct es_ctx {
     cudaGraphExec_t vgraph[2];          // the V-cycle from zero / warm-started, captured on first use
     unsigned long long vgraph_kernels[2];  // kernel launches in each graph
     bool vgraph_off;                    // capture failed once: launch directly
+    cudaEvent_t ev_sync;                // orders the context's stream against a batched launch
     std::vector<double> h_R;  // radii and kinds as created (fixed for the context's life)
     std::vector<int> h_kind;
     double lambda_e, lambda_o;
@@ -191,6 +192,7 @@ cudaError_t materialize_body_force(es_ctx* c);      // the whole stored f_b, whe
 bool fb_fused(const es_ctx* c);                     // the stream-collide evaluates f_b from psi
 // lbm and particles (es_lbm.cu)
 cudaError_t launch_lbm(es_ctx* c);
+cudaError_t launch_lbm_batch(es_ctx* const* cs, int n);  // es_lbm_step_batch
 cudaError_t launch_forces(es_ctx* c);
 cudaError_t launch_advance(es_ctx* c);
 cudaError_t launch_fill_rest(es_ctx* c);

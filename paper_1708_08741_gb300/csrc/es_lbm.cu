@@ -99,16 +99,13 @@ struct FbPsi {
 // HBM: the cell reads 4 bytes of psi (the neighbours' come from cache)
 // instead of 12 of stored f_b.  Cells next to obstacles or walls read the
 // stored field (their D3Q7 ghost-value gradient, k_body_force_near).
-template <class S, bool SLIP, bool FBPSI = false, class C = typename Store<S>::C>
-__global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
-                                             const uint8_t* __restrict__ flags, const int32_t* __restrict__ owner,
-                                             const DParticle* __restrict__ part, const float* __restrict__ partf,
-                                             const C* __restrict__ fb, C ax, C ay, C az, C lam_e, C lam_o,
-                                             int slip_faces, FbPsi fp) {
+template <class S, bool SLIP, bool FBPSI, class C = typename Store<S>::C>
+__device__ __forceinline__ void lbm_cell(const Grid& g, const Streams<S>& P, const uint8_t* __restrict__ flags,
+                                         const int32_t* __restrict__ owner, const DParticle* __restrict__ part,
+                                         const float* __restrict__ partf, const C* __restrict__ fb, C ax, C ay,
+                                         C az, C lam_e, C lam_o, int slip_faces, const FbPsi& fp, int x, int y,
+                                         int z) {
     using St = Store<S>;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= g.nx) return;
     const unsigned N = (unsigned)g.N;
     const int nx = g.nx, nxy = g.nx * g.ny;
     const int c = x + nx * (y + g.ny * z);
@@ -255,6 +252,81 @@ __global__ void __launch_bounds__(128) k_lbm(Grid g, const Streams<S> P,
         const C odd = lam_o * (fo - eq_o) + ao * Fo;
         P.dst[q][c] = St::st(q, f[q] + even + odd);
         P.dst[q + 9][c] = St::st(q + 9, f[q + 9] + even - odd);
+    }
+}
+
+// One thread per cell; a block covers blockDim.x cells of blockDim.y rows
+// (the shape is a parameter: es_params.lbm_block).
+// (the reduced forms keep 40 registers a thread, 1,536 threads per SM: more
+// registers and fewer threads measured slower)
+template <class S, bool SLIP, bool FBPSI = false, class C = typename Store<S>::C>
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 3 : 6) k_lbm(Grid g, const Streams<S> P, const uint8_t* __restrict__ flags,
+                                             const int32_t* __restrict__ owner, const DParticle* __restrict__ part,
+                                             const float* __restrict__ partf, const C* __restrict__ fb, C ax, C ay,
+                                             C az, C lam_e, C lam_o, int slip_faces, FbPsi fp) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    lbm_cell<S, SLIP, FBPSI>(g, P, flags, owner, part, partf, fb, ax, ay, az, lam_e, lam_o, slip_faces, fp, x, y,
+                             z);
+}
+
+// Several resident runs stepped by one persistent launch (es_lbm_step_batch):
+// a work table of the runs' fields and parameters, passed by value, and a
+// flat index of tiles of 32 cells x 4 rows over all runs (run r owns tiles
+// tile0[r] .. tile0[r+1]-1).  Blocks of 128 threads stride over the tiles;
+// each cell runs the same lbm_cell as k_lbm, so a run gives the same bits
+// alone and in a batch.
+constexpr int kBatchTileX = 32, kBatchTileY = 4;
+
+template <class S>
+struct BatchRun {
+    using C = typename Store<S>::C;
+    Grid g;
+    Streams<S> P;
+    const uint8_t* flags;
+    const int32_t* owner;
+    const DParticle* part;
+    const float* partf;
+    const C* fb;
+    C ax, ay, az, lam_e, lam_o;
+    FbPsi fp;
+    int lazy;        // f_b from psi inside the stream-collide
+    int tiles_x;     // tiles per row of tiles: ceil(nx / 32)
+    int tiles_y;     // rows of tiles per plane: ceil(ny / 4)
+    long long tile0; // first tile of the run
+};
+
+template <class S>
+struct BatchTable {
+    BatchRun<S> r[ES_LBM_BATCH_MAX];
+    int n;
+    long long ntiles;
+};
+
+template <class S>
+__global__ void __launch_bounds__(kBatchTileX * kBatchTileY, sizeof(S) == 8 ? 6 : 8)
+    k_lbm_batch(const __grid_constant__ BatchTable<S> T) {
+    const int tx = threadIdx.x % kBatchTileX, ty = threadIdx.x / kBatchTileX;
+    int r = 0;
+    for (long long t = blockIdx.x; t < T.ntiles; t += gridDim.x) {
+        while (r + 1 < T.n && T.r[r + 1].tile0 <= t) r++;
+        const BatchRun<S>& R = T.r[r];
+        const long long loc = t - R.tile0;
+        const int bx = (int)(loc % R.tiles_x);
+        const long long rest = loc / R.tiles_x;
+        const int by = (int)(rest % R.tiles_y), z = (int)(rest / R.tiles_y);
+        const int x = bx * kBatchTileX + tx, y = by * kBatchTileY + ty;
+        if (x >= R.g.nx || y >= R.g.ny) continue;
+        if constexpr (std::is_same<typename Store<S>::C, float>::value) {
+            if (R.lazy) {
+                lbm_cell<S, false, true>(R.g, R.P, R.flags, R.owner, R.part, R.partf, R.fb, R.ax, R.ay, R.az,
+                                         R.lam_e, R.lam_o, 0, R.fp, x, y, z);
+                continue;
+            }
+        }
+        lbm_cell<S, false, false>(R.g, R.P, R.flags, R.owner, R.part, R.partf, R.fb, R.ax, R.ay, R.az, R.lam_e,
+                                  R.lam_o, 0, R.fp, x, y, z);
     }
 }
 
@@ -766,9 +838,17 @@ void dispatch_store(const es_ctx* c, Fn&& fn) {
         fn(0.0);
 }
 
+// The stream-collide's block shape (es_params.lbm_block; 0 = 128 x 1).
+dim3 lbm_block(const es_ctx* c) {
+    const int bx = c->P.lbm_block[0] > 0 ? c->P.lbm_block[0] : 128;
+    const int by = c->P.lbm_block[1] > 0 ? c->P.lbm_block[1] : 1;
+    return dim3(bx, by);
+}
+
 cudaError_t launch_lbm(es_ctx* c) {
     const Grid& g = c->g;
-    dim3 blk(128), grd((g.nx + 127) / 128, g.ny, g.nz);
+    const dim3 blk = lbm_block(c);
+    const dim3 grd((g.nx + blk.x - 1) / blk.x, (g.ny + blk.y - 1) / blk.y, g.nz);
     const double* a = c->P.accel;
     if (mixed(c) && c->np > 0) {
         k_particles_f32<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->np, c->part, c->partf);
@@ -812,6 +892,79 @@ cudaError_t launch_lbm(es_ctx* c) {
     });
     count(c);
     return cudaGetLastError();
+}
+
+// The stream-collide of n contexts (same precision and device, no
+// free-slip faces; checked by the caller) in one launch on cs[0]'s stream,
+// ordered after each context's pending work and before its later work by
+// events.  Each context's per-run preparation (the float particle copy, the
+// body force at cells next to obstacles) runs on its own stream first.
+cudaError_t launch_lbm_batch(es_ctx* const* cs, int n) {
+    cudaStream_t bs = cs[0]->stream;
+    for (int i = 0; i < n; i++) {
+        es_ctx* c = cs[i];
+        if (mixed(c) && c->np > 0) {
+            k_particles_f32<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->np, c->part, c->partf);
+            count(c);
+        }
+        if (c->fb_lazy) {
+            const cudaError_t e = launch_body_force_near(c);
+            if (e != cudaSuccess) return e;
+        }
+        if (!c->ev_sync) {
+            const cudaError_t e = cudaEventCreateWithFlags(&c->ev_sync, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        if (i > 0) {
+            cudaError_t e = cudaEventRecord(c->ev_sync, c->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, c->ev_sync, 0);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    cudaError_t err = cudaSuccess;
+    dispatch_store(cs[0], [&](auto tag) {
+        using S = decltype(tag);
+        using C = typename Store<S>::C;
+        BatchTable<S> T;
+        long long tiles = 0;
+        double cells = 0.0;
+        for (int i = 0; i < n; i++) {
+            es_ctx* c = cs[i];
+            BatchRun<S>& R = T.r[i];
+            R.g = c->g;
+            R.P = streams<S>(c);
+            R.flags = c->flags;
+            R.owner = c->owner;
+            R.part = c->part;
+            R.partf = c->partf;
+            R.fb = (const C*)c->fb;
+            R.ax = (C)c->P.accel[0];
+            R.ay = (C)c->P.accel[1];
+            R.az = (C)c->P.accel[2];
+            R.lam_e = (C)c->lambda_e;
+            R.lam_o = (C)c->lambda_o;
+            const double k2e = c->S.kappa * c->S.kappa * c->S.eps;
+            R.fp = FbPsi{c->psi32, (float)c->P.E_ext[0], (float)c->P.E_ext[1], (float)c->P.E_ext[2], (float)k2e};
+            R.lazy = c->fb_lazy ? 1 : 0;
+            R.tiles_x = (c->g.nx + kBatchTileX - 1) / kBatchTileX;
+            R.tiles_y = (c->g.ny + kBatchTileY - 1) / kBatchTileY;
+            R.tile0 = tiles;
+            tiles += (long long)R.tiles_x * R.tiles_y * c->g.nz;
+            cells += (double)c->g.N;
+        }
+        T.n = n;
+        T.ntiles = tiles;
+        const long long cap = (long long)cs[0]->n_sm * 16;
+        const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+        ProfScope ps(cs[0], "lbm_batch", -1, cells * (38.0 * sizeof(S) + 4.0 + 1.0));
+        k_lbm_batch<S><<<grid, kBatchTileX * kBatchTileY, 0, bs>>>(T);
+        count(cs[0]);
+        err = cudaGetLastError();
+    });
+    if (err != cudaSuccess) return err;
+    err = cudaEventRecord(cs[0]->ev_sync, bs);
+    for (int i = 1; i < n && err == cudaSuccess; i++) err = cudaStreamWaitEvent(cs[i]->stream, cs[0]->ev_sync, 0);
+    return err;
 }
 
 cudaError_t launch_forces(es_ctx* c) {

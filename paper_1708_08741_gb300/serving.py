@@ -234,6 +234,137 @@ class Server:
         return [results[r.rid] for r in requests]
 
 
+class BatchServer:
+    """Continuous batching in lockstep: the resident runs advance one time
+    step together, and their stream-collides go to the GPU as one persistent
+    launch (es_lbm_step_batch) over a work table of the runs' tiles.  Each
+    step: every run's particle mapping (its own stream), every run's
+    potential solve (host threads, so that the solves' norm reads overlap),
+    one batched stream-collide, every run's forces and rigid-body update;
+    every check_every steps of a run its mean particle velocity is compared
+    (the steady-state rule of run_to_steady) and a finished run leaves,
+    freeing its slot and memory for the requests that wait.
+
+    sim_factory(workload, slot) -> es.Simulation; bytes_of(workload) ->
+    device bytes of a run; batch_step(sims) -> one batched stream-collide.
+    """
+
+    def __init__(self, sim_factory: Callable, bytes_of: Callable, batch_step: Callable, slots: int,
+                 budget_bytes: int, check_every: int = 100, rel_tol: float = 1e-4, max_steps: int = 20000,
+                 clock: Callable[[], float] = time.perf_counter):
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
+        self.sim_factory = sim_factory
+        self.bytes_of = bytes_of
+        self.batch_step = batch_step
+        self.slots = slots
+        self.budget = budget_bytes
+        self.check_every = check_every
+        self.rel_tol = rel_tol
+        self.max_steps = max_steps
+        self.clock = clock
+        self.peak_resident = 0
+        self.launches = 0  # batched stream-collide launches
+
+    def serve(self, requests: Sequence[Request], time_scale: float = 1.0) -> List[Result]:
+        from concurrent.futures import ThreadPoolExecutor
+
+        for r in requests:
+            if self.bytes_of(r.wl) > self.budget:
+                raise ValueError(f"request {r.rid} needs more device memory than the budget")
+        queue = sorted(requests, key=lambda r: r.arrival)
+        pending: List[Request] = []
+        results: Dict[int, Result] = {}
+        resident = []  # dicts: req, sim, slot, need, admitted, steps, prev
+        free_slots = list(range(self.slots))
+        used = 0
+        k = 0
+        t0 = self.clock()
+        pool = ThreadPoolExecutor(max_workers=self.slots)
+
+        def retire(run, res):
+            nonlocal used
+            run["sim"].close()
+            results[run["req"].rid] = res
+            free_slots.append(run["slot"])
+            used -= run["need"]
+            resident.remove(run)
+
+        def failed(run, e):
+            retire(run, Result(run["req"].rid, run["req"].arrival * time_scale, run["admitted"],
+                               self.clock() - t0, -1, False, np.full(3, np.nan),
+                               error=f"{type(e).__name__}: {e}"))
+
+        try:
+            while k < len(queue) or pending or resident:
+                now = self.clock() - t0
+                while k < len(queue) and queue[k].arrival * time_scale <= now:
+                    pending.append(queue[k])
+                    k += 1
+                i = 0
+                while i < len(pending) and free_slots:
+                    need = self.bytes_of(pending[i].wl)
+                    if used + need <= self.budget:
+                        req = pending.pop(i)
+                        slot = free_slots.pop(0)
+                        sim = self.sim_factory(req.wl, slot)
+                        used += need
+                        resident.append({"req": req, "sim": sim, "slot": slot, "need": need,
+                                         "admitted": self.clock() - t0, "steps": 0, "prev": None})
+                        self.peak_resident = max(self.peak_resident, len(resident))
+                    else:
+                        i += 1
+                if not resident:
+                    if k < len(queue):
+                        time.sleep(max(0.0, queue[k].arrival * time_scale - (self.clock() - t0)))
+                    continue
+                # one lockstep step of every resident run
+                for run in list(resident):
+                    try:
+                        run["sim"].map_particles()
+                    except Exception as e:
+                        failed(run, e)
+                futs = [(run, pool.submit(run["sim"].solve)) for run in resident]
+                for run, f in futs:
+                    try:
+                        f.result()
+                    except Exception as e:
+                        failed(run, e)
+                if not resident:
+                    continue
+                self.batch_step([run["sim"] for run in resident])
+                self.launches += 1
+                for run in list(resident):
+                    try:
+                        run["sim"].forces_device()
+                        run["sim"].advance()
+                    except Exception as e:
+                        failed(run, e)
+                        continue
+                    run["steps"] += 1
+                    if run["steps"] % self.check_every:
+                        continue
+                    try:
+                        p = run["sim"].particles()
+                    except Exception as e:
+                        failed(run, e)
+                        continue
+                    vm = np.mean(p["v"], axis=0)
+                    prev = run["prev"]
+                    steady = prev is not None and np.linalg.norm(vm - prev) <= self.rel_tol * max(
+                        np.linalg.norm(vm), 1e-300)
+                    if steady or run["steps"] >= self.max_steps:
+                        retire(run, Result(run["req"].rid, run["req"].arrival * time_scale, run["admitted"],
+                                           self.clock() - t0, run["steps"], steady, vm, p["v"], p["x"]))
+                    else:
+                        run["prev"] = vm
+        finally:
+            pool.shutdown(wait=True)
+            for run in list(resident):
+                run["sim"].close()
+        return [results[r.rid] for r in requests]
+
+
 def summarize(results: Sequence[Result]) -> dict:
     """runs/s counts the completed runs (failed ones are listed apart)."""
     ok = [r for r in results if r.error is None]
@@ -272,3 +403,28 @@ def gpu_server(precision: int, slots: int, device: str = "cuda:0", budget_fracti
         return es.device_bytes(wl, precision, overrides)
 
     return Server(factory, bytes_of, slots, int(budget_fraction * free), **kw)
+
+
+def gpu_batch_server(precision: int, slots: int, device: str = "cuda:0", budget_fraction: float = 0.8,
+                     overrides: Optional[dict] = None, tuner=None, **kw) -> BatchServer:
+    """A BatchServer of library contexts, each on its own CUDA stream, whose
+    stream-collides are launched together (es_lbm_step_batch)."""
+    import torch
+
+    import paper_1708_08741_gb300 as es
+
+    dev = torch.device(device)
+    streams = [torch.cuda.Stream(dev) for _ in range(slots)]
+    free, _ = torch.cuda.mem_get_info(dev)
+
+    def factory(wl, slot):
+        torch.cuda.set_device(dev)
+        ov = dict(overrides or {})
+        if tuner is not None:
+            ov.update(tuner.tune(wl))
+        return es.Simulation(wl, precision, device=device, stream=streams[slot], overrides=ov)
+
+    def bytes_of(wl):
+        return es.device_bytes(wl, precision, overrides)
+
+    return BatchServer(factory, bytes_of, es.lbm_step_batch, slots, int(budget_fraction * free), **kw)

@@ -70,6 +70,8 @@ def _create_rc(lib, wl, **over):
     (dict(phi_t=0.5, levels=2), "levels == 1"),
     (dict(fine_layout=2), "fine_layout"),
     (dict(near_list_cells=-1), "near_list_cells"),
+    (dict(lbm_block=(48, 1)), "lbm_block"),
+    (dict(lbm_block=(128, 4)), "lbm_block"),
     (dict(fast_update_cells=-5), "fast_update_cells"),
 ])
 def test_invalid_parameters_rejected_before_any_gpu_call(lib, over, needle):

@@ -32,7 +32,7 @@ def test_tuner_caches_per_class_and_treats_failures_as_slow():
             raise RuntimeError("did not converge")
         return 1.0 / (ov["nu1"] + ov["nu2"])  # more smoothing is faster here
 
-    t = A.Autotuner(measure)
+    t = A.Autotuner(measure, shapes=lambda wl: [])
     wl = W.single_sphere()
     best = t.tune(wl)
     assert (best["nu1"], best["nu2"]) == (3, 3)
@@ -40,3 +40,24 @@ def test_tuner_caches_per_class_and_treats_failures_as_slow():
     assert t.tune(W.single_sphere()) is best and len(calls) == n  # cached
     assert dict(t.log[A.class_key(wl)][0][0]) == {"nu1": 1, "nu2": 1, "smoother": 0}
     assert t.log[A.class_key(wl)][0][1] == math.inf
+
+
+def test_tuner_then_times_block_shapes_with_the_chosen_schedule():
+    """Stage two: with the fastest schedule fixed, the stream-collide block
+    shapes are timed and the fastest kept; the default shape is always a
+    candidate and shapes wider than the grid are skipped."""
+    seen = []
+
+    def measure(wl, ov):
+        seen.append(ov)
+        t = 1.0 / (ov["nu1"] + ov["nu2"])
+        shape = ov.get("lbm_block", (0, 0))
+        return t * (0.5 if shape == (32, 4) else 1.0)
+
+    wl = W.single_sphere()  # nx = 32
+    shapes = A.block_shapes(wl)
+    assert {tuple(s["lbm_block"]) for s in shapes} == {(0, 0), (32, 4), (32, 8)}
+    best = A.Autotuner(measure).tune(wl)
+    assert best["lbm_block"] == (32, 4) and (best["nu1"], best["nu2"]) == (3, 3)
+    stage2 = [ov for ov in seen if "lbm_block" in ov]
+    assert len(stage2) == len(shapes) and all((o["nu1"], o["nu2"]) == (3, 3) for o in stage2)

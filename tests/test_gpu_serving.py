@@ -62,7 +62,9 @@ def test_autotuner_on_the_gpu_picks_a_schedule_that_meets_the_tolerance():
     wl = W.suspension_sample(64)
     tuner = A.Autotuner(A.gpu_measure(es.ES_MIXED32, steps=3, warmup=2))
     best = tuner.tune(wl)
-    assert best in A.candidates(wl)
+    schedule = {k: v for k, v in best.items() if k != "lbm_block"}
+    assert schedule in A.candidates(wl)
+    assert "lbm_block" in best and {"lbm_block": best["lbm_block"]} in A.block_shapes(wl)
     times = [t for _, t in tuner.log[A.class_key(wl)]]
     assert all(t > 0 for t in times) and min(times) < float("inf")
     sim = es.Simulation(wl, es.ES_MIXED32, overrides=best)
@@ -70,3 +72,71 @@ def test_autotuner_on_the_gpu_picks_a_schedule_that_meets_the_tolerance():
         info = sim.step()
         assert info["r"] < info["tol"]
     sim.close()
+
+
+def _runs(precision):
+    """Three resident runs of uneven size (a ragged walled box, a periodic
+    sphere box, a suspension sample), all without free-slip faces."""
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import workloads as W
+
+    return [W.mixed_box(), W.single_sphere(n=32), W.suspension_sample(48, levels=3)]
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed32", "mixed16"])
+def test_batched_stream_collide_equals_single_runs(prec_name):
+    """es_lbm_step_batch steps the stream-collide of several resident runs
+    (different grid sizes, walls, spheres) in one launch: every run's
+    populations and particles after 5 coupled steps are the same bits as
+    when each run steps alone."""
+    import paper_1708_08741_gb300 as es
+
+    precision = {"fp64": es.ES_FP64, "mixed32": es.ES_MIXED32, "mixed16": es.ES_MIXED16}[prec_name]
+    alone = [es.Simulation(wl, precision) for wl in _runs(precision)]
+    batch = [es.Simulation(wl, precision) for wl in _runs(precision)]
+    for _ in range(5):
+        for g in alone:
+            g.step()
+        for g in batch:
+            g.map_particles()
+            g.solve()
+        es.lbm_step_batch(batch)
+        for g in batch:
+            g.forces_device()
+            g.advance()
+    for a, b in zip(alone, batch):
+        np.testing.assert_array_equal(a.field(es.FIELD_PDF), b.field(es.FIELD_PDF))
+        np.testing.assert_array_equal(a.particles()["x"], b.particles()["x"])
+        a.close()
+        b.close()
+
+
+def test_stream_collide_block_shapes_give_the_same_bits():
+    """The stream-collide's block shape (es_params.lbm_block, a tuning knob)
+    does not change the result."""
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import workloads as W
+
+    out = []
+    for shape in ((0, 0), (32, 4), (64, 2), (256, 1)):
+        g = es.Simulation(W.mixed_box(), es.ES_MIXED32, overrides=dict(lbm_block=shape))
+        for _ in range(3):
+            g.step()
+        out.append(g.field(es.FIELD_PDF))
+        g.close()
+    for o in out[1:]:
+        np.testing.assert_array_equal(out[0], o)
+
+
+def test_batch_rejects_mixed_precisions_and_duplicates():
+    import paper_1708_08741_gb300 as es
+    from paper_1708_08741_gb300 import workloads as W
+
+    a = es.Simulation(W.single_sphere(n=16, radius=3.0, levels=2), es.ES_MIXED32)
+    b = es.Simulation(W.single_sphere(n=16, radius=3.0, levels=2), es.ES_FP64)
+    for sims in ([a, b], [a, a]):
+        with pytest.raises(es.EsError) as e:
+            es.lbm_step_batch(sims)
+        assert e.value.code == es.ES_EINVAL
+    a.close()
+    b.close()

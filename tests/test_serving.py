@@ -141,3 +141,63 @@ def test_result_alone_equals_result_in_the_mix_for_a_deterministic_run():
         alone = S.Server(mk, lambda wl: 1, slots=1, budget_bytes=10, check_every=50).serve([r])[0]
         m = mix[r.rid]
         assert alone.steps == m.steps and np.array_equal(alone.v, m.v)
+
+
+class FakeLockstepSim(FakeSim):
+    """FakeSim driven through the calls of one time step, as the lockstep
+    server issues them; advance() moves time on.  fail_at: the solve of that
+    step raises (a run that fails, e.g. on overlapping spheres)."""
+
+    def __init__(self, wl, slot, fail_at=None):
+        super().__init__(wl, slot, step_time=0.0)
+        self.fail_at = fail_at
+        self.calls = []
+
+    def map_particles(self):
+        self.calls.append("map")
+
+    def solve(self):
+        if self.fail_at is not None and self.t + 1 == self.fail_at:
+            raise RuntimeError("planted failure")
+        self.calls.append("solve")
+
+    def forces_device(self):
+        self.calls.append("forces")
+
+    def advance(self):
+        self.t += 1
+
+
+@pytest.mark.parametrize("slots", [1, 3])
+def test_lockstep_batch_server_matches_the_threaded_server(slots):
+    """The lockstep scheduler steps the resident runs together (one batched
+    stream-collide per step for all of them), admits by slots and memory as
+    runs finish, and gives every run the same steps and result as the
+    threaded scheduler."""
+    reqs = S.request_stream(10, rate=200.0, seed=9, edge_range=(32, 64))
+    FakeSim.live = FakeSim.peak = 0
+    budget = int(2.5 * max(r.wl.n_cells * 100 for r in reqs))
+    batches = []
+    srv = S.BatchServer(lambda wl, slot: FakeLockstepSim(wl, slot), lambda wl: wl.n_cells * 100,
+                        lambda sims: batches.append(len(sims)), slots=slots, budget_bytes=budget,
+                        check_every=50, max_steps=2000)
+    res = srv.serve(reqs)
+    ref = S.Server(lambda wl, slot: FakeSim(wl, slot, step_time=0.0), lambda wl: 1, slots=1, budget_bytes=10,
+                   check_every=50, max_steps=2000).serve(reqs)
+    assert [r.rid for r in res] == [r.rid for r in reqs]
+    assert srv.peak_resident <= slots and FakeSim.peak <= slots
+    assert max(batches) <= slots and srv.launches == len(batches)
+    if slots > 1:
+        assert max(batches) > 1  # runs shared a batched launch
+    for a, b in zip(res, ref):
+        assert a.steps == b.steps and a.steady and np.array_equal(a.v, b.v)
+        assert a.finished >= a.admitted >= a.arrival - 1e-9
+
+
+def test_lockstep_batch_server_reports_a_failed_run_and_serves_the_rest():
+    reqs = S.request_stream(4, rate=500.0, seed=4, edge_range=(32, 48))
+    bad = reqs[1].rid
+    mk = lambda wl, slot: FakeLockstepSim(wl, slot, fail_at=30 if wl is reqs[1].wl else None)  # noqa: E731
+    res = S.BatchServer(mk, lambda wl: 1, lambda sims: None, slots=4, budget_bytes=10, check_every=50).serve(reqs)
+    assert res[bad].error is not None and "planted failure" in res[bad].error
+    assert all(r.error is None and r.steady for r in res if r.rid != bad)
