@@ -61,6 +61,8 @@ def parse_args():
                     help="storage of the finest level's multigrid correction")
     ap.add_argument("--fine-layout", choices=["auto", "natural"], default="auto",
                     help="finest-level layout of the multigrid correction and right-hand side")
+    ap.add_argument("--lbm-block", type=int, nargs=2, default=(0, 0), metavar=("X", "Y"),
+                    help="thread-block shape of the stream-collide (0 0: the library default)")
     return ap.parse_args()
 
 
@@ -242,7 +244,8 @@ def run_ours(args):
     mg = es.ES_MG_FP16 if args.mg_storage == "fp16" else es.ES_MG_NATIVE
     lay = es.ES_LAYOUT_NATURAL if args.fine_layout == "natural" else es.ES_LAYOUT_AUTO
     sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev),
-                        overrides=dict(smoother=smoother, mg_storage=mg, fine_layout=lay))
+                        overrides=dict(smoother=smoother, mg_storage=mg, fine_layout=lay,
+                                       lbm_block=tuple(args.lbm_block)))
     stream = sim.stream
     N = wl.n_cells
 

@@ -131,7 +131,7 @@ typedef struct {
                            the lists.)                                             */
     int lbm_block[2];   /* thread-block shape of the stream-collide: cells along x
                            (a multiple of 32 in 32..256) by rows along y, at most
-                           256 threads; {0, 0} selects {128, 1}.  The same result
+                           256 threads; {0, 0} selects {32, 4}.  The same result
                            for every shape (the autotuner times them).         */
     int fast_update_cells; /* reduced forms with the colour-split finest level: on
                            grids of at least this many cells a tolerance-driven

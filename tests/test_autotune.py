@@ -52,12 +52,12 @@ def test_tuner_then_times_block_shapes_with_the_chosen_schedule():
         seen.append(ov)
         t = 1.0 / (ov["nu1"] + ov["nu2"])
         shape = ov.get("lbm_block", (0, 0))
-        return t * (0.5 if shape == (32, 4) else 1.0)
+        return t * (0.5 if shape == (32, 8) else 1.0)
 
     wl = W.single_sphere()  # nx = 32
     shapes = A.block_shapes(wl)
-    assert {tuple(s["lbm_block"]) for s in shapes} == {(0, 0), (32, 4), (32, 8)}
+    assert {tuple(s["lbm_block"]) for s in shapes} == {(0, 0), (32, 8)}
     best = A.Autotuner(measure).tune(wl)
-    assert best["lbm_block"] == (32, 4) and (best["nu1"], best["nu2"]) == (3, 3)
+    assert best["lbm_block"] == (32, 8) and (best["nu1"], best["nu2"]) == (3, 3)
     stage2 = [ov for ov in seen if "lbm_block" in ov]
     assert len(stage2) == len(shapes) and all((o["nu1"], o["nu2"]) == (3, 3) for o in stage2)
