@@ -61,6 +61,8 @@ def parse_args():
                     help="storage of the finest level's multigrid correction")
     ap.add_argument("--fine-layout", choices=["auto", "natural"], default="auto",
                     help="finest-level layout of the multigrid correction and right-hand side")
+    ap.add_argument("--staging", choices=["registers", "bulk"], default="registers",
+                    help="operand staging of the finest level's half sweep")
     ap.add_argument("--lbm-block", type=int, nargs=2, default=(0, 0), metavar=("X", "Y"),
                     help="thread-block shape of the stream-collide (0 0: the library default)")
     return ap.parse_args()
@@ -245,7 +247,8 @@ def run_ours(args):
     lay = es.ES_LAYOUT_NATURAL if args.fine_layout == "natural" else es.ES_LAYOUT_AUTO
     sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev),
                         overrides=dict(smoother=smoother, mg_storage=mg, fine_layout=lay,
-                                       lbm_block=tuple(args.lbm_block)))
+                                       lbm_block=tuple(args.lbm_block),
+                                       sweep_staging=1 if args.staging == "bulk" else 0))
     stream = sim.stream
     N = wl.n_cells
 

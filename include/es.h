@@ -48,6 +48,7 @@ extern "C" {
 #define ES_ENOTCONVERGED (-4)  /* solver hit max_cycles above tolerance     */
 #define ES_ENAN (-5)           /* residual norm is NaN or infinite          */
 #define ES_EOVERLAP (-6)       /* two particles claim a cell, or a sphere cuts a wall */
+#define ES_ETIMEOUT (-7)       /* a kernel's bounded wait for its asynchronous copies ran out */
 
 /* arithmetic forms */
 #define ES_FP64 0    /* everything in double precision                           */
@@ -129,6 +130,14 @@ typedef struct {
                            0 selects the default ES_NEAR_LIST_CELLS; < 0 is
                            ES_EINVAL.  (The colour-split finest level always uses
                            the lists.)                                             */
+    int sweep_staging;  /* colour-split finest level, rows of up to 512 cells:
+                           ES_STAGE_REGISTERS (0, default) each thread loads its
+                           neighbours' rows into registers, marching through z
+                           planes; ES_STAGE_BULK a block stages the other
+                           colour's rows and its right-hand side in shared memory
+                           with bulk asynchronous copies (cp.async.bulk with
+                           mbarrier completion), three planes ahead.  The same
+                           sweep either way.                                    */
     int lbm_block[2];   /* thread-block shape of the stream-collide: cells along x
                            (a multiple of 32 in 32..256) by rows along y, at most
                            256 threads; {0, 0} selects {32, 4}.  The same result
@@ -173,6 +182,10 @@ typedef struct {
    x + nx (y + ny z) is element x + nx (y + ny z). */
 #define ES_LAYOUT_AUTO 0
 #define ES_LAYOUT_NATURAL 1
+
+/* How the finest level's half sweep brings in its operands (sweep_staging). */
+#define ES_STAGE_REGISTERS 0
+#define ES_STAGE_BULK 1
 
 typedef struct {
     double x[3]; /* centre                  */

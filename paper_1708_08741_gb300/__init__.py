@@ -27,6 +27,7 @@ ES_ECUDA = -3
 ES_ENOTCONVERGED = -4
 ES_ENAN = -5
 ES_EOVERLAP = -6
+ES_ETIMEOUT = -7
 
 ES_FP64 = 0
 ES_MIXED32 = 1
@@ -37,6 +38,8 @@ ES_MG_NATIVE = 0
 ES_MG_FP16 = 1
 ES_LAYOUT_AUTO = 0
 ES_LAYOUT_NATURAL = 1
+ES_STAGE_REGISTERS = 0
+ES_STAGE_BULK = 1
 
 FIELD_PSI = 0
 FIELD_RHO = 1
@@ -82,6 +85,7 @@ class Params(ctypes.Structure):
         ("phi_t", ctypes.c_double),
         ("fine_layout", ctypes.c_int),
         ("near_list_cells", ctypes.c_int),
+        ("sweep_staging", ctypes.c_int),
         ("lbm_block", ctypes.c_int * 2),
         ("fast_update_cells", ctypes.c_int),
     ]

@@ -73,6 +73,8 @@ int validate(const es_params* P, const es_particle* parts, int n, std::string& w
     if (!(P->phi_t >= 0.0) || std::isinf(P->phi_t)) return why = "phi_t must be finite and >= 0", ES_EINVAL;
     if (P->fine_layout != ES_LAYOUT_AUTO && P->fine_layout != ES_LAYOUT_NATURAL)
         return why = "fine_layout must be ES_LAYOUT_AUTO or ES_LAYOUT_NATURAL", ES_EINVAL;
+    if (P->sweep_staging != ES_STAGE_REGISTERS && P->sweep_staging != ES_STAGE_BULK)
+        return why = "sweep_staging must be ES_STAGE_REGISTERS or ES_STAGE_BULK", ES_EINVAL;
     if (P->lbm_block[0] != 0 || P->lbm_block[1] != 0) {
         const int bx = P->lbm_block[0], by = P->lbm_block[1];
         if (bx < 32 || bx > 256 || bx % 32 != 0 || by < 1 || bx * by > 256)
@@ -213,6 +215,7 @@ int read_norm_status(es_ctx* c, double* norm, int* status) {
 int status_error(es_ctx* c, int st) {
     if (st & DS_OVERLAP) return fail(c, ES_EOVERLAP, "two particles claim the same cell");
     if (st & DS_WALLCUT) return fail(c, ES_EOVERLAP, "a sphere cuts a non-periodic wall");
+    if (st & DS_TIMEOUT) return fail(c, ES_ETIMEOUT, "a kernel's wait for its asynchronous copies ran out");
     return ES_OK;
 }
 
@@ -293,6 +296,8 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     for (int a = 0; a < 3; a++) c->g.per[a] = params->periodic[a] ? 1 : 0;
     c->rb0 = colour_split(params);
     c->fb_lazy = false;
+    c->bulk_smem_set = false;
+    c->bulk_blocks = 0;
     c->slip = 0;
     for (int f = 0; f < 6; f++)
         if (!c->g.per[f / 2] && params->wall_slip[f]) c->slip |= 1 << f;
@@ -531,7 +536,7 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
             ES_CUDA(c, launch_correct(c));
             rc = read_norm_status(c, &norm, &st);
             if (rc != ES_OK) return rc;
-            if (!(norm < c->tol)) {
+            if (!(norm < c->tol) && !st) {
                 ES_CUDA(c, launch_outer_residual(c));
                 rc = read_norm_status(c, &norm, &st);
                 if (rc != ES_OK) return rc;
@@ -541,6 +546,10 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
             ES_CUDA(c, launch_outer_residual(c));
             rc = read_norm_status(c, &norm, &st);
             if (rc != ES_OK) return rc;
+        }
+        if (st) {
+            cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+            return status_error(c, st);
         }
         cycles += k;
         if (norm > 0.0 && before > 0.0) {

@@ -36,7 +36,7 @@ enum : uint8_t { F_SOLID = 1, F_NEAR19 = 2 };
 // multigrid level states: kind in the low two bits, near-boundary bit
 enum : uint8_t { ST_UNKNOWN = 0, ST_DIR = 1, ST_NEU = 2, ST_KIND = 3, ST_NEAR = 4 };
 // device status bits
-enum : int { DS_OVERLAP = 1, DS_WALLCUT = 2 };
+enum : int { DS_OVERLAP = 1, DS_WALLCUT = 2, DS_TIMEOUT = 4 };
 
 // D3Q19 (Sec. 4.1).  Direction q in 1..9 and q+9 are opposite.
 __host__ __device__ constexpr int cx(int q) {
@@ -146,6 +146,8 @@ struct es_ctx {
     unsigned long long vgraph_kernels[2];  // kernel launches in each graph
     bool vgraph_off;                    // capture failed once: launch directly
     cudaEvent_t ev_sync;                // orders the context's stream against a batched launch
+    bool bulk_smem_set;                 // the staged half sweep's shared-memory size is set
+    int bulk_blocks;                    // resident staged half-sweep blocks per SM; 0 = not queried
     std::vector<double> h_R;  // radii and kinds as created (fixed for the context's life)
     std::vector<int> h_kind;
     double lambda_e, lambda_o;

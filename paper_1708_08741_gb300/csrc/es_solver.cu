@@ -1061,6 +1061,261 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool pred)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::); }
 
+// ---- finest-level half sweep staged by bulk asynchronous copies ----
+//
+// mbarrier and bulk-copy primitives (sm_90 and later).  A wait is bounded:
+// after about a second it reports failure and the kernel records
+// DS_TIMEOUT instead of spinning on.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1LL << 31)) return false;  // (about a second)
+    return true;
+}
+// bytes from global src to shared dst (both 16-byte aligned, bytes a
+// multiple of 16), completing on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Tile of the staged half sweep: a block owns whole compact rows (nxh
+// cells of one colour, tpr = nxh / 4 threads a row, 4 cells a thread) of ty
+// rows and marches through zc planes; kBulkSlots ring slots each hold one
+// plane of the other colour's rows y0 - 1 .. y0 + ty (the y halo) and one
+// plane of the colour's right-hand side rows.
+constexpr int kBulkSlots = 6;
+struct BulkShape {
+    int tpr, ty, zc;
+};
+
+// One half sweep of the interior unknown cells of a tile (see
+// k_smooth_rb_bulk).  Stage k of the pipeline brings the other colour's
+// plane z0 - 1 + k and the right-hand side of plane z0 - 2 + k into slot
+// k % kBulkSlots; plane z0 + j is updated once stages j, j + 1, j + 2 have
+// landed (the other colour below, at and above it, its rhs), and its slot j
+// is refilled with stage j + kBulkSlots after the block's barrier.  FIRST
+// and GS as in rb_march, the same per-cell arithmetic (and so the same bits).
+// Returns false when a wait timed out (the copies still in flight have
+// been waited for, with the same bound).
+template <class T, int FIRST, bool GS>
+__device__ bool rb_bulk_march(const Level<T>& L, T inv_diag0, const uint32_t* __restrict__ mcol, int wpr,
+                              const T* __restrict__ rcol, const T* __restrict__ eo, T* __restrict__ es, T omega,
+                              int colour, const BulkShape& B, int y0, int z0, int z1, T* slots, uint64_t* bars) {
+    const int nxh = L.nx >> 1, ny = L.ny, nz = L.nz;
+    const int W = nxh, TY = B.ty;
+    const int tyc = y0 + TY <= ny ? TY : ny - y0;  // rows of this tile
+    const int zc = z1 - z0, nstage = zc + 2;
+    const size_t slot_floats = (size_t)(2 * TY + 2) * W;
+    auto wrap_y = [&](int y) {
+        int w;
+        if (!wrap_axis(y, ny, L.per[1], w)) w = y < 0 ? 0 : ny - 1;  // (beyond a wall: any valid row)
+        return w;
+    };
+    auto wrap_z = [&](int z) {
+        int w;
+        if (!wrap_axis(z, nz, L.per[2], w)) w = z < 0 ? 0 : nz - 1;
+        return w;
+    };
+    // the producer: one thread issues a stage's bulk copies
+    auto issue = [&](int k) {
+        T* base = slots + (size_t)(k % kBulkSlots) * slot_floats;
+        uint64_t* bar = bars + (k % kBulkSlots);
+        const int zr = z0 - 2 + k;
+        const bool has_r = k >= 2 && zr < z1;
+        const unsigned rowb = (unsigned)W * sizeof(T);
+        unsigned bytes = 0;
+        if (FIRST != 1) bytes += (unsigned)(tyc + 2) * rowb;
+        if (has_r) bytes += (unsigned)tyc * rowb;
+        mbar_expect_tx(bar, bytes);
+        if (FIRST != 1) {
+            const int zo = wrap_z(z0 - 1 + k);
+            const T* pl = eo + (size_t)nxh * ny * zo;
+            bulk_g2s(base, pl + (size_t)nxh * wrap_y(y0 - 1), rowb, bar);
+            bulk_g2s(base + W, pl + (size_t)nxh * y0, (unsigned)tyc * rowb, bar);
+            bulk_g2s(base + (size_t)(tyc + 1) * W, pl + (size_t)nxh * wrap_y(y0 + tyc), rowb, bar);
+        }
+        if (has_r) bulk_g2s(base + (size_t)(TY + 2) * W, rcol + (size_t)nxh * (y0 + (size_t)ny * zr), (unsigned)tyc * rowb, bar);
+    };
+    const int t = threadIdx.x;
+    const int ty = t / B.tpr, iq = 4 * (t % B.tpr);
+    const bool on = ty < tyc;
+    const int y = y0 + (on ? ty : 0);
+    int il, ir;
+    if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
+    if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
+    if (t == 0)
+        for (int k = 0; k < kBulkSlots && k < nstage; k++) issue(k);
+    // this thread's mask word of plane z (loaded a plane ahead)
+    auto mask_word = [&](int z) { return on ? mcol[(size_t)wpr * (y + (size_t)ny * z) + (iq >> 5)] : 0u; };
+    unsigned mw = mask_word(z0);
+    int waited = 0;  // stages waited for
+    bool ok = true;
+    int j = 0;       // planes done
+    for (; j < zc && ok; j++) {
+        const unsigned mw_next = j + 1 < zc ? mask_word(z0 + j + 1) : 0u;
+        while (waited <= j + 2 && ok) {
+            ok = mbar_wait(bars + (waited % kBulkSlots), (unsigned)((waited / kBulkSlots) & 1));
+            if (ok) waited++;
+        }
+        if (!ok) break;
+        const int z = z0 + j;
+        const T* sA = slots + (size_t)(j % kBulkSlots) * slot_floats;        // other colour, z - 1
+        const T* sB = slots + (size_t)((j + 1) % kBulkSlots) * slot_floats;  // other colour, z
+        const T* sC = slots + (size_t)((j + 2) % kBulkSlots) * slot_floats;  // other colour z + 1, rhs z
+        const unsigned m = (mw >> (iq & 31)) & 0xFu;
+        mw = mw_next;
+        if (m) {
+            T X[4], A[4], Bv[4], D[4], F[4], R[4], h = (T)0;
+            const int O = (colour + y + z) & 1;
+            if constexpr (FIRST != 1) {
+                ES_VLD(X, 0, sB + (size_t)(ty + 1) * W + iq);
+                ES_VLD(A, 0, sB + (size_t)ty * W + iq);
+                ES_VLD(Bv, 0, sB + (size_t)(ty + 2) * W + iq);
+                ES_VLD(D, 0, sA + (size_t)(ty + 1) * W + iq);
+                ES_VLD(F, 0, sC + (size_t)(ty + 1) * W + iq);
+                h = sB[(size_t)(ty + 1) * W + (O == 0 ? il : ir)];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) X[k] = A[k] = Bv[k] = D[k] = F[k] = (T)0;
+            }
+            ES_VLD(R, 0, sC + (size_t)(TY + 2) * W + (size_t)ty * W + iq);
+            T C[4] = {(T)0, (T)0, (T)0, (T)0};
+            const size_t rz = (size_t)nxh * (y + (size_t)ny * z) + iq;
+            if constexpr (FIRST == 0 && !GS) ES_VLD(C, 0, es + rz);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (!((m >> k) & 1u)) continue;
+                T left, right;
+                if (O == 0) {
+                    left = k == 0 ? h : X[k - 1];
+                    right = X[k];
+                } else {
+                    left = X[k];
+                    right = k == 3 ? h : X[k + 1];
+                }
+                T o = left;
+                o += right;
+                o += A[k];
+                o += Bv[k];
+                o += D[k];
+                o += F[k];
+                const T gs = (L.h2 * R[k] + o) * inv_diag0;
+                if constexpr (FIRST != 0)
+                    C[k] = omega * gs;
+                else if constexpr (GS)
+                    C[k] = gs;
+                else
+                    C[k] = ((T)1 - omega) * C[k] + omega * gs;
+            }
+            if (m == 0xFu) {
+                vst(es + rz, C[0], C[1], C[2], C[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if ((m >> k) & 1u) es[rz + k] = C[k];
+            }
+        }
+        __syncthreads();  // (every thread is done with slot j % kBulkSlots)
+        if (t == 0 && j + kBulkSlots < nstage) issue(j + kBulkSlots);
+    }
+    if (!ok) {
+        // the copies already issued (the prologue's stages and one more per
+        // plane done) must land before the block leaves
+        const int issued = nstage < kBulkSlots + j ? nstage : kBulkSlots + j;
+        for (int k = waited; k < issued; k++) mbar_wait(bars + (k % kBulkSlots), (unsigned)((k / kBulkSlots) & 1));
+    }
+    return ok;
+}
+
+// The colour-split finest level's half sweep with the other colour's rows
+// and the colour's right-hand side staged in shared memory by bulk
+// asynchronous copies (nx / 2 <= 256 compact cells a row): one thread of a
+// block issues a plane's copies -- a few contiguous row runs, kilobytes each --
+// three planes ahead of the update, so the loads in flight no longer depend
+// on the registers of the threads; the update reads its neighbours from
+// shared memory.  Moves the same 6.06 bytes a cell as k_smooth_rb, computes
+// the same bits, and afterwards takes its share of the colour's
+// near-boundary cells as k_smooth_rb does.  A wait that runs out sets
+// DS_TIMEOUT in status and the block skips the rest.
+template <class T>
+__global__ void __launch_bounds__(256) k_smooth_rb_bulk(Level<T> L, T inv_diag0, const uint32_t* __restrict__ mask,
+                                                        int wpr, const T* __restrict__ rhs, T* __restrict__ e,
+                                                        int colour, int first, T omega, int half, NearWork nw,
+                                                        BulkShape B, int* status) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    __shared__ __align__(8) uint64_t bars[kBulkSlots];
+    T* slots = (T*)bsm;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kBulkSlots; k++) mbar_init(bars + k, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int y0 = (int)blockIdx.x * B.ty;
+    const int z0 = (int)blockIdx.y * B.zc;
+    const int z1 = z0 + B.zc < L.nz ? z0 + B.zc : L.nz;
+    const uint32_t* mcol = mask + (size_t)colour * ((size_t)L.ny * L.nz * wpr);
+    const T* rcol = rhs + (size_t)colour * half;
+    const T* eo = e + (size_t)(colour ^ 1) * half;
+    T* es = e + (size_t)colour * half;
+    bool ok;
+    if (first == 1)
+        ok = rb_bulk_march<T, 1, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, omega, colour, B, y0, z0, z1, slots,
+                                        bars);
+    else if (first == 2)
+        ok = rb_bulk_march<T, 2, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, omega, colour, B, y0, z0, z1, slots,
+                                        bars);
+    else if (omega == (T)1)
+        ok = rb_bulk_march<T, 0, true>(L, inv_diag0, mcol, wpr, rcol, eo, es, omega, colour, B, y0, z0, z1, slots,
+                                       bars);
+    else
+        ok = rb_bulk_march<T, 0, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, omega, colour, B, y0, z0, z1, slots,
+                                        bars);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(status, DS_TIMEOUT);
+        return;
+    }
+    // the colour's near-boundary cells, shared out as in k_smooth_rb
+    const int nblk = (int)(gridDim.x * gridDim.y);
+    const int b = (int)blockIdx.y * (int)gridDim.x + (int)blockIdx.x;
+    const bool many = nblk >= kNearSegs;
+    const RbMap rb{half};
+    const EAcc<T, T> A{(T)1, (T)1};
+    const int tid = (int)threadIdx.x, nth = (int)blockDim.x;
+    for (int seg = many ? b % kNearSegs : b; seg < kNearSegs; seg += many ? kNearSegs : nblk) {
+        const int sb = many ? b / kNearSegs : 0;
+        const int nsb = many ? (nblk - seg + kNearSegs - 1) / kNearSegs : 1;
+        const int k = colour * kNearSegs + seg;
+        const int n = nw.count[k];
+        const int* list = nw.list + (size_t)k * nw.cap;
+        for (int i = sb * nth + tid; i < n; i += nsb * nth) {
+            const int cc = list[i];
+            const int x = cc % L.nx, yz = cc / L.nx;
+            const int yy = yz % L.ny, zz = yz / L.ny;
+            e[rb(cc, colour)] = near_gs<T, T, RbMap>(L, nw.st, rhs, e, x, yy, zz, first, omega, A, rb);
+        }
+    }
+}
+
 template <class T>
 struct RB2 {
     using Span = T[4];
@@ -2252,6 +2507,14 @@ Level<T> level_desc(const es_ctx* c, int l) {
     return L;
 }
 
+// Shared memory of the staged finest-level half sweep (0: not staged).
+size_t bulk_smem_bytes(const es_ctx* c) {
+    const int nxh = c->ln[0][0] / 2;
+    if (!c->rb0 || nxh > 256 || c->P.sweep_staging != ES_STAGE_BULK) return 0;
+    const int ty = 256 / (nxh / 4);
+    return (size_t)kBulkSlots * (2 * ty + 2) * nxh * sizeof(float);
+}
+
 // The coarsest level runs in one block from shared memory: from packed
 // per-colour lists (k_coarse_lists: e, rhs, inverse diagonal, one 4-byte
 // record per cell) when that fits, else k_coarse_solve (e, rhs, states).
@@ -2396,12 +2659,43 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                 const double b_rb_first = nl * (0.5 * es + 0.5 * ts + 0.0625);
                 const double b_rb_half = nl * (1.0 * es + own + 0.5 * ts + 0.0625);
                 const NearWork nw{st, c->near_list[l], cnt, c->near_cap[l]};
+                // rows of up to 256 compact cells: staged by bulk copies on request
+                const int nxh = L.nx / 2;
+                const bool bulk = nxh <= 256 && c->P.sweep_staging == ES_STAGE_BULK;
+                BulkShape bs{nxh / 4, 0, 0};
+                dim3 bgrd;
+                size_t bsm = 0;
+                if (bulk) {
+                    bs.ty = 256 / bs.tpr;
+                    const int ytiles = (L.ny + bs.ty - 1) / bs.ty;
+                    bsm = bulk_smem_bytes(c);
+                    // planes per block: the grid should fill whole waves of
+                    // the resident blocks, and each block pays two planes of
+                    // pipeline start-up; cost ~ waves x (planes + 2)
+                    const long long cap = (long long)(c->bulk_blocks > 0 ? c->bulk_blocks : 1) * c->n_sm;
+                    double best = 1e300;
+                    for (int zq = 4; zq <= 32 && zq <= L.nz; zq++) {
+                        const long long nb = (long long)ytiles * ((L.nz + zq - 1) / zq);
+                        const double cost = (double)((nb + cap - 1) / cap) * (zq + 2);
+                        if (cost < best - 1e-9) {
+                            best = cost;
+                            bs.zc = zq;
+                        }
+                    }
+                    if (bs.zc == 0) bs.zc = L.nz;
+                    bgrd = dim3(ytiles, (L.nz + bs.zc - 1) / bs.zc);
+                }
                 for (int col = 0; col < 2; col++) {
                     const int fs = first ? (col == 0 ? 1 : 2) : 0;
                     ProfScope ps(c, "smooth_half", l,
                                  !first ? b_rb_half : (col == 0 ? b_rb_first : b_rb_half - nl * own));
-                    k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, c->rbmask, c->rb_wpr, rhs, e, col,
-                                                                 fs, omega, rb.half, nw, zc);
+                    if (bulk)
+                        k_smooth_rb_bulk<T><<<bgrd, 256, bsm, c->stream>>>(L, inv_diag0, c->rbmask, c->rb_wpr, rhs, e,
+                                                                           col, fs, omega, rb.half, nw, bs,
+                                                                           c->d_status);
+                    else
+                        k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, c->rbmask, c->rb_wpr, rhs, e,
+                                                                     col, fs, omega, rb.half, nw, zc);
                 }
                 count(c, 2);
                 return;
@@ -2572,12 +2866,35 @@ cudaError_t vcycle_level(es_ctx* c, int l, int warm) {
     return vcycle_impl<T, T>(c, l, warm);
 }
 
+// (set before the V-cycle is captured into a graph).  The attribute belongs
+// to the kernel, not to a context, so it is raised to the most any grid can
+// need -- ty nxh <= 1024 and nxh <= 256 give at most kBulkSlots (2048 + 512)
+// floats -- so that contexts of other sizes never lower it under each other.
+void set_bulk_smem(es_ctx* c) {
+    const size_t sm = bulk_smem_bytes(c);
+    if (sm == 0 || c->bulk_smem_set) return;
+    cudaFuncSetAttribute(k_smooth_rb_bulk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((size_t)kBulkSlots * (2048 + 512) * sizeof(float)));
+    cudaGetLastError();
+    // resident blocks per SM at this context's size (for the plane count)
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_smooth_rb_bulk<float>, 256, sm) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    c->bulk_blocks = b;
+    c->bulk_smem_set = true;
+}
+
+// (the attribute belongs to the kernel: raised to the 200 KB every
+// coarsest level that runs in one block fits, never lowered by a context
+// with a smaller level)
 template <class T>
 void set_coarse_smem(const es_ctx* c) {
     size_t sm = coarse_smem_bytes(c, sizeof(T));
     if (sm > 48 * 1024 && sm <= 200 * 1024) {
-        cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_coarse_lists<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_coarse_lists<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     }
 }
 
@@ -2668,6 +2985,7 @@ cudaError_t launch_vcycle(es_ctx* c, int warm) {
         set_coarse_smem<float>(c);
     else
         set_coarse_smem<double>(c);
+    set_bulk_smem(c);
     const bool graph = !c->prof && !c->vgraph_off && c->stream != nullptr &&
                        c->P.smoother == ES_SMOOTH_TWO_PASS && c->P.mg_storage == ES_MG_NATIVE;
     if (!graph) return vcycle_direct(c, warm);

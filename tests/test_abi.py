@@ -71,6 +71,7 @@ def _create_rc(lib, wl, **over):
     (dict(fine_layout=2), "fine_layout"),
     (dict(near_list_cells=-1), "near_list_cells"),
     (dict(lbm_block=(48, 1)), "lbm_block"),
+    (dict(sweep_staging=2), "sweep_staging"),
     (dict(lbm_block=(128, 4)), "lbm_block"),
     (dict(fast_update_cells=-5), "fast_update_cells"),
 ])

@@ -466,6 +466,23 @@ def test_colour_split_layout_is_bit_identical_to_natural(name):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("name", ["suspension64", "channel64", "mixed_ragged"])
+def test_bulk_staged_half_sweep_is_bit_identical(name):
+    """The finest-level half sweep with its operands staged in shared memory
+    by bulk asynchronous copies (sweep_staging = ES_STAGE_BULK) computes the
+    same sweep as the register version: 6 coupled MIXED32 steps agree bit
+    for bit (walled and periodic boxes, rows of 20 to 32 compact cells)."""
+    out = []
+    for staging in (es.ES_STAGE_REGISTERS, es.ES_STAGE_BULK):
+        g = es.Simulation(CASES[name](), es.ES_MIXED32, overrides=dict(sweep_staging=staging))
+        cyc = [g.step()["cycles"] for _ in range(6)]
+        out.append((cyc, g.field(es.FIELD_PSI), g.field(es.FIELD_U), g.particles()["x"]))
+        g.close()
+    assert out[0][0] == out[1][0]
+    for a, b in zip(out[0][1:], out[1][1:]):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_mixed32_potential_round_trip():
     """MIXED32 stores psi as a float-float pair: a double written with
     es_set_field comes back to within 2^-47 relative."""
