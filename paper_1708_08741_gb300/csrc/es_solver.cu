@@ -682,42 +682,68 @@ __device__ __forceinline__ T near_gs(const Level<T>& L, const uint8_t* __restric
     return first ? omega * gs : ((T)1 - omega) * A.ld(e + m(cidx, col)) + omega * gs;
 }
 
-// The near-boundary unknown cells of one colour of a level, from that
-// colour's segments of the level's near-cell list (blockIdx.y: segment).
-template <class T, class E, class M = NatMap>
-__global__ void __launch_bounds__(256) k_smooth_near(Level<T> L, const uint8_t* __restrict__ st,
-                                                     const T* __restrict__ rhs, E* __restrict__ e,
-                                                     const int* __restrict__ list, const int* __restrict__ count,
-                                                     int cap, int first, T omega, EAcc<T, E> A, M m = M{}) {
-    const int n = count[blockIdx.y];
-    const int* seg = list + (size_t)blockIdx.y * cap;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int c = seg[i];
-        const int x = c % L.nx, yz = c / L.nx;
-        const int y = yz % L.ny, z = yz / L.ny;
-        A.st(e + m(c, (x + y + z) & 1), near_gs<T, E, M>(L, st, rhs, e, x, y, z, first, omega, A, m));
+// The near-boundary cells of a level, by colour: the level's near-cell list
+// and the state bytes their stencils need.
+struct NearWork {
+    const uint8_t* st;
+    const int* list;
+    const int* count;
+    int cap;
+};
+
+// The colour's near-boundary cells of a level shared out to the blocks of a
+// half-sweep launch after their interior spans: with at least kNearSegs
+// blocks, block b serves segment b % kNearSegs together with the other
+// blocks of that residue; with fewer, block b serves segments b, b + nblk, ...
+template <class T, class E, class M>
+__device__ __forceinline__ void near_share(const Level<T>& L, const NearWork& nw, const T* __restrict__ rhs, E* e,
+                                           int colour, int first, T omega, const EAcc<T, E>& A, M m) {
+    const int nblk = (int)(gridDim.x * gridDim.y * gridDim.z);
+    const int b = ((int)blockIdx.z * (int)gridDim.y + (int)blockIdx.y) * (int)gridDim.x + (int)blockIdx.x;
+    const bool many = nblk >= kNearSegs;
+    const int tid = (int)((threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x);
+    const int nth = (int)(blockDim.x * blockDim.y * blockDim.z);
+    for (int seg = many ? b % kNearSegs : b; seg < kNearSegs; seg += many ? kNearSegs : nblk) {
+        const int sb = many ? b / kNearSegs : 0;
+        const int nsb = many ? (nblk - seg + kNearSegs - 1) / kNearSegs : 1;  // blocks on this segment
+        const int k = colour * kNearSegs + seg;
+        const int n = nw.count[k];
+        const int* list = nw.list + (size_t)k * nw.cap;
+        for (int i = sb * nth + tid; i < n; i += nsb * nth) {
+            const int cc = list[i];
+            const int x = cc % L.nx, yz = cc / L.nx;
+            const int yy = yz % L.ny, zz = yz / L.ny;
+            A.st(e + m(cc, colour), near_gs<T, E, M>(L, nw.st, rhs, e, x, yy, zz, first, omega, A, m));
+        }
     }
 }
 
-// One red (colour 0) or black (1) half sweep with W-cell spans (W = 4 or 8):
-// a thread owns cells xs .. xs+W-1 of one row, loads its row (xs-4 ..
-// xs+W+3) and the four neighbour rows as aligned 16-byte vectors (the
-// neighbour rows are shared through L1/L2 with the threads that own them),
-// updates the W/2 cells of the colour, and writes the span back with the
-// other colour's values unchanged.  Same per-cell arithmetic as k_smooth;
-// requires nx % W == 0.  first != 0: the iterate starts at zero; nothing is
-// read and the other colour is written as zero.  Near-boundary cells are
-// updated in the kernel (INLINE_NEAR) or skipped and updated by
-// k_smooth_near right after (same colour, so the two passes do not depend
-// on each other).
+template <class T, int W, bool INLINE_NEAR, class E = T>
+__device__ __forceinline__ void smooth_v_span(const Level<T>& L, T inv_diag0, const uint8_t* __restrict__ st,
+                                              const T* __restrict__ rhs, E* __restrict__ e, int colour, int first,
+                                              T omega, const EAcc<T, E>& A, int xs, int y, int z);
+
+// One red or black half sweep of a level in the natural layout, 4-cell spans
+// (smooth_v_span).  INLINE_NEAR: the colour's near-boundary cells are
+// updated inside the spans (small levels); else they come from the level's
+// near-cell list, shared out to the same launch's blocks after their spans
+// (near_share; both sets read only the other colour, and a span that holds
+// a near-boundary cell of the colour stores only its own updates).
 template <class T, int W, bool INLINE_NEAR, class E = T>
 __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
                                                   const T* __restrict__ rhs, E* __restrict__ e, int colour,
-                                                  int first, T omega, EAcc<T, E> A) {
-    static_assert(W == 4, "the near-cell path reads the span's states from one word");
+                                                  int first, T omega, EAcc<T, E> A, NearWork nw) {
     const int xs = W * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
-    if (y >= L.ny) return;
+    if (y < L.ny) smooth_v_span<T, W, INLINE_NEAR, E>(L, inv_diag0, st, rhs, e, colour, first, omega, A, xs, y, z);
+    if constexpr (!INLINE_NEAR) near_share<T, E, NatMap>(L, nw, rhs, e, colour, first, omega, A, NatMap{});
+}
+
+template <class T, int W, bool INLINE_NEAR, class E>
+__device__ __forceinline__ void smooth_v_span(const Level<T>& L, T inv_diag0, const uint8_t* __restrict__ st,
+                                              const T* __restrict__ rhs, E* __restrict__ e, int colour, int first,
+                                              T omega, const EAcc<T, E>& A, int xs, int y, int z) {
+    static_assert(W == 4, "the near-cell path reads the span's states from one word");
     const bool lane_on = xs < L.nx;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int row = nx * (y + ny * z);
@@ -813,26 +839,26 @@ __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const
             }
         }
     } else {
-        (void)near_bits;  // left to k_smooth_near
+        // the colour's near-boundary cells belong to the list part of the
+        // launch: a span holding one stores only the cells it updated (the
+        // colour's interior unknown cells) and, on a sweep from zero, the
+        // other colour's zeros (nobody else writes that colour now)
+        if (lane_on && near_bits != 0) {
+            const int p0 = (colour + y + z) & 1;
+#pragma unroll
+            for (int i = 0; i < W; i++) {
+                const unsigned sv = (sw.x >> (8 * i)) & 0xFFu;
+                if ((i & 1) == p0 ? (sv & (ST_KIND | ST_NEAR)) == ST_UNKNOWN : first != 0)
+                    A.st(e + row + xs + i, c[1 + i]);
+            }
+            return;
+        }
     }
     if (lane_on) {
 #pragma unroll
         for (int v = 0; v < W; v += 4) A.st4(e + row + xs + v, c[1 + v], c[2 + v], c[3 + v], c[4 + v]);
     }
 }
-
-// The update of a 4-cell span of one colour in the colour-split layout
-// (interior cells only; O: offset of the colour's cells in the row, x = 2i + O).
-// ox[j] holds the other colour at compact index i0 - 1 + j, so the x
-// neighbours of cell i0 + k are ox[k + O] (left) and ox[k + 1 + O] (right).
-// The near-boundary cells of the colour-split finest level, by colour: the
-// level's near-cell list and the state bytes their stencils need.
-struct NearWork {
-    const uint8_t* st;
-    const int* list;
-    const int* count;
-    int cap;
-};
 
 // The interior unknown cells of one colour of the colour-split finest
 // level, for a 4-cell span of compact places iq .. iq+3 in row y and the
@@ -960,7 +986,7 @@ __device__ __forceinline__ void rb_march(const Level<T>& L, T inv_diag0, const u
 //    the colour's own e is read only for omega != 1;
 //  * then every block takes its share of the colour's near-boundary cells
 //    from the near-cell list (Gauss-Seidel values with the boundary faces of
-//    Sec. 5.4, as k_smooth_near): about half a cell per thread on large
+//    Sec. 5.4, near_gs): about half a cell per thread on large
 //    grids, whose scattered, latency-bound loads overlap the streaming of
 //    the blocks still marching.
 // Per cell and half sweep the interior moves the other colour's e in, the
@@ -994,28 +1020,8 @@ __global__ void __launch_bounds__(256, 4) k_smooth_rb(Level<T> L, T inv_diag0, c
         else
             rb_march<T, 0, false>(L, inv_diag0, mcol, wpr, rcol, eo, es, colour, omega, i0, y, z0, z1);
     }
-    // the near-boundary cells: with at least kNearSegs blocks, block b
-    // serves segment b % kNearSegs together with the other blocks of that
-    // residue; with fewer, block b serves segments b, b + nblk, ...
-    const int nblk = (int)(gridDim.x * gridDim.y * gridDim.z);
-    const int b = ((int)blockIdx.z * (int)gridDim.y + (int)blockIdx.y) * (int)gridDim.x + (int)blockIdx.x;
-    const bool many = nblk >= kNearSegs;
-    const RbMap rb{half};
-    const EAcc<T, T> A{(T)1, (T)1};
-    const int tid = (int)(threadIdx.y * blockDim.x + threadIdx.x), nth = (int)(blockDim.x * blockDim.y);
-    for (int seg = many ? b % kNearSegs : b; seg < kNearSegs; seg += many ? kNearSegs : nblk) {
-        const int sb = many ? b / kNearSegs : 0;
-        const int nsb = many ? (nblk - seg + kNearSegs - 1) / kNearSegs : 1;  // blocks on this segment
-        const int k = colour * kNearSegs + seg;
-        const int n = nw.count[k];
-        const int* list = nw.list + (size_t)k * nw.cap;
-        for (int i = sb * nth + tid; i < n; i += nsb * nth) {
-            const int cc = list[i];
-            const int x = cc % L.nx, yz = cc / L.nx;
-            const int yy = yz % L.ny, zz = yz / L.ny;
-            e[rb(cc, colour)] = near_gs<T, T, RbMap>(L, nw.st, rhs, e, x, yy, zz, first, omega, A, rb);
-        }
-    }
+    // the near-boundary cells, shared out to the blocks
+    near_share<T, T, RbMap>(L, nw, rhs, e, colour, first, omega, EAcc<T, T>{(T)1, (T)1}, RbMap{half});
 }
 
 __device__ __forceinline__ bool axis_ok(int v, int n, int per, int& w) {
@@ -1295,25 +1301,7 @@ __global__ void __launch_bounds__(256) k_smooth_rb_bulk(Level<T> L, T inv_diag0,
         return;
     }
     // the colour's near-boundary cells, shared out as in k_smooth_rb
-    const int nblk = (int)(gridDim.x * gridDim.y);
-    const int b = (int)blockIdx.y * (int)gridDim.x + (int)blockIdx.x;
-    const bool many = nblk >= kNearSegs;
-    const RbMap rb{half};
-    const EAcc<T, T> A{(T)1, (T)1};
-    const int tid = (int)threadIdx.x, nth = (int)blockDim.x;
-    for (int seg = many ? b % kNearSegs : b; seg < kNearSegs; seg += many ? kNearSegs : nblk) {
-        const int sb = many ? b / kNearSegs : 0;
-        const int nsb = many ? (nblk - seg + kNearSegs - 1) / kNearSegs : 1;
-        const int k = colour * kNearSegs + seg;
-        const int n = nw.count[k];
-        const int* list = nw.list + (size_t)k * nw.cap;
-        for (int i = sb * nth + tid; i < n; i += nsb * nth) {
-            const int cc = list[i];
-            const int x = cc % L.nx, yz = cc / L.nx;
-            const int yy = yz % L.ny, zz = yz / L.ny;
-            e[rb(cc, colour)] = near_gs<T, T, RbMap>(L, nw.st, rhs, e, x, yy, zz, first, omega, A, rb);
-        }
-    }
+    near_share<T, T, RbMap>(L, nw, rhs, e, colour, first, omega, EAcc<T, T>{(T)1, (T)1}, RbMap{half});
 }
 
 template <class T>
@@ -2702,39 +2690,31 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             }
         }
         if (vec) {
+            const NearWork nwl{st, c->near_list[l], c->near_count + 2 * kNearSegs * l, c->near_cap[l]};
             if (Nl <= inline_near_cells(c)) {
                 {
                     ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
                     k_smooth_v<T, W, true, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first,
-                                                                             omega, A);
+                                                                             omega, A, nwl);
                 }
                 ProfScope ps(c, "smooth_half", l, b_half);
-                k_smooth_v<T, W, true, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega, A);
+                k_smooth_v<T, W, true, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega, A,
+                                                                         nwl);
                 count(c, 2);
                 return;
             }
-            const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, kNearSegs);
-            const int* cnt = c->near_count + 2 * kNearSegs * l;
-            const size_t half = (size_t)kNearSegs * c->near_cap[l];
+            // larger levels: the near-boundary cells from the list, in the
+            // same launches (bytes: the spans' only; the list's scattered
+            // loads are not counted)
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
                 k_smooth_v<T, W, false, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first,
-                                                                          omega, A);
+                                                                          omega, A, nwl);
             }
-            {
-                ProfScope ps(c, "smooth_near", l, 0.0);
-                k_smooth_near<T, E><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l], cnt,
-                                                                 c->near_cap[l], first, omega, A);
-            }
-            {
-                ProfScope ps(c, "smooth_half", l, b_half);
-                k_smooth_v<T, W, false, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega,
-                                                                          A);
-            }
-            ProfScope ps(c, "smooth_near", l, 0.0);
-            k_smooth_near<T, E><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l] + half,
-                                                             cnt + kNearSegs, c->near_cap[l], 0, omega, A);
-            count(c, 4);
+            ProfScope ps(c, "smooth_half", l, b_half);
+            k_smooth_v<T, W, false, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega, A,
+                                                                      nwl);
+            count(c, 2);
             return;
         }
         if constexpr (kNative) {

@@ -150,9 +150,11 @@ def _profiled_names(g, steps):
 
 @pytest.mark.parametrize("name", sorted(LIST_CASES))
 def test_list_passes_fp64_forced_cycles(name):
-    """FP64 with every level but the coarsest on the list-driven near passes
-    (k_smooth_v without inline near cells + k_smooth_near): forced V-cycles
-    against the oracle at 1e-12, then 10 coupled steps."""
+    """FP64 with every level but the coarsest smoothing its near-boundary
+    cells from the near-cell list (k_smooth_v's list variant, the list
+    shared out to the half-sweep launch's blocks; selected for every level
+    above near_list_cells = 1 cell): forced V-cycles against the oracle at
+    1e-12, then 10 coupled steps."""
     wl = LIST_CASES[name]()
     p = Pair(wl, lib_overrides=BENCH_PATHS)
     p.o.map_particles()
@@ -177,9 +179,6 @@ def test_list_passes_fp64_forced_cycles(name):
     assert r["owner_equal"]
     for k in ("psi", "u", "x", "v", "w"):
         assert r[k] < FP64_TOL, (k, r[k])
-    # the list passes did run on the levels between the finest and the coarsest
-    seen = _profiled_names(p.g, 2)
-    assert all(seen.get(("smooth_near", l), 0) > 0 for l in range(wl.levels - 1))
 
 
 @pytest.mark.parametrize("name", sorted(LIST_CASES))
@@ -195,9 +194,6 @@ def test_bench_solver_paths_mixed32_after_100_steps(name):
         assert ginfo["status"] == es.ES_OK and ginfo["r"] < ginfo["tol"]
     _assert_reduced(p.compare())
     seen = _profiled_names(p.g, 6)
-    # (the colour-split finest level updates its near-boundary cells inside
-    # the half-sweep launches; the levels below it in separate list passes)
-    assert all(seen.get(("smooth_near", l), 0) > 0 for l in range(1, wl.levels - 1))
     updates = seen.get(("residual_update", -1), 0)
     assert updates > 0, "the FP32 residual update never ran"
 
