@@ -224,9 +224,17 @@ inline size_t pdf_bytes(int precision) {
 // each segment with its own counter, so that the list builder's atomics
 // spread over that many addresses.
 constexpr int kNearSegs = 64;
-// blocks per segment and per 64 SMs of a near-cell list pass (the passes are
-// bound by the latency of their scattered loads: more threads in flight)
+// blocks per 64 segments and per 64 SMs of a near-cell list pass (the
+// passes are bound by the latency of their scattered loads: more threads in
+// flight)
 constexpr int kNearBlocks = 16;
+
+// Blocks per segment (grid x) of a near-cell list pass: about 16 x 64 blocks
+// per 64 SMs in all, whatever the segment count.
+inline int near_grid_x(const es_ctx* c) {
+    const int x = (c->n_sm + 63) / 64 * kNearBlocks * 64 / kNearSegs;
+    return x < 1 ? 1 : x;
+}
 
 // Capacity of the per-block partial-sum array of the residual norm.
 constexpr int kResPartials = 8192;

@@ -2778,7 +2778,7 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
         if (vec) {
             dim3 rgrd((m[0] / 2 + 31) / 32, (m[1] + 7) / 8, m[2]);
             T* scratch = (T*)c->e2[l];  // (the fused sweep's second iterate; free between sweeps)
-            const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, 2 * kNearSegs);
+            const dim3 ngrd(near_grid_x(c), 2 * kNearSegs);
             const int* cnt = c->near_count + 2 * kNearSegs * l;
             bool done = false;
             if constexpr (kNative && std::is_same<T, float>::value) {
@@ -2899,7 +2899,7 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         int gz = kResPartials / (gx * gy);
         gz = gz < 1 ? 1 : (gz > c->g.nz ? c->g.nz : gz);
         const dim3 grd(gx, gy, gz), blk(32, 8);
-        const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, 2 * kNearSegs);
+        const dim3 ngrd(near_grid_x(c), 2 * kNearSegs);
         if (c->rb0) {
             // r goes to the colour-split right-hand side of the finest level
             k_outer_residual_near_ff<RbMap><<<ngrd, 256, 0, c->stream>>>(
@@ -3034,7 +3034,7 @@ cudaError_t launch_residual_update(es_ctx* c) {
     const int N = (int)c->g.N, nxh = L.nx / 2;
     ProfScope ps(c, "residual_update", -1, (double)N * 13.0);
     float* scratch = (float*)c->e2[0];
-    const dim3 ngrd((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, 2 * kNearSegs);
+    const dim3 ngrd(near_grid_x(c), 2 * kNearSegs);
     k_near_residual<float, float, RbMap><<<ngrd, 256, 0, c->stream>>>(
         L, c->st[0], (const float*)c->rhs[0], (const float*)c->e[0], c->near_list[0], c->near_count,
         c->near_cap[0], 1.0f / L.h2, scratch, EAcc<float, float>{1.0f, 1.0f}, RbMap{N / 2});
@@ -3077,7 +3077,7 @@ cudaError_t launch_body_force_near(es_ctx* c) {
     WallF wall2;
     for (int f = 0; f < 6; f++) wall2.v2[f] = (float)(2.0 * c->S.pot_val[f]);
     ProfScope ps(c, "body_force_near", -1, 0.0);
-    k_body_force_near<<<dim3((c->n_sm + kNearSegs - 1) / kNearSegs * kNearBlocks, kNearSegs), 256, 0, c->stream>>>(
+    k_body_force_near<<<dim3(near_grid_x(c), kNearSegs), 256, 0, c->stream>>>(
         g, c->S, (float)E[0], (float)E[1], (float)E[2], (float)k2e, c->psi32, c->owner, c->st[0],
         (const float2*)c->pbc, wall2, c->bf_list, c->bf_count, c->bf_cap, (float*)c->fb);
     count(c);
