@@ -84,6 +84,59 @@ __device__ __forceinline__ WallSrc wall_source(const Grid& g, int slip_faces, co
     return WallSrc{opp(q), c};
 }
 
+// TRT collision of one cell from its pulled populations f (working values)
+// and its body force plus acceleration: the moments (Eq. MacroscopVel) with
+// the modified velocity (Eq. modified_velocity), the even and odd parts of
+// Eq. TRTOp with the incompressible equilibrium (Eq. EqPDF_TRT) and Luo's
+// forcing (Eq. LBE_forcetermLuo); put(q, v) receives each post-collision
+// value.  Every stream-collide kernel calls this one function, so all give
+// the same bits.
+template <class C, class Put>
+__device__ __forceinline__ void collide(const C (&f)[19], C fx, C fy, C fz, C lam_e, C lam_o, Put&& put) {
+    // moments (Eq. MacroscopVel) with the modified velocity (Eq. modified_velocity)
+    C rho = (C)0, jx = (C)0, jy = (C)0, jz = (C)0;
+#pragma unroll
+    for (int q = 0; q < 19; q++) {
+        rho += f[q];
+        if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
+        if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
+        if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
+    }
+    // in the shifted form rho holds rho - 1; w_q * rho below is then the
+    // shifted equilibrium directly
+    const C ux = jx + (C)0.5 * fx, uy = jy + (C)0.5 * fy, uz = jz + (C)0.5 * fz;
+    const C uu = ux * ux + uy * uy + uz * uz;
+    const C uf = ux * fx + uy * fy + uz * fz;
+    const C ae = (C)1 + (C)0.5 * lam_e, ao = (C)1 + (C)0.5 * lam_o;
+
+    // rest population: even part only
+    {
+        const C w0 = (C)wq(0);
+        const C eq0 = w0 * (rho - (C)1.5 * uu);
+        const C F0 = w0 * ((C)-3 * uf);
+        put(0, f[0] + lam_e * (f[0] - eq0) + ae * F0);
+    }
+    // pairs (q, q+9): TRT split into even and odd parts (Eq. TRTOp, Eq. EqPDF_TRT)
+#pragma unroll
+    for (int q = 1; q <= 9; q++) {
+        const C w = (C)wq(q);
+        const C cu = (C)cx(q) * ux + (C)cy(q) * uy + (C)cz(q) * uz;
+        const C cf = (C)cx(q) * fx + (C)cy(q) * fy + (C)cz(q) * fz;
+        const C eq_e = w * (rho + (C)4.5 * cu * cu - (C)1.5 * uu);
+        const C eq_o = w * (C)3 * cu;
+        const C fe = (C)0.5 * (f[q] + f[q + 9]);
+        const C fo = (C)0.5 * (f[q] - f[q + 9]);
+        // Luo's term (Eq. LBE_forcetermLuo) split: even w(9 cu cf - 3 u.f), odd 3 w cf,
+        // with the (1 + lambda/2) factors that go with the modified velocity
+        const C Fe = w * ((C)9 * cu * cf - (C)3 * uf);
+        const C Fo = w * (C)3 * cf;
+        const C even = lam_e * (fe - eq_e) + ae * Fe;
+        const C odd = lam_o * (fo - eq_o) + ao * Fo;
+        put(q, f[q] + even + odd);
+        put(q + 9, f[q + 9] + even - odd);
+    }
+}
+
 // The electric body force evaluated inside the stream-collide (reduced
 // forms): psi (the float potential), E_ext and kappa^2 eps.
 struct FbPsi {
@@ -211,48 +264,7 @@ __device__ __forceinline__ void lbm_cell(const Grid& g, const Streams<S>& P, con
         }
     }
 
-    // moments (Eq. MacroscopVel) with the modified velocity (Eq. modified_velocity)
-    C rho = (C)0, jx = (C)0, jy = (C)0, jz = (C)0;
-#pragma unroll
-    for (int q = 0; q < 19; q++) {
-        rho += f[q];
-        if (cx(q)) jx += cx(q) > 0 ? f[q] : -f[q];
-        if (cy(q)) jy += cy(q) > 0 ? f[q] : -f[q];
-        if (cz(q)) jz += cz(q) > 0 ? f[q] : -f[q];
-    }
-    // in the shifted form rho holds rho - 1; w_q * rho below is then the
-    // shifted equilibrium directly
-    const C ux = jx + (C)0.5 * fx, uy = jy + (C)0.5 * fy, uz = jz + (C)0.5 * fz;
-    const C uu = ux * ux + uy * uy + uz * uz;
-    const C uf = ux * fx + uy * fy + uz * fz;
-    const C ae = (C)1 + (C)0.5 * lam_e, ao = (C)1 + (C)0.5 * lam_o;
-
-    // rest population: even part only
-    {
-        const C w0 = (C)wq(0);
-        const C eq0 = w0 * (rho - (C)1.5 * uu);
-        const C F0 = w0 * ((C)-3 * uf);
-        P.dst[0][c] = St::st(0, f[0] + lam_e * (f[0] - eq0) + ae * F0);
-    }
-    // pairs (q, q+9): TRT split into even and odd parts (Eq. TRTOp, Eq. EqPDF_TRT)
-#pragma unroll
-    for (int q = 1; q <= 9; q++) {
-        const C w = (C)wq(q);
-        const C cu = (C)cx(q) * ux + (C)cy(q) * uy + (C)cz(q) * uz;
-        const C cf = (C)cx(q) * fx + (C)cy(q) * fy + (C)cz(q) * fz;
-        const C eq_e = w * (rho + (C)4.5 * cu * cu - (C)1.5 * uu);
-        const C eq_o = w * (C)3 * cu;
-        const C fe = (C)0.5 * (f[q] + f[q + 9]);
-        const C fo = (C)0.5 * (f[q] - f[q + 9]);
-        // Luo's term (Eq. LBE_forcetermLuo) split: even w(9 cu cf - 3 u.f), odd 3 w cf,
-        // with the (1 + lambda/2) factors that go with the modified velocity
-        const C Fe = w * ((C)9 * cu * cf - (C)3 * uf);
-        const C Fo = w * (C)3 * cf;
-        const C even = lam_e * (fe - eq_e) + ae * Fe;
-        const C odd = lam_o * (fo - eq_o) + ao * Fo;
-        P.dst[q][c] = St::st(q, f[q] + even + odd);
-        P.dst[q + 9][c] = St::st(q + 9, f[q + 9] + even - odd);
-    }
+    collide<C>(f, fx, fy, fz, lam_e, lam_o, [&](int q, C v) { P.dst[q][c] = St::st(q, v); });
 }
 
 // One thread per cell; a block covers blockDim.x cells of blockDim.y rows
