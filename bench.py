@@ -332,10 +332,12 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     barrier()
     t0 = time.perf_counter()
+    e2e_cycles = 0
     for _ in range(e2e_steps):
         sim._check(sim.lib.es_set_particles(sim.h, parts, wl.n_particles), "es_set_particles")
         sim._check(sim.lib.es_map_particles(sim.h), "es_map_particles")
         sim._check(sim.lib.es_potential_solve(sim.h, -1, info_c), "es_potential_solve")
+        e2e_cycles += info_c.cycles
         sim._check(sim.lib.es_lbm_step(sim.h), "es_lbm_step")
         sim._check(sim.lib.es_forces(sim.h, F.ctypes.data, T.ctypes.data, 0), "es_forces")
         sim._check(sim.lib.es_advance(sim.h), "es_advance")
@@ -385,7 +387,8 @@ def run_ours(args):
         "kernels": kernels,
         "lbm_step_ms": lbm_ms,
         "e2e": {"value": aggregate_throughput(N, e2e_steps, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e / e2e_steps,
+                "vcycles_per_step": e2e_cycles / e2e_steps},
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": base,

@@ -340,7 +340,12 @@ int es_set_field(es_ctx* ctx, int which, const void* src, size_t bytes, int on_d
 
 /* Host copies of the particle state (n must equal the context's count).
    es_set_particles changes positions, velocities, spins, zeta and charge;
-   a sphere's radius and kind are fixed after creation (ES_EINVAL). */
+   a sphere's radius and kind are fixed after creation (ES_EINVAL).  It
+   copies src into a pinned staging buffer and returns without waiting for
+   the device: src may be reused at once, and the new state is in place for
+   every later call on the context's stream.  The surface charge density
+   stays as the last mapping found it until the next es_map_particles.
+   es_get_particles synchronises the context's stream. */
 int es_get_particles(es_ctx* ctx, es_particle* dst, int n);
 int es_set_particles(es_ctx* ctx, const es_particle* src, int n);
 

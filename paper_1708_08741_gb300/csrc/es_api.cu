@@ -150,7 +150,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     if (P->phi_t > 0.0) b += N * 8;  // linearised diagonal of the Poisson-Boltzmann stencil
     if (per_level) *per_level = lv;
     b += lv;
-    b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8 + 14 * 4);
+    b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8 + 14 * 4 + 12 * 8);
     b += (size_t)kResPartials * 8 + 64;
     return b;
 }
@@ -184,6 +184,15 @@ void release(es_ctx* c) {
     if (c->h_status) cudaFreeHost(c->h_status);
     c->h_norm = nullptr;
     c->h_status = nullptr;
+    for (void* h : {(void*)c->h_pset, (void*)c->h_pget, (void*)c->h_force})
+        if (h) cudaFreeHost(h);
+    c->h_pset = nullptr;
+    c->h_pget = nullptr;
+    c->h_force = nullptr;
+    if (c->ev_stage) {
+        cudaEventDestroy(c->ev_stage);
+        c->ev_stage = nullptr;
+    }
     for (auto& r : c->prof_recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -371,6 +380,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->nfaces = (int*)A(np1 * 4);
     c->F = (double*)A(np1 * 3 * 8);
     c->T = (double*)A(np1 * 3 * 8);
+    c->pstage = (double*)A(np1 * 12 * 8);
     c->partial = (double*)A((c->red_blocks > kResPartials ? c->red_blocks : kResPartials) * 8);
     c->d_norm = (double*)A(64);
     c->near_count = (int*)A(2 * kNearSegs * ES_MAXLEV * 4);
@@ -388,7 +398,11 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
         delete c;
         return fail(nullptr, ES_ENOMEM, "device allocation failed");
     }
-    if (cudaMallocHost(&c->h_norm, 64) != cudaSuccess || cudaMallocHost(&c->h_status, 64) != cudaSuccess) {
+    if (cudaMallocHost(&c->h_norm, 64) != cudaSuccess || cudaMallocHost(&c->h_status, 64) != cudaSuccess ||
+        cudaMallocHost(&c->h_pset, np1 * 12 * 8) != cudaSuccess ||
+        cudaMallocHost(&c->h_pget, np1 * sizeof(DParticle)) != cudaSuccess ||
+        cudaMallocHost(&c->h_force, np1 * 6 * 8) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         release(c);
         delete c;
@@ -601,10 +615,19 @@ int es_forces(es_ctx* c, double* F, double* T, int on_device) {
     ES_CUDA(c, launch_forces(c));
     size_t b = (size_t)c->np * 3 * sizeof(double);
     if (c->np == 0) return ES_OK;
-    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (F) ES_CUDA(c, cudaMemcpyAsync(F, c->F, b, k, c->stream));
-    if (T) ES_CUDA(c, cudaMemcpyAsync(T, c->T, b, k, c->stream));
-    if (!on_device && (F || T)) ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (on_device) {
+        if (F) ES_CUDA(c, cudaMemcpyAsync(F, c->F, b, cudaMemcpyDeviceToDevice, c->stream));
+        if (T) ES_CUDA(c, cudaMemcpyAsync(T, c->T, b, cudaMemcpyDeviceToDevice, c->stream));
+        return ES_OK;
+    }
+    if (!F && !T) return ES_OK;
+    // through the pinned staging buffer: F, then T
+    double* h = c->h_force;
+    if (F) ES_CUDA(c, cudaMemcpyAsync(h, c->F, b, cudaMemcpyDeviceToHost, c->stream));
+    if (T) ES_CUDA(c, cudaMemcpyAsync(h + 3 * c->np, c->T, b, cudaMemcpyDeviceToHost, c->stream));
+    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (F) std::memcpy(F, h, b);
+    if (T) std::memcpy(T, h + 3 * c->np, b);
     return ES_OK;
 }
 
@@ -717,10 +740,8 @@ int es_set_field(es_ctx* c, int which, const void* src, size_t bytes, int on_dev
 int es_get_particles(es_ctx* c, es_particle* dst, int n) {
     if (!c || (n > 0 && !dst) || n != c->np) return fail(c, ES_EINVAL, "bad particle array");
     if (n == 0) return ES_OK;
-    std::vector<DParticle> hp(n);
-    std::vector<int> hk(n);
-    ES_CUDA(c, cudaMemcpyAsync(hp.data(), c->part, n * sizeof(DParticle), cudaMemcpyDeviceToHost, c->stream));
-    ES_CUDA(c, cudaMemcpyAsync(hk.data(), c->kind, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    const DParticle* hp = c->h_pget;
+    ES_CUDA(c, cudaMemcpyAsync(c->h_pget, c->part, n * sizeof(DParticle), cudaMemcpyDeviceToHost, c->stream));
     ES_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int p = 0; p < n; p++) {
         for (int a = 0; a < 3; a++) {
@@ -729,7 +750,7 @@ int es_get_particles(es_ctx* c, es_particle* dst, int n) {
             dst[p].w[a] = hp[p].w[a];
         }
         dst[p].R = hp[p].R;
-        dst[p].kind = hk[p];
+        dst[p].kind = c->h_kind[p];
         dst[p].zeta = hp[p].zeta;
         dst[p].q = hp[p].q;
     }
@@ -746,29 +767,25 @@ int es_set_particles(es_ctx* c, const es_particle* src, int n) {
     for (int p = 0; p < n; p++)
         if (src[p].R != c->h_R[p] || src[p].kind != c->h_kind[p])
             return fail(c, ES_EINVAL, "a sphere's radius and kind are fixed after creation");
-    // sigma is recomputed by the next mapping; keep the current one meanwhile
-    std::vector<DParticle> cur(n);
-    ES_CUDA(c, cudaMemcpyAsync(cur.data(), c->part, n * sizeof(DParticle), cudaMemcpyDeviceToHost, c->stream));
-    ES_CUDA(c, cudaStreamSynchronize(c->stream));
-    std::vector<DParticle> hp(n);
-    std::vector<int> hk(n);
+    // the staging buffer is reused once the previous call's copy out of it is done
+    ES_CUDA(c, cudaEventSynchronize(c->ev_stage));
+    double* h = c->h_pset;
     for (int p = 0; p < n; p++) {
-        hp[p] = to_device(c->P, src[p], cur[p].sigma);
-        hk[p] = src[p].kind;
-    }
-    ES_CUDA(c, cudaMemcpyAsync(c->part, hp.data(), n * sizeof(DParticle), cudaMemcpyHostToDevice, c->stream));
-    ES_CUDA(c, cudaMemcpyAsync(c->kind, hk.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
-    std::vector<float> hb;
-    if (c->pbc) {
-        hb.resize(2 * n);
-        for (int p = 0; p < n; p++) {
-            const ff v = ff_from_double(hk[p] == ES_KIND_ZETA ? 2.0 * hp[p].zeta : hp[p].sigma / c->S.eps);
-            hb[2 * p] = v.hi;
-            hb[2 * p + 1] = v.lo;
+        const DParticle d = to_device(c->P, src[p], 0.0);
+        double* r = h + 12 * p;
+        for (int a = 0; a < 3; a++) {
+            r[a] = d.x[a];
+            r[3 + a] = d.v[a];
+            r[6 + a] = d.w[a];
         }
-        ES_CUDA(c, cudaMemcpyAsync(c->pbc, hb.data(), 2 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        r[9] = d.zeta;
+        r[10] = d.q;
+        r[11] = d.qeff;
     }
-    ES_CUDA(c, cudaStreamSynchronize(c->stream));
+    ES_CUDA(c, cudaMemcpyAsync(c->pstage, h, (size_t)n * 12 * 8, cudaMemcpyHostToDevice, c->stream));
+    ES_CUDA(c, cudaEventRecord(c->ev_stage, c->stream));
+    // sigma is recomputed by the next mapping; the kernel keeps the current one meanwhile
+    ES_CUDA(c, launch_set_particles(c));
     return ES_OK;
 }
 

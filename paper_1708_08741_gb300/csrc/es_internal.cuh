@@ -96,6 +96,7 @@ struct es_ctx {
     int* kind;
     int* nfaces;
     double *F, *T;         // np x 3
+    double* pstage;        // np x 12: x, v, w, zeta, q, qeff of es_set_particles, copied in
     // fields
     void* pdf[2];
     int cur, last_src;
@@ -132,6 +133,10 @@ struct es_ctx {
     int* d_status;
     double* h_norm;  // pinned: [0] norm
     int* h_status;   // pinned
+    double* h_pset;  // pinned: np x 12, the staging of es_set_particles
+    es::DParticle* h_pget;  // pinned: np records, es_get_particles
+    double* h_force;        // pinned: np x 6, es_forces into host arrays
+    cudaEvent_t ev_stage;   // the copy out of h_pset has completed
     double tol;
     int have_tol;
     double mg_rate;  // running estimate of the residual reduction per V-cycle
@@ -197,6 +202,7 @@ cudaError_t launch_lbm(es_ctx* c);
 cudaError_t launch_lbm_batch(es_ctx* const* cs, int n);  // es_lbm_step_batch
 cudaError_t launch_forces(es_ctx* c);
 cudaError_t launch_advance(es_ctx* c);
+cudaError_t launch_set_particles(es_ctx* c);  // part (and pbc) from pstage; sigma, mass, inertia kept
 cudaError_t launch_fill_rest(es_ctx* c);
 cudaError_t launch_get_pdf(es_ctx* c, int which_buf, double* dst);
 cudaError_t launch_set_pdf(es_ctx* c, const double* src);

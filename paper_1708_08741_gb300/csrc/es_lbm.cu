@@ -1005,6 +1005,42 @@ cudaError_t launch_forces(es_ctx* c) {
     return cudaGetLastError();
 }
 
+// A new particle state from the host: position, velocities, zeta, q and the
+// charge of the Coulomb force (Eq. SurfChrgZetaRelationDebHuck for a zeta
+// sphere) replace the record's; the surface charge density found by the last
+// mapping stays until the next one recomputes it, and the mass and moment of
+// inertia follow from the fixed radius.  In the MIXED32 form the sphere's
+// boundary value (2 zeta, or sigma / eps) is split into float-float as the
+// mapping does.
+__global__ void k_set_particles(const double* __restrict__ in, DParticle* part, const int* kind, double eps,
+                                float* pbc, int np) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double* s = in + 12 * p;
+    DParticle& d = part[p];
+    for (int a = 0; a < 3; a++) {
+        d.x[a] = s[a];
+        d.v[a] = s[3 + a];
+        d.w[a] = s[6 + a];
+    }
+    d.zeta = s[9];
+    d.q = s[10];
+    d.qeff = s[11];
+    if (pbc) {
+        const ff v = ff_from_double(kind[p] == ES_KIND_ZETA ? 2.0 * d.zeta : d.sigma / eps);
+        pbc[2 * p] = v.hi;
+        pbc[2 * p + 1] = v.lo;
+    }
+}
+
+cudaError_t launch_set_particles(es_ctx* c) {
+    if (c->np == 0) return cudaSuccess;
+    k_set_particles<<<blocks_for(c->np, 128), 128, 0, c->stream>>>(c->pstage, c->part, c->kind, c->S.eps, c->pbc,
+                                                                   c->np);
+    count(c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_advance(es_ctx* c) {
     if (c->np == 0) return cudaSuccess;
     ProfScope ps(c, "advance", -1, 0.0);

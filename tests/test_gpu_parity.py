@@ -2,6 +2,7 @@
 the same seeded inputs.  FP64 bar: 1e-12 relative L2; MIXED32 bar: 1e-4
 relative L2 on velocity, potential and particle position after 100 steps.
 Integer work (the cell-to-sphere mapping) must match exactly."""
+import ctypes
 import numpy as np
 import pytest
 
@@ -684,6 +685,52 @@ def test_radius_and_kind_fixed_after_creation():
     info = g.step()
     assert info["r"] < info["tol"]
     g.close()
+
+
+def test_set_particles_is_staged_and_keeps_the_mapped_state():
+    """es_set_particles copies the caller's array at the call (it may be
+    overwritten at once) and returns without waiting; the state reads back
+    exactly, and a round trip of the current state between steps changes no
+    bit of the coupled step (the surface charge density of a charged sphere
+    and its boundary value are kept until the next mapping)."""
+    wl = W.mixed_box()
+    n = wl.n_particles
+    a = es.Simulation(wl, es.ES_MIXED32)
+    b = es.Simulation(wl, es.ES_MIXED32)
+    for _ in range(2):
+        a.step(forced_cycles=2)
+        cur = (es.Particle * n)()
+        assert b.lib.es_get_particles(b.h, cur, n) == es.ES_OK
+        assert b.lib.es_set_particles(b.h, cur, n) == es.ES_OK
+        ctypes.memset(cur, 0, ctypes.sizeof(cur))
+        b.step(forced_cycles=2)
+    for f in (es.FIELD_PSI, es.FIELD_PDF):
+        np.testing.assert_array_equal(a.field(f), b.field(f))
+    pa, pb = a.particles(), b.particles()
+    for k in ("x", "v", "w"):
+        np.testing.assert_array_equal(pa[k], pb[k])
+
+    rng = np.random.default_rng(5)
+    x = wl.x + rng.uniform(-0.3, 0.3, wl.x.shape)
+    v = rng.normal(0, 1e-3, wl.x.shape)
+    w = rng.normal(0, 1e-4, wl.x.shape)
+    zeta = wl.zeta * 1.5
+    q = wl.q * 0.5
+    src = es.pack_particles(x, v, w, wl.R, wl.kind, zeta, q)
+    assert b.lib.es_set_particles(b.h, src, n) == es.ES_OK
+    ctypes.memset(src, 0, ctypes.sizeof(src))
+    out = (es.Particle * n)()
+    assert b.lib.es_get_particles(b.h, out, n) == es.ES_OK
+    got = {k: np.array([list(getattr(out[i], k)) for i in range(n)]) for k in ("x", "v", "w")}
+    np.testing.assert_array_equal(got["x"], x)
+    np.testing.assert_array_equal(got["v"], v)
+    np.testing.assert_array_equal(got["w"], w)
+    np.testing.assert_array_equal([out[i].zeta for i in range(n)], zeta)
+    np.testing.assert_array_equal([out[i].q for i in range(n)], q)
+    np.testing.assert_array_equal([out[i].kind for i in range(n)], wl.kind)
+    np.testing.assert_array_equal([out[i].R for i in range(n)], wl.R)
+    a.close()
+    b.close()
 
 
 def test_alu_peak_probe():
