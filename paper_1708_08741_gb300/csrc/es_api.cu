@@ -151,7 +151,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     if (per_level) *per_level = lv;
     b += lv;
     b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8 + 14 * 4 + 12 * 8);
-    b += (size_t)kResPartials * 8 + 64;
+    b += res_partial_slots(P->dims[0], P->dims[1], 0) * 8 + 64;
     return b;
 }
 
@@ -381,7 +381,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->F = (double*)A(np1 * 3 * 8);
     c->T = (double*)A(np1 * 3 * 8);
     c->pstage = (double*)A(np1 * 12 * 8);
-    c->partial = (double*)A((c->red_blocks > kResPartials ? c->red_blocks : kResPartials) * 8);
+    c->partial = (double*)A(res_partial_slots(c->g.nx, c->g.ny, c->red_blocks) * 8);
     c->d_norm = (double*)A(64);
     c->near_count = (int*)A(2 * kNearSegs * ES_MAXLEV * 4);
     {

@@ -244,6 +244,14 @@ inline int near_grid_x(const es_ctx* c) {
 
 // Capacity of the per-block partial-sum array of the residual norm.
 constexpr int kResPartials = 8192;
+// Partial-sum slots of the blocked residual norms: one per block of the
+// marching residual passes (at most kResPartials planes of blocks, and a
+// whole x-y plane of (32 lanes, 8 rows) blocks when that is more).
+inline size_t res_partial_slots(int nx, int ny, int red_blocks) {
+    const long long plane = (long long)((nx + 31) / 32) * ((ny + 7) / 8);
+    long long n = plane > kResPartials ? plane : kResPartials;
+    return (size_t)(n > red_blocks ? n : red_blocks);
+}
 
 // Brackets the launches made during its lifetime with CUDA events when the
 // context is profiling (no-op otherwise); bytes: algorithmic bytes of the

@@ -310,16 +310,41 @@ __global__ void __launch_bounds__(256) k_outer_residual_near_ff(Grid g, ff diag0
     }
 }
 
-// SPLIT: r is stored in the colour-split layout (W == 4).
+// The interior unknown cells of level 0 (near-boundary cells come from
+// k_outer_residual_near_ff, launched just before: the pass reads them back
+// into its norm sum).  A thread owns the span xs .. xs+W-1 of row y and
+// marches through the planes z0 .. z1-1: the rows (y, z-1), (y, z) and
+// (y, z+1) of psi roll through registers, so a plane loads the row
+// (y, z+1), the rows (y-1, z) and (y+1, z), two halo values and the state
+// bytes, and the loads of plane z+1 are issued before plane z is formed.
+// SPLIT: r is stored in the colour-split layout (W == 4).  Each block leaves
+// one partial sum of r^2.
+template <int W>
+struct FFSpan {
+    float h[W], l[W];
+};
+
+template <int W>
+__device__ __forceinline__ void load_ff(FFSpan<W>& s, const float* __restrict__ hi, const float* __restrict__ lo,
+                                        int at) {
+    load_span<W>(hi + at, s.h, 0);
+    load_span<W>(lo + at, s.l, 0);
+}
+
+template <int W>
+__device__ __forceinline__ unsigned load_states(const uint8_t* __restrict__ st, int at) {
+    if constexpr (W == 4)
+        return *reinterpret_cast<const unsigned*>(st + at);
+    else
+        return st[at];
+}
+
 template <int W, bool SPLIT>
-__global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, WallFF wall,
-                                                           const float* __restrict__ psi_hi,
+__global__ void __launch_bounds__(256, 2) k_outer_residual_ff(Grid g, ff diag0, const float* __restrict__ psi_hi,
                                                            const float* __restrict__ psi_lo,
                                                            const uint8_t* __restrict__ st0,
-                                                           const int32_t* __restrict__ owner,
-                                                           const float2* __restrict__ pbc, int pot_dir_mask,
                                                            float* __restrict__ r_out,
-                                                           double* __restrict__ partial) {
+                                                           double* __restrict__ partial, int zc) {
     static_assert(!SPLIT || W == 4, "the split store takes 4-cell spans");
     __shared__ float swarp[8];
     const int half = (int)(g.N >> 1);
@@ -329,83 +354,70 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
     const int y = blockIdx.y * 8 + threadIdx.y;
     const bool lane_on = xs < nx;
     const int xq = lane_on ? xs : 0;  // (inactive lanes read a valid span)
-    // unguarded loads: beyond a wall only near-boundary cells would read,
-    // and those are formed from memory by near_residual_ff
-    int ym = y, yp = y, xl = xq, xr = xq;
-    if (y < ny) {
+    const int z0 = (int)blockIdx.z * zc;
+    const int z1 = z0 + zc < nz ? z0 + zc : nz;
+    // y is the same for the 32 lanes of a warp, so the march is warp-uniform
+    if (y < ny && z0 < z1) {
+        // unguarded loads: beyond a wall only near-boundary cells would read,
+        // and those are formed from memory by near_residual_ff
+        int ym, yp, xl, xr;
         if (!wrap_axis(y - 1, ny, g.per[1], ym)) ym = y;
         if (!wrap_axis(y + 1, ny, g.per[1], yp)) yp = y;
         if (!wrap_axis(xq - 1, nx, g.per[0], xl)) xl = xq;
         if (!wrap_axis(xq + W, nx, g.per[0], xr)) xr = xq;
-    }
-    // y is the same for the 32 lanes of a warp, so the loop is warp-uniform
-    for (int z = blockIdx.z; z < nz && y < ny; z += gridDim.z) {
-        const int row = nx * (y + ny * z);
-        int zm, zp;
-        if (!wrap_axis(z - 1, nz, g.per[2], zm)) zm = z;
-        if (!wrap_axis(z + 1, nz, g.per[2], zp)) zp = z;
-        uint8_t sv[W];
-        if constexpr (W == 4) {
-            const uchar4 s4 = *reinterpret_cast<const uchar4*>(st0 + row + xq);
-            sv[0] = s4.x;
-            sv[1] = s4.y;
-            sv[2] = s4.z;
-            sv[3] = s4.w;
-        } else {
-            sv[0] = st0[row + xq];
-        }
-        unsigned near_bits = 0;
-        bool any = false;
-#pragma unroll
-        for (int i = 0; i < W; i++) {
-            if (!lane_on) sv[i] = (uint8_t)ST_NEU;
-            const bool unk = (sv[i] & ST_KIND) == ST_UNKNOWN;
-            any |= unk && !(sv[i] & ST_NEAR);
-            if (unk && (sv[i] & ST_NEAR)) near_bits |= 1u << i;
-        }
-        float out[W];
-#pragma unroll
-        for (int i = 0; i < W; i++) out[i] = 0.0f;
-        if (any) {
-            // interior cells: the x row with one neighbour each side, and the
-            // four neighbour rows, in registers
-            float ch[W + 2], cl[W + 2], ah[W], al[W], bh[W], bl[W], dh[W], dl[W], fh[W], fl[W];
-            ch[0] = psi_hi[row + xl];
-            cl[0] = psi_lo[row + xl];
-            ch[W + 1] = psi_hi[row + xr];
-            cl[W + 1] = psi_lo[row + xr];
-            {
-                float t[W];
-                load_span<W>(psi_hi + row + xq, t, 0);
-#pragma unroll
-                for (int i = 0; i < W; i++) ch[i + 1] = t[i];
-                load_span<W>(psi_lo + row + xq, t, 0);
-#pragma unroll
-                for (int i = 0; i < W; i++) cl[i + 1] = t[i];
-            }
-            const int rym = nx * (ym + ny * z), ryp = nx * (yp + ny * z);
-            const int rzm = nx * (y + ny * zm), rzp = nx * (y + ny * zp);
-            load_span<W>(psi_hi + rym + xq, ah, 0);
-            load_span<W>(psi_lo + rym + xq, al, 0);
-            load_span<W>(psi_hi + ryp + xq, bh, 0);
-            load_span<W>(psi_lo + ryp + xq, bl, 0);
-            load_span<W>(psi_hi + rzm + xq, dh, 0);
-            load_span<W>(psi_lo + rzm + xq, dl, 0);
-            load_span<W>(psi_hi + rzp + xq, fh, 0);
-            load_span<W>(psi_lo + rzp + xq, fl, 0);
+        auto zwrap = [&](int z) {
+            int w;
+            if (!wrap_axis(z, nz, g.per[2], w)) w = z < 0 ? 0 : nz - 1;  // (beyond a wall: any valid row)
+            return w;
+        };
+        auto rowof = [&](int yy, int z) { return nx * (yy + ny * z); };
+        FFSpan<W> D, X, F, A, B;
+        float hlh, hll, hrh, hrl;
+        unsigned sv;
+        auto load = [&](int z, FFSpan<W>& f, FFSpan<W>& a, FFSpan<W>& b, float& lh, float& ll, float& rh, float& rl,
+                        unsigned& s) {
+            const int row = rowof(y, z);
+            s = load_states<W>(st0, row + xq);
+            load_ff<W>(f, psi_hi, psi_lo, rowof(y, zwrap(z + 1)) + xq);
+            load_ff<W>(a, psi_hi, psi_lo, rowof(ym, z) + xq);
+            load_ff<W>(b, psi_hi, psi_lo, rowof(yp, z) + xq);
+            lh = psi_hi[row + xl];
+            ll = psi_lo[row + xl];
+            rh = psi_hi[row + xr];
+            rl = psi_lo[row + xr];
+        };
+        load_ff<W>(D, psi_hi, psi_lo, rowof(y, zwrap(z0 - 1)) + xq);
+        load_ff<W>(X, psi_hi, psi_lo, rowof(y, z0) + xq);
+        load(z0, F, A, B, hlh, hll, hrh, hrl, sv);
+        for (int z = z0; z < z1; z++) {
+            FFSpan<W> nF, nA, nB;
+            float nlh = 0.0f, nll = 0.0f, nrh = 0.0f, nrl = 0.0f;
+            unsigned nsv = 0;
+            if (z + 1 < z1) load(z + 1, nF, nA, nB, nlh, nll, nrh, nrl, nsv);
+            const int row = rowof(y, z);
+            unsigned near_bits = 0;
+            float out[W];
 #pragma unroll
             for (int i = 0; i < W; i++) {
-                if ((sv[i] & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
-                const float hc = ch[i + 1], lc = cl[i + 1];
+                out[i] = 0.0f;
+                const unsigned s = lane_on ? (sv >> (8 * i)) & 0xFFu : (unsigned)ST_NEU;
+                if ((s & ST_KIND) != ST_UNKNOWN) continue;
+                if (s & ST_NEAR) {
+                    near_bits |= 1u << i;
+                    continue;
+                }
+                const float hc = X.h[i], lc = X.l[i];
+                const float lfh = i == 0 ? hlh : X.h[i - 1], lfl = i == 0 ? hll : X.l[i - 1];
+                const float rgh = i == W - 1 ? hrh : X.h[i + 1], rgl = i == W - 1 ? hrl : X.l[i + 1];
                 HiSum hs = {0.0f, 0.0f};
-                hs.add(ch[i]);
-                hs.add(ch[i + 2]);
-                hs.add(ah[i]);
-                hs.add(bh[i]);
-                hs.add(dh[i]);
-                hs.add(fh[i]);
-                float lo = __fadd_rn(__fadd_rn(__fadd_rn(cl[i], cl[i + 2]), __fadd_rn(al[i], bl[i])),
-                                     __fadd_rn(dl[i], fl[i]));
+                hs.add(lfh);
+                hs.add(rgh);
+                hs.add(A.h[i]);
+                hs.add(B.h[i]);
+                hs.add(D.h[i]);
+                hs.add(F.h[i]);
+                float lo = __fadd_rn(__fadd_rn(__fadd_rn(lfl, rgl), __fadd_rn(A.l[i], B.l[i])),
+                                     __fadd_rn(D.l[i], F.l[i]));
                 // - diag * psi_c: high product split exactly, low terms to lo
                 const float p = __fmul_rn(diag0.hi, hc);
                 float t = __fmaf_rn(diag0.hi, hc, -p);
@@ -415,27 +427,39 @@ __global__ void __launch_bounds__(256, 3) k_outer_residual_ff(Grid g, ff diag0, 
                 lo = __fsub_rn(lo, t);
                 out[i] = __fadd_rn(hs.s, __fadd_rn(hs.e, lo));
             }
-        }
-        // near-boundary cells: formed by k_outer_residual_near_ff just before
-        const int col0 = (xs + y + z) & 1;
+            // near-boundary cells: formed by k_outer_residual_near_ff just before
+            const int col0 = (xs + y + z) & 1;
+            if (near_bits) {
 #pragma unroll
-        for (int i = 0; i < W; i++)
-            if ((near_bits >> i) & 1u) {
-                if constexpr (SPLIT)
-                    out[i] = r_out[((col0 + i) & 1) * half + ((row + xs + i) >> 1)];
-                else
-                    out[i] = r_out[row + xs + i];
+                for (int i = 0; i < W; i++)
+                    if ((near_bits >> i) & 1u) {
+                        if constexpr (SPLIT)
+                            out[i] = r_out[((col0 + i) & 1) * half + ((row + xs + i) >> 1)];
+                        else
+                            out[i] = r_out[row + xs + i];
+                    }
             }
 #pragma unroll
-        for (int i = 0; i < W; i++) acc = __fmaf_rn(out[i], out[i], acc);
-        if (lane_on) {
-            if constexpr (SPLIT) {
-                rb_st4(r_out, half, row + xs, col0, out[0], out[1], out[2], out[3]);
-            } else if constexpr (W == 4) {
-                *reinterpret_cast<float4*>(r_out + row + xs) = make_float4(out[0], out[1], out[2], out[3]);
-            } else {
-                r_out[row + xs] = out[0];
+            for (int i = 0; i < W; i++) acc = __fmaf_rn(out[i], out[i], acc);
+            if (lane_on) {
+                if constexpr (SPLIT) {
+                    rb_st4(r_out, half, row + xs, col0, out[0], out[1], out[2], out[3]);
+                } else if constexpr (W == 4) {
+                    *reinterpret_cast<float4*>(r_out + row + xs) = make_float4(out[0], out[1], out[2], out[3]);
+                } else {
+                    r_out[row + xs] = out[0];
+                }
             }
+            D = X;
+            X = F;
+            F = nF;
+            A = nA;
+            B = nB;
+            hlh = nlh;
+            hll = nll;
+            hrh = nrh;
+            hrl = nrl;
+            sv = nsv;
         }
     }
     // per-block partial: float within the block (a few thousand terms), one
@@ -1891,15 +1915,19 @@ __global__ void __launch_bounds__(256) k_restrict_rb(Level<float> L, float inv_h
 // A e h^2 = sum over the faces of (e_c - e_nb) + kappa^2 h^2 e_c: the
 // differences carry no rounding of the smooth part of e, which dominates e
 // near convergence (|e| up to 1/kappa^2 times |r|).  A thread owns 8
-// natural cells of a row (the compact cells X0 .. X0+3 of both colours),
-// loaded as in k_restrict_rb; near-boundary cells take r - A e from
-// k_near_residual's scratch (natural index); other cells keep r = 0.
-// Blocks stride over z and leave per-block partial sums of r^2.
-__global__ void __launch_bounds__(256) k_residual_update_rb(Level<float> L, float inv_h2,
-                                                            const uint8_t* __restrict__ st, float* __restrict__ rhs,
-                                                            const float* __restrict__ e,
-                                                            const float* __restrict__ near_res, int half,
-                                                            double* __restrict__ partial) {
+// natural cells of a row (the compact cells X0 .. X0+3 of both colours) and
+// marches through the planes z0 .. z1-1: the even- and odd-x cells of the
+// rows (y, z-1), (y, z) and (y, z+1) roll through registers, so a plane
+// loads the row (y, z+1), the rows (y-1, z) and (y+1, z), r, two halo
+// values and the state bytes, and the loads of plane z+1 are issued before
+// plane z is formed.  Near-boundary cells take r - A e from
+// k_near_residual's scratch (natural index); other cells keep r = 0.  Each
+// block leaves one partial sum of r^2.
+__global__ void __launch_bounds__(256, 2) k_residual_update_rb(Level<float> L, float inv_h2,
+                                                               const uint8_t* __restrict__ st,
+                                                               float* __restrict__ rhs, const float* __restrict__ e,
+                                                               const float* __restrict__ near_res, int half,
+                                                               double* __restrict__ partial, int zc) {
     __shared__ float swarp[8];
     const int nx = L.nx, ny = L.ny, nz = L.nz, nxh = nx >> 1;
     const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
@@ -1907,80 +1935,138 @@ __global__ void __launch_bounds__(256) k_residual_update_rb(Level<float> L, floa
     const bool lane_on = X0 < nxh;
     const int Xq = lane_on ? X0 : 0;
     const float k2h2 = L.diag0 - 6.0f;  // (exact: diag0 in [6, 12))
+    const int z0 = (int)blockIdx.z * zc;
+    const int z1 = z0 + zc < nz ? z0 + zc : nz;
     float acc = 0.0f;
-    int ym = y, yp = y, il = Xq, ir = Xq;
-    if (y < ny) {
+    if (y < ny && z0 < z1) {
+        int ym, yp, il, ir;
         if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
         if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
         if (!wrap_axis(Xq - 1, nxh, L.per[0], il)) il = Xq;
         if (!wrap_axis(Xq + 4, nxh, L.per[0], ir)) ir = Xq;
-    }
-    for (int z = blockIdx.z; z < nz && y < ny; z += gridDim.z) {
-        int zm, zp;
-        if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
-        if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
-        const int pe = (y + z) & 1;
-        const float* E0 = e + pe * half;
-        const float* E1 = e + (pe ^ 1) * half;
-        const int rowh = nxh * (y + ny * z), rown = nx * (y + ny * z) + 2 * Xq;
-        const int hym = nxh * (ym + ny * z), hyp = nxh * (yp + ny * z);
-        const int hzm = nxh * (y + ny * zm), hzp = nxh * (y + ny * zp);
-        float A[4], B[4], r[4], a[4], b[4], d[4], f[4], out[8];
-        ES_VLD(A, 0, E0 + rowh + Xq);
-        ES_VLD(B, 0, E1 + rowh + Xq);
-        const float hl = E1[rowh + il], hr = E0[rowh + ir];
-        const uint2 sw = *reinterpret_cast<const uint2*>(st + rown);
-        ES_VLD(r, 0, rhs + pe * half + rowh + Xq);
-        ES_VLD(a, 0, E1 + hym + Xq);
-        ES_VLD(b, 0, E1 + hyp + Xq);
-        ES_VLD(d, 0, E1 + hzm + Xq);
-        ES_VLD(f, 0, E1 + hzp + Xq);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const unsigned sv = ((k < 2 ? sw.x : sw.y) >> (16 * (k & 1))) & 0xFFu;
-            out[2 * k] = r[k];  // (0 at non-unknown cells)
-            if ((sv & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
-            const float ec = A[k];
-            float o = ec - (k == 0 ? hl : B[k - 1]);
-            o += ec - B[k];
-            o += ec - a[k];
-            o += ec - b[k];
-            o += ec - d[k];
-            o += ec - f[k];
-            o += k2h2 * ec;
-            out[2 * k] = r[k] - o * inv_h2;
+        // (beyond a wall any valid row: only near-boundary cells would read it)
+        auto zwrap = [&](int z) {
+            int w;
+            if (!wrap_axis(z, nz, L.per[2], w)) w = z < 0 ? 0 : nz - 1;
+            return w;
+        };
+        // compact row of (yy, z), and its colour arrays: E0 holds the cells
+        // of colour (y + z) & 1 of row (y, z), the even-x ones
+        auto E0of = [&](int z) { return e + ((y + z) & 1) * half; };
+        // plane z's loads: the even- and odd-x cells of row (y, z+1), the
+        // rows (y -+ 1, z) of both arrays, r of both colours, the halos
+        // and the state bytes
+        float Fe[4], Fo[4], a1[4], b1[4], a0[4], b0[4], rE[4], rO[4], hl, hr;
+        uint2 sw;
+        auto load = [&](int z, float (&fe)[4], float (&fo)[4], float (&pa1)[4], float (&pb1)[4], float (&pa0)[4],
+                        float (&pb0)[4], float (&re)[4], float (&ro)[4], float& l, float& r, uint2& s) {
+            const int pe = (y + z) & 1;
+            const float* E0 = e + pe * half;
+            const float* E1 = e + (pe ^ 1) * half;
+            const int rowh = nxh * (y + ny * z);
+            const int hzp = nxh * (y + ny * zwrap(z + 1));
+            const int hym = nxh * (ym + ny * z), hyp = nxh * (yp + ny * z);
+            s = *reinterpret_cast<const uint2*>(st + nx * (y + ny * z) + 2 * Xq);
+            ES_VLD(fe, 0, E1 + hzp + Xq);
+            ES_VLD(fo, 0, E0 + hzp + Xq);
+            ES_VLD(pa1, 0, E1 + hym + Xq);
+            ES_VLD(pb1, 0, E1 + hyp + Xq);
+            ES_VLD(pa0, 0, E0 + hym + Xq);
+            ES_VLD(pb0, 0, E0 + hyp + Xq);
+            ES_VLD(re, 0, rhs + pe * half + rowh + Xq);
+            ES_VLD(ro, 0, rhs + (pe ^ 1) * half + rowh + Xq);
+            l = E1[rowh + il];
+            r = E0[rowh + ir];
+        };
+        // the even (De, Ae) and odd (Do, Ao) cells of rows (y, z0-1), (y, z0)
+        float De[4], Do[4], Ae[4], Ao[4];
+        {
+            const int zm = zwrap(z0 - 1), pe = (y + z0) & 1;
+            const int hzm = nxh * (y + ny * zm), rowh = nxh * (y + ny * z0);
+            ES_VLD(De, 0, e + (pe ^ 1) * half + hzm + Xq);
+            ES_VLD(Do, 0, E0of(z0) + hzm + Xq);
+            ES_VLD(Ae, 0, E0of(z0) + rowh + Xq);
+            ES_VLD(Ao, 0, e + (pe ^ 1) * half + rowh + Xq);
         }
-        ES_VLD(r, 0, rhs + (pe ^ 1) * half + rowh + Xq);
-        ES_VLD(a, 0, E0 + hym + Xq);
-        ES_VLD(b, 0, E0 + hyp + Xq);
-        ES_VLD(d, 0, E0 + hzm + Xq);
-        ES_VLD(f, 0, E0 + hzp + Xq);
+        load(z0, Fe, Fo, a1, b1, a0, b0, rE, rO, hl, hr, sw);
+        for (int z = z0; z < z1; z++) {
+            float nFe[4], nFo[4], na1[4], nb1[4], na0[4], nb0[4], nrE[4], nrO[4], nhl = 0.0f, nhr = 0.0f;
+            uint2 nsw = make_uint2(0u, 0u);
+            if (z + 1 < z1) load(z + 1, nFe, nFo, na1, nb1, na0, nb0, nrE, nrO, nhl, nhr, nsw);
+            const int pe = (y + z) & 1;
+            const int rowh = nxh * (y + ny * z), rown = nx * (y + ny * z) + 2 * Xq;
+            float out[8];
+            unsigned near = 0;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const unsigned sv = ((k < 2 ? sw.x : sw.y) >> (16 * (k & 1) + 8)) & 0xFFu;
-            out[2 * k + 1] = r[k];
-            if ((sv & (ST_KIND | ST_NEAR)) != ST_UNKNOWN) continue;
-            const float ec = B[k];
-            float o = ec - A[k];
-            o += ec - (k == 3 ? hr : A[k + 1]);
-            o += ec - a[k];
-            o += ec - b[k];
-            o += ec - d[k];
-            o += ec - f[k];
-            o += k2h2 * ec;
-            out[2 * k + 1] = r[k] - o * inv_h2;
-        }
-        // near-boundary cells from the scratch
+            for (int k = 0; k < 4; k++) {
+                const unsigned sv = ((k < 2 ? sw.x : sw.y) >> (16 * (k & 1))) & 0xFFu;
+                out[2 * k] = rE[k];  // (0 at non-unknown cells)
+                if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+                if (sv & ST_NEAR) {
+                    near |= 1u << (2 * k);
+                    continue;
+                }
+                const float ec = Ae[k];
+                float o = ec - (k == 0 ? hl : Ao[k - 1]);
+                o += ec - Ao[k];
+                o += ec - a1[k];
+                o += ec - b1[k];
+                o += ec - De[k];
+                o += ec - Fe[k];
+                o += k2h2 * ec;
+                out[2 * k] = rE[k] - o * inv_h2;
+            }
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const unsigned sv = ((j < 4 ? sw.x : sw.y) >> (8 * (j & 3))) & 0xFFu;
-            if ((sv & (ST_KIND | ST_NEAR)) == (ST_UNKNOWN | ST_NEAR)) out[j] = near_res[rown + j];
-        }
-        if (lane_on) {
+            for (int k = 0; k < 4; k++) {
+                const unsigned sv = ((k < 2 ? sw.x : sw.y) >> (16 * (k & 1) + 8)) & 0xFFu;
+                out[2 * k + 1] = rO[k];
+                if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+                if (sv & ST_NEAR) {
+                    near |= 1u << (2 * k + 1);
+                    continue;
+                }
+                const float ec = Ao[k];
+                float o = ec - Ae[k];
+                o += ec - (k == 3 ? hr : Ae[k + 1]);
+                o += ec - a0[k];
+                o += ec - b0[k];
+                o += ec - Do[k];
+                o += ec - Fo[k];
+                o += k2h2 * ec;
+                out[2 * k + 1] = rO[k] - o * inv_h2;
+            }
+            // near-boundary cells from the scratch
+            if (near) {
 #pragma unroll
-            for (int j = 0; j < 8; j++) acc = __fmaf_rn(out[j], out[j], acc);
-            vst(rhs + pe * half + rowh + X0, out[0], out[2], out[4], out[6]);
-            vst(rhs + (pe ^ 1) * half + rowh + X0, out[1], out[3], out[5], out[7]);
+                for (int j = 0; j < 8; j++)
+                    if ((near >> j) & 1u) out[j] = near_res[rown + j];
+            }
+            if (lane_on) {
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc = __fmaf_rn(out[j], out[j], acc);
+                vst(rhs + pe * half + rowh + X0, out[0], out[2], out[4], out[6]);
+                vst(rhs + (pe ^ 1) * half + rowh + X0, out[1], out[3], out[5], out[7]);
+            }
+            // plane z+1's even cells are the odd-colour array of row z's
+            // parity, so the roll keeps the even / odd roles
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                De[k] = Ae[k];
+                Do[k] = Ao[k];
+                Ae[k] = Fe[k];
+                Ao[k] = Fo[k];
+                Fe[k] = nFe[k];
+                Fo[k] = nFo[k];
+                a1[k] = na1[k];
+                b1[k] = nb1[k];
+                a0[k] = na0[k];
+                b0[k] = nb0[k];
+                rE[k] = nrE[k];
+                rO[k] = nrO[k];
+            }
+            hl = nhl;
+            hr = nhr;
+            sw = nsw;
         }
     }
     float v = acc;
@@ -2882,6 +2968,19 @@ void set_coarse_smem(const es_ctx* c) {
 
 // Algorithmic bytes per cell: psi (8: double, or float-float) and the state
 // byte in, r out (8 as double, 4 as the float right-hand side).
+// Grid of a marching residual pass over a level of nz planes with (gx, gy)
+// blocks per plane: zc planes per block, about eight blocks per SM in all
+// (up to 16 planes each), and no more blocks than partial-sum slots.
+static void res_march_grid(const es_ctx* c, int gx, int gy, int nz, int& gz, int& zc) {
+    const long long plane = (long long)gx * gy;
+    zc = (int)(plane * nz / (8LL * c->n_sm));
+    zc = zc < 1 ? 1 : (zc > 16 ? 16 : zc);
+    const long long slots = (long long)res_partial_slots(c->g.nx, c->g.ny, c->red_blocks);
+    const long long planes = slots / plane;  // >= 1
+    if ((nz + zc - 1) / zc > planes) zc = (int)((nz + planes - 1) / planes);
+    gz = (nz + zc - 1) / zc;
+}
+
 cudaError_t launch_outer_residual(es_ctx* c) {
     const double diag0 = 6.0 + c->S.kappa * c->S.kappa;
     ProfScope ps(c, "outer_residual", -1, (double)c->g.N * (mixed(c) ? 13.0 : 17.0));
@@ -2896,35 +2995,29 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         }
         const int W = (c->g.nx % 4) == 0 ? 4 : 1;
         const int gx = (c->g.nx / W + 31) / 32, gy = (c->g.ny + 7) / 8;
-        int gz = kResPartials / (gx * gy);
-        gz = gz < 1 ? 1 : (gz > c->g.nz ? c->g.nz : gz);
+        int gz, zc;
+        res_march_grid(c, gx, gy, c->g.nz, gz, zc);
         const dim3 grd(gx, gy, gz), blk(32, 8);
         const dim3 ngrd(near_grid_x(c), 2 * kNearSegs);
+        const ff d0 = ff_from_double(diag0);
+        float* r = (float*)c->rhs[0];
         if (c->rb0) {
             // r goes to the colour-split right-hand side of the finest level
             k_outer_residual_near_ff<RbMap><<<ngrd, 256, 0, c->stream>>>(
-                c->g, ff_from_double(diag0), wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner,
-                (const float2*)c->pbc, c->near_list[0], c->near_count, c->near_cap[0], (float*)c->rhs[0],
-                RbMap{(int)(c->g.N / 2)});
-            k_outer_residual_ff<4, true><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall, c->psi32,
-                                                                      c->psi_lo, c->st[0], c->owner,
-                                                                      (const float2*)c->pbc, mask,
-                                                                      (float*)c->rhs[0], c->partial);
+                c->g, d0, wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner, (const float2*)c->pbc,
+                c->near_list[0], c->near_count, c->near_cap[0], r, RbMap{(int)(c->g.N / 2)});
+            k_outer_residual_ff<4, true><<<grd, blk, 0, c->stream>>>(c->g, d0, c->psi32, c->psi_lo, c->st[0], r,
+                                                                      c->partial, zc);
         } else {
             k_outer_residual_near_ff<NatMap><<<ngrd, 256, 0, c->stream>>>(
-                c->g, ff_from_double(diag0), wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner,
-                (const float2*)c->pbc, c->near_list[0], c->near_count, c->near_cap[0], (float*)c->rhs[0],
-                NatMap{});
+                c->g, d0, wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner, (const float2*)c->pbc,
+                c->near_list[0], c->near_count, c->near_cap[0], r, NatMap{});
             if (W == 4)
-                k_outer_residual_ff<4, false><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall,
-                                                                           c->psi32, c->psi_lo, c->st[0], c->owner,
-                                                                           (const float2*)c->pbc, mask,
-                                                                           (float*)c->rhs[0], c->partial);
+                k_outer_residual_ff<4, false><<<grd, blk, 0, c->stream>>>(c->g, d0, c->psi32, c->psi_lo, c->st[0],
+                                                                           r, c->partial, zc);
             else
-                k_outer_residual_ff<1, false><<<grd, blk, 0, c->stream>>>(c->g, ff_from_double(diag0), wall,
-                                                                           c->psi32, c->psi_lo, c->st[0], c->owner,
-                                                                           (const float2*)c->pbc, mask,
-                                                                           (float*)c->rhs[0], c->partial);
+                k_outer_residual_ff<1, false><<<grd, blk, 0, c->stream>>>(c->g, d0, c->psi32, c->psi_lo, c->st[0],
+                                                                           r, c->partial, zc);
         }
         k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
         count(c, 3);
@@ -3039,10 +3132,10 @@ cudaError_t launch_residual_update(es_ctx* c) {
         L, c->st[0], (const float*)c->rhs[0], (const float*)c->e[0], c->near_list[0], c->near_count,
         c->near_cap[0], 1.0f / L.h2, scratch, EAcc<float, float>{1.0f, 1.0f}, RbMap{N / 2});
     const int gx = (nxh / 4 + 31) / 32, gy = (L.ny + 7) / 8;
-    int gz = kResPartials / (gx * gy);
-    gz = gz < 1 ? 1 : (gz > L.nz ? L.nz : gz);
+    int gz, zc;
+    res_march_grid(c, gx, gy, L.nz, gz, zc);
     k_residual_update_rb<<<dim3(gx, gy, gz), dim3(32, 8), 0, c->stream>>>(
-        L, 1.0f / L.h2, c->st[0], (float*)c->rhs[0], (const float*)c->e[0], scratch, N / 2, c->partial);
+        L, 1.0f / L.h2, c->st[0], (float*)c->rhs[0], (const float*)c->e[0], scratch, N / 2, c->partial, zc);
     k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
     count(c, 3);
     return cudaGetLastError();
