@@ -152,7 +152,7 @@ struct FbPsi {
 // HBM: the cell reads 4 bytes of psi (the neighbours' come from cache)
 // instead of 12 of stored f_b.  Cells next to obstacles or walls read the
 // stored field (their D3Q7 ghost-value gradient, k_body_force_near).
-template <class S, bool SLIP, bool FBPSI, class C = typename Store<S>::C>
+template <class S, bool SLIP, bool FBPSI, bool EARLY, class C = typename Store<S>::C>
 __device__ __forceinline__ void lbm_cell(const Grid& g, const Streams<S>& P, const uint8_t* __restrict__ flags,
                                          const int32_t* __restrict__ owner, const DParticle* __restrict__ part,
                                          const float* __restrict__ partf, const C* __restrict__ fb, C ax, C ay,
@@ -163,16 +163,31 @@ __device__ __forceinline__ void lbm_cell(const Grid& g, const Streams<S>& P, con
     const int nx = g.nx, nxy = g.nx * g.ny;
     const int c = x + nx * (y + g.ny * z);
     const uint8_t fl = flags[c];
+    // The pull sources x - e_q with every axis wrapped: in bounds for every
+    // cell, and the true sources of all cells but the few next to an
+    // obstacle or a wall.  EARLY: they are loaded before the cell's flags
+    // arrive, so the two loads do not follow one another (obstacle cells
+    // load and drop them, and cells next to an obstacle keep those of their
+    // fluid neighbours, the same cells, and replace the others below);
+    // otherwise each path loads what it needs after the flags (fewer live
+    // registers, for the persistent batched kernel).  Same values either way.
+    const int sx[3] = {(x == nx - 1 ? 0 : x + 1) - x, 0, (x == 0 ? nx - 1 : x - 1) - x};
+    const int sy[3] = {((y == g.ny - 1 ? 0 : y + 1) - y) * nx, 0, ((y == 0 ? g.ny - 1 : y - 1) - y) * nx};
+    const int sz[3] = {((z == g.nz - 1 ? 0 : z + 1) - z) * nxy, 0, ((z == 0 ? g.nz - 1 : z - 1) - z) * nxy};
+    C f[19];
+    auto pull = [&]() {
+#pragma unroll
+        for (int q = 0; q < 19; q++) {
+            const int s_ = c + sx[1 + cx(q)] + sy[1 + cy(q)] + sz[1 + cz(q)];
+            f[q] = St::ld(q, __ldg(P.src[q] + s_));
+        }
+    };
+    if constexpr (EARLY) pull();
     if (fl & F_SOLID) return;  // obstacle cells are not updated
 
-    C f[19];
     C fx, fy, fz;  // body force (Sec. 5.6) plus the uniform acceleration
     if (!(fl & F_NEAR19)) {
-        // all 18 pull sources are fluid cells inside the (periodic) domain;
-        // the offset of x - e_q is a sum of per-axis steps (wrapped at faces)
-        const int sx[3] = {(x == nx - 1 ? 0 : x + 1) - x, 0, (x == 0 ? nx - 1 : x - 1) - x};
-        const int sy[3] = {((y == g.ny - 1 ? 0 : y + 1) - y) * nx, 0, ((y == 0 ? g.ny - 1 : y - 1) - y) * nx};
-        const int sz[3] = {((z == g.nz - 1 ? 0 : z + 1) - z) * nxy, 0, ((z == 0 ? g.nz - 1 : z - 1) - z) * nxy};
+        // all 18 pull sources are fluid cells inside the (periodic) domain
         if constexpr (FBPSI) {
             // psi(x + d) at offset sx[1 - dx] + sy[1 - dy] + sz[1 - dz]
             const float* ps = fp.psi + c;
@@ -205,16 +220,12 @@ __device__ __forceinline__ void lbm_cell(const Grid& g, const Streams<S>& P, con
             fy = fb[N + c] + ay;
             fz = fb[2u * N + c] + az;
         }
-#pragma unroll
-        for (int q = 0; q < 19; q++) {
-            const int s_ = c + sx[1 + cx(q)] + sy[1 + cy(q)] + sz[1 + cz(q)];
-            f[q] = St::ld(q, __ldg(P.src[q] + s_));
-        }
+        if constexpr (!EARLY) pull();
     } else {
         fx = fb[c] + ax;
         fy = fb[N + c] + ay;
         fz = fb[2u * N + c] + az;
-        f[0] = St::ld(0, P.src[0][c]);
+        if constexpr (!EARLY) f[0] = St::ld(0, P.src[0][c]);
 #pragma unroll
         for (int q = 1; q < 19; q++) {
             long long nb;
@@ -228,8 +239,8 @@ __device__ __forceinline__ void lbm_cell(const Grid& g, const Streams<S>& P, con
                 continue;
             }
             const int o = owner[nb];
-            if (o < 0) {
-                f[q] = St::ld(q, P.src[q][nb]);
+            if (o < 0) {  // a fluid source: the value pulled above
+                if constexpr (!EARLY) f[q] = St::ld(q, P.src[q][nb]);
                 continue;
             }
             // moving bounce-back (Eq. LBMMovWall): the population sent from x
@@ -269,17 +280,18 @@ __device__ __forceinline__ void lbm_cell(const Grid& g, const Streams<S>& P, con
 
 // One thread per cell; a block covers blockDim.x cells of blockDim.y rows
 // (the shape is a parameter: es_params.lbm_block).
-// (the reduced forms keep 40 registers a thread, 1,536 threads per SM: more
-// registers and fewer threads measured slower)
+// (the reduced forms cap a thread at 48 registers, 1,280 threads per SM: with
+// the pull loads issued ahead of the flag test, 40 registers spill and 64
+// leave too few threads; both measured slower)
 template <class S, bool SLIP, bool FBPSI = false, class C = typename Store<S>::C>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 3 : 6) k_lbm(Grid g, const Streams<S> P, const uint8_t* __restrict__ flags,
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 3 : 5) k_lbm(Grid g, const Streams<S> P, const uint8_t* __restrict__ flags,
                                              const int32_t* __restrict__ owner, const DParticle* __restrict__ part,
                                              const float* __restrict__ partf, const C* __restrict__ fb, C ax, C ay,
                                              C az, C lam_e, C lam_o, int slip_faces, FbPsi fp) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    lbm_cell<S, SLIP, FBPSI>(g, P, flags, owner, part, partf, fb, ax, ay, az, lam_e, lam_o, slip_faces, fp, x, y,
+    lbm_cell<S, SLIP, FBPSI, true>(g, P, flags, owner, part, partf, fb, ax, ay, az, lam_e, lam_o, slip_faces, fp, x, y,
                              z);
 }
 
@@ -332,12 +344,12 @@ __global__ void __launch_bounds__(kBatchTileX * kBatchTileY, sizeof(S) == 8 ? 6 
         if (x >= R.g.nx || y >= R.g.ny) continue;
         if constexpr (std::is_same<typename Store<S>::C, float>::value) {
             if (R.lazy) {
-                lbm_cell<S, false, true>(R.g, R.P, R.flags, R.owner, R.part, R.partf, R.fb, R.ax, R.ay, R.az,
+                lbm_cell<S, false, true, false>(R.g, R.P, R.flags, R.owner, R.part, R.partf, R.fb, R.ax, R.ay, R.az,
                                          R.lam_e, R.lam_o, 0, R.fp, x, y, z);
                 continue;
             }
         }
-        lbm_cell<S, false, false>(R.g, R.P, R.flags, R.owner, R.part, R.partf, R.fb, R.ax, R.ay, R.az, R.lam_e,
+        lbm_cell<S, false, false, false>(R.g, R.P, R.flags, R.owner, R.part, R.partf, R.fb, R.ax, R.ay, R.az, R.lam_e,
                                   R.lam_o, 0, R.fp, x, y, z);
     }
 }
