@@ -130,6 +130,12 @@ bool colour_split(const es_params* P) {
            P->mg_storage == ES_MG_NATIVE && P->levels >= 2 && P->fine_layout == ES_LAYOUT_AUTO;
 }
 
+// Level 1 colour-split as well: it is then not the coarsest level and its
+// x extent keeps whole 8-cell spans.
+bool colour_split1(const es_params* P) {
+    return colour_split(P) && P->levels >= 3 && (P->dims[0] / 2) % 8 == 0;
+}
+
 size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     long long N = (long long)P->dims[0] * P->dims[1] * P->dims[2];
     const size_t s = P->precision == ES_FP64 ? 8 : 4;  // arithmetic type
@@ -141,6 +147,8 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     b += N * 4;           // list of fluid cells next to obstacles (body force)
     if (colour_split(P))  // per-colour update masks of the finest level
         b += (size_t)2 * P->dims[1] * P->dims[2] * ((P->dims[0] + 63) / 64) * 4;
+    if (colour_split1(P))  // and of level 1
+        b += (size_t)2 * (P->dims[1] / 2) * (P->dims[2] / 2) * ((P->dims[0] / 2 + 63) / 64) * 4;
     size_t lv = 0;
     for (int l = 0; l < P->levels; l++) {
         long long Nl = (long long)(P->dims[0] >> l) * (P->dims[1] >> l) * (P->dims[2] >> l);
@@ -304,6 +312,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->g.nz = params->dims[2];
     for (int a = 0; a < 3; a++) c->g.per[a] = params->periodic[a] ? 1 : 0;
     c->rb0 = colour_split(params);
+    c->rb1 = colour_split1(params);
     c->fb_lazy = false;
     c->bulk_smem_set = false;
     c->bulk_blocks = 0;
@@ -393,6 +402,8 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->d_status = (int*)A(64);
     c->rb_wpr = (c->g.nx + 63) / 64;
     c->rbmask = c->rb0 ? (uint32_t*)A((size_t)2 * c->g.ny * c->g.nz * c->rb_wpr * 4) : nullptr;
+    c->rb_wpr1 = (c->ln[1][0] + 63) / 64;
+    c->rbmask1 = c->rb1 ? (uint32_t*)A((size_t)2 * c->ln[1][1] * c->ln[1][2] * c->rb_wpr1 * 4) : nullptr;
     if (!ok) {
         release(c);
         delete c;

@@ -121,6 +121,8 @@ struct es_ctx {
     uint32_t* rbmask;           // colour-split finest level: per colour, one bit per cell (compact order,
                                 // each row padded to rb_wpr words): 1 = interior unknown cell
     int rb_wpr;                 // mask words per row: ceil(nx / 64)
+    uint32_t* rbmask1;          // the same for level 1 when it is colour-split as well (rb1)
+    int rb_wpr1;
     int* bf_list;               // fluid cells with a non-fluid D3Q19 neighbour (level 0), kNearSegs segments
     int bf_cap;                 // capacity of one segment
     int* bf_count;              // device: kNearSegs counts
@@ -143,6 +145,7 @@ struct es_ctx {
     float e_scale;   // ES_MG_FP16: scale of the finest level's stored correction
     int slip;        // bit f: face f (x-lo, x-hi, y-lo, ...) of a non-periodic axis is free-slip
     bool rb0;        // the finest level's e and rhs in the colour-split layout (reduced forms)
+    bool rb1;        // level 1's as well (rb0, at least three levels, nx / 2 % 8 == 0)
     bool fb_lazy;    // f_b is derived from psi by the stream-collide (set by a solve when
                      // fb_fused); the stored field then holds it only after a read or
                      // at the cells next to obstacles
@@ -243,6 +246,10 @@ inline int near_grid_x(const es_ctx* c) {
 }
 
 // Capacity of the per-block partial-sum array of the residual norm.
+// Levels 0 and 1 may be stored colour-split (e and rhs: one colour's cells,
+// then the other's, each in natural order; the states stay natural).
+inline bool split_level(const es_ctx* c, int l) { return (l == 0 && c->rb0) || (l == 1 && c->rb1); }
+
 constexpr int kResPartials = 8192;
 // Partial-sum slots of the blocked residual norms: one per block of the
 // marching residual passes (at most kResPartials planes of blocks, and a

@@ -475,9 +475,13 @@ __global__ void k_near_bits(int nx, int ny, int nz, int px, int py, int pz, uint
 // row (y, z) goes to segment row mod kNearSegs of each colour; a warp walks its row 32 cells at a time with
 // one atomic per step on the segment's counter.  The order within a
 // segment depends on the atomics' order; the consumers write each cell's
-// value to its own place, so results do not.
+// value to its own place, so results do not.  With rbmask (a colour-split
+// level, nx even), also its per-colour update masks as k_lists_l0 builds
+// them: a 32-cell step holds 16 cells of each colour, compact places
+// x0 / 2 .. x0 / 2 + 15, which fill the low or the high half of one word.
 __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const uint8_t* __restrict__ st,
-                                                   int cap, int* list, int* count) {
+                                                   int cap, int* list, int* count, uint32_t* __restrict__ rbmask,
+                                                   int wpr) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -486,10 +490,25 @@ __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const
     const int y = row % ny, z = row / ny;
     for (int x0 = 0; x0 < nx; x0 += 32) {
         const int x = x0 + lane;
-        bool take = false;
+        bool take = false, inner = false;
         if (x < nx) {
             const uint8_t s = st[x + nx * row];
             take = (s & ST_KIND) == ST_UNKNOWN && (s & ST_NEAR);
+            inner = (s & (ST_KIND | ST_NEAR)) == ST_UNKNOWN;
+        }
+        if (rbmask) {
+#pragma unroll
+            for (int colour = 0; colour < 2; colour++) {
+                const bool b = inner && ((x + y + z) & 1) == colour;
+                const unsigned v = __reduce_or_sync(0xffffffffu, b ? 1u << (lane >> 1) : 0u);
+                if (lane == 0) {
+                    uint32_t* m = rbmask + (size_t)colour * ((size_t)ny * nz * wpr) + (size_t)wpr * row + x0 / 64;
+                    if ((x0 & 63) == 0)
+                        *m = v;  // (the high half follows in the next step, or stays 0 past the row's end)
+                    else
+                        *m |= v << 16;
+                }
+            }
         }
 #pragma unroll
         for (int colour = 0; colour < 2; colour++) {
@@ -648,7 +667,8 @@ cudaError_t launch_near_lists(es_ctx* c) {
         const int nb = (rows + 7) / 8;  // a warp per row: every row in flight at once
         ProfScope ps(c, "cell_lists", l, (double)rows * n[0]);
         k_near_list<<<nb, 256, 0, c->stream>>>(n[0], n[1], n[2], c->st[l], c->near_cap[l], c->near_list[l],
-                                                c->near_count + 2 * kNearSegs * l);
+                                                c->near_count + 2 * kNearSegs * l, l == 1 ? c->rbmask1 : nullptr,
+                                                c->rb_wpr1);
         count(c);
     }
     if (l0 == 0) {

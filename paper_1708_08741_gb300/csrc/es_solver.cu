@@ -1624,10 +1624,14 @@ __global__ void __launch_bounds__(128) k_prolong(Level<T> L, const uint8_t* __re
 
 // Vectorized prolongation: a thread owns 4 fine cells of a row (nx % 4 == 0)
 // and adds the correction of their 2 parents.
+// SPLIT: e of this level colour-split (half: half its cells); chalf != 0:
+// the coarse e colour-split too (chalf: half the coarse cells).  C is even,
+// so C and C + 1 sit at place C / 2 of their colours.
 template <class T, class E, bool SPLIT = false>
 __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __restrict__ st, E* __restrict__ e,
                                                    int cnx, int cny, const uint8_t* __restrict__ cst,
-                                                   const T* __restrict__ ce, EAcc<T, E> A, int half = 0) {
+                                                   const T* __restrict__ ce, EAcc<T, E> A, int half = 0,
+                                                   int chalf = 0) {
     const int xs = 4 * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
     if (xs >= L.nx || y >= L.ny) return;
@@ -1635,7 +1639,15 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
     const int C = (xs >> 1) + cnx * ((y >> 1) + cny * (z >> 1));
     const unsigned sw = *reinterpret_cast<const unsigned*>(st + c);
     const uint8_t c0 = cst[C] & ST_KIND, c1 = cst[C + 1] & ST_KIND;
-    const T e0 = ce[C], e1 = ce[C + 1];
+    T e0, e1;
+    if (chalf) {
+        const int cc = ((xs >> 1) + (y >> 1) + (z >> 1)) & 1;
+        e0 = ce[cc * chalf + (C >> 1)];
+        e1 = ce[(cc ^ 1) * chalf + (C >> 1)];
+    } else {
+        e0 = ce[C];
+        e1 = ce[C + 1];
+    }
     const int col0 = (xs + y + z) & 1;
     Q4<T> q;
     if constexpr (SPLIT)
@@ -1653,6 +1665,17 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
         rb_st4(e, half, c, col0, v[0], v[1], v[2], v[3]);
     else
         A.st4(e + c, v[0], v[1], v[2], v[3]);
+}
+
+// Stores coarse cells C .. C+3 (C % 4 == 0, the first of colour col) of a
+// right-hand side: natural order, or colour-split when chalf (half the
+// coarse level's cells) is not 0.
+__device__ __forceinline__ void store_coarse4(float* __restrict__ crhs, int C, int col, int chalf,
+                                              const float (&v)[4]) {
+    if (chalf)
+        rb_st4(crhs, chalf, C, col, v[0], v[1], v[2], v[3]);
+    else
+        *reinterpret_cast<float4*>(crhs + C) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // Vectorized residual + restriction: a thread owns 2 coarse cells of a
@@ -1812,7 +1835,7 @@ __global__ void __launch_bounds__(256) k_restrict_rb(Level<float> L, float inv_h
                                                      const float* __restrict__ rhs, const float* __restrict__ e,
                                                      const float* __restrict__ near_res, int cnx, int cny,
                                                      const uint8_t* __restrict__ cst, float* __restrict__ crhs,
-                                                     int half) {
+                                                     int half, int chalf) {
     __shared__ float4 part[8][32];
     const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
     const int crow = threadIdx.y >> 2, sub = threadIdx.y & 3;
@@ -1906,7 +1929,7 @@ __global__ void __launch_bounds__(256) k_restrict_rb(Level<float> L, float inv_h
     float v[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) v[k] = ((ck[k] & ST_KIND) == ST_UNKNOWN) ? sum[k] / 8.0f : 0.0f;
-    *reinterpret_cast<float4*>(crhs + C) = make_float4(v[0], v[1], v[2], v[3]);
+    store_coarse4(crhs, C, (X0 + cy + cz) & 1, chalf, v);
 }
 
 // The residual of the corrected potential on the colour-split finest level
@@ -2098,7 +2121,7 @@ __global__ void __launch_bounds__(128) k_restrict_red_rb(Level<float> L, float i
                                                          const float* __restrict__ e,
                                                          const float* __restrict__ near_res, int cnx, int cny,
                                                          const uint8_t* __restrict__ cst, float* __restrict__ crhs,
-                                                         int half) {
+                                                         int half, int chalf) {
     __shared__ float4 part[4][32];
     const int nxh = L.nx >> 1, ny = L.ny, nz = L.nz;
     const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
@@ -2167,7 +2190,7 @@ __global__ void __launch_bounds__(128) k_restrict_red_rb(Level<float> L, float i
     float v[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) v[k] = ((ck[k] & ST_KIND) == ST_UNKNOWN) ? sum[k] / 8.0f : 0.0f;
-    *reinterpret_cast<float4*>(crhs + C) = make_float4(v[0], v[1], v[2], v[3]);
+    store_coarse4(crhs, C, (X0 + cy + cz) & 1, chalf, v);
 }
 
 // Coarsest level: one thread block holds the level in shared memory and
@@ -2684,8 +2707,16 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
     // one cell is its own neighbour: no red-black split)
     const bool use_rb = kNative && c->P.smoother == ES_SMOOTH_FUSED && (L.nx % 128) == 0 &&
                         (!L.per[1] || L.ny >= 2) && (!L.per[2] || L.nz >= 2);
-    // the finest level of the reduced forms in the colour-split layout
-    const bool split = kNative && std::is_same<T, float>::value && l == 0 && c->rb0;
+    // levels of the reduced forms in the colour-split layout (the finest,
+    // and level 1 when it is split as well)
+    const bool split = kNative && std::is_same<T, float>::value && split_level(c, l);
+    const uint32_t* rbmask = l == 0 ? c->rbmask : c->rbmask1;
+    const int rb_wpr = l == 0 ? c->rb_wpr : c->rb_wpr1;
+    // half the cells of the next level when it is split too (its right-hand
+    // side is restricted, and its correction prolonged, in that layout)
+    const int chalf = split && l + 1 < c->L && split_level(c, l + 1)
+                          ? c->ln[l + 1][0] * c->ln[l + 1][1] * c->ln[l + 1][2] / 2
+                          : 0;
     const RbMap rb{Nl / 2};
     // reduced forms, Gauss-Seidel: the pre-smoothing ends with a black half
     // sweep, after which only red residuals remain (the restriction adds the
@@ -2735,7 +2766,7 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                 const NearWork nw{st, c->near_list[l], cnt, c->near_cap[l]};
                 // rows of up to 256 compact cells: staged by bulk copies on request
                 const int nxh = L.nx / 2;
-                const bool bulk = nxh <= 256 && c->P.sweep_staging == ES_STAGE_BULK;
+                const bool bulk = l == 0 && nxh <= 256 && c->P.sweep_staging == ES_STAGE_BULK;
                 BulkShape bs{nxh / 4, 0, 0};
                 dim3 bgrd;
                 size_t bsm = 0;
@@ -2764,12 +2795,12 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                     ProfScope ps(c, "smooth_half", l,
                                  !first ? b_rb_half : (col == 0 ? b_rb_first : b_rb_half - nl * own));
                     if (bulk)
-                        k_smooth_rb_bulk<T><<<bgrd, 256, bsm, c->stream>>>(L, inv_diag0, c->rbmask, c->rb_wpr, rhs, e,
+                        k_smooth_rb_bulk<T><<<bgrd, 256, bsm, c->stream>>>(L, inv_diag0, rbmask, rb_wpr, rhs, e,
                                                                            col, fs, omega, rb.half, nw, bs,
                                                                            c->d_status);
                     else
-                        k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, c->rbmask, c->rb_wpr, rhs, e,
-                                                                     col, fs, omega, rb.half, nw, zc);
+                        k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, rbmask, rb_wpr, rhs, e, col,
+                                                                     fs, omega, rb.half, nw, zc);
                 }
                 count(c, 2);
                 return;
@@ -2875,14 +2906,14 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                     const dim3 qgrd((m[0] / 4 + 31) / 32, m[1], m[2]);
                     k_restrict_red_rb<<<qgrd, dim3(32, 4), 0, c->stream>>>(L, (T)1 / L.h2, st, rhs, e, scratch,
                                                                            m[0], m[1], c->st[l + 1],
-                                                                           (T*)c->rhs[l + 1], rb.half);
+                                                                           (T*)c->rhs[l + 1], rb.half, chalf);
                     done = true;
                 } else if (split) {
                     k_near_residual<T, E, RbMap><<<ngrd, 256, 0, c->stream>>>(
                         L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
                     const dim3 qgrd((m[0] / 4 + 31) / 32, (m[1] + 1) / 2, m[2]);
                     k_restrict_rb<<<qgrd, vblk, 0, c->stream>>>(L, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1],
-                                                                c->st[l + 1], (T*)c->rhs[l + 1], rb.half);
+                                                                c->st[l + 1], (T*)c->rhs[l + 1], rb.half, chalf);
                     done = true;
                 }
             }
@@ -2909,7 +2940,7 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
         if constexpr (kNative && std::is_same<T, float>::value) {
             if (split) {
                 k_prolong_v<T, E, true><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1],
-                                                                      (const T*)c->e[l + 1], A, rb.half);
+                                                                      (const T*)c->e[l + 1], A, rb.half, chalf);
                 done = true;
             }
         }
