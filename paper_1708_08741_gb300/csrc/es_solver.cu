@@ -1678,6 +1678,51 @@ __device__ __forceinline__ void store_coarse4(float* __restrict__ crhs, int C, i
         *reinterpret_cast<float4*>(crhs + C) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// Prolongation onto a colour-split level ahead of a Gauss-Seidel
+// post-smoothing (omega = 1): the red half sweep that follows replaces each
+// red unknown cell without reading it, so only the black cells -- the
+// neighbours it reads -- take the correction (e += e_{l+1}(parent) at
+// unknown cells whose parent is unknown, as k_prolong_v); the red cells
+// keep a stale value until that sweep overwrites them.  A thread owns the
+// black compact cells X0 .. X0+3 of one row (natural x = 2X + O,
+// O = (1 + y + z) & 1), whose parents are the consecutive coarse cells
+// X0 .. X0+3 of coarse row (y/2, z/2).  chalf != 0: the coarse e
+// colour-split (chalf: half the coarse cells).
+__global__ void __launch_bounds__(256) k_prolong_black_rb(Level<float> L, const uint8_t* __restrict__ st,
+                                                          float* __restrict__ e, int half, int cnx, int cny,
+                                                          const uint8_t* __restrict__ cst,
+                                                          const float* __restrict__ ce, int chalf) {
+    const int nxh = L.nx >> 1;
+    const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    if (X0 >= nxh || y >= L.ny) return;
+    const int O = (1 + y + z) & 1;
+    float* eb = e + half + nxh * (y + L.ny * z) + X0;
+    const uint2 sw = *reinterpret_cast<const uint2*>(st + L.nx * (y + L.ny * z) + 2 * X0);
+    const int C = X0 + cnx * ((y >> 1) + cny * (z >> 1));
+    const uchar4 cs = *reinterpret_cast<const uchar4*>(cst + C);
+    const uint8_t ck[4] = {cs.x, cs.y, cs.z, cs.w};
+    float cv[4];
+    if (chalf) {
+        const Q4<float> q = rb_ld4(ce, chalf, C, (X0 + (y >> 1) + (z >> 1)) & 1);
+        cv[0] = q.v0;
+        cv[1] = q.v1;
+        cv[2] = q.v2;
+        cv[3] = q.v3;
+    } else {
+        ES_VLD(cv, 0, ce + C);
+    }
+    float v[4];
+    ES_VLD(v, 0, eb);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int j = 2 * k + O;  // natural offset of the black cell in the 8-cell span
+        const unsigned sv = ((j < 4 ? sw.x : sw.y) >> (8 * (j & 3))) & ST_KIND;
+        if (sv == ST_UNKNOWN && (ck[k] & ST_KIND) == ST_UNKNOWN) v[k] += cv[k];
+    }
+    vst(eb, v[0], v[1], v[2], v[3]);
+}
+
 // Vectorized residual + restriction: a thread owns 2 coarse cells of a
 // coarse row, i.e. a 4 x 2 x 2 block of fine cells (nx % 4 == 0).  For each
 // of its 4 fine rows it loads the row (with one cell of x halo from the
@@ -2104,93 +2149,138 @@ __global__ void __launch_bounds__(256, 2) k_residual_update_rb(Level<float> L, f
 }
 
 // Residual + restriction right after a black Gauss-Seidel half sweep
-// (omega = 1) on the colour-split finest level.  That half sweep solved
-// every black cell's equation exactly for the red values around it, which
-// it does not change, so the black residuals vanish (up to rounding) and
-// the restricted residual is the mean of the 4 red children's residuals
-// (the 4 black children count as 0).  Laid out as k_smooth_rb for the red
-// colour: a thread forms the residuals of 4 red cells of one fine row
-// (compact cells X0 .. X0+3, the red children of coarse cells X0 .. X0+3),
-// reading the red e and rhs and the black e around them (7 bytes per fine
-// cell instead of 9); the 4 fine rows of a coarse row are the block's 4
-// warps, added in the order of k_restrict_v (dk outer, dj inner).
-// Near-boundary red children come from k_near_residual (red segments).
-__global__ void __launch_bounds__(128) k_restrict_red_rb(Level<float> L, float inv_h2,
-                                                         const uint8_t* __restrict__ st,
-                                                         const float* __restrict__ rhs,
-                                                         const float* __restrict__ e,
-                                                         const float* __restrict__ near_res, int cnx, int cny,
-                                                         const uint8_t* __restrict__ cst, float* __restrict__ crhs,
-                                                         int half, int chalf) {
-    __shared__ float4 part[4][32];
+// (omega = 1) on a colour-split level.  That half sweep solved every black
+// cell's equation exactly for the red values around it, which it does not
+// change, so the black residuals vanish (up to rounding) and the restricted
+// residual is the mean of the 4 red children's residuals (the 4 black
+// children count as 0).  A thread forms the residuals of the red compact
+// cells X0 .. X0+3 of fine row y (the red children of coarse cells X0 ..
+// X0+3) and marches up the fine planes 2 cz0 .. 2 cz1 - 1: the black rows
+// (y, z-1), (y, z) and (y, z+1) roll through registers, so a plane loads
+// the black rows (y, z+1), (y-1, z) and (y+1, z), one halo value, the red
+// e and rhs of (y, z) and the state bytes (about 7 bytes per fine cell),
+// and the loads of plane z+1 are issued before plane z is formed.  The two
+// warps of a coarse row (dj = 0, 1) meet in shared memory after each pair
+// of fine planes, and the 4 red children are added in the order of
+// k_restrict_v (dk outer, dj inner).  Near-boundary red children come from
+// k_near_residual (red segments).  chalf != 0: the coarse right-hand side
+// is stored colour-split (chalf: half the coarse cells).
+constexpr int kRestrictRows = 4;  // coarse rows per block (2 warps each)
+
+__global__ void __launch_bounds__(32 * 2 * kRestrictRows)
+    k_restrict_red_rb(Level<float> L, float inv_h2, const uint8_t* __restrict__ st, const float* __restrict__ rhs,
+                      const float* __restrict__ e, const float* __restrict__ near_res, int cnx, int cny, int cnz,
+                      const uint8_t* __restrict__ cst, float* __restrict__ crhs, int half, int chalf, int czc) {
+    __shared__ float4 part[2][kRestrictRows][4][32];  // (coarse-plane parity, coarse row, 2 dk + dj, lane)
     const int nxh = L.nx >> 1, ny = L.ny, nz = L.nz;
     const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
-    const int cy = blockIdx.y, cz = blockIdx.z;
-    const int dj = threadIdx.y & 1, dk = threadIdx.y >> 1;
-    const int y = 2 * cy + dj, z = 2 * cz + dk;
-    const bool lane_on = X0 < cnx;
-    const int iq = lane_on ? X0 : 0;
-    const int O = (y + z) & 1;  // red cells of this row: x = 2 i + O
+    const int dj = threadIdx.y & 1, row = threadIdx.y >> 1;
+    const int cy = blockIdx.y * kRestrictRows + row;
+    const int cz0 = (int)blockIdx.z * czc;
+    const int cz1 = cz0 + czc < cnz ? cz0 + czc : cnz;
+    const bool row_on = cy < cny;
+    const bool lane_on = X0 < cnx && row_on;
+    const int iq = X0 < cnx ? X0 : 0;
+    const int y = 2 * (row_on ? cy : 0) + dj;  // (rows past the end march a valid row; nothing is stored)
     const float* eo = e + half;  // black
-    int ym, yp, zm, zp, il, ir;
+    int ym, yp, il, ir;
     if (!wrap_axis(y - 1, ny, L.per[1], ym)) ym = y;
     if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
-    if (!wrap_axis(z - 1, nz, L.per[2], zm)) zm = z;
-    if (!wrap_axis(z + 1, nz, L.per[2], zp)) zp = z;
     if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
     if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
-    const int rowh = nxh * (y + ny * z), rown = L.nx * (y + ny * z) + 2 * iq;
-    float c[4], ox[6], a[4], b[4], d[4], f[4], r[4];
-    ES_VLD(c, 0, e + rowh + iq);
-    ES_VLD(ox, 1, eo + rowh + iq);
-    ox[0] = O == 0 ? eo[rowh + il] : 0.0f;
-    ox[5] = O == 1 ? eo[rowh + ir] : 0.0f;
-    ES_VLD(a, 0, eo + nxh * (ym + ny * z) + iq);
-    ES_VLD(b, 0, eo + nxh * (yp + ny * z) + iq);
-    ES_VLD(d, 0, eo + nxh * (y + ny * zm) + iq);
-    ES_VLD(f, 0, eo + nxh * (y + ny * zp) + iq);
-    ES_VLD(r, 0, rhs + rowh + iq);
-    const uint2 sw = *reinterpret_cast<const uint2*>(st + rown);
-    float res[4];
+    auto zwrap = [&](int z) {
+        int w;
+        if (!wrap_axis(z, nz, L.per[2], w)) w = z < 0 ? 0 : nz - 1;  // (the row itself beyond a wall)
+        return w;
+    };
+    auto hrow = [&](int yy, int z) { return nxh * (yy + ny * z); };
+    // plane z's loads: the black rows (y, z+1), (y-1, z), (y+1, z), the halo
+    // of (y, z), the red e and rhs of (y, z), the state bytes
+    float F[4], A[4], B[4], Cr[4], R[4], h;
+    uint2 sw;
+    auto load = [&](int z, float (&f)[4], float (&a)[4], float (&b)[4], float (&c)[4], float (&r)[4], float& hv,
+                    uint2& s) {
+        const int rz = hrow(y, z);
+        ES_VLD(f, 0, eo + hrow(y, zwrap(z + 1)) + iq);
+        ES_VLD(a, 0, eo + hrow(ym, z) + iq);
+        ES_VLD(b, 0, eo + hrow(yp, z) + iq);
+        ES_VLD(c, 0, e + rz + iq);
+        ES_VLD(r, 0, rhs + rz + iq);
+        hv = ((y + z) & 1) == 0 ? eo[rz + il] : eo[rz + ir];
+        s = *reinterpret_cast<const uint2*>(st + L.nx * (y + ny * z) + 2 * iq);
+    };
+    const int z0 = 2 * cz0, z1 = 2 * cz1;
+    float D[4], X[4];
+    ES_VLD(D, 0, eo + hrow(y, zwrap(z0 - 1)) + iq);
+    ES_VLD(X, 0, eo + hrow(y, z0) + iq);
+    if (z0 < z1) load(z0, F, A, B, Cr, R, h, sw);
+    for (int z = z0; z < z1; z++) {
+        float nF[4], nA[4], nB[4], nC[4], nR[4], nh = 0.0f;
+        uint2 nsw = make_uint2(0u, 0u);
+        if (z + 1 < z1) load(z + 1, nF, nA, nB, nC, nR, nh, nsw);
+        const int O = (y + z) & 1;  // red cells of this row: x = 2 i + O
+        const int rown = L.nx * (y + ny * z) + 2 * iq;
+        // the black row with its halo: ox[0] left of X0 (O = 0), ox[5] right of X0+3 (O = 1)
+        const float ox[6] = {O == 0 ? h : 0.0f, X[0], X[1], X[2], X[3], O == 1 ? h : 0.0f};
+        float res[4];
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int bit = 2 * k + O;
-        const unsigned sv = ((bit < 4 ? sw.x : sw.y) >> (8 * (bit & 3))) & 0xFFu;
-        res[k] = 0.0f;
-        if ((sv & ST_KIND) != ST_UNKNOWN) continue;
-        if (sv & ST_NEAR) {
-            res[k] = near_res[rown + bit];
-            continue;
+        for (int k = 0; k < 4; k++) {
+            const int bit = 2 * k + O;
+            const unsigned sv = ((bit < 4 ? sw.x : sw.y) >> (8 * (bit & 3))) & 0xFFu;
+            res[k] = 0.0f;
+            if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+            if (sv & ST_NEAR) {
+                res[k] = near_res[rown + bit];
+                continue;
+            }
+            float o = O == 0 ? ox[k] : ox[k + 1];  // (left, right, y-, y+, z-, z+ as k_restrict_v)
+            o += O == 0 ? ox[k + 1] : ox[k + 2];
+            o += A[k];
+            o += B[k];
+            o += D[k];
+            o += F[k];
+            res[k] = R[k] - (L.diag0 * Cr[k] - o) * inv_h2;
         }
-        float o = O == 0 ? ox[k] : ox[k + 1];  // (left, right, y-, y+, z-, z+ as k_restrict_v)
-        o += O == 0 ? ox[k + 1] : ox[k + 2];
-        o += a[k];
-        o += b[k];
-        o += d[k];
-        o += f[k];
-        res[k] = r[k] - (L.diag0 * c[k] - o) * inv_h2;
-    }
-    part[threadIdx.y][threadIdx.x] = make_float4(res[0], res[1], res[2], res[3]);
-    __syncthreads();
-    if (threadIdx.y != 0 || !lane_on) return;
-    // per fine row k_restrict_v adds (even child + odd child), one of them
-    // the black child (0): the red residual plus 0, i.e. the red residual
-    float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const int dk = z & 1, par = (z >> 1) & 1;
+        part[par][row][2 * dk + dj][threadIdx.x] = make_float4(res[0], res[1], res[2], res[3]);
+        if (dk == 1) {
+            // (both warps of every row reach this together: whole planes, same bounds)
+            __syncthreads();
+            if (dj == 0 && lane_on) {
+                // per fine row k_restrict_v adds (even child + odd child), one
+                // of them the black child (0): the red residual plus 0
+                float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const float4 p = part[q][threadIdx.x];
-        sum[0] += p.x;
-        sum[1] += p.y;
-        sum[2] += p.z;
-        sum[3] += p.w;
-    }
-    const int C = X0 + cnx * (cy + cny * cz);
-    const uchar4 cs = *reinterpret_cast<const uchar4*>(cst + C);
-    const uint8_t ck[4] = {cs.x, cs.y, cs.z, cs.w};
-    float v[4];
+                for (int q = 0; q < 4; q++) {
+                    const float4 p = part[par][row][q][threadIdx.x];
+                    sum[0] += p.x;
+                    sum[1] += p.y;
+                    sum[2] += p.z;
+                    sum[3] += p.w;
+                }
+                const int cz = z >> 1;
+                const int C = X0 + cnx * (cy + cny * cz);
+                const uchar4 cs = *reinterpret_cast<const uchar4*>(cst + C);
+                const uint8_t ck[4] = {cs.x, cs.y, cs.z, cs.w};
+                float v[4];
 #pragma unroll
-    for (int k = 0; k < 4; k++) v[k] = ((ck[k] & ST_KIND) == ST_UNKNOWN) ? sum[k] / 8.0f : 0.0f;
-    store_coarse4(crhs, C, (X0 + cy + cz) & 1, chalf, v);
+                for (int k = 0; k < 4; k++) v[k] = ((ck[k] & ST_KIND) == ST_UNKNOWN) ? sum[k] / 8.0f : 0.0f;
+                store_coarse4(crhs, C, (X0 + cy + cz) & 1, chalf, v);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            D[k] = X[k];
+            X[k] = F[k];
+            F[k] = nF[k];
+            A[k] = nA[k];
+            B[k] = nB[k];
+            Cr[k] = nC[k];
+            R[k] = nR[k];
+        }
+        h = nh;
+        sw = nsw;
+    }
 }
 
 // Coarsest level: one thread block holds the level in shared memory and
@@ -2903,10 +2993,14 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                     // (red near cells only: the first kNearSegs segments)
                     k_near_residual<T, E, RbMap><<<dim3(ngrd.x, kNearSegs), 256, 0, c->stream>>>(
                         L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
-                    const dim3 qgrd((m[0] / 4 + 31) / 32, m[1], m[2]);
-                    k_restrict_red_rb<<<qgrd, dim3(32, 4), 0, c->stream>>>(L, (T)1 / L.h2, st, rhs, e, scratch,
-                                                                           m[0], m[1], c->st[l + 1],
-                                                                           (T*)c->rhs[l + 1], rb.half, chalf);
+                    // coarse planes per block: up to 8, about 16 blocks per SM in all
+                    const int qx = (m[0] / 4 + 31) / 32, qy = (m[1] + kRestrictRows - 1) / kRestrictRows;
+                    int czc = (int)((long long)qx * qy * m[2] / (16LL * c->n_sm));
+                    czc = czc < 1 ? 1 : (czc > 8 ? 8 : czc);
+                    const dim3 qgrd(qx, qy, (m[2] + czc - 1) / czc);
+                    k_restrict_red_rb<<<qgrd, dim3(32, 2 * kRestrictRows), 0, c->stream>>>(
+                        L, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1], m[2], c->st[l + 1], (T*)c->rhs[l + 1],
+                        rb.half, chalf, czc);
                     done = true;
                 } else if (split) {
                     k_near_residual<T, E, RbMap><<<ngrd, 256, 0, c->stream>>>(
@@ -2935,10 +3029,19 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
     cudaError_t err = vcycle_level<T>(c, l + 1, 0);
     if (err != cudaSuccess) return err;
     {
-        ProfScope ps(c, "prolong", l, nl * (2.0 * es + 1.0) + nc * (ts + 1.0));
+        // (the black cells only ahead of a Gauss-Seidel post-smoothing: e in
+        // and out for half the cells)
+        const bool black_only = split && c->P.omega == 1.0 && c->P.nu2 >= 1;
+        ProfScope ps(c, "prolong", l,
+                     nl * ((black_only ? 1.0 : 2.0) * es + 1.0) + nc * (ts + 1.0));
         bool done = false;
         if constexpr (kNative && std::is_same<T, float>::value) {
-            if (split) {
+            if (black_only) {
+                const dim3 bgrd((L.nx / 8 + 31) / 32, (L.ny + 7) / 8, L.nz);
+                k_prolong_black_rb<<<bgrd, vblk, 0, c->stream>>>(L, st, e, rb.half, m[0], m[1], c->st[l + 1],
+                                                                 (const T*)c->e[l + 1], chalf);
+                done = true;
+            } else if (split) {
                 k_prolong_v<T, E, true><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1],
                                                                       (const T*)c->e[l + 1], A, rb.half, chalf);
                 done = true;
@@ -2997,8 +3100,6 @@ void set_coarse_smem(const es_ctx* c) {
 
 }  // namespace
 
-// Algorithmic bytes per cell: psi (8: double, or float-float) and the state
-// byte in, r out (8 as double, 4 as the float right-hand side).
 // Grid of a marching residual pass over a level of nz planes with (gx, gy)
 // blocks per plane: zc planes per block, about eight blocks per SM in all
 // (up to 16 planes each), and no more blocks than partial-sum slots.
@@ -3012,6 +3113,8 @@ static void res_march_grid(const es_ctx* c, int gx, int gy, int nz, int& gz, int
     gz = (nz + zc - 1) / zc;
 }
 
+// Algorithmic bytes per cell: psi (8: double, or float-float) and the state
+// byte in, r out (8 as double, 4 as the float right-hand side).
 cudaError_t launch_outer_residual(es_ctx* c) {
     const double diag0 = 6.0 + c->S.kappa * c->S.kappa;
     ProfScope ps(c, "outer_residual", -1, (double)c->g.N * (mixed(c) ? 13.0 : 17.0));
