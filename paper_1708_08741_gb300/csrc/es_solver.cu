@@ -365,36 +365,38 @@ __global__ void __launch_bounds__(256, 2) k_outer_residual_ff(Grid g, ff diag0, 
         if (!wrap_axis(y + 1, ny, g.per[1], yp)) yp = y;
         if (!wrap_axis(xq - 1, nx, g.per[0], xl)) xl = xq;
         if (!wrap_axis(xq + W, nx, g.per[0], xr)) xr = xq;
-        auto zwrap = [&](int z) {
-            int w;
-            if (!wrap_axis(z, nz, g.per[2], w)) w = z < 0 ? 0 : nz - 1;  // (beyond a wall: any valid row)
-            return w;
-        };
-        auto rowof = [&](int yy, int z) { return nx * (yy + ny * z); };
+        // row offsets carried from plane to plane; z + 1 past the last
+        // plane is the first (periodic) or the row itself (a wall: any
+        // valid row)
+        const int plane = nx * ny, back = (nz - 1) * plane, zwall = g.per[2] ? 0 : 1;
+        int orow = nx * (y + ny * z0);  // row (y, z)
+        int oa = nx * (ym + ny * z0) + xq, ob = nx * (yp + ny * z0) + xq;
+        const int dl = xl - xq, dr = xr - xq;
         FFSpan<W> D, X, F, A, B;
         float hlh, hll, hrh, hrl;
         unsigned sv;
-        auto load = [&](int z, FFSpan<W>& f, FFSpan<W>& a, FFSpan<W>& b, float& lh, float& ll, float& rh, float& rl,
-                        unsigned& s) {
-            const int row = rowof(y, z);
-            s = load_states<W>(st0, row + xq);
-            load_ff<W>(f, psi_hi, psi_lo, rowof(y, zwrap(z + 1)) + xq);
-            load_ff<W>(a, psi_hi, psi_lo, rowof(ym, z) + xq);
-            load_ff<W>(b, psi_hi, psi_lo, rowof(yp, z) + xq);
-            lh = psi_hi[row + xl];
-            ll = psi_lo[row + xl];
-            rh = psi_hi[row + xr];
-            rl = psi_lo[row + xr];
+        auto load = [&](int z, int row, int a_off, int b_off, FFSpan<W>& f, FFSpan<W>& a, FFSpan<W>& b, float& lh,
+                        float& ll, float& rh, float& rl, unsigned& s) {
+            const int c0 = row + xq;
+            s = load_states<W>(st0, c0);
+            load_ff<W>(f, psi_hi, psi_lo, z + 1 < nz ? c0 + plane : (zwall ? c0 : c0 - back));
+            load_ff<W>(a, psi_hi, psi_lo, a_off);
+            load_ff<W>(b, psi_hi, psi_lo, b_off);
+            lh = psi_hi[c0 + dl];
+            ll = psi_lo[c0 + dl];
+            rh = psi_hi[c0 + dr];
+            rl = psi_lo[c0 + dr];
         };
-        load_ff<W>(D, psi_hi, psi_lo, rowof(y, zwrap(z0 - 1)) + xq);
-        load_ff<W>(X, psi_hi, psi_lo, rowof(y, z0) + xq);
-        load(z0, F, A, B, hlh, hll, hrh, hrl, sv);
+        load_ff<W>(D, psi_hi, psi_lo, z0 > 0 ? orow + xq - plane : (zwall ? orow + xq : orow + xq + back));
+        load_ff<W>(X, psi_hi, psi_lo, orow + xq);
+        load(z0, orow, oa, ob, F, A, B, hlh, hll, hrh, hrl, sv);
         for (int z = z0; z < z1; z++) {
             FFSpan<W> nF, nA, nB;
             float nlh = 0.0f, nll = 0.0f, nrh = 0.0f, nrl = 0.0f;
             unsigned nsv = 0;
-            if (z + 1 < z1) load(z + 1, nF, nA, nB, nlh, nll, nrh, nrl, nsv);
-            const int row = rowof(y, z);
+            if (z + 1 < z1)
+                load(z + 1, orow + plane, oa + plane, ob + plane, nF, nA, nB, nlh, nll, nrh, nrl, nsv);
+            const int row = orow;
             unsigned near_bits = 0;
             float out[W];
 #pragma unroll
@@ -460,6 +462,9 @@ __global__ void __launch_bounds__(256, 2) k_outer_residual_ff(Grid g, ff diag0, 
             hrh = nrh;
             hrl = nrl;
             sv = nsv;
+            orow += plane;
+            oa += plane;
+            ob += plane;
         }
     }
     // per-block partial: float within the block (a few thousand terms), one
@@ -884,8 +889,8 @@ __device__ __forceinline__ void smooth_v_span(const Level<T>& L, T inv_diag0, co
     }
 }
 
-// The interior unknown cells of one colour of the colour-split finest
-// level, for a 4-cell span of compact places iq .. iq+3 in row y and the
+// The interior unknown cells of one colour of a colour-split level, for a
+// 4-cell span of compact places iq .. iq+3 in row y and the
 // planes z0 .. z1-1 (see k_smooth_rb).  The other colour's rows of the
 // planes z-1, z and z+1 at row y roll through registers (the row z+1 of one
 // plane is the row z of the next and the row z-1 of the one after), so a
@@ -896,6 +901,9 @@ __device__ __forceinline__ void smooth_v_span(const Level<T>& L, T inv_diag0, co
 // is not needed).  A cell's update sums its neighbours in the order of
 // k_smooth_v's span_update (x left, x right, y-1, y+1, z-1, z+1), so both
 // finest-level layouts give the same bits.
+// The row offsets are carried from plane to plane (one add a row a plane),
+// the wrap of z + 1 is a select, and the four cells are formed without
+// branches (the mask picks the stores only): fewer issued instructions.
 template <class T, int FIRST, bool GS>
 __device__ __forceinline__ void rb_march(const Level<T>& L, T inv_diag0, const uint32_t* __restrict__ mcol, int wpr,
                                          const T* __restrict__ rcol, const T* __restrict__ eo, T* __restrict__ es,
@@ -906,28 +914,31 @@ __device__ __forceinline__ void rb_march(const Level<T>& L, T inv_diag0, const u
     if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
     if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
     if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
-    const int msh = iq & 31, mw = iq >> 5;
-    auto zwrap = [&](int z) {
-        int w;
-        if (!wrap_axis(z, nz, L.per[2], w)) w = z < 0 ? 0 : nz - 1;  // (beyond a wall: any valid row)
-        return w;
-    };
-    // plane z's loads: rows (y, z+1), (y-1, z), (y+1, z), the halo of row
-    // (y, z), rhs and the mask word
+    const int msh = iq & 31;
+    const int plane = nxh * ny, mplane = wpr * ny;
+    int oe = nxh * (y + ny * z0) + iq;        // row (y, z): rhs, the other colour, the colour
+    int oa = nxh * (ym + ny * z0) + iq;       // row (y-1, z)
+    int ob = nxh * (yp + ny * z0) + iq;       // row (y+1, z)
+    int om = wpr * (y + ny * z0) + (iq >> 5);  // mask word
+    const int hl = il - iq, hr = ir - iq;     // halo offsets in the row
+    const int back = (nz - 1) * plane;        // from the last plane to the first
+    const int zwall = L.per[2] ? 0 : 1;
     T F[4], A[4], B[4], R[4], h = (T)0;
     unsigned m = 0;
-    auto load = [&](int z, T (&f)[4], T (&a)[4], T (&b)[4], T (&r)[4], T& hv, unsigned& mv) {
-        const int rz = nxh * (y + ny * z);
-        mv = (mcol[(size_t)wpr * (y + ny * z) + mw] >> msh) & 0xFu;
-        ES_VLD(r, 0, rcol + rz + iq);
+    int O = (colour + y + z0) & 1;
+    // plane z's loads; row (y, z+1) is the next plane, or past the last one
+    // the first (periodic) or the row itself (a wall)
+    auto load = [&](int z, int o, int e_off, int a_off, int b_off, int m_off, T (&f)[4], T (&a)[4], T (&b)[4],
+                    T (&r)[4], T& hv, unsigned& mv) {
+        mv = (mcol[m_off] >> msh) & 0xFu;
+        ES_VLD(r, 0, rcol + e_off);
         if constexpr (FIRST != 1) {
-            const int zp = zwrap(z + 1);
-            ES_VLD(f, 0, eo + nxh * (y + ny * zp) + iq);
-            ES_VLD(a, 0, eo + nxh * (ym + ny * z) + iq);
-            ES_VLD(b, 0, eo + nxh * (yp + ny * z) + iq);
-            hv = ((colour + y + z) & 1) == 0 ? eo[rz + il] : eo[rz + ir];
+            const int f_off = z + 1 < nz ? e_off + plane : (zwall ? e_off : e_off - back);
+            ES_VLD(f, 0, eo + f_off);
+            ES_VLD(a, 0, eo + a_off);
+            ES_VLD(b, 0, eo + b_off);
+            hv = eo[e_off + (o == 0 ? hl : hr)];
         } else {
-            // (the iterate starts at zero: every neighbour is zero)
 #pragma unroll
             for (int k = 0; k < 4; k++) f[k] = a[k] = b[k] = (T)0;
             hv = (T)0;
@@ -935,30 +946,22 @@ __device__ __forceinline__ void rb_march(const Level<T>& L, T inv_diag0, const u
     };
     T D[4] = {(T)0, (T)0, (T)0, (T)0}, X[4] = {(T)0, (T)0, (T)0, (T)0};
     if constexpr (FIRST != 1) {
-        ES_VLD(D, 0, eo + nxh * (y + ny * zwrap(z0 - 1)) + iq);
-        ES_VLD(X, 0, eo + nxh * (y + ny * z0) + iq);
+        const int d_off = z0 > 0 ? oe - plane : (zwall ? oe : oe + back);
+        ES_VLD(D, 0, eo + d_off);
+        ES_VLD(X, 0, eo + oe);
     }
-    load(z0, F, A, B, R, h, m);
+    load(z0, O, oe, oa, ob, om, F, A, B, R, h, m);
     for (int z = z0; z < z1; z++) {
         T nF[4], nA[4], nB[4], nR[4], nh = (T)0;
         unsigned nm = 0;
-        if (z + 1 < z1) load(z + 1, nF, nA, nB, nR, nh, nm);
+        if (z + 1 < z1) load(z + 1, O ^ 1, oe + plane, oa + plane, ob + plane, om + mplane, nF, nA, nB, nR, nh, nm);
         if (m) {
-            const int rz = nxh * (y + ny * z) + iq;
             T C[4] = {(T)0, (T)0, (T)0, (T)0};
-            if constexpr (FIRST == 0 && !GS) ES_VLD(C, 0, es + rz);
-            const int O = (colour + y + z) & 1;
+            if constexpr (FIRST == 0 && !GS) ES_VLD(C, 0, es + oe);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                if (!((m >> k) & 1u)) continue;
-                T left, right;
-                if (O == 0) {
-                    left = k == 0 ? h : X[k - 1];
-                    right = X[k];
-                } else {
-                    left = X[k];
-                    right = k == 3 ? h : X[k + 1];
-                }
+                const T left = O == 0 ? (k == 0 ? h : X[k - 1]) : X[k];
+                const T right = O == 0 ? X[k] : (k == 3 ? h : X[k + 1]);
                 T o = left;
                 o += right;
                 o += A[k];
@@ -974,12 +977,12 @@ __device__ __forceinline__ void rb_march(const Level<T>& L, T inv_diag0, const u
                     C[k] = ((T)1 - omega) * C[k] + omega * gs;
             }
             if (m == 0xFu) {
-                vst(es + rz, C[0], C[1], C[2], C[3]);
+                vst(es + oe, C[0], C[1], C[2], C[3]);
             } else {
                 // (the colour's near-boundary cells belong to the near blocks)
 #pragma unroll
                 for (int k = 0; k < 4; k++)
-                    if ((m >> k) & 1u) es[rz + k] = C[k];
+                    if ((m >> k) & 1u) es[oe + k] = C[k];
             }
         }
 #pragma unroll
@@ -993,6 +996,11 @@ __device__ __forceinline__ void rb_march(const Level<T>& L, T inv_diag0, const u
         }
         h = nh;
         m = nm;
+        O ^= 1;
+        oe += plane;
+        oa += plane;
+        ob += plane;
+        om += mplane;
     }
 }
 
@@ -2012,57 +2020,58 @@ __global__ void __launch_bounds__(256, 2) k_residual_update_rb(Level<float> L, f
         if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
         if (!wrap_axis(Xq - 1, nxh, L.per[0], il)) il = Xq;
         if (!wrap_axis(Xq + 4, nxh, L.per[0], ir)) ir = Xq;
-        // (beyond a wall any valid row: only near-boundary cells would read it)
-        auto zwrap = [&](int z) {
-            int w;
-            if (!wrap_axis(z, nz, L.per[2], w)) w = z < 0 ? 0 : nz - 1;
-            return w;
-        };
-        // compact row of (yy, z), and its colour arrays: E0 holds the cells
-        // of colour (y + z) & 1 of row (y, z), the even-x ones
-        auto E0of = [&](int z) { return e + ((y + z) & 1) * half; };
+        // row offsets carried from plane to plane (compact rows: rowh, y -+ 1;
+        // natural: the state bytes); z + 1 past the last plane is the first
+        // (periodic) or the row itself (a wall: any valid row, only
+        // near-boundary cells would read it)
+        const int plane = nxh * ny, back = (nz - 1) * plane, zwall = L.per[2] ? 0 : 1;
+        int orh = nxh * (y + ny * z0) + Xq, oym = nxh * (ym + ny * z0) + Xq, oyp = nxh * (yp + ny * z0) + Xq;
+        int ost = nx * (y + ny * z0) + 2 * Xq;
+        const int dl = il - Xq, dr = ir - Xq;
         // plane z's loads: the even- and odd-x cells of row (y, z+1), the
         // rows (y -+ 1, z) of both arrays, r of both colours, the halos
-        // and the state bytes
+        // and the state bytes.  E0 holds the cells of colour (y + z) & 1 of
+        // row (y, z), the even-x ones.
         float Fe[4], Fo[4], a1[4], b1[4], a0[4], b0[4], rE[4], rO[4], hl, hr;
         uint2 sw;
-        auto load = [&](int z, float (&fe)[4], float (&fo)[4], float (&pa1)[4], float (&pb1)[4], float (&pa0)[4],
-                        float (&pb0)[4], float (&re)[4], float (&ro)[4], float& l, float& r, uint2& s) {
+        auto load = [&](int z, int rh, int hm, int hp, int so, float (&fe)[4], float (&fo)[4], float (&pa1)[4],
+                        float (&pb1)[4], float (&pa0)[4], float (&pb0)[4], float (&re)[4], float (&ro)[4], float& l,
+                        float& r, uint2& s) {
             const int pe = (y + z) & 1;
             const float* E0 = e + pe * half;
             const float* E1 = e + (pe ^ 1) * half;
-            const int rowh = nxh * (y + ny * z);
-            const int hzp = nxh * (y + ny * zwrap(z + 1));
-            const int hym = nxh * (ym + ny * z), hyp = nxh * (yp + ny * z);
-            s = *reinterpret_cast<const uint2*>(st + nx * (y + ny * z) + 2 * Xq);
-            ES_VLD(fe, 0, E1 + hzp + Xq);
-            ES_VLD(fo, 0, E0 + hzp + Xq);
-            ES_VLD(pa1, 0, E1 + hym + Xq);
-            ES_VLD(pb1, 0, E1 + hyp + Xq);
-            ES_VLD(pa0, 0, E0 + hym + Xq);
-            ES_VLD(pb0, 0, E0 + hyp + Xq);
-            ES_VLD(re, 0, rhs + pe * half + rowh + Xq);
-            ES_VLD(ro, 0, rhs + (pe ^ 1) * half + rowh + Xq);
-            l = E1[rowh + il];
-            r = E0[rowh + ir];
+            const int hzp = z + 1 < nz ? rh + plane : (zwall ? rh : rh - back);
+            s = *reinterpret_cast<const uint2*>(st + so);
+            ES_VLD(fe, 0, E1 + hzp);
+            ES_VLD(fo, 0, E0 + hzp);
+            ES_VLD(pa1, 0, E1 + hm);
+            ES_VLD(pb1, 0, E1 + hp);
+            ES_VLD(pa0, 0, E0 + hm);
+            ES_VLD(pb0, 0, E0 + hp);
+            ES_VLD(re, 0, rhs + pe * half + rh);
+            ES_VLD(ro, 0, rhs + (pe ^ 1) * half + rh);
+            l = E1[rh + dl];
+            r = E0[rh + dr];
         };
         // the even (De, Ae) and odd (Do, Ao) cells of rows (y, z0-1), (y, z0)
         float De[4], Do[4], Ae[4], Ao[4];
         {
-            const int zm = zwrap(z0 - 1), pe = (y + z0) & 1;
-            const int hzm = nxh * (y + ny * zm), rowh = nxh * (y + ny * z0);
-            ES_VLD(De, 0, e + (pe ^ 1) * half + hzm + Xq);
-            ES_VLD(Do, 0, E0of(z0) + hzm + Xq);
-            ES_VLD(Ae, 0, E0of(z0) + rowh + Xq);
-            ES_VLD(Ao, 0, e + (pe ^ 1) * half + rowh + Xq);
+            const int pe = (y + z0) & 1;
+            const int hzm = z0 > 0 ? orh - plane : (zwall ? orh : orh + back);
+            ES_VLD(De, 0, e + (pe ^ 1) * half + hzm);
+            ES_VLD(Do, 0, e + pe * half + hzm);
+            ES_VLD(Ae, 0, e + pe * half + orh);
+            ES_VLD(Ao, 0, e + (pe ^ 1) * half + orh);
         }
-        load(z0, Fe, Fo, a1, b1, a0, b0, rE, rO, hl, hr, sw);
+        load(z0, orh, oym, oyp, ost, Fe, Fo, a1, b1, a0, b0, rE, rO, hl, hr, sw);
         for (int z = z0; z < z1; z++) {
             float nFe[4], nFo[4], na1[4], nb1[4], na0[4], nb0[4], nrE[4], nrO[4], nhl = 0.0f, nhr = 0.0f;
             uint2 nsw = make_uint2(0u, 0u);
-            if (z + 1 < z1) load(z + 1, nFe, nFo, na1, nb1, na0, nb0, nrE, nrO, nhl, nhr, nsw);
+            if (z + 1 < z1)
+                load(z + 1, orh + plane, oym + plane, oyp + plane, ost + nx * ny, nFe, nFo, na1, nb1, na0, nb0, nrE,
+                     nrO, nhl, nhr, nsw);
             const int pe = (y + z) & 1;
-            const int rowh = nxh * (y + ny * z), rown = nx * (y + ny * z) + 2 * Xq;
+            const int rowh = orh - Xq, rown = ost;
             float out[8];
             unsigned near = 0;
 #pragma unroll
@@ -2135,6 +2144,10 @@ __global__ void __launch_bounds__(256, 2) k_residual_update_rb(Level<float> L, f
             hl = nhl;
             hr = nhr;
             sw = nsw;
+            orh += plane;
+            oym += plane;
+            oyp += plane;
+            ost += nx * ny;
         }
     }
     float v = acc;
@@ -2188,38 +2201,39 @@ __global__ void __launch_bounds__(32 * 2 * kRestrictRows)
     if (!wrap_axis(y + 1, ny, L.per[1], yp)) yp = y;
     if (!wrap_axis(iq - 1, nxh, L.per[0], il)) il = iq;
     if (!wrap_axis(iq + 4, nxh, L.per[0], ir)) ir = iq;
-    auto zwrap = [&](int z) {
-        int w;
-        if (!wrap_axis(z, nz, L.per[2], w)) w = z < 0 ? 0 : nz - 1;  // (the row itself beyond a wall)
-        return w;
-    };
-    auto hrow = [&](int yy, int z) { return nxh * (yy + ny * z); };
+    // row offsets carried from plane to plane (compact rows; natural: the
+    // state bytes); z + 1 past the last plane is the first (periodic) or the
+    // row itself (a wall)
+    const int z0 = 2 * cz0, z1 = 2 * cz1;
+    const int plane = nxh * ny, back = (nz - 1) * plane, zwall = L.per[2] ? 0 : 1;
+    int orh = nxh * (y + ny * z0) + iq, oym = nxh * (ym + ny * z0) + iq, oyp = nxh * (yp + ny * z0) + iq;
+    int ost = L.nx * (y + ny * z0) + 2 * iq;
+    const int dl = il - iq, dr = ir - iq;
     // plane z's loads: the black rows (y, z+1), (y-1, z), (y+1, z), the halo
     // of (y, z), the red e and rhs of (y, z), the state bytes
     float F[4], A[4], B[4], Cr[4], R[4], h;
     uint2 sw;
-    auto load = [&](int z, float (&f)[4], float (&a)[4], float (&b)[4], float (&c)[4], float (&r)[4], float& hv,
-                    uint2& s) {
-        const int rz = hrow(y, z);
-        ES_VLD(f, 0, eo + hrow(y, zwrap(z + 1)) + iq);
-        ES_VLD(a, 0, eo + hrow(ym, z) + iq);
-        ES_VLD(b, 0, eo + hrow(yp, z) + iq);
-        ES_VLD(c, 0, e + rz + iq);
-        ES_VLD(r, 0, rhs + rz + iq);
-        hv = ((y + z) & 1) == 0 ? eo[rz + il] : eo[rz + ir];
-        s = *reinterpret_cast<const uint2*>(st + L.nx * (y + ny * z) + 2 * iq);
+    auto load = [&](int z, int rh, int hm, int hp, int so, float (&f)[4], float (&a)[4], float (&b)[4],
+                    float (&c)[4], float (&r)[4], float& hv, uint2& s) {
+        ES_VLD(f, 0, eo + (z + 1 < nz ? rh + plane : (zwall ? rh : rh - back)));
+        ES_VLD(a, 0, eo + hm);
+        ES_VLD(b, 0, eo + hp);
+        ES_VLD(c, 0, e + rh);
+        ES_VLD(r, 0, rhs + rh);
+        hv = eo[rh + (((y + z) & 1) == 0 ? dl : dr)];
+        s = *reinterpret_cast<const uint2*>(st + so);
     };
-    const int z0 = 2 * cz0, z1 = 2 * cz1;
     float D[4], X[4];
-    ES_VLD(D, 0, eo + hrow(y, zwrap(z0 - 1)) + iq);
-    ES_VLD(X, 0, eo + hrow(y, z0) + iq);
-    if (z0 < z1) load(z0, F, A, B, Cr, R, h, sw);
+    ES_VLD(D, 0, eo + (z0 > 0 ? orh - plane : (zwall ? orh : orh + back)));
+    ES_VLD(X, 0, eo + orh);
+    if (z0 < z1) load(z0, orh, oym, oyp, ost, F, A, B, Cr, R, h, sw);
     for (int z = z0; z < z1; z++) {
         float nF[4], nA[4], nB[4], nC[4], nR[4], nh = 0.0f;
         uint2 nsw = make_uint2(0u, 0u);
-        if (z + 1 < z1) load(z + 1, nF, nA, nB, nC, nR, nh, nsw);
+        if (z + 1 < z1)
+            load(z + 1, orh + plane, oym + plane, oyp + plane, ost + L.nx * ny, nF, nA, nB, nC, nR, nh, nsw);
         const int O = (y + z) & 1;  // red cells of this row: x = 2 i + O
-        const int rown = L.nx * (y + ny * z) + 2 * iq;
+        const int rown = ost;
         // the black row with its halo: ox[0] left of X0 (O = 0), ox[5] right of X0+3 (O = 1)
         const float ox[6] = {O == 0 ? h : 0.0f, X[0], X[1], X[2], X[3], O == 1 ? h : 0.0f};
         float res[4];
@@ -2280,6 +2294,10 @@ __global__ void __launch_bounds__(32 * 2 * kRestrictRows)
         }
         h = nh;
         sw = nsw;
+        orh += plane;
+        oym += plane;
+        oyp += plane;
+        ost += L.nx * ny;
     }
 }
 
