@@ -28,6 +28,28 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
+// Programmatic dependent launch for the V-cycle's chain of kernels: a
+// kernel launched by launch_pdl may be scheduled while the one before it
+// on the stream drains, and waits here (before touching memory) until that
+// one has completed and its writes are visible; launched plainly, the wait
+// returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(const es_ctx* c, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // (errors: cudaGetLastError)
+}
+
 __device__ __forceinline__ bool wrap_axis(int v, int n, int per, int& out) {
     if (v < 0 || v >= n) {
         if (!per) return false;
@@ -641,6 +663,7 @@ template <class T>
 __global__ void __launch_bounds__(128) k_smooth(Level<T> L, const uint8_t* __restrict__ st,
                                                 const T* __restrict__ rhs, T* __restrict__ e, int colour,
                                                 int first, T omega, const T* __restrict__ dk = nullptr) {
+    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (2 * t >= L.nx) return;
@@ -762,6 +785,7 @@ template <class T, int W, bool INLINE_NEAR, class E = T>
 __global__ void __launch_bounds__(256) k_smooth_v(Level<T> L, T inv_diag0, const uint8_t* __restrict__ st,
                                                   const T* __restrict__ rhs, E* __restrict__ e, int colour,
                                                   int first, T omega, EAcc<T, E> A, NearWork nw) {
+    pdl_wait();
     const int xs = W * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
     if (y < L.ny) smooth_v_span<T, W, INLINE_NEAR, E>(L, inv_diag0, st, rhs, e, colour, first, omega, A, xs, y, z);
@@ -1034,6 +1058,7 @@ __global__ void __launch_bounds__(256, 4) k_smooth_rb(Level<T> L, T inv_diag0, c
                                                       int wpr, const T* __restrict__ rhs, T* __restrict__ e,
                                                       int colour, int first, T omega, int half, NearWork nw,
                                                       int zc) {
+    pdl_wait();
     const int i0 = 4 * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y;
     if (y < L.ny && i0 < (L.nx >> 1)) {
@@ -1300,6 +1325,7 @@ __global__ void __launch_bounds__(256) k_smooth_rb_bulk(Level<T> L, T inv_diag0,
                                                         int wpr, const T* __restrict__ rhs, T* __restrict__ e,
                                                         int colour, int first, T omega, int half, NearWork nw,
                                                         BulkShape B, int* status) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char bsm[];
     __shared__ __align__(8) uint64_t bars[kBulkSlots];
     T* slots = (T*)bsm;
@@ -1389,6 +1415,7 @@ __global__ void __launch_bounds__(32 * (kRbRows + 1), sizeof(T) == 4 ? 2 : 1) k_
                                                                   const T* __restrict__ rhs,
                                                                   const T* __restrict__ ein, T* __restrict__ eout,
                                                                   int first, T omega, int zc) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char rb2_smem[];
     __shared__ T sbuf[kRbRows][32 * 4];
     constexpr int SE = kRbRows * kRbSpans * 4;  // elements of one plane slot
@@ -1593,6 +1620,7 @@ __global__ void __launch_bounds__(128) k_residual_restrict(Level<T> L, const uin
                                                            const T* __restrict__ rhs, const T* __restrict__ e,
                                                            int cnx, int cny, const uint8_t* __restrict__ cst,
                                                            T* __restrict__ crhs) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i >= cnx) return;
@@ -1622,6 +1650,7 @@ template <class T>
 __global__ void __launch_bounds__(128) k_prolong(Level<T> L, const uint8_t* __restrict__ st, T* __restrict__ e,
                                                  int cnx, int cny, const uint8_t* __restrict__ cst,
                                                  const T* __restrict__ ce) {
+    pdl_wait();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= L.nx) return;
@@ -1640,6 +1669,7 @@ __global__ void __launch_bounds__(256) k_prolong_v(Level<T> L, const uint8_t* __
                                                    int cnx, int cny, const uint8_t* __restrict__ cst,
                                                    const T* __restrict__ ce, EAcc<T, E> A, int half = 0,
                                                    int chalf = 0) {
+    pdl_wait();
     const int xs = 4 * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
     if (xs >= L.nx || y >= L.ny) return;
@@ -1700,6 +1730,7 @@ __global__ void __launch_bounds__(256) k_prolong_black_rb(Level<float> L, const 
                                                           float* __restrict__ e, int half, int cnx, int cny,
                                                           const uint8_t* __restrict__ cst,
                                                           const float* __restrict__ ce, int chalf) {
+    pdl_wait();
     const int nxh = L.nx >> 1;
     const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
     const int y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
@@ -1757,6 +1788,7 @@ __global__ void __launch_bounds__(256) k_near_residual(Level<T> L, const uint8_t
                                                        const int* __restrict__ list, const int* __restrict__ count,
                                                        int cap, T inv_h2, T* __restrict__ out, EAcc<T, E> A,
                                                        M m = M{}) {
+    pdl_wait();
     // blockIdx.y: list segment
     const int n = count[blockIdx.y];
     const int* seg = list + (size_t)blockIdx.y * cap;
@@ -1774,6 +1806,7 @@ __global__ void __launch_bounds__(256) k_restrict_v(Level<T> L, T inv_diag0, T i
                                                     const T* __restrict__ near_res, int cnx,
                                                     int cny, const uint8_t* __restrict__ cst, T* __restrict__ crhs,
                                                     EAcc<T, E> A, int half = 0, int red_only = 0) {
+    pdl_wait();
     const int cx_warp = 2 * (blockIdx.x * 32);
     const int cxs = cx_warp + 2 * threadIdx.x;
     const int cy = blockIdx.y * 8 + threadIdx.y, cz = blockIdx.z;
@@ -1889,6 +1922,7 @@ __global__ void __launch_bounds__(256) k_restrict_rb(Level<float> L, float inv_h
                                                      const float* __restrict__ near_res, int cnx, int cny,
                                                      const uint8_t* __restrict__ cst, float* __restrict__ crhs,
                                                      int half, int chalf) {
+    pdl_wait();
     __shared__ float4 part[8][32];
     const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
     const int crow = threadIdx.y >> 2, sub = threadIdx.y & 3;
@@ -2184,6 +2218,7 @@ __global__ void __launch_bounds__(32 * 2 * kRestrictRows)
     k_restrict_red_rb(Level<float> L, float inv_h2, const uint8_t* __restrict__ st, const float* __restrict__ rhs,
                       const float* __restrict__ e, const float* __restrict__ near_res, int cnx, int cny, int cnz,
                       const uint8_t* __restrict__ cst, float* __restrict__ crhs, int half, int chalf, int czc) {
+    pdl_wait();
     __shared__ float4 part[2][kRestrictRows][4][32];  // (coarse-plane parity, coarse row, 2 dk + dj, lane)
     const int nxh = L.nx >> 1, ny = L.ny, nz = L.nz;
     const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
@@ -2306,6 +2341,7 @@ __global__ void __launch_bounds__(32 * 2 * kRestrictRows)
 template <class T>
 __global__ void __launch_bounds__(1024) k_coarse_solve(Level<T> L, const uint8_t* st, const T* rhs, T* e,
                                                        int sweeps, T omega) {
+    pdl_wait();
     extern __shared__ unsigned char smem[];
     const int n = L.nx * L.ny * L.nz;
     T* se = (T*)smem;
@@ -2350,6 +2386,7 @@ template <class T>
 __global__ void __launch_bounds__(1024) k_coarse_lists(Level<T> L, const uint8_t* __restrict__ st,
                                                        const T* __restrict__ rhs, T* __restrict__ e, int sweeps,
                                                        T omega) {
+    pdl_wait();
     extern __shared__ unsigned char smem[];
     __shared__ T inv_tab[13];  // 1 / (diag0 + k), k = -6 .. 6
     __shared__ int cnt[2];
@@ -2424,6 +2461,7 @@ __global__ void __launch_bounds__(1024) k_coarse_lists(Level<T> L, const uint8_t
 
 template <class T>
 __global__ void k_zero(T* p, int n) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = (T)0;
 }
@@ -2841,8 +2879,8 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             if (use_rb) {
                 ProfScope ps(c, "smooth_fused", l, nl * ((first ? 2.0 : 3.0) * ts + 1.0));
                 T* eo = (T*)c->e2[l];
-                k_smooth_rb2<T><<<rb_grid, dim3(32, kRbRows + 1), RB2<T>::smem, c->stream>>>(
-                    L, inv_diag0, st, rhs, e, eo, first, omega, rb_zc);
+                launch_pdl(c, k_smooth_rb2<T>, rb_grid, dim3(32, kRbRows + 1), RB2<T>::smem, L, inv_diag0, st, rhs, e,
+                           eo, first, omega, rb_zc);
                 c->e2[l] = c->e[l];
                 c->e[l] = eo;
                 e = eo;
@@ -2903,12 +2941,11 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
                     ProfScope ps(c, "smooth_half", l,
                                  !first ? b_rb_half : (col == 0 ? b_rb_first : b_rb_half - nl * own));
                     if (bulk)
-                        k_smooth_rb_bulk<T><<<bgrd, 256, bsm, c->stream>>>(L, inv_diag0, rbmask, rb_wpr, rhs, e,
-                                                                           col, fs, omega, rb.half, nw, bs,
-                                                                           c->d_status);
+                        launch_pdl(c, k_smooth_rb_bulk<T>, bgrd, 256, bsm, L, inv_diag0, rbmask, rb_wpr, rhs, e, col,
+                                   fs, omega, rb.half, nw, bs, c->d_status);
                     else
-                        k_smooth_rb<T><<<sgrd, vblk, 0, c->stream>>>(L, inv_diag0, rbmask, rb_wpr, rhs, e, col,
-                                                                     fs, omega, rb.half, nw, zc);
+                        launch_pdl(c, k_smooth_rb<T>, sgrd, vblk, 0, L, inv_diag0, rbmask, rb_wpr, rhs, e, col, fs,
+                                   omega, rb.half, nw, zc);
                 }
                 count(c, 2);
                 return;
@@ -2919,12 +2956,11 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             if (Nl <= inline_near_cells(c)) {
                 {
                     ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
-                    k_smooth_v<T, W, true, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first,
-                                                                             omega, A, nwl);
+                    launch_pdl(c, k_smooth_v<T, W, true, E>, vgrd, vblk, 0, L, inv_diag0, st, rhs, e, 0, first, omega,
+                               A, nwl);
                 }
                 ProfScope ps(c, "smooth_half", l, b_half);
-                k_smooth_v<T, W, true, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega, A,
-                                                                         nwl);
+                launch_pdl(c, k_smooth_v<T, W, true, E>, vgrd, vblk, 0, L, inv_diag0, st, rhs, e, 1, 0, omega, A, nwl);
                 count(c, 2);
                 return;
             }
@@ -2933,22 +2969,21 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             // loads are not counted)
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
-                k_smooth_v<T, W, false, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 0, first,
-                                                                          omega, A, nwl);
+                launch_pdl(c, k_smooth_v<T, W, false, E>, vgrd, vblk, 0, L, inv_diag0, st, rhs, e, 0, first, omega, A,
+                           nwl);
             }
             ProfScope ps(c, "smooth_half", l, b_half);
-            k_smooth_v<T, W, false, E><<<vgrd, vblk, 0, c->stream>>>(L, inv_diag0, st, rhs, e, 1, 0, omega, A,
-                                                                      nwl);
+            launch_pdl(c, k_smooth_v<T, W, false, E>, vgrd, vblk, 0, L, inv_diag0, st, rhs, e, 1, 0, omega, A, nwl);
             count(c, 2);
             return;
         }
         if constexpr (kNative) {
             {
                 ProfScope ps(c, "smooth_half", l, first ? b_first : b_half);
-                k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, first, omega);
+                launch_pdl(c, k_smooth<T>, half, blk, 0, L, st, rhs, e, 0, first, omega, (const T*)nullptr);
             }
             ProfScope ps(c, "smooth_half", l, b_half);
-            k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega);
+            launch_pdl(c, k_smooth<T>, half, blk, 0, L, st, rhs, e, 1, 0, omega, (const T*)nullptr);
             count(c, 2);
         }
     };
@@ -2959,10 +2994,10 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             for (int s = 0; s < c->P.coarse_sweeps; s++) {
                 {
                     ProfScope ps(c, "smooth_half", l, nl * (2.0 * ts + 1.0));
-                    k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 0, s == 0, omega, (const T*)c->dk);
+                    launch_pdl(c, k_smooth<T>, half, blk, 0, L, st, rhs, e, 0, s == 0, omega, (const T*)c->dk);
                 }
                 ProfScope ps(c, "smooth_half", l, nl * (2.0 * ts + 1.0));
-                k_smooth<T><<<half, blk, 0, c->stream>>>(L, st, rhs, e, 1, 0, omega, (const T*)c->dk);
+                launch_pdl(c, k_smooth<T>, half, blk, 0, L, st, rhs, e, 1, 0, omega, (const T*)c->dk);
                 count(c, 2);
             }
             if (c->P.coarse_sweeps == 0) {
@@ -2976,13 +3011,13 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             if (sm <= 200 * 1024) {
                 ProfScope ps(c, "coarse_solve", l, nl * (2.0 * ts + 1.0));
                 if (coarse_by_lists(c, sizeof(T)))
-                    k_coarse_lists<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
+                    launch_pdl(c, k_coarse_lists<T>, 1, 1024, sm, L, st, rhs, e, c->P.coarse_sweeps, omega);
                 else
-                    k_coarse_solve<T><<<1, 1024, sm, c->stream>>>(L, st, rhs, e, c->P.coarse_sweeps, omega);
+                    launch_pdl(c, k_coarse_solve<T>, 1, 1024, sm, L, st, rhs, e, c->P.coarse_sweeps, omega);
                 count(c);
             } else {
                 if (c->P.coarse_sweeps == 0) {
-                    k_zero<T><<<(Nl + 255) / 256, 256, 0, c->stream>>>(e, Nl);
+                    launch_pdl(c, k_zero<T>, (Nl + 255) / 256, 256, 0, e, Nl);
                     count(c);
                 }
                 for (int s = 0; s < c->P.coarse_sweeps; s++) sweep(s == 0);
@@ -3009,38 +3044,36 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
             if constexpr (kNative && std::is_same<T, float>::value) {
                 if (split && red_only) {
                     // (red near cells only: the first kNearSegs segments)
-                    k_near_residual<T, E, RbMap><<<dim3(ngrd.x, kNearSegs), 256, 0, c->stream>>>(
-                        L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
+                    launch_pdl(c, k_near_residual<T, E, RbMap>, dim3(ngrd.x, kNearSegs), 256, 0, L, st, rhs, e,
+                               c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
                     // coarse planes per block: up to 8, about 16 blocks per SM in all
                     const int qx = (m[0] / 4 + 31) / 32, qy = (m[1] + kRestrictRows - 1) / kRestrictRows;
                     int czc = (int)((long long)qx * qy * m[2] / (16LL * c->n_sm));
                     czc = czc < 1 ? 1 : (czc > 8 ? 8 : czc);
                     const dim3 qgrd(qx, qy, (m[2] + czc - 1) / czc);
-                    k_restrict_red_rb<<<qgrd, dim3(32, 2 * kRestrictRows), 0, c->stream>>>(
-                        L, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1], m[2], c->st[l + 1], (T*)c->rhs[l + 1],
-                        rb.half, chalf, czc);
+                    launch_pdl(c, k_restrict_red_rb, qgrd, dim3(32, 2 * kRestrictRows), 0, L, (T)1 / L.h2, st, rhs, e,
+                               scratch, m[0], m[1], m[2], c->st[l + 1], (T*)c->rhs[l + 1], rb.half, chalf, czc);
                     done = true;
                 } else if (split) {
-                    k_near_residual<T, E, RbMap><<<ngrd, 256, 0, c->stream>>>(
-                        L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
+                    launch_pdl(c, k_near_residual<T, E, RbMap>, ngrd, 256, 0, L, st, rhs, e, c->near_list[l], cnt,
+                               c->near_cap[l], (T)1 / L.h2, scratch, A, rb);
                     const dim3 qgrd((m[0] / 4 + 31) / 32, (m[1] + 1) / 2, m[2]);
-                    k_restrict_rb<<<qgrd, vblk, 0, c->stream>>>(L, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1],
-                                                                c->st[l + 1], (T*)c->rhs[l + 1], rb.half, chalf);
+                    launch_pdl(c, k_restrict_rb, qgrd, vblk, 0, L, (T)1 / L.h2, st, rhs, e, scratch, m[0], m[1],
+                               c->st[l + 1], (T*)c->rhs[l + 1], rb.half, chalf);
                     done = true;
                 }
             }
             if (!done) {
-                k_near_residual<T, E><<<ngrd, 256, 0, c->stream>>>(L, st, rhs, e, c->near_list[l], cnt,
-                                                                   c->near_cap[l], (T)1 / L.h2, scratch, A);
-                k_restrict_v<T, E><<<rgrd, vblk, 0, c->stream>>>(L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch,
-                                                                 m[0], m[1], c->st[l + 1], (T*)c->rhs[l + 1], A, 0,
-                                                                 red_only ? 1 : 0);
+                launch_pdl(c, k_near_residual<T, E>, ngrd, 256, 0, L, st, rhs, e, c->near_list[l], cnt, c->near_cap[l],
+                           (T)1 / L.h2, scratch, A, NatMap{});
+                launch_pdl(c, k_restrict_v<T, E>, rgrd, vblk, 0, L, inv_diag0, (T)1 / L.h2, st, rhs, e, scratch, m[0],
+                           m[1], c->st[l + 1], (T*)c->rhs[l + 1], A, 0, red_only ? 1 : 0);
             }
             count(c, 2);
         } else if constexpr (kNative) {
             dim3 cgrid((m[0] + 127) / 128, m[1], m[2]);
-            k_residual_restrict<T><<<cgrid, blk, 0, c->stream>>>(L, st, rhs, e, m[0], m[1], c->st[l + 1],
-                                                                 (T*)c->rhs[l + 1]);
+            launch_pdl(c, k_residual_restrict<T>, cgrid, blk, 0, L, st, rhs, e, m[0], m[1], c->st[l + 1],
+                       (T*)c->rhs[l + 1]);
             count(c);
         }
     }
@@ -3056,21 +3089,21 @@ cudaError_t vcycle_impl(es_ctx* c, int l, int warm) {
         if constexpr (kNative && std::is_same<T, float>::value) {
             if (black_only) {
                 const dim3 bgrd((L.nx / 8 + 31) / 32, (L.ny + 7) / 8, L.nz);
-                k_prolong_black_rb<<<bgrd, vblk, 0, c->stream>>>(L, st, e, rb.half, m[0], m[1], c->st[l + 1],
-                                                                 (const T*)c->e[l + 1], chalf);
+                launch_pdl(c, k_prolong_black_rb, bgrd, vblk, 0, L, st, e, rb.half, m[0], m[1], c->st[l + 1],
+                           (const T*)c->e[l + 1], chalf);
                 done = true;
             } else if (split) {
-                k_prolong_v<T, E, true><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1],
-                                                                      (const T*)c->e[l + 1], A, rb.half, chalf);
+                launch_pdl(c, k_prolong_v<T, E, true>, vgrd, vblk, 0, L, st, e, m[0], m[1], c->st[l + 1],
+                           (const T*)c->e[l + 1], A, rb.half, chalf);
                 done = true;
             }
         }
         if (done) {
         } else if (vec)
-            k_prolong_v<T, E><<<vgrd, vblk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1],
-                                                            (const T*)c->e[l + 1], A);
+            launch_pdl(c, k_prolong_v<T, E>, vgrd, vblk, 0, L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1],
+                       A, 0, 0);
         else if constexpr (kNative)
-            k_prolong<T><<<full, blk, 0, c->stream>>>(L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
+            launch_pdl(c, k_prolong<T>, full, blk, 0, L, st, e, m[0], m[1], c->st[l + 1], (const T*)c->e[l + 1]);
     }
     count(c);
     for (int s = 0; s < c->P.nu2; s++) sweep(0);
