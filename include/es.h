@@ -331,7 +331,8 @@ int es_gather(es_ctx* ctx, int which, const int64_t* idx, int n, double* out);
  *    part of it needs to start at zero.  Calls whose GPU work overlaps (two
  *    streams or two host threads at once) race on it: serialise them.
  *  - Copies the indices from the caller's (pageable) host array and
- *    synchronises the context's stream, like es_gather.                    */
+ *    synchronises the context's stream, like es_gather, so that stream
+ *    must not be one that is being captured into a graph.                 */
 #define ES_GATHER_NOALLOC_MAX 4096
 int es_gather_noalloc(es_ctx* ctx, int which, const int64_t* idx, int n, double* out);
 
