@@ -406,7 +406,7 @@ def run_ours(args):
 # current form, by kernel key; a kernel missing here has no capture of its
 # current code (traffic null).
 # (ncu --set full of the 320^3 workload, scaled to 512^3 by the cell count)
-TRAFFIC = {"smooth_half L0": 193.6e6 * 4.096, "lbm": 5247.9e6 * 4.096}
+TRAFFIC = {"smooth_half L0": 194.1e6 * 4.096, "lbm": 5220.8e6 * 4.096}
 
 
 def kernel_table(prof, lbm_bytes, peak):
