@@ -412,6 +412,8 @@ __global__ void __launch_bounds__(256, 2) k_outer_residual_ff(Grid g, ff diag0, 
         load_ff<W>(D, psi_hi, psi_lo, z0 > 0 ? orow + xq - plane : (zwall ? orow + xq : orow + xq + back));
         load_ff<W>(X, psi_hi, psi_lo, orow + xq);
         load(z0, orow, oa, ob, F, A, B, hlh, hll, hrh, hrl, sv);
+        // (four planes an iteration: the rolled rows are renamed, not moved)
+#pragma unroll 4
         for (int z = z0; z < z1; z++) {
             FFSpan<W> nF, nA, nB;
             float nlh = 0.0f, nll = 0.0f, nrh = 0.0f, nrl = 0.0f;
