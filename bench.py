@@ -63,6 +63,8 @@ def parse_args():
                     help="finest-level layout of the multigrid correction and right-hand side")
     ap.add_argument("--staging", choices=["registers", "bulk"], default="registers",
                     help="operand staging of the finest level's half sweep")
+    ap.add_argument("--nu", type=int, nargs=2, default=None, metavar=("NU1", "NU2"),
+                    help="pre- and post-smoothing sweeps of the V-cycle (default: the workload's 2, 2)")
     ap.add_argument("--lbm-block", type=int, nargs=2, default=(0, 0), metavar=("X", "Y"),
                     help="thread-block shape of the stream-collide (0 0: the library default)")
     return ap.parse_args()
@@ -248,6 +250,7 @@ def run_ours(args):
     sim = es.Simulation(wl, es.ES_MIXED32, device=str(dev),
                         overrides=dict(smoother=smoother, mg_storage=mg, fine_layout=lay,
                                        lbm_block=tuple(args.lbm_block),
+                                       **({"nu1": args.nu[0], "nu2": args.nu[1]} if args.nu else {}),
                                        sweep_staging=1 if args.staging == "bulk" else 0))
     stream = sim.stream
     N = wl.n_cells

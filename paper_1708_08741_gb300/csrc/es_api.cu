@@ -557,8 +557,7 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
             // ~1e-6 of the residual before the correction); the float-float
             // residual is formed again only if the updated one is not yet
             // below the tolerance
-            ES_CUDA(c, launch_residual_update(c));
-            ES_CUDA(c, launch_correct(c));
+            ES_CUDA(c, launch_residual_update(c, true));
             rc = read_norm_status(c, &norm, &st);
             if (rc != ES_OK) return rc;
             if (!(norm < c->tol) && !st) {

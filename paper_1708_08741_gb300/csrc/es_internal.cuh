@@ -195,7 +195,7 @@ cudaError_t launch_vcycle(es_ctx* c, int warm);
 cudaError_t launch_split_psi(es_ctx* c, const double* src);  // MIXED32: psi = src
 cudaError_t launch_join_psi(es_ctx* c, double* dst);         // MIXED32: dst = psi
 cudaError_t launch_correct(es_ctx* c);
-cudaError_t launch_residual_update(es_ctx* c);
+cudaError_t launch_residual_update(es_ctx* c, bool correct);  // correct: psi += e in the same pass
 cudaError_t launch_body_force(es_ctx* c);
 cudaError_t launch_body_force_near(es_ctx* c);      // f_b at the listed cells next to obstacles
 cudaError_t materialize_body_force(es_ctx* c);      // the whole stored f_b, when it is evaluated on the fly

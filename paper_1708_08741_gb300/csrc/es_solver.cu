@@ -2035,11 +2035,16 @@ __global__ void __launch_bounds__(256) k_restrict_rb(Level<float> L, float inv_h
 // plane z is formed.  Near-boundary cells take r - A e from
 // k_near_residual's scratch (natural index); other cells keep r = 0.  Each
 // block leaves one partial sum of r^2.
+// CORRECT: the same pass applies the correction psi += e (float-float, at
+// unknown cells, as k_correct_ff) to the 8 natural cells of each plane it
+// forms, so e and the state bytes are read once for both.
+template <bool CORRECT>
 __global__ void __launch_bounds__(256, 2) k_residual_update_rb(Level<float> L, float inv_h2,
                                                                const uint8_t* __restrict__ st,
                                                                float* __restrict__ rhs, const float* __restrict__ e,
                                                                const float* __restrict__ near_res, int half,
-                                                               double* __restrict__ partial, int zc) {
+                                                               double* __restrict__ partial, int zc,
+                                                               float* __restrict__ psi_hi, float* __restrict__ psi_lo) {
     __shared__ float swarp[8];
     const int nx = L.nx, ny = L.ny, nz = L.nz, nxh = nx >> 1;
     const int X0 = 4 * (blockIdx.x * 32 + threadIdx.x);
@@ -2159,6 +2164,26 @@ __global__ void __launch_bounds__(256, 2) k_residual_update_rb(Level<float> L, f
                 for (int j = 0; j < 8; j++) acc = __fmaf_rn(out[j], out[j], acc);
                 vst(rhs + pe * half + rowh + X0, out[0], out[2], out[4], out[6]);
                 vst(rhs + (pe ^ 1) * half + rowh + X0, out[1], out[3], out[5], out[7]);
+                if constexpr (CORRECT) {
+                    // natural cells 2 X0 .. 2 X0 + 7: e of the even cells is Ae, of the odd ones Ao
+                    float hv[8], lv[8];
+                    ES_VLD(hv, 0, psi_hi + rown);
+                    ES_VLD(hv, 4, psi_hi + rown + 4);
+                    ES_VLD(lv, 0, psi_lo + rown);
+                    ES_VLD(lv, 4, psi_lo + rown + 4);
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const unsigned sv = ((j < 4 ? sw.x : sw.y) >> (8 * (j & 3))) & 0xFFu;
+                        if ((sv & ST_KIND) != ST_UNKNOWN) continue;
+                        const ff v = ff_add_f({hv[j], lv[j]}, (j & 1) ? Ao[j >> 1] : Ae[j >> 1]);
+                        hv[j] = v.hi;
+                        lv[j] = v.lo;
+                    }
+                    vst(psi_hi + rown, hv[0], hv[1], hv[2], hv[3]);
+                    vst(psi_hi + rown + 4, hv[4], hv[5], hv[6], hv[7]);
+                    vst(psi_lo + rown, lv[0], lv[1], lv[2], lv[3]);
+                    vst(psi_lo + rown + 4, lv[4], lv[5], lv[6], lv[7]);
+                }
             }
             // plane z+1's even cells are the odd-colour array of row z's
             // parity, so the roll keeps the even / odd roles
@@ -3307,12 +3332,13 @@ cudaError_t launch_correct(es_ctx* c) {
 }
 
 // The FP32 residual update of the colour-split finest level (reduced
-// forms), after k_correct_ff.  Algorithmic bytes per cell: e (4), r in and
-// out (8), the state byte.
-cudaError_t launch_residual_update(es_ctx* c) {
+// forms); correct: with the correction psi += e in the same pass (else
+// k_correct_ff applies it).  Algorithmic bytes per cell: e (4), r in and out
+// (8), the state byte, and with the correction psi in and out (16).
+cudaError_t launch_residual_update(es_ctx* c, bool correct) {
     Level<float> L = level_desc<float>(c, 0);
     const int N = (int)c->g.N, nxh = L.nx / 2;
-    ProfScope ps(c, "residual_update", -1, (double)N * 13.0);
+    ProfScope ps(c, correct ? "residual_update_correct" : "residual_update", -1, (double)N * (correct ? 29.0 : 13.0));
     float* scratch = (float*)c->e2[0];
     const dim3 ngrd(near_grid_x(c), 2 * kNearSegs);
     k_near_residual<float, float, RbMap><<<ngrd, 256, 0, c->stream>>>(
@@ -3321,8 +3347,14 @@ cudaError_t launch_residual_update(es_ctx* c) {
     const int gx = (nxh / 4 + 31) / 32, gy = (L.ny + 7) / 8;
     int gz, zc;
     res_march_grid(c, gx, gy, L.nz, gz, zc);
-    k_residual_update_rb<<<dim3(gx, gy, gz), dim3(32, 8), 0, c->stream>>>(
-        L, 1.0f / L.h2, c->st[0], (float*)c->rhs[0], (const float*)c->e[0], scratch, N / 2, c->partial, zc);
+    if (correct)
+        k_residual_update_rb<true><<<dim3(gx, gy, gz), dim3(32, 8), 0, c->stream>>>(
+            L, 1.0f / L.h2, c->st[0], (float*)c->rhs[0], (const float*)c->e[0], scratch, N / 2, c->partial, zc,
+            c->psi32, c->psi_lo);
+    else
+        k_residual_update_rb<false><<<dim3(gx, gy, gz), dim3(32, 8), 0, c->stream>>>(
+            L, 1.0f / L.h2, c->st[0], (float*)c->rhs[0], (const float*)c->e[0], scratch, N / 2, c->partial, zc,
+            nullptr, nullptr);
     k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
     count(c, 3);
     return cudaGetLastError();

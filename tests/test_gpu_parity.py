@@ -195,7 +195,8 @@ def test_bench_solver_paths_mixed32_after_100_steps(name):
         assert ginfo["status"] == es.ES_OK and ginfo["r"] < ginfo["tol"]
     _assert_reduced(p.compare())
     seen = _profiled_names(p.g, 6)
-    updates = seen.get(("residual_update", -1), 0)
+    # (the update carries the correction psi += e in the same pass)
+    updates = seen.get(("residual_update_correct", -1), 0)
     assert updates > 0, "the FP32 residual update never ran"
 
 
