@@ -160,6 +160,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     b += lv;
     b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8 + 14 * 4 + 12 * 8);
     b += res_partial_slots(P->dims[0], P->dims[1], 0) * 8 + 64;
+    b += (size_t)kFlipCap * 4 + 3 * 256;  // flipped-cell list, its count, the moved flag
     return b;
 }
 
@@ -400,6 +401,12 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
         c->bf_count = (int*)A(kNearSegs * 4);
     }
     c->d_status = (int*)A(64);
+    c->d_moved = (int*)A(64);
+    c->flip_cap = kFlipCap;
+    c->flip_list = (int*)A((size_t)kFlipCap * 4);
+    c->flip_count = (int*)A(64);
+    c->res_valid = false;
+    c->res_age = 0;
     c->rb_wpr = (c->g.nx + 63) / 64;
     c->rbmask = c->rb0 ? (uint32_t*)A((size_t)2 * c->g.ny * c->g.nz * c->rb_wpr * 4) : nullptr;
     c->rb_wpr1 = (c->ln[1][0] + 63) / 64;
@@ -447,6 +454,8 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     if (e == cudaSuccess) e = cudaMemsetAsync(c->F, 0, np1 * 3 * 8, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->T, 0, np1 * 3 * 8, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 64, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_moved, 0, 64, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flip_count, 0, 64, c->stream);
     if (e == cudaSuccess) e = launch_init_flags(c);
     if (e == cudaSuccess) e = launch_coarse_states(c);
     if (e == cudaSuccess) e = launch_near_lists(c);
@@ -491,6 +500,12 @@ constexpr double kCycleTarget = 0.85;
 // at 5000 x tol that stays near 0.5 % of the tolerance, inside the margin
 // kCycleTarget leaves.
 constexpr double kFastUpdate = 5000.0;
+// A solve may start from the previous solve's residual patched around the
+// spheres (k_flip_patch) this many times in a row; the next one forms
+// it in full.  The residual carried between solves then holds at most this
+// many corrections' FP32 updates, each ~1e-6 of a residual within
+// kFastUpdate x tol, so its drift stays a small fraction of the tolerance.
+constexpr int kResAgeMax = 8;
 // (on small grids the float-float residual costs about a launch and the
 // update's occasional second norm read costs a host round trip: the update
 // is used from fast_update_cells cells on, default 2^21)
@@ -502,7 +517,15 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
     if (!c) return fail(nullptr, ES_EINVAL, "ctx is NULL");
     double norm;
     int st;
-    ES_CUDA(c, launch_outer_residual(c));
+    // The residual of the previous solve's potential is still in the finest
+    // right-hand side: form it again only around the spheres (unless one
+    // moved far, which the device decides), and in full every kResAgeMax
+    // solves, so that the FP32 updates of the corrections cannot drift.
+    const bool patch = forced_cycles < 0 && c->rb0 && c->res_valid && c->res_age < kResAgeMax &&
+                       c->g.N >= fast_update_cells(c);
+    c->res_valid = false;
+    ES_CUDA(c, launch_outer_residual(c, patch));
+    c->res_age = patch ? c->res_age + 1 : 0;
     int rc = read_norm_status(c, &norm, &st);
     if (rc != ES_OK) return rc;
     if (st) {
@@ -588,6 +611,9 @@ int es_potential_solve(es_ctx* c, int forced_cycles, es_solve_info* info) {
         info->r_final = norm;
         info->tol = c->tol;
     }
+    // (every path of the loop leaves the residual of the final psi in the
+    // finest right-hand side)
+    c->res_valid = result == ES_OK;
     ES_CUDA(c, launch_body_force(c));
     return result;
 }
@@ -729,6 +755,7 @@ int es_set_field(es_ctx* c, int which, const void* src, size_t bytes, int on_dev
         return fail(c, ES_EINVAL, "field is read-only");
     if (bytes != field_size(c, which)) return fail(c, ES_EINVAL, "wrong size");
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (which == ES_FIELD_PSI) c->res_valid = false;  // (the carried residual belongs to the old psi)
     if (which == ES_FIELD_PSI && !mixed(c)) {
         ES_CUDA(c, cudaMemcpyAsync(c->psi, src, bytes, k, c->stream));
     } else {

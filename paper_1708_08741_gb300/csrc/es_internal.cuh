@@ -133,6 +133,13 @@ struct es_ctx {
     int red_blocks;
     double* d_norm;
     int* d_status;
+    int* d_moved;    // device: 1 when a sphere moved half a cell or more since the last solve's start
+                     // (or the flipped-cell list overflowed)
+    int* flip_list;  // device: cells that changed between obstacle and fluid since then
+    int* flip_count;
+    int flip_cap;
+    bool res_valid;  // the finest right-hand side holds the residual of the current psi (reduced forms)
+    int res_age;     // solves started from a patched residual since the last full one
     double* h_norm;  // pinned: [0] norm
     int* h_status;   // pinned
     double* h_pset;  // pinned: np x 12, the staging of es_set_particles
@@ -190,7 +197,7 @@ cudaError_t launch_map(es_ctx* c);
 cudaError_t launch_coarse_states(es_ctx* c);
 cudaError_t launch_near_lists(es_ctx* c);
 // solver (es_solver.cu)
-cudaError_t launch_outer_residual(es_ctx* c);
+cudaError_t launch_outer_residual(es_ctx* c, bool patch = false);  // patch: see k_residual_patch
 cudaError_t launch_vcycle(es_ctx* c, int warm);
 cudaError_t launch_split_psi(es_ctx* c, const double* src);  // MIXED32: psi = src
 cudaError_t launch_join_psi(es_ctx* c, double* dst);         // MIXED32: dst = psi
@@ -250,6 +257,7 @@ inline int near_grid_x(const es_ctx* c) {
 // then the other's, each in natural order; the states stay natural).
 inline bool split_level(const es_ctx* c, int l) { return (l == 0 && c->rb0) || (l == 1 && c->rb1); }
 
+constexpr int kFlipCap = 1 << 16;  // cells of the flipped-cell list (obstacle <-> fluid between solves)
 constexpr int kResPartials = 8192;
 // Partial-sum slots of the blocked residual norms: one per block of the
 // marching residual passes (at most kResPartials planes of blocks, and a

@@ -86,6 +86,23 @@ __device__ Box union_box(const Grid& g, const double* Xo, const double* Xn, doub
 // in thread 0 and share it; per cell they work in integers and FP32 and
 // fall back to the FP64 cell-in-sphere test only where FP32 cannot decide.
 
+// Cells whose state flipped since the last solve (obstacle <-> fluid) go to
+// a short list for the patched residual at the next solve's start
+// (k_flip_patch); when it is full the next solve forms the residual in full.
+struct FlipList {
+    int* cells;
+    int* count;
+    int cap;
+    int* full;  // set when a cell did not fit
+    __device__ __forceinline__ void add(long long c) const {
+        const int i = atomicAdd(count, 1);
+        if (i < cap)
+            cells[i] = (int)c;
+        else
+            *full = 1;
+    }
+};
+
 __global__ void k_clear(Grid g, const DParticle* part, const double* mapped, int32_t* owner) {
     __shared__ Box sb;
     int p = blockIdx.x;
@@ -104,7 +121,7 @@ __global__ void k_clear(Grid g, const DParticle* part, const double* mapped, int
 }
 
 __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* owner, double* psi,
-                      float* psi_hi, float* psi_lo, int* status) {
+                      float* psi_hi, float* psi_lo, int* status, FlipList flips) {
     __shared__ Box sb;
     __shared__ BallF sball;
     __shared__ double sbval;
@@ -143,6 +160,7 @@ __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* o
         long long c = lin(g, x, y, z);
         int old = atomicExch(&owner[c], p);
         if (old >= 0 && old != p) atomicOr(status, DS_OVERLAP);
+        if (old == -1) flips.add(c);  // (a fluid cell became an obstacle cell)
         if (psi) {
             psi[c] = sbval;
         } else {
@@ -153,7 +171,8 @@ __global__ void k_set(Grid g, const DParticle* part, const int* kind, int32_t* o
 }
 
 template <class S>
-__global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, int32_t* owner, S* pdf) {
+__global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, int32_t* owner, S* pdf,
+                          FlipList flips) {
     __shared__ Box sb;
     int p = blockIdx.x;
     const double* M = mapped + 9 * p;  // x, v, w at the last mapping
@@ -169,6 +188,7 @@ __global__ void k_uncover(Grid g, const DParticle* part, const double* mapped, i
         long long c = lin(g, x, y, z);
         if (owner[c] != -2 - p) continue;
         owner[c] = -1;
+        flips.add(c);  // (an obstacle cell became a fluid cell)
         double u[3];
         surface_velocity(g, M, M + 3, M + 6, x, y, z, u);
         double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -329,10 +349,18 @@ __global__ void k_flags(Grid g, DParticle* part, const double* mapped, const int
 // Keeps the mapped state for the next reconstruction and, in the MIXED32
 // form, the sphere's boundary value for the float-float outer residual:
 // 2 zeta for a Dirichlet sphere, sigma / eps for a charged one (Sec. 5.4).
-__global__ void k_store_mapped(const DParticle* part, const int* kind, double eps, double* mapped, float* pbc,
-                               int np) {
+// Raises *moved when the sphere moved half a cell or more along an axis
+// since the previous mapping (minimum image on periodic axes).
+__global__ void k_store_mapped(Grid g, const DParticle* part, const int* kind, double eps, double* mapped,
+                               float* pbc, int np, int* moved) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
+    for (int a = 0; a < 3; a++) {
+        double d = fabs(part[p].x[a] - mapped[9 * p + a]);
+        const double L = (double)gdim(g, a);
+        if (g.per[a] && d > 0.5 * L) d = L - d;
+        if (!(d < 0.5)) *moved = 1;
+    }
     for (int a = 0; a < 3; a++) {
         mapped[9 * p + a] = part[p].x[a];
         mapped[9 * p + 3 + a] = part[p].v[a];
@@ -691,22 +719,27 @@ cudaError_t launch_map(es_ctx* c) {
     if (c->np == 0) return cudaSuccess;
     const Grid& g = c->g;
     const int T = 256;
+    const FlipList flips{c->flip_list, c->flip_count, c->flip_cap, c->d_moved};
     {
         ProfScope ps(c, "map_clear", -1, 0.0);
         k_clear<<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner);
     }
     {
         ProfScope ps(c, "map_set", -1, 0.0);
-        k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->psi32, c->psi_lo, c->d_status);
+        k_set<<<c->np, T, 0, c->stream>>>(g, c->part, c->kind, c->owner, c->psi, c->psi32, c->psi_lo, c->d_status,
+                                          flips);
     }
     {
         ProfScope ps(c, "map_uncover", -1, 0.0);
         if (c->P.precision == ES_MIXED16)
-            k_uncover<__half><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (__half*)c->pdf[c->cur]);
+            k_uncover<__half><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (__half*)c->pdf[c->cur],
+                                                            flips);
         else if (mixed(c))
-            k_uncover<float><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (float*)c->pdf[c->cur]);
+            k_uncover<float><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (float*)c->pdf[c->cur],
+                                                           flips);
         else
-            k_uncover<double><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (double*)c->pdf[c->cur]);
+            k_uncover<double><<<c->np, T, 0, c->stream>>>(g, c->part, c->mapped, c->owner, (double*)c->pdf[c->cur],
+                                                            flips);
     }
     {
         ProfScope ps(c, "map_flags", -1, 0.0);
@@ -714,8 +747,8 @@ cudaError_t launch_map(es_ctx* c) {
                                             c->nfaces, c->mapped_once ? 0 : 1);
         c->mapped_once = true;
     }
-    k_store_mapped<<<(c->np + 127) / 128, 128, 0, c->stream>>>(c->part, c->kind, c->S.eps, c->mapped, c->pbc,
-                                                                c->np);
+    k_store_mapped<<<(c->np + 127) / 128, 128, 0, c->stream>>>(g, c->part, c->kind, c->S.eps, c->mapped, c->pbc,
+                                                                c->np, c->d_moved);
     count(c, 5);
     return cudaGetLastError();
 }

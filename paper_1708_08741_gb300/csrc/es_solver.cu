@@ -366,8 +366,10 @@ __global__ void __launch_bounds__(256, 2) k_outer_residual_ff(Grid g, ff diag0, 
                                                            const float* __restrict__ psi_lo,
                                                            const uint8_t* __restrict__ st0,
                                                            float* __restrict__ r_out,
-                                                           double* __restrict__ partial, int zc) {
+                                                           double* __restrict__ partial, int zc,
+                                                           const int* __restrict__ gate) {
     static_assert(!SPLIT || W == 4, "the split store takes 4-cell spans");
+    if (gate && *gate == 0) return;  // (uniform over the grid: the patched residual runs instead)
     __shared__ float swarp[8];
     const int half = (int)(g.N >> 1);
     float acc = 0.0f;
@@ -3176,6 +3178,87 @@ void set_coarse_smem(const es_ctx* c) {
     }
 }
 
+// The start of a solve when the float-float residual of the previous
+// solve's potential is still in the finest right-hand side (colour-split,
+// reduced forms) and every sphere has moved less than half a cell since
+// then.  The residual changes only where a cell's stencil or boundary value
+// changed: at the listed near-boundary cells (their boundary values and the
+// spheres' surface charges), formed again by k_outer_residual_near_ff, and
+// at the cells that flipped between obstacle and fluid (k_set, k_uncover)
+// and their six neighbours (which covers the cells that stopped being
+// near-boundary cells), formed here: 0 at obstacle cells.  A cell reached
+// from several entries gets the same value each time.  gate: 1 when some
+// sphere moved farther or the list overflowed (the full residual runs
+// instead).
+template <class M>
+__global__ void __launch_bounds__(256) k_flip_patch(Grid g, ff diag0, WallFF wall, int pot_dir_mask,
+                                                    const float* __restrict__ psi_hi,
+                                                    const float* __restrict__ psi_lo,
+                                                    const uint8_t* __restrict__ st0,
+                                                    const int32_t* __restrict__ owner,
+                                                    const float2* __restrict__ pbc,
+                                                    const int* __restrict__ flips, const int* __restrict__ nflips,
+                                                    int cap, float* __restrict__ r_out, M m,
+                                                    const int* __restrict__ gate) {
+    if (*gate != 0) return;
+    const int n = *nflips < cap ? *nflips : cap;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 7 * n; i += gridDim.x * blockDim.x) {
+        const int c = flips[i / 7], k = i % 7;
+        int p3[3] = {c % nx, (c / nx) % ny, c / (nx * ny)};
+        if (k > 0) {
+            const int ax = (k - 1) >> 1, side = (k & 1) ? -1 : 1;
+            const int n3 = ax == 0 ? nx : (ax == 1 ? ny : nz);
+            int q = p3[ax] + side;
+            if (q < 0 || q >= n3) {
+                if (!g.per[ax]) continue;  // (beyond a wall: no cell)
+                q = q < 0 ? q + n3 : q - n3;
+            }
+            p3[ax] = q;
+        }
+        const int cc = p3[0] + nx * (p3[1] + ny * p3[2]);
+        const float v = (st0[cc] & ST_KIND) == ST_UNKNOWN
+                            ? near_residual_ff(g, diag0, wall, pot_dir_mask, psi_hi, psi_lo, st0, owner, pbc, p3[0],
+                                               p3[1], p3[2])
+                            : 0.0f;
+        r_out[m(cc, (p3[0] + p3[1] + p3[2]) & 1)] = v;
+    }
+}
+
+// Sum of r^2 over the colour-split finest right-hand side, with the block
+// layout and partial slots of k_outer_residual_ff<4, true> (zc planes a
+// block), for the patched residual.  gate: 1 when the full residual runs
+// instead.
+__global__ void __launch_bounds__(256) k_rhs_norm_rb(Grid g, const float* __restrict__ r, int zc,
+                                                     double* __restrict__ partial, const int* __restrict__ gate) {
+    if (*gate != 0) return;
+    __shared__ float swarp[8];
+    const int half = (int)(g.N >> 1);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int xs = 4 * (blockIdx.x * 32 + threadIdx.x);
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    const int z0 = (int)blockIdx.z * zc;
+    const int z1 = z0 + zc < nz ? z0 + zc : nz;
+    float acc = 0.0f;
+    if (xs < nx && y < ny)
+        for (int z = z0; z < z1; z++) {
+            const Q4<float> q = rb_ld4(r, half, xs + nx * (y + ny * z), (xs + y + z) & 1);
+            acc = __fmaf_rn(q.v0, q.v0, acc);
+            acc = __fmaf_rn(q.v1, q.v1, acc);
+            acc = __fmaf_rn(q.v2, q.v2, acc);
+            acc = __fmaf_rn(q.v3, q.v3, acc);
+        }
+    float v = acc;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) swarp[threadIdx.y] = v;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; w++) tot += (double)swarp[w];
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+    }
+}
+
 }  // namespace
 
 // Grid of a marching residual pass over a level of nz planes with (gx, gy)
@@ -3193,9 +3276,12 @@ static void res_march_grid(const es_ctx* c, int gx, int gy, int nz, int& gz, int
 
 // Algorithmic bytes per cell: psi (8: double, or float-float) and the state
 // byte in, r out (8 as double, 4 as the float right-hand side).
-cudaError_t launch_outer_residual(es_ctx* c) {
+cudaError_t launch_outer_residual(es_ctx* c, bool patch) {
     const double diag0 = 6.0 + c->S.kappa * c->S.kappa;
-    ProfScope ps(c, "outer_residual", -1, (double)c->g.N * (mixed(c) ? 13.0 : 17.0));
+    patch = patch && mixed(c) && c->rb0;
+    // (bytes: the full residual's; a patched start moves r once, 4 a cell, plus the listed cells)
+    ProfScope ps(c, patch ? "residual_patch" : "outer_residual", -1,
+                 (double)c->g.N * (patch ? 4.0 : (mixed(c) ? 13.0 : 17.0)));
     if (mixed(c)) {
         WallFF wall;
         int mask = 0;
@@ -3213,26 +3299,42 @@ cudaError_t launch_outer_residual(es_ctx* c) {
         const dim3 ngrd(near_grid_x(c), 2 * kNearSegs);
         const ff d0 = ff_from_double(diag0);
         float* r = (float*)c->rhs[0];
+        // patch: the full residual only if the mapping flagged a sphere that
+        // moved half a cell or more (the gate), else the patched one
+        const int* gate = patch ? c->d_moved : nullptr;
         if (c->rb0) {
             // r goes to the colour-split right-hand side of the finest level
+            const RbMap rb{(int)(c->g.N / 2)};
             k_outer_residual_near_ff<RbMap><<<ngrd, 256, 0, c->stream>>>(
                 c->g, d0, wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner, (const float2*)c->pbc,
-                c->near_list[0], c->near_count, c->near_cap[0], r, RbMap{(int)(c->g.N / 2)});
+                c->near_list[0], c->near_count, c->near_cap[0], r, rb);
             k_outer_residual_ff<4, true><<<grd, blk, 0, c->stream>>>(c->g, d0, c->psi32, c->psi_lo, c->st[0], r,
-                                                                      c->partial, zc);
+                                                                      c->partial, zc, gate);
+            if (patch) {
+                k_flip_patch<RbMap><<<2 * c->n_sm, 256, 0, c->stream>>>(
+                    c->g, d0, wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner, (const float2*)c->pbc,
+                    c->flip_list, c->flip_count, c->flip_cap, r, rb, c->d_moved);
+                k_rhs_norm_rb<<<grd, blk, 0, c->stream>>>(c->g, r, zc, c->partial, c->d_moved);
+                count(c, 2);
+            }
         } else {
             k_outer_residual_near_ff<NatMap><<<ngrd, 256, 0, c->stream>>>(
                 c->g, d0, wall, mask, c->psi32, c->psi_lo, c->st[0], c->owner, (const float2*)c->pbc,
                 c->near_list[0], c->near_count, c->near_cap[0], r, NatMap{});
             if (W == 4)
                 k_outer_residual_ff<4, false><<<grd, blk, 0, c->stream>>>(c->g, d0, c->psi32, c->psi_lo, c->st[0],
-                                                                           r, c->partial, zc);
+                                                                           r, c->partial, zc, nullptr);
             else
                 k_outer_residual_ff<1, false><<<grd, blk, 0, c->stream>>>(c->g, d0, c->psi32, c->psi_lo, c->st[0],
-                                                                           r, c->partial, zc);
+                                                                           r, c->partial, zc, nullptr);
         }
         k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
         count(c, 3);
+        // (the mapping raises the flag again when a sphere moves far, and
+        // lists the cells that flip from here on)
+        cudaError_t err = cudaMemsetAsync(c->d_moved, 0, sizeof(int), c->stream);
+        if (err == cudaSuccess) err = cudaMemsetAsync(c->flip_count, 0, sizeof(int), c->stream);
+        if (err != cudaSuccess) return err;
         return cudaGetLastError();
     }
     const double k2 = c->S.kappa * c->S.kappa;

@@ -198,6 +198,8 @@ def test_bench_solver_paths_mixed32_after_100_steps(name):
     # (the update carries the correction psi += e in the same pass)
     updates = seen.get(("residual_update_correct", -1), 0)
     assert updates > 0, "the FP32 residual update never ran"
+    # solves that start from the carried residual, patched around the spheres
+    assert seen.get(("residual_patch", -1), 0) > 0, "no solve started from a patched residual"
 
 
 @pytest.mark.parametrize("precision", [es.ES_MIXED32, es.ES_MIXED16])
