@@ -202,6 +202,35 @@ def test_bench_solver_paths_mixed32_after_100_steps(name):
     assert seen.get(("residual_patch", -1), 0) > 0, "no solve started from a patched residual"
 
 
+@pytest.mark.parametrize("name", sorted(LIST_CASES))
+def test_patched_residual_equals_the_full_one(name):
+    """A solve that starts from the previous solve's residual, formed again
+    only at the near-boundary cells and around the cells that flipped
+    between obstacle and fluid, starts from the norm the full float-float
+    residual gives (to the FP32 updates the carried residual holds); the
+    full one is forced on a twin run by writing its psi back unchanged."""
+    wl = LIST_CASES[name]()
+    a = es.Simulation(wl, es.ES_MIXED32, overrides=BENCH_PATHS)
+    b = es.Simulation(wl, es.ES_MIXED32, overrides=BENCH_PATHS)
+    for _ in range(7):
+        a.step()
+        b.step()
+    # (the twins are in the same state here)
+    b.set_field(es.FIELD_PSI, b.field(es.FIELD_PSI))  # (the carried residual is dropped)
+    ra, rb = [], []
+    for sim, out in ((a, ra), (b, rb)):
+        sim.map_particles()
+        sim.profile_start()
+        out.append(sim.solve())
+        out.append({(r["name"], r["level"]) for r in sim.profile_stop()})
+    assert ("residual_patch", -1) in ra[1] and ("outer_residual", -1) in rb[1]
+    print("start residual: patched", ra[0]["r0"], "full", rb[0]["r0"], "tol", ra[0]["tol"])
+    assert ra[0]["r0"] == pytest.approx(rb[0]["r0"], rel=1e-5)
+    assert ra[0]["cycles"] == rb[0]["cycles"]
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("precision", [es.ES_MIXED32, es.ES_MIXED16])
 @pytest.mark.parametrize("name", ["channel64", "suspension64", "mixed_ragged"])
 def test_fused_body_force_equals_the_stored_field(name, precision):
