@@ -196,6 +196,13 @@ def cpu_baseline(n=128):
                                   "all 100 steps, serial build"}}
 
 
+def workload_name(n, n_spheres, levels, res_rf):
+    """The benchmark workload as both arms name it in `config` (the
+    arithmetic form is the line's `dtype`)."""
+    return (f"suspension {n}^3 periodic, {n_spheres} charged spheres R=5, lambda_D=4, E=1e-3, "
+            f"{levels}-level V(2,2) to RES_RF {res_rf:g}")
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores (OpenMP build), each step
     one oracle step of an n^3 sub-box of the suspension; rank 0 only."""
@@ -209,12 +216,15 @@ def run_reference(args):
     wl = W.suspension_sample(n)
     value, dt = _oracle_mlups(wl, args.steps, args.warmup, omp=True)
     cores = oracle.threads(True)
+    full = W.suspension(n=args.n, n_spheres=int(round(2880 * (args.n / 512) ** 3)),
+                        levels=6 if args.n % 32 == 0 else 4)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"suspension sample {n}^3, {wl.n_particles} spheres R=5 (density of 2,880 in 512^3)",
-                   "parallelism": f"host cores x{cores}"},
+        "config": {"workload": workload_name(args.n, full.n_particles, full.levels, full.res_rf),
+                   "cells": full.n_cells, "parallelism": f"host cores x{cores}",
+                   "sample": f"{n}^3 periodic sub-box, {wl.n_particles} spheres R=5 (the same density)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step one oracle step of the {n}^3 sub-box (OpenMP build, all host cores)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -372,8 +382,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"suspension {args.n}^3 periodic, {wl.n_particles} charged spheres R=5, "
-                               f"lambda_D=4, E=1e-3, MIXED32, {levels}-level V(2,2) to RES_RF {wl.res_rf:g}"
+        "config": {"workload": workload_name(args.n, wl.n_particles, levels, wl.res_rf)
                                + (", FP16 finest-level correction" if mg == es.ES_MG_FP16 else ""),
                    "cells": N, "fluid_cells": n_fluid, "parallelism": f"replicas x{world}",
                    "l2_policy": "inputs larger than L2 (PDF fields 20 GB)"},
