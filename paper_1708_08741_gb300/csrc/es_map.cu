@@ -516,6 +516,7 @@ __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const
     if (row >= ny * nz) return;  // whole warps
     const int seg = row % kNearSegs;
     const int y = row % ny, z = row / ny;
+    unsigned pend[2] = {0u, 0u};  // (low halves of the mask words, stored with their high halves)
     for (int x0 = 0; x0 < nx; x0 += 32) {
         const int x = x0 + lane;
         bool take = false, inner = false;
@@ -529,12 +530,12 @@ __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const
             for (int colour = 0; colour < 2; colour++) {
                 const bool b = inner && ((x + y + z) & 1) == colour;
                 const unsigned v = __reduce_or_sync(0xffffffffu, b ? 1u << (lane >> 1) : 0u);
-                if (lane == 0) {
-                    uint32_t* m = rbmask + (size_t)colour * ((size_t)ny * nz * wpr) + (size_t)wpr * row + x0 / 64;
-                    if ((x0 & 63) == 0)
-                        *m = v;  // (the high half follows in the next step, or stays 0 past the row's end)
-                    else
-                        *m |= v << 16;
+                const bool last = x0 + 32 >= nx;
+                if ((x0 & 63) == 0) pend[colour] = v;
+                if (lane == 0 && ((x0 & 63) != 0 || last)) {
+                    // the word of compact places x0/2 & ~31 .. +31 (a high half past the row's end stays 0)
+                    const unsigned word = (x0 & 63) != 0 ? (pend[colour] | (v << 16)) : v;
+                    rbmask[(size_t)colour * ((size_t)ny * nz * wpr) + (size_t)wpr * row + x0 / 64] = word;
                 }
             }
         }
