@@ -197,7 +197,7 @@ cudaError_t launch_map(es_ctx* c);
 cudaError_t launch_coarse_states(es_ctx* c);
 cudaError_t launch_near_lists(es_ctx* c);
 // solver (es_solver.cu)
-cudaError_t launch_outer_residual(es_ctx* c, bool patch = false);  // patch: see k_residual_patch
+cudaError_t launch_outer_residual(es_ctx* c, bool patch = false);  // patch: see k_flip_patch
 cudaError_t launch_vcycle(es_ctx* c, int warm);
 cudaError_t launch_split_psi(es_ctx* c, const double* src);  // MIXED32: psi = src
 cudaError_t launch_join_psi(es_ctx* c, double* dst);         // MIXED32: dst = psi
