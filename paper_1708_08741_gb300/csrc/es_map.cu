@@ -622,17 +622,25 @@ __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const 
             sw = *reinterpret_cast<const unsigned*>(st + xs + nx * row);
             fw = *reinterpret_cast<const unsigned*>(flags + xs + nx * row);
         }
+        // the three tests on the lane's four cells at once: bit 0 of each
+        // byte (state values < 8, flag values < 4) gathered into a nibble,
+        // cell i at bit i
+        sw &= 0x07070707u;
+        fw &= 0x03030303u;
+        auto nibble = [](unsigned b) { return ((b & 0x01010101u) * 0x01020408u) >> 24; };
+        const unsigned in4 = nibble(~(sw | (sw >> 1) | (sw >> 2)));  // state 0: interior unknown cell
+        const unsigned nr4 = nibble((sw >> 2) & ~(sw | (sw >> 1)));  // state 4: near-boundary unknown cell
+        const unsigned bf4 = nibble((fw >> 1) & ~fw);                // flags 2: next to an obstacle, fluid
+        const int p0 = (y + z) & 1;                                  // colour of cells xs and xs + 2
         if (rbmask) {
-            // lane's cells of colour k: xs + O and xs + 2 + O, O = (k + y + z) & 1,
-            // at compact places xs / 2 and xs / 2 + 1 (bits 2 lane, 2 lane + 1
+            // lane's cells of colour k: xs + O and xs + 2 + O, O = k ^ p0, at
+            // compact places xs / 2 and xs / 2 + 1 (bits 2 lane, 2 lane + 1
             // of this span's 64)
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const int O = (k + y + z) & 1;
-                const unsigned s0 = (sw >> (8 * O)) & 0xFFu, s1 = (sw >> (8 * (2 + O))) & 0xFFu;
-                const unsigned v = (((s0 & (ST_KIND | ST_NEAR)) == ST_UNKNOWN) ? 1u : 0u) |
-                                   (((s1 & (ST_KIND | ST_NEAR)) == ST_UNKNOWN) ? 2u : 0u);
-                const unsigned sh = (xs < nx ? v : 0u) << ((2 * lane) & 31);
+                const int O = k ^ p0;
+                const unsigned v = ((in4 >> O) & 1u) | (((in4 >> (O + 2)) & 1u) << 1);
+                const unsigned sh = v << ((2 * lane) & 31);
                 const unsigned lo = __reduce_or_sync(0xffffffffu, lane < 16 ? sh : 0u);
                 const unsigned hi = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : sh);
                 const int w0 = x0 / 64;  // (x0 is a multiple of 128)
@@ -641,28 +649,26 @@ __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const 
                 if (lane == 16 && w0 + 1 < wpr) m[w0 + 1] = hi;
             }
         }
-        unsigned m_near[2] = {0, 0}, m_bf = 0;
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const unsigned s8 = (sw >> (8 * i)) & 0xFFu, f8 = (fw >> (8 * i)) & 0xFFu;
-            if ((s8 & ST_KIND) == ST_UNKNOWN && (s8 & ST_NEAR)) m_near[(xs + i + y + z) & 1] |= 1u << i;
-            if ((f8 & F_NEAR19) && !(f8 & F_SOLID)) m_bf |= 1u << i;
-        }
         // (most 128-cell spans hold no listed cell: one vote skips them)
-        if (!__any_sync(0xffffffffu, (m_near[0] | m_near[1] | m_bf) != 0)) continue;
+        if (!__any_sync(0xffffffffu, (nr4 | bf4) != 0)) continue;
+        // near-boundary cells by colour: cells i = 0, 2 have colour p0, i = 1, 3 the other
+        const unsigned ms[3] = {p0 == 0 ? nr4 & 0x5u : nr4 & 0xAu, p0 == 0 ? nr4 & 0xAu : nr4 & 0x5u, bf4};
+        // one scan for the three lists: 8-bit fields (a warp lists at most 128 cells of one list)
+        int total;
+        const int excl = warp_excl_scan((int)(__popc(ms[0]) | (__popc(ms[1]) << 8) | (__popc(ms[2]) << 16)), total);
+        int base = 0;
+        if (lane < 3) {
+            const int tl = (total >> (8 * lane)) & 0xFF;
+            int* cnt = lane < 2 ? &count[lane * kNearSegs + seg] : &bf_count[seg];
+            if (tl) base = atomicAdd(cnt, tl);
+        }
 #pragma unroll
         for (int t = 0; t < 3; t++) {
-            const unsigned m = t < 2 ? m_near[t] : m_bf;
-            if (!__any_sync(0xffffffffu, m != 0)) continue;
-            int total;
-            const int excl = warp_excl_scan(__popc(m), total);
-            int* cnt = t < 2 ? &count[t * kNearSegs + seg] : &bf_count[seg];
-            int base = 0;
-            if (lane == 0) base = atomicAdd(cnt, total);
-            base = __shfl_sync(0xffffffffu, base, 0);
+            const int bt = __shfl_sync(0xffffffffu, base, t);
+            const unsigned m = ms[t];
             int* out = t < 2 ? list + (size_t)(t * kNearSegs + seg) * cap : bf_list + (size_t)seg * bf_cap;
             const int c_out = t < 2 ? cap : bf_cap;
-            int k = base + excl;
+            int k = bt + ((excl >> (8 * t)) & 0xFF);
 #pragma unroll
             for (int i = 0; i < 4; i++)
                 if ((m >> i) & 1u) {
