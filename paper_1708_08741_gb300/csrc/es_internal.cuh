@@ -138,6 +138,8 @@ struct es_ctx {
     int* flip_list;  // device: cells that changed between obstacle and fluid since then
     int* flip_count;
     int flip_cap;
+    int* local_list;  // device scratch of the local correction at a solve's start (colour-split levels)
+    float* local_f;   // 3 x kLocalCells floats
     bool res_valid;  // the finest right-hand side holds the residual of the current psi (reduced forms)
     int res_age;     // solves started from a patched residual since the last full one
     double* h_norm;  // pinned: [0] norm
@@ -257,7 +259,9 @@ inline int near_grid_x(const es_ctx* c) {
 // then the other's, each in natural order; the states stay natural).
 inline bool split_level(const es_ctx* c, int l) { return (l == 0 && c->rb0) || (l == 1 && c->rb1); }
 
-constexpr int kFlipCap = 1 << 16;  // cells of the flipped-cell list (obstacle <-> fluid between solves)
+constexpr int kFlipCap = 1 << 16;
+// cells of the local correction's region and ring: at most 16 flipped cells, boxes of radius 9
+constexpr int kLocalCells = 16 * 19 * 19 * 19;  // cells of the flipped-cell list (obstacle <-> fluid between solves)
 constexpr int kResPartials = 8192;
 // Partial-sum slots of the blocked residual norms: one per block of the
 // marching residual passes (at most kResPartials planes of blocks, and a

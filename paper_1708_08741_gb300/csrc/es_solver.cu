@@ -3259,6 +3259,224 @@ __global__ void __launch_bounds__(256) k_rhs_norm_rb(Grid g, const float* __rest
     }
 }
 
+// A local correction at a solve's start (after the patched residual).
+// Between two solves the equation changes only around the few cells that
+// flipped between obstacle and fluid, and there the start residual sits:
+// the correction it asks for is a few screened point responses that decay
+// like exp(-r kappa).  So the correction equation A e = r is first solved
+// on the unknown cells within Chebyshev distance kLocalR of a flipped cell
+// (e = 0 beyond them), by conjugate gradients in one block, before any
+// V-cycle: psi += e there, r -= A e there and on the ring one cell further
+// out, and the residual norm is updated by the change of r^2 over those
+// cells.  The V-cycles then start from that residual (none when it is
+// already below the tolerance).  Cells of the region carry bit 7 of their
+// flag byte, ring cells bit 6, while the kernel runs.  gate: 1 when the full
+// residual ran (a sphere moved far or the flip list overflowed); more than
+// kLocalFlips flips, or a region over kLocalCap cells, leave the V-cycles
+// alone.
+constexpr int kLocalR = 8;
+constexpr int kLocalFlips = 16;
+constexpr int kLocalIters = 40;
+constexpr int kLocalCap = kLocalFlips * (2 * kLocalR + 3) * (2 * kLocalR + 3) * (2 * kLocalR + 3);
+static_assert(kLocalCap == kLocalCells, "the scratch sized at creation");
+constexpr int kLocalThreads = 1024;
+
+__device__ __forceinline__ double block_sum_all(double v, double* sh) {
+    v = block_sum(v, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) sh[0] = v;
+    __syncthreads();
+    v = sh[0];
+    __syncthreads();
+    return v;
+}
+
+// Visits the cells of the boxes of radius rb around the flipped cells
+// (periodic axes wrapped, cells beyond a wall skipped); fn(cell, chebyshev
+// distance).  Every thread of the block walks its share of each box.
+template <class Fn>
+__device__ __forceinline__ void local_boxes(const Level<float>& L, const int* flips, int nf, int rb, Fn&& fn) {
+    const int nx = L.nx, ny = L.ny, nz = L.nz, side = 2 * rb + 1;
+    const int vol = side * side * side;
+    for (int f = 0; f < nf; f++) {
+        const int c0 = flips[f];
+        const int x0 = c0 % nx, y0 = (c0 / nx) % ny, z0 = c0 / (nx * ny);
+        for (int t = threadIdx.x; t < vol; t += blockDim.x) {
+            const int d3[3] = {t % side - rb, (t / side) % side - rb, t / (side * side) - rb};
+            const int o3[3] = {x0, y0, z0}, n3[3] = {nx, ny, nz};
+            int p3[3];
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                int v = o3[a] + d3[a];
+                if (v < 0 || v >= n3[a]) {
+                    if (!L.per[a]) {
+                        ok = false;
+                        break;
+                    }
+                    v = ((v % n3[a]) + n3[a]) % n3[a];
+                }
+                p3[a] = v;
+            }
+            if (!ok) continue;
+            const int dist = max(abs(d3[0]), max(abs(d3[1]), abs(d3[2])));
+            fn(p3[0] + nx * (p3[1] + ny * p3[2]), dist);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kLocalThreads) k_local_solve(Level<float> L, const uint8_t* __restrict__ st,
+                                                               uint8_t* flags, const int* __restrict__ flips,
+                                                               const int* __restrict__ nflips, int fcap,
+                                                               float* r, float* e, float* p, float* psi_hi,
+                                                               float* psi_lo, int* list, float* rl, float* ec,
+                                                               float* q, double* norm, const int* __restrict__ gate,
+                                                               int half) {
+    __shared__ int s_n[2];
+    __shared__ int s_over;
+    __shared__ double sh[32];
+    if (*gate != 0) return;
+    const int nf = *nflips;
+    if (nf <= 0 || nf > kLocalFlips || nf > fcap) return;
+    const RbMap rb{half};
+    const int nx = L.nx, ny = L.ny;
+    const float inv_h2 = 1.0f / L.h2;
+    auto col = [&](int c) { return (c % nx + (c / nx) % ny + c / (nx * ny)) & 1; };
+    auto word = [&](int c) { return reinterpret_cast<unsigned*>(flags + (c & ~3)); };
+    if (threadIdx.x == 0) {
+        s_n[0] = s_n[1] = 0;
+        s_over = 0;
+    }
+    __syncthreads();
+    // the region (distance <= kLocalR), then the ring (distance kLocalR + 1)
+    // not in the region; each unknown cell listed once (its bit)
+    for (int pass = 0; pass < 2; pass++) {
+        const unsigned mark = pass == 0 ? 0x80u : 0x40u;
+        local_boxes(L, flips, nf, kLocalR + pass, [&](int cc, int dist) {
+            if (pass == 1 && dist != kLocalR + 1) return;
+            if ((st[cc] & ST_KIND) != ST_UNKNOWN) return;
+            const int sh8 = 8 * (cc & 3);
+            const unsigned old = atomicOr(word(cc), mark << sh8);
+            if ((old >> sh8) & (pass == 0 ? 0x80u : 0xC0u)) return;  // (listed already, or in the region)
+            const int i = atomicAdd(&s_n[1], 1);
+            if (i < kLocalCap)
+                list[i] = cc;
+            else
+                s_over = 1;
+        });
+        __syncthreads();
+        if (pass == 0 && threadIdx.x == 0) s_n[0] = s_n[1];
+        __syncthreads();
+    }
+    const int ni = min(s_n[0], kLocalCap), nt = min(s_n[1], kLocalCap);
+    if (!s_over) {
+        // e = p = 0 on the listed cells (the ring keeps 0: A restricted to the region)
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int cc = list[i], cl = col(cc);
+            e[rb(cc, cl)] = 0.0f;
+            p[rb(cc, cl)] = 0.0f;
+        }
+        __syncthreads();
+        double rr = 0.0, old_sq = 0.0;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int cc = list[i];
+            const float v = r[rb(cc, col(cc))];
+            old_sq += (double)v * v;
+            if (i < ni) {
+                rl[i] = v;
+                ec[i] = 0.0f;
+                p[rb(cc, col(cc))] = v;
+                rr += (double)v * v;
+            }
+        }
+        rr = block_sum_all(rr, sh);
+        old_sq = block_sum_all(old_sq, sh);
+        const double rr0 = rr;
+        for (int it = 0; it < kLocalIters && rr > 1e-6 * rr0 && rr > 0.0; it++) {
+            double pq = 0.0;
+            for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+                const int cc = list[i];
+                const int x = cc % nx, y = (cc / nx) % ny, z = cc / (nx * ny);
+                float dg, off;
+                level_stencil<float, true, float, RbMap>(L, st, p, x, y, z, st[cc], dg, off,
+                                                         EAcc<float, float>{1.0f, 1.0f}, rb);
+                const float pv = p[rb(cc, col(cc))];
+                const float qv = (dg * pv - off) * inv_h2;
+                q[i] = qv;
+                pq += (double)pv * qv;
+            }
+            pq = block_sum_all(pq, sh);
+            if (!(pq > 0.0)) break;
+            const double alpha = rr / pq;
+            double rn = 0.0;
+            for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+                const int cc = list[i];
+                ec[i] += (float)alpha * p[rb(cc, col(cc))];
+                rl[i] -= (float)alpha * q[i];
+                rn += (double)rl[i] * rl[i];
+            }
+            rn = block_sum_all(rn, sh);  // (also: every thread is done reading p)
+            const float beta = (float)(rn / rr);
+            for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+                const int cc = list[i];
+                float* pp = p + rb(cc, col(cc));
+                *pp = rl[i] + beta * *pp;
+            }
+            __syncthreads();
+            rr = rn;
+        }
+        // psi += e on the region; e in place for the residual
+        for (int i = threadIdx.x; i < ni; i += blockDim.x) {
+            const int cc = list[i];
+            e[rb(cc, col(cc))] = ec[i];
+            const ff v = ff_add_f({psi_hi[cc], psi_lo[cc]}, ec[i]);
+            psi_hi[cc] = v.hi;
+            psi_lo[cc] = v.lo;
+        }
+        __syncthreads();
+        // r -= A e on the region and the ring (e = 0 beyond the region: a
+        // neighbour counts only if it carries the region's bit)
+        double new_sq = 0.0;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int cc = list[i];
+            const int x = cc % nx, y = (cc / nx) % ny, z = cc / (nx * ny);
+            float dg, off0;
+            level_stencil<float, false, float, RbMap>(L, st, e, x, y, z, st[cc], dg, off0,
+                                                      EAcc<float, float>{1.0f, 1.0f}, rb);
+            const int c3[3] = {x, y, z}, n3[3] = {L.nx, L.ny, L.nz}, stride[3] = {1, nx, nx * ny};
+            const int ncol = 1 - ((x + y + z) & 1);
+            float off = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int sd = -1; sd <= 1; sd += 2) {
+                    int v = c3[a] + sd;
+                    if (v < 0 || v >= n3[a]) {
+                        if (!L.per[a]) continue;
+                        v = v < 0 ? v + n3[a] : v - n3[a];
+                    }
+                    const int nb = cc + (v - c3[a]) * stride[a];
+                    if ((st[nb] & ST_KIND) != ST_UNKNOWN) continue;
+                    if ((flags[nb] & 0x80u) == 0) continue;  // (e = 0 there)
+                    off += e[rb(nb, ncol)];
+                }
+            const float ev = i < ni ? ec[i] : 0.0f;
+            float* rp = r + rb(cc, col(cc));
+            const float rv = *rp - (dg * ev - off) * inv_h2;
+            *rp = rv;
+            new_sq += (double)rv * rv;
+        }
+        new_sq = block_sum_all(new_sq, sh);
+        if (threadIdx.x == 0) {
+            const double n2 = norm[0] * norm[0] + (new_sq - old_sq);
+            norm[0] = sqrt(n2 > 0.0 ? n2 : 0.0);
+        }
+    }
+    __syncthreads();
+    // clear the bits (every box cell: also those an overflow left unlisted)
+    local_boxes(L, flips, nf, kLocalR + 1, [&](int cc, int) { atomicAnd(word(cc), ~(0xC0u << (8 * (cc & 3)))); });
+}
+
 }  // namespace
 
 // Grid of a marching residual pass over a level of nz planes with (gx, gy)
@@ -3330,6 +3548,14 @@ cudaError_t launch_outer_residual(es_ctx* c, bool patch) {
         }
         k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
         count(c, 3);
+        if (patch && c->local_list) {
+            // the local correction around the flipped cells (k_local_solve)
+            k_local_solve<<<1, kLocalThreads, 0, c->stream>>>(
+                level_desc<float>(c, 0), c->st[0], c->flags, c->flip_list, c->flip_count, c->flip_cap, r,
+                (float*)c->e[0], (float*)c->e2[0], c->psi32, c->psi_lo, c->local_list, c->local_f,
+                c->local_f + kLocalCap, c->local_f + 2 * kLocalCap, c->d_norm, c->d_moved, (int)(c->g.N / 2));
+            count(c);
+        }
         // (the mapping raises the flag again when a sphere moves far, and
         // lists the cells that flip from here on)
         cudaError_t err = cudaMemsetAsync(c->d_moved, 0, sizeof(int), c->stream);

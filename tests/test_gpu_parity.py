@@ -203,12 +203,15 @@ def test_bench_solver_paths_mixed32_after_100_steps(name):
 
 
 @pytest.mark.parametrize("name", sorted(LIST_CASES))
-def test_patched_residual_equals_the_full_one(name):
-    """A solve that starts from the previous solve's residual, formed again
+def test_patched_start_and_local_correction(name):
+    """A solve that starts from the previous solve's residual -- formed again
     only at the near-boundary cells and around the cells that flipped
-    between obstacle and fluid, starts from the norm the full float-float
-    residual gives (to the FP32 updates the carried residual holds); the
-    full one is forced on a twin run by writing its psi back unchanged."""
+    between obstacle and fluid, then lowered by the local correction around
+    those cells -- ends at the potential a full start gives (twin run, the
+    full start forced by writing psi back unchanged), starts no higher, and
+    leaves a carried residual that is the residual of its potential: a
+    second solve on the same potential starts from the carried norm, a
+    third with the residual formed in full from the same norm."""
     wl = LIST_CASES[name]()
     a = es.Simulation(wl, es.ES_MIXED32, overrides=BENCH_PATHS)
     b = es.Simulation(wl, es.ES_MIXED32, overrides=BENCH_PATHS)
@@ -224,9 +227,18 @@ def test_patched_residual_equals_the_full_one(name):
         out.append(sim.solve())
         out.append({(r["name"], r["level"]) for r in sim.profile_stop()})
     assert ("residual_patch", -1) in ra[1] and ("outer_residual", -1) in rb[1]
-    print("start residual: patched", ra[0]["r0"], "full", rb[0]["r0"], "tol", ra[0]["tol"])
-    assert ra[0]["r0"] == pytest.approx(rb[0]["r0"], rel=1e-5)
-    assert ra[0]["cycles"] == rb[0]["cycles"]
+    print("start residual: patched and corrected", ra[0]["r0"], "full", rb[0]["r0"], "tol", ra[0]["tol"],
+          "cycles", ra[0]["cycles"], rb[0]["cycles"])
+    assert ra[0]["r0"] <= rb[0]["r0"] * (1 + 1e-3)
+    assert ra[0]["cycles"] <= rb[0]["cycles"]
+    pa, pb = a.field(es.FIELD_PSI), b.field(es.FIELD_PSI)
+    assert rel_l2(pa, pb) < 1e-5
+    again = a.solve()  # nothing changed: the carried residual of the final psi
+    a.set_field(es.FIELD_PSI, a.field(es.FIELD_PSI))
+    full = a.solve()  # the same psi, residual formed in full
+    print("carried", again["r0"], "full", full["r0"], "final", ra[0]["r"])
+    assert again["r0"] == pytest.approx(ra[0]["r"], rel=1e-3)
+    assert full["r0"] == pytest.approx(again["r0"], rel=0.05)
     a.close()
     b.close()
 
