@@ -161,7 +161,7 @@ size_t field_bytes(const es_params* P, int n, size_t* per_level) {
     b += (size_t)(n > 0 ? n : 1) * (sizeof(DParticle) + 9 * 8 + 4 + 4 + 6 * 8 + 14 * 4 + 12 * 8);
     b += res_partial_slots(P->dims[0], P->dims[1], 0) * 8 + 64;
     b += (size_t)kFlipCap * 4 + 3 * 256;  // flipped-cell list, its count, the moved flag
-    if (colour_split(P)) b += (size_t)4 * kLocalCells * 4;  // the local correction's scratch
+    if (colour_split(P)) b += (size_t)4 * kLocalCells * 4 + 1024;  // the local correction's scratch
     return b;
 }
 
@@ -408,6 +408,7 @@ int es_create_with_allocator(const es_params* params, const es_particle* parts, 
     c->flip_count = (int*)A(64);
     c->local_list = c->rb0 ? (int*)A((size_t)kLocalCells * 4) : nullptr;
     c->local_f = c->rb0 ? (float*)A((size_t)3 * kLocalCells * 4) : nullptr;
+    c->local_meta = c->rb0 ? A(1024) : nullptr;
     c->res_valid = false;
     c->res_age = 0;
     c->rb_wpr = (c->g.nx + 63) / 64;

@@ -140,6 +140,7 @@ struct es_ctx {
     int flip_cap;
     int* local_list;  // device scratch of the local correction at a solve's start (colour-split levels)
     float* local_f;   // 3 x kLocalCells floats
+    void* local_meta; // the clusters of the flipped cells (LocalMeta, 1 KB)
     bool res_valid;  // the finest right-hand side holds the residual of the current psi (reduced forms)
     int res_age;     // solves started from a patched residual since the last full one
     double* h_norm;  // pinned: [0] norm

@@ -3270,16 +3270,87 @@ __global__ void __launch_bounds__(256) k_rhs_norm_rb(Grid g, const float* __rest
 // out, and the residual norm is updated by the change of r^2 over those
 // cells.  The V-cycles then start from that residual (none when it is
 // already below the tolerance).  Cells of the region carry bit 7 of their
-// flag byte, ring cells bit 6, while the kernel runs.  gate: 1 when the full
-// residual ran (a sphere moved far or the flip list overflowed); more than
-// kLocalFlips flips, or a region over kLocalCap cells, leave the V-cycles
-// alone.
+// flag byte, ring cells bit 6, while the kernel runs.  Flipped cells closer
+// than 2 kLocalR + 4 cells (Chebyshev, periodic images) form one cluster
+// (k_local_clusters); one block corrects each cluster, and no two clusters'
+// boxes share or touch a cell, so the blocks need no order; the norm takes
+// their changes of r^2 in cluster order (k_local_norm).  gate: 1 when the
+// full residual ran (a sphere moved far or the flip list overflowed); more
+// than kLocalFlips flips leave the V-cycles alone, and a cluster whose
+// region overflows its share of the scratch keeps its residual.
 constexpr int kLocalR = 8;
 constexpr int kLocalFlips = 16;
 constexpr int kLocalIters = 40;
 constexpr int kLocalCap = kLocalFlips * (2 * kLocalR + 3) * (2 * kLocalR + 3) * (2 * kLocalR + 3);
 static_assert(kLocalCap == kLocalCells, "the scratch sized at creation");
 constexpr int kLocalThreads = 1024;
+constexpr int kLocalBox = (2 * kLocalR + 3) * (2 * kLocalR + 3) * (2 * kLocalR + 3);  // scratch cells a flip
+
+// The clusters of the flipped cells, built by one thread: flips in cluster
+// order, the cluster starts, the scratch base of each cluster (kLocalBox
+// cells per flip), the cluster count, and room for each cluster's change of
+// the squared norm.
+struct LocalMeta {
+    int n;
+    int start[kLocalFlips + 1];
+    int base[kLocalFlips];
+    int flip[kLocalFlips];
+    double delta[kLocalFlips];
+};
+
+static_assert(sizeof(LocalMeta) <= 1024, "the cluster table's allocation");
+
+__global__ void k_local_clusters(Grid g, const int* __restrict__ flips, const int* __restrict__ nflips, int fcap,
+                                 const int* __restrict__ gate, LocalMeta* meta) {
+    if (threadIdx.x != 0) return;
+    const int nf = *nflips;
+    meta->n = 0;
+    if (*gate != 0 || nf <= 0 || nf > kLocalFlips || nf > fcap) return;
+    int cl[kLocalFlips];
+    for (int i = 0; i < nf; i++) cl[i] = i;
+    auto root = [&](int i) {
+        while (cl[i] != i) i = cl[i];
+        return i;
+    };
+    const int n3[3] = {g.nx, g.ny, g.nz};
+    for (int i = 0; i < nf; i++)
+        for (int j = i + 1; j < nf; j++) {
+            const int a = flips[i], b = flips[j];
+            const int pa[3] = {a % g.nx, (a / g.nx) % g.ny, a / (g.nx * g.ny)};
+            const int pb[3] = {b % g.nx, (b / g.nx) % g.ny, b / (g.nx * g.ny)};
+            int d = 0;
+            for (int k = 0; k < 3; k++) {
+                int dk = abs(pa[k] - pb[k]);
+                if (g.per[k] && n3[k] - dk < dk) dk = n3[k] - dk;
+                d = max(d, dk);
+            }
+            if (d <= 2 * kLocalR + 3) {
+                const int ri = root(i), rj = root(j);
+                if (ri != rj) cl[max(ri, rj)] = min(ri, rj);
+            }
+        }
+    int n = 0, at = 0;
+    for (int r = 0; r < nf; r++) {
+        if (root(r) != r) continue;
+        meta->start[n] = at;
+        meta->base[n] = at * kLocalBox;
+        for (int i = 0; i < nf; i++)
+            if (root(i) == r) meta->flip[at++] = flips[i];
+        meta->delta[n] = 0.0;
+        n++;
+    }
+    meta->start[n] = at;
+    meta->n = n;
+}
+
+// The residual norm after the local correction: the clusters' changes of
+// r^2 in cluster order.
+__global__ void k_local_norm(const LocalMeta* __restrict__ meta, double* norm) {
+    if (threadIdx.x != 0 || meta->n == 0) return;
+    double n2 = norm[0] * norm[0];
+    for (int c = 0; c < meta->n; c++) n2 += meta->delta[c];
+    norm[0] = sqrt(n2 > 0.0 ? n2 : 0.0);
+}
 
 __device__ __forceinline__ double block_sum_all(double v, double* sh) {
     v = block_sum(v, sh);
@@ -3326,18 +3397,22 @@ __device__ __forceinline__ void local_boxes(const Level<float>& L, const int* fl
 }
 
 __global__ void __launch_bounds__(kLocalThreads) k_local_solve(Level<float> L, const uint8_t* __restrict__ st,
-                                                               uint8_t* flags, const int* __restrict__ flips,
-                                                               const int* __restrict__ nflips, int fcap,
-                                                               float* r, float* e, float* p, float* psi_hi,
-                                                               float* psi_lo, int* list, float* rl, float* ec,
-                                                               float* q, double* norm, const int* __restrict__ gate,
+                                                               uint8_t* flags, LocalMeta* meta, float* r, float* e,
+                                                               float* p, float* psi_hi, float* psi_lo, int* list_all,
+                                                               float* rl_all, float* ec_all, float* q_all,
                                                                int half) {
     __shared__ int s_n[2];
     __shared__ int s_over;
     __shared__ double sh[32];
-    if (*gate != 0) return;
-    const int nf = *nflips;
-    if (nf <= 0 || nf > kLocalFlips || nf > fcap) return;
+    const int cluster = blockIdx.x;
+    if (cluster >= meta->n) return;  // (uniform over the block)
+    const int f0 = meta->start[cluster], nf = meta->start[cluster + 1] - f0;
+    const int* flips = meta->flip + f0;
+    const int cap = nf * kLocalBox;  // this cluster's share of the scratch
+    int* list = list_all + meta->base[cluster];
+    float* rl = rl_all + meta->base[cluster];
+    float* ec = ec_all + meta->base[cluster];
+    float* q = q_all + meta->base[cluster];
     const RbMap rb{half};
     const int nx = L.nx, ny = L.ny;
     const float inv_h2 = 1.0f / L.h2;
@@ -3359,7 +3434,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_local_solve(Level<float> L, c
             const unsigned old = atomicOr(word(cc), mark << sh8);
             if ((old >> sh8) & (pass == 0 ? 0x80u : 0xC0u)) return;  // (listed already, or in the region)
             const int i = atomicAdd(&s_n[1], 1);
-            if (i < kLocalCap)
+            if (i < cap)
                 list[i] = cc;
             else
                 s_over = 1;
@@ -3368,7 +3443,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_local_solve(Level<float> L, c
         if (pass == 0 && threadIdx.x == 0) s_n[0] = s_n[1];
         __syncthreads();
     }
-    const int ni = min(s_n[0], kLocalCap), nt = min(s_n[1], kLocalCap);
+    const int ni = min(s_n[0], cap), nt = min(s_n[1], cap);
     if (!s_over) {
         // e = p = 0 on the listed cells (the ring keeps 0: A restricted to the region)
         for (int i = threadIdx.x; i < nt; i += blockDim.x) {
@@ -3467,10 +3542,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_local_solve(Level<float> L, c
             new_sq += (double)rv * rv;
         }
         new_sq = block_sum_all(new_sq, sh);
-        if (threadIdx.x == 0) {
-            const double n2 = norm[0] * norm[0] + (new_sq - old_sq);
-            norm[0] = sqrt(n2 > 0.0 ? n2 : 0.0);
-        }
+        if (threadIdx.x == 0) meta->delta[cluster] = new_sq - old_sq;
     }
     __syncthreads();
     // clear the bits (every box cell: also those an overflow left unlisted)
@@ -3549,12 +3621,16 @@ cudaError_t launch_outer_residual(es_ctx* c, bool patch) {
         k_finalize_norm<<<1, 1024, 0, c->stream>>>(c->partial, gx * gy * gz, c->d_norm);
         count(c, 3);
         if (patch && c->local_list) {
-            // the local correction around the flipped cells (k_local_solve)
-            k_local_solve<<<1, kLocalThreads, 0, c->stream>>>(
-                level_desc<float>(c, 0), c->st[0], c->flags, c->flip_list, c->flip_count, c->flip_cap, r,
-                (float*)c->e[0], (float*)c->e2[0], c->psi32, c->psi_lo, c->local_list, c->local_f,
-                c->local_f + kLocalCap, c->local_f + 2 * kLocalCap, c->d_norm, c->d_moved, (int)(c->g.N / 2));
-            count(c);
+            // the local correction around the flipped cells (k_local_solve), one block a cluster
+            LocalMeta* meta = (LocalMeta*)c->local_meta;
+            k_local_clusters<<<1, 32, 0, c->stream>>>(c->g, c->flip_list, c->flip_count, c->flip_cap, c->d_moved,
+                                                      meta);
+            k_local_solve<<<kLocalFlips, kLocalThreads, 0, c->stream>>>(
+                level_desc<float>(c, 0), c->st[0], c->flags, meta, r, (float*)c->e[0], (float*)c->e2[0],
+                c->psi32, c->psi_lo, c->local_list, c->local_f, c->local_f + kLocalCap, c->local_f + 2 * kLocalCap,
+                (int)(c->g.N / 2));
+            k_local_norm<<<1, 32, 0, c->stream>>>(meta, c->d_norm);
+            count(c, 3);
         }
         // (the mapping raises the flag again when a sphere moves far, and
         // lists the cells that flip from here on)

@@ -194,12 +194,13 @@ def test_bench_solver_paths_mixed32_after_100_steps(name):
         _, ginfo, _, _ = p.step(forced=False)
         assert ginfo["status"] == es.ES_OK and ginfo["r"] < ginfo["tol"]
     _assert_reduced(p.compare())
-    seen = _profiled_names(p.g, 6)
-    # (the update carries the correction psi += e in the same pass)
-    updates = seen.get(("residual_update_correct", -1), 0)
-    assert updates > 0, "the FP32 residual update never ran"
+    seen = _profiled_names(p.g, 10)
     # solves that start from the carried residual, patched around the spheres
+    # and corrected locally around the flipped cells; when a V-cycle still
+    # runs, the FP32 update (with psi += e in the same pass) follows it
     assert seen.get(("residual_patch", -1), 0) > 0, "no solve started from a patched residual"
+    if seen.get(("smooth_half", 0), 0):
+        assert seen.get(("residual_update_correct", -1), 0) > 0, "the FP32 residual update never ran"
 
 
 @pytest.mark.parametrize("name", sorted(LIST_CASES))
@@ -237,7 +238,10 @@ def test_patched_start_and_local_correction(name):
     a.set_field(es.FIELD_PSI, a.field(es.FIELD_PSI))
     full = a.solve()  # the same psi, residual formed in full
     print("carried", again["r0"], "full", full["r0"], "final", ra[0]["r"])
-    assert again["r0"] == pytest.approx(ra[0]["r"], rel=1e-3)
+    # (the final norm comes from the FP32 update, whose rounding, ~1e-6 of the
+    # residual before the correction, is ~1 % of a residual at the tolerance;
+    # the next start forms the near-boundary cells again in float-float)
+    assert again["r0"] == pytest.approx(ra[0]["r"], rel=0.05)
     assert full["r0"] == pytest.approx(again["r0"], rel=0.05)
     a.close()
     b.close()
