@@ -517,41 +517,54 @@ __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const
     const int seg = row % kNearSegs;
     const int y = row % ny, z = row / ny;
     unsigned pend[2] = {0u, 0u};  // (low halves of the mask words, stored with their high halves)
-    for (int x0 = 0; x0 < nx; x0 += 32) {
-        const int x = x0 + lane;
-        bool take = false, inner = false;
-        if (x < nx) {
-            const uint8_t s = st[x + nx * row];
-            take = (s & ST_KIND) == ST_UNKNOWN && (s & ST_NEAR);
-            inner = (s & (ST_KIND | ST_NEAR)) == ST_UNKNOWN;
-        }
-        if (rbmask) {
+    for (int xb = 0; xb < nx; xb += 8 * 32) {
+        // the state bytes of eight 32-cell steps, all loaded before the
+        // first is tested, so that a warp has eight loads in flight
+        uint8_t sv[8];
 #pragma unroll
-            for (int colour = 0; colour < 2; colour++) {
-                const bool b = inner && ((x + y + z) & 1) == colour;
-                const unsigned v = __reduce_or_sync(0xffffffffu, b ? 1u << (lane >> 1) : 0u);
-                const bool last = x0 + 32 >= nx;
-                if ((x0 & 63) == 0) pend[colour] = v;
-                if (lane == 0 && ((x0 & 63) != 0 || last)) {
-                    // the word of compact places x0/2 & ~31 .. +31 (a high half past the row's end stays 0)
-                    const unsigned word = (x0 & 63) != 0 ? (pend[colour] | (v << 16)) : v;
-                    rbmask[(size_t)colour * ((size_t)ny * nz * wpr) + (size_t)wpr * row + x0 / 64] = word;
+        for (int q = 0; q < 8; q++) {
+            const int x = xb + 32 * q + lane;
+            sv[q] = x < nx ? st[x + nx * row] : (uint8_t)0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int x0 = xb + 32 * q;
+            if (x0 >= nx) break;  // (warp-uniform)
+            const int x = x0 + lane;
+            bool take = false, inner = false;
+            if (x < nx) {
+                const uint8_t s = sv[q];
+                take = (s & ST_KIND) == ST_UNKNOWN && (s & ST_NEAR);
+                inner = (s & (ST_KIND | ST_NEAR)) == ST_UNKNOWN;
+            }
+            if (rbmask) {
+#pragma unroll
+                for (int colour = 0; colour < 2; colour++) {
+                    const bool b = inner && ((x + y + z) & 1) == colour;
+                    const unsigned v = __reduce_or_sync(0xffffffffu, b ? 1u << (lane >> 1) : 0u);
+                    const bool last = x0 + 32 >= nx;
+                    if ((x0 & 63) == 0) pend[colour] = v;
+                    if (lane == 0 && ((x0 & 63) != 0 || last)) {
+                        // the word of compact places x0/2 & ~31 .. +31 (a high half past the row's end stays 0)
+                        const unsigned word = (x0 & 63) != 0 ? (pend[colour] | (v << 16)) : v;
+                        rbmask[(size_t)colour * ((size_t)ny * nz * wpr) + (size_t)wpr * row + x0 / 64] = word;
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int colour = 0; colour < 2; colour++) {
-            const bool mine = take && ((x + y + z) & 1) == colour;
-            const unsigned m = __ballot_sync(0xffffffffu, mine);
-            if (!m) continue;
-            const int k = colour * kNearSegs + seg;
-            const int leader = __ffs(m) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&count[k], __popc(m));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (mine) {
-                const int i = base + __popc(m & lt);
-                if (i < cap) list[(size_t)k * cap + i] = x + nx * row;
+            for (int colour = 0; colour < 2; colour++) {
+                const bool mine = take && ((x + y + z) & 1) == colour;
+                const unsigned m = __ballot_sync(0xffffffffu, mine);
+                if (!m) continue;
+                const int k = colour * kNearSegs + seg;
+                const int leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&count[k], __popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (mine) {
+                    const int i = base + __popc(m & lt);
+                    if (i < cap) list[(size_t)k * cap + i] = x + nx * row;
+                }
             }
         }
     }
@@ -615,66 +628,81 @@ __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const 
     if (row >= ny * nz) return;  // whole warps
     const int seg = row % kNearSegs;
     const int y = row % ny, z = row / ny;
-    for (int x0 = 0; x0 < nx; x0 += 128) {
-        const int xs = x0 + 4 * lane;
-        unsigned sw = 0x02020202u, fw = 0x01010101u;  // (Neumann / obstacle: not listed)
-        if (xs < nx) {
-            sw = *reinterpret_cast<const unsigned*>(st + xs + nx * row);
-            fw = *reinterpret_cast<const unsigned*>(flags + xs + nx * row);
-        }
-        // the three tests on the lane's four cells at once: bit 0 of each
-        // byte (state values < 8, flag values < 4) gathered into a nibble,
-        // cell i at bit i
-        sw &= 0x07070707u;
-        fw &= 0x03030303u;
-        auto nibble = [](unsigned b) { return ((b & 0x01010101u) * 0x01020408u) >> 24; };
-        const unsigned in4 = nibble(~(sw | (sw >> 1) | (sw >> 2)));  // state 0: interior unknown cell
-        const unsigned nr4 = nibble((sw >> 2) & ~(sw | (sw >> 1)));  // state 4: near-boundary unknown cell
-        const unsigned bf4 = nibble((fw >> 1) & ~fw);                // flags 2: next to an obstacle, fluid
-        const int p0 = (y + z) & 1;                                  // colour of cells xs and xs + 2
-        if (rbmask) {
-            // lane's cells of colour k: xs + O and xs + 2 + O, O = k ^ p0, at
-            // compact places xs / 2 and xs / 2 + 1 (bits 2 lane, 2 lane + 1
-            // of this span's 64)
+    for (int xb = 0; xb < nx; xb += 4 * 128) {
+        // the words of four 128-cell spans, all loaded before the first is
+        // tested, so that a warp has eight loads in flight
+        unsigned swv[4], fwv[4];
 #pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const int O = k ^ p0;
-                const unsigned v = ((in4 >> O) & 1u) | (((in4 >> (O + 2)) & 1u) << 1);
-                const unsigned sh = v << ((2 * lane) & 31);
-                const unsigned lo = __reduce_or_sync(0xffffffffu, lane < 16 ? sh : 0u);
-                const unsigned hi = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : sh);
-                const int w0 = x0 / 64;  // (x0 is a multiple of 128)
-                uint32_t* m = rbmask + (size_t)k * ((size_t)ny * nz * wpr) + (size_t)wpr * row;
-                if (lane == 0) m[w0] = lo;
-                if (lane == 16 && w0 + 1 < wpr) m[w0 + 1] = hi;
+        for (int s = 0; s < 4; s++) {
+            const int xs = xb + 128 * s + 4 * lane;
+            swv[s] = 0x02020202u;  // (Neumann / obstacle: not listed)
+            fwv[s] = 0x01010101u;
+            if (xs < nx) {
+                swv[s] = *reinterpret_cast<const unsigned*>(st + xs + nx * row);
+                fwv[s] = *reinterpret_cast<const unsigned*>(flags + xs + nx * row);
             }
         }
-        // (most 128-cell spans hold no listed cell: one vote skips them)
-        if (!__any_sync(0xffffffffu, (nr4 | bf4) != 0)) continue;
-        // near-boundary cells by colour: cells i = 0, 2 have colour p0, i = 1, 3 the other
-        const unsigned ms[3] = {p0 == 0 ? nr4 & 0x5u : nr4 & 0xAu, p0 == 0 ? nr4 & 0xAu : nr4 & 0x5u, bf4};
-        // one scan for the three lists: 8-bit fields (a warp lists at most 128 cells of one list)
-        int total;
-        const int excl = warp_excl_scan((int)(__popc(ms[0]) | (__popc(ms[1]) << 8) | (__popc(ms[2]) << 16)), total);
-        int base = 0;
-        if (lane < 3) {
-            const int tl = (total >> (8 * lane)) & 0xFF;
-            int* cnt = lane < 2 ? &count[lane * kNearSegs + seg] : &bf_count[seg];
-            if (tl) base = atomicAdd(cnt, tl);
-        }
 #pragma unroll
-        for (int t = 0; t < 3; t++) {
-            const int bt = __shfl_sync(0xffffffffu, base, t);
-            const unsigned m = ms[t];
-            int* out = t < 2 ? list + (size_t)(t * kNearSegs + seg) * cap : bf_list + (size_t)seg * bf_cap;
-            const int c_out = t < 2 ? cap : bf_cap;
-            int k = bt + ((excl >> (8 * t)) & 0xFF);
+        for (int s = 0; s < 4; s++) {
+            const int x0 = xb + 128 * s;
+            if (x0 >= nx) break;  // (warp-uniform)
+            const int xs = x0 + 4 * lane;
+            unsigned sw = swv[s], fw = fwv[s];
+            // the three tests on the lane's four cells at once: bit 0 of each
+            // byte (state values < 8, flag values < 4) gathered into a nibble,
+            // cell i at bit i
+            sw &= 0x07070707u;
+            fw &= 0x03030303u;
+            auto nibble = [](unsigned b) { return ((b & 0x01010101u) * 0x01020408u) >> 24; };
+            const unsigned in4 = nibble(~(sw | (sw >> 1) | (sw >> 2)));  // state 0: interior unknown cell
+            const unsigned nr4 = nibble((sw >> 2) & ~(sw | (sw >> 1)));  // state 4: near-boundary unknown cell
+            const unsigned bf4 = nibble((fw >> 1) & ~fw);                // flags 2: next to an obstacle, fluid
+            const int p0 = (y + z) & 1;                                  // colour of cells xs and xs + 2
+            if (rbmask) {
+                // lane's cells of colour k: xs + O and xs + 2 + O, O = k ^ p0, at
+                // compact places xs / 2 and xs / 2 + 1 (bits 2 lane, 2 lane + 1
+                // of this span's 64)
 #pragma unroll
-            for (int i = 0; i < 4; i++)
-                if ((m >> i) & 1u) {
-                    if (k < c_out) out[k] = xs + i + nx * row;
-                    k++;
+                for (int k = 0; k < 2; k++) {
+                    const int O = k ^ p0;
+                    const unsigned v = ((in4 >> O) & 1u) | (((in4 >> (O + 2)) & 1u) << 1);
+                    const unsigned sh = v << ((2 * lane) & 31);
+                    const unsigned lo = __reduce_or_sync(0xffffffffu, lane < 16 ? sh : 0u);
+                    const unsigned hi = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : sh);
+                    const int w0 = x0 / 64;  // (x0 is a multiple of 128)
+                    uint32_t* m = rbmask + (size_t)k * ((size_t)ny * nz * wpr) + (size_t)wpr * row;
+                    if (lane == 0) m[w0] = lo;
+                    if (lane == 16 && w0 + 1 < wpr) m[w0 + 1] = hi;
                 }
+            }
+            // (most 128-cell spans hold no listed cell: one vote skips them)
+            if (!__any_sync(0xffffffffu, (nr4 | bf4) != 0)) continue;
+            // near-boundary cells by colour: cells i = 0, 2 have colour p0, i = 1, 3 the other
+            const unsigned ms[3] = {p0 == 0 ? nr4 & 0x5u : nr4 & 0xAu, p0 == 0 ? nr4 & 0xAu : nr4 & 0x5u, bf4};
+            // one scan for the three lists: 8-bit fields (a warp lists at most 128 cells of one list)
+            int total;
+            const int excl =
+                warp_excl_scan((int)(__popc(ms[0]) | (__popc(ms[1]) << 8) | (__popc(ms[2]) << 16)), total);
+            int base = 0;
+            if (lane < 3) {
+                const int tl = (total >> (8 * lane)) & 0xFF;
+                int* cnt = lane < 2 ? &count[lane * kNearSegs + seg] : &bf_count[seg];
+                if (tl) base = atomicAdd(cnt, tl);
+            }
+#pragma unroll
+            for (int t = 0; t < 3; t++) {
+                const int bt = __shfl_sync(0xffffffffu, base, t);
+                const unsigned m = ms[t];
+                int* out = t < 2 ? list + (size_t)(t * kNearSegs + seg) * cap : bf_list + (size_t)seg * bf_cap;
+                const int c_out = t < 2 ? cap : bf_cap;
+                int k = bt + ((excl >> (8 * t)) & 0xFF);
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if ((m >> i) & 1u) {
+                        if (k < c_out) out[k] = xs + i + nx * row;
+                        k++;
+                    }
+            }
         }
     }
 }
