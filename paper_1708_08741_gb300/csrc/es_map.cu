@@ -498,24 +498,39 @@ __global__ void k_near_bits(int nx, int ny, int nz, int px, int py, int pz, uint
     st[c] = near ? (uint8_t)(ST_UNKNOWN | ST_NEAR) : (uint8_t)ST_UNKNOWN;
 }
 
+// Exclusive prefix sum of v over the warp; total = the sum of all lanes.
+__device__ __forceinline__ int warp_excl_scan(int v, int& total) {
+    const int lane = threadIdx.x & 31;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - v;
+}
+
 // Lists the near-boundary unknown cells of a level, by colour, for the
 // separate near-cell passes of the smoother, residual and restriction.  A
-// row (y, z) goes to segment row mod kNearSegs of each colour; a warp walks its row 32 cells at a time with
-// one atomic per step on the segment's counter.  The order within a
-// segment depends on the atomics' order; the consumers write each cell's
-// value to its own place, so results do not.  With rbmask (a colour-split
-// level, nx even), also its per-colour update masks as k_lists_l0 builds
-// them: a 32-cell step holds 16 cells of each colour, compact places
-// x0 / 2 .. x0 / 2 + 15, which fill the low or the high half of one word.
+// row (y, z) goes to segment row mod kNearSegs of each colour; a warp walks
+// its row 256 cells at a time, lane l taking cells l, l + 32, ..., which
+// all have one colour, with one prefix sum and one atomic per colour on the
+// segment's counters.  The order within a segment depends on the atomics'
+// order; the consumers write each cell's value to its own place, so results
+// do not.  With rbmask (a colour-split level, nx even), also its per-colour
+// update masks as k_lists_l0 builds them: a 32-cell step holds 16 cells of
+// each colour, compact places x0 / 2 .. x0 / 2 + 15, which fill the low or
+// the high half of one word.
 __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const uint8_t* __restrict__ st,
                                                    int cap, int* list, int* count, uint32_t* __restrict__ rbmask,
                                                    int wpr) {
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= ny * nz) return;  // whole warps
     const int seg = row % kNearSegs;
     const int y = row % ny, z = row / ny;
+    const int colour = (lane + y + z) & 1;  // of the lane's cells (steps of 32 keep it)
     unsigned pend[2] = {0u, 0u};  // (low halves of the mask words, stored with their high halves)
     for (int xb = 0; xb < nx; xb += 8 * 32) {
         // the state bytes of eight 32-cell steps, all loaded before the
@@ -526,6 +541,7 @@ __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const
             const int x = xb + 32 * q + lane;
             sv[q] = x < nx ? st[x + nx * row] : (uint8_t)0;
         }
+        unsigned tk = 0;  // bit q: cell xb + 32 q + lane is listed
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const int x0 = xb + 32 * q;
@@ -537,35 +553,39 @@ __global__ void __launch_bounds__(256) k_near_list(int nx, int ny, int nz, const
                 take = (s & ST_KIND) == ST_UNKNOWN && (s & ST_NEAR);
                 inner = (s & (ST_KIND | ST_NEAR)) == ST_UNKNOWN;
             }
+            tk |= (take ? 1u : 0u) << q;
             if (rbmask) {
 #pragma unroll
-                for (int colour = 0; colour < 2; colour++) {
-                    const bool b = inner && ((x + y + z) & 1) == colour;
+                for (int k = 0; k < 2; k++) {
+                    const bool b = inner && colour == k;
                     const unsigned v = __reduce_or_sync(0xffffffffu, b ? 1u << (lane >> 1) : 0u);
                     const bool last = x0 + 32 >= nx;
-                    if ((x0 & 63) == 0) pend[colour] = v;
+                    if ((x0 & 63) == 0) pend[k] = v;
                     if (lane == 0 && ((x0 & 63) != 0 || last)) {
                         // the word of compact places x0/2 & ~31 .. +31 (a high half past the row's end stays 0)
-                        const unsigned word = (x0 & 63) != 0 ? (pend[colour] | (v << 16)) : v;
-                        rbmask[(size_t)colour * ((size_t)ny * nz * wpr) + (size_t)wpr * row + x0 / 64] = word;
+                        const unsigned word = (x0 & 63) != 0 ? (pend[k] | (v << 16)) : v;
+                        rbmask[(size_t)k * ((size_t)ny * nz * wpr) + (size_t)wpr * row + x0 / 64] = word;
                     }
                 }
             }
-#pragma unroll
-            for (int colour = 0; colour < 2; colour++) {
-                const bool mine = take && ((x + y + z) & 1) == colour;
-                const unsigned m = __ballot_sync(0xffffffffu, mine);
-                if (!m) continue;
-                const int k = colour * kNearSegs + seg;
-                const int leader = __ffs(m) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&count[k], __popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (mine) {
-                    const int i = base + __popc(m & lt);
-                    if (i < cap) list[(size_t)k * cap + i] = x + nx * row;
-                }
-            }
+        }
+        if (!__any_sync(0xffffffffu, tk != 0)) continue;
+        // one scan for both colours, in 10-bit fields (at most 128 cells of
+        // a colour in 256)
+        int total;
+        const int excl = warp_excl_scan(__popc(tk) << (10 * colour), total);
+        int base = 0;
+        if (lane < 2) {
+            const int tl = (total >> (10 * lane)) & 0x3FF;
+            if (tl) base = atomicAdd(&count[lane * kNearSegs + seg], tl);
+        }
+        const int b0 = __shfl_sync(0xffffffffu, base, 0), b1 = __shfl_sync(0xffffffffu, base, 1);
+        int k = (colour ? b1 : b0) + ((excl >> (10 * colour)) & 0x3FF);
+        int* out = list + (size_t)(colour * kNearSegs + seg) * cap;
+        for (unsigned m = tk; m; m &= m - 1u) {
+            const int q = __ffs(m) - 1;
+            if (k < cap) out[k] = xb + 32 * q + lane + nx * row;
+            k++;
         }
     }
 }
@@ -602,20 +622,9 @@ __global__ void __launch_bounds__(256) k_near19_list(int nx, int ny, int nz, con
 
 // Level 0 in one pass: both lists (near-boundary unknown cells by colour,
 // and fluid cells next to obstacles) from 4 cells per lane (x extent a
-// multiple of 4), with warp prefix sums so that each warp step costs one
-// atomic per list.
-__device__ __forceinline__ int warp_excl_scan(int v, int& total) {
-    const int lane = threadIdx.x & 31;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    total = __shfl_sync(0xffffffffu, incl, 31);
-    return incl - v;
-}
-
+// multiple of 4), a warp per row, 512 cells at a time.  The counts of the
+// chunk's four 128-cell spans go through one warp prefix sum and one atomic
+// per list, so that a warp waits for one atomic round trip per chunk.
 // With rbmask (the colour-split finest level), also the per-colour update
 // masks of the half sweeps: bit j of colour k's row (wpr words, compact
 // index j = x / 2) is set iff that cell is an interior unknown cell.
@@ -628,6 +637,8 @@ __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const 
     if (row >= ny * nz) return;  // whole warps
     const int seg = row % kNearSegs;
     const int y = row % ny, z = row / ny;
+    const int p0 = (y + z) & 1;  // colour of the cells x with x % 4 = 0 or 2
+    auto nibble = [](unsigned b) { return ((b & 0x01010101u) * 0x01020408u) >> 24; };
     for (int xb = 0; xb < nx; xb += 4 * 128) {
         // the words of four 128-cell spans, all loaded before the first is
         // tested, so that a warp has eight loads in flight
@@ -642,26 +653,25 @@ __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const 
                 fwv[s] = *reinterpret_cast<const unsigned*>(flags + xs + nx * row);
             }
         }
+        // the lane's listed cells: bit 4 s + i of ms[t] is cell
+        // xb + 128 s + 4 lane + i of list t (near cells of colour p0, of the
+        // other colour, fluid cells next to obstacles)
+        unsigned ms[3] = {0u, 0u, 0u};
 #pragma unroll
         for (int s = 0; s < 4; s++) {
             const int x0 = xb + 128 * s;
             if (x0 >= nx) break;  // (warp-uniform)
-            const int xs = x0 + 4 * lane;
-            unsigned sw = swv[s], fw = fwv[s];
             // the three tests on the lane's four cells at once: bit 0 of each
             // byte (state values < 8, flag values < 4) gathered into a nibble,
             // cell i at bit i
-            sw &= 0x07070707u;
-            fw &= 0x03030303u;
-            auto nibble = [](unsigned b) { return ((b & 0x01010101u) * 0x01020408u) >> 24; };
+            const unsigned sw = swv[s] & 0x07070707u, fw = fwv[s] & 0x03030303u;
             const unsigned in4 = nibble(~(sw | (sw >> 1) | (sw >> 2)));  // state 0: interior unknown cell
             const unsigned nr4 = nibble((sw >> 2) & ~(sw | (sw >> 1)));  // state 4: near-boundary unknown cell
             const unsigned bf4 = nibble((fw >> 1) & ~fw);                // flags 2: next to an obstacle, fluid
-            const int p0 = (y + z) & 1;                                  // colour of cells xs and xs + 2
             if (rbmask) {
-                // lane's cells of colour k: xs + O and xs + 2 + O, O = k ^ p0, at
-                // compact places xs / 2 and xs / 2 + 1 (bits 2 lane, 2 lane + 1
-                // of this span's 64)
+                // lane's cells of colour k: x0 + 4 lane + O and + 2 + O,
+                // O = k ^ p0, at compact places 2 lane and 2 lane + 1 of
+                // this span's 64
 #pragma unroll
                 for (int k = 0; k < 2; k++) {
                     const int O = k ^ p0;
@@ -675,33 +685,36 @@ __global__ void __launch_bounds__(256) k_lists_l0(int nx, int ny, int nz, const 
                     if (lane == 16 && w0 + 1 < wpr) m[w0 + 1] = hi;
                 }
             }
-            // (most 128-cell spans hold no listed cell: one vote skips them)
-            if (!__any_sync(0xffffffffu, (nr4 | bf4) != 0)) continue;
             // near-boundary cells by colour: cells i = 0, 2 have colour p0, i = 1, 3 the other
-            const unsigned ms[3] = {p0 == 0 ? nr4 & 0x5u : nr4 & 0xAu, p0 == 0 ? nr4 & 0xAu : nr4 & 0x5u, bf4};
-            // one scan for the three lists: 8-bit fields (a warp lists at most 128 cells of one list)
-            int total;
-            const int excl =
-                warp_excl_scan((int)(__popc(ms[0]) | (__popc(ms[1]) << 8) | (__popc(ms[2]) << 16)), total);
-            int base = 0;
-            if (lane < 3) {
-                const int tl = (total >> (8 * lane)) & 0xFF;
-                int* cnt = lane < 2 ? &count[lane * kNearSegs + seg] : &bf_count[seg];
-                if (tl) base = atomicAdd(cnt, tl);
-            }
+            ms[0] |= (nr4 & 0x5u) << (4 * s);
+            ms[1] |= (nr4 & 0xAu) << (4 * s);
+            ms[2] |= bf4 << (4 * s);
+        }
+        // (most chunks hold no listed cell: one vote skips them)
+        if (!__any_sync(0xffffffffu, (ms[0] | ms[1] | ms[2]) != 0)) continue;
+        // one scan for the three lists, in fields of 10, 10 and 11 bits (a
+        // warp lists at most 256 cells of a colour and 512 next to obstacles)
+        int total;
+        const int excl =
+            warp_excl_scan((int)(__popc(ms[0]) | (__popc(ms[1]) << 10) | (__popc(ms[2]) << 20)), total);
+        int base = 0;
+        if (lane < 3) {
+            const int tl = (total >> (10 * lane)) & (lane < 2 ? 0x3FF : 0x7FF);
+            // (ms[t] holds cells of colour t ^ p0)
+            int* cnt = lane < 2 ? &count[(lane ^ p0) * kNearSegs + seg] : &bf_count[seg];
+            if (tl) base = atomicAdd(cnt, tl);
+        }
 #pragma unroll
-            for (int t = 0; t < 3; t++) {
-                const int bt = __shfl_sync(0xffffffffu, base, t);
-                const unsigned m = ms[t];
-                int* out = t < 2 ? list + (size_t)(t * kNearSegs + seg) * cap : bf_list + (size_t)seg * bf_cap;
-                const int c_out = t < 2 ? cap : bf_cap;
-                int k = bt + ((excl >> (8 * t)) & 0xFF);
-#pragma unroll
-                for (int i = 0; i < 4; i++)
-                    if ((m >> i) & 1u) {
-                        if (k < c_out) out[k] = xs + i + nx * row;
-                        k++;
-                    }
+        for (int t = 0; t < 3; t++) {
+            const int bt = __shfl_sync(0xffffffffu, base, t);
+            const int kl = t < 2 ? t ^ p0 : 2;  // (list 0, 1: colour; 2: next to obstacles)
+            int* out = kl < 2 ? list + (size_t)(kl * kNearSegs + seg) * cap : bf_list + (size_t)seg * bf_cap;
+            const int c_out = kl < 2 ? cap : bf_cap;
+            int k = bt + ((excl >> (10 * t)) & (t < 2 ? 0x3FF : 0x7FF));
+            for (unsigned m = ms[t]; m; m &= m - 1u) {
+                const int b = __ffs(m) - 1;
+                if (k < c_out) out[k] = xb + 128 * (b >> 2) + 4 * lane + (b & 3) + nx * row;
+                k++;
             }
         }
     }
