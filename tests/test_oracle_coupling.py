@@ -84,7 +84,10 @@ def test_overlap_and_wall_cut_are_errors():
 
 def test_reconstruction_has_equilibrium_moments():
     """Uncovered cells get f^eq(rho_0, u_s) of the previous step (Sec. 4.2):
-    density 1 and momentum u_s of the old surface velocity."""
+    density 1 and momentum u_s = V + Omega x (x_c - X) of the old owner's
+    state, the one it was mapped with.  A force and a torque change V and
+    Omega in the update between the two mappings, so a reconstruction from
+    the new velocities (or about the new centre) is off by more than 1e-3."""
     wl = W.single_sphere(n=16, radius=3.0, levels=1)
     wl.v = np.array([[0.6, 0.0, 0.0]])
     wl.w = np.array([[0.0, 0.0, 0.05]])
@@ -92,8 +95,13 @@ def test_reconstruction_has_equilibrium_moments():
     o.map_particles()
     before = o.owner() >= 0
     xs0 = wl.x[0].copy()
-    o.set_forces(np.zeros(3), np.zeros(3))
-    o.advance()  # moves the sphere by V (semi-implicit, F = 0)
+    m = 1.195 * 4.0 / 3.0 * np.pi * 27.0
+    I = 0.4 * m * 9.0
+    dv, dw = np.array([0.1, 0.05, 0.0]), np.array([0.0, 0.0, 0.02])
+    o.set_forces(m * dv, I * dw)
+    o.advance()  # V += F/m, X += V, Omega += T/I (semi-implicit)
+    new = o.particles()
+    np.testing.assert_allclose(new["v"][0], wl.v[0] + dv, rtol=1e-14)
     o.map_particles()
     after = o.owner() >= 0
     uncovered = before & ~after
@@ -101,10 +109,13 @@ def test_reconstruction_has_equilibrium_moments():
     f = o.field(oracle.FIELD_PDF)
     c, w = oracle.lattice()
     for (k, j, i) in zip(*np.nonzero(uncovered)):
-        r = np.array([i + 0.5, j + 0.5, k + 0.5]) - xs0
-        us = wl.v[0] + np.cross(wl.w[0], r)
+        xc = np.array([i + 0.5, j + 0.5, k + 0.5])
+        us = wl.v[0] + np.cross(wl.w[0], xc - xs0)
         assert abs(f[:, k, j, i].sum() - 1.0) < 1e-15
         np.testing.assert_allclose(c.T @ f[:, k, j, i], us, rtol=0, atol=1e-15)
+        # (the new state's surface velocity differs: the test tells them apart)
+        for v, om, X in ((new["v"][0], new["w"][0], xs0), (wl.v[0], wl.w[0], new["x"][0])):
+            assert np.abs(v + np.cross(om, xc - X) - us).max() > 1e-3
 
 
 def _settle(o, steps):
