@@ -345,6 +345,38 @@ def test_coupled_channel_fp64():
         assert r[k] < FP64_TOL, (k, r[k])
 
 
+def _electro_osmotic_channel():
+    """32^3 channel (walls in z, periodic x and y) with no spheres and
+    Dirichlet potentials zeta = 1 and -0.5 on its two walls (the wall
+    condition of Sec. 5.5), lambda_D = 3, E = 2e-3 along x: the field acts on
+    the walls' double layers and drives an electro-osmotic flow."""
+    wl = W.channel(n=32, n_spheres=0, radius=3.0, levels=3, res_rf=1e-10)
+    wl.pot_bc = (0, 0, 0, 0, 1, 1)
+    wl.pot_val = (0.0, 0.0, 0.0, 0.0, 1.0, -0.5)
+    return wl
+
+
+def test_electro_osmotic_channel_without_spheres_fp64():
+    """An empty particle array (the mapping, force and update launches have
+    no work) and charged walls: potential and flow within 1e-12 of the
+    oracle after 20 steps, the flow (up to 0.018) far above FP64 rounding."""
+    p, r = _coupled(_electro_osmotic_channel(), 20)
+    assert r["owner_equal"]
+    for k in ("psi", "u"):
+        assert r[k] < FP64_TOL, (k, r[k])
+    assert np.abs(p.g.field(es.FIELD_U)).max() > 1e-2
+
+
+def test_electro_osmotic_channel_without_spheres_mixed32():
+    """The same channel in MIXED32 after 100 steps: potential and flow within
+    1e-4 of the FP64 oracle."""
+    p, r = _coupled(_electro_osmotic_channel(), 100, precision=es.ES_MIXED32, forced=False)
+    print("relative L2 against the oracle:", {k: float(r[k]) for k in ("psi", "u")})
+    assert r["owner_equal"]
+    for k in ("psi", "u"):
+        assert r[k] < MIXED_TOL, (k, r[k])
+
+
 def test_channel_128_full_size_fp64():
     """The channel configuration at its own size: 128^3, no-slip and
     zero-flux walls at the z faces, periodic x and y, 64 moving spheres of
