@@ -201,6 +201,9 @@ double or_q_from_zeta(double R, double zeta, double kappa, double eps) {
     return 4.0 * M_PI * R * R * sigma;
 }
 
+/* Charge q_p of the electrostatic force F_C = q_p E (Sec. 5.6): the given
+ * total charge of a charge sphere; for a zeta sphere the charge of its
+ * Debye-Hueckel double layer (Eq. SurfChrgZetaRelationDebHuck, above).      */
 static double particle_charge(const or_ctx* c, const or_particle* p) {
     if (p->kind == OR_KIND_CHARGE) return p->q;
     return or_q_from_zeta(p->R, p->zeta, c->P.kappa, c->P.eps);
@@ -379,6 +382,10 @@ static double level_diag(const or_ctx* c, int l, int i, int j, int k) {
     return d;
 }
 
+/* Potential assembly (Sec. 4.3, Eq. DiscrFV, with the boundary treatment of
+ * Sec. 5.4) after a mapping: the cell states of every level, the stencil
+ * diagonals, the Neumann charge of each boundary face and the right-hand
+ * side of the finest level.                                                  */
 static void assemble(or_ctx* c) {
     static const int F[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
     /* level-0 states from the mapping */
@@ -459,6 +466,9 @@ static void assemble(or_ctx* c) {
             }
 }
 
+/* The mapping step of Algorithm 1 (Sec. 4.2, Sec. 5.5): obstacle cells from
+ * the particle positions, PDF reconstruction at the cells the particles
+ * uncovered, the boundary values kept in psi, then the assembly.            */
 int or_map(or_ctx* c) {
     int status = OR_OK;
     memcpy(c->owner_prev, c->owner, sizeof(int) * c->N);
@@ -556,6 +566,11 @@ static void level_residual(or_ctx* c, int l, double* r) {
             }
 }
 
+/* One V-cycle on A_l e = rhs_l from e = 0 (Sec. 5.3 puts a V-cycle where
+ * the red-black SOR sub-sweeps were; its parts are readings, the paper gives
+ * none): nu1 red-black sweeps, the residual restricted as the mean of the 8
+ * children, the cycle on the next level, its correction injected into the
+ * unknown children, nu2 sweeps; coarse_sweeps sweeps on the coarsest level. */
 static void vcycle(or_ctx* c, int l) {
     const int* m = c->ln[l];
     long Nl = (long)m[0] * m[1] * m[2];
@@ -744,6 +759,8 @@ static void gradient_at(const or_ctx* c, int i, int j, int k, double g[3]) {
     for (int a = 0; a < 3; a++) g[a] = 0.5 * (face_value(c, i, j, k, a, +1) - face_value(c, i, j, k, a, -1));
 }
 
+/* The gradient of psi at every unknown cell as the body force uses it
+ * (gradient_at, Sec. 5.6); zero elsewhere.  For the tests.                   */
 void or_gradient(const or_ctx* c, double* g_out) {
     for (int k = 0; k < c->n[2]; k++)
         for (int j = 0; j < c->n[1]; j++)
@@ -857,6 +874,11 @@ static double wall_population(const or_ctx* c, const double* src, int i, int j, 
     return src[(long)opposite(q) * c->N + id];
 }
 
+/* One fused stream-collide step (Sec. 4.1): every fluid cell pulls its
+ * populations from x - e_q (Eq. LBMstreamStep), takes the moving bounce-back
+ * (Eq. LBMMovWall) where x - e_q is an obstacle cell and the wall rule where
+ * it lies beyond a wall, and collides with TRT and the forcing term
+ * (collide_cell); obstacle cells are not updated.                            */
 int or_lbm(or_ctx* c) {
     const double* src = c->f[c->cur];
     double* dst = c->f[1 - c->cur];
