@@ -267,6 +267,28 @@ def suspension(n: int = 512, n_spheres: int = 2880, radius: float = 5.0, seed: i
                           np.full(n_spheres, KIND_CHARGE), np.zeros(n_spheres), q)
 
 
+def paper_node(blocks: Sequence[int] = (2, 4, 2), block: int = 144, levels: int = 6) -> Workload:
+    """The problem of one node in the paper's scaling runs (Sec. 7): blocks of
+    144^3 cells, 2 x 4 x 2 of them a node (288 x 576 x 288 cells), each with
+    4^3 spheres of radius 6 spaced 36 cells apart, the first centred at
+    (19, 19, 19) (1,024 spheres; their obstacle cells cover 1.955 % of the
+    domain, the paper's "about 1.95 %").  Periodic in y; no-slip walls with a
+    zero-flux potential on the x and z faces; zeta spheres, the field along
+    y, 240 steps to RES_RF 4e-6.  Parameters of the scaling runs (Tab.
+    ElectrophorValidSpheres_Parameters): lambda_D = 15.08 cells, tau = 6, and
+    in units of zeta = 10 mV and dx = 5 nm the field E_y,Sc = 38.0e6 V/m is
+    38.0e6 * 5e-9 / 0.01 = 0.019."""
+    dims = [block * b for b in blocks]
+    c = [19.0 + 36.0 * np.arange(d // 36) for d in dims]
+    Z, Y, X = np.meshgrid(c[2], c[1], c[0], indexing="ij")
+    centres = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    n = centres.shape[0]
+    wl = Workload(name=f"paper_node_{dims[0]}x{dims[1]}x{dims[2]}_{n}xR6", dims=dims, periodic=(0, 1, 0),
+                  tau=6.0, kappa=1.0 / 15.08, eps=1.0, E_ext=(0.0, 0.019, 0.0), levels=levels, res_rf=4e-6,
+                  steps=240, coarse_sweeps=8)
+    return _set_particles(wl, centres, np.full(n, 6.0), np.full(n, KIND_ZETA), np.ones(n), np.zeros(n))
+
+
 def suspension_sample(n: int, seed: int = 3, radius: float = 5.0, levels: int = 4) -> Workload:
     """A sub-box of the 512^3 suspension with the same sphere number density."""
     n_spheres = max(1, int(round(2880 * (n / 512.0) ** 3)))
